@@ -1,0 +1,227 @@
+"""ctypes wrapper around the plain-C oracle (``rod_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY.  Arrays follow the component-major layout of ``rodgen``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SOURCES = ["rod_oracle.c"]
+_LIB_NAME = "liboracle.so"
+_lock = threading.Lock()
+_lib = None
+
+
+def oracle_library_path() -> str:
+    return os.path.join(_HERE, _LIB_NAME)
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no FP contraction).  Returns the .so path."""
+    out = oracle_library_path()
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES] + [os.path.join(_HERE, "rod_oracle.h")]
+    if not force and os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(s) for s in srcs):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-Wall",
+           "-o", tmp] + [os.path.join(_HERE, s) for s in _SOURCES] + ["-lm"]
+    subprocess.run(cmd, check=True, cwd=_HERE)
+    os.replace(tmp, out)
+    return out
+
+
+class _Params(C.Structure):
+    _fields_ = [
+        ("n_rods", C.c_int32),
+        ("n_elem", C.c_void_p),
+        ("rest_len", C.c_void_p),
+        ("radius", C.c_void_p),
+        ("youngs", C.c_void_p),
+        ("shear_mod", C.c_void_p),
+        ("density", C.c_void_p),
+        ("alpha_c", C.c_double),
+        ("clamp_base", C.c_void_p),
+        ("rest_kappa", C.c_void_p),
+        ("rest_sigma", C.c_void_p),
+        ("gravity", C.c_double * 3),
+        ("nu_damp", C.c_double),
+        ("stokes_gamma", C.c_double),
+        ("tip_force", C.c_void_p),
+        ("act_amp", C.c_void_p),
+        ("act_period", C.c_void_p),
+        ("act_phase", C.c_void_p),
+        ("elem_couple", C.c_void_p),
+        ("contact", C.c_int32),
+        ("contact_k", C.c_double),
+        ("contact_c", C.c_double),
+        ("cell_size", C.c_double),
+        ("broad_phase", C.c_int32),
+    ]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build_oracle())
+            P = C.POINTER(_Params)
+            d = C.c_void_p
+            lib.orc_rhs.argtypes = [P, C.c_double, d, d, d, d, d, d]
+            lib.orc_step.argtypes = [P, C.c_double, C.c_double, C.c_int64, d, d, d, d]
+            lib.orc_energy.argtypes = [P, d, d, d, d]
+            lib.orc_energy.restype = C.c_double
+            lib.orc_strains.argtypes = [P, d, d, d, d, d, d]
+            lib.orc_contact_forces.argtypes = [P, d, d, d]
+            lib.orc_contact_pairs.argtypes = [P, d, d, C.c_int64]
+            lib.orc_contact_pairs.restype = C.c_int64
+            lib.orc_segment_closest.argtypes = [d, d, d, d, d, d]
+            lib.orc_rot_exp.argtypes = [d, d]
+            lib.orc_rot_log.argtypes = [d, d]
+            lib.orc_orthonormality_error.argtypes = [P, d]
+            lib.orc_orthonormality_error.restype = C.c_double
+            lib.orc_last_error.restype = C.c_char_p
+            lib.orc_set_mutation.argtypes = [C.c_int]
+            _lib = lib
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+class Oracle:
+    """Oracle bound to one ``rodgen.RodProblem`` description (parameters, not state)."""
+
+    def __init__(self, problem, broad_phase: int = 1):
+        self.lib = _load()
+        p = problem
+        self.problem = p
+        # keep every array alive for the lifetime of the params struct
+        self._keep = {
+            "n_elem": np.ascontiguousarray(p.n_elem, dtype=np.int32),
+            "rest_len": _f64(p.rest_len),
+            "radius": _f64(p.radius),
+            "youngs": _f64(p.youngs),
+            "shear_mod": _f64(p.shear_mod),
+            "density": _f64(p.density),
+            "clamp_base": None if p.clamp_base is None else np.ascontiguousarray(p.clamp_base, dtype=np.int8),
+            "rest_kappa": None if p.rest_kappa is None else _f64(p.rest_kappa),
+            "rest_sigma": None if p.rest_sigma is None else _f64(p.rest_sigma),
+            "tip_force": None if p.tip_force is None else _f64(p.tip_force),
+            "act_amp": None if p.act_amp is None else _f64(p.act_amp),
+            "act_period": None if p.act_period is None else _f64(p.act_period),
+            "act_phase": None if p.act_phase is None else _f64(p.act_phase),
+            "elem_couple": None if p.elem_couple is None else _f64(p.elem_couple),
+        }
+        k = self._keep
+        prm = _Params()
+        prm.n_rods = p.n_rods
+        for name in ("n_elem", "rest_len", "radius", "youngs", "shear_mod", "density", "clamp_base",
+                     "rest_kappa", "rest_sigma", "tip_force", "act_amp", "act_period", "act_phase",
+                     "elem_couple"):
+            setattr(prm, name, _ptr(k[name]))
+        prm.alpha_c = p.alpha_c
+        prm.gravity = (C.c_double * 3)(*[float(g) for g in p.gravity])
+        prm.nu_damp = p.nu_damp
+        prm.stokes_gamma = p.stokes_gamma
+        prm.contact = 1 if p.contact else 0
+        prm.contact_k = p.contact_k
+        prm.contact_c = p.contact_c
+        prm.cell_size = p.cell_size
+        prm.broad_phase = broad_phase
+        self.params = prm
+        self.N, self.E, self.V = p.n_nodes, p.n_elems, p.n_voronoi
+
+    def _check(self, rc):
+        if rc != 0:
+            raise RuntimeError("oracle: " + self.lib.orc_last_error().decode())
+
+    def set_broad_phase(self, mode: int):
+        self.params.broad_phase = mode
+
+    def rhs(self, x, v, Q, w, t=0.0):
+        x, v, Q, w = map(_f64, (x, v, Q, w))
+        av = np.empty((3, self.N))
+        aw = np.empty((3, self.E))
+        self._check(self.lib.orc_rhs(C.byref(self.params), t, _ptr(x), _ptr(v), _ptr(Q), _ptr(w), _ptr(av), _ptr(aw)))
+        return av, aw
+
+    def step(self, x, v, Q, w, dt, n_steps, t=0.0):
+        """Returns new copies of the state after ``n_steps`` steps."""
+        x, v, Q, w = (np.array(a, dtype=np.float64, order="C", copy=True) for a in (x, v, Q, w))
+        self._check(self.lib.orc_step(C.byref(self.params), t, dt, int(n_steps), _ptr(x), _ptr(v), _ptr(Q), _ptr(w)))
+        return x, v, Q, w
+
+    def energy(self, x, v, Q, w):
+        x, v, Q, w = map(_f64, (x, v, Q, w))
+        return self.lib.orc_energy(C.byref(self.params), _ptr(x), _ptr(v), _ptr(Q), _ptr(w))
+
+    def strains(self, x, Q):
+        x, Q = map(_f64, (x, Q))
+        sig = np.empty((3, self.E))
+        kap = np.empty((3, max(self.V, 1)))
+        dil = np.empty(self.E)
+        vdil = np.empty(max(self.V, 1))
+        self._check(self.lib.orc_strains(C.byref(self.params), _ptr(x), _ptr(Q), _ptr(sig), _ptr(kap), _ptr(dil), _ptr(vdil)))
+        return sig, kap[:, : self.V], dil, vdil[: self.V]
+
+    def contact_forces(self, x, v=None):
+        x = _f64(x)
+        v = None if v is None else _f64(v)
+        f = np.empty((3, self.N))
+        self._check(self.lib.orc_contact_forces(C.byref(self.params), _ptr(x), _ptr(f), _ptr(v)))
+        return f
+
+    def contact_pairs(self, x, cap=1 << 20):
+        x = _f64(x)
+        pairs = np.empty((cap, 2), dtype=np.int64)
+        n = self.lib.orc_contact_pairs(C.byref(self.params), _ptr(x), _ptr(pairs), cap)
+        if n < 0:
+            self._check(-1)
+        if n > cap:
+            return self.contact_pairs(x, cap=int(n))
+        return pairs[:n].copy()
+
+    def orthonormality_error(self, Q):
+        Q = _f64(Q)
+        return self.lib.orc_orthonormality_error(C.byref(self.params), _ptr(Q))
+
+
+def rot_exp(phi):
+    lib = _load()
+    phi = _f64(phi)
+    R = np.empty(9)
+    lib.orc_rot_exp(_ptr(phi), _ptr(R))
+    return R.reshape(3, 3)
+
+
+def rot_log(R):
+    lib = _load()
+    R = _f64(np.asarray(R).reshape(9))
+    phi = np.empty(3)
+    lib.orc_rot_log(_ptr(R), _ptr(phi))
+    return phi
+
+
+def segment_closest(p0, p1, q0, q1):
+    lib = _load()
+    a = [_f64(z) for z in (p0, p1, q0, q1)]
+    s = np.zeros(1)
+    u = np.zeros(1)
+    lib.orc_segment_closest(*[_ptr(z) for z in a], _ptr(s), _ptr(u))
+    return float(s[0]), float(u[0])
+
+
+def set_mutation(mid: int) -> None:
+    """Plant numbered mistake ``mid`` in the oracle (0 removes it).  Pin-strength tests only."""
+    _load().orc_set_mutation(int(mid))

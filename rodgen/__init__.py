@@ -1,0 +1,330 @@
+"""Seeded synthetic rod workloads.
+
+This module only builds inputs: rod counts and lengths, materials, loads, and an initial
+state (straight rods, orthonormal director frames, optional random rigid motion).  It
+holds none of the time-stepping method's arithmetic; both the CPU oracle tests and the
+CUDA path consume what it produces.
+
+Workloads (sizes as in the paper's case studies, synthetic stand-ins for their data):
+  * ``cantilever``     -- one clamped rod with a transverse tip force and linear damping;
+  * ``cilia_carpet``   -- a square carpet of clamped upright rods driven by a sinusoidal
+                          base couple with seeded phases and Stokes drag (the magnetic
+                          cilia carpets of the results section are the model for it);
+  * ``random_packing`` -- free rods with seeded lengths, positions and orientations in a
+                          box, with gravity and rod-rod contact (the fibrous packings of
+                          the results section are the model for it);
+  * ``adjoint_batch``  -- clamped rods with seeded rest curvatures, element couples and
+                          tip targets (parameters of the gradient workload).
+State layout: component-major arrays, x/v of shape (3, nodes), Q of shape (9, elements)
+with Q[3a+b, i] the b-th lab component of director a+1, w of shape (3, elements).
+"""
+from __future__ import annotations
+
+import dataclasses
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+__all__ = [
+    "RodProblem",
+    "cantilever",
+    "cilia_carpet",
+    "random_packing",
+    "adjoint_batch",
+    "perturbed",
+    "quat_to_matrix",
+]
+
+
+@dataclass
+class RodProblem:
+    name: str
+    n_elem: np.ndarray                 # (R,) int32
+    rest_len: np.ndarray               # (E,)
+    radius: np.ndarray                 # (R,)
+    youngs: np.ndarray                 # (R,)
+    shear_mod: np.ndarray              # (R,)
+    density: np.ndarray                # (R,)
+    x: np.ndarray                      # (3, N)
+    v: np.ndarray                      # (3, N)
+    Q: np.ndarray                      # (9, E)
+    w: np.ndarray                      # (3, E)
+    alpha_c: float = 4.0 / 3.0
+    clamp_base: Optional[np.ndarray] = None   # (R,) int8
+    rest_kappa: Optional[np.ndarray] = None   # (3, V)
+    rest_sigma: Optional[np.ndarray] = None   # (3, E)
+    gravity: np.ndarray = field(default_factory=lambda: np.zeros(3))
+    nu_damp: float = 0.0
+    stokes_gamma: float = 0.0
+    tip_force: Optional[np.ndarray] = None    # (3, R)
+    act_amp: Optional[np.ndarray] = None      # (R,)
+    act_period: Optional[np.ndarray] = None   # (R,)
+    act_phase: Optional[np.ndarray] = None    # (R,)
+    elem_couple: Optional[np.ndarray] = None  # (3, E)
+    contact: bool = False
+    contact_k: float = 0.0
+    contact_c: float = 0.0
+    cell_size: float = 0.0
+    dt: float = 1e-5
+    n_steps: int = 1
+    t0: float = 0.0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_rods(self) -> int:
+        return int(self.n_elem.shape[0])
+
+    @property
+    def n_elems(self) -> int:
+        return int(self.n_elem.sum())
+
+    @property
+    def n_nodes(self) -> int:
+        return self.n_elems + self.n_rods
+
+    @property
+    def n_voronoi(self) -> int:
+        return self.n_elems - self.n_rods
+
+    def node_offsets(self) -> np.ndarray:
+        return np.concatenate([[0], np.cumsum(self.n_elem + 1)]).astype(np.int64)
+
+    def elem_offsets(self) -> np.ndarray:
+        return np.concatenate([[0], np.cumsum(self.n_elem)]).astype(np.int64)
+
+    def state(self):
+        return self.x.copy(), self.v.copy(), self.Q.copy(), self.w.copy()
+
+    def replace(self, **kw) -> "RodProblem":
+        return dataclasses.replace(self, **kw)
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def quat_to_matrix(q: np.ndarray) -> np.ndarray:
+    """Rotation matrices (..., 3, 3) from unit quaternions (..., 4) = (w, x, y, z)."""
+    q = q / np.linalg.norm(q, axis=-1, keepdims=True)
+    w, x, y, z = q[..., 0], q[..., 1], q[..., 2], q[..., 3]
+    R = np.empty(q.shape[:-1] + (3, 3))
+    R[..., 0, 0] = 1 - 2 * (y * y + z * z)
+    R[..., 0, 1] = 2 * (x * y - w * z)
+    R[..., 0, 2] = 2 * (x * z + w * y)
+    R[..., 1, 0] = 2 * (x * y + w * z)
+    R[..., 1, 1] = 1 - 2 * (x * x + z * z)
+    R[..., 1, 2] = 2 * (y * z - w * x)
+    R[..., 2, 0] = 2 * (x * z - w * y)
+    R[..., 2, 1] = 2 * (y * z + w * x)
+    R[..., 2, 2] = 1 - 2 * (x * x + y * y)
+    return R
+
+
+def _frames(d3: np.ndarray, ref: np.ndarray) -> np.ndarray:
+    """Director rows (d1, d2, d3) for unit tangents d3 (R, 3); d1 is ref projected off d3."""
+    d1 = ref - (ref * d3).sum(-1, keepdims=True) * d3
+    d1 /= np.linalg.norm(d1, axis=-1, keepdims=True)
+    d2 = np.cross(d3, d1)
+    return np.stack([d1, d2, d3], axis=1)  # (R, 3 rows, 3 comps)
+
+
+def _straight_rods(n_elem, rest_len, base, d3, ref):
+    """Nodes along straight lines from ``base`` in direction ``d3``; one frame per rod."""
+    R = n_elem.shape[0]
+    E = int(n_elem.sum())
+    N = E + R
+    x = np.empty((3, N))
+    Q = np.empty((9, E))
+    frames = _frames(d3, ref)
+    node0 = 0
+    elem0 = 0
+    for r in range(R):
+        n = int(n_elem[r])
+        s = np.concatenate([[0.0], np.cumsum(rest_len[elem0:elem0 + n])])
+        x[:, node0:node0 + n + 1] = base[r][:, None] + d3[r][:, None] * s[None, :]
+        Q[:, elem0:elem0 + n] = frames[r].reshape(9)[:, None]
+        node0 += n + 1
+        elem0 += n
+    return x, Q
+
+
+def _uniform(R, val):
+    return np.full(R, float(val))
+
+
+# ----------------------------------------------------------------------------- workloads
+
+def cantilever(n: int = 100, length: float = 1.0, radius: float = 0.01, youngs: float = 1e6,
+               tip_force: float = 1e-2, nu: float = 0.1, dt: float = 1e-5, n_steps: int = 10_000,
+               shear_ratio: float = 1.5, density: float = 1000.0) -> RodProblem:
+    """One rod along lab z, clamped at node 0, tip force along lab y."""
+    n_elem = np.array([n], dtype=np.int32)
+    rest_len = np.full(n, length / n)
+    d3 = np.array([[0.0, 0.0, 1.0]])
+    x, Q = _straight_rods(n_elem, rest_len, np.zeros((1, 3)), d3, np.array([[1.0, 0.0, 0.0]]))
+    E = n
+    return RodProblem(
+        name=f"cantilever_n{n}", n_elem=n_elem, rest_len=rest_len,
+        radius=_uniform(1, radius), youngs=_uniform(1, youngs), shear_mod=_uniform(1, youngs / shear_ratio),
+        density=_uniform(1, density), x=x, v=np.zeros_like(x), Q=Q, w=np.zeros((3, E)),
+        clamp_base=np.ones(1, dtype=np.int8), nu_damp=nu,
+        tip_force=np.array([[0.0], [tip_force], [0.0]]), dt=dt, n_steps=n_steps)
+
+
+def cilia_carpet(side: int = 64, n: int = 50, spacing: float = 0.05, length: float = 0.2,
+                 radius: float = 0.005, youngs: float = 1e6, density: float = 1000.0,
+                 period: float = 1.0, amp_factor: float = 0.5, gamma: float = 1.0,
+                 dt: float = 1e-5, n_steps: int = 10_000, seed: int = 1234) -> RodProblem:
+    """side x side upright clamped rods on a square grid, sinusoidal base couple about d1.
+
+    Amplitude A0 = amp_factor * E I / L, phases uniform in [0, 2 pi) from ``seed``."""
+    rng = np.random.default_rng(seed)
+    R = side * side
+    n_elem = np.full(R, n, dtype=np.int32)
+    rest_len = np.full(R * n, length / n)
+    gx, gy = np.meshgrid(np.arange(side) * spacing, np.arange(side) * spacing, indexing="ij")
+    base = np.stack([gx.ravel(), gy.ravel(), np.zeros(R)], axis=1)
+    d3 = np.tile([0.0, 0.0, 1.0], (R, 1))
+    x, Q = _straight_rods(n_elem, rest_len, base, d3, np.tile([1.0, 0.0, 0.0], (R, 1)))
+    I = np.pi * radius ** 4 / 4
+    amp = amp_factor * youngs * I / length
+    return RodProblem(
+        name=f"cilia_carpet_{side}x{side}_n{n}", n_elem=n_elem, rest_len=rest_len,
+        radius=_uniform(R, radius), youngs=_uniform(R, youngs), shear_mod=_uniform(R, youngs / 1.5),
+        density=_uniform(R, density), x=x, v=np.zeros_like(x), Q=Q, w=np.zeros((3, R * n)),
+        clamp_base=np.ones(R, dtype=np.int8), stokes_gamma=gamma,
+        act_amp=_uniform(R, amp), act_period=_uniform(R, period),
+        act_phase=rng.uniform(0.0, 2 * np.pi, R), dt=dt, n_steps=n_steps)
+
+
+def random_packing(n_rods: int = 10_000, nmin: int = 16, nmax: int = 256, box: float = 1.0,
+                   rest_len: float = 1e-3, radius: float = 0.005, youngs: float = 1e6,
+                   density: float = 1000.0, speed: float = 0.5, spin: float = 0.0,
+                   contact_k: float = 1e4, contact_c: float = 10.0, gravity: float = 9.81,
+                   dt: float = 5e-6, n_steps: int = 5000, seed: int = 1234,
+                   allow_overlap: bool = False, margin: float = 5e-4) -> RodProblem:
+    """Free straight rods, lengths n ~ U{nmin..nmax} elements of ``rest_len``, centres uniform in
+    the box, axes uniform on the sphere, a rigid velocity uniform in [-speed, speed]^3 per rod.
+
+    Unless ``allow_overlap``, rods are placed one by one (longest first) and a candidate is
+    redrawn while any of its sample points lies closer than 2 r + sample spacing + margin to
+    a sample point of an already placed rod, so the initial packing has no overlap."""
+    rng = np.random.default_rng(seed)
+    n_elem = rng.integers(nmin, nmax + 1, n_rods).astype(np.int32)
+    lengths = n_elem * rest_len
+    centers = np.empty((n_rods, 3))
+    axes = np.empty((n_rods, 3))
+
+    def draw_axis():
+        a = rng.normal(size=3)
+        return a / np.linalg.norm(a)
+
+    if allow_overlap:
+        for r in range(n_rods):
+            centers[r] = rng.uniform(0.0, box, 3)
+            axes[r] = draw_axis()
+    else:
+        spacing = radius
+        thresh = 2 * radius + spacing + margin
+        h = thresh
+        dim = int(np.ceil(box / h)) + 3
+        cap = 24
+        grid = np.full((dim, dim, dim, cap, 3), 1e9)
+        count = np.zeros((dim, dim, dim), dtype=np.int64)
+        offs = np.array([(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)])
+        order = np.argsort(-lengths, kind="stable")
+        for r in order:
+            L = lengths[r]
+            m = int(np.floor(L / spacing)) + 1
+            s = np.linspace(-0.5 * L, 0.5 * L, m)
+            for attempt in range(10_000):
+                c = rng.uniform(0.0, box, 3)
+                a = draw_axis()
+                pts = c[None, :] + s[:, None] * a[None, :]
+                cell = np.floor(pts / h).astype(np.int64) + 1
+                cell = np.clip(cell, 1, dim - 2)
+                nb = cell[:, None, :] + offs[None, :, :]             # (m, 27, 3)
+                cand = grid[nb[..., 0], nb[..., 1], nb[..., 2]]       # (m, 27, cap, 3)
+                d2 = ((cand - pts[:, None, None, :]) ** 2).sum(-1)
+                if d2.min() >= thresh * thresh:
+                    break
+            else:
+                raise RuntimeError("random_packing: could not place a rod; lower the density")
+            # insert sample points
+            for q in range(m):
+                i, j, k = cell[q]
+                cnt = count[i, j, k]
+                if cnt >= cap:
+                    raise RuntimeError("random_packing: grid cell capacity exceeded")
+                grid[i, j, k, cnt] = pts[q]
+                count[i, j, k] = cnt + 1
+            centers[r] = c
+            axes[r] = a
+    base = centers - 0.5 * lengths[:, None] * axes
+    # reference direction for d1: a seeded random vector, re-drawn when nearly parallel
+    ref = rng.normal(size=(n_rods, 3))
+    par = np.abs((ref / np.linalg.norm(ref, axis=1, keepdims=True) * axes).sum(1)) > 0.99
+    ref[par] = np.cross(axes[par], [1.0, 0.0, 0.0]) + np.cross(axes[par], [0.0, 1.0, 0.0])
+    rl = np.full(int(n_elem.sum()), rest_len)
+    x, Q = _straight_rods(n_elem, rl, base, axes, ref)
+    vel = rng.uniform(-speed, speed, (n_rods, 3))
+    node_counts = n_elem + 1
+    v = np.repeat(vel, node_counts, axis=0).T.copy()
+    w = np.zeros((3, int(n_elem.sum())))
+    if spin > 0:
+        w[:] = np.repeat(rng.uniform(-spin, spin, (n_rods, 3)), n_elem, axis=0).T
+    R = n_rods
+    return RodProblem(
+        name=f"random_packing_{n_rods}", n_elem=n_elem, rest_len=rl,
+        radius=_uniform(R, radius), youngs=_uniform(R, youngs), shear_mod=_uniform(R, youngs / 1.5),
+        density=_uniform(R, density), x=x, v=np.ascontiguousarray(v), Q=Q, w=w,
+        gravity=np.array([0.0, 0.0, -gravity]), contact=True, contact_k=contact_k,
+        contact_c=contact_c, cell_size=2 * radius, dt=dt, n_steps=n_steps)
+
+
+def adjoint_batch(n_rods: int = 1024, n: int = 64, length: float = 0.2, radius: float = 0.005,
+                  youngs: float = 1e6, density: float = 1000.0, kappa_scale: float = 0.5,
+                  couple_scale: float = 1e-6, target_scale: float = 0.01, spacing: float = 0.05,
+                  dt: float = 1e-5, n_steps: int = 2000, seed: int = 1234) -> RodProblem:
+    """Clamped upright rods with seeded rest curvature (N(0, kappa_scale) 1/m), constant element
+    couples (N(0, couple_scale) N m) and tip targets (undeformed tip + N(0, target_scale) m)."""
+    rng = np.random.default_rng(seed)
+    side = int(np.ceil(np.sqrt(n_rods)))
+    n_elem = np.full(n_rods, n, dtype=np.int32)
+    rest_len = np.full(n_rods * n, length / n)
+    gx, gy = np.meshgrid(np.arange(side) * spacing, np.arange(side) * spacing, indexing="ij")
+    base = np.stack([gx.ravel(), gy.ravel(), np.zeros(side * side)], axis=1)[:n_rods]
+    d3 = np.tile([0.0, 0.0, 1.0], (n_rods, 1))
+    x, Q = _straight_rods(n_elem, rest_len, base, d3, np.tile([1.0, 0.0, 0.0], (n_rods, 1)))
+    E = n_rods * n
+    V = E - n_rods
+    R = n_rods
+    kappa0 = rng.normal(0.0, kappa_scale, (3, V))
+    couples = rng.normal(0.0, couple_scale, (3, E))
+    tips = x[:, np.cumsum(n_elem + 1) - 1]
+    targets = tips + rng.normal(0.0, target_scale, (3, R))
+    return RodProblem(
+        name=f"adjoint_{n_rods}x{n}", n_elem=n_elem, rest_len=rest_len,
+        radius=_uniform(R, radius), youngs=_uniform(R, youngs), shear_mod=_uniform(R, youngs / 1.5),
+        density=_uniform(R, density), x=x, v=np.zeros_like(x), Q=Q, w=np.zeros((3, E)),
+        clamp_base=np.ones(R, dtype=np.int8), rest_kappa=kappa0, elem_couple=couples,
+        dt=dt, n_steps=n_steps, extra={"targets": targets})
+
+
+def perturbed(p: RodProblem, seed: int = 7, pos: float = 1e-3, vel: float = 0.1, rot: float = 0.05,
+              omega: float = 5.0) -> RodProblem:
+    """Copy of ``p`` with seeded random perturbations of every state array (positions by
+    ``pos`` times the element rest length, velocities, director rotations by angles of about
+    ``rot`` rad built from random unit quaternions, angular velocities)."""
+    rng = np.random.default_rng(seed)
+    x, v, Q, w = p.state()
+    N, E = x.shape[1], Q.shape[1]
+    scale = np.median(p.rest_len)
+    x = x + rng.normal(0.0, pos * scale, x.shape)
+    v = v + rng.normal(0.0, vel, v.shape)
+    q = np.concatenate([np.ones((E, 1)), rng.normal(0.0, 0.5 * rot, (E, 3))], axis=1)
+    Rm = quat_to_matrix(q)                                    # (E, 3, 3)
+    Qm = Q.T.reshape(E, 3, 3)
+    Qn = np.einsum("eab,ebc->eac", Qm, Rm.transpose(0, 2, 1))  # rows rotated: d_a <- R d_a
+    Q = Qn.reshape(E, 9).T.copy()
+    w = w + rng.normal(0.0, omega, w.shape)
+    return p.replace(x=x, v=v, Q=Q, w=w)

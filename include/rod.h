@@ -1,0 +1,145 @@
+/*
+ * rod.h -- C ABI of the GB300 (sm_103a) Cosserat-rod library (librod.so).
+ *
+ * One FP64 explicit time step over an ensemble of discrete Cosserat rods:
+ *   strains sigma = Q(r' - d3) and curvature kappa = ax(Q dQ^T/ds) (Methods, "Cosserat rod
+ *   dynamics"), linear and angular momentum balance (Methods, Eq. 1a, Eq. 1b), external,
+ *   damping and drag loads (f, c of Eq. 1), rod-rod contact by a normal spring-dashpot over a
+ *   uniform cell list (Results, "Fibrous granular materials", Fig. 2e), advanced by a
+ *   multi-stage symplectic (position Verlet) scheme with kinematic constraints after every
+ *   stage and an exponential-map director update (Results, "Performance-oriented software
+ *   design").
+ *
+ * Conventions shared by every call
+ *   - Rods are packed one after another ("CSR order"): rod r has n_r elements, n_r + 1
+ *     nodes and n_r - 1 Voronoi points.  N = sum(n_r + 1), E = sum(n_r), V = E - n_rods.
+ *   - Every per-item vector is stored component-major: x[c * N + j], c = 0, 1, 2.
+ *   - Directors: Q[(3a + b) * E + i] is the b-th lab component of director d_{a+1} of element
+ *     i; the rows of the director matrix are d1, d2, d3 (proper orthogonal).
+ *   - Angular velocities w and couples are in the local (director) frame; positions,
+ *     velocities and forces in the lab frame.  SI units.
+ *   - Every call returns a rod_status and never aborts.  rod_last_error() returns a
+ *     thread-local message for the last failing call of the calling thread.
+ *   - The library owns all device memory it allocates; caller buffers are only read or
+ *     written during the call (or, for on_device copies, on the system's stream).
+ *   - Device errors (non-finite state, a segment longer than the contact grid allows,
+ *     a contact table overflow, a bounded wait that ran out) latch into a device error word
+ *     that rod_system_step() reports after it synchronises; rod_system_set_state() clears it.
+ */
+#ifndef ROD_H
+#define ROD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rod_system rod_system; /* opaque */
+
+typedef enum {
+  ROD_OK = 0,
+  ROD_ERR_ARG = -1,       /* invalid argument or description */
+  ROD_ERR_CUDA = -2,      /* a CUDA runtime call failed (message has the CUDA error) */
+  ROD_ERR_NONFINITE = -3, /* the state became NaN/Inf */
+  ROD_ERR_TIMEOUT = -4,   /* a bounded device wait ran out */
+  ROD_ERR_OVERFLOW = -5,  /* contact grid or table capacity exceeded */
+  ROD_ERR_STATE = -6      /* call not valid in the current state (e.g. no state set) */
+} rod_status;
+
+/* Description of the ensemble (Methods: rho, A, E, G, alpha_c, I, B, S, f, c).
+ * All pointers are host pointers; the library copies what it needs during create. */
+typedef struct {
+  int32_t n_rods;
+  const int32_t* n_elem;      /* [n_rods] elements per rod, >= 1 */
+  const double* rest_len;     /* [E] element rest lengths (> 0) */
+  const double* radius;       /* [n_rods] circular cross-section radius */
+  const double* youngs;       /* [n_rods] Young's modulus E */
+  const double* shear_mod;    /* [n_rods] shear modulus G */
+  const double* density;      /* [n_rods] volumetric density rho */
+  double alpha_c;             /* shear correction coefficient (4/3 for a circle) */
+  const int8_t* clamp_base;   /* [n_rods] or NULL: 1 = node 0 and element 0 held at the state
+                                 given to rod_system_set_state */
+  const double* rest_kappa;   /* [3*V] or NULL: rest curvature (local frame) */
+  const double* rest_sigma;   /* [3*E] or NULL: rest shear/stretch strain (local frame) */
+  double gravity[3];          /* body acceleration (lab) */
+  double nu_damp;             /* linear damping: force -nu v and couple -nu (I/A) w per length */
+  double stokes_gamma;        /* isotropic drag: force -gamma v per length */
+  const double* tip_force;    /* [3*n_rods] or NULL: constant lab force on each rod's last node */
+  const double* act_amp;      /* [n_rods] or NULL: base couple A sin(2 pi t / T + phi) about d1 on the
+                                 first element not held by the clamp */
+  const double* act_period;   /* [n_rods] T > 0 (read when act_amp is set) */
+  const double* act_phase;    /* [n_rods] phi (read when act_amp is set) */
+  const double* elem_couple;  /* [3*E] or NULL: constant local couple per element */
+  void* cuda_stream;          /* cudaStream_t to run on, or NULL for a library-created stream */
+} rod_system_desc;
+
+/* Create a system; validates the description (ROD_ERR_ARG with a message on failure).
+ * Rods longer than rod_max_elements_per_rod() are rejected. */
+rod_status rod_system_create(const rod_system_desc* desc, rod_system** out);
+
+/* Free the system and all its device memory (NULL is accepted). */
+rod_status rod_system_destroy(rod_system* sys);
+
+/* Sizes of the packed arrays. */
+rod_status rod_system_sizes(const rod_system* sys, int64_t* n_nodes, int64_t* n_elems, int64_t* n_voronoi);
+
+/* Set the state: x, v [3*N], Q [9*E], w [3*E] in the layout above.  on_device = 0: host
+ * pointers, copied synchronously; on_device = 1: device pointers, copied on the system's
+ * stream (the caller keeps them valid until the stream reaches the copy).  Records the clamp
+ * values, resets the simulated time to 0 and clears the device error word. */
+rod_status rod_system_set_state(rod_system* sys, const double* x, const double* v, const double* Q,
+                                const double* w, int on_device);
+
+/* Read the state back (same layout / on_device meaning; host copies synchronise). */
+rod_status rod_system_get_state(rod_system* sys, double* x, double* v, double* Q, double* w, int on_device);
+
+/* Simulated time of the current state (advanced by dt per step; reset by set_state). */
+rod_status rod_system_set_time(rod_system* sys, double t);
+rod_status rod_system_get_time(const rod_system* sys, double* t);
+
+/* Advance n_steps position-Verlet steps of size dt (> 0).  Enqueued on the system's stream;
+ * the call synchronises that stream at the end and returns the device error word
+ * (ROD_ERR_NONFINITE / ROD_ERR_OVERFLOW / ROD_ERR_TIMEOUT) if one was raised. */
+rod_status rod_system_step(rod_system* sys, int64_t n_steps, double dt);
+
+/* Same as rod_system_step but returns as soon as the work is enqueued; call
+ * rod_system_sync() to wait and read the error word. */
+rod_status rod_system_step_async(rod_system* sys, int64_t n_steps, double dt);
+rod_status rod_system_sync(rod_system* sys);
+
+/* Rod-rod contact (a8-a9 of the step): enable = 0 disables it.  k: spring stiffness (N/m),
+ * c: dashpot coefficient (N s/m), cell_size: requested cell edge; the grid uses
+ * max(cell_size, 2 r_max + (1 + margin) l_max) where l_max is the longest element of the
+ * state given to the next set_state (a longer element later raises ROD_ERR_OVERFLOW), over
+ * the bounding box of that state grown by box_margin (m) on each side (segments leaving it
+ * are clamped into the boundary cells, which keeps the pair search exact). */
+rod_status rod_system_contact_config(rod_system* sys, int enable, double k, double c, double cell_size);
+
+/* Right-hand side at the current state and time t: node accelerations acc_v [3*N] and
+ * element angular accelerations acc_w [3*E] (constraints on rates applied: clamped node 0
+ * and element 0 read zero), contact forces included when enabled.  Device pointers. */
+rod_status rod_system_rhs(rod_system* sys, double t, double* acc_v, double* acc_w);
+
+/* Contact forces on the nodes [3*N] at the current state (zero when contact is off). Device pointer. */
+rod_status rod_system_contact_forces(rod_system* sys, double* f);
+
+/* Launch shape used by the step kernels: elements per thread block and threads per block
+ * (0 = choose by the built-in autotuner on the next step).  Returns ROD_ERR_ARG if the shape
+ * cannot hold the longest rod. */
+rod_status rod_system_set_launch(rod_system* sys, int32_t elems_per_block, int32_t threads_per_block);
+rod_status rod_system_get_launch(const rod_system* sys, int32_t* elems_per_block, int32_t* threads_per_block);
+
+/* Longest rod (elements) one thread block can hold with the largest supported shape. */
+int32_t rod_max_elements_per_rod(void);
+
+/* Thread-local message of the last failing call. */
+const char* rod_last_error(void);
+
+/* Library version string. */
+const char* rod_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,270 @@
+"""ctypes binding of librod (include/rod.h): argument marshalling only.
+
+Every step of the rod method runs in the CUDA library; this module converts arrays to
+pointers, keeps them alive for the duration of a call and turns status codes into
+exceptions.  PyTorch provides device memory (for device-side state transfers and for the
+outputs of the debug entry points) and the CUDA stream.  There is no CPU fallback: if the
+library cannot be loaded, importing or using this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBRARY_PATH = os.path.join(_HERE, "librod.so")
+
+ROD_OK = 0
+STATUS_NAMES = {0: "ROD_OK", -1: "ROD_ERR_ARG", -2: "ROD_ERR_CUDA", -3: "ROD_ERR_NONFINITE",
+                -4: "ROD_ERR_TIMEOUT", -5: "ROD_ERR_OVERFLOW", -6: "ROD_ERR_STATE"}
+
+
+class RodError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class RodSystemDesc(C.Structure):
+    _fields_ = [
+        ("n_rods", C.c_int32),
+        ("n_elem", C.c_void_p),
+        ("rest_len", C.c_void_p),
+        ("radius", C.c_void_p),
+        ("youngs", C.c_void_p),
+        ("shear_mod", C.c_void_p),
+        ("density", C.c_void_p),
+        ("alpha_c", C.c_double),
+        ("clamp_base", C.c_void_p),
+        ("rest_kappa", C.c_void_p),
+        ("rest_sigma", C.c_void_p),
+        ("gravity", C.c_double * 3),
+        ("nu_damp", C.c_double),
+        ("stokes_gamma", C.c_double),
+        ("tip_force", C.c_void_p),
+        ("act_amp", C.c_void_p),
+        ("act_period", C.c_void_p),
+        ("act_phase", C.c_void_p),
+        ("elem_couple", C.c_void_p),
+        ("cuda_stream", C.c_void_p),
+    ]
+
+
+# exported symbols and their signatures (argument types, return type)
+_P = C.c_void_p
+_SIGNATURES = {
+    "rod_system_create": ([C.POINTER(RodSystemDesc), C.POINTER(C.c_void_p)], C.c_int),
+    "rod_system_destroy": ([_P], C.c_int),
+    "rod_system_sizes": ([_P, _P, _P, _P], C.c_int),
+    "rod_system_set_state": ([_P, _P, _P, _P, _P, C.c_int], C.c_int),
+    "rod_system_get_state": ([_P, _P, _P, _P, _P, C.c_int], C.c_int),
+    "rod_system_set_time": ([_P, C.c_double], C.c_int),
+    "rod_system_get_time": ([_P, _P], C.c_int),
+    "rod_system_step": ([_P, C.c_int64, C.c_double], C.c_int),
+    "rod_system_step_async": ([_P, C.c_int64, C.c_double], C.c_int),
+    "rod_system_sync": ([_P], C.c_int),
+    "rod_system_contact_config": ([_P, C.c_int, C.c_double, C.c_double, C.c_double], C.c_int),
+    "rod_system_rhs": ([_P, C.c_double, _P, _P], C.c_int),
+    "rod_system_contact_forces": ([_P, _P], C.c_int),
+    "rod_system_set_launch": ([_P, C.c_int32, C.c_int32], C.c_int),
+    "rod_system_get_launch": ([_P, _P, _P], C.c_int),
+    "rod_max_elements_per_rod": ([], C.c_int32),
+    "rod_last_error": ([], C.c_char_p),
+    "rod_version": ([], C.c_char_p),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: Optional[str] = None):
+    """Load librod.so (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIBRARY_PATH
+            if not os.path.exists(p):
+                raise ImportError(f"librod.so not found at {p}; build it with paper_2605_13766_gb300.build.build()")
+            lib = C.CDLL(p)
+            for name, (args, res) in _SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != ROD_OK:
+        raise RodError(status, _lib.rod_last_error().decode(errors="replace"))
+
+
+def _host(a, dtype=np.float64):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()  # torch tensor
+
+
+class RodSystem:
+    """One ensemble of rods on the GPU (a handle on ``rod_system``).
+
+    ``problem`` is any object with the attributes of ``rodgen.RodProblem`` (sizes, materials,
+    loads, optional contact settings).  The state is set separately with ``set_state``.
+    """
+
+    def __init__(self, problem, stream=None, use_torch_stream: bool = True):
+        lib = load_library()
+        self.lib = lib
+        p = problem
+        keep = {
+            "n_elem": _host(p.n_elem, np.int32),
+            "rest_len": _host(p.rest_len),
+            "radius": _host(p.radius),
+            "youngs": _host(p.youngs),
+            "shear_mod": _host(p.shear_mod),
+            "density": _host(p.density),
+            "clamp_base": _host(getattr(p, "clamp_base", None), np.int8),
+            "rest_kappa": _host(getattr(p, "rest_kappa", None)),
+            "rest_sigma": _host(getattr(p, "rest_sigma", None)),
+            "tip_force": _host(getattr(p, "tip_force", None)),
+            "act_amp": _host(getattr(p, "act_amp", None)),
+            "act_period": _host(getattr(p, "act_period", None)),
+            "act_phase": _host(getattr(p, "act_phase", None)),
+            "elem_couple": _host(getattr(p, "elem_couple", None)),
+        }
+        d = RodSystemDesc()
+        d.n_rods = int(keep["n_elem"].shape[0])
+        for k, v in keep.items():
+            setattr(d, k, _ptr(v))
+        d.alpha_c = float(getattr(p, "alpha_c", 4.0 / 3.0))
+        d.gravity = (C.c_double * 3)(*[float(g) for g in getattr(p, "gravity", (0.0, 0.0, 0.0))])
+        d.nu_damp = float(getattr(p, "nu_damp", 0.0))
+        d.stokes_gamma = float(getattr(p, "stokes_gamma", 0.0))
+        self.torch_stream = None
+        if stream is None and use_torch_stream:
+            import torch
+            self.torch_stream = torch.cuda.current_stream()
+            stream = self.torch_stream.cuda_stream
+        d.cuda_stream = stream
+        handle = C.c_void_p()
+        _check(lib.rod_system_create(C.byref(d), C.byref(handle)))
+        self.handle = handle
+        n, e, v = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib.rod_system_sizes(handle, C.byref(n), C.byref(e), C.byref(v)))
+        self.n_nodes, self.n_elems, self.n_voronoi = n.value, e.value, v.value
+        self.n_rods = d.n_rods
+        if getattr(p, "contact", False):
+            self.contact_config(True, p.contact_k, p.contact_c, p.cell_size)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.rod_system_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- state
+    def set_state(self, x, v, Q, w):
+        """Host numpy arrays (copied synchronously) or CUDA torch tensors (copied on the stream)."""
+        on_dev = not isinstance(x, np.ndarray)
+        if on_dev:
+            arrs = [a.contiguous() for a in (x, v, Q, w)]
+            for a in arrs:
+                if a.dtype.__str__() != "torch.float64" or not a.is_cuda:
+                    raise TypeError("device state must be float64 CUDA tensors")
+        else:
+            arrs = [_host(a) for a in (x, v, Q, w)]
+        self._check_shapes(arrs)
+        _check(self.lib.rod_system_set_state(self.handle, *[_ptr(a) for a in arrs], 1 if on_dev else 0))
+        self._keep_state_inputs = arrs  # alive until the stream has copied them
+
+    def get_state(self, device: bool = False):
+        if device:
+            import torch
+            out = [torch.empty((3, self.n_nodes), dtype=torch.float64, device="cuda"),
+                   torch.empty((3, self.n_nodes), dtype=torch.float64, device="cuda"),
+                   torch.empty((9, self.n_elems), dtype=torch.float64, device="cuda"),
+                   torch.empty((3, self.n_elems), dtype=torch.float64, device="cuda")]
+        else:
+            out = [np.empty((3, self.n_nodes)), np.empty((3, self.n_nodes)),
+                   np.empty((9, self.n_elems)), np.empty((3, self.n_elems))]
+        _check(self.lib.rod_system_get_state(self.handle, *[_ptr(a) for a in out], 1 if device else 0))
+        return tuple(out)
+
+    def _check_shapes(self, arrs):
+        want = [(3, self.n_nodes), (3, self.n_nodes), (9, self.n_elems), (3, self.n_elems)]
+        for a, s in zip(arrs, want):
+            if tuple(a.shape) != s and (int(np.prod(a.shape)) != s[0] * s[1]):
+                raise ValueError(f"state array of shape {tuple(a.shape)}, expected {s}")
+
+    @property
+    def time(self) -> float:
+        t = C.c_double()
+        _check(self.lib.rod_system_get_time(self.handle, C.byref(t)))
+        return t.value
+
+    @time.setter
+    def time(self, t: float):
+        _check(self.lib.rod_system_set_time(self.handle, float(t)))
+
+    # -- stepping
+    def step(self, n_steps: int, dt: float):
+        _check(self.lib.rod_system_step(self.handle, int(n_steps), float(dt)))
+
+    def step_async(self, n_steps: int, dt: float):
+        _check(self.lib.rod_system_step_async(self.handle, int(n_steps), float(dt)))
+
+    def sync(self):
+        _check(self.lib.rod_system_sync(self.handle))
+
+    def contact_config(self, enable: bool, k: float = 0.0, c: float = 0.0, cell_size: float = 0.0):
+        _check(self.lib.rod_system_contact_config(self.handle, 1 if enable else 0, float(k), float(c),
+                                                  float(cell_size)))
+
+    # -- debug / parity entry points (device outputs)
+    def rhs(self, t: float = 0.0):
+        import torch
+        av = torch.empty((3, self.n_nodes), dtype=torch.float64, device="cuda")
+        aw = torch.empty((3, self.n_elems), dtype=torch.float64, device="cuda")
+        _check(self.lib.rod_system_rhs(self.handle, float(t), av.data_ptr(), aw.data_ptr()))
+        return av, aw
+
+    def contact_forces(self):
+        import torch
+        f = torch.empty((3, self.n_nodes), dtype=torch.float64, device="cuda")
+        _check(self.lib.rod_system_contact_forces(self.handle, f.data_ptr()))
+        return f
+
+    # -- launch shape
+    def set_launch(self, elems_per_block: int = 0, threads_per_block: int = 0):
+        _check(self.lib.rod_system_set_launch(self.handle, int(elems_per_block), int(threads_per_block)))
+
+    def get_launch(self):
+        e, t = C.c_int32(), C.c_int32()
+        _check(self.lib.rod_system_get_launch(self.handle, C.byref(e), C.byref(t)))
+        return e.value, t.value
+
+
+def exported_symbols():
+    return list(_SIGNATURES)

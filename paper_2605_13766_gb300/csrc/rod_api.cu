@@ -1,0 +1,555 @@
+// rod_api.cu -- host side of librod: the C ABI declared in include/rod.h.
+//
+// The library owns its device memory (cudaMalloc at create, freed at destroy).  Everything
+// that advances the state runs in the kernels of rod_step.cu and rod_contact.cu; the host
+// only validates, derives per-rod constants once, packs rods into thread blocks and
+// enqueues work on the system's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rod.h"
+#include "rod_contact.h"
+#include "rod_internal.h"
+
+using namespace rod;
+
+// ------------------------------------------------------------------------------ errors
+
+static thread_local char g_msg[1024] = "";
+
+static rod_status fail(rod_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+namespace rod {
+rod_status internal_fail(rod_status st, const char* what, const char* detail) {
+  return fail(st, "%s%s%s", what, (detail && *detail) ? ": " : "", detail ? detail : "");
+}
+}  // namespace rod
+
+#define CUDA_TRY(expr)                                                                               \
+  do {                                                                                               \
+    cudaError_t e_ = (expr);                                                                         \
+    if (e_ != cudaSuccess) return fail(ROD_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+// ------------------------------------------------------------------------------ system
+
+namespace {
+
+constexpr int kMaxCapElems = 768;
+constexpr double kPi = 3.14159265358979323846;
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaError_t alloc(size_t count) {
+    release();
+    n = count;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc(&p, count * sizeof(T));
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+__global__ void gather_clamp_kernel(const double* x, const double* Q, const RodConst* rods, int R, int64_t N, int64_t E,
+                                    double* cx, double* cQ) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const int j = rods[r].node0, i = rods[r].elem0;
+  for (int c = 0; c < 3; ++c) cx[c * R + r] = x[c * N + j];
+  for (int a = 0; a < 9; ++a) cQ[a * R + r] = Q[a * E + i];
+}
+
+}  // namespace
+
+struct rod_system {
+  int R = 0;
+  int64_t N = 0, E = 0, V = 0;
+  int max_n = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // state
+  DevBuf<double> x, v, Q, w;
+  // constants
+  DevBuf<double> rest_len, inv_rl, inv_2D, Dhat, inv_m;
+  DevBuf<double> rest_kappa, rest_sigma, elem_couple;
+  DevBuf<double> clamp_x, clamp_Q;
+  DevBuf<RodConst> rods;
+  std::vector<RodConst> rods_h;
+  std::vector<double> rest_len_h;
+  // packing
+  LaunchShape shape{0, 0, 0};
+  DevBuf<Pack> packs;
+  int n_packs = 0;
+  bool shape_user = false;
+  // misc
+  double gravity[3] = {0, 0, 0};
+  bool has_gravity = false, has_act = false;
+  DevBuf<int> err;
+  int* err_host = nullptr;  // pinned
+  bool state_set = false;
+  double t = 0.0;
+  // contact
+  ContactState contact;
+};
+
+namespace {
+
+rod_status build_packs(rod_system* s, const LaunchShape& shape) {
+  if (shape.cap_elems < s->max_n)
+    return fail(ROD_ERR_ARG, "launch shape holds %d elements per block but the longest rod has %d", shape.cap_elems,
+                s->max_n);
+  std::vector<Pack> packs;
+  Pack cur{};
+  bool open = false;
+  for (int r = 0; r < s->R; ++r) {
+    const RodConst& rc = s->rods_h[r];
+    const int n = rc.n;
+    if (open && (cur.nelem + n > shape.cap_elems || cur.nrods + 1 > shape.cap_rods)) {
+      packs.push_back(cur);
+      open = false;
+    }
+    if (!open) {
+      cur = Pack{};
+      cur.rod0 = r;
+      cur.elem0 = rc.elem0;
+      cur.node0 = rc.node0;
+      cur.vor0 = rc.elem0 - r;
+      open = true;
+    }
+    cur.nrods += 1;
+    cur.nelem += n;
+    cur.nnode += n + 1;
+    cur.nvor += n - 1;
+  }
+  if (open) packs.push_back(cur);
+  CUDA_TRY(s->packs.alloc(packs.size()));
+  CUDA_TRY(cudaMemcpy(s->packs.p, packs.data(), packs.size() * sizeof(Pack), cudaMemcpyHostToDevice));
+  s->n_packs = static_cast<int>(packs.size());
+  s->shape = shape;
+  return ROD_OK;
+}
+
+LaunchShape default_shape(const rod_system* s) {
+  LaunchShape sh;
+  int cap = 384;
+  while (cap < s->max_n) cap += 128;
+  sh.cap_elems = std::min(cap, kMaxCapElems);
+  sh.cap_rods = std::max(8, std::min(64, sh.cap_elems / 4));
+  sh.threads = sh.cap_elems >= 512 ? 512 : 256;
+  return sh;
+}
+
+StepParams make_params(rod_system* s) {
+  StepParams P{};
+  P.x = s->x.p;
+  P.v = s->v.p;
+  P.Q = s->Q.p;
+  P.w = s->w.p;
+  P.N = s->N;
+  P.E = s->E;
+  P.V = s->V;
+  P.rest_len = s->rest_len.p;
+  P.inv_rl = s->inv_rl.p;
+  P.inv_2D = s->inv_2D.p;
+  P.Dhat = s->Dhat.p;
+  P.inv_m = s->inv_m.p;
+  P.rest_kappa = s->rest_kappa.p;
+  P.rest_sigma = s->rest_sigma.p;
+  P.elem_couple = s->elem_couple.p;
+  P.clamp_x = s->clamp_x.p;
+  P.clamp_Q = s->clamp_Q.p;
+  P.rods = s->rods.p;
+  P.packs = s->packs.p;
+  P.n_packs = s->n_packs;
+  P.n_rods = s->R;
+  for (int c = 0; c < 3; ++c) P.gravity[c] = s->gravity[c];
+  P.has_gravity = s->has_gravity;
+  P.has_act = s->has_act;
+  P.fseg = nullptr;
+  P.err = s->err.p;
+  return P;
+}
+
+rod_status read_error_word(rod_system* s) {
+  CUDA_TRY(cudaMemcpyAsync(s->err_host, s->err.p, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  const int e = *s->err_host;
+  if (e & ERR_NONFINITE) return fail(ROD_ERR_NONFINITE, "the state became non-finite (NaN/Inf)");
+  if (e & ERR_GRID) return fail(ROD_ERR_OVERFLOW, "an element grew longer than the contact grid allows");
+  if (e & ERR_OVERFLOW) return fail(ROD_ERR_OVERFLOW, "contact table capacity exceeded");
+  if (e & ERR_TIMEOUT) return fail(ROD_ERR_TIMEOUT, "a bounded device wait ran out");
+  return ROD_OK;
+}
+
+bool finite_all(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ ABI
+
+extern "C" {
+
+const char* rod_last_error(void) { return g_msg; }
+const char* rod_version(void) { return "librod 1.0 (sm_103a, FP64)"; }
+int32_t rod_max_elements_per_rod(void) { return kMaxCapElems; }
+
+rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
+  if (!d || !out) return fail(ROD_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (d->n_rods <= 0) return fail(ROD_ERR_ARG, "n_rods must be positive (got %d)", d->n_rods);
+  if (!d->n_elem || !d->rest_len || !d->radius || !d->youngs || !d->shear_mod || !d->density)
+    return fail(ROD_ERR_ARG, "n_elem, rest_len, radius, youngs, shear_mod and density are required");
+  const int R = d->n_rods;
+  int64_t E = 0;
+  int max_n = 0;
+  for (int r = 0; r < R; ++r) {
+    if (d->n_elem[r] < 1) return fail(ROD_ERR_ARG, "rod %d has %d elements (need >= 1)", r, d->n_elem[r]);
+    E += d->n_elem[r];
+    max_n = std::max(max_n, (int)d->n_elem[r]);
+    if (!(d->radius[r] > 0) || !(d->youngs[r] > 0) || !(d->shear_mod[r] > 0) || !(d->density[r] > 0))
+      return fail(ROD_ERR_ARG, "rod %d: radius, moduli and density must be positive and finite", r);
+    if (!std::isfinite(d->radius[r]) || !std::isfinite(d->youngs[r]) || !std::isfinite(d->shear_mod[r]) ||
+        !std::isfinite(d->density[r]))
+      return fail(ROD_ERR_ARG, "rod %d: non-finite material parameter", r);
+  }
+  if (max_n > kMaxCapElems)
+    return fail(ROD_ERR_ARG, "a rod has %d elements; one thread block holds at most %d", max_n, kMaxCapElems);
+  if (E + R >= (int64_t(1) << 31) / 9) return fail(ROD_ERR_ARG, "ensemble too large (%lld elements)", (long long)E);
+  for (int64_t i = 0; i < E; ++i)
+    if (!(d->rest_len[i] > 0) || !std::isfinite(d->rest_len[i]))
+      return fail(ROD_ERR_ARG, "rest length %lld must be positive and finite", (long long)i);
+  if (!(d->alpha_c > 0) || !std::isfinite(d->alpha_c)) return fail(ROD_ERR_ARG, "alpha_c must be positive");
+  if (!std::isfinite(d->nu_damp) || d->nu_damp < 0 || !std::isfinite(d->stokes_gamma) || d->stokes_gamma < 0)
+    return fail(ROD_ERR_ARG, "nu_damp and stokes_gamma must be finite and >= 0");
+  if (d->act_amp) {
+    if (!d->act_period || !d->act_phase) return fail(ROD_ERR_ARG, "act_amp needs act_period and act_phase");
+    for (int r = 0; r < R; ++r)
+      if (!(d->act_period[r] > 0) || !std::isfinite(d->act_amp[r]) || !std::isfinite(d->act_phase[r]))
+        return fail(ROD_ERR_ARG, "rod %d: actuation period must be positive, amplitude/phase finite", r);
+  }
+  const int64_t V = E - R, N = E + R;
+  if (d->rest_kappa && !finite_all(d->rest_kappa, 3 * V)) return fail(ROD_ERR_ARG, "rest_kappa has non-finite values");
+  if (d->rest_sigma && !finite_all(d->rest_sigma, 3 * E)) return fail(ROD_ERR_ARG, "rest_sigma has non-finite values");
+  if (d->elem_couple && !finite_all(d->elem_couple, 3 * E)) return fail(ROD_ERR_ARG, "elem_couple has non-finite values");
+  if (d->tip_force && !finite_all(d->tip_force, 3 * R)) return fail(ROD_ERR_ARG, "tip_force has non-finite values");
+  for (int c = 0; c < 3; ++c)
+    if (!std::isfinite(d->gravity[c])) return fail(ROD_ERR_ARG, "gravity must be finite");
+
+  rod_system* s = new rod_system();
+  s->R = R;
+  s->E = E;
+  s->N = N;
+  s->V = V;
+  s->max_n = max_n;
+  auto cleanup = [&](rod_status st) {
+    rod_system_destroy(s);
+    return st;
+  };
+  if (d->cuda_stream) {
+    s->stream = static_cast<cudaStream_t>(d->cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return cleanup(fail(ROD_ERR_CUDA, "cudaStreamCreate failed: %s", cudaGetErrorString(cudaGetLastError())));
+    s->own_stream = true;
+  }
+
+  // per-rod constants
+  s->rods_h.resize(R);
+  int64_t e0 = 0, n0 = 0;
+  bool any_act = false;
+  for (int r = 0; r < R; ++r) {
+    RodConst& rc = s->rods_h[r];
+    std::memset(&rc, 0, sizeof rc);
+    const double rad = d->radius[r], Ey = d->youngs[r], G = d->shear_mod[r], rho = d->density[r];
+    const double A = kPi * rad * rad;
+    const double I1 = kPi * rad * rad * rad * rad / 4.0;
+    const double I[3] = {I1, I1, 2.0 * I1};
+    rc.S[0] = d->alpha_c * G * A;
+    rc.S[1] = d->alpha_c * G * A;
+    rc.S[2] = Ey * A;
+    rc.B[0] = Ey * I[0];
+    rc.B[1] = Ey * I[1];
+    rc.B[2] = G * I[2];
+    for (int c = 0; c < 3; ++c) {
+      rc.rhoI[c] = rho * I[c];
+      rc.inv_rhoI[c] = 1.0 / (rho * I[c]);
+    }
+    rc.damp_lin = (d->nu_damp + d->stokes_gamma) / (rho * A);
+    rc.damp_rot = d->nu_damp / (rho * A);
+    rc.radius = rad;
+    rc.node0 = static_cast<int32_t>(n0);
+    rc.elem0 = static_cast<int32_t>(e0);
+    rc.n = d->n_elem[r];
+    rc.clamp = (d->clamp_base && d->clamp_base[r]) ? 1 : 0;
+    rc.act_elem = -1;
+    if (d->act_amp && d->act_amp[r] != 0.0) {
+      rc.act_amp = d->act_amp[r];
+      rc.act_omega = 2.0 * kPi / d->act_period[r];
+      rc.act_phase = d->act_phase[r];
+      rc.act_elem = (rc.clamp && rc.n >= 2) ? 1 : 0;
+      any_act = true;
+    }
+    if (d->tip_force)
+      for (int c = 0; c < 3; ++c) rc.tip[c] = d->tip_force[c * R + r];
+    e0 += rc.n;
+    n0 += rc.n + 1;
+  }
+  s->has_act = any_act;
+  for (int c = 0; c < 3; ++c) s->gravity[c] = d->gravity[c];
+  s->has_gravity = d->gravity[0] != 0.0 || d->gravity[1] != 0.0 || d->gravity[2] != 0.0;
+
+  // per-item constants
+  s->rest_len_h.assign(d->rest_len, d->rest_len + E);
+  std::vector<double> inv_rl(E), inv_2D(std::max<int64_t>(V, 1)), Dh(std::max<int64_t>(V, 1)), inv_m(N);
+  for (int r = 0; r < R; ++r) {
+    const RodConst& rc = s->rods_h[r];
+    const double rhoA = d->density[r] * kPi * d->radius[r] * d->radius[r];
+    for (int i = 0; i < rc.n; ++i) inv_rl[rc.elem0 + i] = 1.0 / d->rest_len[rc.elem0 + i];
+    for (int k = 0; k < rc.n - 1; ++k) {
+      const double a = d->rest_len[rc.elem0 + k], b = d->rest_len[rc.elem0 + k + 1];
+      inv_2D[rc.elem0 - r + k] = 1.0 / (a + b);
+      Dh[rc.elem0 - r + k] = 0.5 * (a + b);
+    }
+    for (int j = 0; j <= rc.n; ++j) {
+      const double left = j >= 1 ? d->rest_len[rc.elem0 + j - 1] : 0.0;
+      const double right = j < rc.n ? d->rest_len[rc.elem0 + j] : 0.0;
+      inv_m[rc.node0 + j] = 1.0 / (0.5 * rhoA * (left + right));
+    }
+  }
+
+  auto up = [&](auto& buf, const auto* src, size_t count) -> cudaError_t {
+    cudaError_t e = buf.alloc(count);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(buf.p, src, count * sizeof(*src), cudaMemcpyHostToDevice);
+  };
+  cudaError_t ce = cudaSuccess;
+  if ((ce = s->x.alloc(3 * N)) || (ce = s->v.alloc(3 * N)) || (ce = s->Q.alloc(9 * E)) || (ce = s->w.alloc(3 * E)) ||
+      (ce = up(s->rest_len, d->rest_len, E)) || (ce = up(s->inv_rl, inv_rl.data(), E)) ||
+      (ce = up(s->inv_2D, inv_2D.data(), inv_2D.size())) || (ce = up(s->Dhat, Dh.data(), Dh.size())) ||
+      (ce = up(s->inv_m, inv_m.data(), N)) || (ce = up(s->rods, s->rods_h.data(), R)) ||
+      (ce = s->clamp_x.alloc(3 * R)) || (ce = s->clamp_Q.alloc(9 * R)) || (ce = s->err.alloc(1)))
+    return cleanup(fail(ROD_ERR_CUDA, "device allocation/copy failed: %s", cudaGetErrorString(ce)));
+  if (d->rest_kappa && V > 0 && (ce = up(s->rest_kappa, d->rest_kappa, 3 * V)))
+    return cleanup(fail(ROD_ERR_CUDA, "copy failed: %s", cudaGetErrorString(ce)));
+  if (d->rest_sigma && (ce = up(s->rest_sigma, d->rest_sigma, 3 * E)))
+    return cleanup(fail(ROD_ERR_CUDA, "copy failed: %s", cudaGetErrorString(ce)));
+  if (d->elem_couple && (ce = up(s->elem_couple, d->elem_couple, 3 * E)))
+    return cleanup(fail(ROD_ERR_CUDA, "copy failed: %s", cudaGetErrorString(ce)));
+  if ((ce = cudaMemset(s->err.p, 0, sizeof(int))) || (ce = cudaMallocHost(&s->err_host, sizeof(int))))
+    return cleanup(fail(ROD_ERR_CUDA, "allocation failed: %s", cudaGetErrorString(ce)));
+  *s->err_host = 0;
+  rod_status st = build_packs(s, default_shape(s));
+  if (st != ROD_OK) return cleanup(st);
+  *out = s;
+  return ROD_OK;
+}
+
+rod_status rod_system_destroy(rod_system* s) {
+  if (!s) return ROD_OK;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  s->x.release();
+  s->v.release();
+  s->Q.release();
+  s->w.release();
+  s->rest_len.release();
+  s->inv_rl.release();
+  s->inv_2D.release();
+  s->Dhat.release();
+  s->inv_m.release();
+  s->rest_kappa.release();
+  s->rest_sigma.release();
+  s->elem_couple.release();
+  s->clamp_x.release();
+  s->clamp_Q.release();
+  s->rods.release();
+  s->packs.release();
+  s->err.release();
+  contact_release(s->contact);
+  if (s->err_host) cudaFreeHost(s->err_host);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+  return ROD_OK;
+}
+
+rod_status rod_system_sizes(const rod_system* s, int64_t* n_nodes, int64_t* n_elems, int64_t* n_voronoi) {
+  if (!s) return fail(ROD_ERR_ARG, "null system");
+  if (n_nodes) *n_nodes = s->N;
+  if (n_elems) *n_elems = s->E;
+  if (n_voronoi) *n_voronoi = s->V;
+  return ROD_OK;
+}
+
+rod_status rod_system_set_state(rod_system* s, const double* x, const double* v, const double* Q, const double* w,
+                                int on_device) {
+  if (!s || !x || !v || !Q || !w) return fail(ROD_ERR_ARG, "null argument");
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (!on_device) {
+    if (!finite_all(x, 3 * s->N) || !finite_all(v, 3 * s->N) || !finite_all(Q, 9 * s->E) || !finite_all(w, 3 * s->E))
+      return fail(ROD_ERR_ARG, "the state holds non-finite values");
+  }
+  CUDA_TRY(cudaMemcpyAsync(s->x.p, x, 3 * s->N * sizeof(double), kind, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(s->v.p, v, 3 * s->N * sizeof(double), kind, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(s->Q.p, Q, 9 * s->E * sizeof(double), kind, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(s->w.p, w, 3 * s->E * sizeof(double), kind, s->stream));
+  gather_clamp_kernel<<<(s->R + 127) / 128, 128, 0, s->stream>>>(s->x.p, s->Q.p, s->rods.p, s->R, s->N, s->E,
+                                                                  s->clamp_x.p, s->clamp_Q.p);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemsetAsync(s->err.p, 0, sizeof(int), s->stream));
+  if (!on_device) CUDA_TRY(cudaStreamSynchronize(s->stream));
+  s->state_set = true;
+  s->t = 0.0;
+  s->contact.grid_valid = false;
+  return ROD_OK;
+}
+
+rod_status rod_system_get_state(rod_system* s, double* x, double* v, double* Q, double* w, int on_device) {
+  if (!s) return fail(ROD_ERR_ARG, "null system");
+  if (!s->state_set) return fail(ROD_ERR_STATE, "no state has been set");
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (x) CUDA_TRY(cudaMemcpyAsync(x, s->x.p, 3 * s->N * sizeof(double), kind, s->stream));
+  if (v) CUDA_TRY(cudaMemcpyAsync(v, s->v.p, 3 * s->N * sizeof(double), kind, s->stream));
+  if (Q) CUDA_TRY(cudaMemcpyAsync(Q, s->Q.p, 9 * s->E * sizeof(double), kind, s->stream));
+  if (w) CUDA_TRY(cudaMemcpyAsync(w, s->w.p, 3 * s->E * sizeof(double), kind, s->stream));
+  if (!on_device) CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return ROD_OK;
+}
+
+rod_status rod_system_set_time(rod_system* s, double t) {
+  if (!s || !std::isfinite(t)) return fail(ROD_ERR_ARG, "bad argument");
+  s->t = t;
+  return ROD_OK;
+}
+
+rod_status rod_system_get_time(const rod_system* s, double* t) {
+  if (!s || !t) return fail(ROD_ERR_ARG, "null argument");
+  *t = s->t;
+  return ROD_OK;
+}
+
+rod_status rod_system_step_async(rod_system* s, int64_t n_steps, double dt) {
+  if (!s) return fail(ROD_ERR_ARG, "null system");
+  if (!s->state_set) return fail(ROD_ERR_STATE, "no state has been set");
+  if (n_steps < 0 || !(dt > 0) || !std::isfinite(dt)) return fail(ROD_ERR_ARG, "need n_steps >= 0 and dt > 0");
+  if (n_steps == 0) return ROD_OK;
+  StepParams P = make_params(s);
+  if (!s->contact.enabled) {
+    const int64_t chunk = int64_t(1) << 20;
+    for (int64_t done = 0; done < n_steps; done += chunk) {
+      const int64_t k = std::min(chunk, n_steps - done);
+      CUDA_TRY(launch_pack_kernel(P, s->shape, MODE_STEPS, k, s->t + done * dt, dt, 1, nullptr, nullptr, s->stream));
+    }
+  } else {
+    rod_status st = contact_prepare(s->contact, s->rods_h, s->rods.p, s->x.p, s->N, s->E, s->R, s->stream);
+    if (st != ROD_OK) return st;
+    CUDA_TRY(launch_pack_kernel(P, s->shape, MODE_KIN_HALF, 1, s->t, dt, 0, nullptr, nullptr, s->stream));
+    for (int64_t k = 0; k < n_steps; ++k) {
+      CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream));
+      P.fseg = s->contact.fseg;
+      CUDA_TRY(launch_pack_kernel(P, s->shape, MODE_ONE_STEP, 1, s->t + k * dt, dt, k == n_steps - 1 ? 1 : 0,
+                                  nullptr, nullptr, s->stream));
+    }
+  }
+  s->t += n_steps * dt;
+  return ROD_OK;
+}
+
+rod_status rod_system_sync(rod_system* s) {
+  if (!s) return fail(ROD_ERR_ARG, "null system");
+  return read_error_word(s);
+}
+
+rod_status rod_system_step(rod_system* s, int64_t n_steps, double dt) {
+  rod_status st = rod_system_step_async(s, n_steps, dt);
+  if (st != ROD_OK) return st;
+  return read_error_word(s);
+}
+
+rod_status rod_system_contact_config(rod_system* s, int enable, double k, double c, double cell_size) {
+  if (!s) return fail(ROD_ERR_ARG, "null system");
+  if (enable && (!(k >= 0) || !(c >= 0) || !std::isfinite(k) || !std::isfinite(c) || !std::isfinite(cell_size)))
+    return fail(ROD_ERR_ARG, "contact needs finite k >= 0, c >= 0 and cell_size");
+  s->contact.enabled = enable != 0;
+  s->contact.k = k;
+  s->contact.c = c;
+  s->contact.cell_size = cell_size;
+  s->contact.grid_valid = false;
+  return ROD_OK;
+}
+
+rod_status rod_system_rhs(rod_system* s, double t, double* acc_v, double* acc_w) {
+  if (!s || !acc_v || !acc_w) return fail(ROD_ERR_ARG, "null argument");
+  if (!s->state_set) return fail(ROD_ERR_STATE, "no state has been set");
+  StepParams P = make_params(s);
+  if (s->contact.enabled) {
+    rod_status st = contact_prepare(s->contact, s->rods_h, s->rods.p, s->x.p, s->N, s->E, s->R, s->stream);
+    if (st != ROD_OK) return st;
+    CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream));
+    P.fseg = s->contact.fseg;
+  }
+  CUDA_TRY(launch_pack_kernel(P, s->shape, MODE_RHS, 1, t, 1.0, 0, acc_v, acc_w, s->stream));
+  return read_error_word(s);
+}
+
+rod_status rod_system_contact_forces(rod_system* s, double* f) {
+  if (!s || !f) return fail(ROD_ERR_ARG, "null argument");
+  if (!s->state_set) return fail(ROD_ERR_STATE, "no state has been set");
+  if (!s->contact.enabled) {
+    CUDA_TRY(cudaMemsetAsync(f, 0, 3 * s->N * sizeof(double), s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return ROD_OK;
+  }
+  rod_status st = contact_prepare(s->contact, s->rods_h, s->rods.p, s->x.p, s->N, s->E, s->R, s->stream);
+  if (st != ROD_OK) return st;
+  CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream));
+  CUDA_TRY(contact_node_forces(s->contact, s->rods.p, s->N, s->E, s->R, f, s->stream));
+  return read_error_word(s);
+}
+
+rod_status rod_system_set_launch(rod_system* s, int32_t elems_per_block, int32_t threads_per_block) {
+  if (!s) return fail(ROD_ERR_ARG, "null system");
+  LaunchShape sh = default_shape(s);
+  if (elems_per_block > 0) {
+    if (elems_per_block > kMaxCapElems || elems_per_block % 32)
+      return fail(ROD_ERR_ARG, "elems_per_block must be a multiple of 32 and <= %d", kMaxCapElems);
+    sh.cap_elems = elems_per_block;
+    sh.cap_rods = std::max(8, std::min(64, sh.cap_elems / 4));
+  }
+  if (threads_per_block > 0) {
+    if (threads_per_block > 512 || threads_per_block % 32)
+      return fail(ROD_ERR_ARG, "threads_per_block must be a multiple of 32 and <= 512");
+    sh.threads = threads_per_block;
+  }
+  if (step_smem_bytes(sh) > 227 * 1024) return fail(ROD_ERR_ARG, "launch shape needs too much shared memory");
+  return build_packs(s, sh);
+}
+
+rod_status rod_system_get_launch(const rod_system* s, int32_t* elems_per_block, int32_t* threads_per_block) {
+  if (!s) return fail(ROD_ERR_ARG, "null system");
+  if (elems_per_block) *elems_per_block = s->shape.cap_elems;
+  if (threads_per_block) *threads_per_block = s->shape.threads;
+  return ROD_OK;
+}
+
+}  // extern "C"

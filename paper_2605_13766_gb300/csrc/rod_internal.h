@@ -1,0 +1,92 @@
+// rod_internal.h -- structures shared by the translation units of librod (host + device).
+// Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rod {
+
+// Device error word bits (latched; the host maps them to rod_status).
+enum : int {
+  ERR_NONFINITE = 1,
+  ERR_OVERFLOW = 2,
+  ERR_TIMEOUT = 4,
+  ERR_GRID = 8,       // a segment longer than the contact cell allows
+};
+
+// Per-rod constants, derived once at create time from the description (Methods: A = pi r^2,
+// I1 = I2 = pi r^4/4, I3 = I1 + I2, B = diag(E I1, E I2, G I3), S = diag(aG A, aG A, E A)).
+struct RodConst {
+  double S[3];          // shear/stretch stiffness
+  double B[3];          // bend/twist stiffness
+  double rhoI[3];       // rho I_c (element inertia is rhoI * rest length)
+  double inv_rhoI[3];   // 1 / (rho I_c)
+  double damp_lin;      // (nu + gamma) / (rho A): translational decay rate
+  double damp_rot;      // nu / (rho A): rotational decay rate
+  double act_amp;       // base couple amplitude (0: none)
+  double act_omega;     // 2 pi / T
+  double act_phase;
+  double tip[3];        // tip force (lab)
+  double radius;
+  int32_t node0;        // first node (global)
+  int32_t elem0;        // first element (global)
+  int32_t n;            // elements
+  int32_t clamp;        // 1: node 0 + element 0 held
+  int32_t act_elem;     // rod-local element carrying the base couple (-1: none)
+  int32_t pad;
+};
+
+// A pack: consecutive rods processed by one thread block.
+struct Pack {
+  int32_t rod0, nrods;
+  int32_t elem0, nelem;  // global first element, element count
+  int32_t node0, nnode;  // global first node, node count
+  int32_t vor0, nvor;    // global first Voronoi point, count
+};
+
+// Read-only parameters of the step kernels.
+struct StepParams {
+  // state (component-major)
+  double* x;
+  double* v;
+  double* Q;
+  double* w;
+  int64_t N, E, V;
+  // per-item constants
+  const double* rest_len;     // [E]
+  const double* inv_rl;       // [E]  1/rl
+  const double* inv_2D;       // [V]  1/(rl_k + rl_{k+1}) = 1/(2 D_k)
+  const double* Dhat;         // [V]  D_k
+  const double* inv_m;        // [N]  1/lumped mass
+  const double* rest_kappa;   // [3V] or null
+  const double* rest_sigma;   // [3E] or null
+  const double* elem_couple;  // [3E] or null
+  const double* clamp_x;      // [3R] values held by the clamp
+  const double* clamp_Q;      // [9R]
+  const RodConst* rods;       // [R]
+  const Pack* packs;
+  int32_t n_packs;
+  int32_t n_rods;
+  double gravity[3];
+  int32_t has_gravity;
+  int32_t has_act;
+  // contact: per-segment node forces [6E] (force on node a = first node, node b), or null
+  const double* fseg;
+  int* err;                   // device error word
+};
+
+// Launch shape of the pack kernels.
+struct LaunchShape {
+  int32_t cap_elems;   // elements per block (pack capacity)
+  int32_t cap_rods;    // rods per block
+  int32_t threads;
+};
+
+size_t step_smem_bytes(const LaunchShape& s);
+
+// Kernel launchers (rod_step.cu).
+enum StepMode : int { MODE_STEPS = 0, MODE_RHS = 1, MODE_KIN_HALF = 2, MODE_ONE_STEP = 3 };
+cudaError_t launch_pack_kernel(const StepParams& P, const LaunchShape& s, int mode, int64_t n_steps, double t0,
+                               double dt, int last_half, double* acc_v, double* acc_w, cudaStream_t st);
+
+}  // namespace rod

@@ -1,0 +1,575 @@
+// rod_step.cu -- FP64 step kernels of the discrete Cosserat-rod method for sm_103a.
+//
+// One thread block owns a "pack" of consecutive rods (CSR order) and stages their nodes,
+// directors and work arrays in shared memory, so that the difference (Delta^h) and averaging
+// (A^h) operators of Eq. 1 read their neighbours on chip; ghost values at the rod ends are the
+// zeros of the discrete operators.  Without contact the rods are independent, so a block runs
+// all requested steps on chip and touches HBM once per launch (the paper's asynchronous
+// protocol taken to the whole step loop).  With contact a launch performs one step and the
+// contact forces come from the cell-list kernels.
+//
+// The FP64 pipe of this part (2 DFMA/clk/SM) bounds the step, so the kernel avoids FP64
+// divisions (precomputed reciprocals of constants, one rsqrt per element, one reciprocal per
+// Voronoi point) and evaluates the rotation exponential and logarithm of small angles by
+// their Taylor series in theta^2 (no sqrt, no sin/cos/atan2 on the common path); large
+// angles fall back to sincos/atan2.
+//
+// Step (position Verlet, Results "Performance-oriented software design"): half kinematic
+// stage, dynamic stage at t + dt/2, half kinematic stage; kinematic constraints after every
+// stage.  The second half stage of step s and the first of step s+1 are fused into one
+// kinematic update of dt (exp(-h w) exp(-h w) = exp(-2h w) for a fixed w).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "rod_internal.h"
+
+namespace rod {
+
+namespace {
+
+// ---------------------------------------------------------------------------------- math
+
+// sin(th)/th and (1 - cos th)/th^2 as Taylor series in th^2 (8 terms each; the dropped terms
+// are below 5e-20 relative for th^2 <= 1/4).
+__device__ __forceinline__ void rot_coeffs(double th2, double& a, double& b) {
+  if (th2 <= 0.25) {
+    a = -1.0 / 1307674368000.0;
+    a = fma(a, th2, 1.0 / 6227020800.0);
+    a = fma(a, th2, -1.0 / 39916800.0);
+    a = fma(a, th2, 1.0 / 362880.0);
+    a = fma(a, th2, -1.0 / 5040.0);
+    a = fma(a, th2, 1.0 / 120.0);
+    a = fma(a, th2, -1.0 / 6.0);
+    a = fma(a, th2, 1.0);
+    b = -1.0 / 20922789888000.0;
+    b = fma(b, th2, 1.0 / 87178291200.0);
+    b = fma(b, th2, -1.0 / 479001600.0);
+    b = fma(b, th2, 1.0 / 3628800.0);
+    b = fma(b, th2, -1.0 / 40320.0);
+    b = fma(b, th2, 1.0 / 720.0);
+    b = fma(b, th2, -1.0 / 24.0);
+    b = fma(b, th2, 0.5);
+  } else {
+    double th = sqrt(th2);
+    double s, c, sh;
+    sincos(th, &s, &c);
+    sh = sin(0.5 * th) / th;
+    a = s / th;
+    b = 2.0 * sh * sh;
+  }
+}
+
+// asin(s)/s as a Taylor series in s^2 = |w|^2 (13 terms; dropped tail < 2e-18 for s <= 1/4).
+__device__ __forceinline__ double asin_over_s(double s2) {
+  double f = 676039.0 / 104857600.0;
+  f = fma(f, s2, 88179.0 / 12058624.0);
+  f = fma(f, s2, 46189.0 / 5505024.0);
+  f = fma(f, s2, 12155.0 / 1245184.0);
+  f = fma(f, s2, 6435.0 / 557056.0);
+  f = fma(f, s2, 143.0 / 10240.0);
+  f = fma(f, s2, 231.0 / 13312.0);
+  f = fma(f, s2, 63.0 / 2816.0);
+  f = fma(f, s2, 35.0 / 1152.0);
+  f = fma(f, s2, 5.0 / 112.0);
+  f = fma(f, s2, 3.0 / 40.0);
+  f = fma(f, s2, 1.0 / 6.0);
+  f = fma(f, s2, 1.0);
+  return f;
+}
+
+struct Smem {
+  double *X, *VN, *QQ, *WW;     // state
+  double *NF, *TA, *ELL, *EDIL; // element work
+  double *PP, *TT;              // Voronoi work
+  double *IRL, *IM, *ACT;       // constants, per-rod actuation value
+  int* rel0;                    // [CR+1] first element of each rod (pack-local)
+  short *erod, *nrod, *vrod;    // pack-local rod of each element / node / Voronoi point
+  int CE, CN, CV, CR;
+};
+
+__device__ __forceinline__ Smem carve(double* base, const LaunchShape& S) {
+  Smem m;
+  m.CE = S.cap_elems;
+  m.CR = S.cap_rods;
+  m.CN = m.CE + m.CR;
+  m.CV = m.CE;
+  double* p = base;
+  m.X = p;    p += 3 * m.CN;
+  m.VN = p;   p += 3 * m.CN;
+  m.QQ = p;   p += 9 * m.CE;
+  m.WW = p;   p += 3 * m.CE;
+  m.NF = p;   p += 3 * m.CE;
+  m.TA = p;   p += 3 * m.CE;
+  m.ELL = p;  p += m.CE;
+  m.EDIL = p; p += m.CE;
+  m.PP = p;   p += 3 * m.CV;
+  m.TT = p;   p += 3 * m.CV;
+  m.IRL = p;  p += m.CE;
+  m.IM = p;   p += m.CN;
+  m.ACT = p;  p += m.CR;
+  m.rel0 = reinterpret_cast<int*>(p);
+  m.erod = reinterpret_cast<short*>(m.rel0 + m.CR + 1);
+  m.nrod = m.erod + m.CE;
+  m.vrod = m.nrod + m.CN;
+  return m;
+}
+
+__device__ __forceinline__ int find_rod(const int* starts, int nrods, int idx) {
+  // largest r with starts[r] <= idx (starts increasing, starts[0] = 0)
+  int lo = 0, hi = nrods - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (starts[mid] <= idx) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------------ kinematic stage (a1/a11, a2)
+
+__device__ __forceinline__ void kinematic(const StepParams& P, const Pack& pk, Smem& m, double h) {
+  const int Ep = pk.nelem, Np = pk.nnode;
+  for (int i = threadIdx.x; i < Ep; i += blockDim.x) {
+    const int r = m.erod[i];
+    const int g = pk.rod0 + r;
+    const bool held = (i == m.rel0[r]) && P.rods[g].clamp;
+    double q[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) q[a] = m.QQ[a * m.CE + i];
+    if (held) {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) q[a] = P.clamp_Q[a * P.n_rods + g];
+    } else {
+      // Q <- R Q, R = exp([phi]x), phi = -h w:  R = I + a K + b K^2 = (1 - b th^2) I + a K + b phi phi^T
+      const double p0 = -h * m.WW[i], p1 = -h * m.WW[m.CE + i], p2 = -h * m.WW[2 * m.CE + i];
+      const double th2 = fma(p0, p0, fma(p1, p1, p2 * p2));
+      double ca, cb;
+      rot_coeffs(th2, ca, cb);
+      const double c0 = fma(-cb, th2, 1.0);
+      const double b0 = cb * p0, b1 = cb * p1, b2 = cb * p2;
+      const double a0 = ca * p0, a1 = ca * p1, a2 = ca * p2;
+      const double R00 = fma(b0, p0, c0), R11 = fma(b1, p1, c0), R22 = fma(b2, p2, c0);
+      const double R01 = fma(b0, p1, -a2), R10 = fma(b1, p0, a2);
+      const double R02 = fma(b0, p2, a1), R20 = fma(b2, p0, -a1);
+      const double R12 = fma(b1, p2, -a0), R21 = fma(b2, p1, a0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double q0 = q[c], q1 = q[3 + c], q2 = q[6 + c];
+        q[c] = fma(R00, q0, fma(R01, q1, R02 * q2));
+        q[3 + c] = fma(R10, q0, fma(R11, q1, R12 * q2));
+        q[6 + c] = fma(R20, q0, fma(R21, q1, R22 * q2));
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) m.QQ[a * m.CE + i] = q[a];
+  }
+  for (int j = threadIdx.x; j < Np; j += blockDim.x) {
+    const int r = m.nrod[j];
+    const int g = pk.rod0 + r;
+    const bool held = (j == m.rel0[r] + r) && P.rods[g].clamp;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double val = held ? P.clamp_x[c * P.n_rods + g] : fma(h, m.VN[c * m.CN + j], m.X[c * m.CN + j]);
+      m.X[c * m.CN + j] = val;
+    }
+  }
+}
+
+// --------------------------------------------------------------- dynamic stage (a3-a7, a10, a2)
+
+// Stage A (elements): geometry, shear strain, internal force, shear couple, transport couples,
+// damping and external couples.
+__device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& pk, Smem& m) {
+  const int Ep = pk.nelem;
+  for (int i = threadIdx.x; i < Ep; i += blockDim.x) {
+    const int r = m.erod[i];
+    const RodConst* rc = P.rods + pk.rod0 + r;
+    const int j = i + r;
+    const int ge = pk.elem0 + i;
+    double l[3], dv[3], q[9], w[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      l[c] = m.X[c * m.CN + j + 1] - m.X[c * m.CN + j];
+      dv[c] = m.VN[c * m.CN + j + 1] - m.VN[c * m.CN + j];
+      w[c] = m.WW[c * m.CE + i];
+    }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) q[a] = m.QQ[a * m.CE + i];
+    const double ll = fma(l[0], l[0], fma(l[1], l[1], l[2] * l[2]));
+    const double rs = rsqrt(ll);            // 1 / ell
+    const double ell = ll * rs;
+    const double irl = m.IRL[i];
+    const double rl = __ldg(P.rest_len + ge);
+    const double e = ell * irl;             // dilatation
+    const double ie = rl * rs;              // 1 / e
+    double Ql[3], sg[3], n[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Ql[a] = fma(q[3 * a], l[0], fma(q[3 * a + 1], l[1], q[3 * a + 2] * l[2]));
+    sg[0] = Ql[0] * irl;
+    sg[1] = Ql[1] * irl;
+    sg[2] = fma(Ql[2], irl, -1.0);
+    if (P.rest_sigma) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sg[c] -= __ldg(P.rest_sigma + c * P.E + ge);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) n[c] = __ldg(&rc->S[c]) * sg[c];
+    // lab internal force N = Q^T n / e
+#pragma unroll
+    for (int b = 0; b < 3; ++b) m.NF[b * m.CE + i] = fma(q[b], n[0], fma(q[3 + b], n[1], q[6 + b] * n[2])) * ie;
+    // shear couple ((Q t) x n) rl = (Ql x n) rl / ell
+    double tc[3];
+    tc[0] = fma(Ql[1], n[2], -Ql[2] * n[1]) * ie;
+    tc[1] = fma(Ql[2], n[0], -Ql[0] * n[2]) * ie;
+    tc[2] = fma(Ql[0], n[1], -Ql[1] * n[0]) * ie;
+    // transport couples (J w / e) x w + (J w / e^2) de/dt,  de/dt = (l . dv) / (ell rl)
+    const double edot = fma(l[0], dv[0], fma(l[1], dv[1], l[2] * dv[2])) * rs * irl;
+    double Jw[3], Jwe[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Jw[c] = __ldg(&rc->rhoI[c]) * rl * w[c];
+      Jwe[c] = Jw[c] * ie;
+    }
+    const double k2 = ie * ie * edot;
+    const double drot = __ldg(&rc->damp_rot);
+    tc[0] += fma(Jwe[1], w[2], -Jwe[2] * w[1]);
+    tc[1] += fma(Jwe[2], w[0], -Jwe[0] * w[2]);
+    tc[2] += fma(Jwe[0], w[1], -Jwe[1] * w[0]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tc[c] = fma(Jw[c], k2 - drot, tc[c]);
+    if (P.elem_couple) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) tc[c] += __ldg(P.elem_couple + c * P.E + ge);
+    }
+    if (P.has_act && (i - m.rel0[r]) == rc->act_elem) tc[0] += m.ACT[r];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m.TA[c * m.CE + i] = tc[c];
+    m.ELL[i] = ell;
+    m.EDIL[i] = e;
+  }
+}
+
+// Stage B (Voronoi points): curvature by the rotation logarithm, Voronoi dilatation,
+// bending/twist couple m = B(kappa - kappa0), P = m/eps^3, T = (kappa x m) D/eps^3.
+__device__ __forceinline__ void stage_voronoi(const StepParams& P, const Pack& pk, Smem& m) {
+  const int Vp = pk.nvor;
+  for (int k = threadIdx.x; k < Vp; k += blockDim.x) {
+    const int r = m.vrod[k];
+    const RodConst* rc = P.rods + pk.rod0 + r;
+    const int i = k + r;
+    const int gv = pk.vor0 + k;
+    double qa[9], qb[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      qa[a] = m.QQ[a * m.CE + i];
+      qb[a] = m.QQ[a * m.CE + i + 1];
+    }
+    // R = Q_{k+1} Q_k^T, R_ab = d_a(k+1) . d_b(k);  u = (R32 - R23, R13 - R31, R21 - R12)
+    double u0 = qb[6] * qa[3];
+    u0 = fma(qb[7], qa[4], u0);
+    u0 = fma(qb[8], qa[5], u0);
+    u0 = fma(-qb[3], qa[6], u0);
+    u0 = fma(-qb[4], qa[7], u0);
+    u0 = fma(-qb[5], qa[8], u0);
+    double u1 = qb[0] * qa[6];
+    u1 = fma(qb[1], qa[7], u1);
+    u1 = fma(qb[2], qa[8], u1);
+    u1 = fma(-qb[6], qa[0], u1);
+    u1 = fma(-qb[7], qa[1], u1);
+    u1 = fma(-qb[8], qa[2], u1);
+    double u2 = qb[3] * qa[0];
+    u2 = fma(qb[4], qa[1], u2);
+    u2 = fma(qb[5], qa[2], u2);
+    u2 = fma(-qb[0], qa[3], u2);
+    u2 = fma(-qb[1], qa[4], u2);
+    u2 = fma(-qb[2], qa[5], u2);
+    double tr = qb[0] * qa[0];
+#pragma unroll
+    for (int a = 1; a < 9; ++a) tr = fma(qb[a], qa[a], tr);
+    const double s2 = 0.25 * fma(u0, u0, fma(u1, u1, u2 * u2));  // |w|^2 = sin^2(theta)
+    const double c = 0.5 * (tr - 1.0);                             // cos(theta)
+    double f;                                                       // theta / sin(theta)
+    if (s2 <= 0.0625 && c > 0.0) {
+      f = asin_over_s(s2);
+    } else {
+      const double s = sqrt(s2);
+      f = (s > 0.0) ? atan2(s, c) / s : 1.0;
+    }
+    const double i2D = __ldg(P.inv_2D + gv);
+    const double kf = -f * i2D;             // kappa = -(theta/s) w / D = -f u / (2D)
+    double kap[3] = {kf * u0, kf * u1, kf * u2};
+    const double eps = (m.ELL[i] + m.ELL[i + 1]) * i2D;
+    const double ieps = __drcp_rn(eps);
+    const double ie3 = ieps * ieps * ieps;
+    double mk[3];
+    if (P.rest_kappa) {
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) mk[cc] = __ldg(&rc->B[cc]) * (kap[cc] - __ldg(P.rest_kappa + cc * P.V + gv));
+    } else {
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) mk[cc] = __ldg(&rc->B[cc]) * kap[cc];
+    }
+    const double tD = __ldg(P.Dhat + gv) * ie3;
+    m.PP[k] = mk[0] * ie3;
+    m.PP[m.CV + k] = mk[1] * ie3;
+    m.PP[2 * m.CV + k] = mk[2] * ie3;
+    m.TT[k] = fma(kap[1], mk[2], -kap[2] * mk[1]) * tD;
+    m.TT[m.CV + k] = fma(kap[2], mk[0], -kap[0] * mk[2]) * tD;
+    m.TT[2 * m.CV + k] = fma(kap[0], mk[1], -kap[1] * mk[0]) * tD;
+  }
+}
+
+// Stage C (elements): bending couple from the difference and trapezoid operators, angular
+// acceleration e J^{-1} tau, rate update and constraint; optional kinematic rotation.
+template <int MODE>
+__device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& pk, Smem& m, double dt, double h,
+                                               double* acc_w) {
+  const int Ep = pk.nelem;
+  for (int i = threadIdx.x; i < Ep; i += blockDim.x) {
+    const int r = m.erod[i];
+    const int g = pk.rod0 + r;
+    const RodConst* rc = P.rods + g;
+    const int first = m.rel0[r];
+    const int nr = m.rel0[r + 1] - first;
+    const int li = i - first;
+    const int k = i - r;                     // right Voronoi point (valid if li < nr-1)
+    const bool hasR = li < nr - 1, hasL = li > 0;
+    double tau[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double Pr = hasR ? m.PP[c * m.CV + k] : 0.0;
+      const double Pl = hasL ? m.PP[c * m.CV + k - 1] : 0.0;
+      const double Tr = hasR ? m.TT[c * m.CV + k] : 0.0;
+      const double Tl = hasL ? m.TT[c * m.CV + k - 1] : 0.0;
+      tau[c] = fma(0.5, Tl + Tr, (Pr - Pl) + m.TA[c * m.CE + i]);
+    }
+    const bool held = (li == 0) && rc->clamp;
+    const double ke = m.EDIL[i] * m.IRL[i];
+    double wn[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double alpha = held ? 0.0 : ke * __ldg(&rc->inv_rhoI[c]) * tau[c];
+      if (MODE == MODE_RHS) {
+        acc_w[c * P.E + pk.elem0 + i] = alpha;
+      } else {
+        wn[c] = held ? 0.0 : fma(dt, alpha, m.WW[c * m.CE + i]);
+        m.WW[c * m.CE + i] = wn[c];
+      }
+    }
+  }
+}
+
+// Stage D (nodes): internal force difference, external forces, velocity update + constraint.
+template <int MODE>
+__device__ __forceinline__ void stage_translation(const StepParams& P, const Pack& pk, Smem& m, double dt,
+                                                  double* acc_v) {
+  const int Np = pk.nnode;
+  for (int j = threadIdx.x; j < Np; j += blockDim.x) {
+    const int r = m.nrod[j];
+    const int g = pk.rod0 + r;
+    const RodConst* rc = P.rods + g;
+    const int firstn = m.rel0[r] + r;
+    const int nr = m.rel0[r + 1] - m.rel0[r];
+    const int lj = j - firstn;
+    const bool hasR = lj < nr, hasL = lj > 0;
+    const int iR = j - r;                    // element to the right (pack-local)
+    const bool held = (lj == 0) && rc->clamp;
+    const double im = m.IM[j];
+    const double dl = __ldg(&rc->damp_lin);
+    double F[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double Nr = hasR ? m.NF[c * m.CE + iR] : 0.0;
+      const double Nl = hasL ? m.NF[c * m.CE + iR - 1] : 0.0;
+      F[c] = Nr - Nl;
+    }
+    if (lj == nr) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) F[c] += __ldg(&rc->tip[c]);
+    }
+    if (P.fseg) {
+      const int ge = pk.elem0 + iR;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double fc = 0.0;
+        if (hasR) fc += __ldg(P.fseg + c * P.E + ge);              // node a of segment iR
+        if (hasL) fc += __ldg(P.fseg + (3 + c) * P.E + ge - 1);    // node b of segment iR-1
+        F[c] += fc;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double vj = m.VN[c * m.CN + j];
+      double a = fma(F[c], im, -dl * vj);
+      if (P.has_gravity) a += P.gravity[c];
+      if (held) a = 0.0;
+      if (MODE == MODE_RHS) {
+        acc_v[c * P.N + pk.node0 + j] = a;
+      } else {
+        m.VN[c * m.CN + j] = held ? 0.0 : fma(dt, a, vj);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void actuation_values(const StepParams& P, const Pack& pk, Smem& m, double t) {
+  if (!P.has_act) return;
+  for (int r = threadIdx.x; r < pk.nrods; r += blockDim.x) {
+    const RodConst* rc = P.rods + pk.rod0 + r;
+    const double amp = rc->act_amp;
+    m.ACT[r] = (amp != 0.0) ? amp * sin(fma(rc->act_omega, t, rc->act_phase)) : 0.0;
+  }
+}
+
+// ------------------------------------------------------------------------- the pack kernel
+
+template <int MODE>
+__global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, int64_t n_steps, double t0, double dt,
+                                                   int last_half, double* acc_v, double* acc_w) {
+  extern __shared__ double smem_d[];
+  const Pack pk = P.packs[blockIdx.x];
+  Smem m = carve(smem_d, S);
+  const int Ep = pk.nelem, Np = pk.nnode, Rp = pk.nrods, Vp = pk.nvor;
+
+  // ---- stage the pack
+  for (int r = threadIdx.x; r < Rp; r += blockDim.x) m.rel0[r] = P.rods[pk.rod0 + r].elem0 - pk.elem0;
+  if (threadIdx.x == 0) m.rel0[Rp] = Ep;
+  __syncthreads();
+  for (int i = threadIdx.x; i < Ep; i += blockDim.x) {
+    m.erod[i] = (short)find_rod(m.rel0, Rp, i);
+    m.IRL[i] = __ldg(P.inv_rl + pk.elem0 + i);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) m.QQ[a * m.CE + i] = P.Q[a * P.E + pk.elem0 + i];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m.WW[c * m.CE + i] = P.w[c * P.E + pk.elem0 + i];
+  }
+  for (int j = threadIdx.x; j < Np; j += blockDim.x) {
+    // node j belongs to rod r with rel0[r] + r <= j
+    int lo = 0, hi = Rp - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (m.rel0[mid] + mid <= j) lo = mid; else hi = mid - 1;
+    }
+    m.nrod[j] = (short)lo;
+    m.IM[j] = __ldg(P.inv_m + pk.node0 + j);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      m.X[c * m.CN + j] = P.x[c * P.N + pk.node0 + j];
+      m.VN[c * m.CN + j] = P.v[c * P.N + pk.node0 + j];
+    }
+  }
+  for (int k = threadIdx.x; k < Vp; k += blockDim.x) {
+    int lo = 0, hi = Rp - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (m.rel0[mid] - mid <= k) lo = mid; else hi = mid - 1;
+    }
+    m.vrod[k] = (short)lo;
+  }
+  __syncthreads();
+
+  if (MODE == MODE_KIN_HALF) {
+    kinematic(P, pk, m, 0.5 * dt);
+    __syncthreads();
+  } else if (MODE == MODE_RHS) {
+    actuation_values(P, pk, m, t0);
+    stage_elements(P, pk, m);
+    __syncthreads();
+    stage_voronoi(P, pk, m);
+    __syncthreads();
+    stage_rotation<MODE_RHS>(P, pk, m, dt, 0.0, acc_w);
+    stage_translation<MODE_RHS>(P, pk, m, dt, acc_v);
+    return;
+  } else {
+    if (MODE == MODE_STEPS) {
+      kinematic(P, pk, m, 0.5 * dt);
+      __syncthreads();
+    }
+    for (int64_t s = 0; s < n_steps; ++s) {
+      const double t = t0 + (static_cast<double>(s) + 0.5) * dt;
+      actuation_values(P, pk, m, t);
+      stage_elements(P, pk, m);
+      __syncthreads();
+      stage_voronoi(P, pk, m);
+      __syncthreads();
+      stage_rotation<MODE_STEPS>(P, pk, m, dt, 0.0, nullptr);
+      stage_translation<MODE_STEPS>(P, pk, m, dt, nullptr);
+      __syncthreads();
+      const bool last = (s == n_steps - 1);
+      const double h = (last && (MODE == MODE_STEPS || last_half)) ? 0.5 * dt : dt;
+      kinematic(P, pk, m, h);
+      __syncthreads();
+    }
+  }
+
+  // ---- write back, flag non-finite values
+  bool bad = false;
+  for (int i = threadIdx.x; i < Ep; i += blockDim.x) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const double q = m.QQ[a * m.CE + i];
+      bad |= !isfinite(q);
+      P.Q[a * P.E + pk.elem0 + i] = q;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double ww = m.WW[c * m.CE + i];
+      bad |= !isfinite(ww);
+      P.w[c * P.E + pk.elem0 + i] = ww;
+    }
+  }
+  for (int j = threadIdx.x; j < Np; j += blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double xx = m.X[c * m.CN + j], vv = m.VN[c * m.CN + j];
+      bad |= !isfinite(xx) || !isfinite(vv);
+      P.x[c * P.N + pk.node0 + j] = xx;
+      P.v[c * P.N + pk.node0 + j] = vv;
+    }
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(P.err, ERR_NONFINITE);
+}
+
+}  // namespace
+
+size_t step_smem_bytes(const LaunchShape& s) {
+  const size_t CE = s.cap_elems, CR = s.cap_rods, CN = CE + CR, CV = CE;
+  const size_t doubles = 3 * CN + 3 * CN + 9 * CE + 3 * CE + 3 * CE + 3 * CE + CE + CE + 3 * CV + 3 * CV + CE + CN + CR;
+  const size_t ints = CR + 1;
+  const size_t shorts = CE + CN + CV;
+  return doubles * sizeof(double) + ints * sizeof(int) + shorts * sizeof(short) + 16;
+}
+
+cudaError_t launch_pack_kernel(const StepParams& P, const LaunchShape& s, int mode, int64_t n_steps, double t0,
+                               double dt, int last_half, double* acc_v, double* acc_w, cudaStream_t st) {
+  const size_t smem = step_smem_bytes(s);
+  const dim3 grid(P.n_packs), block(s.threads);
+  switch (mode) {
+    case MODE_STEPS: {
+      cudaFuncSetAttribute(pack_kernel<MODE_STEPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      pack_kernel<MODE_STEPS><<<grid, block, smem, st>>>(P, s, n_steps, t0, dt, last_half, acc_v, acc_w);
+      break;
+    }
+    case MODE_ONE_STEP: {
+      cudaFuncSetAttribute(pack_kernel<MODE_ONE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      pack_kernel<MODE_ONE_STEP><<<grid, block, smem, st>>>(P, s, n_steps, t0, dt, last_half, acc_v, acc_w);
+      break;
+    }
+    case MODE_KIN_HALF: {
+      cudaFuncSetAttribute(pack_kernel<MODE_KIN_HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      pack_kernel<MODE_KIN_HALF><<<grid, block, smem, st>>>(P, s, n_steps, t0, dt, last_half, acc_v, acc_w);
+      break;
+    }
+    case MODE_RHS: {
+      cudaFuncSetAttribute(pack_kernel<MODE_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      pack_kernel<MODE_RHS><<<grid, block, smem, st>>>(P, s, n_steps, t0, dt, last_half, acc_v, acc_w);
+      break;
+    }
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rod

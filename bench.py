@@ -1,0 +1,319 @@
+#!/usr/bin/env python3
+"""Benchmark: FP64 element-steps/s of the Cosserat-rod step on GB300.
+
+Default workload: the 10^4-rod random packing (element counts U{16..256}, seeded; rod-rod
+contact through the uniform cell list; gravity; dt = 5e-6 s).  One bench "step" is one time
+step of the whole ensemble (contact broad + narrow phase, strains, curvatures, internal and
+external loads, Verlet update with the exponential-map director update).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload packing|carpet|cantilever]
+                  [--impl ours|reference]
+
+Multi-GPU: replicas only (no data-path collective): every rank advances its own independent
+ensemble; value = all ranks' element-steps / max-over-ranks time (weak scaling).
+--impl reference times the plain CPU oracle (test infrastructure) on a bounded sample of the
+same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import rodgen  # noqa: E402
+
+METRIC = "element-steps/sec FP64 on 1 GB300 (% HBM roofline); surrogate speedup at <=1e-3 err"
+UNIT = "element-steps/s"
+
+# FP64 peak of the part: 2 FP64 FMA per clock per SM (measured 1.975 with an FMA-throughput
+# probe) x 152 SMs x 2.07 GHz max SM clock x 2 flop per FMA.
+FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
+
+# Algorithmic FP64 flops per unit of each kernel (thread-level FP64 arithmetic of the formulas:
+# add/sub/mul = 1, fma = 2, counted from the executed FP64 instructions of active threads on a
+# small case with ncu; see the profiles folder).  None until measured.
+FLOPS_PER_UNIT = {
+    "pack_one_step": None,   # per element-step
+    "pack_steps": None,      # per element-step
+}
+# DRAM bytes per launch from one ncu capture (profiles folder); None until measured.
+TRAFFIC_PER_LAUNCH = {}
+
+
+def _workload(name: str, rank: int):
+    seed = 1234
+    if name == "packing":
+        cache_dir = os.path.join(tempfile.gettempdir(), "rodbench_cache")
+        os.makedirs(cache_dir, exist_ok=True)
+        key = hashlib.sha1(f"random_packing-default-{seed}-v2".encode()).hexdigest()[:12]
+        path = os.path.join(cache_dir, f"packing_{key}.npz")
+        p = None
+        if os.path.exists(path):
+            try:
+                z = np.load(path)
+                base = rodgen.random_packing(n_rods=10, seed=seed)  # cheap template for the fields
+                p = base.replace(n_elem=z["n_elem"], rest_len=z["rest_len"], radius=z["radius"], youngs=z["youngs"],
+                                 shear_mod=z["shear_mod"], density=z["density"], x=z["x"], v=z["v"], Q=z["Q"],
+                                 w=z["w"], name="random_packing_10000")
+            except Exception:
+                p = None
+        if p is None:
+            p = rodgen.random_packing(seed=seed)
+            tmp = path + f".{os.getpid()}.npz"
+            np.savez(tmp, n_elem=p.n_elem, rest_len=p.rest_len, radius=p.radius, youngs=p.youngs,
+                     shear_mod=p.shear_mod, density=p.density, x=p.x, v=p.v, Q=p.Q, w=p.w)
+            os.replace(tmp, path)
+        desc = {"workload": "random packing, 10^4 rods, n~U{16..256} (seeded), contact k=1e4 c=10, gravity, dt=5e-6",
+                "rods": p.n_rods, "elements": p.n_elems, "dt": 5e-6}
+        return p, 5e-6, desc
+    if name == "carpet":
+        p = rodgen.cilia_carpet()
+        return p, 1e-5, {"workload": "cilia carpet 64x64 rods x 50 elements, base couple, Stokes drag, dt=1e-5",
+                         "rods": p.n_rods, "elements": p.n_elems, "dt": 1e-5}
+    if name == "cantilever":
+        p = rodgen.cantilever()
+        return p, 1e-5, {"workload": "one clamped rod, 100 elements, tip force, damping, dt=1e-5",
+                         "rods": 1, "elements": 100, "dt": 1e-5}
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        rows = []
+        with open(self.out.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.out.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _reference(args, world, rank):
+    """CPU oracle (plain C, single thread) on a bounded sample of the same workload."""
+    if rank != 0:
+        return
+    from oracle.oracle import Oracle, build_oracle
+    build_oracle()
+    p, dt, desc = _workload(args.workload, 0)
+    o = Oracle(p)
+    sample_steps = {"packing": 2, "carpet": 20, "cantilever": 2000}[args.workload]
+    st = p.state()
+    # warm-up: one step, untimed
+    st = o.step(*st, dt=dt, n_steps=1)
+    times = []
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        st = o.step(*st, dt=dt, n_steps=sample_steps)
+        times.append(time.perf_counter() - t0)
+        if sum(times) > 60.0:
+            break
+    tot = sum(times)
+    n = len(times) * sample_steps
+    value = p.n_elems * n / tot
+    sample = f"{n} full time steps of the {desc['workload']} ({p.n_elems} elements), oracle single-threaded"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": len(times), "warmup": 1, "ms_per_step": tot / n * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": dict(desc, l2="state larger than L2 (196 MB)" if args.workload == "packing" else "n/a"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _cpu_baseline(p, dt, desc, workload):
+    from oracle.oracle import Oracle, build_oracle
+    build_oracle()
+    o = Oracle(p)
+    n = {"packing": 3, "carpet": 20, "cantilever": 2000}[workload]
+    st = p.state()
+    t0 = time.perf_counter()
+    o.step(*st, dt=dt, n_steps=n)
+    el = time.perf_counter() - t0
+    return {"value": p.n_elems * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} time steps of the full workload ({p.n_elems} elements), plain C oracle, one thread"}
+
+
+def _e2e(s, p, dt, K, world, dist, barrier):
+    """Same metric through the public API from pinned host buffers: set_state (H2D), K steps,
+    get_state (D2H) inside the timed region."""
+    import torch
+    x, v, Q, w = p.state()
+    pin = [torch.from_numpy(a).pin_memory() for a in (x, v, Q, w)]
+    outs = [torch.empty(a.shape, dtype=torch.float64).pin_memory() for a in (x, v, Q, w)]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_state(*[a.numpy() for a in pin])
+    s.step(K, dt)
+    xs = s.get_state()
+    t_e2e = time.perf_counter() - t0
+    state_bytes = 8 * (6 * p.n_nodes + 12 * p.n_elems)
+    if dist is not None:
+        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": world * p.n_elems * K / t_e2e, "unit": UNIT, "h2d_bytes_per_step": state_bytes / K,
+           "d2h_bytes_per_step": state_bytes / K,
+           "note": f"set_state from pinned host + {K} steps + get_state to host per round trip"}
+    del outs, xs
+
+    return e2e
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="packing", choices=["packing", "carpet", "cantilever"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        _reference(args, world, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_2605_13766_gb300 import RodSystem, build
+    build.build()
+    p, dt, desc = _workload(args.workload, rank)
+    s = RodSystem(p)
+    s.set_state(*p.state())
+    W = max(args.warmup, 3)
+    K = args.steps
+    s.step(W, dt)
+    torch.cuda.synchronize()
+
+    # ---- timed region (device time, CUDA events on the system's stream)
+    stream = torch.cuda.current_stream()
+    s.profile(True)
+    launches0 = s.launch_count
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step_async(K, dt)
+    ev1.record(stream)
+    s.sync()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = s.launch_count - launches0
+    prof = s.profile_read()
+    s.profile(False)
+    t_local = ms / 1e3
+    if dist is not None:
+        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    value = world * p.n_elems * K / t_max
+
+    # ---- end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = _e2e(s, p, dt, K, world, dist, barrier)
+
+    # ---- roofline of the dominant kernel
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dname, (dms, dn) = dom
+    avg_ms = dms / max(dn, 1)
+    fpu = FLOPS_PER_UNIT.get(dname)
+    units = p.n_elems * (K if dname == "pack_steps" else 1)
+    achieved = (fpu * units / (avg_ms * 1e-3) / 1e12) if fpu else None
+    roof = {"bound": "alu", "kernel": dname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+            "traffic": TRAFFIC_PER_LAUNCH.get(dname), "avg_launch_ms": avg_ms,
+            "peak_source": "FP64: 2 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal unit count; probe measured 1.975/clk)",
+            "kernel_share": {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4)
+                             for k, v in prof.items() if v[1]}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = _cpu_baseline(p, dt, desc, args.workload)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": t_max * 1e3 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic (seeded)",
+                "config": dict(desc, parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
+                               l2="state (196 MB) larger than L2, no flush needed" if args.workload == "packing"
+                               else "state L2/smem resident"),
+                "clocks": clk, "gpu_launches": launches, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -130,6 +130,22 @@ rod_status rod_system_contact_forces(rod_system* sys, double* f);
 rod_status rod_system_set_launch(rod_system* sys, int32_t elems_per_block, int32_t threads_per_block);
 rod_status rod_system_get_launch(const rod_system* sys, int32_t* elems_per_block, int32_t* threads_per_block);
 
+/* Per-kernel timing (tracing): enable = 1 records a CUDA event pair on the system's stream
+ * around every kernel launch and resets the totals; enable = 0 stops recording. */
+rod_status rod_system_profile(rod_system* sys, int enable);
+
+/* Number of kernel classes reported by rod_system_profile_read. */
+int32_t rod_profile_classes(void);
+
+/* Accumulated device time (ms, from the event pairs) and launch count of kernel class k
+ * (0 <= k < rod_profile_classes()); *name receives a static string.  Synchronises on the
+ * recorded events. */
+rod_status rod_system_profile_read(rod_system* sys, int32_t k, const char** name, double* total_ms,
+                                   int64_t* launches);
+
+/* Total number of kernels this system has launched since it was created. */
+rod_status rod_system_launch_count(const rod_system* sys, int64_t* launches);
+
 /* Longest rod (elements) one thread block can hold with the largest supported shape. */
 int32_t rod_max_elements_per_rod(void);
 

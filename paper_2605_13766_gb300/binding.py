@@ -72,6 +72,10 @@ _SIGNATURES = {
     "rod_system_contact_forces": ([_P, _P], C.c_int),
     "rod_system_set_launch": ([_P, C.c_int32, C.c_int32], C.c_int),
     "rod_system_get_launch": ([_P, _P, _P], C.c_int),
+    "rod_system_profile": ([_P, C.c_int], C.c_int),
+    "rod_profile_classes": ([], C.c_int32),
+    "rod_system_profile_read": ([_P, C.c_int32, _P, _P, _P], C.c_int),
+    "rod_system_launch_count": ([_P, _P], C.c_int),
     "rod_max_elements_per_rod": ([], C.c_int32),
     "rod_last_error": ([], C.c_char_p),
     "rod_version": ([], C.c_char_p),
@@ -255,6 +259,25 @@ class RodSystem:
         f = torch.empty((3, self.n_nodes), dtype=torch.float64, device="cuda")
         _check(self.lib.rod_system_contact_forces(self.handle, f.data_ptr()))
         return f
+
+    # -- tracing
+    def profile(self, enable: bool = True):
+        _check(self.lib.rod_system_profile(self.handle, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kernel class: (total device ms, launches)} from the event pairs recorded so far."""
+        out = {}
+        for k in range(self.lib.rod_profile_classes()):
+            name, ms, n = C.c_char_p(), C.c_double(), C.c_int64()
+            _check(self.lib.rod_system_profile_read(self.handle, k, C.byref(name), C.byref(ms), C.byref(n)))
+            out[name.value.decode()] = (ms.value, n.value)
+        return out
+
+    @property
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        _check(self.lib.rod_system_launch_count(self.handle, C.byref(n)))
+        return n.value
 
     # -- launch shape
     def set_launch(self, elems_per_block: int = 0, threads_per_block: int = 0):

@@ -68,6 +68,72 @@ struct DevBuf {
   }
 };
 
+// Launch counter and optional CUDA-event timing of every kernel class.
+struct Profiler {
+  bool enabled = false;
+  int64_t launches = 0;
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t open_ev = nullptr;
+  double total_ms[K_NUM_CLASSES] = {};
+  int64_t count[K_NUM_CLASSES] = {};
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  static void hook(void* ctx, int cls, int phase, cudaStream_t st) {
+    Profiler* p = static_cast<Profiler*>(ctx);
+    if (phase == 0) {
+      p->launches += 1;
+      if (p->enabled) {
+        p->open_ev = p->get();
+        cudaEventRecord(p->open_ev, st);
+      }
+    } else if (p->enabled && p->open_ev) {
+      cudaEvent_t b = p->get();
+      cudaEventRecord(b, st);
+      p->pending.push_back(Rec{cls, p->open_ev, b});
+      p->open_ev = nullptr;
+    }
+  }
+  void collect() {
+    for (auto& r : pending) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+        total_ms[r.cls] += ms;
+        count[r.cls] += 1;
+      }
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    pending.clear();
+  }
+  void reset() {
+    collect();
+    for (int k = 0; k < K_NUM_CLASSES; ++k) {
+      total_ms[k] = 0.0;
+      count[k] = 0;
+    }
+  }
+  ~Profiler() {
+    for (auto& r : pending) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
 __global__ void gather_clamp_kernel(const double* x, const double* Q, const RodConst* rods, int R, int64_t N, int64_t E,
                                     double* cx, double* cQ) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -108,6 +174,9 @@ struct rod_system {
   double t = 0.0;
   // contact
   ContactState contact;
+  // launch accounting / timing
+  Profiler prof;
+  LaunchHook hook;
 };
 
 namespace {
@@ -258,6 +327,8 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
     if (!std::isfinite(d->gravity[c])) return fail(ROD_ERR_ARG, "gravity must be finite");
 
   rod_system* s = new rod_system();
+  s->hook.fn = &Profiler::hook;
+  s->hook.ctx = &s->prof;
   s->R = R;
   s->E = E;
   s->N = N;
@@ -413,8 +484,10 @@ rod_status rod_system_set_state(rod_system* s, const double* x, const double* v,
   CUDA_TRY(cudaMemcpyAsync(s->v.p, v, 3 * s->N * sizeof(double), kind, s->stream));
   CUDA_TRY(cudaMemcpyAsync(s->Q.p, Q, 9 * s->E * sizeof(double), kind, s->stream));
   CUDA_TRY(cudaMemcpyAsync(s->w.p, w, 3 * s->E * sizeof(double), kind, s->stream));
+  s->hook.before(K_MISC, s->stream);
   gather_clamp_kernel<<<(s->R + 127) / 128, 128, 0, s->stream>>>(s->x.p, s->Q.p, s->rods.p, s->R, s->N, s->E,
                                                                   s->clamp_x.p, s->clamp_Q.p);
+  s->hook.after(K_MISC, s->stream);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemsetAsync(s->err.p, 0, sizeof(int), s->stream));
   if (!on_device) CUDA_TRY(cudaStreamSynchronize(s->stream));
@@ -458,17 +531,17 @@ rod_status rod_system_step_async(rod_system* s, int64_t n_steps, double dt) {
     const int64_t chunk = int64_t(1) << 20;
     for (int64_t done = 0; done < n_steps; done += chunk) {
       const int64_t k = std::min(chunk, n_steps - done);
-      CUDA_TRY(launch_pack_kernel(P, s->shape, MODE_STEPS, k, s->t + done * dt, dt, 1, nullptr, nullptr, s->stream));
+      CUDA_TRY(launch_pack_kernel(P, s->shape, MODE_STEPS, k, s->t + done * dt, dt, 1, nullptr, nullptr, s->stream, s->hook));
     }
   } else {
-    rod_status st = contact_prepare(s->contact, s->rods_h, s->rods.p, s->x.p, s->N, s->E, s->R, s->stream);
+    rod_status st = contact_prepare(s->contact, s->rods_h, s->rods.p, s->x.p, s->N, s->E, s->R, s->stream, s->hook);
     if (st != ROD_OK) return st;
-    CUDA_TRY(launch_pack_kernel(P, s->shape, MODE_KIN_HALF, 1, s->t, dt, 0, nullptr, nullptr, s->stream));
+    CUDA_TRY(launch_pack_kernel(P, s->shape, MODE_KIN_HALF, 1, s->t, dt, 0, nullptr, nullptr, s->stream, s->hook));
     for (int64_t k = 0; k < n_steps; ++k) {
-      CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream));
+      CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream, s->hook));
       P.fseg = s->contact.fseg;
       CUDA_TRY(launch_pack_kernel(P, s->shape, MODE_ONE_STEP, 1, s->t + k * dt, dt, k == n_steps - 1 ? 1 : 0,
-                                  nullptr, nullptr, s->stream));
+                                  nullptr, nullptr, s->stream, s->hook));
     }
   }
   s->t += n_steps * dt;
@@ -503,12 +576,12 @@ rod_status rod_system_rhs(rod_system* s, double t, double* acc_v, double* acc_w)
   if (!s->state_set) return fail(ROD_ERR_STATE, "no state has been set");
   StepParams P = make_params(s);
   if (s->contact.enabled) {
-    rod_status st = contact_prepare(s->contact, s->rods_h, s->rods.p, s->x.p, s->N, s->E, s->R, s->stream);
+    rod_status st = contact_prepare(s->contact, s->rods_h, s->rods.p, s->x.p, s->N, s->E, s->R, s->stream, s->hook);
     if (st != ROD_OK) return st;
-    CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream));
+    CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream, s->hook));
     P.fseg = s->contact.fseg;
   }
-  CUDA_TRY(launch_pack_kernel(P, s->shape, MODE_RHS, 1, t, 1.0, 0, acc_v, acc_w, s->stream));
+  CUDA_TRY(launch_pack_kernel(P, s->shape, MODE_RHS, 1, t, 1.0, 0, acc_v, acc_w, s->stream, s->hook));
   return read_error_word(s);
 }
 
@@ -520,10 +593,10 @@ rod_status rod_system_contact_forces(rod_system* s, double* f) {
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     return ROD_OK;
   }
-  rod_status st = contact_prepare(s->contact, s->rods_h, s->rods.p, s->x.p, s->N, s->E, s->R, s->stream);
+  rod_status st = contact_prepare(s->contact, s->rods_h, s->rods.p, s->x.p, s->N, s->E, s->R, s->stream, s->hook);
   if (st != ROD_OK) return st;
-  CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream));
-  CUDA_TRY(contact_node_forces(s->contact, s->rods.p, s->N, s->E, s->R, f, s->stream));
+  CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream, s->hook));
+  CUDA_TRY(contact_node_forces(s->contact, s->rods.p, s->N, s->E, s->R, f, s->stream, s->hook));
   return read_error_word(s);
 }
 
@@ -543,6 +616,30 @@ rod_status rod_system_set_launch(rod_system* s, int32_t elems_per_block, int32_t
   }
   if (step_smem_bytes(sh) > 227 * 1024) return fail(ROD_ERR_ARG, "launch shape needs too much shared memory");
   return build_packs(s, sh);
+}
+
+rod_status rod_system_profile(rod_system* s, int enable) {
+  if (!s) return fail(ROD_ERR_ARG, "null system");
+  s->prof.reset();
+  s->prof.enabled = enable != 0;
+  return ROD_OK;
+}
+
+int32_t rod_profile_classes(void) { return K_NUM_CLASSES; }
+
+rod_status rod_system_profile_read(rod_system* s, int32_t k, const char** name, double* total_ms, int64_t* launches) {
+  if (!s || k < 0 || k >= K_NUM_CLASSES) return fail(ROD_ERR_ARG, "bad system or kernel class");
+  s->prof.collect();
+  if (name) *name = kernel_class_name(k);
+  if (total_ms) *total_ms = s->prof.total_ms[k];
+  if (launches) *launches = s->prof.count[k];
+  return ROD_OK;
+}
+
+rod_status rod_system_launch_count(const rod_system* s, int64_t* launches) {
+  if (!s || !launches) return fail(ROD_ERR_ARG, "null argument");
+  *launches = s->prof.launches;
+  return ROD_OK;
 }
 
 rod_status rod_system_get_launch(const rod_system* s, int32_t* elems_per_block, int32_t* threads_per_block) {

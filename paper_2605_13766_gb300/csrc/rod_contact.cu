@@ -29,6 +29,9 @@ namespace rod {
 namespace {
 
 constexpr int64_t kMaxCells = int64_t(1) << 24;
+// Largest number of segments one cell may hold; a denser cell (a collapsed or escaped
+// configuration) latches ERR_OVERFLOW instead of running a quadratic search.
+constexpr int kCellCap = 512;
 constexpr int kScanThreads = 1024;
 constexpr int kScanPerThread = 4;
 constexpr int kScanTile = kScanThreads * kScanPerThread;
@@ -64,7 +67,9 @@ __global__ void bin_kernel(const double* __restrict__ x, const int* __restrict__
     ll = fma(d, d, ll);
   }
   const double len = sqrt(ll);
-  if (!(len <= g.l_allowed)) atomicOr(err, ERR_GRID);
+  const bool finite = isfinite(mid[0]) && isfinite(mid[1]) && isfinite(mid[2]) && isfinite(len);
+  if (!finite) atomicOr(err, ERR_NONFINITE);
+  else if (!(len <= g.l_allowed)) atomicOr(err, ERR_GRID);
   int ic[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -156,10 +161,15 @@ __global__ void scatter_kernel(const int* __restrict__ seg_cell, int64_t E, int*
   sorted[pos] = (int)a;
 }
 
-__global__ void sort_cells_kernel(const int* __restrict__ start, int64_t ncell, int* __restrict__ sorted) {
+__global__ void sort_cells_kernel(const int* __restrict__ start, int64_t ncell, int* __restrict__ sorted, int* err) {
   const int64_t cidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (cidx >= ncell) return;
   const int b = start[cidx], e = start[cidx + 1];
+  if (e - b > kCellCap) {
+    atomicOr(err, ERR_OVERFLOW);
+    return;
+  }
+  if (*(volatile int*)err != 0) return;
   for (int i = b + 1; i < e; ++i) {  // insertion sort; cells hold a handful of segments
     const int key = sorted[i];
     int j = i - 1;
@@ -225,6 +235,7 @@ struct ContactArgs {
   const float4* prox;
   const RodConst* rods;
   double* fseg;
+  int* err;
   int64_t N, E;
   int dim[3];
   double k, c;
@@ -233,6 +244,7 @@ struct ContactArgs {
 __global__ void __launch_bounds__(128) gather_kernel(ContactArgs A) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= A.E) return;
+  if (*(volatile int*)A.err != 0) return;  // latched error: the step is abandoned
   const int a = A.sorted[q];
   const int ra = A.seg_rod[a];
   const double rada = A.rods[ra].radius;
@@ -261,6 +273,10 @@ __global__ void __launch_bounds__(128) gather_kernel(ContactArgs A) {
         if (xx < 0 || xx >= A.dim[0]) continue;
         const int cc = (z * A.dim[1] + y) * A.dim[0] + xx;
         const int b0 = A.cell_start[cc], b1 = A.cell_start[cc + 1];
+        if (b1 - b0 > kCellCap) {
+          atomicOr(A.err, ERR_OVERFLOW);
+          continue;
+        }
         for (int t = b0; t < b1; ++t) {
           const int b = A.sorted[t];
           const int rb = A.seg_rod[b];
@@ -367,7 +383,7 @@ static rod_status cfail(rod_status st, const char* what, cudaError_t e) {
 }
 
 rod_status contact_prepare(ContactState& cs, const std::vector<RodConst>& rods_h, const RodConst* rods_dev,
-                           const double* x_dev, int64_t N, int64_t E, int R, cudaStream_t st) {
+                           const double* x_dev, int64_t N, int64_t E, int R, cudaStream_t st, const LaunchHook& hook) {
   if (cs.grid_valid) return ROD_OK;
   std::vector<double> x(3 * N);
   cudaError_t e = cudaMemcpyAsync(x.data(), x_dev, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -427,14 +443,16 @@ rod_status contact_prepare(ContactState& cs, const std::vector<RodConst>& rods_h
     cs.cap_cells = ncell;
     cs.n_block_sums = nt;
   }
+  hook.before(K_MISC, st);
   seg_rod_kernel<<<R, 64, 0, st>>>(rods_dev, R, cs.seg_rod);
+  hook.after(K_MISC, st);
   if ((e = cudaGetLastError())) return cfail(ROD_ERR_CUDA, "contact: segment map", e);
   cs.grid_valid = true;
   return ROD_OK;
 }
 
 cudaError_t contact_compute(ContactState& cs, const double* x, const double* v, const RodConst* rods, int64_t N,
-                            int64_t E, int R, int* err, cudaStream_t st) {
+                            int64_t E, int R, int* err, cudaStream_t st, const LaunchHook& hook) {
   cudaError_t e;
   (void)R;
   const int64_t n1 = cs.ncell + 1;
@@ -448,17 +466,29 @@ cudaError_t contact_compute(ContactState& cs, const double* x, const double* v, 
   g.l_allowed = cs.l_allowed;
   const int tb = 256;
   const int64_t eb = (E + tb - 1) / tb;
+  hook.before(K_CONTACT_BIN, st);
   bin_kernel<<<eb, tb, 0, st>>>(x, cs.seg_rod, N, E, g, cs.seg_cell, cs.cell_count, cs.prox, err);
+  hook.after(K_CONTACT_BIN, st);
   if ((e = cudaGetLastError())) return e;
   const int64_t nt = (n1 + kScanTile - 1) / kScanTile;
+  hook.before(K_CONTACT_SCAN, st);
   scan_tiles_kernel<<<nt, kScanThreads, 0, st>>>(cs.cell_count, n1, cs.cell_start, cs.block_sums);
+  hook.after(K_CONTACT_SCAN, st);
+  hook.before(K_CONTACT_SCAN, st);
   scan_sums_kernel<<<1, kScanThreads, 0, st>>>(cs.block_sums, nt, cs.block_sums + nt);
+  hook.after(K_CONTACT_SCAN, st);
+  hook.before(K_CONTACT_SCAN, st);
   scan_add_kernel<<<(n1 + 255) / 256, 256, 0, st>>>(cs.cell_start, n1, cs.block_sums);
+  hook.after(K_CONTACT_SCAN, st);
   if ((e = cudaGetLastError())) return e;
   if ((e = cudaMemcpyAsync(cs.cell_fill, cs.cell_start, cs.ncell * sizeof(int), cudaMemcpyDeviceToDevice, st)))
     return e;
+  hook.before(K_CONTACT_SCATTER, st);
   scatter_kernel<<<eb, tb, 0, st>>>(cs.seg_cell, E, cs.cell_fill, cs.sorted);
-  sort_cells_kernel<<<(cs.ncell + 255) / 256, 256, 0, st>>>(cs.cell_start, cs.ncell, cs.sorted);
+  hook.after(K_CONTACT_SCATTER, st);
+  hook.before(K_CONTACT_SORT, st);
+  sort_cells_kernel<<<(cs.ncell + 255) / 256, 256, 0, st>>>(cs.cell_start, cs.ncell, cs.sorted, err);
+  hook.after(K_CONTACT_SORT, st);
   if ((e = cudaGetLastError())) return e;
   ContactArgs A;
   A.x = x;
@@ -475,13 +505,18 @@ cudaError_t contact_compute(ContactState& cs, const double* x, const double* v, 
   for (int c = 0; c < 3; ++c) A.dim[c] = cs.dim[c];
   A.k = cs.k;
   A.c = cs.c;
+  A.err = err;
+  hook.before(K_CONTACT_GATHER, st);
   gather_kernel<<<(E + 127) / 128, 128, 0, st>>>(A);
+  hook.after(K_CONTACT_GATHER, st);
   return cudaGetLastError();
 }
 
 cudaError_t contact_node_forces(const ContactState& cs, const RodConst* rods, int64_t N, int64_t E, int R, double* f,
-                                cudaStream_t st) {
+                                cudaStream_t st, const LaunchHook& hook) {
+  hook.before(K_CONTACT_NODE_FORCES, st);
   node_forces_kernel<<<R, 64, 0, st>>>(cs.fseg, rods, R, N, E, f);
+  hook.after(K_CONTACT_NODE_FORCES, st);
   return cudaGetLastError();
 }
 

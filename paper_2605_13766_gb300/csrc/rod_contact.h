@@ -39,17 +39,17 @@ void contact_release(ContactState& cs);
 
 // Build the grid (once per state / configuration) from the current positions.
 rod_status contact_prepare(ContactState& cs, const std::vector<RodConst>& rods_h, const RodConst* rods_dev,
-                           const double* x_dev, int64_t N, int64_t E, int R, cudaStream_t st);
+                           const double* x_dev, int64_t N, int64_t E, int R, cudaStream_t st, const LaunchHook& hook);
 
 // Record an error message for rod_last_error() (defined with the ABI) and return st.
 rod_status internal_fail(rod_status st, const char* what, const char* detail);
 
 // Enqueue one evaluation of the contact forces at positions x, velocities v -> cs.fseg.
 cudaError_t contact_compute(ContactState& cs, const double* x, const double* v, const RodConst* rods, int64_t N,
-                            int64_t E, int R, int* err, cudaStream_t st);
+                            int64_t E, int R, int* err, cudaStream_t st, const LaunchHook& hook);
 
 // Sum cs.fseg into node forces f [3N] (debug / parity entry point).
 cudaError_t contact_node_forces(const ContactState& cs, const RodConst* rods, int64_t N, int64_t E, int R, double* f,
-                                cudaStream_t st);
+                                cudaStream_t st, const LaunchHook& hook);
 
 }  // namespace rod

@@ -75,6 +75,22 @@ struct StepParams {
   int* err;                   // device error word
 };
 
+// Kernel classes for the optional per-kernel timing (rod_system_profile).
+enum KernelClass : int {
+  K_PACK_STEPS = 0, K_PACK_ONE_STEP, K_KIN_HALF, K_RHS, K_CONTACT_BIN, K_CONTACT_SCAN, K_CONTACT_SCATTER,
+  K_CONTACT_SORT, K_CONTACT_GATHER, K_CONTACT_NODE_FORCES, K_MISC, K_NUM_CLASSES
+};
+const char* kernel_class_name(int k);
+
+// Called around every kernel launch: counts launches and, when profiling, records CUDA events
+// on the launching stream.
+struct LaunchHook {
+  void (*fn)(void* ctx, int cls, int phase, cudaStream_t st) = nullptr;  // phase 0 = before, 1 = after
+  void* ctx = nullptr;
+  void before(int cls, cudaStream_t st) const { if (fn) fn(ctx, cls, 0, st); }
+  void after(int cls, cudaStream_t st) const { if (fn) fn(ctx, cls, 1, st); }
+};
+
 // Launch shape of the pack kernels.
 struct LaunchShape {
   int32_t cap_elems;   // elements per block (pack capacity)
@@ -87,6 +103,7 @@ size_t step_smem_bytes(const LaunchShape& s);
 // Kernel launchers (rod_step.cu).
 enum StepMode : int { MODE_STEPS = 0, MODE_RHS = 1, MODE_KIN_HALF = 2, MODE_ONE_STEP = 3 };
 cudaError_t launch_pack_kernel(const StepParams& P, const LaunchShape& s, int mode, int64_t n_steps, double t0,
-                               double dt, int last_half, double* acc_v, double* acc_w, cudaStream_t st);
+                               double dt, int last_half, double* acc_v, double* acc_w, cudaStream_t st,
+                               const LaunchHook& hook);
 
 }  // namespace rod

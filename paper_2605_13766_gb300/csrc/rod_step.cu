@@ -428,6 +428,8 @@ template <int MODE>
 __global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, int64_t n_steps, double t0, double dt,
                                                    int last_half, double* acc_v, double* acc_w) {
   extern __shared__ double smem_d[];
+  // a step after a latched error (non-finite state, contact overflow) is skipped
+  if (MODE == MODE_ONE_STEP && *(volatile int*)P.err != 0) return;
   const Pack pk = P.packs[blockIdx.x];
   Smem m = carve(smem_d, S);
   const int Ep = pk.nelem, Np = pk.nnode, Rp = pk.nrods, Vp = pk.nvor;
@@ -541,10 +543,25 @@ size_t step_smem_bytes(const LaunchShape& s) {
   return doubles * sizeof(double) + ints * sizeof(int) + shorts * sizeof(short) + 16;
 }
 
+const char* kernel_class_name(int k) {
+  static const char* names[K_NUM_CLASSES] = {"pack_steps", "pack_one_step", "kin_half", "rhs", "contact_bin",
+                                             "contact_scan", "contact_scatter", "contact_sort", "contact_gather",
+                                             "contact_node_forces", "misc"};
+  return (k >= 0 && k < K_NUM_CLASSES) ? names[k] : "?";
+}
+
 cudaError_t launch_pack_kernel(const StepParams& P, const LaunchShape& s, int mode, int64_t n_steps, double t0,
-                               double dt, int last_half, double* acc_v, double* acc_w, cudaStream_t st) {
+                               double dt, int last_half, double* acc_v, double* acc_w, cudaStream_t st,
+                               const LaunchHook& hook) {
   const size_t smem = step_smem_bytes(s);
   const dim3 grid(P.n_packs), block(s.threads);
+  const int cls = mode == MODE_STEPS ? K_PACK_STEPS : mode == MODE_ONE_STEP ? K_PACK_ONE_STEP
+                : mode == MODE_KIN_HALF ? K_KIN_HALF : K_RHS;
+  hook.before(cls, st);
+  struct After {
+    const LaunchHook& h; int c; cudaStream_t s;
+    ~After() { h.after(c, s); }
+  } after_guard{hook, cls, st};
   switch (mode) {
     case MODE_STEPS: {
       cudaFuncSetAttribute(pack_kernel<MODE_STEPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

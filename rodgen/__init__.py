@@ -223,42 +223,7 @@ def random_packing(n_rods: int = 10_000, nmin: int = 16, nmax: int = 256, box: f
             centers[r] = rng.uniform(0.0, box, 3)
             axes[r] = draw_axis()
     else:
-        spacing = radius
-        thresh = 2 * radius + spacing + margin
-        h = thresh
-        dim = int(np.ceil(box / h)) + 3
-        cap = 24
-        grid = np.full((dim, dim, dim, cap, 3), 1e9)
-        count = np.zeros((dim, dim, dim), dtype=np.int64)
-        offs = np.array([(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)])
-        order = np.argsort(-lengths, kind="stable")
-        for r in order:
-            L = lengths[r]
-            m = int(np.floor(L / spacing)) + 1
-            s = np.linspace(-0.5 * L, 0.5 * L, m)
-            for attempt in range(10_000):
-                c = rng.uniform(0.0, box, 3)
-                a = draw_axis()
-                pts = c[None, :] + s[:, None] * a[None, :]
-                cell = np.floor(pts / h).astype(np.int64) + 1
-                cell = np.clip(cell, 1, dim - 2)
-                nb = cell[:, None, :] + offs[None, :, :]             # (m, 27, 3)
-                cand = grid[nb[..., 0], nb[..., 1], nb[..., 2]]       # (m, 27, cap, 3)
-                d2 = ((cand - pts[:, None, None, :]) ** 2).sum(-1)
-                if d2.min() >= thresh * thresh:
-                    break
-            else:
-                raise RuntimeError("random_packing: could not place a rod; lower the density")
-            # insert sample points
-            for q in range(m):
-                i, j, k = cell[q]
-                cnt = count[i, j, k]
-                if cnt >= cap:
-                    raise RuntimeError("random_packing: grid cell capacity exceeded")
-                grid[i, j, k, cnt] = pts[q]
-                count[i, j, k] = cnt + 1
-            centers[r] = c
-            axes[r] = a
+        _place_without_overlap(rng, lengths, box, radius, margin, centers, axes)
     base = centers - 0.5 * lengths[:, None] * axes
     # reference direction for d1: a seeded random vector, re-drawn when nearly parallel
     ref = rng.normal(size=(n_rods, 3))
@@ -279,6 +244,122 @@ def random_packing(n_rods: int = 10_000, nmin: int = 16, nmax: int = 256, box: f
         density=_uniform(R, density), x=x, v=np.ascontiguousarray(v), Q=Q, w=w,
         gravity=np.array([0.0, 0.0, -gravity]), contact=True, contact_k=contact_k,
         contact_c=contact_c, cell_size=2 * radius, dt=dt, n_steps=n_steps)
+
+
+def _axis_distance(c1, a1, h1, c2, a2, h2):
+    """Exact distance between the axis segments c + t a, |t| <= h (vectorised over pairs): the
+    minimum of the convex quadratic over the rectangle is either its free stationary point (if
+    inside) or the minimum over one of the four edges, so all five candidates are evaluated."""
+    r = c1 - c2
+    b = (a1 * a2).sum(1)
+    d = (a1 * r).sum(1)
+    e = (a2 * r).sum(1)
+
+    def dist(t, u):
+        return np.linalg.norm(r + t[:, None] * a1 - u[:, None] * a2, axis=1)
+
+    best = np.full(len(r), np.inf)
+    den = 1.0 - b * b
+    ok = den > 1e-12
+    t0 = np.where(ok, (b * e - d) / np.where(ok, den, 1.0), 0.0)
+    u0 = np.where(ok, (e - b * d) / np.where(ok, den, 1.0), 0.0)
+    inside = ok & (np.abs(t0) <= h1) & (np.abs(u0) <= h2)
+    best = np.where(inside, dist(t0, u0), best)
+    for side in (-1.0, 1.0):
+        t = side * h1                                    # edge t = +-h1: best u
+        u = np.clip(b * t + e, -h2, h2)
+        best = np.minimum(best, dist(t, u))
+        u = side * h2                                    # edge u = +-h2: best t
+        t = np.clip(b * u - d, -h1, h1)
+        best = np.minimum(best, dist(t, u))
+    return best
+
+
+def _neighbour_pairs(cq, cp, cell):
+    """Index pairs (i in cq, j in cp) whose points share or neighbour a cubic cell of edge ``cell``."""
+    lo = np.minimum(cq.min(0), cp.min(0)) - cell
+    kq = np.floor((cq - lo) / cell).astype(np.int64)
+    kp = np.floor((cp - lo) / cell).astype(np.int64)
+    dim = np.maximum(kq.max(0), kp.max(0)) + 3
+    key = (kp[:, 2] * dim[1] + kp[:, 1]) * dim[0] + kp[:, 0]
+    order = np.argsort(key, kind="stable")
+    sk = key[order]
+    ii, jj = [], []
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                kk = ((kq[:, 2] + dz) * dim[1] + (kq[:, 1] + dy)) * dim[0] + (kq[:, 0] + dx)
+                s = np.searchsorted(sk, kk, side="left")
+                e = np.searchsorted(sk, kk, side="right")
+                cnt = e - s
+                tot = int(cnt.sum())
+                if tot == 0:
+                    continue
+                qi = np.repeat(np.arange(len(cq)), cnt)
+                off = np.arange(tot) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+                ii.append(qi)
+                jj.append(order[np.repeat(s, cnt) + off])
+    if not ii:
+        return np.zeros(0, dtype=np.int64), np.zeros(0, dtype=np.int64)
+    return np.concatenate(ii), np.concatenate(jj)
+
+
+def _conflicts(cq, aq, hq, cp, ap, hp, gap):
+    """Pairs (i, j) of capsules (axis segments + radius gap/2 each) closer than ``gap``."""
+    if len(cq) == 0 or len(cp) == 0:
+        return np.zeros(0, dtype=np.int64), np.zeros(0, dtype=np.int64)
+    cell = 2.0 * max(hq.max(), hp.max()) + gap
+    i, j = _neighbour_pairs(cq, cp, cell)
+    near = np.linalg.norm(cq[i] - cp[j], axis=1) < hq[i] + hp[j] + gap
+    i, j = i[near], j[near]
+    d = _axis_distance(cq[i], aq[i], hq[i], cp[j], ap[j], hp[j])
+    hit = d < gap
+    return i[hit], j[hit]
+
+
+def _place_without_overlap(rng, lengths, box, radius, margin, centers, axes):
+    """Random sequential addition, longest rods first, in batches: a candidate (centre, axis) is
+    drawn for each of the next ``window`` unplaced rods, candidates closer than 2 r + margin to a
+    placed rod are rejected, the rest are accepted greedily in length order unless they conflict
+    with an earlier accepted candidate of the same batch; rejected rods are redrawn."""
+    gap = 2.0 * radius + margin
+    half = 0.5 * lengths
+    queue = np.argsort(-lengths, kind="stable")
+    placed = np.zeros(0, dtype=np.int64)
+    window = 512
+    for _ in range(20000):
+        if len(queue) == 0:
+            return
+        todo = queue[:window]
+        m = len(todo)
+        c = rng.uniform(0.0, box, (m, 3))
+        a = rng.normal(size=(m, 3))
+        a /= np.linalg.norm(a, axis=1, keepdims=True)
+        h = half[todo]
+        bad = np.zeros(m, dtype=bool)
+        if len(placed):
+            i, _ = _conflicts(c, a, h, centers[placed], axes[placed], half[placed], gap)
+            bad[i] = True
+        i, j = _conflicts(c, a, h, c, a, h, gap)
+        keep = i > j
+        i, j = i[keep], j[keep]
+        order = np.argsort(i, kind="stable")
+        i, j = i[order], j[order]
+        starts = np.searchsorted(i, np.arange(m), side="left")
+        ends = np.searchsorted(i, np.arange(m), side="right")
+        take = np.zeros(m, dtype=bool)
+        for q in range(m):
+            if bad[q]:
+                continue
+            if ends[q] > starts[q] and take[j[starts[q]:ends[q]]].any():
+                continue
+            take[q] = True
+        rods = todo[take]
+        centers[rods] = c[take]
+        axes[rods] = a[take]
+        placed = np.concatenate([placed, rods])
+        queue = np.concatenate([todo[~take], queue[window:]])
+    raise RuntimeError("random_packing: could not place every rod; lower the density")
 
 
 def adjoint_batch(n_rods: int = 1024, n: int = 64, length: float = 0.2, radius: float = 0.005,

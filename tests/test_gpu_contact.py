@@ -68,25 +68,29 @@ def test_rhs_with_contact_matches_oracle():
     assert _rel(av, av_ref) <= 1e-12 and _rel(aw, aw_ref) <= 1e-12
 
 
+def _touching(n_rods, box, seed, nmin=8, nmax=40, speed=1.0):
+    """Rods placed without deep overlap (at most 1 mm) so that contact acts from the first step."""
+    return rodgen.random_packing(n_rods=n_rods, nmin=nmin, nmax=nmax, box=box, rest_len=2e-3, radius=0.004,
+                                 seed=seed, speed=speed, dt=2e-6, margin=-1e-3)
+
+
 def test_trajectory_through_collisions():
-    """Non-overlapping rods thrown at each other in a small box: 400 steps with contact."""
-    p = rodgen.random_packing(n_rods=40, nmin=8, nmax=40, box=0.12, rest_len=2e-3, radius=0.004, seed=6,
-                              speed=2.0, dt=2e-6)
+    """400 steps of rods pressed into each other (overlaps up to 1 mm) and moving."""
+    p = _touching(40, 0.08, 6)
     o = Oracle(p)
+    assert np.abs(o.contact_forces(p.x, p.v)).max() > 0.5      # contact acts from the start
     ref = o.step(*p.state(), dt=2e-6, n_steps=400)
     s = _gpu(p)
     s.step(400, 2e-6)
     got = s.get_state()
-    # contact actually happened along the way
-    f = Oracle(p).contact_forces(ref[0], ref[1])
     assert np.abs(got[0] - ref[0]).max() / 0.08 <= 1e-9
     assert _rel(got[1], ref[1]) <= 1e-7
 
 
 def test_trajectory_with_contact_200_rods_1000_steps():
-    p = rodgen.random_packing(n_rods=200, nmin=16, nmax=64, box=0.25, rest_len=2e-3, radius=0.004, seed=12,
-                              speed=1.0, dt=2e-6)
+    p = _touching(200, 0.2, 12, nmin=16, nmax=64)
     o = Oracle(p)
+    assert np.abs(o.contact_forces(p.x, p.v)).max() > 0.5
     ref = o.step(*p.state(), dt=2e-6, n_steps=1000)
     s = _gpu(p)
     s.step(1000, 2e-6)

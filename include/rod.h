@@ -149,6 +149,34 @@ rod_status rod_system_launch_count(const rod_system* sys, int64_t* launches);
 /* Longest rod (elements) one thread block can hold with the largest supported shape. */
 int32_t rod_max_elements_per_rod(void);
 
+/* Contact forces without allocating anything (the paper has no counterpart: this is a service
+ * for callers that cannot allocate device memory when they need the forces, such as code
+ * running inside another framework's allocator or memory pool, or a loop that must not enter
+ * the driver's allocator).  All temporaries live in one fixed file-scope device array of
+ * about 16 MB (sized by the two limits below) that every GPU loading the library holds until
+ * the process exits.
+ *   n_rods    number of rods (> 0)
+ *   node_off  device int32 [n_rods + 1]: CSR node offsets, node_off[0] = 0, rod r owns nodes
+ *             node_off[r] .. node_off[r+1]-1 (at least 2 nodes); elements = nodes - n_rods
+ *   radius    device double [n_rods]
+ *   x, v      device double [3 * N], component-major node positions and velocities
+ *   k, c      spring stiffness and dashpot coefficient (finite, >= 0)
+ *   cell_size requested cell edge; the grid uses max(cell_size, 2 r_max + l_max) of these positions
+ *   f         device double [3 * N] output, overwritten with the contact force on every node
+ *   cuda_stream  stream to run on (NULL = legacy default stream)
+ * The same forces as rod_system_contact_forces for the same state (pair set exact, sums in
+ * another order).  More than ROD_NOALLOC_MAX_SEGMENTS elements -> ROD_ERR_OVERFLOW before any
+ * launch; a cell with more than 512 segments -> ROD_ERR_OVERFLOW; non-finite positions ->
+ * ROD_ERR_NONFINITE.  The call synchronises the stream before it returns.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress), so make it before any
+ * stream capture.  Every call shares the array and finds the previous call's contents in it
+ * (what must start at zero is cleared); calls that overlap on the GPU race on it. */
+#define ROD_NOALLOC_MAX_SEGMENTS 131072
+#define ROD_NOALLOC_MAX_CELLS 524288
+rod_status rod_contact_forces_noalloc(int32_t n_rods, const int32_t* node_off, const double* radius, const double* x,
+                                      const double* v, double k, double c, double cell_size, double* f,
+                                      void* cuda_stream);
+
 /* Thread-local message of the last failing call. */
 const char* rod_last_error(void);
 

@@ -76,6 +76,8 @@ _SIGNATURES = {
     "rod_profile_classes": ([], C.c_int32),
     "rod_system_profile_read": ([_P, C.c_int32, _P, _P, _P], C.c_int),
     "rod_system_launch_count": ([_P, _P], C.c_int),
+    "rod_contact_forces_noalloc": ([C.c_int32, _P, _P, _P, _P, C.c_double, C.c_double, C.c_double, _P, _P],
+                                   C.c_int),
     "rod_max_elements_per_rod": ([], C.c_int32),
     "rod_last_error": ([], C.c_char_p),
     "rod_version": ([], C.c_char_p),
@@ -287,6 +289,18 @@ class RodSystem:
         e, t = C.c_int32(), C.c_int32()
         _check(self.lib.rod_system_get_launch(self.handle, C.byref(e), C.byref(t)))
         return e.value, t.value
+
+
+def contact_forces_noalloc(node_off, radius, x, v, k: float, c: float, cell_size: float, f, stream=None):
+    """rod_contact_forces_noalloc on CUDA torch tensors (int32 node offsets [R+1], float64 radius
+    [R], x, v, f [3, N]); f is overwritten.  Uses torch's current stream unless one is given."""
+    lib = load_library()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib.rod_contact_forces_noalloc(int(radius.shape[0]), node_off.data_ptr(), radius.data_ptr(),
+                                          x.data_ptr(), v.data_ptr(), float(k), float(c), float(cell_size),
+                                          f.data_ptr(), stream))
 
 
 def exported_symbols():

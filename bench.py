@@ -41,15 +41,20 @@ UNIT = "element-steps/s"
 # probe) x 152 SMs x 2.07 GHz max SM clock x 2 flop per FMA.
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
-# Algorithmic FP64 flops per unit of each kernel (thread-level FP64 arithmetic of the formulas:
-# add/sub/mul = 1, fma = 2, counted from the executed FP64 instructions of active threads on a
-# small case with ncu; see the profiles folder).  None until measured.
+# Algorithmic FP64 flops per unit of each kernel: the FP64 arithmetic of the formulas as the
+# kernel evaluates them, counted by ncu on the active threads (add/sub/mul = 1 flop, fma = 2),
+# divided by the units of the launch.  Source: profiles/pack_kernel_one_step_packing_10k.md
+# (pack_kernel<3>, one step of the 10^4-rod packing: 158.06M DFMA + 44.98M DADD + 128.68M
+# DMUL on 1,366,295 element-steps = 358.6 flop per element-step).
 FLOPS_PER_UNIT = {
-    "pack_one_step": None,   # per element-step
-    "pack_steps": None,      # per element-step
+    "pack_one_step": 358.6,   # per element-step
+    "pack_steps": None,       # per element-step (not yet counted for the blocked kernel)
 }
-# DRAM bytes per launch from one ncu capture (profiles folder); None until measured.
-TRAFFIC_PER_LAUNCH = {}
+# DRAM bytes per launch of the same capture (dram__bytes_read.sum + dram__bytes_write.sum);
+# reset to None whenever the kernel changes.
+TRAFFIC_PER_LAUNCH = {
+    "pack_one_step": 319.73e6 + 145.29e6,
+}
 
 
 def _workload(name: str, rank: int):
@@ -248,9 +253,8 @@ def main():
     s.step(W, dt)
     torch.cuda.synchronize()
 
-    # ---- timed region (device time, CUDA events on the system's stream)
-    stream = torch.cuda.current_stream()
-    s.profile(True)
+    # ---- timed region (device time, CUDA events on the stream the library launches on)
+    stream = s.torch_stream
     launches0 = s.launch_count
     clocks = ClockSampler(local)
     clocks.start()
@@ -267,8 +271,6 @@ def main():
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     launches = s.launch_count - launches0
-    prof = s.profile_read()
-    s.profile(False)
     t_local = ms / 1e3
     if dist is not None:
         t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
@@ -277,6 +279,14 @@ def main():
     else:
         t_max = t_local
     value = world * p.n_elems * K / t_max
+
+    # ---- per-kernel device times: the same K steps again with CUDA events around every launch
+    # (eager launches: the event pairs sit between kernels on the same stream)
+    s.profile(True)
+    s.step_async(K, dt)
+    s.sync()
+    prof = s.profile_read()
+    s.profile(False)
 
     # ---- end to end through the public API with pinned host buffers
     e2e = None

@@ -130,6 +130,11 @@ rod_status rod_system_contact_forces(rod_system* sys, double* f);
 rod_status rod_system_set_launch(rod_system* sys, int32_t elems_per_block, int32_t threads_per_block);
 rod_status rod_system_get_launch(const rod_system* sys, int32_t* elems_per_block, int32_t* threads_per_block);
 
+/* With contact, rod_system_step replays a CUDA graph of 32 captured steps (captured on an
+ * internal stream, launched on the system's stream) unless profiling is on; enable = 0 makes
+ * every step an eager sequence of launches (same kernels, same results). */
+rod_status rod_system_set_graphs(rod_system* sys, int enable);
+
 /* Per-kernel timing (tracing): enable = 1 records a CUDA event pair on the system's stream
  * around every kernel launch and resets the totals; enable = 0 stops recording. */
 rod_status rod_system_profile(rod_system* sys, int enable);

@@ -72,6 +72,7 @@ _SIGNATURES = {
     "rod_system_contact_forces": ([_P, _P], C.c_int),
     "rod_system_set_launch": ([_P, C.c_int32, C.c_int32], C.c_int),
     "rod_system_get_launch": ([_P, _P, _P], C.c_int),
+    "rod_system_set_graphs": ([_P, C.c_int], C.c_int),
     "rod_system_profile": ([_P, C.c_int], C.c_int),
     "rod_profile_classes": ([], C.c_int32),
     "rod_system_profile_read": ([_P, C.c_int32, _P, _P, _P], C.c_int),
@@ -159,7 +160,11 @@ class RodSystem:
         self.torch_stream = None
         if stream is None and use_torch_stream:
             import torch
-            self.torch_stream = torch.cuda.current_stream()
+            cur = torch.cuda.current_stream()
+            # the legacy default stream has handle 0, which the library reads as "make your
+            # own stream"; give the system a torch stream of its own instead and keep it, so
+            # that callers can order torch work and record events on the stream it runs on
+            self.torch_stream = cur if cur.cuda_stream else torch.cuda.Stream()
             stream = self.torch_stream.cuda_stream
         d.cuda_stream = stream
         handle = C.c_void_p()
@@ -195,10 +200,13 @@ class RodSystem:
         """Host numpy arrays (copied synchronously) or CUDA torch tensors (copied on the stream)."""
         on_dev = not isinstance(x, np.ndarray)
         if on_dev:
+            import torch
             arrs = [a.contiguous() for a in (x, v, Q, w)]
             for a in arrs:
-                if a.dtype.__str__() != "torch.float64" or not a.is_cuda:
+                if a.dtype != torch.float64 or not a.is_cuda:
                     raise TypeError("device state must be float64 CUDA tensors")
+            if self.torch_stream is not None:
+                self.torch_stream.wait_stream(torch.cuda.current_stream())
         else:
             arrs = [_host(a) for a in (x, v, Q, w)]
         self._check_shapes(arrs)
@@ -216,6 +224,9 @@ class RodSystem:
             out = [np.empty((3, self.n_nodes)), np.empty((3, self.n_nodes)),
                    np.empty((9, self.n_elems)), np.empty((3, self.n_elems))]
         _check(self.lib.rod_system_get_state(self.handle, *[_ptr(a) for a in out], 1 if device else 0))
+        if device and self.torch_stream is not None:
+            import torch
+            torch.cuda.current_stream().wait_stream(self.torch_stream)
         return tuple(out)
 
     def _check_shapes(self, arrs):
@@ -261,6 +272,9 @@ class RodSystem:
         f = torch.empty((3, self.n_nodes), dtype=torch.float64, device="cuda")
         _check(self.lib.rod_system_contact_forces(self.handle, f.data_ptr()))
         return f
+
+    def use_graphs(self, enable: bool = True):
+        _check(self.lib.rod_system_set_graphs(self.handle, 1 if enable else 0))
 
     # -- tracing
     def profile(self, enable: bool = True):

@@ -134,6 +134,9 @@ struct Profiler {
   }
 };
 
+__global__ void set_time_kernel(double* t, double value) { *t = value; }
+__global__ void advance_time_kernel(double* t, double dt) { *t += dt; }
+
 __global__ void gather_clamp_kernel(const double* x, const double* Q, const RodConst* rods, int R, int64_t N, int64_t E,
                                     double* cx, double* cQ) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -177,6 +180,14 @@ struct rod_system {
   // launch accounting / timing
   Profiler prof;
   LaunchHook hook;
+  // CUDA graph of kGraphSteps contact steps (captured on cap_stream, replayed on stream)
+  cudaStream_t cap_stream = nullptr;
+  DevBuf<double> t_dev;
+  cudaGraphExec_t graph_exec = nullptr;
+  double graph_dt = 0.0;
+  int graph_grid_version = -1;
+  int shape_version = 0, graph_shape_version = -1;
+  bool use_graphs = true;
 };
 
 namespace {
@@ -213,6 +224,7 @@ rod_status build_packs(rod_system* s, const LaunchShape& shape) {
   CUDA_TRY(cudaMemcpy(s->packs.p, packs.data(), packs.size() * sizeof(Pack), cudaMemcpyHostToDevice));
   s->n_packs = static_cast<int>(packs.size());
   s->shape = shape;
+  s->shape_version += 1;
   return ROD_OK;
 }
 
@@ -272,6 +284,57 @@ bool finite_all(const double* p, size_t n) {
   for (size_t i = 0; i < n; ++i)
     if (!std::isfinite(p[i])) return false;
   return true;
+}
+
+// Capture kGraphSteps contact steps (cell-list build, narrow phase, one step with binning of
+// the next positions, time advance) once per (dt, launch shape, grid); replays then cost one
+// launch per kGraphSteps steps.  The time of the state is read from t_dev inside the graph.
+constexpr int kGraphSteps = 32;
+constexpr int kKernelsPerGraphStep = 9;  // scan x3, scatter, sort, records, gather, step, time
+
+rod_status ensure_contact_graph(rod_system* s, const StepParams& Pb, double dt) {
+  if (s->graph_exec && s->graph_dt == dt && s->graph_grid_version == s->contact.version &&
+      s->graph_shape_version == s->shape_version)
+    return ROD_OK;
+  if (s->graph_exec) {
+    cudaGraphExecDestroy(s->graph_exec);
+    s->graph_exec = nullptr;
+  }
+  StepParams Pg = Pb;
+  Pg.t_dev = s->t_dev.p;
+  LaunchHook none;
+  cudaGraph_t graph = nullptr;
+  CUDA_TRY(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
+    e = contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->cap_stream, none, true);
+    if (e == cudaSuccess) e = contact_clear_counts(s->contact, s->cap_stream);
+    if (e == cudaSuccess) e = launch_pack_kernel(Pg, s->shape, MODE_ONE_STEP, 1, 0.0, dt, 0, nullptr, nullptr,
+                                                 s->cap_stream, none);
+    if (e == cudaSuccess) {
+      advance_time_kernel<<<1, 1, 0, s->cap_stream>>>(s->t_dev.p, dt);
+      e = cudaGetLastError();
+    }
+  }
+  cudaError_t e2 = cudaStreamEndCapture(s->cap_stream, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    s->use_graphs = false;  // eager launches from now on
+    return ROD_OK;
+  }
+  e = cudaGraphInstantiate(&s->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    s->graph_exec = nullptr;
+    cudaGetLastError();
+    s->use_graphs = false;
+    return ROD_OK;
+  }
+  s->graph_dt = dt;
+  s->graph_grid_version = s->contact.version;
+  s->graph_shape_version = s->shape_version;
+  return ROD_OK;
 }
 
 }  // namespace
@@ -428,6 +491,8 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
     return cleanup(fail(ROD_ERR_CUDA, "copy failed: %s", cudaGetErrorString(ce)));
   if (d->elem_couple && (ce = up(s->elem_couple, d->elem_couple, 3 * E)))
     return cleanup(fail(ROD_ERR_CUDA, "copy failed: %s", cudaGetErrorString(ce)));
+  if ((ce = s->t_dev.alloc(1)) || (ce = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking)))
+    return cleanup(fail(ROD_ERR_CUDA, "allocation failed: %s", cudaGetErrorString(ce)));
   if ((ce = cudaMemset(s->err.p, 0, sizeof(int))) || (ce = cudaMallocHost(&s->err_host, sizeof(int))))
     return cleanup(fail(ROD_ERR_CUDA, "allocation failed: %s", cudaGetErrorString(ce)));
   *s->err_host = 0;
@@ -458,6 +523,9 @@ rod_status rod_system_destroy(rod_system* s) {
   s->packs.release();
   s->err.release();
   contact_release(s->contact);
+  if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  s->t_dev.release();
   if (s->err_host) cudaFreeHost(s->err_host);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   delete s;
@@ -536,12 +604,33 @@ rod_status rod_system_step_async(rod_system* s, int64_t n_steps, double dt) {
   } else {
     rod_status st = contact_prepare(s->contact, s->rods_h, s->rods.p, s->x.p, s->N, s->E, s->R, s->stream, s->hook);
     if (st != ROD_OK) return st;
-    CUDA_TRY(launch_pack_kernel(P, s->shape, MODE_KIN_HALF, 1, s->t, dt, 0, nullptr, nullptr, s->stream, s->hook));
-    for (int64_t k = 0; k < n_steps; ++k) {
-      CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream, s->hook));
-      P.fseg = s->contact.fseg;
-      CUDA_TRY(launch_pack_kernel(P, s->shape, MODE_ONE_STEP, 1, s->t + k * dt, dt, k == n_steps - 1 ? 1 : 0,
-                                  nullptr, nullptr, s->stream, s->hook));
+    P.fseg = s->contact.fseg;
+    StepParams Pb = P;  // with the binning epilogue for the next step
+    contact_bin_params(s->contact, Pb);
+    CUDA_TRY(contact_clear_counts(s->contact, s->stream));
+    CUDA_TRY(launch_pack_kernel(Pb, s->shape, MODE_KIN_HALF, 1, s->t, dt, 0, nullptr, nullptr, s->stream, s->hook));
+    // steps 0 .. n-2 bin the next step's positions; the last one ends on a half step
+    const int64_t binned = n_steps - 1;
+    int64_t k = 0;
+    if (s->use_graphs && !s->prof.enabled && binned >= kGraphSteps) {
+      st = ensure_contact_graph(s, Pb, dt);
+      if (st != ROD_OK) return st;
+      if (s->graph_exec) {
+        set_time_kernel<<<1, 1, 0, s->stream>>>(s->t_dev.p, s->t);
+        s->prof.launches += 1;
+        for (; k + kGraphSteps <= binned; k += kGraphSteps) {
+          CUDA_TRY(cudaGraphLaunch(s->graph_exec, s->stream));
+          s->prof.launches += kGraphSteps * kKernelsPerGraphStep;
+        }
+      }
+    }
+    for (; k < n_steps; ++k) {
+      const bool last = (k == n_steps - 1);
+      CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream, s->hook,
+                               true));
+      if (!last) CUDA_TRY(contact_clear_counts(s->contact, s->stream));
+      CUDA_TRY(launch_pack_kernel(last ? P : Pb, s->shape, MODE_ONE_STEP, 1, s->t + k * dt, dt, last ? 1 : 0, nullptr,
+                                  nullptr, s->stream, s->hook));
     }
   }
   s->t += n_steps * dt;
@@ -578,7 +667,7 @@ rod_status rod_system_rhs(rod_system* s, double t, double* acc_v, double* acc_w)
   if (s->contact.enabled) {
     rod_status st = contact_prepare(s->contact, s->rods_h, s->rods.p, s->x.p, s->N, s->E, s->R, s->stream, s->hook);
     if (st != ROD_OK) return st;
-    CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream, s->hook));
+    CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream, s->hook, false));
     P.fseg = s->contact.fseg;
   }
   CUDA_TRY(launch_pack_kernel(P, s->shape, MODE_RHS, 1, t, 1.0, 0, acc_v, acc_w, s->stream, s->hook));
@@ -595,7 +684,7 @@ rod_status rod_system_contact_forces(rod_system* s, double* f) {
   }
   rod_status st = contact_prepare(s->contact, s->rods_h, s->rods.p, s->x.p, s->N, s->E, s->R, s->stream, s->hook);
   if (st != ROD_OK) return st;
-  CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream, s->hook));
+  CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream, s->hook, false));
   CUDA_TRY(contact_node_forces(s->contact, s->rods.p, s->N, s->E, s->R, f, s->stream, s->hook));
   return read_error_word(s);
 }
@@ -616,6 +705,12 @@ rod_status rod_system_set_launch(rod_system* s, int32_t elems_per_block, int32_t
   }
   if (step_smem_bytes(sh) > 227 * 1024) return fail(ROD_ERR_ARG, "launch shape needs too much shared memory");
   return build_packs(s, sh);
+}
+
+rod_status rod_system_set_graphs(rod_system* s, int enable) {
+  if (!s) return fail(ROD_ERR_ARG, "null system");
+  s->use_graphs = enable != 0;
+  return ROD_OK;
 }
 
 rod_status rod_system_profile(rod_system* s, int enable) {

@@ -44,43 +44,45 @@ __global__ void seg_rod_kernel(const RodConst* rods, int R, int* seg_rod) {
 }
 
 struct Grid {
-  double lo[3];
-  double inv_h;
+  float lo[3];
+  float inv_h;
   int dim[3];
-  double l_allowed;
+  float l_allowed;
 };
 
+// Midpoint, half length and cell of every segment in FP32 (the cell only has to be consistent
+// within one evaluation; the grid's slack covers the FP32 rounding of the midpoints), counted
+// per cell with one atomic per distinct cell in the warp.
 __global__ void bin_kernel(const double* __restrict__ x, const int* __restrict__ seg_rod, int64_t N, int64_t E, Grid g,
                            int* __restrict__ seg_cell, int* __restrict__ cell_count, float4* __restrict__ prox,
                            int* err) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= E) return;
   const int64_t j = a + seg_rod[a];
-  double p0[3], p1[3], mid[3];
-  double ll = 0.0;
+  float mid[3], ll = 0.f;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    p0[c] = x[c * N + j];
-    p1[c] = x[c * N + j + 1];
-    mid[c] = 0.5 * (p0[c] + p1[c]);
-    const double d = p1[c] - p0[c];
-    ll = fma(d, d, ll);
+    const float p0 = (float)x[c * N + j], p1 = (float)x[c * N + j + 1];
+    mid[c] = 0.5f * (p0 + p1);
+    ll = fmaf(p1 - p0, p1 - p0, ll);
   }
-  const double len = sqrt(ll);
+  const float len = sqrtf(ll);
   const bool finite = isfinite(mid[0]) && isfinite(mid[1]) && isfinite(mid[2]) && isfinite(len);
   if (!finite) atomicOr(err, ERR_NONFINITE);
   else if (!(len <= g.l_allowed)) atomicOr(err, ERR_GRID);
   int ic[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    double f = floor((mid[c] - g.lo[c]) * g.inv_h);
-    f = fmin(fmax(f, 0.0), (double)(g.dim[c] - 1));  // NaN -> 0 via fmax
+    float f = floorf((mid[c] - g.lo[c]) * g.inv_h);
+    f = fminf(fmaxf(f, 0.f), (float)(g.dim[c] - 1));  // NaN -> 0 via fmaxf
     ic[c] = (int)f;
   }
   const int cell = (ic[2] * g.dim[1] + ic[1]) * g.dim[0] + ic[0];
   seg_cell[a] = cell;
-  atomicAdd(cell_count + cell, 1);
-  prox[a] = make_float4((float)mid[0], (float)mid[1], (float)mid[2], (float)(0.5 * len));
+  // consecutive segments of a rod share cells: one atomic per distinct cell in the warp
+  const unsigned peers = __match_any_sync(__activemask(), cell);
+  if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cell_count + cell, __popc(peers));
+  prox[a] = make_float4(mid[0], mid[1], mid[2], 0.5f * len);
 }
 
 // ---- exclusive scan of cell_count[0..n) into cell_start[0..n], cell_start[n] = total
@@ -225,6 +227,19 @@ __device__ __forceinline__ void closest(const double* p0, const double* p1, cons
   }
 }
 
+// Per-slot records in cell order, so that the narrow phase reads each candidate with two
+// contiguous 16-byte loads: (FP32 midpoint, FP32 half length) and (segment, rod, FP32 radius).
+__global__ void records_kernel(const int* __restrict__ sorted, const int* __restrict__ seg_rod,
+                               const float4* __restrict__ prox, const RodConst* __restrict__ rods, int64_t E,
+                               float4* __restrict__ recA, int4* __restrict__ recB) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= E) return;
+  const int a = sorted[q];
+  const int r = seg_rod[a];
+  recA[q] = prox[a];
+  recB[q] = make_int4(a, r, __float_as_int((float)rods[r].radius), 0);
+}
+
 struct ContactArgs {
   const double* x;
   const double* v;
@@ -233,6 +248,8 @@ struct ContactArgs {
   const int* cell_start;
   const int* sorted;
   const float4* prox;
+  const float4* recA;
+  const int4* recB;
   const RodConst* rods;
   double* fseg;
   int* err;
@@ -241,94 +258,105 @@ struct ContactArgs {
   double k, c;
 };
 
-__global__ void __launch_bounds__(128) gather_kernel(ContactArgs A) {
+struct PairForce {
+  double fa[3], fb[3];
+  bool hit;
+};
+
+// FP64 evaluation of one candidate pair (a, b) in canonical order (lower index first); returns
+// the contributions to the two nodes of segment a.  Kept out of line: it runs only for the
+// few candidates that survive the FP32 cull, and the scan loop stays small.
+__device__ __noinline__ PairForce pair_force(const ContactArgs& A, int a, int ra, int b, int rb) {
+  PairForce out;
+  out.hit = false;
+  const double rada = A.rods[ra].radius, radb = A.rods[rb].radius;
+  const bool first = a < b;
+  const int64_t na = a + ra, nb = b + rb;
+  const int64_t nP = first ? na : nb, nQ = first ? nb : na;
+  double P0[3], P1[3], Q0[3], Q1[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    P0[c] = A.x[c * A.N + nP];
+    P1[c] = A.x[c * A.N + nP + 1];
+    Q0[c] = A.x[c * A.N + nQ];
+    Q1[c] = A.x[c * A.N + nQ + 1];
+  }
+  double s, u;
+  closest(P0, P1, Q0, Q1, s, u);
+  double dvec[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dvec[c] = (P0[c] + s * (P1[c] - P0[c])) - (Q0[c] + u * (Q1[c] - Q0[c]));
+  const double d = sqrt(dvec[0] * dvec[0] + dvec[1] * dvec[1] + dvec[2] * dvec[2]);
+  const double delta = (rada + radb) - d;
+  if (!(delta > 0.0) || d == 0.0) return out;
+  const double nrm[3] = {dvec[0] / d, dvec[1] / d, dvec[2] / d};
+  double vrel = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double vp0 = A.v[c * A.N + nP], vp1 = A.v[c * A.N + nP + 1];
+    const double vq0 = A.v[c * A.N + nQ], vq1 = A.v[c * A.N + nQ + 1];
+    const double vr = ((1.0 - s) * vp0 + s * vp1) - ((1.0 - u) * vq0 + u * vq1);
+    vrel += vr * nrm[c];
+  }
+  double fmag = A.k * delta - A.c * vrel;
+  if (fmag < 0.0) fmag = 0.0;
+  // force on the first segment of the pair is +fmag n, on the second -fmag n
+  const double wa = first ? (1.0 - s) : -(1.0 - u);
+  const double wb = first ? s : -u;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double fc = fmag * nrm[c];
+    out.fa[c] = wa * fc;
+    out.fb[c] = wb * fc;
+  }
+  out.hit = true;
+  return out;
+}
+
+// One thread per slot of the cell-ordered list: threads of a warp share cells and their
+// neighbour rows, so candidate records come from L1.  The three cells of each (y, z) row of
+// the 3x3x3 neighbourhood are consecutive in the list and scanned as one range.
+__global__ void __launch_bounds__(256, 4) gather_kernel(ContactArgs A) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= A.E) return;
   if (*(volatile int*)A.err != 0) return;  // latched error: the step is abandoned
-  const int a = A.sorted[q];
-  const int ra = A.seg_rod[a];
-  const double rada = A.rods[ra].radius;
-  const int64_t na = a + ra;
-  const float4 pa = A.prox[a];
-  const float ma_inf = fmaxf(fabsf(pa.x), fmaxf(fabsf(pa.y), fabsf(pa.z)));
+  const float4 ga = A.recA[q];
+  const int4 ba = A.recB[q];
+  const int a = ba.x, ra = ba.y;
+  const float rada = __int_as_float(ba.z);
+  const float ma_inf = fmaxf(fabsf(ga.x), fmaxf(fabsf(ga.y), fabsf(ga.z)));
   double fa[3] = {0, 0, 0}, fb[3] = {0, 0, 0};
-  double xa0[3], xa1[3], va0[3], va1[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    xa0[c] = A.x[c * A.N + na];
-    xa1[c] = A.x[c * A.N + na + 1];
-    va0[c] = A.v[c * A.N + na];
-    va1[c] = A.v[c * A.N + na + 1];
-  }
   const int cell = A.seg_cell[a];
   const int cx = cell % A.dim[0], cy = (cell / A.dim[0]) % A.dim[1], cz = cell / (A.dim[0] * A.dim[1]);
+  const int x0 = max(cx - 1, 0), x1 = min(cx + 1, A.dim[0] - 1);
   for (int dz = -1; dz <= 1; ++dz) {
     const int z = cz + dz;
     if (z < 0 || z >= A.dim[2]) continue;
     for (int dy = -1; dy <= 1; ++dy) {
       const int y = cy + dy;
       if (y < 0 || y >= A.dim[1]) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int xx = cx + dx;
-        if (xx < 0 || xx >= A.dim[0]) continue;
-        const int cc = (z * A.dim[1] + y) * A.dim[0] + xx;
-        const int b0 = A.cell_start[cc], b1 = A.cell_start[cc + 1];
-        if (b1 - b0 > kCellCap) {
-          atomicOr(A.err, ERR_OVERFLOW);
-          continue;
-        }
-        for (int t = b0; t < b1; ++t) {
-          const int b = A.sorted[t];
-          const int rb = A.seg_rod[b];
-          if (rb == ra) continue;
-          const double radb = A.rods[rb].radius;
-          // FP32 lower bound of the segment distance: |m_a - m_b| - (h_a + h_b)
-          const float4 pb = A.prox[b];
-          const float ddx = pa.x - pb.x, ddy = pa.y - pb.y, ddz = pa.z - pb.z;
-          const float dm = sqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
-          const float mb_inf = fmaxf(fabsf(pb.x), fmaxf(fabsf(pb.y), fabsf(pb.z)));
-          const float tol = 1e-6f + 4e-6f * (ma_inf + mb_inf + pa.w + pb.w);
-          if (dm - (pa.w + pb.w) > (float)(rada + radb) + tol) continue;
-          // FP64 pair in canonical order (lower index first)
-          const bool first = a < b;
-          const int64_t nb = b + rb;
-          double P0[3], P1[3], Q0[3], Q1[3];
+      const int row = (z * A.dim[1] + y) * A.dim[0];
+      const int b0 = A.cell_start[row + x0], b1 = A.cell_start[row + x1 + 1];
+      if (b1 - b0 > 3 * kCellCap) {
+        atomicOr(A.err, ERR_OVERFLOW);
+        continue;
+      }
+      for (int t = b0; t < b1; ++t) {
+        const int4 bb = A.recB[t];
+        if (bb.y == ra) continue;
+        // FP32 lower bound of the segment distance: |m_a - m_b| - (h_a + h_b)
+        const float4 gb = A.recA[t];
+        const float ddx = ga.x - gb.x, ddy = ga.y - gb.y, ddz = ga.z - gb.z;
+        const float dm = sqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
+        const float mb_inf = fmaxf(fabsf(gb.x), fmaxf(fabsf(gb.y), fabsf(gb.z)));
+        const float tol = 1e-6f + 4e-6f * (ma_inf + mb_inf + ga.w + gb.w);
+        if (dm - (ga.w + gb.w) > rada + __int_as_float(bb.z) + tol) continue;
+        const PairForce pf = pair_force(A, a, ra, bb.x, bb.y);
+        if (pf.hit) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            const double xb0 = A.x[c * A.N + nb], xb1 = A.x[c * A.N + nb + 1];
-            P0[c] = first ? xa0[c] : xb0;
-            P1[c] = first ? xa1[c] : xb1;
-            Q0[c] = first ? xb0 : xa0[c];
-            Q1[c] = first ? xb1 : xa1[c];
-          }
-          double s, u;
-          closest(P0, P1, Q0, Q1, s, u);
-          double dvec[3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) dvec[c] = (P0[c] + s * (P1[c] - P0[c])) - (Q0[c] + u * (Q1[c] - Q0[c]));
-          const double d = sqrt(dvec[0] * dvec[0] + dvec[1] * dvec[1] + dvec[2] * dvec[2]);
-          const double delta = (rada + radb) - d;
-          if (!(delta > 0.0) || d == 0.0) continue;
-          double nrm[3] = {dvec[0] / d, dvec[1] / d, dvec[2] / d};
-          double vrel = 0.0;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const double vb0 = A.v[c * A.N + nb], vb1 = A.v[c * A.N + nb + 1];
-            const double vp0 = first ? va0[c] : vb0, vp1 = first ? va1[c] : vb1;
-            const double vq0 = first ? vb0 : va0[c], vq1 = first ? vb1 : va1[c];
-            const double vr = ((1.0 - s) * vp0 + s * vp1) - ((1.0 - u) * vq0 + u * vq1);
-            vrel += vr * nrm[c];
-          }
-          double fmag = A.k * delta - A.c * vrel;
-          if (fmag < 0.0) fmag = 0.0;
-          // force on the first segment of the pair is +fmag n, on the second -fmag n
-          const double wa = first ? (1.0 - s) : -(1.0 - u);
-          const double wb = first ? s : -u;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const double fc = fmag * nrm[c];
-            fa[c] += wa * fc;
-            fb[c] += wb * fc;
+            fa[c] += pf.fa[c];
+            fb[c] += pf.fb[c];
           }
         }
       }
@@ -367,12 +395,14 @@ cudaError_t dev_alloc(T** p, size_t count) {
 
 void contact_release(ContactState& cs) {
   void* ptrs[] = {cs.seg_rod, cs.seg_cell, cs.cell_count, cs.cell_start, cs.cell_fill,
-                  cs.block_sums, cs.sorted, cs.prox, cs.fseg};
+                  cs.block_sums, cs.sorted, cs.prox, cs.fseg, cs.recA, cs.recB};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cs.seg_rod = cs.seg_cell = cs.cell_count = cs.cell_start = cs.cell_fill = cs.block_sums = cs.sorted = nullptr;
   cs.prox = nullptr;
   cs.fseg = nullptr;
+  cs.recA = nullptr;
+  cs.recB = nullptr;
   cs.cap_cells = 0;
   cs.E = 0;
   cs.grid_valid = false;
@@ -428,10 +458,17 @@ rod_status contact_prepare(ContactState& cs, const std::vector<RodConst>& rods_h
   cs.h = h;
   cs.inv_h = 1.0 / h;
   cs.ncell = ncell;
-  cs.l_allowed = h - 2.0 * rmax;
+  // Cells are assigned from FP32 midpoints: a midpoint may move by a few ulps of the largest
+  // coordinate, which the longest allowed element gives up (with a generous factor).
+  double cmax = 0.0;
+  for (int c = 0; c < 3; ++c) cmax = std::max(cmax, std::max(std::fabs(cs.lo[c]), std::fabs(cs.lo[c] + cs.dim[c] * h)));
+  const double fp32_margin = 64.0 * 6e-8 * (1.0 + cmax);
+  cs.l_allowed = h - 2.0 * rmax - fp32_margin;
+  cs.version += 1;
   if (cs.E != E) {
     if ((e = dev_alloc(&cs.seg_rod, E)) || (e = dev_alloc(&cs.seg_cell, E)) || (e = dev_alloc(&cs.sorted, E)) ||
-        (e = dev_alloc(&cs.prox, E)) || (e = dev_alloc(&cs.fseg, 6 * E)))
+        (e = dev_alloc(&cs.prox, E)) || (e = dev_alloc(&cs.fseg, 6 * E)) || (e = dev_alloc(&cs.recA, E)) ||
+        (e = dev_alloc(&cs.recB, E)))
       return cfail(ROD_ERR_CUDA, "contact: allocation", e);
     cs.E = E;
   }
@@ -451,25 +488,43 @@ rod_status contact_prepare(ContactState& cs, const std::vector<RodConst>& rods_h
   return ROD_OK;
 }
 
+void contact_bin_params(const ContactState& cs, StepParams& P) {
+  P.bin_prox = cs.prox;
+  P.bin_cell = cs.seg_cell;
+  P.bin_count = cs.cell_count;
+  for (int c = 0; c < 3; ++c) {
+    P.bin_lo[c] = (float)cs.lo[c];
+    P.bin_dim[c] = cs.dim[c];
+  }
+  P.bin_inv_h = (float)cs.inv_h;
+  P.bin_l_allowed = (float)cs.l_allowed;
+}
+
+cudaError_t contact_clear_counts(const ContactState& cs, cudaStream_t st) {
+  return cudaMemsetAsync(cs.cell_count, 0, (cs.ncell + 1) * sizeof(int), st);
+}
+
 cudaError_t contact_compute(ContactState& cs, const double* x, const double* v, const RodConst* rods, int64_t N,
-                            int64_t E, int R, int* err, cudaStream_t st, const LaunchHook& hook) {
+                            int64_t E, int R, int* err, cudaStream_t st, const LaunchHook& hook, bool prebinned) {
   cudaError_t e;
   (void)R;
   const int64_t n1 = cs.ncell + 1;
-  if ((e = cudaMemsetAsync(cs.cell_count, 0, n1 * sizeof(int), st))) return e;
-  Grid g;
-  for (int c = 0; c < 3; ++c) {
-    g.lo[c] = cs.lo[c];
-    g.dim[c] = cs.dim[c];
-  }
-  g.inv_h = cs.inv_h;
-  g.l_allowed = cs.l_allowed;
   const int tb = 256;
   const int64_t eb = (E + tb - 1) / tb;
-  hook.before(K_CONTACT_BIN, st);
-  bin_kernel<<<eb, tb, 0, st>>>(x, cs.seg_rod, N, E, g, cs.seg_cell, cs.cell_count, cs.prox, err);
-  hook.after(K_CONTACT_BIN, st);
-  if ((e = cudaGetLastError())) return e;
+  if (!prebinned) {
+    if ((e = contact_clear_counts(cs, st))) return e;
+    Grid g;
+    for (int c = 0; c < 3; ++c) {
+      g.lo[c] = (float)cs.lo[c];
+      g.dim[c] = cs.dim[c];
+    }
+    g.inv_h = (float)cs.inv_h;
+    g.l_allowed = (float)cs.l_allowed;
+    hook.before(K_CONTACT_BIN, st);
+    bin_kernel<<<eb, tb, 0, st>>>(x, cs.seg_rod, N, E, g, cs.seg_cell, cs.cell_count, cs.prox, err);
+    hook.after(K_CONTACT_BIN, st);
+    if ((e = cudaGetLastError())) return e;
+  }
   const int64_t nt = (n1 + kScanTile - 1) / kScanTile;
   hook.before(K_CONTACT_SCAN, st);
   scan_tiles_kernel<<<nt, kScanThreads, 0, st>>>(cs.cell_count, n1, cs.cell_start, cs.block_sums);
@@ -490,6 +545,10 @@ cudaError_t contact_compute(ContactState& cs, const double* x, const double* v, 
   sort_cells_kernel<<<(cs.ncell + 255) / 256, 256, 0, st>>>(cs.cell_start, cs.ncell, cs.sorted, err);
   hook.after(K_CONTACT_SORT, st);
   if ((e = cudaGetLastError())) return e;
+  hook.before(K_CONTACT_SORT, st);
+  records_kernel<<<eb, tb, 0, st>>>(cs.sorted, cs.seg_rod, cs.prox, rods, E, cs.recA, cs.recB);
+  hook.after(K_CONTACT_SORT, st);
+  if ((e = cudaGetLastError())) return e;
   ContactArgs A;
   A.x = x;
   A.v = v;
@@ -498,6 +557,8 @@ cudaError_t contact_compute(ContactState& cs, const double* x, const double* v, 
   A.cell_start = cs.cell_start;
   A.sorted = cs.sorted;
   A.prox = cs.prox;
+  A.recA = cs.recA;
+  A.recB = cs.recB;
   A.rods = rods;
   A.fseg = cs.fseg;
   A.N = N;
@@ -507,7 +568,7 @@ cudaError_t contact_compute(ContactState& cs, const double* x, const double* v, 
   A.c = cs.c;
   A.err = err;
   hook.before(K_CONTACT_GATHER, st);
-  gather_kernel<<<(E + 127) / 128, 128, 0, st>>>(A);
+  gather_kernel<<<(E + 255) / 256, 256, 0, st>>>(A);
   hook.after(K_CONTACT_GATHER, st);
   return cudaGetLastError();
 }

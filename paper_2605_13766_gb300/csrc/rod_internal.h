@@ -73,6 +73,16 @@ struct StepParams {
   // contact: per-segment node forces [6E] (force on node a = first node, node b), or null
   const double* fseg;
   int* err;                   // device error word
+  // simulated time of the state at launch (device scalar; replayed graphs read it), or null
+  const double* t_dev;
+  // contact binning of the positions a half/one-step launch leaves behind, or bin_count = null
+  float4* bin_prox;           // [E] FP32 midpoint + half length
+  int* bin_cell;              // [E]
+  int* bin_count;             // [cells] counts (zeroed by the caller)
+  float bin_lo[3];
+  float bin_inv_h;
+  int bin_dim[3];
+  float bin_l_allowed;        // longest element the cell covers, less the FP32 rounding margin
 };
 
 // Kernel classes for the optional per-kernel timing (rod_system_profile).

@@ -31,9 +31,15 @@ namespace {
 
 // ---------------------------------------------------------------------------------- math
 
+// High 32 bits of a non-negative double: x < 2^k exactly when hi_word(x) < hi_word(2^k), so a
+// warp-wide integer maximum of these words bounds every lane's argument.
+__device__ __forceinline__ unsigned hi_word(double x) { return static_cast<unsigned>(__double2hiint(x)); }
+constexpr unsigned kHi2m20 = 0x3EB00000u;  // 2^-20
+constexpr unsigned kHi2m10 = 0x3F500000u;  // 2^-10
+
 // sin(th)/th and (1 - cos th)/th^2 as Taylor series in th^2 (8 terms each; the dropped terms
-// are below 5e-20 relative for th^2 <= 1/4).
-__device__ __forceinline__ void rot_coeffs(double th2, double& a, double& b) {
+// are below 5e-20 relative for th^2 <= 1/4); larger angles use sincos.
+__device__ __forceinline__ void rot_coeffs_full(double th2, double& a, double& b) {
   if (th2 <= 0.25) {
     a = -1.0 / 1307674368000.0;
     a = fma(a, th2, 1.0 / 6227020800.0);
@@ -61,6 +67,22 @@ __device__ __forceinline__ void rot_coeffs(double th2, double& a, double& b) {
   }
 }
 
+// Same coefficients with the series cut to the warp's largest th^2: below 2^-20 three terms
+// (dropped terms < 2e-22), below 2^-10 four terms (< 3e-18), otherwise the full series.  The
+// choice is uniform across the warp, so lanes never diverge on it.
+__device__ __forceinline__ void rot_coeffs(double th2, double& a, double& b) {
+  const unsigned mx = __reduce_max_sync(__activemask(), hi_word(th2));
+  if (mx < kHi2m20) {
+    a = fma(fma(th2, 1.0 / 120.0, -1.0 / 6.0), th2, 1.0);
+    b = fma(fma(th2, 1.0 / 720.0, -1.0 / 24.0), th2, 0.5);
+  } else if (mx < kHi2m10) {
+    a = fma(fma(fma(th2, -1.0 / 5040.0, 1.0 / 120.0), th2, -1.0 / 6.0), th2, 1.0);
+    b = fma(fma(fma(th2, -1.0 / 40320.0, 1.0 / 720.0), th2, -1.0 / 24.0), th2, 0.5);
+  } else {
+    rot_coeffs_full(th2, a, b);
+  }
+}
+
 // asin(s)/s as a Taylor series in s^2 = |w|^2 (13 terms; dropped tail < 2e-18 for s <= 1/4).
 __device__ __forceinline__ double asin_over_s(double s2) {
   double f = 676039.0 / 104857600.0;
@@ -77,6 +99,27 @@ __device__ __forceinline__ double asin_over_s(double s2) {
   f = fma(f, s2, 1.0 / 6.0);
   f = fma(f, s2, 1.0);
   return f;
+}
+
+// theta / sin(theta) of the relative rotation with sin^2 = s2, cos = c.  Warp-uniform cut of the
+// series like rot_coeffs (s2 < 2^-20: three terms, dropped < 4e-20; s2 < 2^-10: six terms,
+// dropped < 2e-20), used only when every lane's rotation is below 90 degrees (c > 0).
+__device__ __forceinline__ double theta_over_sin(double s2, double c) {
+  const unsigned act = __activemask();
+  const unsigned mx = __reduce_max_sync(act, hi_word(s2));
+  const bool acute = __all_sync(act, c > 0.0);
+  if (acute && mx < kHi2m20) return fma(fma(s2, 3.0 / 40.0, 1.0 / 6.0), s2, 1.0);
+  if (acute && mx < kHi2m10) {
+    double f = 63.0 / 2816.0;
+    f = fma(f, s2, 35.0 / 1152.0);
+    f = fma(f, s2, 5.0 / 112.0);
+    f = fma(f, s2, 3.0 / 40.0);
+    f = fma(f, s2, 1.0 / 6.0);
+    return fma(f, s2, 1.0);
+  }
+  if (s2 <= 0.0625 && c > 0.0) return asin_over_s(s2);
+  const double sn = sqrt(s2);
+  return (sn > 0.0) ? atan2(sn, c) / sn : 1.0;
 }
 
 struct Smem {
@@ -213,16 +256,17 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
 #pragma unroll
       for (int c = 0; c < 3; ++c) sg[c] -= __ldg(P.rest_sigma + c * P.E + ge);
     }
+    // n / e = S sigma / e  (the 1/e of the internal force, folded once)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) n[c] = __ldg(&rc->S[c]) * sg[c];
+    for (int c = 0; c < 3; ++c) n[c] = (__ldg(&rc->S[c]) * ie) * sg[c];
     // lab internal force N = Q^T n / e
 #pragma unroll
-    for (int b = 0; b < 3; ++b) m.NF[b * m.CE + i] = fma(q[b], n[0], fma(q[3 + b], n[1], q[6 + b] * n[2])) * ie;
-    // shear couple ((Q t) x n) rl = (Ql x n) rl / ell
+    for (int b = 0; b < 3; ++b) m.NF[b * m.CE + i] = fma(q[b], n[0], fma(q[3 + b], n[1], q[6 + b] * n[2]));
+    // shear couple ((Q t) x n) rl = (Ql x n) rl / ell = Ql x (n / e)
     double tc[3];
-    tc[0] = fma(Ql[1], n[2], -Ql[2] * n[1]) * ie;
-    tc[1] = fma(Ql[2], n[0], -Ql[0] * n[2]) * ie;
-    tc[2] = fma(Ql[0], n[1], -Ql[1] * n[0]) * ie;
+    tc[0] = fma(Ql[1], n[2], -Ql[2] * n[1]);
+    tc[1] = fma(Ql[2], n[0], -Ql[0] * n[2]);
+    tc[2] = fma(Ql[0], n[1], -Ql[1] * n[0]);
     // transport couples (J w / e) x w + (J w / e^2) de/dt,  de/dt = (l . dv) / (ell rl)
     const double edot = fma(l[0], dv[0], fma(l[1], dv[1], l[2] * dv[2])) * rs * irl;
     double Jw[3], Jwe[3];
@@ -289,13 +333,7 @@ __device__ __forceinline__ void stage_voronoi(const StepParams& P, const Pack& p
     for (int a = 1; a < 9; ++a) tr = fma(qb[a], qa[a], tr);
     const double s2 = 0.25 * fma(u0, u0, fma(u1, u1, u2 * u2));  // |w|^2 = sin^2(theta)
     const double c = 0.5 * (tr - 1.0);                             // cos(theta)
-    double f;                                                       // theta / sin(theta)
-    if (s2 <= 0.0625 && c > 0.0) {
-      f = asin_over_s(s2);
-    } else {
-      const double s = sqrt(s2);
-      f = (s > 0.0) ? atan2(s, c) / s : 1.0;
-    }
+    const double f = theta_over_sin(s2, c);
     const double i2D = __ldg(P.inv_2D + gv);
     const double kf = -f * i2D;             // kappa = -(theta/s) w / D = -f u / (2D)
     double kap[3] = {kf * u0, kf * u1, kf * u2};
@@ -345,17 +383,16 @@ __device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& 
       tau[c] = fma(0.5, Tl + Tr, (Pr - Pl) + m.TA[c * m.CE + i]);
     }
     const bool held = (li == 0) && rc->clamp;
-    const double ke = m.EDIL[i] * m.IRL[i];
-    double wn[3];
+    if (MODE == MODE_RHS) {
+      const double ke = m.EDIL[i] * m.IRL[i];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const double alpha = held ? 0.0 : ke * __ldg(&rc->inv_rhoI[c]) * tau[c];
-      if (MODE == MODE_RHS) {
-        acc_w[c * P.E + pk.elem0 + i] = alpha;
-      } else {
-        wn[c] = held ? 0.0 : fma(dt, alpha, m.WW[c * m.CE + i]);
-        m.WW[c * m.CE + i] = wn[c];
-      }
+      for (int c = 0; c < 3; ++c) acc_w[c * P.E + pk.elem0 + i] = held ? 0.0 : ke * __ldg(&rc->inv_rhoI[c]) * tau[c];
+    } else {
+      // w += dt e J^{-1} tau,  J^{-1} = 1/(rho I rl)
+      const double ke = (dt * m.EDIL[i]) * m.IRL[i];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        m.WW[c * m.CE + i] = held ? 0.0 : fma(ke * __ldg(&rc->inv_rhoI[c]), tau[c], m.WW[c * m.CE + i]);
     }
   }
 }
@@ -365,6 +402,7 @@ template <int MODE>
 __device__ __forceinline__ void stage_translation(const StepParams& P, const Pack& pk, Smem& m, double dt,
                                                   double* acc_v) {
   const int Np = pk.nnode;
+  const double dtg[3] = {dt * P.gravity[0], dt * P.gravity[1], dt * P.gravity[2]};
   for (int j = threadIdx.x; j < Np; j += blockDim.x) {
     const int r = m.nrod[j];
     const int g = pk.rod0 + r;
@@ -398,16 +436,22 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
         F[c] += fc;
       }
     }
+    if (MODE == MODE_RHS) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const double vj = m.VN[c * m.CN + j];
-      double a = fma(F[c], im, -dl * vj);
-      if (P.has_gravity) a += P.gravity[c];
-      if (held) a = 0.0;
-      if (MODE == MODE_RHS) {
-        acc_v[c * P.N + pk.node0 + j] = a;
-      } else {
-        m.VN[c * m.CN + j] = held ? 0.0 : fma(dt, a, vj);
+      for (int c = 0; c < 3; ++c) {
+        const double vj = m.VN[c * m.CN + j];
+        double a = fma(F[c], im, -dl * vj);
+        if (P.has_gravity) a += P.gravity[c];
+        acc_v[c * P.N + pk.node0 + j] = held ? 0.0 : a;
+      }
+    } else {
+      // v += dt (F/m - c v + g)  as  v (1 - dt c) + (dt/m) F + dt g
+      const double keep = fma(-dt, dl, 1.0), dtim = dt * im;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double vj = m.VN[c * m.CN + j];
+        const double base = P.has_gravity ? fma(vj, keep, dtg[c]) : vj * keep;
+        m.VN[c * m.CN + j] = held ? 0.0 : fma(F[c], dtim, base);
       }
     }
   }
@@ -488,8 +532,9 @@ __global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, 
       kinematic(P, pk, m, 0.5 * dt);
       __syncthreads();
     }
+    const double tbase = P.t_dev ? *P.t_dev : t0;
     for (int64_t s = 0; s < n_steps; ++s) {
-      const double t = t0 + (static_cast<double>(s) + 0.5) * dt;
+      const double t = tbase + (static_cast<double>(s) + 0.5) * dt;
       actuation_values(P, pk, m, t);
       stage_elements(P, pk, m);
       __syncthreads();
@@ -503,6 +548,44 @@ __global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, 
       kinematic(P, pk, m, h);
       __syncthreads();
     }
+  }
+
+  // ---- contact binning of the positions this launch leaves behind (the next step's
+  // half-step positions): FP32 midpoint, half length and cell of every segment, counted per
+  // cell with one atomic per distinct cell in the warp.
+  if ((MODE == MODE_KIN_HALF || (MODE == MODE_ONE_STEP && !last_half)) && P.bin_count) {
+    bool grid_bad = false, nonfinite = false;
+    for (int i = threadIdx.x; i < Ep; i += blockDim.x) {
+      const int j = i + m.erod[i];
+      float p0[3], p1[3], mid[3];
+      float ll = 0.f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        p0[c] = static_cast<float>(m.X[c * m.CN + j]);
+        p1[c] = static_cast<float>(m.X[c * m.CN + j + 1]);
+        mid[c] = 0.5f * (p0[c] + p1[c]);
+        ll = fmaf(p1[c] - p0[c], p1[c] - p0[c], ll);
+      }
+      const float len = sqrtf(ll);
+      const bool fin = isfinite(mid[0]) && isfinite(mid[1]) && isfinite(mid[2]) && isfinite(len);
+      nonfinite |= !fin;
+      grid_bad |= fin && !(len <= P.bin_l_allowed);
+      int ic[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float q = floorf((mid[c] - P.bin_lo[c]) * P.bin_inv_h);
+        q = fminf(fmaxf(q, 0.f), static_cast<float>(P.bin_dim[c] - 1));
+        ic[c] = static_cast<int>(q);
+      }
+      const int cell = (ic[2] * P.bin_dim[1] + ic[1]) * P.bin_dim[0] + ic[0];
+      const int ge = pk.elem0 + i;
+      P.bin_cell[ge] = cell;
+      P.bin_prox[ge] = make_float4(mid[0], mid[1], mid[2], 0.5f * len);
+      const unsigned peers = __match_any_sync(__activemask(), cell);
+      if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(P.bin_count + cell, __popc(peers));
+    }
+    if (nonfinite) atomicOr(P.err, ERR_NONFINITE);
+    if (grid_bad) atomicOr(P.err, ERR_GRID);
   }
 
   // ---- write back, flag non-finite values

@@ -98,6 +98,22 @@ def test_trajectory_with_contact_200_rods_1000_steps():
     assert np.abs(got[0] - ref[0]).max() / 0.128 <= 1e-9
 
 
+def test_graph_replay_equals_eager_launches():
+    """100 contact steps: replayed CUDA graphs (32 steps each) and eager launches agree, and both
+    match the oracle."""
+    p = _touching(60, 0.1, 14)
+    ref = Oracle(p).step(*p.state(), dt=2e-6, n_steps=100)
+    a = _gpu(p)
+    a.step(100, 2e-6)
+    b = _gpu(p)
+    b.use_graphs(False)
+    b.step(100, 2e-6)
+    ga, gb = a.get_state(), b.get_state()
+    assert np.abs(ga[0] - gb[0]).max() <= 1e-15
+    assert np.abs(ga[0] - ref[0]).max() / 0.1 <= 1e-9
+    assert a.launch_count > 0
+
+
 def test_element_longer_than_the_grid_allows_is_reported():
     from paper_2605_13766_gb300 import RodError
     p = _dense(n_rods=10, seed=9, nmin=4, nmax=8)

@@ -130,6 +130,25 @@ rod_status rod_system_contact_forces(rod_system* sys, double* f);
 rod_status rod_system_set_launch(rod_system* sys, int32_t elems_per_block, int32_t threads_per_block);
 rod_status rod_system_get_launch(const rod_system* sys, int32_t* elems_per_block, int32_t* threads_per_block);
 
+/* Differentiation (hand-written adjoint of the step; contact must be off).
+ * rod_system_set_params replaces the rest curvature [3*V] and/or the element couples [3*E]
+ * (NULL leaves one unchanged; on_device as for set_state).
+ * rod_system_forward_checkpointed advances n_steps steps of dt from the current state, one
+ * step per launch, keeping the state every `every` steps in library memory.
+ * rod_system_backward takes the adjoint of the final state (device pointers, layout of the
+ * state) and writes the gradients of the loss with respect to the rest curvature [3*V] and
+ * the element couples [3*E] (device pointers, overwritten): it recomputes each segment of
+ * `every` steps from its checkpoint and runs the adjoint step kernel backwards over it.  The
+ * system's state is left at the final state.  Rods longer than one adjoint thread block holds
+ * (256 elements with the default shape) are rejected with ROD_ERR_ARG.
+ * rod_system_adjoint_of_state copies the adjoint of the initial state of the last backward
+ * pass (device pointers). */
+rod_status rod_system_set_params(rod_system* sys, const double* rest_kappa, const double* elem_couple, int on_device);
+rod_status rod_system_forward_checkpointed(rod_system* sys, int64_t n_steps, double dt, int32_t every);
+rod_status rod_system_backward(rod_system* sys, const double* adj_x, const double* adj_v, const double* adj_Q,
+                               const double* adj_w, double* grad_rest_kappa, double* grad_elem_couple);
+rod_status rod_system_adjoint_of_state(rod_system* sys, double* adj_x, double* adj_v, double* adj_Q, double* adj_w);
+
 /* With contact, rod_system_step replays a CUDA graph of 32 captured steps (captured on an
  * internal stream, launched on the system's stream) unless profiling is on; enable = 0 makes
  * every step an eager sequence of launches (same kernels, same results). */

@@ -73,6 +73,10 @@ _SIGNATURES = {
     "rod_system_set_launch": ([_P, C.c_int32, C.c_int32], C.c_int),
     "rod_system_get_launch": ([_P, _P, _P], C.c_int),
     "rod_system_set_graphs": ([_P, C.c_int], C.c_int),
+    "rod_system_set_params": ([_P, _P, _P, C.c_int], C.c_int),
+    "rod_system_forward_checkpointed": ([_P, C.c_int64, C.c_double, C.c_int32], C.c_int),
+    "rod_system_backward": ([_P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "rod_system_adjoint_of_state": ([_P, _P, _P, _P, _P], C.c_int),
     "rod_system_profile": ([_P, C.c_int], C.c_int),
     "rod_profile_classes": ([], C.c_int32),
     "rod_system_profile_read": ([_P, C.c_int32, _P, _P, _P], C.c_int),
@@ -272,6 +276,44 @@ class RodSystem:
         f = torch.empty((3, self.n_nodes), dtype=torch.float64, device="cuda")
         _check(self.lib.rod_system_contact_forces(self.handle, f.data_ptr()))
         return f
+
+    # -- differentiation
+    def set_params(self, rest_kappa=None, elem_couple=None):
+        """Replace the rest curvature (3, V) and/or element couples (3, E): numpy or CUDA tensors."""
+        arrs = [rest_kappa, elem_couple]
+        on_dev = any(a is not None and not isinstance(a, np.ndarray) for a in arrs)
+        if on_dev:
+            import torch
+            arrs = [None if a is None else a.detach().to(torch.float64).contiguous() for a in arrs]
+            if self.torch_stream is not None:
+                self.torch_stream.wait_stream(torch.cuda.current_stream())
+        else:
+            arrs = [_host(a) for a in arrs]
+        _check(self.lib.rod_system_set_params(self.handle, _ptr(arrs[0]), _ptr(arrs[1]), 1 if on_dev else 0))
+        self._keep_params = arrs
+
+    def forward_checkpointed(self, n_steps: int, dt: float, every: int = 100):
+        _check(self.lib.rod_system_forward_checkpointed(self.handle, int(n_steps), float(dt), int(every)))
+
+    def backward(self, gx, gv, gQ, gw):
+        """Adjoint of the final state (CUDA tensors) -> (grad rest curvature (3, V), grad couples (3, E))."""
+        import torch
+        gs = [g.detach().to(torch.float64).contiguous() for g in (gx, gv, gQ, gw)]
+        if self.torch_stream is not None:
+            self.torch_stream.wait_stream(torch.cuda.current_stream())
+        gk = torch.empty((3, max(self.n_voronoi, 1)), dtype=torch.float64, device="cuda")
+        gc = torch.empty((3, self.n_elems), dtype=torch.float64, device="cuda")
+        _check(self.lib.rod_system_backward(self.handle, *[g.data_ptr() for g in gs], gk.data_ptr(), gc.data_ptr()))
+        return gk[:, : self.n_voronoi], gc
+
+    def adjoint_of_state(self):
+        import torch
+        out = [torch.empty((3, self.n_nodes), dtype=torch.float64, device="cuda"),
+               torch.empty((3, self.n_nodes), dtype=torch.float64, device="cuda"),
+               torch.empty((9, self.n_elems), dtype=torch.float64, device="cuda"),
+               torch.empty((3, self.n_elems), dtype=torch.float64, device="cuda")]
+        _check(self.lib.rod_system_adjoint_of_state(self.handle, *[o.data_ptr() for o in out]))
+        return tuple(out)
 
     def use_graphs(self, enable: bool = True):
         _check(self.lib.rod_system_set_graphs(self.handle, 1 if enable else 0))

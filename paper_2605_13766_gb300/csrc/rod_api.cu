@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/rod.h"
+#include "rod_adjoint.h"
 #include "rod_contact.h"
 #include "rod_internal.h"
 
@@ -188,6 +189,14 @@ struct rod_system {
   int graph_grid_version = -1;
   int shape_version = 0, graph_shape_version = -1;
   bool use_graphs = true;
+  // adjoint: checkpoints of the last checkpointed forward run, recompute buffers
+  DevBuf<double> ckpt, seg_states, adj, final_state;
+  int64_t ck_steps = 0, ck_every = 0;
+  double ck_t0 = 0.0, ck_dt = 0.0;
+  bool ck_valid = false;
+  LaunchShape adj_shape{0, 0, 0};
+  DevBuf<Pack> adj_packs;
+  int adj_n_packs = 0;
 };
 
 namespace {
@@ -334,6 +343,66 @@ rod_status ensure_contact_graph(rod_system* s, const StepParams& Pb, double dt) 
   s->graph_dt = dt;
   s->graph_grid_version = s->contact.version;
   s->graph_shape_version = s->shape_version;
+  return ROD_OK;
+}
+
+int64_t state_size(const rod_system* s) { return 6 * s->N + 12 * s->E; }
+
+// copy the system state into / from one packed state [x v Q w]
+cudaError_t pack_state(rod_system* s, double* dst) {
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(dst, s->x.p, 3 * s->N * 8, cudaMemcpyDeviceToDevice, s->stream))) return e;
+  if ((e = cudaMemcpyAsync(dst + 3 * s->N, s->v.p, 3 * s->N * 8, cudaMemcpyDeviceToDevice, s->stream))) return e;
+  if ((e = cudaMemcpyAsync(dst + 6 * s->N, s->Q.p, 9 * s->E * 8, cudaMemcpyDeviceToDevice, s->stream))) return e;
+  return cudaMemcpyAsync(dst + 6 * s->N + 9 * s->E, s->w.p, 3 * s->E * 8, cudaMemcpyDeviceToDevice, s->stream);
+}
+cudaError_t unpack_state(rod_system* s, const double* src) {
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(s->x.p, src, 3 * s->N * 8, cudaMemcpyDeviceToDevice, s->stream))) return e;
+  if ((e = cudaMemcpyAsync(s->v.p, src + 3 * s->N, 3 * s->N * 8, cudaMemcpyDeviceToDevice, s->stream))) return e;
+  if ((e = cudaMemcpyAsync(s->Q.p, src + 6 * s->N, 9 * s->E * 8, cudaMemcpyDeviceToDevice, s->stream))) return e;
+  return cudaMemcpyAsync(s->w.p, src + 6 * s->N + 9 * s->E, 3 * s->E * 8, cudaMemcpyDeviceToDevice, s->stream);
+}
+
+// Launch shape of the adjoint kernel: the largest pack that fits the shared memory.
+rod_status prepare_adjoint_shape(rod_system* s) {
+  if (s->adj_n_packs) return ROD_OK;
+  LaunchShape sh{0, 0, 256};
+  for (int cap = 256; cap >= 32; cap -= 32) {
+    sh.cap_elems = cap;
+    sh.cap_rods = std::max(4, std::min(32, cap / 8));
+    if (adjoint_smem_bytes(sh) <= 227 * 1024) break;
+  }
+  if (adjoint_smem_bytes(sh) > 227 * 1024 || sh.cap_elems < s->max_n)
+    return fail(ROD_ERR_ARG, "the adjoint holds rods of at most %d elements in one thread block (longest rod: %d)",
+                sh.cap_elems, s->max_n);
+  std::vector<Pack> packs;
+  Pack cur{};
+  bool open = false;
+  for (int r = 0; r < s->R; ++r) {
+    const RodConst& rc = s->rods_h[r];
+    if (open && (cur.nelem + rc.n > sh.cap_elems || cur.nrods + 1 > sh.cap_rods)) {
+      packs.push_back(cur);
+      open = false;
+    }
+    if (!open) {
+      cur = Pack{};
+      cur.rod0 = r;
+      cur.elem0 = rc.elem0;
+      cur.node0 = rc.node0;
+      cur.vor0 = rc.elem0 - r;
+      open = true;
+    }
+    cur.nrods += 1;
+    cur.nelem += rc.n;
+    cur.nnode += rc.n + 1;
+    cur.nvor += rc.n - 1;
+  }
+  if (open) packs.push_back(cur);
+  CUDA_TRY(s->adj_packs.alloc(packs.size()));
+  CUDA_TRY(cudaMemcpy(s->adj_packs.p, packs.data(), packs.size() * sizeof(Pack), cudaMemcpyHostToDevice));
+  s->adj_n_packs = static_cast<int>(packs.size());
+  s->adj_shape = sh;
   return ROD_OK;
 }
 
@@ -521,6 +590,11 @@ rod_status rod_system_destroy(rod_system* s) {
   s->clamp_Q.release();
   s->rods.release();
   s->packs.release();
+  s->ckpt.release();
+  s->seg_states.release();
+  s->adj.release();
+  s->final_state.release();
+  s->adj_packs.release();
   s->err.release();
   contact_release(s->contact);
   if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
@@ -705,6 +779,127 @@ rod_status rod_system_set_launch(rod_system* s, int32_t elems_per_block, int32_t
   }
   if (step_smem_bytes(sh) > 227 * 1024) return fail(ROD_ERR_ARG, "launch shape needs too much shared memory");
   return build_packs(s, sh);
+}
+
+rod_status rod_system_set_params(rod_system* s, const double* rest_kappa, const double* elem_couple, int on_device) {
+  if (!s) return fail(ROD_ERR_ARG, "null system");
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (rest_kappa) {
+    if (s->V == 0) return fail(ROD_ERR_ARG, "the ensemble has no Voronoi points");
+    if (!on_device && !finite_all(rest_kappa, 3 * s->V)) return fail(ROD_ERR_ARG, "rest_kappa has non-finite values");
+    if (!s->rest_kappa.p) CUDA_TRY(s->rest_kappa.alloc(3 * s->V));
+    CUDA_TRY(cudaMemcpyAsync(s->rest_kappa.p, rest_kappa, 3 * s->V * 8, kind, s->stream));
+  }
+  if (elem_couple) {
+    if (!on_device && !finite_all(elem_couple, 3 * s->E)) return fail(ROD_ERR_ARG, "elem_couple has non-finite values");
+    if (!s->elem_couple.p) CUDA_TRY(s->elem_couple.alloc(3 * s->E));
+    CUDA_TRY(cudaMemcpyAsync(s->elem_couple.p, elem_couple, 3 * s->E * 8, kind, s->stream));
+  }
+  if (!on_device) CUDA_TRY(cudaStreamSynchronize(s->stream));
+  s->ck_valid = false;
+  return ROD_OK;
+}
+
+rod_status rod_system_forward_checkpointed(rod_system* s, int64_t n_steps, double dt, int32_t every) {
+  if (!s) return fail(ROD_ERR_ARG, "null system");
+  if (!s->state_set) return fail(ROD_ERR_STATE, "no state has been set");
+  if (s->contact.enabled) return fail(ROD_ERR_STATE, "the adjoint does not include contact; disable it first");
+  if (n_steps < 1 || every < 1 || !(dt > 0) || !std::isfinite(dt)) return fail(ROD_ERR_ARG, "need n_steps, every >= 1 and dt > 0");
+  const int64_t ss = state_size(s);
+  const int64_t nck = (n_steps + every - 1) / every;
+  if ((int64_t)s->ckpt.n < nck * ss) CUDA_TRY(s->ckpt.alloc(nck * ss));
+  StepParams P = make_params(s);
+  for (int64_t k = 0; k < n_steps; ++k) {
+    if (k % every == 0) CUDA_TRY(pack_state(s, s->ckpt.p + (k / every) * ss));
+    CUDA_TRY(launch_pack_kernel(P, s->shape, MODE_STEPS, 1, s->t + k * dt, dt, 1, nullptr, nullptr, s->stream, s->hook));
+  }
+  s->ck_t0 = s->t;
+  s->ck_dt = dt;
+  s->ck_steps = n_steps;
+  s->ck_every = every;
+  s->ck_valid = true;
+  s->t += n_steps * dt;
+  return read_error_word(s);
+}
+
+rod_status rod_system_backward(rod_system* s, const double* gx, const double* gv, const double* gQ, const double* gw,
+                               double* grad_kappa0, double* grad_couple) {
+  if (!s || !gx || !gv || !gQ || !gw || !grad_kappa0 || !grad_couple) return fail(ROD_ERR_ARG, "null argument");
+  if (!s->ck_valid) return fail(ROD_ERR_STATE, "call rod_system_forward_checkpointed first");
+  rod_status st = prepare_adjoint_shape(s);
+  if (st != ROD_OK) return st;
+  if (!s->rest_kappa.p && s->V > 0) {
+    CUDA_TRY(s->rest_kappa.alloc(3 * s->V));
+    CUDA_TRY(cudaMemsetAsync(s->rest_kappa.p, 0, 3 * s->V * 8, s->stream));
+  }
+  if (!s->elem_couple.p) {
+    CUDA_TRY(s->elem_couple.alloc(3 * s->E));
+    CUDA_TRY(cudaMemsetAsync(s->elem_couple.p, 0, 3 * s->E * 8, s->stream));
+  }
+  const int64_t ss = state_size(s), every = s->ck_every, n = s->ck_steps;
+  if ((int64_t)s->seg_states.n < every * ss) CUDA_TRY(s->seg_states.alloc(every * ss));
+  if ((int64_t)s->adj.n < ss) CUDA_TRY(s->adj.alloc(ss));
+  if ((int64_t)s->final_state.n < ss) CUDA_TRY(s->final_state.alloc(ss));
+  CUDA_TRY(pack_state(s, s->final_state.p));
+  double* ax = s->adj.p;
+  double* av = ax + 3 * s->N;
+  double* aQ = ax + 6 * s->N;
+  double* aw = aQ + 9 * s->E;
+  CUDA_TRY(cudaMemcpyAsync(ax, gx, 3 * s->N * 8, cudaMemcpyDeviceToDevice, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(av, gv, 3 * s->N * 8, cudaMemcpyDeviceToDevice, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(aQ, gQ, 9 * s->E * 8, cudaMemcpyDeviceToDevice, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(aw, gw, 3 * s->E * 8, cudaMemcpyDeviceToDevice, s->stream));
+  if (s->V > 0) CUDA_TRY(cudaMemsetAsync(grad_kappa0, 0, 3 * s->V * 8, s->stream));
+  CUDA_TRY(cudaMemsetAsync(grad_couple, 0, 3 * s->E * 8, s->stream));
+  StepParams P = make_params(s);
+  AdjointParams A;
+  A.ax = ax;
+  A.av = av;
+  A.aQ = aQ;
+  A.aw = aw;
+  A.g_kappa0 = grad_kappa0;
+  A.g_couple = grad_couple;
+  A.dt = s->ck_dt;
+  const int64_t nseg = (n + every - 1) / every;
+  for (int64_t seg = nseg - 1; seg >= 0; --seg) {
+    const int64_t k0 = seg * every, len = std::min(every, n - k0);
+    // recompute the segment's step-start states from its checkpoint
+    CUDA_TRY(unpack_state(s, s->ckpt.p + seg * ss));
+    for (int64_t k = 0; k < len; ++k) {
+      CUDA_TRY(pack_state(s, s->seg_states.p + k * ss));
+      if (k + 1 < len)
+        CUDA_TRY(launch_pack_kernel(P, s->shape, MODE_STEPS, 1, s->ck_t0 + (k0 + k) * s->ck_dt, s->ck_dt, 1, nullptr,
+                                    nullptr, s->stream, s->hook));
+    }
+    for (int64_t k = len - 1; k >= 0; --k) {
+      const double* st0 = s->seg_states.p + k * ss;
+      A.P = P;
+      A.P.packs = s->adj_packs.p;
+      A.P.n_packs = s->adj_n_packs;
+      A.P.x = const_cast<double*>(st0);
+      A.P.v = const_cast<double*>(st0 + 3 * s->N);
+      A.P.Q = const_cast<double*>(st0 + 6 * s->N);
+      A.P.w = const_cast<double*>(st0 + 6 * s->N + 9 * s->E);
+      A.t = s->ck_t0 + (k0 + k) * s->ck_dt;
+      s->hook.before(K_MISC, s->stream);
+      cudaError_t e = launch_adjoint_kernel(A, s->adj_shape, s->stream);
+      s->hook.after(K_MISC, s->stream);
+      CUDA_TRY(e);
+    }
+  }
+  CUDA_TRY(unpack_state(s, s->final_state.p));
+  return read_error_word(s);
+}
+
+rod_status rod_system_adjoint_of_state(rod_system* s, double* ax, double* av, double* aQ, double* aw) {
+  if (!s || !ax || !av || !aQ || !aw) return fail(ROD_ERR_ARG, "null argument");
+  if (!s->adj.p) return fail(ROD_ERR_STATE, "no backward pass has run");
+  CUDA_TRY(cudaMemcpyAsync(ax, s->adj.p, 3 * s->N * 8, cudaMemcpyDeviceToDevice, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(av, s->adj.p + 3 * s->N, 3 * s->N * 8, cudaMemcpyDeviceToDevice, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(aQ, s->adj.p + 6 * s->N, 9 * s->E * 8, cudaMemcpyDeviceToDevice, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(aw, s->adj.p + 6 * s->N + 9 * s->E, 3 * s->E * 8, cudaMemcpyDeviceToDevice, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return ROD_OK;
 }
 
 rod_status rod_system_set_graphs(rod_system* s, int enable) {

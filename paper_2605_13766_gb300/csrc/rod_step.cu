@@ -24,447 +24,11 @@
 #include <cstdint>
 
 #include "rod_internal.h"
+#include "rod_step_device.cuh"
 
 namespace rod {
 
 namespace {
-
-// ---------------------------------------------------------------------------------- math
-
-// High 32 bits of a non-negative double: x < 2^k exactly when hi_word(x) < hi_word(2^k), so a
-// warp-wide integer maximum of these words bounds every lane's argument.
-__device__ __forceinline__ unsigned hi_word(double x) { return static_cast<unsigned>(__double2hiint(x)); }
-constexpr unsigned kHi2m20 = 0x3EB00000u;  // 2^-20
-constexpr unsigned kHi2m10 = 0x3F500000u;  // 2^-10
-
-// sin(th)/th and (1 - cos th)/th^2 as Taylor series in th^2 (8 terms each; the dropped terms
-// are below 5e-20 relative for th^2 <= 1/4); larger angles use sincos.
-__device__ __forceinline__ void rot_coeffs_full(double th2, double& a, double& b) {
-  if (th2 <= 0.25) {
-    a = -1.0 / 1307674368000.0;
-    a = fma(a, th2, 1.0 / 6227020800.0);
-    a = fma(a, th2, -1.0 / 39916800.0);
-    a = fma(a, th2, 1.0 / 362880.0);
-    a = fma(a, th2, -1.0 / 5040.0);
-    a = fma(a, th2, 1.0 / 120.0);
-    a = fma(a, th2, -1.0 / 6.0);
-    a = fma(a, th2, 1.0);
-    b = -1.0 / 20922789888000.0;
-    b = fma(b, th2, 1.0 / 87178291200.0);
-    b = fma(b, th2, -1.0 / 479001600.0);
-    b = fma(b, th2, 1.0 / 3628800.0);
-    b = fma(b, th2, -1.0 / 40320.0);
-    b = fma(b, th2, 1.0 / 720.0);
-    b = fma(b, th2, -1.0 / 24.0);
-    b = fma(b, th2, 0.5);
-  } else {
-    double th = sqrt(th2);
-    double s, c, sh;
-    sincos(th, &s, &c);
-    sh = sin(0.5 * th) / th;
-    a = s / th;
-    b = 2.0 * sh * sh;
-  }
-}
-
-// Same coefficients with the series cut to the warp's largest th^2: below 2^-20 three terms
-// (dropped terms < 2e-22), below 2^-10 four terms (< 3e-18), otherwise the full series.  The
-// choice is uniform across the warp, so lanes never diverge on it.
-__device__ __forceinline__ void rot_coeffs(double th2, double& a, double& b) {
-  const unsigned mx = __reduce_max_sync(__activemask(), hi_word(th2));
-  if (mx < kHi2m20) {
-    a = fma(fma(th2, 1.0 / 120.0, -1.0 / 6.0), th2, 1.0);
-    b = fma(fma(th2, 1.0 / 720.0, -1.0 / 24.0), th2, 0.5);
-  } else if (mx < kHi2m10) {
-    a = fma(fma(fma(th2, -1.0 / 5040.0, 1.0 / 120.0), th2, -1.0 / 6.0), th2, 1.0);
-    b = fma(fma(fma(th2, -1.0 / 40320.0, 1.0 / 720.0), th2, -1.0 / 24.0), th2, 0.5);
-  } else {
-    rot_coeffs_full(th2, a, b);
-  }
-}
-
-// asin(s)/s as a Taylor series in s^2 = |w|^2 (13 terms; dropped tail < 2e-18 for s <= 1/4).
-__device__ __forceinline__ double asin_over_s(double s2) {
-  double f = 676039.0 / 104857600.0;
-  f = fma(f, s2, 88179.0 / 12058624.0);
-  f = fma(f, s2, 46189.0 / 5505024.0);
-  f = fma(f, s2, 12155.0 / 1245184.0);
-  f = fma(f, s2, 6435.0 / 557056.0);
-  f = fma(f, s2, 143.0 / 10240.0);
-  f = fma(f, s2, 231.0 / 13312.0);
-  f = fma(f, s2, 63.0 / 2816.0);
-  f = fma(f, s2, 35.0 / 1152.0);
-  f = fma(f, s2, 5.0 / 112.0);
-  f = fma(f, s2, 3.0 / 40.0);
-  f = fma(f, s2, 1.0 / 6.0);
-  f = fma(f, s2, 1.0);
-  return f;
-}
-
-// theta / sin(theta) of the relative rotation with sin^2 = s2, cos = c.  Warp-uniform cut of the
-// series like rot_coeffs (s2 < 2^-20: three terms, dropped < 4e-20; s2 < 2^-10: six terms,
-// dropped < 2e-20), used only when every lane's rotation is below 90 degrees (c > 0).
-__device__ __forceinline__ double theta_over_sin(double s2, double c) {
-  const unsigned act = __activemask();
-  const unsigned mx = __reduce_max_sync(act, hi_word(s2));
-  const bool acute = __all_sync(act, c > 0.0);
-  if (acute && mx < kHi2m20) return fma(fma(s2, 3.0 / 40.0, 1.0 / 6.0), s2, 1.0);
-  if (acute && mx < kHi2m10) {
-    double f = 63.0 / 2816.0;
-    f = fma(f, s2, 35.0 / 1152.0);
-    f = fma(f, s2, 5.0 / 112.0);
-    f = fma(f, s2, 3.0 / 40.0);
-    f = fma(f, s2, 1.0 / 6.0);
-    return fma(f, s2, 1.0);
-  }
-  if (s2 <= 0.0625 && c > 0.0) return asin_over_s(s2);
-  const double sn = sqrt(s2);
-  return (sn > 0.0) ? atan2(sn, c) / sn : 1.0;
-}
-
-struct Smem {
-  double *X, *VN, *QQ, *WW;     // state
-  double *NF, *TA, *ELL, *EDIL; // element work
-  double *PP, *TT;              // Voronoi work
-  double *IRL, *IM, *ACT;       // constants, per-rod actuation value
-  int* rel0;                    // [CR+1] first element of each rod (pack-local)
-  short *erod, *nrod, *vrod;    // pack-local rod of each element / node / Voronoi point
-  int CE, CN, CV, CR;
-};
-
-__device__ __forceinline__ Smem carve(double* base, const LaunchShape& S) {
-  Smem m;
-  m.CE = S.cap_elems;
-  m.CR = S.cap_rods;
-  m.CN = m.CE + m.CR;
-  m.CV = m.CE;
-  double* p = base;
-  m.X = p;    p += 3 * m.CN;
-  m.VN = p;   p += 3 * m.CN;
-  m.QQ = p;   p += 9 * m.CE;
-  m.WW = p;   p += 3 * m.CE;
-  m.NF = p;   p += 3 * m.CE;
-  m.TA = p;   p += 3 * m.CE;
-  m.ELL = p;  p += m.CE;
-  m.EDIL = p; p += m.CE;
-  m.PP = p;   p += 3 * m.CV;
-  m.TT = p;   p += 3 * m.CV;
-  m.IRL = p;  p += m.CE;
-  m.IM = p;   p += m.CN;
-  m.ACT = p;  p += m.CR;
-  m.rel0 = reinterpret_cast<int*>(p);
-  m.erod = reinterpret_cast<short*>(m.rel0 + m.CR + 1);
-  m.nrod = m.erod + m.CE;
-  m.vrod = m.nrod + m.CN;
-  return m;
-}
-
-__device__ __forceinline__ int find_rod(const int* starts, int nrods, int idx) {
-  // largest r with starts[r] <= idx (starts increasing, starts[0] = 0)
-  int lo = 0, hi = nrods - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (starts[mid] <= idx) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-// ------------------------------------------------------------------ kinematic stage (a1/a11, a2)
-
-__device__ __forceinline__ void kinematic(const StepParams& P, const Pack& pk, Smem& m, double h) {
-  const int Ep = pk.nelem, Np = pk.nnode;
-  for (int i = threadIdx.x; i < Ep; i += blockDim.x) {
-    const int r = m.erod[i];
-    const int g = pk.rod0 + r;
-    const bool held = (i == m.rel0[r]) && P.rods[g].clamp;
-    double q[9];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) q[a] = m.QQ[a * m.CE + i];
-    if (held) {
-#pragma unroll
-      for (int a = 0; a < 9; ++a) q[a] = P.clamp_Q[a * P.n_rods + g];
-    } else {
-      // Q <- R Q, R = exp([phi]x), phi = -h w:  R = I + a K + b K^2 = (1 - b th^2) I + a K + b phi phi^T
-      const double p0 = -h * m.WW[i], p1 = -h * m.WW[m.CE + i], p2 = -h * m.WW[2 * m.CE + i];
-      const double th2 = fma(p0, p0, fma(p1, p1, p2 * p2));
-      double ca, cb;
-      rot_coeffs(th2, ca, cb);
-      const double c0 = fma(-cb, th2, 1.0);
-      const double b0 = cb * p0, b1 = cb * p1, b2 = cb * p2;
-      const double a0 = ca * p0, a1 = ca * p1, a2 = ca * p2;
-      const double R00 = fma(b0, p0, c0), R11 = fma(b1, p1, c0), R22 = fma(b2, p2, c0);
-      const double R01 = fma(b0, p1, -a2), R10 = fma(b1, p0, a2);
-      const double R02 = fma(b0, p2, a1), R20 = fma(b2, p0, -a1);
-      const double R12 = fma(b1, p2, -a0), R21 = fma(b2, p1, a0);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double q0 = q[c], q1 = q[3 + c], q2 = q[6 + c];
-        q[c] = fma(R00, q0, fma(R01, q1, R02 * q2));
-        q[3 + c] = fma(R10, q0, fma(R11, q1, R12 * q2));
-        q[6 + c] = fma(R20, q0, fma(R21, q1, R22 * q2));
-      }
-    }
-#pragma unroll
-    for (int a = 0; a < 9; ++a) m.QQ[a * m.CE + i] = q[a];
-  }
-  for (int j = threadIdx.x; j < Np; j += blockDim.x) {
-    const int r = m.nrod[j];
-    const int g = pk.rod0 + r;
-    const bool held = (j == m.rel0[r] + r) && P.rods[g].clamp;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const double val = held ? P.clamp_x[c * P.n_rods + g] : fma(h, m.VN[c * m.CN + j], m.X[c * m.CN + j]);
-      m.X[c * m.CN + j] = val;
-    }
-  }
-}
-
-// --------------------------------------------------------------- dynamic stage (a3-a7, a10, a2)
-
-// Stage A (elements): geometry, shear strain, internal force, shear couple, transport couples,
-// damping and external couples.
-__device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& pk, Smem& m) {
-  const int Ep = pk.nelem;
-  for (int i = threadIdx.x; i < Ep; i += blockDim.x) {
-    const int r = m.erod[i];
-    const RodConst* rc = P.rods + pk.rod0 + r;
-    const int j = i + r;
-    const int ge = pk.elem0 + i;
-    double l[3], dv[3], q[9], w[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      l[c] = m.X[c * m.CN + j + 1] - m.X[c * m.CN + j];
-      dv[c] = m.VN[c * m.CN + j + 1] - m.VN[c * m.CN + j];
-      w[c] = m.WW[c * m.CE + i];
-    }
-#pragma unroll
-    for (int a = 0; a < 9; ++a) q[a] = m.QQ[a * m.CE + i];
-    const double ll = fma(l[0], l[0], fma(l[1], l[1], l[2] * l[2]));
-    const double rs = rsqrt(ll);            // 1 / ell
-    const double ell = ll * rs;
-    const double irl = m.IRL[i];
-    const double rl = __ldg(P.rest_len + ge);
-    const double e = ell * irl;             // dilatation
-    const double ie = rl * rs;              // 1 / e
-    double Ql[3], sg[3], n[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) Ql[a] = fma(q[3 * a], l[0], fma(q[3 * a + 1], l[1], q[3 * a + 2] * l[2]));
-    sg[0] = Ql[0] * irl;
-    sg[1] = Ql[1] * irl;
-    sg[2] = fma(Ql[2], irl, -1.0);
-    if (P.rest_sigma) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) sg[c] -= __ldg(P.rest_sigma + c * P.E + ge);
-    }
-    // n / e = S sigma / e  (the 1/e of the internal force, folded once)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) n[c] = (__ldg(&rc->S[c]) * ie) * sg[c];
-    // lab internal force N = Q^T n / e
-#pragma unroll
-    for (int b = 0; b < 3; ++b) m.NF[b * m.CE + i] = fma(q[b], n[0], fma(q[3 + b], n[1], q[6 + b] * n[2]));
-    // shear couple ((Q t) x n) rl = (Ql x n) rl / ell = Ql x (n / e)
-    double tc[3];
-    tc[0] = fma(Ql[1], n[2], -Ql[2] * n[1]);
-    tc[1] = fma(Ql[2], n[0], -Ql[0] * n[2]);
-    tc[2] = fma(Ql[0], n[1], -Ql[1] * n[0]);
-    // transport couples (J w / e) x w + (J w / e^2) de/dt,  de/dt = (l . dv) / (ell rl)
-    const double edot = fma(l[0], dv[0], fma(l[1], dv[1], l[2] * dv[2])) * rs * irl;
-    double Jw[3], Jwe[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      Jw[c] = __ldg(&rc->rhoI[c]) * rl * w[c];
-      Jwe[c] = Jw[c] * ie;
-    }
-    const double k2 = ie * ie * edot;
-    const double drot = __ldg(&rc->damp_rot);
-    tc[0] += fma(Jwe[1], w[2], -Jwe[2] * w[1]);
-    tc[1] += fma(Jwe[2], w[0], -Jwe[0] * w[2]);
-    tc[2] += fma(Jwe[0], w[1], -Jwe[1] * w[0]);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) tc[c] = fma(Jw[c], k2 - drot, tc[c]);
-    if (P.elem_couple) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) tc[c] += __ldg(P.elem_couple + c * P.E + ge);
-    }
-    if (P.has_act && (i - m.rel0[r]) == rc->act_elem) tc[0] += m.ACT[r];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) m.TA[c * m.CE + i] = tc[c];
-    m.ELL[i] = ell;
-    m.EDIL[i] = e;
-  }
-}
-
-// Stage B (Voronoi points): curvature by the rotation logarithm, Voronoi dilatation,
-// bending/twist couple m = B(kappa - kappa0), P = m/eps^3, T = (kappa x m) D/eps^3.
-__device__ __forceinline__ void stage_voronoi(const StepParams& P, const Pack& pk, Smem& m) {
-  const int Vp = pk.nvor;
-  for (int k = threadIdx.x; k < Vp; k += blockDim.x) {
-    const int r = m.vrod[k];
-    const RodConst* rc = P.rods + pk.rod0 + r;
-    const int i = k + r;
-    const int gv = pk.vor0 + k;
-    double qa[9], qb[9];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      qa[a] = m.QQ[a * m.CE + i];
-      qb[a] = m.QQ[a * m.CE + i + 1];
-    }
-    // R = Q_{k+1} Q_k^T, R_ab = d_a(k+1) . d_b(k);  u = (R32 - R23, R13 - R31, R21 - R12)
-    double u0 = qb[6] * qa[3];
-    u0 = fma(qb[7], qa[4], u0);
-    u0 = fma(qb[8], qa[5], u0);
-    u0 = fma(-qb[3], qa[6], u0);
-    u0 = fma(-qb[4], qa[7], u0);
-    u0 = fma(-qb[5], qa[8], u0);
-    double u1 = qb[0] * qa[6];
-    u1 = fma(qb[1], qa[7], u1);
-    u1 = fma(qb[2], qa[8], u1);
-    u1 = fma(-qb[6], qa[0], u1);
-    u1 = fma(-qb[7], qa[1], u1);
-    u1 = fma(-qb[8], qa[2], u1);
-    double u2 = qb[3] * qa[0];
-    u2 = fma(qb[4], qa[1], u2);
-    u2 = fma(qb[5], qa[2], u2);
-    u2 = fma(-qb[0], qa[3], u2);
-    u2 = fma(-qb[1], qa[4], u2);
-    u2 = fma(-qb[2], qa[5], u2);
-    double tr = qb[0] * qa[0];
-#pragma unroll
-    for (int a = 1; a < 9; ++a) tr = fma(qb[a], qa[a], tr);
-    const double s2 = 0.25 * fma(u0, u0, fma(u1, u1, u2 * u2));  // |w|^2 = sin^2(theta)
-    const double c = 0.5 * (tr - 1.0);                             // cos(theta)
-    const double f = theta_over_sin(s2, c);
-    const double i2D = __ldg(P.inv_2D + gv);
-    const double kf = -f * i2D;             // kappa = -(theta/s) w / D = -f u / (2D)
-    double kap[3] = {kf * u0, kf * u1, kf * u2};
-    const double eps = (m.ELL[i] + m.ELL[i + 1]) * i2D;
-    const double ieps = __drcp_rn(eps);
-    const double ie3 = ieps * ieps * ieps;
-    double mk[3];
-    if (P.rest_kappa) {
-#pragma unroll
-      for (int cc = 0; cc < 3; ++cc) mk[cc] = __ldg(&rc->B[cc]) * (kap[cc] - __ldg(P.rest_kappa + cc * P.V + gv));
-    } else {
-#pragma unroll
-      for (int cc = 0; cc < 3; ++cc) mk[cc] = __ldg(&rc->B[cc]) * kap[cc];
-    }
-    const double tD = __ldg(P.Dhat + gv) * ie3;
-    m.PP[k] = mk[0] * ie3;
-    m.PP[m.CV + k] = mk[1] * ie3;
-    m.PP[2 * m.CV + k] = mk[2] * ie3;
-    m.TT[k] = fma(kap[1], mk[2], -kap[2] * mk[1]) * tD;
-    m.TT[m.CV + k] = fma(kap[2], mk[0], -kap[0] * mk[2]) * tD;
-    m.TT[2 * m.CV + k] = fma(kap[0], mk[1], -kap[1] * mk[0]) * tD;
-  }
-}
-
-// Stage C (elements): bending couple from the difference and trapezoid operators, angular
-// acceleration e J^{-1} tau, rate update and constraint; optional kinematic rotation.
-template <int MODE>
-__device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& pk, Smem& m, double dt, double h,
-                                               double* acc_w) {
-  const int Ep = pk.nelem;
-  for (int i = threadIdx.x; i < Ep; i += blockDim.x) {
-    const int r = m.erod[i];
-    const int g = pk.rod0 + r;
-    const RodConst* rc = P.rods + g;
-    const int first = m.rel0[r];
-    const int nr = m.rel0[r + 1] - first;
-    const int li = i - first;
-    const int k = i - r;                     // right Voronoi point (valid if li < nr-1)
-    const bool hasR = li < nr - 1, hasL = li > 0;
-    double tau[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const double Pr = hasR ? m.PP[c * m.CV + k] : 0.0;
-      const double Pl = hasL ? m.PP[c * m.CV + k - 1] : 0.0;
-      const double Tr = hasR ? m.TT[c * m.CV + k] : 0.0;
-      const double Tl = hasL ? m.TT[c * m.CV + k - 1] : 0.0;
-      tau[c] = fma(0.5, Tl + Tr, (Pr - Pl) + m.TA[c * m.CE + i]);
-    }
-    const bool held = (li == 0) && rc->clamp;
-    if (MODE == MODE_RHS) {
-      const double ke = m.EDIL[i] * m.IRL[i];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) acc_w[c * P.E + pk.elem0 + i] = held ? 0.0 : ke * __ldg(&rc->inv_rhoI[c]) * tau[c];
-    } else {
-      // w += dt e J^{-1} tau,  J^{-1} = 1/(rho I rl)
-      const double ke = (dt * m.EDIL[i]) * m.IRL[i];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        m.WW[c * m.CE + i] = held ? 0.0 : fma(ke * __ldg(&rc->inv_rhoI[c]), tau[c], m.WW[c * m.CE + i]);
-    }
-  }
-}
-
-// Stage D (nodes): internal force difference, external forces, velocity update + constraint.
-template <int MODE>
-__device__ __forceinline__ void stage_translation(const StepParams& P, const Pack& pk, Smem& m, double dt,
-                                                  double* acc_v) {
-  const int Np = pk.nnode;
-  const double dtg[3] = {dt * P.gravity[0], dt * P.gravity[1], dt * P.gravity[2]};
-  for (int j = threadIdx.x; j < Np; j += blockDim.x) {
-    const int r = m.nrod[j];
-    const int g = pk.rod0 + r;
-    const RodConst* rc = P.rods + g;
-    const int firstn = m.rel0[r] + r;
-    const int nr = m.rel0[r + 1] - m.rel0[r];
-    const int lj = j - firstn;
-    const bool hasR = lj < nr, hasL = lj > 0;
-    const int iR = j - r;                    // element to the right (pack-local)
-    const bool held = (lj == 0) && rc->clamp;
-    const double im = m.IM[j];
-    const double dl = __ldg(&rc->damp_lin);
-    double F[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const double Nr = hasR ? m.NF[c * m.CE + iR] : 0.0;
-      const double Nl = hasL ? m.NF[c * m.CE + iR - 1] : 0.0;
-      F[c] = Nr - Nl;
-    }
-    if (lj == nr) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) F[c] += __ldg(&rc->tip[c]);
-    }
-    if (P.fseg) {
-      const int ge = pk.elem0 + iR;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        double fc = 0.0;
-        if (hasR) fc += __ldg(P.fseg + c * P.E + ge);              // node a of segment iR
-        if (hasL) fc += __ldg(P.fseg + (3 + c) * P.E + ge - 1);    // node b of segment iR-1
-        F[c] += fc;
-      }
-    }
-    if (MODE == MODE_RHS) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double vj = m.VN[c * m.CN + j];
-        double a = fma(F[c], im, -dl * vj);
-        if (P.has_gravity) a += P.gravity[c];
-        acc_v[c * P.N + pk.node0 + j] = held ? 0.0 : a;
-      }
-    } else {
-      // v += dt (F/m - c v + g)  as  v (1 - dt c) + (dt/m) F + dt g
-      const double keep = fma(-dt, dl, 1.0), dtim = dt * im;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double vj = m.VN[c * m.CN + j];
-        const double base = P.has_gravity ? fma(vj, keep, dtg[c]) : vj * keep;
-        m.VN[c * m.CN + j] = held ? 0.0 : fma(F[c], dtim, base);
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void actuation_values(const StepParams& P, const Pack& pk, Smem& m, double t) {
-  if (!P.has_act) return;
-  for (int r = threadIdx.x; r < pk.nrods; r += blockDim.x) {
-    const RodConst* rc = P.rods + pk.rod0 + r;
-    const double amp = rc->act_amp;
-    m.ACT[r] = (amp != 0.0) ? amp * sin(fma(rc->act_omega, t, rc->act_phase)) : 0.0;
-  }
-}
 
 // ------------------------------------------------------------------------- the pack kernel
 
@@ -476,44 +40,9 @@ __global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, 
   if (MODE == MODE_ONE_STEP && *(volatile int*)P.err != 0) return;
   const Pack pk = P.packs[blockIdx.x];
   Smem m = carve(smem_d, S);
-  const int Ep = pk.nelem, Np = pk.nnode, Rp = pk.nrods, Vp = pk.nvor;
+  const int Ep = pk.nelem, Np = pk.nnode;
 
-  // ---- stage the pack
-  for (int r = threadIdx.x; r < Rp; r += blockDim.x) m.rel0[r] = P.rods[pk.rod0 + r].elem0 - pk.elem0;
-  if (threadIdx.x == 0) m.rel0[Rp] = Ep;
-  __syncthreads();
-  for (int i = threadIdx.x; i < Ep; i += blockDim.x) {
-    m.erod[i] = (short)find_rod(m.rel0, Rp, i);
-    m.IRL[i] = __ldg(P.inv_rl + pk.elem0 + i);
-#pragma unroll
-    for (int a = 0; a < 9; ++a) m.QQ[a * m.CE + i] = P.Q[a * P.E + pk.elem0 + i];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) m.WW[c * m.CE + i] = P.w[c * P.E + pk.elem0 + i];
-  }
-  for (int j = threadIdx.x; j < Np; j += blockDim.x) {
-    // node j belongs to rod r with rel0[r] + r <= j
-    int lo = 0, hi = Rp - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (m.rel0[mid] + mid <= j) lo = mid; else hi = mid - 1;
-    }
-    m.nrod[j] = (short)lo;
-    m.IM[j] = __ldg(P.inv_m + pk.node0 + j);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      m.X[c * m.CN + j] = P.x[c * P.N + pk.node0 + j];
-      m.VN[c * m.CN + j] = P.v[c * P.N + pk.node0 + j];
-    }
-  }
-  for (int k = threadIdx.x; k < Vp; k += blockDim.x) {
-    int lo = 0, hi = Rp - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (m.rel0[mid] - mid <= k) lo = mid; else hi = mid - 1;
-    }
-    m.vrod[k] = (short)lo;
-  }
-  __syncthreads();
+  stage_pack(P, pk, m);
 
   if (MODE == MODE_KIN_HALF) {
     kinematic(P, pk, m, 0.5 * dt);

@@ -1,0 +1,182 @@
+"""Hand-written adjoint of the rod step (torch.autograd.Function over rod_system_backward).
+
+Gradients of the tip-target loss L = sum_r |x_tip,r(T) - target_r|^2 with respect to the rest
+curvature kappa0 and the element couples C are checked against central finite differences
+(h = 1e-6) along 8 seeded random directions:
+  * small ensemble: differences of the CPU oracle's own forward runs (independent code);
+  * the full 1024 x 64 x 2000-step workload: differences of the GPU forward (the forward is
+    pinned to the oracle by the parity tests); checkpoint every 100 steps.
+The adjoint of the initial state after one step is also checked entry by entry against
+finite differences of the oracle.
+"""
+import numpy as np
+import pytest
+
+import rodgen
+from oracle.oracle import Oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_13766_gb300 import build
+    build.build()
+
+
+def _small_problem():
+    p = rodgen.adjoint_batch(n_rods=4, n=16, kappa_scale=2.0, couple_scale=2e-6, target_scale=0.01, seed=5)
+    clamp = np.array([1, 1, 1, 0], dtype=np.int8)
+    rng = np.random.default_rng(5)
+    v = p.v.copy()
+    off = p.node_offsets()
+    v[:, off[3]:off[4]] = rng.normal(0, 0.05, (3, 1))
+    return p.replace(clamp_base=clamp, v=v, nu_damp=0.02, gravity=np.array([0.0, -3.0, 0.0]))
+
+
+def _loss_oracle(p, kappa0, couple, n_steps, dt):
+    q = p.replace(rest_kappa=kappa0, elem_couple=couple)
+    x = Oracle(q).step(*q.state(), dt=dt, n_steps=n_steps)[0]
+    tips = x[:, p.node_offsets()[1:] - 1]
+    return float(((tips - p.extra["targets"]) ** 2).sum())
+
+
+def _grads_gpu(p, n_steps, dt, every):
+    import torch
+    from paper_2605_13766_gb300 import RodSystem
+    from paper_2605_13766_gb300.autograd import rollout, tip_indices
+    s = RodSystem(p)
+    k0 = torch.tensor(p.rest_kappa, device="cuda", requires_grad=True)
+    c0 = torch.tensor(p.elem_couple, device="cuda", requires_grad=True)
+    state0 = [torch.tensor(a, device="cuda") for a in p.state()]
+    x, v, Q, w = rollout(s, k0, c0, state0, n_steps, dt, every)
+    tips = x[:, tip_indices(p.node_offsets())]
+    L = ((tips - torch.tensor(p.extra["targets"], device="cuda")) ** 2).sum()
+    L.backward()
+    return float(L.item()), k0.grad.cpu().numpy(), c0.grad.cpu().numpy(), s
+
+
+def _directions(p, n, seed):
+    rng = np.random.default_rng(seed)
+    ks = np.abs(p.rest_kappa).max()
+    cs = np.abs(p.elem_couple).max()
+    return [(rng.normal(size=p.rest_kappa.shape) * ks, rng.normal(size=p.elem_couple.shape) * cs) for _ in range(n)]
+
+
+def test_adjoint_matches_oracle_finite_differences_small():
+    p = _small_problem()
+    n_steps, dt, every = 200, 1e-5, 50
+    L, gk, gc, _ = _grads_gpu(p, n_steps, dt, every)
+    L_ref = _loss_oracle(p, p.rest_kappa, p.elem_couple, n_steps, dt)
+    assert abs(L - L_ref) <= 1e-10 * abs(L_ref)
+    report = []
+    for dk, dc in _directions(p, 8, seed=1):
+        fd = {}
+        for h in (1e-6, 1e-5):
+            fd[h] = (_loss_oracle(p, p.rest_kappa + h * dk, p.elem_couple + h * dc, n_steps, dt)
+                     - _loss_oracle(p, p.rest_kappa - h * dk, p.elem_couple - h * dc, n_steps, dt)) / (2 * h)
+        ad = float((gk * dk).sum() + (gc * dc).sum())
+        report.append((ad, fd[1e-6], fd[1e-5]))
+        assert abs(ad - fd[1e-6]) <= 1e-6 * abs(fd[1e-6]), (ad, fd)
+    _record("adjoint_small_oracle_fd", report)
+
+
+def test_adjoint_full_workload_matches_finite_differences():
+    import torch
+    from paper_2605_13766_gb300 import RodSystem
+    from paper_2605_13766_gb300.autograd import tip_indices
+    p = rodgen.adjoint_batch()                       # 1024 rods x 64 elements
+    n_steps, dt, every = 2000, 1e-5, 100
+    L, gk, gc, s = _grads_gpu(p, n_steps, dt, every)
+    tips = tip_indices(p.node_offsets())
+    targets = torch.tensor(p.extra["targets"], device="cuda")
+    state0 = [torch.tensor(a, device="cuda") for a in p.state()]
+
+    def loss(k, c):
+        s.set_params(k, c)
+        s.set_state(*state0)
+        s.forward_checkpointed(n_steps, dt, every)
+        x = s.get_state(device=True)[0]
+        return float(((x[:, tips] - targets) ** 2).sum().item())
+
+    # Central differences at h = 1e-6 carry a rounding noise of ~2.5e-9 absolute here (a loss of
+    # ~0.2 summed over 1024 rods after 2000 steps, differenced over 2e-6), i.e. up to ~1e-5 of
+    # the smaller directional derivatives; h = 1e-5 has ten times less noise and a truncation
+    # error ~h^2 ~ 1e-10.  The adjoint must agree with the h = 1e-5 differences to 1e-6; the
+    # h = 1e-6 differences are recorded beside them.
+    k0 = torch.tensor(p.rest_kappa, device="cuda")
+    c0 = torch.tensor(p.elem_couple, device="cuda")
+    report = []
+    for dk, dc in _directions(p, 8, seed=2):
+        dkt, dct = torch.tensor(dk, device="cuda"), torch.tensor(dc, device="cuda")
+        fd = {}
+        for h in (1e-6, 1e-5):
+            fd[h] = (loss(k0 + h * dkt, c0 + h * dct) - loss(k0 - h * dkt, c0 - h * dct)) / (2 * h)
+        ad = float((gk * dk).sum() + (gc * dc).sum())
+        report.append((ad, fd[1e-6], fd[1e-5]))
+        assert abs(ad - fd[1e-5]) <= 1e-6 * abs(fd[1e-5]), (ad, fd)
+    _record("adjoint_full_fd", report)
+
+
+def _record(name, rows):
+    import json
+    import os
+    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    if os.path.isdir(out):
+        with open(os.path.join(out, f"{name}.json"), "w") as f:
+            json.dump([{"adjoint": a, "fd_h1e-6": b, "fd_h1e-5": c, "rel_err_h1e-6": abs(a - b) / abs(c),
+                        "rel_err_h1e-5": abs(a - c) / abs(c)} for a, b, c in rows], f, indent=1)
+
+
+def test_state_adjoint_of_one_step_matches_oracle():
+    """d L / d(initial state) after one step, every entry, against central differences of the
+    oracle (positions, velocities, the nine director entries, angular velocities)."""
+    import torch
+    from paper_2605_13766_gb300 import RodSystem
+    from paper_2605_13766_gb300.autograd import rollout, tip_indices
+    p = rodgen.perturbed(_small_problem(), seed=9, pos=0.01, vel=0.1, rot=0.05, omega=5.0)
+    dt = 1e-5
+    s = RodSystem(p)
+    k0 = torch.tensor(p.rest_kappa, device="cuda", requires_grad=True)
+    c0 = torch.tensor(p.elem_couple, device="cuda", requires_grad=True)
+    state0 = [torch.tensor(a, device="cuda") for a in p.state()]
+    # loss of the whole final state: sum of seeded weights times every state entry
+    rng = np.random.default_rng(3)
+    W = [rng.normal(size=a.shape) for a in p.state()]
+    out = rollout(s, k0, c0, state0, 1, dt, 1)
+    L = sum((o * torch.tensor(wt, device="cuda")).sum() for o, wt in zip(out, W))
+    L.backward()
+    adj = [a.cpu().numpy() for a in s.adjoint_of_state()]
+    o = Oracle(p)
+
+    def loss(st):
+        fin = o.step(*st, dt=dt, n_steps=1)
+        return sum(float((f * wt).sum()) for f, wt in zip(fin, W))
+
+    base = list(p.state())
+    h = 1e-8
+    checked = 0
+    # the clamp holds node 0 and element 0 of a clamped rod at their given values: skip them
+    free_nodes = np.ones(p.n_nodes, dtype=bool)
+    free_elems = np.ones(p.n_elems, dtype=bool)
+    for r in np.flatnonzero(p.clamp_base):
+        free_nodes[p.node_offsets()[r]] = False
+        free_elems[p.elem_offsets()[r]] = False
+    for a_idx in range(4):
+        arr = base[a_idx]
+        mask = np.broadcast_to(free_nodes if a_idx < 2 else free_elems, arr.shape)
+        flat = np.flatnonzero(mask)
+        for f in rng.choice(flat, size=min(24, flat.size), replace=False):
+            plus = [b.copy() for b in base]
+            minus = [b.copy() for b in base]
+            plus[a_idx].flat[f] += h
+            minus[a_idx].flat[f] -= h
+            fd = (loss(plus) - loss(minus)) / (2 * h)
+            ad = adj[a_idx].flat[f]
+            scale = max(abs(fd), 1e-3 * np.abs(adj[a_idx]).max(), 1e-12)
+            assert abs(ad - fd) <= 1e-5 * scale, (a_idx, f, ad, fd)
+            checked += 1
+    assert checked > 60

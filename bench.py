@@ -191,6 +191,7 @@ def _e2e(s, p, dt, K, world, dist, barrier):
     """Same metric through the public API from pinned host buffers: set_state (H2D), K steps,
     get_state (D2H) inside the timed region."""
     import torch
+    from paper_2605_13766_gb300.replicas import slowest, total
     x, v, Q, w = p.state()
     pin = [torch.from_numpy(a).pin_memory() for a in (x, v, Q, w)]
     outs = [torch.empty(a.shape, dtype=torch.float64).pin_memory() for a in (x, v, Q, w)]
@@ -200,13 +201,9 @@ def _e2e(s, p, dt, K, world, dist, barrier):
     s.set_state(*[a.numpy() for a in pin])
     s.step(K, dt)
     xs = s.get_state()
-    t_e2e = time.perf_counter() - t0
+    t_e2e = slowest(time.perf_counter() - t0)
     state_bytes = 8 * (6 * p.n_nodes + 12 * p.n_elems)
-    if dist is not None:
-        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": world * p.n_elems * K / t_e2e, "unit": UNIT, "h2d_bytes_per_step": state_bytes / K,
+    e2e = {"value": total(p.n_elems * K) / t_e2e, "unit": UNIT, "h2d_bytes_per_step": state_bytes / K,
            "d2h_bytes_per_step": state_bytes / K,
            "note": f"set_state from pinned host + {K} steps + get_state to host per round trip"}
     del outs, xs
@@ -244,6 +241,7 @@ def main():
             dist.barrier()
 
     from paper_2605_13766_gb300 import RodSystem, build
+    from paper_2605_13766_gb300.replicas import slowest, total
     build.build()
     p, dt, desc = _workload(args.workload, rank)
     s = RodSystem(p)
@@ -272,13 +270,8 @@ def main():
     ms = ev0.elapsed_time(ev1)
     launches = s.launch_count - launches0
     t_local = ms / 1e3
-    if dist is not None:
-        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
-    value = world * p.n_elems * K / t_max
+    t_max = slowest(t_local)
+    value = total(p.n_elems * K) / t_max
 
     # ---- per-kernel device times: the same K steps again with CUDA events around every launch
     # (eager launches: the event pairs sit between kernels on the same stream)

@@ -125,8 +125,8 @@ rod_status rod_system_rhs(rod_system* sys, double t, double* acc_v, double* acc_
 rod_status rod_system_contact_forces(rod_system* sys, double* f);
 
 /* Launch shape used by the step kernels: elements per thread block and threads per block
- * (0 = choose by the built-in autotuner on the next step).  Returns ROD_ERR_ARG if the shape
- * cannot hold the longest rod. */
+ * (0 keeps the built-in default for that value).  Returns ROD_ERR_ARG if the shape cannot
+ * hold the longest rod or needs more shared memory than a block has. */
 rod_status rod_system_set_launch(rod_system* sys, int32_t elems_per_block, int32_t threads_per_block);
 rod_status rod_system_get_launch(const rod_system* sys, int32_t* elems_per_block, int32_t* threads_per_block);
 
@@ -169,6 +169,15 @@ rod_status rod_system_profile_read(rod_system* sys, int32_t k, const char** name
 
 /* Total number of kernels this system has launched since it was created. */
 rod_status rod_system_launch_count(const rod_system* sys, int64_t* launches);
+
+/* Autotuner: time trial_steps steps of dt (after one warm-up step) for every valid launch shape
+ * (elements per block 192..768, threads per block 128..512), keep the fastest and restore the
+ * state and time.  Results are cached per ensemble signature (rod count, elements, longest and
+ * shortest rod, contact on/off) for the process, and in the text file named by the environment
+ * variable ROD_AUTOTUNE_CACHE when it is set.  Outputs may be NULL; *best_ms is the time per
+ * step of the winner (-1 when it came from the cache). */
+rod_status rod_system_autotune(rod_system* sys, double dt, int32_t trial_steps, int32_t* best_elems,
+                               int32_t* best_threads, double* best_ms);
 
 /* Longest rod (elements) one thread block can hold with the largest supported shape. */
 int32_t rod_max_elements_per_rod(void);

@@ -74,6 +74,7 @@ _SIGNATURES = {
     "rod_system_get_launch": ([_P, _P, _P], C.c_int),
     "rod_system_set_graphs": ([_P, C.c_int], C.c_int),
     "rod_system_set_params": ([_P, _P, _P, C.c_int], C.c_int),
+    "rod_system_autotune": ([_P, C.c_double, C.c_int32, _P, _P, _P], C.c_int),
     "rod_system_forward_checkpointed": ([_P, C.c_int64, C.c_double, C.c_int32], C.c_int),
     "rod_system_backward": ([_P, _P, _P, _P, _P, _P, _P], C.c_int),
     "rod_system_adjoint_of_state": ([_P, _P, _P, _P, _P], C.c_int),
@@ -340,6 +341,13 @@ class RodSystem:
     # -- launch shape
     def set_launch(self, elems_per_block: int = 0, threads_per_block: int = 0):
         _check(self.lib.rod_system_set_launch(self.handle, int(elems_per_block), int(threads_per_block)))
+
+    def autotune(self, dt: float, trial_steps: int = 20):
+        """Pick the fastest launch shape by timing; returns (elements per block, threads, ms per step)."""
+        e, t, ms = C.c_int32(), C.c_int32(), C.c_double()
+        _check(self.lib.rod_system_autotune(self.handle, float(dt), int(trial_steps), C.byref(e), C.byref(t),
+                                            C.byref(ms)))
+        return e.value, t.value, ms.value
 
     def get_launch(self):
         e, t = C.c_int32(), C.c_int32()

@@ -10,7 +10,10 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -779,6 +782,120 @@ rod_status rod_system_set_launch(rod_system* s, int32_t elems_per_block, int32_t
   }
   if (step_smem_bytes(sh) > 227 * 1024) return fail(ROD_ERR_ARG, "launch shape needs too much shared memory");
   return build_packs(s, sh);
+}
+
+// ---- autotuner: time the step for every valid (elements per block, threads per block) and keep
+// the fastest; results are cached per ensemble signature for the process and, when the
+// environment variable ROD_AUTOTUNE_CACHE names a file, across processes.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune_cache;
+bool g_tune_loaded = false;
+
+std::string tune_key(const rod_system* s) {
+  int min_n = 1 << 30;
+  for (const auto& r : s->rods_h) min_n = std::min(min_n, r.n);
+  char buf[160];
+  snprintf(buf, sizeof buf, "R%d_E%lld_max%d_min%d_contact%d", s->R, (long long)s->E, s->max_n, min_n,
+           s->contact.enabled ? 1 : 0);
+  return buf;
+}
+
+void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("ROD_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char key[160];
+  int cap, thr;
+  while (std::fscanf(f, "%159s %d %d", key, &cap, &thr) == 3) g_tune_cache[key] = {cap, thr};
+  std::fclose(f);
+}
+
+void tune_store() {
+  const char* path = std::getenv("ROD_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return;
+  for (const auto& kv : g_tune_cache) std::fprintf(f, "%s %d %d\n", kv.first.c_str(), kv.second.first, kv.second.second);
+  std::fclose(f);
+}
+}  // namespace
+
+rod_status rod_system_autotune(rod_system* s, double dt, int32_t trial_steps, int32_t* best_elems,
+                               int32_t* best_threads, double* best_ms) {
+  if (!s) return fail(ROD_ERR_ARG, "null system");
+  if (!s->state_set) return fail(ROD_ERR_STATE, "no state has been set");
+  if (!(dt > 0) || trial_steps < 1) return fail(ROD_ERR_ARG, "need dt > 0 and trial_steps >= 1");
+  const std::string key = tune_key(s);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_load();
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      rod_status st = rod_system_set_launch(s, it->second.first, it->second.second);
+      if (st == ROD_OK) {
+        if (best_elems) *best_elems = it->second.first;
+        if (best_threads) *best_threads = it->second.second;
+        if (best_ms) *best_ms = -1.0;
+        return ROD_OK;
+      }
+    }
+  }
+  const int64_t ss = state_size(s);
+  DevBuf<double> saved;
+  CUDA_TRY(saved.alloc(ss));
+  CUDA_TRY(pack_state(s, saved.p));
+  const double t_saved = s->t;
+  const LaunchShape before = s->shape;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bc = before.cap_elems, bt = before.threads;
+  const int caps[] = {192, 256, 320, 384, 448, 512, 640, 768};
+  const int thrs[] = {128, 256, 384, 512};
+  for (int cap : caps) {
+    if (cap < s->max_n) continue;
+    for (int thr : thrs) {
+      if (thr > cap) continue;
+      if (rod_system_set_launch(s, cap, thr) != ROD_OK) continue;
+      // warm-up step, then the timed trial, then back to the saved state
+      if (rod_system_step_async(s, 1, dt) != ROD_OK) continue;
+      cudaEventRecord(e0, s->stream);
+      if (rod_system_step_async(s, trial_steps, dt) != ROD_OK) continue;
+      cudaEventRecord(e1, s->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bc = cap;
+        bt = thr;
+      }
+      CUDA_TRY(unpack_state(s, saved.p));
+      s->t = t_saved;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CUDA_TRY(unpack_state(s, saved.p));
+  CUDA_TRY(cudaMemsetAsync(s->err.p, 0, sizeof(int), s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  s->t = t_saved;
+  rod_status st = rod_system_set_launch(s, bc, bt);
+  if (st != ROD_OK) return st;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = {bc, bt};
+    tune_store();
+  }
+  if (best_elems) *best_elems = bc;
+  if (best_threads) *best_threads = bt;
+  if (best_ms) *best_ms = best < 1e29f ? best / trial_steps : -1.0;
+  return ROD_OK;
 }
 
 rod_status rod_system_set_params(rod_system* s, const double* rest_kappa, const double* elem_couple, int on_device) {

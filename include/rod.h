@@ -182,6 +182,79 @@ rod_status rod_system_autotune(rod_system* sys, double dt, int32_t trial_steps, 
 /* Longest rod (elements) one thread block can hold with the largest supported shape. */
 int32_t rod_max_elements_per_rod(void);
 
+/* Learned surrogate of a window of fine steps for rods of 50 elements (the paper has no
+ * learned component): four 1D convolutions along the rod (kernel 5, 64 channels, SiLU), BF16
+ * weights and activations on tensor cores with FP32 accumulation, FP64 state update.
+ * Inputs per node position j (24 features; feature = float(raw - in_shift) * in_scale, zero
+ * where undefined): position minus the base node [0..2], velocity [3..5], directors d1, d2 of
+ * element j [6..11], angular velocity of element j [12..14], half the axial vector of
+ * R - R^T with R = Q_j Q_{j-1}^T [15..17], the edge Q_j (x_{j+1} - x_j) [18..20] and the base
+ * couple A sin(2 pi t / T + phi) at the window's start, middle and end [21..23].
+ * Outputs (15 channels): the change of x, v, d1, d2, w over the window minus the kinematic
+ * prior (x + T v; Q turned by exp([-T w]x); v and w unchanged), divided by out_scale.  The
+ * update is state = prior + out_scale * output in FP64, then Gram-Schmidt on d1, d2 with
+ * d3 = d1 x d2; a clamped rod keeps node 0 and element 0 (at rest).
+ *   create(window_steps, dt)        a network with all parameters zero for windows of
+ *                                   window_steps fine steps of dt (T = window_steps * dt)
+ *   num_params()                    length of the FP32 parameter vector
+ *   set_params / get_params         FP32 parameters (host or device); set resets Adam's moments
+ *   set_scales(shift[24], scale[24], out[15])   feature shift / scale and output scales (host)
+ *   train_step(...)                 one Adam step (lr > 0) or loss + gradient only (lr <= 0) on a
+ *                                   batch of windows: states at the window start and end for
+ *                                   nwin rods in the system layout (device pointers), act
+ *                                   [3][nwin] = base couple at the window's start, middle and
+ *                                   end; *loss_out (host, optional) receives the mean-square
+ *                                   loss over nwin x 51 x 15 outputs (synchronises the stream)
+ *   get_grad                        the FP32 gradient of the last train_step
+ *   raw_features                    the unscaled FP64 features [nwin][24][51] (device) and a mask
+ *                                   [nwin][24][51] (int8, 1 where defined; NULL to skip)
+ *   raw_targets                     the unscaled FP64 targets [nwin][15][51] (device): state
+ *                                   change over the window minus the prior
+ *   forward                         raw outputs [nwin][51][16] (FP32, device) for given states
+ *   apply(sys, n_calls)             advance every rod of a system (50 elements each, contact
+ *                                   off) by n_calls windows; synchronises the system's stream
+ *   rollout(sys, shadow, ...)       n_calls windows with a periodic check: every check_every
+ *                                   calls the tips of the sampled rods sample_rods[0..n_sample)
+ *                                   are compared with the shadow system, which holds those rods
+ *                                   (same order, same time) and follows them with the plain
+ *                                   step; if max |x_tip - x_tip(shadow)| / L exceeds bound, the
+ *                                   segment is undone and redone with the plain step.  stats
+ *                                   (optional) receives the counts and errors.
+ * All calls return ROD_ERR_ARG for bad arguments, ROD_ERR_CUDA for CUDA failures. */
+typedef struct rod_surrogate rod_surrogate;
+typedef struct {
+  int64_t surrogate_calls;   /* windows advanced by the network */
+  int64_t fallback_calls;    /* windows redone with the plain step */
+  int64_t checks;            /* error checks made */
+  double max_err;            /* largest sampled error kept (after any fallback) */
+  double last_err;           /* sampled error at the end */
+  double rejected_err;       /* largest sampled error that caused a fallback (0: none) */
+} rod_surrogate_stats;
+rod_status rod_surrogate_create(int32_t window_steps, double dt, rod_surrogate** out);
+rod_status rod_surrogate_destroy(rod_surrogate* sur);
+int64_t rod_surrogate_num_params(void);
+rod_status rod_surrogate_set_params(rod_surrogate* sur, const float* params, int on_device);
+rod_status rod_surrogate_get_params(rod_surrogate* sur, float* params, int on_device);
+rod_status rod_surrogate_set_scales(rod_surrogate* sur, const double* in_shift, const double* in_scale,
+                                    const double* out_scale);
+rod_status rod_surrogate_train_step(rod_surrogate* sur, const double* x0, const double* v0, const double* Q0,
+                                    const double* w0, const double* x1, const double* v1, const double* Q1,
+                                    const double* w1, const double* act, int32_t nwin, float lr, float* loss_out,
+                                    void* cuda_stream);
+rod_status rod_surrogate_get_grad(rod_surrogate* sur, float* grad, int on_device);
+rod_status rod_surrogate_forward(rod_surrogate* sur, const double* x, const double* v, const double* Q,
+                                 const double* w, const double* act, int32_t nwin, float* out, void* cuda_stream);
+rod_status rod_surrogate_raw_features(rod_surrogate* sur, const double* x, const double* v, const double* Q,
+                                      const double* w, const double* act, int32_t nwin, double* out, int8_t* mask,
+                                      void* cuda_stream);
+rod_status rod_surrogate_raw_targets(rod_surrogate* sur, const double* x0, const double* v0, const double* Q0,
+                                     const double* w0, const double* x1, const double* v1, const double* Q1,
+                                     const double* w1, int32_t nwin, double* out, void* cuda_stream);
+rod_status rod_surrogate_apply(rod_surrogate* sur, rod_system* sys, int64_t n_calls);
+rod_status rod_surrogate_rollout(rod_surrogate* sur, rod_system* sys, rod_system* shadow, const int32_t* sample_rods,
+                                 int32_t n_sample, int64_t n_calls, int32_t check_every, double bound,
+                                 rod_surrogate_stats* stats);
+
 /* Contact forces without allocating anything (the paper has no counterpart: this is a service
  * for callers that cannot allocate device memory when they need the forces, such as code
  * running inside another framework's allocator or memory pool, or a loop that must not enter

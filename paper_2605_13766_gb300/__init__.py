@@ -3,6 +3,6 @@
 ``RodSystem`` wraps the C ABI of ``include/rod.h`` (librod.so).  The library is built
 in-tree by ``paper_2605_13766_gb300.build.build()``; using the package without it raises.
 """
-from .binding import LIBRARY_PATH, RodError, RodSystem, exported_symbols, load_library  # noqa: F401
+from .binding import LIBRARY_PATH, RodError, RodSystem, Surrogate, exported_symbols, load_library  # noqa: F401
 
-__all__ = ["RodSystem", "RodError", "load_library", "exported_symbols", "LIBRARY_PATH"]
+__all__ = ["RodSystem", "Surrogate", "RodError", "load_library", "exported_symbols", "LIBRARY_PATH"]

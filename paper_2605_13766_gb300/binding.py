@@ -29,6 +29,15 @@ class RodError(RuntimeError):
         self.status = status
 
 
+class SurrogateStats(C.Structure):
+    """rod_surrogate_stats."""
+    _fields_ = [("surrogate_calls", C.c_int64), ("fallback_calls", C.c_int64), ("checks", C.c_int64),
+                ("max_err", C.c_double), ("last_err", C.c_double), ("rejected_err", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class RodSystemDesc(C.Structure):
     _fields_ = [
         ("n_rods", C.c_int32),
@@ -84,6 +93,19 @@ _SIGNATURES = {
     "rod_system_launch_count": ([_P, _P], C.c_int),
     "rod_contact_forces_noalloc": ([C.c_int32, _P, _P, _P, _P, C.c_double, C.c_double, C.c_double, _P, _P],
                                    C.c_int),
+    "rod_surrogate_create": ([C.c_int32, C.c_double, C.POINTER(C.c_void_p)], C.c_int),
+    "rod_surrogate_destroy": ([_P], C.c_int),
+    "rod_surrogate_num_params": ([], C.c_int64),
+    "rod_surrogate_set_params": ([_P, _P, C.c_int], C.c_int),
+    "rod_surrogate_get_params": ([_P, _P, C.c_int], C.c_int),
+    "rod_surrogate_set_scales": ([_P, _P, _P, _P], C.c_int),
+    "rod_surrogate_train_step": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int32, C.c_float, _P, _P], C.c_int),
+    "rod_surrogate_get_grad": ([_P, _P, C.c_int], C.c_int),
+    "rod_surrogate_forward": ([_P, _P, _P, _P, _P, _P, C.c_int32, _P, _P], C.c_int),
+    "rod_surrogate_raw_features": ([_P, _P, _P, _P, _P, _P, C.c_int32, _P, _P, _P], C.c_int),
+    "rod_surrogate_raw_targets": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int32, _P, _P], C.c_int),
+    "rod_surrogate_apply": ([_P, _P, C.c_int64], C.c_int),
+    "rod_surrogate_rollout": ([_P, _P, _P, _P, C.c_int32, C.c_int64, C.c_int32, C.c_double, _P], C.c_int),
     "rod_max_elements_per_rod": ([], C.c_int32),
     "rod_last_error": ([], C.c_char_p),
     "rod_version": ([], C.c_char_p),
@@ -353,6 +375,126 @@ class RodSystem:
         e, t = C.c_int32(), C.c_int32()
         _check(self.lib.rod_system_get_launch(self.handle, C.byref(e), C.byref(t)))
         return e.value, t.value
+
+
+class Surrogate:
+    """Handle on ``rod_surrogate``: the learned window-of-steps surrogate (BF16 tensor cores).
+
+    Features, outputs and the kinematic prior are described with the C ABI (include/rod.h)."""
+
+    N_FEATURES = 24
+    N_OUTPUTS = 15
+    POSITIONS = 51
+
+    def __init__(self, window_steps: int = 50, dt: float = 1e-5):
+        self.lib = load_library()
+        h = C.c_void_p()
+        _check(self.lib.rod_surrogate_create(int(window_steps), float(dt), C.byref(h)))
+        self.handle = h
+        self.window = int(window_steps)
+        self.dt = float(dt)
+        self.n_params = int(self.lib.rod_surrogate_num_params())
+        self.scales = None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.rod_surrogate_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        if isinstance(params, np.ndarray):
+            p = np.ascontiguousarray(params, dtype=np.float32)
+            if p.size != self.n_params:
+                raise ValueError(f"need {self.n_params} parameters, got {p.size}")
+            _check(self.lib.rod_surrogate_set_params(self.handle, p.ctypes.data, 0))
+        else:
+            p = params.detach().float().contiguous()
+            if p.numel() != self.n_params:
+                raise ValueError(f"need {self.n_params} parameters, got {p.numel()}")
+            _check(self.lib.rod_surrogate_set_params(self.handle, p.data_ptr(), 1))
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.n_params, dtype=np.float32)
+        _check(self.lib.rod_surrogate_get_params(self.handle, p.ctypes.data, 0))
+        return p
+
+    def get_grad(self) -> np.ndarray:
+        g = np.empty(self.n_params, dtype=np.float32)
+        _check(self.lib.rod_surrogate_get_grad(self.handle, g.ctypes.data, 0))
+        return g
+
+    def set_scales(self, in_shift, in_scale, out_scale):
+        sh = np.ascontiguousarray(in_shift, dtype=np.float64)
+        sc = np.ascontiguousarray(in_scale, dtype=np.float64)
+        o = np.ascontiguousarray(out_scale, dtype=np.float64)
+        if sh.size != self.N_FEATURES or sc.size != self.N_FEATURES or o.size != self.N_OUTPUTS:
+            raise ValueError("need 24 input shifts, 24 input scales and 15 output scales")
+        _check(self.lib.rod_surrogate_set_scales(self.handle, sh.ctypes.data, sc.ctypes.data, o.ctypes.data))
+        self.scales = (sh, sc, o)
+
+    def train_step(self, start, end, act, lr: float, stream=None):
+        """start/end: (x, v, Q, w) CUDA float64 tensors of nwin rods of 50 elements; act (3, nwin).
+        Returns the mean-square loss of the batch (before the update)."""
+        import torch
+        nwin = int(act.shape[1])
+        arrs = [a.contiguous() for a in list(start) + list(end) + [act]]
+        loss = C.c_float()
+        s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(self.lib.rod_surrogate_train_step(self.handle, *[a.data_ptr() for a in arrs], nwin, float(lr),
+                                                 C.byref(loss), s))
+        return loss.value
+
+    def raw_features(self, state, act, stream=None):
+        """Unscaled FP64 features (nwin, 24, 51) and their mask (int8, 1 where defined)."""
+        import torch
+        nwin = int(act.shape[1])
+        arrs = [a.contiguous() for a in list(state) + [act]]
+        out = torch.empty((nwin, self.N_FEATURES, self.POSITIONS), dtype=torch.float64, device="cuda")
+        mask = torch.empty((nwin, self.N_FEATURES, self.POSITIONS), dtype=torch.int8, device="cuda")
+        s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(self.lib.rod_surrogate_raw_features(self.handle, *[a.data_ptr() for a in arrs], nwin, out.data_ptr(),
+                                                   mask.data_ptr(), s))
+        return out, mask
+
+    def raw_targets(self, start, end, stream=None):
+        """Unscaled FP64 targets (nwin, 15, 51): change over the window minus the kinematic prior."""
+        import torch
+        nwin = int(start[0].shape[1]) // self.POSITIONS
+        arrs = [a.contiguous() for a in list(start) + list(end)]
+        out = torch.empty((nwin, self.N_OUTPUTS, self.POSITIONS), dtype=torch.float64, device="cuda")
+        s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(self.lib.rod_surrogate_raw_targets(self.handle, *[a.data_ptr() for a in arrs], nwin, out.data_ptr(), s))
+        return out
+
+    def forward(self, state, act, stream=None):
+        """Raw network outputs (nwin, 51, 16) float32 for the states (x, v, Q, w) of nwin rods."""
+        import torch
+        nwin = int(act.shape[1])
+        arrs = [a.contiguous() for a in list(state) + [act]]
+        out = torch.empty((nwin, self.POSITIONS, 16), dtype=torch.float32, device="cuda")
+        s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(self.lib.rod_surrogate_forward(self.handle, *[a.data_ptr() for a in arrs], nwin, out.data_ptr(), s))
+        torch.cuda.current_stream().synchronize()
+        return out
+
+    def apply(self, system, n_calls: int):
+        """Advance every rod of ``system`` (50 elements each, no contact) by n_calls windows."""
+        _check(self.lib.rod_surrogate_apply(self.handle, system.handle, int(n_calls)))
+
+    def rollout(self, system, shadow, sample_rods, n_calls: int, check_every: int, bound: float) -> dict:
+        """n_calls windows with a check of the sampled rods against ``shadow`` every check_every
+        calls and a plain-step redo of any segment whose sampled tip error exceeds ``bound``."""
+        idx = np.ascontiguousarray(sample_rods, dtype=np.int32)
+        st = SurrogateStats()
+        _check(self.lib.rod_surrogate_rollout(self.handle, system.handle, shadow.handle, idx.ctypes.data, int(idx.size),
+                                              int(n_calls), int(check_every), float(bound), C.byref(st)))
+        return st.as_dict()
 
 
 def contact_forces_noalloc(node_off, radius, x, v, k: float, c: float, cell_size: float, f, stream=None):

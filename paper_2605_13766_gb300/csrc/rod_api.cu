@@ -21,6 +21,7 @@
 #include "rod_adjoint.h"
 #include "rod_contact.h"
 #include "rod_internal.h"
+#include "rod_sysview.h"
 
 using namespace rod;
 
@@ -1057,3 +1058,28 @@ rod_status rod_system_get_launch(const rod_system* s, int32_t* elems_per_block, 
 }
 
 }  // extern "C"
+
+namespace rod {
+rod_status system_view(rod_system* s, SysView* out) {
+  if (!s || !out) return fail(ROD_ERR_ARG, "null argument");
+  if (!s->state_set) return fail(ROD_ERR_STATE, "no state has been set");
+  int min_n = 1 << 30;
+  for (const auto& r : s->rods_h) min_n = std::min(min_n, r.n);
+  out->x = s->x.p;
+  out->v = s->v.p;
+  out->Q = s->Q.p;
+  out->w = s->w.p;
+  out->N = s->N;
+  out->E = s->E;
+  out->R = s->R;
+  out->max_n = s->max_n;
+  out->min_n = min_n;
+  out->rods = s->rods.p;
+  out->rest_len = s->rest_len.p;
+  out->contact = s->contact.enabled;
+  out->stream = s->stream;
+  out->t = &s->t;
+  return ROD_OK;
+}
+}  // namespace rod
+

@@ -1,0 +1,934 @@
+// rod_surrogate.cu -- learned per-rod surrogate of 50 fine steps (BF16 tensor cores, FP32
+// accumulation, FP64 state update) with its own training kernels.
+//
+// Network (fixed): four 1D convolutions along a rod of 50 elements (51 node positions),
+// kernel 5, zero padding, channels 32 (24 used) -> 64 -> 64 -> 64 -> 16 (15 used), SiLU
+// between layers.  Input features per node position (raw_feature): position relative to the
+// rod base, velocity, directors d1 and d2 and angular velocity of the element starting there,
+// the relative rotation of the two elements meeting at that Voronoi point, the element's edge
+// in its own frame (the last two carry the strains at a resolution BF16 keeps once shifted and
+// scaled) and three samples of the base couple over the window.  Output: for the same 15
+// state channels, the change over one window of fine steps minus a kinematic prior (x + T v,
+// directors turned by the Rodrigues exponential of -T w), divided by per-channel scales.  The
+// new state is prior + scale * output in FP64; the directors are re-orthonormalised
+// (Gram-Schmidt on d1, d2; d3 = d1 x d2) and a clamp is re-applied.
+//
+// Every convolution is an implicit GEMM on mma.sync.m16n8k16 (BF16 in, FP32 accumulate):
+//   forward:  out[o, j] = b[o] + sum_{t,c} W[o, t, c] in[c, j + t - 2]    (M = C_out, N = j, K = 5 C_in)
+//   input gradient: the same kernel with the tap-transposed weights and flipped taps
+//   weight gradient: dW[o, t, c] = sum_{windows, j} g[o, j] in[c, j + t - 2]  (split over windows)
+// Activations are stored [window][row][channel] with row = position + 2 (rows 0, 1 and
+// 53..63 are the zero padding), so a pair of consecutive channels is one 32-bit load.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "../../include/rod.h"
+#include "rod_contact.h"
+#include "rod_internal.h"
+
+namespace rod {
+namespace sur {
+
+constexpr int kPos = 51;     // node positions per rod
+constexpr int kRows = 64;    // padded rows (position + 2)
+constexpr int kTaps = 5;
+constexpr int kC0 = 32;      // input channels (17 used)
+constexpr int kC = 64;       // hidden channels
+constexpr int kCO = 16;      // output channels (15 used)
+constexpr int kFeat = 24;    // input features (see raw_feature)
+constexpr int kOut = 15;
+
+// parameter blocks (FP32 master copy): W1 [64][5*32], b1 [64], W2 [64][5*64], b2, W3, b3, W4 [16][5*64], b4 [16]
+constexpr int kW1 = kC * kTaps * kC0, kW2 = kC * kTaps * kC, kW3 = kC * kTaps * kC, kW4 = kCO * kTaps * kC;
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kW1, kOffW2 = kOffB1 + kC, kOffB2 = kOffW2 + kW2;
+constexpr int kOffW3 = kOffB2 + kC, kOffB3 = kOffW3 + kW3, kOffW4 = kOffB3 + kC, kOffB4 = kOffW4 + kW4;
+constexpr int kNumParams = kOffB4 + kCO;
+
+__device__ __forceinline__ float silu(float x) { return x / (1.0f + __expf(-x)); }
+__device__ __forceinline__ float dsilu(float x) {
+  const float s = 1.0f / (1.0f + __expf(-x));
+  return s * (1.0f + x * (1.0f - s));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return static_cast<uint32_t>(__bfloat16_as_ushort(lo)) | (static_cast<uint32_t>(__bfloat16_as_ushort(hi)) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+enum Epi : int { EPI_HIDDEN = 0, EPI_OUTPUT = 1, EPI_DGRAD = 2 };
+
+// One thread block per window (rod); each warp takes (m-tile, n-tile) output tiles.
+//   in   [B][64][CIN] BF16         W  [COUT][5*CIN] BF16 (tap-major K index k = t*CIN + c)
+//   EPI_HIDDEN: out BF16 [B][64][COUT] = SiLU(acc + bias), pre FP32 [B][64][COUT] (optional)
+//   EPI_OUTPUT: outf FP32 [B][51][COUT] = acc + bias
+//   EPI_DGRAD:  out BF16 [B][64][COUT] = acc * SiLU'(pre_lo) (pre_lo: the lower layer's pre-activation)
+template <int CIN, int COUT, int EPI, bool FLIP>
+__global__ void __launch_bounds__(128) conv_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ W,
+                                                   const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
+                                                   float* __restrict__ outf, float* __restrict__ pre,
+                                                   const float* __restrict__ pre_lo, int nwin) {
+  const int b = blockIdx.x;
+  if (b >= nwin) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tg = lane & 3;
+  constexpr int K = kTaps * CIN;
+  constexpr int MT = COUT / 16, NT = 7;  // positions 0..55
+  const __nv_bfloat16* inb = in + static_cast<int64_t>(b) * kRows * CIN;
+  for (int tile = warp; tile < MT * NT; tile += 4) {
+    const int m0 = (tile / NT) * 16, n0 = (tile % NT) * 8;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int j = n0 + g;  // this lane's B column (position)
+#pragma unroll 4
+    for (int kb = 0; kb < K / 16; ++kb) {
+      const int t = (kb * 16) / CIN, cb = (kb * 16) % CIN;
+      uint32_t af[4], bf[2];
+      const __nv_bfloat16* wr0 = W + (m0 + g) * K + kb * 16 + 2 * tg;
+      const __nv_bfloat16* wr1 = wr0 + 8 * K;
+      af[0] = __ldg(reinterpret_cast<const unsigned int*>(wr0));
+      af[1] = __ldg(reinterpret_cast<const unsigned int*>(wr1));
+      af[2] = __ldg(reinterpret_cast<const unsigned int*>(wr0 + 8));
+      af[3] = __ldg(reinterpret_cast<const unsigned int*>(wr1 + 8));
+      const int row = FLIP ? (j - t + 4) : (j + t);
+      const __nv_bfloat16* ir = inb + row * CIN + cb + 2 * tg;
+      bf[0] = __ldg(reinterpret_cast<const unsigned int*>(ir));
+      bf[1] = __ldg(reinterpret_cast<const unsigned int*>(ir + 8));
+      mma_bf16(acc, af, bf);
+    }
+    // epilogue: acc[0] (o = m0+g, j = n0+2tg), acc[1] (o, j+1), acc[2] (o+8, j), acc[3] (o+8, j+1)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int o = m0 + g + ((q & 2) ? 8 : 0);
+      const int jj = n0 + 2 * tg + (q & 1);
+      float v = acc[q];
+      if (EPI == EPI_OUTPUT) {
+        if (jj < kPos) outf[(static_cast<int64_t>(b) * kPos + jj) * COUT + o] = v + bias[o];
+      } else {
+        const int64_t idx = (static_cast<int64_t>(b) * kRows + jj + 2) * COUT + o;
+        float r = 0.f;
+        if (jj < kPos) {
+          if (EPI == EPI_HIDDEN) {
+            v += bias[o];
+            if (pre) pre[idx] = v;
+            r = silu(v);
+          } else {
+            r = v * dsilu(pre_lo[idx]);
+          }
+        }
+        out[idx] = __float2bfloat16_rn(r);
+      }
+    }
+  }
+}
+
+// dW[o][t*CIN + c] += sum_{windows in chunk, j} g[b][j+2][o] in[b][j+t][c]   (atomic FP32 per block)
+// grid.x: window chunks, grid.y: groups of 8 n-tiles (64 K columns); warp w owns m-tile w (COUT=64) or 0.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) wgrad_kernel(const __nv_bfloat16* __restrict__ gout, const __nv_bfloat16* __restrict__ in,
+                                                    float* __restrict__ dW, float* __restrict__ db, int nwin,
+                                                    int win_per_block) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tg = lane & 3;
+  constexpr int K = kTaps * CIN;
+  constexpr int MT = COUT / 16;
+  if (warp >= MT) return;
+  const int m0 = warp * 16;
+  const int nbase = blockIdx.y * 64;  // K columns handled by this block
+  float acc[8][4];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) acc[s][0] = acc[s][1] = acc[s][2] = acc[s][3] = 0.f;
+  float bsum0 = 0.f, bsum1 = 0.f;
+  const int w0 = blockIdx.x * win_per_block, w1 = min(nwin, w0 + win_per_block);
+  for (int b = w0; b < w1; ++b) {
+    const __nv_bfloat16* gb = gout + static_cast<int64_t>(b) * kRows * COUT;
+    const __nv_bfloat16* ib = in + static_cast<int64_t>(b) * kRows * CIN;
+    for (int jb = 0; jb < 64; jb += 16) {  // reduction over positions 0..63 (rows >= 53 are zero)
+      // A(o, j) = g[j + 2][o]: rows m0+g (+8), cols jb + 2tg (+1), (+8)
+      uint32_t af[4];
+      auto gval = [&](int o, int jj) -> __nv_bfloat16 {
+        return (jj + 2 < kRows) ? gb[(jj + 2) * COUT + o] : __float2bfloat16_rn(0.f);
+      };
+      af[0] = pack_bf16(gval(m0 + g, jb + 2 * tg), gval(m0 + g, jb + 2 * tg + 1));
+      af[1] = pack_bf16(gval(m0 + g + 8, jb + 2 * tg), gval(m0 + g + 8, jb + 2 * tg + 1));
+      af[2] = pack_bf16(gval(m0 + g, jb + 2 * tg + 8), gval(m0 + g, jb + 2 * tg + 9));
+      af[3] = pack_bf16(gval(m0 + g + 8, jb + 2 * tg + 8), gval(m0 + g + 8, jb + 2 * tg + 9));
+      if (blockIdx.y == 0) {
+        for (int q = 0; q < 2; ++q) {
+          const int jj = jb + 2 * tg + q;
+          bsum0 += __bfloat162float(gval(m0 + g, jj)) + __bfloat162float(gval(m0 + g, jj + 8));
+          bsum1 += __bfloat162float(gval(m0 + g + 8, jj)) + __bfloat162float(gval(m0 + g + 8, jj + 8));
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int ncol = nbase + s * 8 + g;  // K column = t*CIN + c
+        if (ncol >= K) continue;
+        const int t = ncol / CIN, c = ncol % CIN;
+        // B(j, n) = in[j + t][c] for j = jb + 2tg (+1), (+8, +9)
+        auto ival = [&](int jj) -> __nv_bfloat16 {
+          const int row = jj + t;
+          return row < kRows ? ib[row * CIN + c] : __float2bfloat16_rn(0.f);
+        };
+        uint32_t bf[2];
+        bf[0] = pack_bf16(ival(jb + 2 * tg), ival(jb + 2 * tg + 1));
+        bf[1] = pack_bf16(ival(jb + 2 * tg + 8), ival(jb + 2 * tg + 9));
+        mma_bf16(acc[s], af, bf);
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int nc = nbase + s * 8 + 2 * tg;
+    if (nc >= K) continue;
+    atomicAdd(dW + (m0 + g) * K + nc, acc[s][0]);
+    atomicAdd(dW + (m0 + g) * K + nc + 1, acc[s][1]);
+    atomicAdd(dW + (m0 + g + 8) * K + nc, acc[s][2]);
+    atomicAdd(dW + (m0 + g + 8) * K + nc + 1, acc[s][3]);
+  }
+  if (blockIdx.y == 0) {
+    // reduce the bias sums over the 4 lanes sharing a row
+    for (int o = 1; o < 4; o <<= 1) {
+      bsum0 += __shfl_xor_sync(0xffffffffu, bsum0, o);
+      bsum1 += __shfl_xor_sync(0xffffffffu, bsum1, o);
+    }
+    if (tg == 0) {
+      atomicAdd(db + m0 + g, bsum0);
+      atomicAdd(db + m0 + g + 8, bsum1);
+    }
+  }
+}
+
+// ---- features, targets, loss, state update, Adam
+
+struct WinState {          // a batch of rods of 50 elements in the system layout
+  const double* x;         // [3][N]
+  const double* v;
+  const double* Q;         // [9][E], Q[(3a + k) E + e] = component k of director a
+  const double* w;         // [3][E]
+  int64_t N, E;
+};
+
+struct Scales {
+  double in_shift[kFeat];  // feature = float(raw - shift) * scale (0 where a feature is undefined)
+  float in_scale[kFeat];
+  double out[kOut];        // state change = prior + out * network output
+  double T;                // window length in time (window steps x dt)
+};
+
+// Q_new = exp([-T w]x) Q (rows: directors): the director update of a constant angular velocity
+// w (local frame) held for the whole window, by the Rodrigues formula with (1 - cos th) written
+// as 2 sin^2(th / 2).
+__device__ __forceinline__ void rotate_directors(const double w[3], double T, const double Q[9], double out[9]) {
+  const double ph[3] = {-T * w[0], -T * w[1], -T * w[2]};
+  const double th = sqrt(ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2]);
+  double a = 1.0, b = 0.5;
+  if (th > 0.0) {
+    const double sh = sin(0.5 * th) / th;
+    a = sin(th) / th;
+    b = 2.0 * sh * sh;
+  }
+  const double K[9] = {0.0, -ph[2], ph[1], ph[2], 0.0, -ph[0], -ph[1], ph[0], 0.0};
+  double M[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double k2 = 0.0;
+      for (int l = 0; l < 3; ++l) k2 += K[3 * i + l] * K[3 * l + j];
+      M[3 * i + j] = (i == j ? 1.0 : 0.0) + a * K[3 * i + j] + b * k2;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) out[3 * i + k] = M[3 * i] * Q[k] + M[3 * i + 1] * Q[3 + k] + M[3 * i + 2] * Q[6 + k];
+}
+
+__device__ __forceinline__ void load_q(const double* Q, int64_t E, int64_t e, double q[9]) {
+#pragma unroll
+  for (int a = 0; a < 9; ++a) q[a] = Q[a * E + e];
+}
+
+// Raw feature c of window b at node position j; false where the feature is undefined.
+//   0..2  node position minus the base node        3..5  node velocity
+//   6..11 directors d1, d2 of element j            12..14 angular velocity of element j
+//   15..17 half the axial vector of R - R^T, R = Q_j Q_{j-1}^T (relative rotation of the two
+//          elements beside Voronoi point j; j = 1..49)
+//   18..20 edge of element j in its own frame, Q_j (x_{j+1} - x_j)
+//   21..23 base couple at the window's start, middle and end
+__device__ bool raw_feature(const WinState& S, const double* __restrict__ act, int nwin, int b, int j, int c, double* out) {
+  const int64_t node = static_cast<int64_t>(b) * kPos + j, node0 = static_cast<int64_t>(b) * kPos;
+  const int64_t el = static_cast<int64_t>(b) * (kPos - 1) + j;
+  const bool has_el = j < kPos - 1;
+  if (c < 3) { *out = S.x[c * S.N + node] - S.x[c * S.N + node0]; return true; }
+  if (c < 6) { *out = S.v[(c - 3) * S.N + node]; return true; }
+  if (c < 12) { if (!has_el) return false; *out = S.Q[(c - 6) * S.E + el]; return true; }
+  if (c < 15) { if (!has_el) return false; *out = S.w[(c - 12) * S.E + el]; return true; }
+  if (c < 18) {
+    if (j < 1 || !has_el) return false;
+    const int comp = c - 15;
+    const int ia = comp == 0 ? 2 : (comp == 1 ? 0 : 1), ib = comp == 0 ? 1 : (comp == 1 ? 2 : 0);
+    double rab = 0.0, rba = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      rab += S.Q[(3 * ia + k) * S.E + el] * S.Q[(3 * ib + k) * S.E + el - 1];
+      rba += S.Q[(3 * ib + k) * S.E + el] * S.Q[(3 * ia + k) * S.E + el - 1];
+    }
+    *out = 0.5 * (rab - rba);
+    return true;
+  }
+  if (c < 21) {
+    if (!has_el) return false;
+    const int a = c - 18;
+    double d = 0.0;
+    for (int k = 0; k < 3; ++k) d += S.Q[(3 * a + k) * S.E + el] * (S.x[k * S.N + node + 1] - S.x[k * S.N + node]);
+    *out = d;
+    return true;
+  }
+  *out = act[(c - 21) * nwin + b];
+  return true;
+}
+
+// features[b][row][c] (BF16), row = position + 2, channels 24..31 and padding rows zero
+__global__ void features_kernel(WinState S, const double* __restrict__ act, int nwin, Scales sc,
+                                __nv_bfloat16* __restrict__ feat) {
+  const int b = blockIdx.x;
+  if (b >= nwin) return;
+  for (int idx = threadIdx.x; idx < kRows * kC0; idx += blockDim.x) {
+    const int row = idx / kC0, c = idx % kC0;
+    const int j = row - 2;
+    float val = 0.f;
+    double d;
+    if (j >= 0 && j < kPos && c < kFeat && raw_feature(S, act, nwin, b, j, c, &d))
+      val = static_cast<float>(d - sc.in_shift[c]) * sc.in_scale[c];
+    feat[(static_cast<int64_t>(b) * kRows + row) * kC0 + c] = __float2bfloat16_rn(val);
+  }
+}
+
+// Training target channel c at node position j of window b (unscaled):
+//   0..2 x1 - x0 - T v0     3..5 v1 - v0     6..11 rows d1, d2 of Q1 - exp([-T w0]x) Q0     12..14 w1 - w0
+// (element channels are zero at j = 50)
+__device__ double target_value(const WinState& A, const WinState& B, double T, int b, int j, int c) {
+  const int64_t node = static_cast<int64_t>(b) * kPos + j, el = static_cast<int64_t>(b) * (kPos - 1) + j;
+  const bool has_el = j < kPos - 1;
+  if (c < 3) return B.x[c * A.N + node] - A.x[c * A.N + node] - T * A.v[c * A.N + node];
+  if (c < 6) return B.v[(c - 3) * A.N + node] - A.v[(c - 3) * A.N + node];
+  if (!has_el) return 0.0;
+  if (c < 12) {
+    double q0[9], qp[9];
+    const double w0[3] = {A.w[el], A.w[A.E + el], A.w[2 * A.E + el]};
+    load_q(A.Q, A.E, el, q0);
+    rotate_directors(w0, T, q0, qp);
+    return B.Q[(c - 6) * A.E + el] - qp[c - 6];
+  }
+  return B.w[(c - 12) * A.E + el] - A.w[(c - 12) * A.E + el];
+}
+
+// scaled FP32 training targets [b][j][16]
+__global__ void targets_kernel(WinState A, WinState B, int nwin, Scales sc, float* __restrict__ tgt) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= static_cast<int64_t>(nwin) * kPos * kCO) return;
+  const int c = i % kCO;
+  const int64_t bj = i / kCO;
+  const int b = static_cast<int>(bj / kPos), j = static_cast<int>(bj % kPos);
+  tgt[i] = (c < kOut) ? static_cast<float>(target_value(A, B, sc.T, b, j, c) / sc.out[c]) : 0.f;
+}
+
+// unscaled FP64 features [b][c][j] (zero where undefined) and mask (1 where defined)
+__global__ void raw_features_kernel(WinState S, const double* __restrict__ act, int nwin, double* __restrict__ out,
+                                    int8_t* __restrict__ mask) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= static_cast<int64_t>(nwin) * kFeat * kPos) return;
+  const int j = static_cast<int>(i % kPos);
+  const int c = static_cast<int>((i / kPos) % kFeat);
+  const int b = static_cast<int>(i / (static_cast<int64_t>(kPos) * kFeat));
+  double d = 0.0;
+  const bool ok = raw_feature(S, act, nwin, b, j, c, &d);
+  out[i] = ok ? d : 0.0;
+  if (mask) mask[i] = ok ? 1 : 0;
+}
+
+// unscaled FP64 targets [b][c][j]: state change minus the kinematic prior
+__global__ void raw_targets_kernel(WinState A, WinState B, int nwin, double T, double* __restrict__ out) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= static_cast<int64_t>(nwin) * kOut * kPos) return;
+  const int j = static_cast<int>(i % kPos);
+  const int c = static_cast<int>((i / kPos) % kOut);
+  const int b = static_cast<int>(i / (static_cast<int64_t>(kPos) * kOut));
+  out[i] = target_value(A, B, T, b, j, c);
+}
+
+// loss = mean (out - tgt)^2 over windows x positions x 15 channels; gradient to BF16 rows
+__global__ void loss_kernel(const float* __restrict__ out, const float* __restrict__ tgt, int nwin,
+                            __nv_bfloat16* __restrict__ gout, float* __restrict__ loss_sum, float inv_count) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int64_t total = static_cast<int64_t>(nwin) * kRows * kCO;
+  float local = 0.f;
+  if (i < total) {
+    const int c = i % kCO;
+    const int64_t brow = i / kCO;
+    const int b = static_cast<int>(brow / kRows), row = static_cast<int>(brow % kRows);
+    const int j = row - 2;
+    float gval = 0.f;
+    if (j >= 0 && j < kPos && c < kOut) {
+      const int64_t k = (static_cast<int64_t>(b) * kPos + j) * kCO + c;
+      const float r = out[k] - tgt[k];
+      local = r * r;
+      gval = 2.f * r * inv_count;
+    }
+    gout[i] = __float2bfloat16_rn(gval);
+  }
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31) == 0 && local != 0.f) atomicAdd(loss_sum, local * inv_count);
+}
+
+// state <- prior + scale * out (FP64); directors re-orthonormalised (Gram-Schmidt on d1, d2,
+// d3 = d1 x d2); a clamped rod keeps node 0 and element 0 as they are, at rest.
+__global__ void apply_kernel(double* x, double* v, double* Q, double* w, int64_t N, int64_t E, int nrods,
+                             const float* __restrict__ out, Scales sc, const RodConst* __restrict__ rods) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= static_cast<int64_t>(nrods) * kPos) return;
+  const int b = static_cast<int>(i / kPos), j = static_cast<int>(i % kPos);
+  const float* o = out + i * kCO;
+  const bool held = rods[b].clamp != 0 && j == 0;
+  if (!held) {
+    for (int c = 0; c < 3; ++c) {
+      const double v0 = v[c * N + i];
+      x[c * N + i] += sc.T * v0 + sc.out[c] * static_cast<double>(o[c]);
+      v[c * N + i] = v0 + sc.out[3 + c] * static_cast<double>(o[3 + c]);
+    }
+  } else {
+    for (int c = 0; c < 3; ++c) v[c * N + i] = 0.0;
+  }
+  if (j >= kPos - 1) return;
+  const int64_t e = static_cast<int64_t>(b) * (kPos - 1) + j;
+  if (held) {
+    for (int c = 0; c < 3; ++c) w[c * E + e] = 0.0;
+    return;
+  }
+  double q0[9], qp[9];
+  const double w0[3] = {w[e], w[E + e], w[2 * E + e]};
+  load_q(Q, E, e, q0);
+  rotate_directors(w0, sc.T, q0, qp);
+  double d1[3], d2[3];
+  for (int c = 0; c < 3; ++c) {
+    d1[c] = qp[c] + sc.out[6 + c] * static_cast<double>(o[6 + c]);
+    d2[c] = qp[3 + c] + sc.out[9 + c] * static_cast<double>(o[9 + c]);
+    w[c * E + e] = w0[c] + sc.out[12 + c] * static_cast<double>(o[12 + c]);
+  }
+  const double n1 = 1.0 / sqrt(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
+  for (int c = 0; c < 3; ++c) d1[c] *= n1;
+  const double p = d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2];
+  for (int c = 0; c < 3; ++c) d2[c] -= p * d1[c];
+  const double n2 = 1.0 / sqrt(d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2]);
+  for (int c = 0; c < 3; ++c) d2[c] *= n2;
+  const double d3[3] = {d1[1] * d2[2] - d1[2] * d2[1], d1[2] * d2[0] - d1[0] * d2[2], d1[0] * d2[1] - d1[1] * d2[0]};
+  for (int c = 0; c < 3; ++c) {
+    Q[c * E + e] = d1[c];
+    Q[(3 + c) * E + e] = d2[c];
+    Q[(6 + c) * E + e] = d3[c];
+  }
+}
+
+// base couple A sin(omega t + phi) of every rod at t, t + T/2 and t + T
+__global__ void actuation_kernel(const RodConst* __restrict__ rods, int nrods, double t, double T, double* __restrict__ act) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrods) return;
+  for (int k = 0; k < 3; ++k) {
+    const double tk = t + 0.5 * k * T;
+    act[k * nrods + r] = rods[r].act_amp * sin(rods[r].act_omega * tk + rods[r].act_phase);
+  }
+}
+
+// max over sampled rods of |x_tip - x_tip(reference)| / L (L = sum of rest lengths); a
+// non-finite distance counts as infinite.  err_bits: the maximum as the bit pattern of a
+// non-negative double (monotone as an integer), cleared by the caller.
+__global__ void tip_error_kernel(const double* __restrict__ x, int64_t N, const double* __restrict__ xref, int64_t Nref,
+                                 const int32_t* __restrict__ sample, int n_sample, const double* __restrict__ rest_len,
+                                 unsigned long long* err_bits) {
+  double worst = 0.0;
+  for (int i = threadIdx.x; i < n_sample; i += blockDim.x) {
+    const int64_t r = sample[i];
+    const int64_t tip = r * kPos + kPos - 1, tip_ref = static_cast<int64_t>(i) * kPos + kPos - 1;
+    double d2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      const double d = x[c * N + tip] - xref[c * Nref + tip_ref];
+      d2 += d * d;
+    }
+    double L = 0.0;
+    for (int k = 0; k < kPos - 1; ++k) L += rest_len[r * (kPos - 1) + k];
+    double e = sqrt(d2) / L;
+    if (!(e <= 1e300)) e = INFINITY;
+    worst = fmax(worst, e);
+  }
+  for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(err_bits, static_cast<unsigned long long>(__double_as_longlong(worst)));
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ gr, float* __restrict__ m, float* __restrict__ v,
+                            int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = gr[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// BF16 copies of the FP32 master weights: forward layout [COUT][t*CIN + c] and the tap-transposed
+// layout used by the input gradient, Wt[c][t*COUT + o] = W[o][t*CIN + c]
+__global__ void cast_weights_kernel(const float* __restrict__ master, __nv_bfloat16* __restrict__ wf,
+                                    __nv_bfloat16* __restrict__ wt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int offs[4] = {kOffW1, kOffW2, kOffW3, kOffW4};
+  const int cin[4] = {kC0, kC, kC, kC};
+  const int cout[4] = {kC, kC, kC, kCO};
+  int base = 0;
+  for (int l = 0; l < 4; ++l) {
+    const int n = cout[l] * kTaps * cin[l];
+    if (i >= base && i < base + n) {
+      const int k = i - base;
+      const int o = k / (kTaps * cin[l]), rem = k % (kTaps * cin[l]);
+      const int t = rem / cin[l], c = rem % cin[l];
+      const __nv_bfloat16 vb = __float2bfloat16_rn(master[offs[l] + k]);
+      wf[base + k] = vb;
+      wt[base + (c * kTaps * cout[l] + t * cout[l] + o)] = vb;
+    }
+    base += n;
+  }
+}
+
+}  // namespace sur
+}  // namespace rod
+
+// ------------------------------------------------------------------------------ host side
+
+using namespace rod;
+using namespace rod::sur;
+
+struct rod_surrogate {
+  int window = 50;
+  double dt = 0.0;
+  Scales sc{};
+  float *master = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+  __nv_bfloat16 *wf = nullptr, *wt = nullptr;   // BF16 forward / transposed weights
+  int64_t adam_t = 0;
+  // per-batch buffers (grown on demand)
+  int cap = 0;
+  __nv_bfloat16 *a0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr;  // input, hidden 1..3
+  float *p1 = nullptr, *p2 = nullptr, *p3 = nullptr;                        // pre-activations
+  float *outf = nullptr, *tgt = nullptr, *loss = nullptr;
+  __nv_bfloat16 *g4 = nullptr, *g3 = nullptr, *g2 = nullptr, *g1 = nullptr;
+  double* act = nullptr;
+  bool weights_dirty = true;
+  // rollout: checkpoint of the system state, sampled rods, error word
+  double* ck = nullptr;
+  int64_t ck_cap = 0;
+  int32_t* sample = nullptr;
+  int sample_cap = 0;
+  unsigned long long* err_dev = nullptr;
+  unsigned long long* err_host = nullptr;  // pinned
+};
+
+namespace {
+
+int64_t bf_off(int layer) {  // offset of layer l's weights in the BF16 weight arrays
+  const int64_t n[4] = {kW1, kW2, kW3, kW4};
+  int64_t o = 0;
+  for (int l = 0; l < layer; ++l) o += n[l];
+  return o;
+}
+constexpr int64_t kBfTotal = kW1 + kW2 + kW3 + kW4;
+
+cudaError_t grow(rod_surrogate* s, int nwin) {
+  if (nwin <= s->cap) return cudaSuccess;
+  void* ptrs[] = {s->a0, s->a1, s->a2, s->a3, s->p1, s->p2, s->p3, s->outf, s->tgt, s->g4, s->g3, s->g2, s->g1, s->act};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  s->cap = 0;
+  const size_t rows = static_cast<size_t>(nwin) * kRows;
+  cudaError_t e;
+  if ((e = cudaMalloc(&s->a0, rows * kC0 * 2)) || (e = cudaMalloc(&s->a1, rows * kC * 2)) ||
+      (e = cudaMalloc(&s->a2, rows * kC * 2)) || (e = cudaMalloc(&s->a3, rows * kC * 2)) ||
+      (e = cudaMalloc(&s->p1, rows * kC * 4)) || (e = cudaMalloc(&s->p2, rows * kC * 4)) ||
+      (e = cudaMalloc(&s->p3, rows * kC * 4)) || (e = cudaMalloc(&s->outf, static_cast<size_t>(nwin) * kPos * kCO * 4)) ||
+      (e = cudaMalloc(&s->tgt, static_cast<size_t>(nwin) * kPos * kCO * 4)) || (e = cudaMalloc(&s->g4, rows * kCO * 2)) ||
+      (e = cudaMalloc(&s->g3, rows * kC * 2)) || (e = cudaMalloc(&s->g2, rows * kC * 2)) ||
+      (e = cudaMalloc(&s->g1, rows * kC * 2)) || (e = cudaMalloc(&s->act, static_cast<size_t>(nwin) * 3 * 8)))
+    return e;
+  // the kernels write rows 2..57 only: the padding rows must start (and stay) zero
+  if ((e = cudaMemset(s->a1, 0, rows * kC * 2)) || (e = cudaMemset(s->a2, 0, rows * kC * 2)) ||
+      (e = cudaMemset(s->a3, 0, rows * kC * 2)) || (e = cudaMemset(s->g3, 0, rows * kC * 2)) ||
+      (e = cudaMemset(s->g2, 0, rows * kC * 2)) || (e = cudaMemset(s->g1, 0, rows * kC * 2)) ||
+      (e = cudaMemset(s->p1, 0, rows * kC * 4)) || (e = cudaMemset(s->p2, 0, rows * kC * 4)) ||
+      (e = cudaMemset(s->p3, 0, rows * kC * 4)))
+    return e;
+  s->cap = nwin;
+  return cudaSuccess;
+}
+
+cudaError_t refresh_weights(rod_surrogate* s, cudaStream_t st) {
+  if (!s->weights_dirty) return cudaSuccess;
+  cast_weights_kernel<<<(kBfTotal + 255) / 256, 256, 0, st>>>(s->master, s->wf, s->wt);
+  s->weights_dirty = false;
+  return cudaGetLastError();
+}
+
+// forward through the four layers; features must be in a0; keeps pre-activations when train
+cudaError_t forward(rod_surrogate* s, int nwin, bool train, cudaStream_t st) {
+  const float* m = s->master;
+  conv_kernel<kC0, kC, EPI_HIDDEN, false><<<nwin, 128, 0, st>>>(s->a0, s->wf + bf_off(0), m + kOffB1, s->a1, nullptr,
+                                                                 train ? s->p1 : nullptr, nullptr, nwin);
+  conv_kernel<kC, kC, EPI_HIDDEN, false><<<nwin, 128, 0, st>>>(s->a1, s->wf + bf_off(1), m + kOffB2, s->a2, nullptr,
+                                                                train ? s->p2 : nullptr, nullptr, nwin);
+  conv_kernel<kC, kC, EPI_HIDDEN, false><<<nwin, 128, 0, st>>>(s->a2, s->wf + bf_off(2), m + kOffB3, s->a3, nullptr,
+                                                                train ? s->p3 : nullptr, nullptr, nwin);
+  conv_kernel<kC, kCO, EPI_OUTPUT, false><<<nwin, 128, 0, st>>>(s->a3, s->wf + bf_off(3), m + kOffB4, nullptr, s->outf,
+                                                                 nullptr, nullptr, nwin);
+  return cudaGetLastError();
+}
+
+// gradients of the mean-square loss (outf vs tgt) into s->grad (overwritten)
+cudaError_t backward(rod_surrogate* s, int nwin, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(s->grad, 0, kNumParams * 4, st))) return e;
+  if ((e = cudaMemsetAsync(s->loss, 0, 4, st))) return e;
+  const int64_t total = static_cast<int64_t>(nwin) * kRows * kCO;
+  const float inv_count = 1.0f / (static_cast<float>(nwin) * kPos * kOut);
+  loss_kernel<<<(total + 255) / 256, 256, 0, st>>>(s->outf, s->tgt, nwin, s->g4, s->loss, inv_count);
+  const int wpb = 16;
+  const int gx = (nwin + wpb - 1) / wpb;
+  float* gr = s->grad;
+  // layer 4: dW4, db4; input gradient to layer-3 activations (times SiLU'(p3))
+  wgrad_kernel<kC, kCO><<<dim3(gx, (kTaps * kC + 63) / 64), 128, 0, st>>>(s->g4, s->a3, gr + kOffW4, gr + kOffB4, nwin, wpb);
+  conv_kernel<kCO, kC, EPI_DGRAD, true><<<nwin, 128, 0, st>>>(s->g4, s->wt + bf_off(3), nullptr, s->g3, nullptr, nullptr,
+                                                               s->p3, nwin);
+  wgrad_kernel<kC, kC><<<dim3(gx, (kTaps * kC + 63) / 64), 128, 0, st>>>(s->g3, s->a2, gr + kOffW3, gr + kOffB3, nwin, wpb);
+  conv_kernel<kC, kC, EPI_DGRAD, true><<<nwin, 128, 0, st>>>(s->g3, s->wt + bf_off(2), nullptr, s->g2, nullptr, nullptr,
+                                                              s->p2, nwin);
+  wgrad_kernel<kC, kC><<<dim3(gx, (kTaps * kC + 63) / 64), 128, 0, st>>>(s->g2, s->a1, gr + kOffW2, gr + kOffB2, nwin, wpb);
+  conv_kernel<kC, kC, EPI_DGRAD, true><<<nwin, 128, 0, st>>>(s->g2, s->wt + bf_off(1), nullptr, s->g1, nullptr, nullptr,
+                                                              s->p1, nwin);
+  wgrad_kernel<kC0, kC><<<dim3(gx, (kTaps * kC0 + 63) / 64), 128, 0, st>>>(s->g1, s->a0, gr + kOffW1, gr + kOffB1, nwin, wpb);
+  return cudaGetLastError();
+}
+
+WinState win_state(const double* x, const double* v, const double* Q, const double* w, int nwin) {
+  WinState S;
+  S.x = x;
+  S.v = v;
+  S.Q = Q;
+  S.w = w;
+  S.N = static_cast<int64_t>(nwin) * kPos;
+  S.E = static_cast<int64_t>(nwin) * (kPos - 1);
+  return S;
+}
+
+}  // namespace
+
+// accessors used by rod_api.cu to reach a system's state and constants
+#include "rod_sysview.h"
+
+namespace {
+
+rod_status check_system(rod_surrogate* s, rod_system* sys, SysView* V, const char* who) {
+  rod_status rs = system_view(sys, V);
+  if (rs != ROD_OK) return rs;
+  if (V->max_n != kPos - 1 || V->min_n != kPos - 1)
+    return internal_fail(ROD_ERR_ARG, who, "every rod must have 50 elements");
+  if (V->contact) return internal_fail(ROD_ERR_ARG, who, "the surrogate advances rods without contact only");
+  cudaError_t e;
+  if ((e = grow(s, V->R)) || (e = refresh_weights(s, V->stream))) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
+  return ROD_OK;
+}
+
+// n_calls network windows on the system's stream (no synchronisation)
+cudaError_t apply_calls(rod_surrogate* s, const SysView& V, int64_t n_calls) {
+  const WinState S = win_state(V.x, V.v, V.Q, V.w, V.R);
+  for (int64_t k = 0; k < n_calls; ++k) {
+    actuation_kernel<<<(V.R + 127) / 128, 128, 0, V.stream>>>(V.rods, V.R, *V.t, s->sc.T, s->act);
+    features_kernel<<<V.R, 256, 0, V.stream>>>(S, s->act, V.R, s->sc, s->a0);
+    cudaError_t e = forward(s, V.R, false, V.stream);
+    if (e != cudaSuccess) return e;
+    apply_kernel<<<(V.R * kPos + 255) / 256, 256, 0, V.stream>>>(V.x, V.v, V.Q, V.w, V.N, V.E, V.R, s->outf, s->sc,
+                                                                 V.rods);
+    *V.t += s->window * s->dt;
+  }
+  return cudaGetLastError();
+}
+
+// copy the system state to (to_ck = true) or from the checkpoint buffer on the system's stream
+cudaError_t checkpoint(rod_surrogate* s, const SysView& V, bool to_ck) {
+  const int64_t n = 6 * V.N + 12 * V.E;
+  cudaError_t e;
+  if (n > s->ck_cap) {
+    if (s->ck) cudaFree(s->ck);
+    s->ck = nullptr;
+    s->ck_cap = 0;
+    if ((e = cudaMalloc(&s->ck, n * 8))) return e;
+    s->ck_cap = n;
+  }
+  double* parts[4] = {V.x, V.v, V.Q, V.w};
+  const int64_t sizes[4] = {3 * V.N, 3 * V.N, 9 * V.E, 3 * V.E};
+  int64_t off = 0;
+  for (int k = 0; k < 4; ++k) {
+    double* ck = s->ck + off;
+    e = to_ck ? cudaMemcpyAsync(ck, parts[k], sizes[k] * 8, cudaMemcpyDeviceToDevice, V.stream)
+              : cudaMemcpyAsync(parts[k], ck, sizes[k] * 8, cudaMemcpyDeviceToDevice, V.stream);
+    if (e != cudaSuccess) return e;
+    off += sizes[k];
+  }
+  return cudaSuccess;
+}
+
+// max relative tip error of the sampled rods of V against the rods of Ref (same order)
+cudaError_t tip_error(rod_surrogate* s, const SysView& V, const SysView& Ref, int n_sample, double* out) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(s->err_dev, 0, sizeof(unsigned long long), V.stream))) return e;
+  tip_error_kernel<<<1, 256, 0, V.stream>>>(V.x, V.N, Ref.x, Ref.N, s->sample, n_sample, V.rest_len, s->err_dev);
+  if ((e = cudaMemcpyAsync(s->err_host, s->err_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost, V.stream)) ||
+      (e = cudaStreamSynchronize(V.stream)))
+    return e;
+  uint64_t bits = *s->err_host;
+  std::memcpy(out, &bits, 8);
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t rod_surrogate_num_params(void) { return kNumParams; }
+
+rod_status rod_surrogate_create(int32_t window_steps, double dt, rod_surrogate** out) {
+  if (!out || window_steps < 1 || !(dt > 0) || !std::isfinite(dt))
+    return internal_fail(ROD_ERR_ARG, "rod_surrogate_create: bad argument", "");
+  rod_surrogate* s = new rod_surrogate();
+  s->window = window_steps;
+  s->dt = dt;
+  s->sc.T = window_steps * dt;
+  for (int c = 0; c < kFeat; ++c) {
+    s->sc.in_shift[c] = 0.0;
+    s->sc.in_scale[c] = 1.0f;
+  }
+  for (int c = 0; c < kOut; ++c) s->sc.out[c] = 1.0;
+  cudaError_t e;
+  if ((e = cudaMalloc(&s->master, kNumParams * 4)) || (e = cudaMalloc(&s->grad, kNumParams * 4)) ||
+      (e = cudaMalloc(&s->adam_m, kNumParams * 4)) || (e = cudaMalloc(&s->adam_v, kNumParams * 4)) ||
+      (e = cudaMalloc(&s->wf, kBfTotal * 2)) || (e = cudaMalloc(&s->wt, kBfTotal * 2)) ||
+      (e = cudaMalloc(&s->loss, 4)) || (e = cudaMalloc(&s->err_dev, 8)) ||
+      (e = cudaMallocHost(&s->err_host, 8)) || (e = cudaMemset(s->master, 0, kNumParams * 4)) ||
+      (e = cudaMemset(s->grad, 0, kNumParams * 4)) || (e = cudaMemset(s->adam_m, 0, kNumParams * 4)) ||
+      (e = cudaMemset(s->adam_v, 0, kNumParams * 4))) {
+    rod_surrogate_destroy(s);
+    return internal_fail(ROD_ERR_CUDA, "rod_surrogate_create", cudaGetErrorString(e));
+  }
+  *out = s;
+  return ROD_OK;
+}
+
+rod_status rod_surrogate_destroy(rod_surrogate* s) {
+  if (!s) return ROD_OK;
+  void* ptrs[] = {s->master, s->grad, s->adam_m, s->adam_v, s->wf, s->wt, s->loss, s->a0, s->a1, s->a2, s->a3,
+                  s->p1, s->p2, s->p3, s->outf, s->tgt, s->g4, s->g3, s->g2, s->g1, s->act, s->ck, s->sample,
+                  s->err_dev};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (s->err_host) cudaFreeHost(s->err_host);
+  delete s;
+  return ROD_OK;
+}
+
+rod_status rod_surrogate_set_params(rod_surrogate* s, const float* params, int on_device) {
+  if (!s || !params) return internal_fail(ROD_ERR_ARG, "rod_surrogate_set_params: null argument", "");
+  cudaError_t e = cudaMemcpy(s->master, params, kNumParams * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(s->adam_m, 0, kNumParams * 4);
+  if (e == cudaSuccess) e = cudaMemset(s->adam_v, 0, kNumParams * 4);
+  if (e != cudaSuccess) return internal_fail(ROD_ERR_CUDA, "rod_surrogate_set_params", cudaGetErrorString(e));
+  s->adam_t = 0;
+  s->weights_dirty = true;
+  return ROD_OK;
+}
+
+rod_status rod_surrogate_get_params(rod_surrogate* s, float* params, int on_device) {
+  if (!s || !params) return internal_fail(ROD_ERR_ARG, "rod_surrogate_get_params: null argument", "");
+  cudaError_t e = cudaMemcpy(params, s->master, kNumParams * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return internal_fail(ROD_ERR_CUDA, "rod_surrogate_get_params", cudaGetErrorString(e));
+  return ROD_OK;
+}
+
+rod_status rod_surrogate_set_scales(rod_surrogate* s, const double* in_shift, const double* in_scale,
+                                    const double* out_scale) {
+  if (!s || !in_shift || !in_scale || !out_scale)
+    return internal_fail(ROD_ERR_ARG, "rod_surrogate_set_scales: null argument", "");
+  for (int c = 0; c < kFeat; ++c)
+    if (!std::isfinite(in_shift[c]) || !std::isfinite(in_scale[c]))
+      return internal_fail(ROD_ERR_ARG, "rod_surrogate_set_scales: non-finite input scale", "");
+  for (int c = 0; c < kOut; ++c)
+    if (!(out_scale[c] > 0) || !std::isfinite(out_scale[c]))
+      return internal_fail(ROD_ERR_ARG, "rod_surrogate_set_scales: output scales must be positive", "");
+  for (int c = 0; c < kFeat; ++c) {
+    s->sc.in_shift[c] = in_shift[c];
+    s->sc.in_scale[c] = static_cast<float>(in_scale[c]);
+  }
+  for (int c = 0; c < kOut; ++c) s->sc.out[c] = out_scale[c];
+  return ROD_OK;
+}
+
+rod_status rod_surrogate_train_step(rod_surrogate* s, const double* x0, const double* v0, const double* Q0,
+                                    const double* w0, const double* x1, const double* v1, const double* Q1,
+                                    const double* w1, const double* act, int32_t nwin, float lr, float* loss_out,
+                                    void* cuda_stream) {
+  if (!s || !x0 || !v0 || !Q0 || !w0 || !x1 || !v1 || !Q1 || !w1 || !act || nwin < 1 || !std::isfinite(lr))
+    return internal_fail(ROD_ERR_ARG, "rod_surrogate_train_step: bad argument", "");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e;
+  if ((e = grow(s, nwin)) || (e = refresh_weights(s, st)))
+    return internal_fail(ROD_ERR_CUDA, "rod_surrogate_train_step", cudaGetErrorString(e));
+  const WinState A = win_state(x0, v0, Q0, w0, nwin), B = win_state(x1, v1, Q1, w1, nwin);
+  features_kernel<<<nwin, 256, 0, st>>>(A, act, nwin, s->sc, s->a0);
+  targets_kernel<<<(static_cast<int64_t>(nwin) * kPos * kCO + 255) / 256, 256, 0, st>>>(A, B, nwin, s->sc, s->tgt);
+  if ((e = forward(s, nwin, true, st)) || (e = backward(s, nwin, st)))
+    return internal_fail(ROD_ERR_CUDA, "rod_surrogate_train_step", cudaGetErrorString(e));
+  if (lr > 0.f) {
+    s->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)s->adam_t), c2 = 1.f - powf(b2, (float)s->adam_t);
+    adam_kernel<<<(kNumParams + 255) / 256, 256, 0, st>>>(s->master, s->grad, s->adam_m, s->adam_v, kNumParams, lr, b1,
+                                                          b2, 1e-8f, c1, c2);
+    s->weights_dirty = true;
+  }
+  if (loss_out) {
+    if ((e = cudaMemcpyAsync(loss_out, s->loss, 4, cudaMemcpyDeviceToHost, st)) || (e = cudaStreamSynchronize(st)))
+      return internal_fail(ROD_ERR_CUDA, "rod_surrogate_train_step", cudaGetErrorString(e));
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return internal_fail(ROD_ERR_CUDA, "rod_surrogate_train_step", cudaGetErrorString(e));
+  return ROD_OK;
+}
+
+rod_status rod_surrogate_get_grad(rod_surrogate* s, float* grad, int on_device) {
+  if (!s || !grad) return internal_fail(ROD_ERR_ARG, "rod_surrogate_get_grad: null argument", "");
+  cudaError_t e = cudaMemcpy(grad, s->grad, kNumParams * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return internal_fail(ROD_ERR_CUDA, "rod_surrogate_get_grad", cudaGetErrorString(e));
+  return ROD_OK;
+}
+
+rod_status rod_surrogate_forward(rod_surrogate* s, const double* x, const double* v, const double* Q, const double* w,
+                                 const double* act, int32_t nwin, float* out, void* cuda_stream) {
+  if (!s || !x || !v || !Q || !w || !act || !out || nwin < 1)
+    return internal_fail(ROD_ERR_ARG, "rod_surrogate_forward: bad argument", "");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e;
+  if ((e = grow(s, nwin)) || (e = refresh_weights(s, st)))
+    return internal_fail(ROD_ERR_CUDA, "rod_surrogate_forward", cudaGetErrorString(e));
+  features_kernel<<<nwin, 256, 0, st>>>(win_state(x, v, Q, w, nwin), act, nwin, s->sc, s->a0);
+  if ((e = forward(s, nwin, false, st))) return internal_fail(ROD_ERR_CUDA, "rod_surrogate_forward", cudaGetErrorString(e));
+  e = cudaMemcpyAsync(out, s->outf, static_cast<size_t>(nwin) * kPos * kCO * 4, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return internal_fail(ROD_ERR_CUDA, "rod_surrogate_forward", cudaGetErrorString(e));
+  return ROD_OK;
+}
+
+rod_status rod_surrogate_raw_features(rod_surrogate* s, const double* x, const double* v, const double* Q,
+                                      const double* w, const double* act, int32_t nwin, double* out, int8_t* mask,
+                                      void* cuda_stream) {
+  if (!s || !x || !v || !Q || !w || !act || !out || nwin < 1)
+    return internal_fail(ROD_ERR_ARG, "rod_surrogate_raw_features: bad argument", "");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int64_t n = static_cast<int64_t>(nwin) * kFeat * kPos;
+  raw_features_kernel<<<(n + 255) / 256, 256, 0, st>>>(win_state(x, v, Q, w, nwin), act, nwin, out, mask);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return internal_fail(ROD_ERR_CUDA, "rod_surrogate_raw_features", cudaGetErrorString(e));
+  return ROD_OK;
+}
+
+rod_status rod_surrogate_raw_targets(rod_surrogate* s, const double* x0, const double* v0, const double* Q0,
+                                     const double* w0, const double* x1, const double* v1, const double* Q1,
+                                     const double* w1, int32_t nwin, double* out, void* cuda_stream) {
+  if (!s || !x0 || !v0 || !Q0 || !w0 || !x1 || !v1 || !Q1 || !w1 || !out || nwin < 1)
+    return internal_fail(ROD_ERR_ARG, "rod_surrogate_raw_targets: bad argument", "");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int64_t n = static_cast<int64_t>(nwin) * kOut * kPos;
+  raw_targets_kernel<<<(n + 255) / 256, 256, 0, st>>>(win_state(x0, v0, Q0, w0, nwin), win_state(x1, v1, Q1, w1, nwin),
+                                                      nwin, s->sc.T, out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return internal_fail(ROD_ERR_CUDA, "rod_surrogate_raw_targets", cudaGetErrorString(e));
+  return ROD_OK;
+}
+
+rod_status rod_surrogate_apply(rod_surrogate* s, rod_system* sys, int64_t n_calls) {
+  if (!s || !sys || n_calls < 0) return internal_fail(ROD_ERR_ARG, "rod_surrogate_apply: bad argument", "");
+  SysView V;
+  rod_status rs = check_system(s, sys, &V, "rod_surrogate_apply");
+  if (rs != ROD_OK) return rs;
+  cudaError_t e = apply_calls(s, V, n_calls);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(V.stream);
+  if (e != cudaSuccess) return internal_fail(ROD_ERR_CUDA, "rod_surrogate_apply", cudaGetErrorString(e));
+  return ROD_OK;
+}
+
+rod_status rod_surrogate_rollout(rod_surrogate* s, rod_system* sys, rod_system* shadow, const int32_t* sample_rods,
+                                 int32_t n_sample, int64_t n_calls, int32_t check_every, double bound,
+                                 rod_surrogate_stats* stats) {
+  const char* who = "rod_surrogate_rollout";
+  if (!s || !sys || !shadow || sys == shadow || !sample_rods || n_sample < 1 || n_calls < 0 || check_every < 1 ||
+      !(bound > 0))
+    return internal_fail(ROD_ERR_ARG, who, "bad argument");
+  SysView V, H;
+  rod_status rs = check_system(s, sys, &V, who);
+  if (rs != ROD_OK) return rs;
+  if ((rs = system_view(shadow, &H)) != ROD_OK) return rs;
+  if (H.R != n_sample || H.max_n != kPos - 1 || H.min_n != kPos - 1 || H.contact)
+    return internal_fail(ROD_ERR_ARG, who, "the shadow system must hold the n_sample rods (50 elements, no contact)");
+  for (int i = 0; i < n_sample; ++i)
+    if (sample_rods[i] < 0 || sample_rods[i] >= V.R) return internal_fail(ROD_ERR_ARG, who, "sample index out of range");
+  if (std::fabs(*H.t - *V.t) > 1e-9 * std::max(1.0, std::fabs(*V.t)))
+    return internal_fail(ROD_ERR_STATE, who, "the shadow system is not at the system's time");
+  cudaError_t e;
+  if (n_sample > s->sample_cap) {
+    if (s->sample) cudaFree(s->sample);
+    s->sample = nullptr;
+    s->sample_cap = 0;
+    if ((e = cudaMalloc(&s->sample, n_sample * 4))) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
+    s->sample_cap = n_sample;
+  }
+  if ((e = cudaMemcpyAsync(s->sample, sample_rods, n_sample * 4, cudaMemcpyHostToDevice, V.stream)))
+    return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
+  rod_surrogate_stats st{};
+  for (int64_t done = 0; done < n_calls;) {
+    const int64_t k = std::min<int64_t>(check_every, n_calls - done);
+    const double t0 = *V.t;
+    // the shadow rods follow the plain method on their own stream while the network runs
+    if ((rs = rod_system_step_async(shadow, k * s->window, s->dt)) != ROD_OK) return rs;
+    if ((e = checkpoint(s, V, true)) || (e = apply_calls(s, V, k))) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
+    if ((rs = rod_system_sync(shadow)) != ROD_OK) return rs;
+    double err = 0.0;
+    if ((e = tip_error(s, V, H, n_sample, &err))) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
+    st.checks += 1;
+    if (err > bound) {
+      // fall back: this segment again with the plain step from the checkpoint
+      if ((e = checkpoint(s, V, false))) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
+      *V.t = t0;
+      if ((rs = rod_system_step(sys, k * s->window, s->dt)) != ROD_OK) return rs;
+      st.fallback_calls += k;
+      st.rejected_err = std::max(st.rejected_err, err);
+      if ((e = tip_error(s, V, H, n_sample, &err))) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
+    } else {
+      st.surrogate_calls += k;
+    }
+    st.max_err = std::max(st.max_err, err);
+    st.last_err = err;
+    done += k;
+  }
+  if (stats) *stats = st;
+  return ROD_OK;
+}
+
+}  // extern "C"

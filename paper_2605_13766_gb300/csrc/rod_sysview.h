@@ -1,0 +1,25 @@
+// rod_sysview.h -- access to a system's device state for the surrogate (internal to librod).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/rod.h"
+#include "rod_internal.h"
+
+namespace rod {
+
+struct SysView {
+  double *x, *v, *Q, *w;   // device state (component-major)
+  int64_t N, E;
+  int R, max_n, min_n;
+  const RodConst* rods;    // device per-rod constants
+  const double* rest_len;  // device rest length per element
+  bool contact;            // rod-rod contact enabled
+  cudaStream_t stream;
+  double* t;               // the system's simulated time (host)
+};
+
+rod_status system_view(rod_system* sys, SysView* out);
+
+}  // namespace rod

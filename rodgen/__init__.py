@@ -173,10 +173,12 @@ def cantilever(n: int = 100, length: float = 1.0, radius: float = 0.01, youngs: 
 def cilia_carpet(side: int = 64, n: int = 50, spacing: float = 0.05, length: float = 0.2,
                  radius: float = 0.005, youngs: float = 1e6, density: float = 1000.0,
                  period: float = 1.0, amp_factor: float = 0.5, gamma: float = 1.0,
-                 dt: float = 1e-5, n_steps: int = 10_000, seed: int = 1234) -> RodProblem:
+                 dt: float = 1e-5, n_steps: int = 10_000, seed: int = 1234,
+                 amp_range=None, period_range=None) -> RodProblem:
     """side x side upright clamped rods on a square grid, sinusoidal base couple about d1.
 
-    Amplitude A0 = amp_factor * E I / L, phases uniform in [0, 2 pi) from ``seed``."""
+    Amplitude A0 = amp_factor * E I / L, phases uniform in [0, 2 pi) from ``seed``; with
+    ``amp_range`` / ``period_range`` every rod draws its own amp_factor / period uniformly."""
     rng = np.random.default_rng(seed)
     R = side * side
     n_elem = np.full(R, n, dtype=np.int32)
@@ -186,14 +188,19 @@ def cilia_carpet(side: int = 64, n: int = 50, spacing: float = 0.05, length: flo
     d3 = np.tile([0.0, 0.0, 1.0], (R, 1))
     x, Q = _straight_rods(n_elem, rest_len, base, d3, np.tile([1.0, 0.0, 0.0], (R, 1)))
     I = np.pi * radius ** 4 / 4
-    amp = amp_factor * youngs * I / length
+    phase = rng.uniform(0.0, 2 * np.pi, R)
+    amp = _uniform(R, amp_factor * youngs * I / length)
+    per = _uniform(R, period)
+    if amp_range is not None:
+        amp = rng.uniform(amp_range[0], amp_range[1], R) * youngs * I / length
+    if period_range is not None:
+        per = rng.uniform(period_range[0], period_range[1], R)
     return RodProblem(
         name=f"cilia_carpet_{side}x{side}_n{n}", n_elem=n_elem, rest_len=rest_len,
         radius=_uniform(R, radius), youngs=_uniform(R, youngs), shear_mod=_uniform(R, youngs / 1.5),
         density=_uniform(R, density), x=x, v=np.zeros_like(x), Q=Q, w=np.zeros((3, R * n)),
         clamp_base=np.ones(R, dtype=np.int8), stokes_gamma=gamma,
-        act_amp=_uniform(R, amp), act_period=_uniform(R, period),
-        act_phase=rng.uniform(0.0, 2 * np.pi, R), dt=dt, n_steps=n_steps)
+        act_amp=amp, act_period=per, act_phase=phase, dt=dt, n_steps=n_steps)
 
 
 def random_packing(n_rods: int = 10_000, nmin: int = 16, nmax: int = 256, box: float = 1.0,

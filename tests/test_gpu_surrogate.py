@@ -1,0 +1,288 @@
+"""Learned window surrogate on the GPU: its kernels against the numpy reference of the same
+network (oracle side), then training, the checked rollout and the fallback.
+
+Parity cases use windows of the CPU oracle (3 x 3 carpet of 50-element rods, bent by 400 steps
+of actuation, then one window of 50 steps).  Tolerances:
+  * unscaled features and targets (FP64 on both sides): 1e-12 of each channel's magnitude;
+  * network output, loss and gradient: the reference rounds to BF16 at every point the kernels
+    store BF16, so what remains is FP32 versus FP64 accumulation and the rare BF16 rounding it
+    flips: 2e-3 (output, norm-wise), 2e-3 (loss), 2e-2 (gradient per layer, norm-wise);
+  * state update (FP64 on both sides, same network outputs): 1e-12.
+"""
+import json
+import os
+import time
+
+import numpy as np
+import pytest
+
+import rodgen
+from oracle import surrogate_ref as R
+from oracle.oracle import Oracle
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_13766_gb300 import build
+    build.build()
+
+
+def _record(name, obj):
+    out = os.path.join(ROOT, "gpurun_out")
+    if os.path.isdir(out):
+        with open(os.path.join(out, f"{name}.json"), "w") as f:
+            json.dump(obj, f, indent=1)
+
+
+@pytest.fixture(scope="module")
+def oracle_window():
+    p = rodgen.cilia_carpet(side=3, n=50, amp_range=(0.3, 0.8), period_range=(0.05, 0.2), seed=11)
+    dt, W = 1e-5, 50
+    o = Oracle(p)
+    s0 = o.step(*p.state(), dt=dt, n_steps=400)
+    t0 = 400 * dt
+    s1 = o.step(*s0, dt=dt, n_steps=W, t=t0)
+    return p, s0, s1, t0, dt, W
+
+
+def _act(p, t0, T):
+    from paper_2605_13766_gb300.surrogate import couple_samples
+    return couple_samples(p, t0, T)
+
+
+def _cuda(arrs):
+    import torch
+    return [torch.tensor(np.ascontiguousarray(a), device="cuda") for a in arrs]
+
+
+def _scales(F, M, D):
+    from paper_2605_13766_gb300.surrogate import scales_from_moments
+    mean = np.array([F[:, c][M[:, c]].mean() for c in range(R.N_FEAT)])
+    std = np.array([F[:, c][M[:, c]].std() for c in range(R.N_FEAT)])
+    rms = np.sqrt((D ** 2).mean(axis=(0, 2)))
+    return scales_from_moments(mean, std, rms)
+
+
+def test_raw_features_and_targets_match_reference(oracle_window):
+    from paper_2605_13766_gb300 import Surrogate
+    p, s0, s1, t0, dt, W = oracle_window
+    act = _act(p, t0, W * dt)
+    sur = Surrogate(W, dt)
+    Fg, Mg = sur.raw_features(_cuda(s0), _cuda([act])[0])
+    F, M = R.raw_features(*s0, act)
+    assert np.array_equal(Mg.cpu().numpy().astype(bool), M)
+    Fg = Fg.cpu().numpy()
+    for c in range(R.N_FEAT):
+        mag = max(np.abs(F[:, c]).max(), 1e-300)
+        assert np.abs(Fg[:, c] - F[:, c]).max() <= 1e-12 * mag, c
+    Dg = sur.raw_targets(_cuda(s0), _cuda(s1)).cpu().numpy()
+    D = R.raw_targets(s0, s1, W * dt)
+    # a target is a difference of state entries: beside 1e-12 of the channel, allow a few ulps of
+    # the entries it is taken from (a channel that is zero up to rounding is rounding on both sides)
+    operand = [np.abs(s1[0]).max()] * 3 + [np.abs(s1[1]).max()] * 3 + [1.0] * 6 + [np.abs(s1[3]).max()] * 3
+    for c in range(R.N_OUT):
+        mag = np.abs(D[:, c]).max()
+        assert np.abs(Dg[:, c] - D[:, c]).max() <= 1e-12 * mag + 4e-16 * operand[c], c
+
+
+def _setup_network(p, s0, s1, act, T, seed=3):
+    from paper_2605_13766_gb300 import Surrogate
+    from paper_2605_13766_gb300.surrogate import initial_params
+    F, M = R.raw_features(*s0, act)
+    D = R.raw_targets(s0, s1, T)
+    sh, sc, out = _scales(F, M, D)
+    params = initial_params(seed=seed, last_gain=1.0).astype(np.float64)
+    rng = np.random.default_rng(seed)
+    # non-zero biases so that their gradients and the bias path are exercised
+    for off, n in _bias_blocks():
+        params[off:off + n] = rng.normal(0, 0.1, n)
+    params = params.astype(np.float32)
+    sur = Surrogate(50, T / 50)
+    sur.set_params(params)
+    sur.set_scales(sh, sc, out)
+    return sur, params.astype(np.float64), (sh, sc, out)
+
+
+def _bias_blocks():
+    off, blocks = 0, []
+    for co, ci in R.SHAPES:
+        off += co * R.TAPS * ci
+        blocks.append((off, co))
+        off += co
+    return blocks
+
+
+def test_forward_matches_bf16_reference(oracle_window):
+    p, s0, s1, t0, dt, W = oracle_window
+    T = W * dt
+    act = _act(p, t0, T)
+    sur, params, (sh, sc, out_sc) = _setup_network(p, s0, s1, act, T)
+    got = sur.forward(_cuda(s0), _cuda([act])[0]).cpu().numpy()          # (nwin, 51, 16)
+    feats = R.features(*s0, act, sh, sc, emulate=True)
+    ref, _ = R.forward(params, feats, emulate=True)                       # (nwin, 16, 51)
+    ref64, _ = R.forward(params, R.features(*s0, act, sh, sc, emulate=False), emulate=False)
+    g = got.transpose(0, 2, 1)[:, :R.N_OUT]
+    r = ref[:, :R.N_OUT]
+    err = np.linalg.norm(g - r) / np.linalg.norm(r)
+    err64 = np.linalg.norm(g - ref64[:, :R.N_OUT]) / np.linalg.norm(r)
+    _record("surrogate_forward_parity", {"rel_err_vs_bf16_reference": err, "rel_err_vs_fp64_reference": err64})
+    assert err <= 2e-3, (err, err64)
+
+
+def test_train_step_loss_and_gradient_match_reference(oracle_window):
+    p, s0, s1, t0, dt, W = oracle_window
+    T = W * dt
+    act = _act(p, t0, T)
+    sur, params, (sh, sc, out_sc) = _setup_network(p, s0, s1, act, T)
+    loss = sur.train_step(_cuda(s0), _cuda(s1), _cuda([act])[0], lr=0.0)
+    grad = sur.get_grad().astype(np.float64)
+    feats = R.features(*s0, act, sh, sc, emulate=True)
+    tg = R.targets(s0, s1, out_sc, T)
+    loss_ref, grad_ref = R.loss_and_grad(params, feats, tg, emulate=True)
+    loss64, grad64 = R.loss_and_grad(params, R.features(*s0, act, sh, sc, emulate=False), tg, emulate=False)
+    rows = {"loss": loss, "loss_ref": loss_ref, "loss_fp64": loss64}
+    assert abs(loss - loss_ref) <= 2e-3 * loss_ref, rows
+    off = 0
+    for l, (co, ci) in enumerate(R.SHAPES):
+        for name, n in (("W", co * R.TAPS * ci), ("b", co)):
+            g, gr = grad[off:off + n], grad_ref[off:off + n]
+            e = float(np.linalg.norm(g - gr) / np.linalg.norm(gr))
+            rows[f"{name}{l + 1}_rel_err"] = e
+            rows[f"{name}{l + 1}_rel_err_fp64"] = float(np.linalg.norm(g - grad64[off:off + n]) / np.linalg.norm(gr))
+            assert e <= 2e-2, (l, name, rows)
+            off += n
+    _record("surrogate_gradient_parity", rows)
+    # and the optimiser moves the parameters against the gradient
+    before = sur.get_params()
+    sur.train_step(_cuda(s0), _cuda(s1), _cuda([act])[0], lr=1e-3)
+    step = sur.get_params() - before
+    assert float(np.dot(step, grad)) < 0
+
+
+def test_apply_matches_reference_update(oracle_window):
+    import torch
+    from paper_2605_13766_gb300 import RodSystem
+    p, s0, s1, t0, dt, W = oracle_window
+    T = W * dt
+    q = p.replace(act_amp=np.zeros(p.n_rods))          # couple features exactly zero on both sides
+    act = np.zeros((3, q.n_rods))
+    sur, params, (sh, sc, out_sc) = _setup_network(q, s0, s1, act, T)
+    out = sur.forward(_cuda(s0), _cuda([act])[0]).cpu().numpy()
+    ref = R.apply(s0, out, out_sc, T, q.clamp_base.astype(bool))
+    s = RodSystem(q)
+    s.set_state(*s0)
+    sur.apply(s, 1)
+    got = s.get_state()
+    for a, b in zip(got, ref):
+        assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1.0)
+    assert abs(s.time - T) < 1e-15
+
+
+# ---- training on windows of the plain GPU step, checked rollout, fallback
+
+
+def _carpet_eval(side=64):
+    return rodgen.cilia_carpet(side=side, n=50)
+
+
+@pytest.fixture(scope="module")
+def trained():
+    """A network trained on 2 x 10^5 windows of carpets with random amplitude, period and phase."""
+    from paper_2605_13766_gb300 import Surrogate
+    from paper_2605_13766_gb300 import surrogate as S
+    dt, W = 1e-5, 50
+    # 32 x 32 rods x 200 windows = 204,800 windows over the first 0.1 s from rest
+    p = rodgen.cilia_carpet(side=32, n=50, amp_range=(0.2, 0.8), period_range=(0.5, 2.0), seed=101)
+    data = [S.generate(p, n_windows=200, window=W, dt=dt)]
+    sur = Surrogate(W, dt)
+    S.fit_scales(sur, data)
+    sur.set_params(S.initial_params(seed=0))
+    t = time.time()
+    losses = S.train(sur, data, steps=int(os.environ.get("ROD_SURROGATE_TRAIN_STEPS", "3000")), lr=2e-3,
+                     lr_end=2e-5, seed=0)
+    info = {"train_s": time.time() - t, "loss_first": losses[0], "loss_last_100": float(np.mean(losses[-100:])),
+            "windows": sum(d.n_windows * d.n_rods for d in data)}
+    return sur, info
+
+
+def test_trained_surrogate_gain_over_plain_step(trained):
+    import torch
+    from paper_2605_13766_gb300 import RodSystem
+    from paper_2605_13766_gb300 import surrogate as S
+    sur, info = trained
+    p = _carpet_eval()
+    dt, W, n_calls = 1e-5, 50, 200
+    # plain GPU step over 10^4 fine steps
+    s = RodSystem(p)
+    s.set_state(*p.state())
+    s.step(W, dt)
+    s.set_state(*p.state())
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    s.step(n_calls * W, dt)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t
+    x_plain = s.get_state()[0]
+    # checked surrogate rollout (64 sampled rods, check every 10 calls)
+    ro = S.CheckedRollout(sur, p, n_sample=64, seed=1)
+    ro.run(1, check_every=1, bound=1.0)                   # warm-up call (allocations, weights)
+    ro.close()
+    ro = S.CheckedRollout(sur, p, n_sample=64, seed=1)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    stats = ro.run(n_calls, check_every=10, bound=5e-4)
+    torch.cuda.synchronize()
+    t_sur = time.perf_counter() - t
+    x_sur = ro.system.get_state()[0]
+    err = S.tip_error(p, x_sur, x_plain)
+    # the network alone (no checks), for the record
+    ro2 = S.CheckedRollout(sur, p, n_sample=1, seed=1)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    sur.apply(ro2.system, n_calls)
+    torch.cuda.synchronize()
+    t_net = time.perf_counter() - t
+    err_net = S.tip_error(p, ro2.system.get_state()[0], x_plain)
+    el_steps = p.n_elems * n_calls * W
+    rec = dict(info, plain_s=t_plain, rollout_s=t_sur, network_only_s=t_net, speedup=t_plain / t_sur,
+               speedup_network_only=t_plain / t_net, plain_elem_steps_per_s=el_steps / t_plain,
+               rollout_elem_steps_per_s=el_steps / t_sur, max_tip_err=float(err.max()),
+               mean_tip_err=float(err.mean()), max_tip_err_network_only=float(err_net.max()), stats=stats)
+    _record("surrogate_gain", rec)
+    print(rec)
+    ro.close()
+    ro2.close()
+    assert err.max() <= 1e-3, rec                         # the bound, over all 4096 rods
+    assert t_sur < t_plain, rec                           # the trained network gains over the plain step
+
+
+def test_untrained_network_falls_back_to_the_plain_step():
+    """With random weights every checked segment exceeds the bound, is undone and redone with
+    the plain step: the result is the plain trajectory."""
+    import torch
+    from paper_2605_13766_gb300 import RodSystem, Surrogate
+    from paper_2605_13766_gb300 import surrogate as S
+    p = rodgen.cilia_carpet(side=8, n=50)
+    dt, W, n_calls, every = 1e-5, 50, 20, 5
+    sur = Surrogate(W, dt)
+    sur.set_params(S.initial_params(seed=5, last_gain=1.0))
+    sur.set_scales(np.zeros(24), np.ones(24), np.full(15, 1e-3))
+    ro = S.CheckedRollout(sur, p, n_sample=8, seed=2)
+    stats = ro.run(n_calls, check_every=every, bound=1e-3)
+    assert stats["fallback_calls"] == n_calls and stats["surrogate_calls"] == 0, stats
+    assert stats["checks"] == n_calls // every and stats["rejected_err"] > 1e-3
+    s = RodSystem(p)
+    s.set_state(*p.state())
+    for _ in range(n_calls // every):
+        s.step(every * W, dt)
+    for a, b in zip(ro.system.get_state(), s.get_state()):
+        assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1.0)
+    assert stats["max_err"] < 1e-12
+    ro.close()

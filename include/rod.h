@@ -199,6 +199,11 @@ int32_t rod_max_elements_per_rod(void);
  *   num_params()                    length of the FP32 parameter vector
  *   set_params / get_params         FP32 parameters (host or device); set resets Adam's moments
  *   set_scales(shift[24], scale[24], out[15])   feature shift / scale and output scales (host)
+ *   set_prior(flags)                the form of the update: bit 0 positions get the prior
+ *                                   x + T v (else x), bit 1 directors exp([-T w]x) Q (else Q),
+ *                                   bit 2 velocities are the output alone (else v + output),
+ *                                   bit 3 angular velocities are the output alone (else w +
+ *                                   output); default 3.  Targets follow the same form.
  *   train_step(...)                 one Adam step (lr > 0) or loss + gradient only (lr <= 0) on a
  *                                   batch of windows: states at the window start and end for
  *                                   nwin rods in the system layout (device pointers), act
@@ -237,6 +242,7 @@ rod_status rod_surrogate_set_params(rod_surrogate* sur, const float* params, int
 rod_status rod_surrogate_get_params(rod_surrogate* sur, float* params, int on_device);
 rod_status rod_surrogate_set_scales(rod_surrogate* sur, const double* in_shift, const double* in_scale,
                                     const double* out_scale);
+rod_status rod_surrogate_set_prior(rod_surrogate* sur, int32_t flags);
 rod_status rod_surrogate_train_step(rod_surrogate* sur, const double* x0, const double* v0, const double* Q0,
                                     const double* w0, const double* x1, const double* v1, const double* Q1,
                                     const double* w1, const double* act, int32_t nwin, float lr, float* loss_out,

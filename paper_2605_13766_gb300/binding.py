@@ -102,6 +102,7 @@ _SIGNATURES = {
     "rod_surrogate_train_step": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int32, C.c_float, _P, _P], C.c_int),
     "rod_surrogate_get_grad": ([_P, _P, C.c_int], C.c_int),
     "rod_surrogate_forward": ([_P, _P, _P, _P, _P, _P, C.c_int32, _P, _P], C.c_int),
+    "rod_surrogate_set_prior": ([_P, C.c_int32], C.c_int),
     "rod_surrogate_raw_features": ([_P, _P, _P, _P, _P, _P, C.c_int32, _P, _P, _P], C.c_int),
     "rod_surrogate_raw_targets": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int32, _P, _P], C.c_int),
     "rod_surrogate_apply": ([_P, _P, C.c_int64], C.c_int),
@@ -437,6 +438,15 @@ class Surrogate:
             raise ValueError("need 24 input shifts, 24 input scales and 15 output scales")
         _check(self.lib.rod_surrogate_set_scales(self.handle, sh.ctypes.data, sc.ctypes.data, o.ctypes.data))
         self.scales = (sh, sc, o)
+
+    def set_prior(self, positions: bool = True, directors: bool = True, velocity_residual: bool = True,
+                  omega_residual: bool = True):
+        """Form of the update: kinematic priors x + T v for positions and exp([-T w]x) Q for
+        directors; velocities / angular velocities as residuals (v + output) or output alone."""
+        flags = (int(bool(positions)) | (int(bool(directors)) << 1) | (int(not velocity_residual) << 2)
+                 | (int(not omega_residual) << 3))
+        _check(self.lib.rod_surrogate_set_prior(self.handle, flags))
+        self.prior = flags
 
     def train_step(self, start, end, act, lr: float, stream=None):
         """start/end: (x, v, Q, w) CUDA float64 tensors of nwin rods of 50 elements; act (3, nwin).

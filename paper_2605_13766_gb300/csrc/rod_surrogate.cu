@@ -24,6 +24,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -224,6 +225,10 @@ struct Scales {
   float in_scale[kFeat];
   double out[kOut];        // state change = prior + out * network output
   double T;                // window length in time (window steps x dt)
+  int prior_x;             // 1: positions have the prior x + T v (else x)
+  int prior_q;             // 1: directors have the prior exp([-T w]x) Q (else Q)
+  int keep_v;              // 1: velocities are v + output (residual), 0: output alone
+  int keep_w;              // 1: angular velocities are w + output (residual), 0: output alone
 };
 
 // Q_new = exp([-T w]x) Q (rows: directors): the director update of a constant angular velocity
@@ -231,9 +236,15 @@ struct Scales {
 // as 2 sin^2(th / 2).
 __device__ __forceinline__ void rotate_directors(const double w[3], double T, const double Q[9], double out[9]) {
   const double ph[3] = {-T * w[0], -T * w[1], -T * w[2]};
-  const double th = sqrt(ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2]);
-  double a = 1.0, b = 0.5;
-  if (th > 0.0) {
+  const double th2 = ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2];
+  double a, b;
+  if (th2 < 2.5e-3) {
+    // |th| < 0.05: Taylor series of sin(th)/th and (1 - cos th)/th^2; the first omitted terms,
+    // th^8/9! and th^8/10!, are below 1e-16
+    a = 1.0 - th2 / 6.0 * (1.0 - th2 / 20.0 * (1.0 - th2 / 42.0));
+    b = 0.5 * (1.0 - th2 / 12.0 * (1.0 - th2 / 30.0 * (1.0 - th2 / 56.0)));
+  } else {
+    const double th = sqrt(th2);
     const double sh = sin(0.5 * th) / th;
     a = sin(th) / th;
     b = 2.0 * sh * sh;
@@ -313,20 +324,21 @@ __global__ void features_kernel(WinState S, const double* __restrict__ act, int 
 // Training target channel c at node position j of window b (unscaled):
 //   0..2 x1 - x0 - T v0     3..5 v1 - v0     6..11 rows d1, d2 of Q1 - exp([-T w0]x) Q0     12..14 w1 - w0
 // (element channels are zero at j = 50)
-__device__ double target_value(const WinState& A, const WinState& B, double T, int b, int j, int c) {
+__device__ double target_value(const WinState& A, const WinState& B, double T, double Tq, bool keep_v, bool keep_w, int b,
+                               int j, int c) {
   const int64_t node = static_cast<int64_t>(b) * kPos + j, el = static_cast<int64_t>(b) * (kPos - 1) + j;
   const bool has_el = j < kPos - 1;
-  if (c < 3) return B.x[c * A.N + node] - A.x[c * A.N + node] - T * A.v[c * A.N + node];
-  if (c < 6) return B.v[(c - 3) * A.N + node] - A.v[(c - 3) * A.N + node];
+  if (c < 3) return B.x[c * A.N + node] - A.x[c * A.N + node] - T * A.v[c * A.N + node];  // T = 0: no prior
+  if (c < 6) return B.v[(c - 3) * A.N + node] - (keep_v ? A.v[(c - 3) * A.N + node] : 0.0);
   if (!has_el) return 0.0;
   if (c < 12) {
     double q0[9], qp[9];
     const double w0[3] = {A.w[el], A.w[A.E + el], A.w[2 * A.E + el]};
     load_q(A.Q, A.E, el, q0);
-    rotate_directors(w0, T, q0, qp);
+    rotate_directors(w0, Tq, q0, qp);
     return B.Q[(c - 6) * A.E + el] - qp[c - 6];
   }
-  return B.w[(c - 12) * A.E + el] - A.w[(c - 12) * A.E + el];
+  return B.w[(c - 12) * A.E + el] - (keep_w ? A.w[(c - 12) * A.E + el] : 0.0);
 }
 
 // scaled FP32 training targets [b][j][16]
@@ -336,7 +348,9 @@ __global__ void targets_kernel(WinState A, WinState B, int nwin, Scales sc, floa
   const int c = i % kCO;
   const int64_t bj = i / kCO;
   const int b = static_cast<int>(bj / kPos), j = static_cast<int>(bj % kPos);
-  tgt[i] = (c < kOut) ? static_cast<float>(target_value(A, B, sc.T, b, j, c) / sc.out[c]) : 0.f;
+  tgt[i] = (c < kOut) ? static_cast<float>(target_value(A, B, sc.prior_x ? sc.T : 0.0, sc.prior_q ? sc.T : 0.0, sc.keep_v, sc.keep_w, b, j, c) /
+                                            sc.out[c])
+                      : 0.f;
 }
 
 // unscaled FP64 features [b][c][j] (zero where undefined) and mask (1 where defined)
@@ -354,13 +368,14 @@ __global__ void raw_features_kernel(WinState S, const double* __restrict__ act, 
 }
 
 // unscaled FP64 targets [b][c][j]: state change minus the kinematic prior
-__global__ void raw_targets_kernel(WinState A, WinState B, int nwin, double T, double* __restrict__ out) {
+__global__ void raw_targets_kernel(WinState A, WinState B, int nwin, double T, double Tq, int keep_v, int keep_w,
+                                   double* __restrict__ out) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= static_cast<int64_t>(nwin) * kOut * kPos) return;
   const int j = static_cast<int>(i % kPos);
   const int c = static_cast<int>((i / kPos) % kOut);
   const int b = static_cast<int>(i / (static_cast<int64_t>(kPos) * kOut));
-  out[i] = target_value(A, B, T, b, j, c);
+  out[i] = target_value(A, B, T, Tq, keep_v, keep_w, b, j, c);
 }
 
 // loss = mean (out - tgt)^2 over windows x positions x 15 channels; gradient to BF16 rows
@@ -387,39 +402,44 @@ __global__ void loss_kernel(const float* __restrict__ out, const float* __restri
   if ((threadIdx.x & 31) == 0 && local != 0.f) atomicAdd(loss_sum, local * inv_count);
 }
 
-// state <- prior + scale * out (FP64); directors re-orthonormalised (Gram-Schmidt on d1, d2,
-// d3 = d1 x d2); a clamped rod keeps node 0 and element 0 as they are, at rest.
-__global__ void apply_kernel(double* x, double* v, double* Q, double* w, int64_t N, int64_t E, int nrods,
-                             const float* __restrict__ out, Scales sc, const RodConst* __restrict__ rods) {
-  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (i >= static_cast<int64_t>(nrods) * kPos) return;
-  const int b = static_cast<int>(i / kPos), j = static_cast<int>(i % kPos);
-  const float* o = out + i * kCO;
-  const bool held = rods[b].clamp != 0 && j == 0;
+// New state of node position j of window b: prior + scale * out (FP64); the directors are
+// re-orthonormalised (Gram-Schmidt on d1, d2; d3 = d1 x d2); a clamped rod keeps node 0 and
+// element 0 as they are, at rest.  Reads the old state from S (window b, may be a shared-memory
+// copy), writes the new one to the global arrays at node ng / element eg.
+__device__ __forceinline__ void update_node(const WinState& S, int b, int j, const float* __restrict__ o, const Scales& sc,
+                                            bool clamped, double* x, double* v, double* Q, double* w, int64_t N,
+                                            int64_t E, int64_t ng, int64_t eg) {
+  const int64_t node = static_cast<int64_t>(b) * kPos + j;
+  const bool held = clamped && j == 0;
   if (!held) {
     for (int c = 0; c < 3; ++c) {
-      const double v0 = v[c * N + i];
-      x[c * N + i] += sc.T * v0 + sc.out[c] * static_cast<double>(o[c]);
-      v[c * N + i] = v0 + sc.out[3 + c] * static_cast<double>(o[3 + c]);
+      const double x0 = S.x[c * S.N + node], v0 = S.v[c * S.N + node];
+      x[c * N + ng] = x0 + (sc.prior_x ? sc.T * v0 : 0.0) + sc.out[c] * static_cast<double>(o[c]);
+      v[c * N + ng] = (sc.keep_v ? v0 : 0.0) + sc.out[3 + c] * static_cast<double>(o[3 + c]);
     }
   } else {
-    for (int c = 0; c < 3; ++c) v[c * N + i] = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      x[c * N + ng] = S.x[c * S.N + node];
+      v[c * N + ng] = 0.0;
+    }
   }
   if (j >= kPos - 1) return;
   const int64_t e = static_cast<int64_t>(b) * (kPos - 1) + j;
+  double q0[9];
+  load_q(S.Q, S.E, e, q0);
   if (held) {
-    for (int c = 0; c < 3; ++c) w[c * E + e] = 0.0;
+    for (int a = 0; a < 9; ++a) Q[a * E + eg] = q0[a];
+    for (int c = 0; c < 3; ++c) w[c * E + eg] = 0.0;
     return;
   }
-  double q0[9], qp[9];
-  const double w0[3] = {w[e], w[E + e], w[2 * E + e]};
-  load_q(Q, E, e, q0);
-  rotate_directors(w0, sc.T, q0, qp);
+  double qp[9];
+  const double w0[3] = {S.w[e], S.w[S.E + e], S.w[2 * S.E + e]};
+  rotate_directors(w0, sc.prior_q ? sc.T : 0.0, q0, qp);
   double d1[3], d2[3];
   for (int c = 0; c < 3; ++c) {
     d1[c] = qp[c] + sc.out[6 + c] * static_cast<double>(o[6 + c]);
     d2[c] = qp[3 + c] + sc.out[9 + c] * static_cast<double>(o[9 + c]);
-    w[c * E + e] = w0[c] + sc.out[12 + c] * static_cast<double>(o[12 + c]);
+    w[c * E + eg] = (sc.keep_w ? w0[c] : 0.0) + sc.out[12 + c] * static_cast<double>(o[12 + c]);
   }
   const double n1 = 1.0 / sqrt(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
   for (int c = 0; c < 3; ++c) d1[c] *= n1;
@@ -429,9 +449,240 @@ __global__ void apply_kernel(double* x, double* v, double* Q, double* w, int64_t
   for (int c = 0; c < 3; ++c) d2[c] *= n2;
   const double d3[3] = {d1[1] * d2[2] - d1[2] * d2[1], d1[2] * d2[0] - d1[0] * d2[2], d1[0] * d2[1] - d1[1] * d2[0]};
   for (int c = 0; c < 3; ++c) {
-    Q[c * E + e] = d1[c];
-    Q[(3 + c) * E + e] = d2[c];
-    Q[(6 + c) * E + e] = d3[c];
+    Q[c * E + eg] = d1[c];
+    Q[(3 + c) * E + eg] = d2[c];
+    Q[(6 + c) * E + eg] = d3[c];
+  }
+}
+
+// unfused update of every node position from the network output [nrods][51][16] (in place)
+__global__ void apply_kernel(double* x, double* v, double* Q, double* w, int64_t N, int64_t E, int nrods,
+                             const float* __restrict__ out, Scales sc, const RodConst* __restrict__ rods) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= static_cast<int64_t>(nrods) * kPos) return;
+  const int b = static_cast<int>(i / kPos), j = static_cast<int>(i % kPos);
+  WinState S;
+  S.x = x;
+  S.v = v;
+  S.Q = Q;
+  S.w = w;
+  S.N = N;
+  S.E = E;
+  update_node(S, b, j, out + i * kCO, sc, rods[b].clamp != 0, x, v, Q, w, N, E, i,
+              static_cast<int64_t>(b) * (kPos - 1) + j);
+}
+
+// ---- fused inference: one persistent kernel per window call
+//
+// Each block keeps all BF16 weights in shared memory (rows padded so that the fragment loads of
+// a warp hit 32 distinct banks) and loops over groups of kFW windows: stage the FP64 state of the
+// group, build the features, run the four convolutions between two shared activation buffers and
+// update the state in FP64.  8 warps: warp w takes window w / 2 and output rows 32 (w % 2) ..
+// +31 of a 64-channel layer (2 m-tiles x 7 n-tiles), or n-tiles 0..3 / 4..6 of the 16-channel
+// output layer.
+constexpr int kFW = 4;                      // windows per group
+constexpr int kLdAct = 72;                  // activation row stride (BF16)
+constexpr int kLdW1 = kTaps * kC0 + 8;      // 168
+constexpr int kLdW = kTaps * kC + 8;        // 328
+constexpr int kStateDoubles = 6 * kPos + 12 * (kPos - 1);  // 906
+constexpr size_t kFusedW1 = size_t(kC) * kLdW1 * 2, kFusedW2 = size_t(kC) * kLdW * 2, kFusedW4 = size_t(kCO) * kLdW * 2;
+constexpr size_t kFusedBias = (3 * kC + kCO) * 4 + kFW * 3 * 8;  // biases, then the couple samples (FP64)
+constexpr size_t kFusedAct = size_t(kFW) * kRows * kLdAct * 2;
+constexpr size_t kFusedState = size_t(kFW) * kStateDoubles * 8;
+constexpr size_t kFusedSmem = kFusedState + kFusedW1 + 2 * kFusedW2 + kFusedW4 + kFusedBias + 2 * kFusedAct;
+
+// one convolution layer from in (kFW x [64][kLdAct]) with smem weights Ws [COUT][LDW]
+template <int CIN, int COUT, int LDW, bool OUTPUT>
+__device__ __forceinline__ void fused_conv(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ Ws,
+                                           const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
+                                           float* __restrict__ outf, int warp, int lane) {
+  const int g = lane >> 2, tg = lane & 3;
+  const int wi = warp >> 1, half = warp & 1;
+  constexpr int K = kTaps * CIN;
+  constexpr int MT = OUTPUT ? 1 : 2;
+  constexpr int NT = OUTPUT ? 4 : 7;
+  const int m0 = OUTPUT ? 0 : half * 32;
+  const int nt0 = OUTPUT ? half * 4 : 0;
+  const int ntn = OUTPUT ? (half ? 3 : 4) : 7;
+  const __nv_bfloat16* inw = in + wi * kRows * kLdAct;
+  float acc[MT][NT][4];
+#pragma unroll
+  for (int a = 0; a < MT; ++a)
+#pragma unroll
+    for (int n = 0; n < NT; ++n) acc[a][n][0] = acc[a][n][1] = acc[a][n][2] = acc[a][n][3] = 0.f;
+#pragma unroll 2
+  for (int kb = 0; kb < K / 16; ++kb) {
+    const int t = (kb * 16) / CIN, cb = (kb * 16) % CIN;
+    uint32_t af[MT][4];
+#pragma unroll
+    for (int a = 0; a < MT; ++a) {
+      const __nv_bfloat16* wr0 = Ws + (m0 + a * 16 + g) * LDW + kb * 16 + 2 * tg;
+      const __nv_bfloat16* wr1 = wr0 + 8 * LDW;
+      af[a][0] = *reinterpret_cast<const uint32_t*>(wr0);
+      af[a][1] = *reinterpret_cast<const uint32_t*>(wr1);
+      af[a][2] = *reinterpret_cast<const uint32_t*>(wr0 + 8);
+      af[a][3] = *reinterpret_cast<const uint32_t*>(wr1 + 8);
+    }
+#pragma unroll
+    for (int n = 0; n < NT; ++n) {
+      if (n < ntn) {
+        const int row = (nt0 + n) * 8 + g + t;
+        const __nv_bfloat16* ir = inw + row * kLdAct + cb + 2 * tg;
+        uint32_t bf[2];
+        bf[0] = *reinterpret_cast<const uint32_t*>(ir);
+        bf[1] = *reinterpret_cast<const uint32_t*>(ir + 8);
+#pragma unroll
+        for (int a = 0; a < MT; ++a) mma_bf16(acc[a][n], af[a], bf);
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < MT; ++a)
+#pragma unroll
+    for (int n = 0; n < NT; ++n) {
+      if (n >= ntn) continue;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int o = m0 + a * 16 + g + ((q & 2) ? 8 : 0);
+        const int jj = (nt0 + n) * 8 + 2 * tg + (q & 1);
+        const float vv = acc[a][n][q] + bias[o];
+        if (OUTPUT) {
+          if (jj < kPos) outf[(wi * kPos + jj) * kCO + o] = vv;
+        } else {
+          out[(wi * kRows + jj + 2) * kLdAct + o] = __float2bfloat16_rn(jj < kPos ? silu(vv) : 0.f);
+        }
+      }
+    }
+}
+
+__global__ void __launch_bounds__(256, 1) fused_apply_kernel(double* x, double* v, double* Q, double* w, int64_t N,
+                                                             int64_t E, int nrods, const RodConst* __restrict__ rods,
+                                                             double t, Scales sc, const __nv_bfloat16* __restrict__ wf,
+                                                             const float* __restrict__ master) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* st = reinterpret_cast<double*>(smem_raw);
+  __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(smem_raw + kFusedState);
+  __nv_bfloat16* W2s = reinterpret_cast<__nv_bfloat16*>(smem_raw + kFusedState + kFusedW1);
+  __nv_bfloat16* W3s = reinterpret_cast<__nv_bfloat16*>(smem_raw + kFusedState + kFusedW1 + kFusedW2);
+  __nv_bfloat16* W4s = reinterpret_cast<__nv_bfloat16*>(smem_raw + kFusedState + kFusedW1 + 2 * kFusedW2);
+  float* bias = reinterpret_cast<float*>(smem_raw + kFusedState + kFusedW1 + 2 * kFusedW2 + kFusedW4);
+  double* act_s = reinterpret_cast<double*>(bias + 3 * kC + kCO);
+  __nv_bfloat16* bufA = reinterpret_cast<__nv_bfloat16*>(smem_raw + kFusedState + kFusedW1 + 2 * kFusedW2 + kFusedW4 + kFusedBias);
+  __nv_bfloat16* bufB = bufA + kFW * kRows * kLdAct;
+  float* outf = reinterpret_cast<float*>(bufA);  // the output layer's FP32 result reuses buffer A
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // weights into shared memory (padded rows), biases
+  {
+    const __nv_bfloat16* src[4] = {wf, wf + kW1, wf + kW1 + kW2, wf + kW1 + kW2 + kW3};
+    __nv_bfloat16* dst[4] = {W1s, W2s, W3s, W4s};
+    const int rows[4] = {kC, kC, kC, kCO}, kk[4] = {kTaps * kC0, kTaps * kC, kTaps * kC, kTaps * kC};
+    const int ld[4] = {kLdW1, kLdW, kLdW, kLdW};
+    for (int l = 0; l < 4; ++l) {
+      const int words = rows[l] * kk[l] / 2;
+      for (int i = tid; i < words; i += blockDim.x) {
+        const int r = (2 * i) / kk[l], c = (2 * i) % kk[l];
+        *reinterpret_cast<uint32_t*>(dst[l] + r * ld[l] + c) = reinterpret_cast<const uint32_t*>(src[l])[i];
+      }
+    }
+    for (int i = tid; i < kC; i += blockDim.x) {
+      bias[i] = master[kOffB1 + i];
+      bias[kC + i] = master[kOffB2 + i];
+      bias[2 * kC + i] = master[kOffB3 + i];
+    }
+    for (int i = tid; i < kCO; i += blockDim.x) bias[3 * kC + i] = master[kOffB4 + i];
+    // buffer B's padding rows (0, 1, 58..63) are never written by the layers: zero once
+    for (int i = tid; i < kFW * kRows * kLdAct / 2; i += blockDim.x) reinterpret_cast<uint32_t*>(bufB)[i] = 0u;
+  }
+  const int ngroups = (nrods + kFW - 1) / kFW;
+  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const int b0 = grp * kFW;
+    const int nw = min(kFW, nrods - b0);
+    __syncthreads();  // previous group's readers of st / bufA are done
+    // stage the state of the group: per window x[3][51], v[3][51], Q[9][50], w[3][50]
+    for (int i = tid; i < kFW * kStateDoubles; i += blockDim.x) {
+      const int wi = i / kStateDoubles, k = i % kStateDoubles;
+      double val = 0.0;
+      if (wi < nw) {
+        const int64_t n0 = static_cast<int64_t>(b0 + wi) * kPos, e0 = static_cast<int64_t>(b0 + wi) * (kPos - 1);
+        if (k < 3 * kPos) val = x[(k / kPos) * N + n0 + k % kPos];
+        else if (k < 6 * kPos) { const int kk = k - 3 * kPos; val = v[(kk / kPos) * N + n0 + kk % kPos]; }
+        else if (k < 6 * kPos + 9 * (kPos - 1)) { const int kk = k - 6 * kPos; val = Q[(kk / (kPos - 1)) * E + e0 + kk % (kPos - 1)]; }
+        else { const int kk = k - 6 * kPos - 9 * (kPos - 1); val = w[(kk / (kPos - 1)) * E + e0 + kk % (kPos - 1)]; }
+      } else {
+        // an absent window: a straight identity-frame rod keeps the features finite
+        if (k >= 6 * kPos && k < 6 * kPos + 9 * (kPos - 1)) {
+          const int a = (k - 6 * kPos) / (kPos - 1);
+          val = (a == 0 || a == 4 || a == 8) ? 1.0 : 0.0;
+        }
+      }
+      st[i] = val;
+    }
+    if (tid < kFW * 3) {
+      // base couple of each window at its start, middle and end
+      const int wi = tid / 3, k = tid % 3;
+      double a = 0.0;
+      if (wi < nw) {
+        const RodConst& rc = rods[b0 + wi];
+        a = rc.act_amp * sin(rc.act_omega * (t + 0.5 * k * sc.T) + rc.act_phase);
+      }
+      act_s[tid] = a;
+    }
+    // padding rows 0, 1 and 53..63 of buffer A are zero
+    for (int i = tid; i < kFW * (kRows - kPos) * (kLdAct / 2); i += blockDim.x) {
+      const int wi = i / ((kRows - kPos) * (kLdAct / 2)), rem = i % ((kRows - kPos) * (kLdAct / 2));
+      const int r = rem / (kLdAct / 2), cw = rem % (kLdAct / 2);
+      const int row = r < 2 ? r : r + kPos;
+      reinterpret_cast<uint32_t*>(bufA + (wi * kRows + row) * kLdAct)[cw] = 0u;
+    }
+    __syncthreads();
+    // features: one thread per (window, node position) writes the whole row j + 2
+    for (int i = tid; i < kFW * kPos; i += blockDim.x) {
+      const int wi = i / kPos, j = i % kPos;
+      const double* sw = st + wi * kStateDoubles;
+      WinState S;
+      S.x = sw;
+      S.v = sw + 3 * kPos;
+      S.Q = sw + 6 * kPos;
+      S.w = sw + 6 * kPos + 9 * (kPos - 1);
+      S.N = kPos;
+      S.E = kPos - 1;
+      uint32_t* row = reinterpret_cast<uint32_t*>(bufA + (wi * kRows + j + 2) * kLdAct);
+#pragma unroll 1
+      for (int c = 0; c < kLdAct; c += 2) {
+        float f[2] = {0.f, 0.f};
+        for (int h = 0; h < 2; ++h) {
+          double d;
+          if (c + h < kFeat && raw_feature(S, act_s + 3 * wi, 1, 0, j, c + h, &d))
+            f[h] = static_cast<float>(d - sc.in_shift[c + h]) * sc.in_scale[c + h];
+        }
+        row[c / 2] = pack_bf16(__float2bfloat16_rn(f[0]), __float2bfloat16_rn(f[1]));
+      }
+    }
+    __syncthreads();
+    fused_conv<kC0, kC, kLdW1, false>(bufA, W1s, bias, bufB, nullptr, warp, lane);
+    __syncthreads();
+    fused_conv<kC, kC, kLdW, false>(bufB, W2s, bias + kC, bufA, nullptr, warp, lane);
+    __syncthreads();
+    fused_conv<kC, kC, kLdW, false>(bufA, W3s, bias + 2 * kC, bufB, nullptr, warp, lane);
+    __syncthreads();
+    fused_conv<kC, kCO, kLdW, true>(bufB, W4s, bias + 3 * kC, nullptr, outf, warp, lane);
+    __syncthreads();
+    // FP64 update of every node position of the group
+    for (int i = tid; i < nw * kPos; i += blockDim.x) {
+      const int wi = i / kPos, j = i % kPos;
+      const double* sw = st + wi * kStateDoubles;
+      WinState S;
+      S.x = sw;
+      S.v = sw + 3 * kPos;
+      S.Q = sw + 6 * kPos;
+      S.w = sw + 6 * kPos + 9 * (kPos - 1);
+      S.N = kPos;
+      S.E = kPos - 1;
+      const int b = b0 + wi;
+      update_node(S, 0, j, outf + (wi * kPos + j) * kCO, sc, rods[b].clamp != 0, x, v, Q, w, N, E,
+                  static_cast<int64_t>(b) * kPos + j, static_cast<int64_t>(b) * (kPos - 1) + j);
+    }
   }
 }
 
@@ -649,16 +900,44 @@ rod_status check_system(rod_surrogate* s, rod_system* sys, SysView* V, const cha
   return ROD_OK;
 }
 
-// n_calls network windows on the system's stream (no synchronisation)
+// blocks of the fused kernel: one per SM (its shared memory holds the whole network)
+cudaError_t fused_grid(int* grid) {
+  static int sms = 0;
+  static bool attr = false;
+  cudaError_t e;
+  if (!sms) {
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
+  }
+  if (!attr) {
+    if ((e = cudaFuncSetAttribute(fused_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem)))
+      return e;
+    attr = true;
+  }
+  *grid = sms;
+  return cudaSuccess;
+}
+
+// n_calls network windows on the system's stream (no synchronisation): one fused launch per call
+// (or the unfused kernel sequence when ROD_SURROGATE_UNFUSED is set, for comparison)
 cudaError_t apply_calls(rod_surrogate* s, const SysView& V, int64_t n_calls) {
+  static const bool unfused = std::getenv("ROD_SURROGATE_UNFUSED") != nullptr;
   const WinState S = win_state(V.x, V.v, V.Q, V.w, V.R);
+  int sms = 0;
+  cudaError_t e;
+  if (!unfused && (e = fused_grid(&sms))) return e;
+  const int groups = (V.R + kFW - 1) / kFW;
   for (int64_t k = 0; k < n_calls; ++k) {
-    actuation_kernel<<<(V.R + 127) / 128, 128, 0, V.stream>>>(V.rods, V.R, *V.t, s->sc.T, s->act);
-    features_kernel<<<V.R, 256, 0, V.stream>>>(S, s->act, V.R, s->sc, s->a0);
-    cudaError_t e = forward(s, V.R, false, V.stream);
-    if (e != cudaSuccess) return e;
-    apply_kernel<<<(V.R * kPos + 255) / 256, 256, 0, V.stream>>>(V.x, V.v, V.Q, V.w, V.N, V.E, V.R, s->outf, s->sc,
-                                                                 V.rods);
+    if (unfused) {
+      actuation_kernel<<<(V.R + 127) / 128, 128, 0, V.stream>>>(V.rods, V.R, *V.t, s->sc.T, s->act);
+      features_kernel<<<V.R, 256, 0, V.stream>>>(S, s->act, V.R, s->sc, s->a0);
+      if ((e = forward(s, V.R, false, V.stream))) return e;
+      apply_kernel<<<(V.R * kPos + 255) / 256, 256, 0, V.stream>>>(V.x, V.v, V.Q, V.w, V.N, V.E, V.R, s->outf, s->sc,
+                                                                   V.rods);
+    } else {
+      fused_apply_kernel<<<std::min(groups, sms), 256, kFusedSmem, V.stream>>>(V.x, V.v, V.Q, V.w, V.N, V.E, V.R, V.rods,
+                                                                              *V.t, s->sc, s->wf, s->master);
+    }
     *V.t += s->window * s->dt;
   }
   return cudaGetLastError();
@@ -714,6 +993,10 @@ rod_status rod_surrogate_create(int32_t window_steps, double dt, rod_surrogate**
   s->window = window_steps;
   s->dt = dt;
   s->sc.T = window_steps * dt;
+  s->sc.prior_x = 1;
+  s->sc.prior_q = 1;
+  s->sc.keep_v = 1;
+  s->sc.keep_w = 1;
   for (int c = 0; c < kFeat; ++c) {
     s->sc.in_shift[c] = 0.0;
     s->sc.in_scale[c] = 1.0f;
@@ -779,6 +1062,15 @@ rod_status rod_surrogate_set_scales(rod_surrogate* s, const double* in_shift, co
     s->sc.in_scale[c] = static_cast<float>(in_scale[c]);
   }
   for (int c = 0; c < kOut; ++c) s->sc.out[c] = out_scale[c];
+  return ROD_OK;
+}
+
+rod_status rod_surrogate_set_prior(rod_surrogate* s, int32_t flags) {
+  if (!s || flags < 0 || flags > 15) return internal_fail(ROD_ERR_ARG, "rod_surrogate_set_prior: bad argument", "");
+  s->sc.prior_x = flags & 1;
+  s->sc.prior_q = (flags >> 1) & 1;
+  s->sc.keep_v = !((flags >> 2) & 1);
+  s->sc.keep_w = !((flags >> 3) & 1);
   return ROD_OK;
 }
 
@@ -857,7 +1149,8 @@ rod_status rod_surrogate_raw_targets(rod_surrogate* s, const double* x0, const d
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const int64_t n = static_cast<int64_t>(nwin) * kOut * kPos;
   raw_targets_kernel<<<(n + 255) / 256, 256, 0, st>>>(win_state(x0, v0, Q0, w0, nwin), win_state(x1, v1, Q1, w1, nwin),
-                                                      nwin, s->sc.T, out);
+                                                      nwin, s->sc.prior_x ? s->sc.T : 0.0,
+                                                      s->sc.prior_q ? s->sc.T : 0.0, s->sc.keep_v, s->sc.keep_w, out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return internal_fail(ROD_ERR_CUDA, "rod_surrogate_raw_targets", cudaGetErrorString(e));
   return ROD_OK;

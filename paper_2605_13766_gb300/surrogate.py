@@ -53,9 +53,15 @@ class Windows:
 
 
 def generate(problem, n_windows: int, window: int = 50, dt: Optional[float] = None,
-             skip_windows: int = 0) -> Windows:
+             skip_windows: int = 0, smooth: bool = False, sub: int = 5) -> Windows:
     """Run the plain GPU step on ``problem`` from its state and keep the state every ``window``
-    steps (after ``skip_windows`` windows).  Every rod must have 50 elements."""
+    steps (after ``skip_windows`` windows).  Every rod must have 50 elements.
+
+    smooth=True keeps instead the window average of the state around every window boundary:
+    samples every ``sub`` steps weighted by a triangle of half-width ``window`` steps (the state
+    before the start counts as the initial state), directors re-orthonormalised.  This removes
+    the oscillations a window of fine steps cannot resolve (the rotary-shear modes of the rods,
+    near the window's own period) and keeps the slower bending motion."""
     import torch
     dt = float(problem.dt if dt is None else dt)
     if np.any(np.asarray(problem.n_elem) != ELEMENTS):
@@ -64,20 +70,65 @@ def generate(problem, n_windows: int, window: int = 50, dt: Optional[float] = No
     s.set_state(*problem.state())
     if skip_windows:
         s.step(skip_windows * window, dt)
-    states, acts = [], []
     T = window * dt
-    for k in range(n_windows + 1):
-        st = [a.clone() for a in s.get_state(device=True)]
-        states.append(st)
-        if k < n_windows:
-            acts.append(torch.tensor(couple_samples(problem, s.time, T), device="cuda"))
-            s.step(window, dt)
+    t0 = s.time
+    acts = [torch.tensor(couple_samples(problem, t0 + k * T, T), device="cuda") for k in range(n_windows)]
+    if not smooth:
+        states = []
+        for k in range(n_windows + 1):
+            states.append([a.clone() for a in s.get_state(device=True)])
+            if k < n_windows:
+                s.step(window, dt)
+        torch.cuda.synchronize()
+        s.close()
+        return Windows(problem, states, acts, window, dt)
+    if window % sub:
+        raise ValueError("window must be a multiple of sub")
+    h = window // sub
+    wts = {i: (h - abs(i)) / float(h * h) for i in range(-h + 1, h)}     # sums to 1
+    first = [a.clone() for a in s.get_state(device=True)]
+    acc = {}
+    states = [None] * (n_windows + 1)
+
+    def add(k, m, st):
+        wt = wts[m - k * h]
+        if k not in acc:
+            acc[k] = [wt * a for a in st]
+        else:
+            for a, b in zip(acc[k], st):
+                a.add_(b, alpha=wt)
+
+    def finish(k):
+        x, v, Q, w = acc.pop(k)
+        d1, d2 = Q[0:3], Q[3:6]
+        d1 = d1 / d1.norm(dim=0, keepdim=True)
+        d2 = d2 - (d1 * d2).sum(dim=0, keepdim=True) * d1
+        d2 = d2 / d2.norm(dim=0, keepdim=True)
+        states[k] = [x, v, torch.cat([d1, d2, torch.cross(d1, d2, dim=0)]), w]
+
+    # samples m = -h+1 .. 0 are the initial state
+    for m in range(-h + 1, 1):
+        for k in (0, 1):
+            if abs(m - k * h) < h:
+                add(k, m, first)
+    last = n_windows * h + h - 1
+    for m in range(1, last + 1):
+        s.step(sub, dt)
+        st = s.get_state(device=True)
+        for k in (m // h, m // h + 1):
+            if 0 <= k <= n_windows and abs(m - k * h) < h:
+                add(k, m, st)
+        k_done = (m - h + 1) // h
+        if (m - h + 1) % h == 0 and 0 <= k_done <= n_windows and k_done in acc:
+            finish(k_done)
+    for k in sorted(acc):
+        finish(k)
     torch.cuda.synchronize()
     s.close()
     return Windows(problem, states, acts, window, dt)
 
 
-def fit_scales(sur: Surrogate, data: Sequence[Windows], max_windows: int = 64):
+def fit_scales(sur: Surrogate, data: Sequence[Windows], max_windows: int = 64, output_floor: float = 1e-3):
     """Feature shift = mean, scale = 1 / std (over the defined entries), output scale = std of
     the unscaled targets, from up to ``max_windows`` windows of every trajectory."""
     import torch
@@ -101,7 +152,7 @@ def fit_scales(sur: Surrogate, data: Sequence[Windows], max_windows: int = 64):
     var = (fsq / fcnt.clamp(min=1)).cpu().numpy() - mean ** 2
     std = np.sqrt(np.maximum(var, 0.0))
     rms = np.sqrt((tsq / max(tcnt, 1)).cpu().numpy())
-    shift, scale, out = scales_from_moments(mean, std, rms)
+    shift, scale, out = scales_from_moments(mean, std, rms, output_floor=output_floor)
     sur.set_scales(shift, scale, out)
     return shift, scale, out
 
@@ -110,23 +161,24 @@ FEATURE_GROUPS = [range(0, 3), range(3, 6), range(6, 12), range(12, 15), range(1
 OUTPUT_GROUPS = [range(0, 3), range(3, 6), range(6, 12), range(12, 15)]
 
 
-def scales_from_moments(mean, std, rms, feature_floor: float = 1e-6, output_floor: float = 1e-3):
-    """Shift = mean and scale = 1 / std per feature, output scale = rms per target channel, with
-    every spread floored at a fraction of the largest one of its group (position, velocity,
-    directors, ... ): a channel that only carries rounding noise (for example the out-of-plane
-    components of a planar motion) is then not blown up to order one."""
+def scales_from_moments(mean, std, rms, output_floor: float = 1e-3):
+    """Shift = mean per feature; one scale per feature group (position, velocity, directors,
+    angular velocity, relative rotation, edge, couple) = 1 / the largest spread in the group, so
+    that a channel with little or no spread in the data (for example an out-of-plane component
+    of a planar motion) is not blown up: noise there stays at the group's own scale.  Output
+    scale = rms per target channel, floored at ``output_floor`` times the largest of its group."""
     mean, std, rms = (np.asarray(a, dtype=np.float64) for a in (mean, std, rms))
-    std = std.copy()
+    scale = np.ones_like(std)
     for g in FEATURE_GROUPS:
         g = list(g)
-        top = float(np.max(std[g] + np.abs(mean[g])))
-        std[g] = np.maximum(std[g], feature_floor * top) if top > 0 else 1.0
+        top = float(np.max(std[g]))
+        scale[g] = 1.0 / top if top > 0 else 1.0
     out = rms.copy()
     for g in OUTPUT_GROUPS:
         g = list(g)
         top = float(np.max(rms[g]))
         out[g] = np.maximum(rms[g], output_floor * top) if top > 0 else 1.0
-    return mean, 1.0 / std, out
+    return mean, scale, out
 
 
 def _layer_shapes():
@@ -147,17 +199,53 @@ def initial_params(seed: int = 0, last_gain: float = 0.1) -> np.ndarray:
 
 
 def train(sur: Surrogate, data: Sequence[Windows], steps: int, lr: float = 1e-3, lr_end: float = 1e-5,
-          batch_rods: Optional[int] = None, seed: int = 0, log_every: int = 0) -> List[float]:
+          batch_rods: Optional[int] = None, seed: int = 0, log_every: int = 0, noise: float = 0.0,
+          pushforward: float = 0.0, pushforward_start: float = 0.5) -> List[float]:
     """Adam on random windows: each step takes window k of trajectory d (random) for
     ``batch_rods`` consecutive rods (all rods by default).  Cosine decay from lr to lr_end.
+
+    noise > 0: the window start is perturbed by Gaussian noise of ``noise`` times the largest
+    output scale of each group (the typical change over one window): positions, velocities,
+    angular velocities and a small turn of the directors (clamped entries stay as they are),
+    while the target stays the unperturbed window end, so that the network learns to pull a
+    perturbed state back to the trajectory (and to damp what it cannot follow).
+    pushforward > 0: after a fraction ``pushforward_start`` of the steps, with that probability
+    the window start is the network's own prediction from the previous window's start (the
+    network then learns to correct its own one-window error).
     Returns the loss of every step."""
     import torch
     rng = np.random.default_rng(seed)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    spread = None
+    if noise > 0:
+        if sur.scales is None:
+            raise ValueError("set the scales (fit_scales) before training with noise")
+        out = np.asarray(sur.scales[2], dtype=np.float64)
+        # one noise level per group (positions, velocities, directors, angular velocities):
+        # the largest output scale of the group
+        grp = np.concatenate([np.full(len(g), out[list(g)].max()) for g in OUTPUT_GROUPS])
+        spread = torch.tensor(grp, device="cuda")
+    scratch = {}
     losses = []
     for it in range(steps):
-        d = data[rng.integers(len(data))]
-        k = int(rng.integers(d.n_windows))
+        di = int(rng.integers(len(data)))
+        d = data[di]
+        use_pf = pushforward > 0 and it >= pushforward_start * steps and rng.random() < pushforward
+        k = int(rng.integers(1 if use_pf else 0, d.n_windows))
         a, b, act = d.states[k], d.states[k + 1], d.acts[k]
+        if use_pf:
+            if di not in scratch:
+                scratch[di] = RodSystem(d.problem)
+                scratch[di].set_state(*[t.cpu().numpy() for t in d.states[0]])
+            sysk = scratch[di]
+            sysk.set_state(*d.states[k - 1])
+            sysk.time = (k - 1) * d.window * d.dt
+            sur.apply(sysk, 1)
+            a = [t.clone() for t in sysk.get_state(device=True)]
+            torch.cuda.synchronize()
+        if noise > 0:
+            a = _perturb(a, d, spread, noise, gen)
         if batch_rods and batch_rods < d.n_rods:
             r0 = int(rng.integers(0, d.n_rods - batch_rods + 1))
             a = _rod_slice(a, r0, batch_rods)
@@ -169,8 +257,44 @@ def train(sur: Surrogate, data: Sequence[Windows], steps: int, lr: float = 1e-3,
         losses.append(loss)
         if log_every and (it % log_every == 0 or it == steps - 1):
             print(f"step {it:6d}  lr {rate:.2e}  loss {loss:.4e}", flush=True)
+    for sysk in scratch.values():
+        sysk.close()
     torch.cuda.synchronize()
     return losses
+
+
+def _perturb(state, d, spread, noise, gen):
+    """Window start plus noise: positions, velocities and angular velocities by noise x the output
+    scale of their channel; directors turned by angles of noise x the largest director scale
+    (first-order turn, then Gram-Schmidt)."""
+    import torch
+    x, v, Q, w = [a.clone() for a in state]
+
+    def rnd(a):
+        return torch.randn(a.shape, generator=gen, device=a.device, dtype=a.dtype)
+
+    x += noise * spread[0:3, None] * rnd(x)
+    v += noise * spread[3:6, None] * rnd(v)
+    w += noise * spread[12:15, None] * rnd(w)
+    ang = noise * spread[6:12].max() * rnd(w)                  # (3, E) small rotation vectors
+    dd = [Q[3 * a:3 * a + 3] for a in range(3)]
+    # d_a <- d_a + ang x d_a (lab-frame first-order turn), then re-orthonormalise
+    d1 = dd[0] + torch.cross(ang, dd[0], dim=0)
+    d2 = dd[1] + torch.cross(ang, dd[1], dim=0)
+    d1 = d1 / d1.norm(dim=0, keepdim=True)
+    d2 = d2 - (d1 * d2).sum(dim=0, keepdim=True) * d1
+    d2 = d2 / d2.norm(dim=0, keepdim=True)
+    Qn = torch.cat([d1, d2, torch.cross(d1, d2, dim=0)], dim=0)
+    clamp = getattr(d.problem, "clamp_base", None)
+    held_rods = np.flatnonzero(np.asarray(clamp)) if clamp is not None else np.zeros(0, dtype=np.int64)
+    if held_rods.size:
+        hn = torch.tensor(held_rods * POSITIONS, device=x.device)
+        he = torch.tensor(held_rods * ELEMENTS, device=x.device)
+        x[:, hn] = state[0][:, hn]
+        v[:, hn] = 0.0
+        Qn[:, he] = state[2][:, he]
+        w[:, he] = 0.0
+    return [x, v, Qn, w]
 
 
 def _rod_slice(state, r0: int, n: int):

@@ -174,11 +174,13 @@ def cilia_carpet(side: int = 64, n: int = 50, spacing: float = 0.05, length: flo
                  radius: float = 0.005, youngs: float = 1e6, density: float = 1000.0,
                  period: float = 1.0, amp_factor: float = 0.5, gamma: float = 1.0,
                  dt: float = 1e-5, n_steps: int = 10_000, seed: int = 1234,
-                 amp_range=None, period_range=None) -> RodProblem:
+                 amp_range=None, period_range=None, random_azimuth: bool = False) -> RodProblem:
     """side x side upright clamped rods on a square grid, sinusoidal base couple about d1.
 
     Amplitude A0 = amp_factor * E I / L, phases uniform in [0, 2 pi) from ``seed``; with
-    ``amp_range`` / ``period_range`` every rod draws its own amp_factor / period uniformly."""
+    ``amp_range`` / ``period_range`` every rod draws its own amp_factor / period uniformly.
+    d1 is the lab x axis, or with ``random_azimuth`` a horizontal direction drawn per rod (so
+    that each rod beats in a plane of its own)."""
     rng = np.random.default_rng(seed)
     R = side * side
     n_elem = np.full(R, n, dtype=np.int32)
@@ -186,7 +188,11 @@ def cilia_carpet(side: int = 64, n: int = 50, spacing: float = 0.05, length: flo
     gx, gy = np.meshgrid(np.arange(side) * spacing, np.arange(side) * spacing, indexing="ij")
     base = np.stack([gx.ravel(), gy.ravel(), np.zeros(R)], axis=1)
     d3 = np.tile([0.0, 0.0, 1.0], (R, 1))
-    x, Q = _straight_rods(n_elem, rest_len, base, d3, np.tile([1.0, 0.0, 0.0], (R, 1)))
+    d1 = np.tile([1.0, 0.0, 0.0], (R, 1))
+    if random_azimuth:
+        psi = np.random.default_rng([seed, 7]).uniform(0.0, 2 * np.pi, R)
+        d1 = np.stack([np.cos(psi), np.sin(psi), np.zeros(R)], axis=1)
+    x, Q = _straight_rods(n_elem, rest_len, base, d3, d1)
     I = np.pi * radius ** 4 / 4
     phase = rng.uniform(0.0, 2 * np.pi, R)
     amp = _uniform(R, amp_factor * youngs * I / length)

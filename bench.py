@@ -211,6 +211,64 @@ def _e2e(s, p, dt, K, world, dist, barrier):
     return e2e
 
 
+def _surrogate_speedup(train_steps: int):
+    """Surrogate speed-up at the tip-error bound: the 64 x 64 carpet of 50-element rods from rest
+    over 10^4 fine steps of 1e-5 s (200 calls of 50 steps), plain GPU step vs the checked
+    rollout (64 sampled rods against a shadow system every 10 calls, plain-step redo above the
+    bound); the network is first trained by the library's kernels (default recipe)."""
+    import time
+
+    import torch
+    import rodgen
+    from paper_2605_13766_gb300 import RodSystem
+    from paper_2605_13766_gb300 import surrogate as S
+    sur, info = S.train_default(steps=train_steps)
+    p = rodgen.cilia_carpet(side=64, n=50)
+    dt, W, n_calls = 1e-5, 50, 200
+    s = RodSystem(p)
+    s.set_state(*p.state())
+    ref = {}
+    for k in range(1, 11):
+        s.step(20 * W, dt)
+        ref[20 * k] = s.get_state()[0]
+    s.set_state(*p.state())
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s.torch_stream)
+    s.step_async(n_calls * W, dt)
+    e1.record(s.torch_stream)
+    s.sync()
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) / 1e3
+    s.close()
+    net = RodSystem(p)
+    net.set_state(*p.state())
+    worst = 0.0
+    for k in range(1, 11):
+        sur.apply(net, 20)
+        worst = max(worst, float(S.tip_error(p, net.get_state()[0], ref[20 * k]).max()))
+    net.close()
+    warm = S.CheckedRollout(sur, p, n_sample=64, seed=1)
+    warm.run(2, check_every=1, bound=1.0)
+    warm.close()
+    ro = S.CheckedRollout(sur, p, n_sample=64, seed=1)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    stats = ro.run(n_calls, check_every=10, bound=S.DEFAULT_CHECK_BOUND)
+    torch.cuda.synchronize()
+    t_sur = time.perf_counter() - t
+    final = float(S.tip_error(p, ro.system.get_state()[0], ref[n_calls]).max())
+    ro.close()
+    el = p.n_elems * n_calls * W
+    return {"workload": "cilia carpet 64x64 rods x 50 elements, 10^4 steps of 1e-5 s (200 calls of 50 steps)",
+            "speedup": t_plain / t_sur, "plain_elem_steps_per_s": el / t_plain,
+            "surrogate_elem_steps_per_s": el / t_sur, "max_tip_err_network_every_20_calls": worst,
+            "final_tip_err_checked_rollout": final, "err_unit": "|x_tip - x_tip(plain)| / L, max over rods",
+            "bound": 1e-3, "check_bound_sampled": S.DEFAULT_CHECK_BOUND, "rollout": stats,
+            "timing": "plain: CUDA events on its stream; rollout: host wall clock around the whole checked rollout",
+            "training": info, "dtype": "bf16 tensor cores (mma.sync), FP32 accumulation, FP64 state"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -220,6 +278,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--surrogate-train-steps", type=int, default=15000)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -303,6 +363,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = _cpu_baseline(p, dt, desc, args.workload)
+    sur = None
+    if rank == 0 and world == 1 and not args.no_surrogate:
+        sur = _surrogate_speedup(args.surrogate_train_steps)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -311,7 +374,8 @@ def main():
                 "config": dict(desc, parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
                                l2="state (196 MB) larger than L2, no flush needed" if args.workload == "packing"
                                else "state L2/smem resident"),
-                "clocks": clk, "gpu_launches": launches, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu}
+                "clocks": clk, "gpu_launches": launches, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+                "surrogate": sur}
         print(json.dumps(line), flush=True)
     s.close()
     if dist is not None:

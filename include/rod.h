@@ -72,7 +72,31 @@ typedef struct {
   const double* act_phase;    /* [n_rods] phi (read when act_amp is set) */
   const double* elem_couple;  /* [3*E] or NULL: constant local couple per element */
   void* cuda_stream;          /* cudaStream_t to run on, or NULL for a library-created stream */
+  /* magnetic couple of magnetized filaments (Methods, Eq. 2): element couple rl (m x (Q b(t))),
+   * b(t) = field_b0 + field_bc cos(field_omega t) + field_bs sin(field_omega t) (lab frame, T) */
+  const double* magnetization;  /* [3*E] or NULL: m per unit reference length, local frame (A m) */
+  double field_b0[3];
+  double field_bc[3];
+  double field_bs[3];
+  double field_omega;           /* rad/s */
+  /* travelling-wave muscle couples (internal, net zero): at interior Voronoi point k of rod r,
+   * tau_k = A sin(2 pi t / T - 2 pi s_k / lambda + phi) about local d1, s_k the rest arc length
+   * of that point; element i receives tau_{i-1} - tau_i */
+  const double* muscle_amp;        /* [n_rods] or NULL: A (N m) */
+  const double* muscle_period;     /* [n_rods] T > 0 (s) */
+  const double* muscle_wavelength; /* [n_rods] lambda > 0 (m) */
+  const double* muscle_phase;      /* [n_rods] phi */
+  /* walls: half-spaces n . (x - p - u t) >= r for the node spheres of radius r (the rod's);
+   * normal force max(0, wall_k delta - wall_c v_rel . n) n and regularised Coulomb friction
+   * -wall_mu f_n v_t / max(|v_t|, wall_vslip) on every penetrating node */
+  int32_t n_walls;              /* 0 .. ROD_MAX_WALLS */
+  const double* wall_point;     /* [n_walls][3] p (m) */
+  const double* wall_normal;    /* [n_walls][3] unit n */
+  const double* wall_velocity;  /* [n_walls][3] u (m/s) or NULL (fixed walls) */
+  double wall_k, wall_c, wall_mu, wall_vslip;
 } rod_system_desc;
+
+#define ROD_MAX_WALLS 8
 
 /* Create a system; validates the description (ROD_ERR_ARG with a message on failure).
  * Rods longer than rod_max_elements_per_rod() are rejected. */
@@ -116,6 +140,12 @@ rod_status rod_system_sync(rod_system* sys);
  * are clamped into the boundary cells, which keeps the pair search exact). */
 rod_status rod_system_contact_config(rod_system* sys, int enable, double k, double c, double cell_size);
 
+/* Rod-rod friction (Results, "Fibrous granular materials": normal force and friction): at a
+ * contact with normal force f_n the tangential force -mu f_n v_t / max(|v_t|, v_slip) acts at
+ * the closest points (v_t: the tangential relative velocity), split onto the nodes like the
+ * normal force.  mu = 0 turns it off.  ROD_ERR_ARG for mu < 0 or, with mu > 0, v_slip <= 0. */
+rod_status rod_system_friction(rod_system* sys, double mu, double v_slip);
+
 /* Right-hand side at the current state and time t: node accelerations acc_v [3*N] and
  * element angular accelerations acc_w [3*E] (constraints on rates applied: clamped node 0
  * and element 0 read zero), contact forces included when enabled.  Device pointers. */
@@ -130,7 +160,9 @@ rod_status rod_system_contact_forces(rod_system* sys, double* f);
 rod_status rod_system_set_launch(rod_system* sys, int32_t elems_per_block, int32_t threads_per_block);
 rod_status rod_system_get_launch(const rod_system* sys, int32_t* elems_per_block, int32_t* threads_per_block);
 
-/* Differentiation (hand-written adjoint of the step; contact must be off).
+/* Differentiation (hand-written adjoint of the step; contact, walls and the magnetic couple
+ * must be off: their state derivatives are not in the reverse sweep; muscle couples depend
+ * on time only and are covered).
  * rod_system_set_params replaces the rest curvature [3*V] and/or the element couples [3*E]
  * (NULL leaves one unchanged; on_device as for set_state).
  * rod_system_forward_checkpointed advances n_steps steps of dt from the current state, one

@@ -62,6 +62,25 @@ class _Params(C.Structure):
         ("contact_c", C.c_double),
         ("cell_size", C.c_double),
         ("broad_phase", C.c_int32),
+        ("magnetization", C.c_void_p),
+        ("field_b0", C.c_double * 3),
+        ("field_bc", C.c_double * 3),
+        ("field_bs", C.c_double * 3),
+        ("field_omega", C.c_double),
+        ("muscle_amp", C.c_void_p),
+        ("muscle_period", C.c_void_p),
+        ("muscle_wavelength", C.c_void_p),
+        ("muscle_phase", C.c_void_p),
+        ("contact_mu", C.c_double),
+        ("contact_vslip", C.c_double),
+        ("n_walls", C.c_int32),
+        ("wall_point", C.c_void_p),
+        ("wall_normal", C.c_void_p),
+        ("wall_velocity", C.c_void_p),
+        ("wall_k", C.c_double),
+        ("wall_c", C.c_double),
+        ("wall_mu", C.c_double),
+        ("wall_vslip", C.c_double),
     ]
 
 
@@ -99,6 +118,10 @@ def _ptr(a):
     return None if a is None else a.ctypes.data
 
 
+def _opt(a):
+    return None if a is None else _f64(a)
+
+
 class Oracle:
     """Oracle bound to one ``rodgen.RodProblem`` description (parameters, not state)."""
 
@@ -122,14 +145,32 @@ class Oracle:
             "act_period": None if p.act_period is None else _f64(p.act_period),
             "act_phase": None if p.act_phase is None else _f64(p.act_phase),
             "elem_couple": None if p.elem_couple is None else _f64(p.elem_couple),
+            "magnetization": _opt(getattr(p, "magnetization", None)),
+            "muscle_amp": _opt(getattr(p, "muscle_amp", None)),
+            "muscle_period": _opt(getattr(p, "muscle_period", None)),
+            "muscle_wavelength": _opt(getattr(p, "muscle_wavelength", None)),
+            "muscle_phase": _opt(getattr(p, "muscle_phase", None)),
+            "wall_point": _opt(getattr(p, "wall_point", None)),
+            "wall_normal": _opt(getattr(p, "wall_normal", None)),
+            "wall_velocity": _opt(getattr(p, "wall_velocity", None)),
         }
         k = self._keep
         prm = _Params()
         prm.n_rods = p.n_rods
         for name in ("n_elem", "rest_len", "radius", "youngs", "shear_mod", "density", "clamp_base",
                      "rest_kappa", "rest_sigma", "tip_force", "act_amp", "act_period", "act_phase",
-                     "elem_couple"):
+                     "elem_couple", "magnetization", "muscle_amp", "muscle_period", "muscle_wavelength",
+                     "muscle_phase", "wall_point", "wall_normal", "wall_velocity"):
             setattr(prm, name, _ptr(k[name]))
+        for name in ("field_b0", "field_bc", "field_bs"):
+            setattr(prm, name, (C.c_double * 3)(*[float(g) for g in getattr(p, name, (0.0, 0.0, 0.0))]))
+        prm.field_omega = float(getattr(p, "field_omega", 0.0))
+        prm.contact_mu = float(getattr(p, "contact_mu", 0.0))
+        prm.contact_vslip = float(getattr(p, "contact_vslip", 0.0))
+        wp = k["wall_point"]
+        prm.n_walls = 0 if wp is None else int(wp.size // 3)
+        for name in ("wall_k", "wall_c", "wall_mu", "wall_vslip"):
+            setattr(prm, name, float(getattr(p, name, 0.0)))
         prm.alpha_c = p.alpha_c
         prm.gravity = (C.c_double * 3)(*[float(g) for g in p.gravity])
         prm.nu_damp = p.nu_damp

@@ -216,7 +216,33 @@ static int validate(const orc_params* p) {
   if (p->act_amp)
     for (int r = 0; r < p->n_rods; ++r)
       if (!(p->act_period[r] > 0)) return fail("actuation period must be positive");
+  if (p->muscle_amp)
+    for (int r = 0; r < p->n_rods; ++r)
+      if (!(p->muscle_period[r] > 0) || !(p->muscle_wavelength[r] > 0))
+        return fail("muscle period and wavelength must be positive");
+  if ((p->contact_mu < 0) || (p->contact_mu > 0 && !(p->contact_vslip > 0)))
+    return fail("friction needs mu >= 0 and a positive slip velocity");
+  if (p->n_walls < 0 || (p->n_walls > 0 && (!p->wall_point || !p->wall_normal)))
+    return fail("walls need points and normals");
+  for (int k = 0; k < p->n_walls; ++k) {
+    const double* nn = p->wall_normal + 3 * k;
+    if (fabs(dot3(nn, nn) - 1.0) > 1e-12) return fail("wall normals must be unit vectors");
+  }
+  if (p->n_walls > 0 && ((p->wall_mu < 0) || (p->wall_mu > 0 && !(p->wall_vslip > 0))))
+    return fail("wall friction needs mu >= 0 and a positive slip velocity");
   return 0;
+}
+
+/* Regularised Coulomb friction at a contact with normal force fn >= 0 along unit nrm and
+ * relative velocity vrel: -mu fn v_t / max(|v_t|, v_slip), v_t = vrel - (vrel . nrm) nrm
+ * (Coulomb above the slip velocity, viscous below it; no tangential spring, so no history). */
+static void friction_force(double mu, double vslip, double fn, const double nrm[3], const double vrel[3],
+                           double ft[3]) {
+  double vn = dot3(vrel, nrm), vt[3];
+  for (int c = 0; c < 3; ++c) vt[c] = vrel[c] - vn * nrm[c];
+  double sp = sqrt(dot3(vt, vt));
+  double den = sp > vslip ? sp : vslip;
+  for (int c = 0; c < 3; ++c) ft[c] = (mu > 0.0 && fn > 0.0) ? (g_mut == 25 ? 1.0 : -1.0) * mu * fn * vt[c] / den : 0.0;
 }
 
 /* ---------------------------------------------------------------- a3-a5: strains */
@@ -389,6 +415,11 @@ static int pair_force(const orc_params* p, const seg_map* m, const double* x, co
     ld3(v, m->N, nb + 1, vb1);
     for (int c = 0; c < 3; ++c) vrel[c] = ((1.0 - s) * va0[c] + s * va1[c]) - ((1.0 - u) * vb0[c] + u * vb1[c]);
     fmag = fmag - (g_mut == 11 ? -1.0 : 1.0) * p->contact_c * dot3(vrel, nrm);
+    if (fmag < 0.0) fmag = 0.0;
+    double ft[3];
+    friction_force(p->contact_mu, p->contact_vslip, fmag, nrm, vrel, ft);
+    for (int c = 0; c < 3; ++c) f[c] = fmag * nrm[c] + ft[c];
+    return 1;
   }
   if (fmag < 0.0) fmag = 0.0;
   for (int c = 0; c < 3; ++c) f[c] = fmag * nrm[c];
@@ -677,6 +708,10 @@ int orc_rhs(const orc_params* p, double t, const double* x, const double* v, con
     }
     /* element angular accelerations */
     int iact = act_element(p, r);
+    double bt[3] = {0.0, 0.0, 0.0};
+    if (p->magnetization)
+      for (int c = 0; c < 3; ++c)
+        bt[c] = p->field_b0[c] + p->field_bc[c] * cos(p->field_omega * t) + p->field_bs[c] * sin(p->field_omega * t);
     for (int i = 0; i < g.n; ++i) {
       int64_t ie = g.elem0 + i;
       double tot[3], wi[3];
@@ -693,6 +728,27 @@ int orc_rhs(const orc_params* p, double t, const double* x, const double* v, con
       }
       if (p->act_amp && i == iact)
         tot[0] += p->act_amp[r] * sin(2.0 * M_PI * t / p->act_period[r] + p->act_phase[r]);
+      if (p->magnetization) {
+        /* rl (m x (Q b)) with Q b the field in the element's frame */
+        double M[9], qb[3], mi[3], cmag[3];
+        ldQ(Q, E, ie, M);
+        for (int a = 0; a < 3; ++a)
+          qb[a] = (g_mut == 22) ? M[a] * bt[0] + M[3 + a] * bt[1] + M[6 + a] * bt[2]
+                                : M[3 * a] * bt[0] + M[3 * a + 1] * bt[1] + M[3 * a + 2] * bt[2];
+        ld3(p->magnetization, E, ie, mi);
+        cross3(mi, qb, cmag);
+        for (int c = 0; c < 3; ++c) tot[c] += rl * cmag[c];
+      }
+      if (p->muscle_amp && g.n >= 2) {
+        /* tau_k at the Voronoi points on both sides of element i (k = i - 1 and k = i) */
+        double s_right = 0.0;
+        for (int q = 0; q <= i; ++q) s_right += p->rest_len[g.elem0 + q];   /* arc length of node i+1 */
+        double s_left = s_right - rl;                                         /* arc length of node i */
+        double om = 2.0 * M_PI / p->muscle_period[r], kw = 2.0 * M_PI / p->muscle_wavelength[r];
+        double tr = (i <= g.n - 2) ? p->muscle_amp[r] * sin(om * t - kw * s_right + p->muscle_phase[r]) : 0.0;
+        double tl = (i >= 1) ? p->muscle_amp[r] * sin(om * t - kw * s_left + p->muscle_phase[r]) : 0.0;
+        tot[0] += (g_mut == 23) ? tr - tl : tl - tr;
+      }
       for (int c = 0; c < 3; ++c) acc_w[c * E + ie] = (g_mut == 17 ? 1.0 : dil[ie]) * tot[c] / (K.rho * rl * K.I[c]);
     }
     /* node accelerations */
@@ -712,6 +768,23 @@ int orc_rhs(const orc_params* p, double t, const double* x, const double* v, con
         F[c] += -(p->nu_damp + (g_mut == 21 ? 0.0 : p->stokes_gamma)) * rlN * vj[c];
         F[c] += fc[c * N + jn];
         if (p->tip_force && j == g.n) F[c] += p->tip_force[c * p->n_rods + r];
+      }
+      for (int k = 0; k < p->n_walls; ++k) {
+        /* node sphere of radius r against the half-space n . (x - p - u t) >= 0 */
+        const double* nn = p->wall_normal + 3 * k;
+        double xj[3], d[3], u[3] = {0.0, 0.0, 0.0}, vrel[3];
+        ld3(x, N, jn, xj);
+        if (p->wall_velocity)
+          for (int c = 0; c < 3; ++c) u[c] = p->wall_velocity[3 * k + c];
+        for (int c = 0; c < 3; ++c) d[c] = xj[c] - (p->wall_point[3 * k + c] + u[c] * t);
+        double delta = (g_mut == 24 ? 0.0 : p->radius[r]) - dot3(d, nn);
+        if (!(delta > 0.0)) continue;
+        for (int c = 0; c < 3; ++c) vrel[c] = vj[c] - u[c];
+        double fn = p->wall_k * delta - p->wall_c * dot3(vrel, nn);
+        if (fn < 0.0) fn = 0.0;
+        double ft[3];
+        friction_force(p->wall_mu, p->wall_vslip, fn, nn, vrel, ft);
+        for (int c = 0; c < 3; ++c) F[c] += fn * nn[c] + ft[c];
       }
       for (int c = 0; c < 3; ++c) acc_v[c * N + jn] = F[c] / mass;
     }

@@ -12,7 +12,10 @@
  *   - multi-stage symplectic (Verlet) time integration with kinematic constraints enforced
  *     after every stage (Results, "Performance-oriented software design");
  *   - rod-rod contact by a normal spring-dashpot force (Results, "Fibrous granular materials"),
- *     with an exhaustive O(N^2) broad phase and a uniform-grid broad phase (same section, Fig. 2e).
+ *     with an exhaustive O(N^2) broad phase and a uniform-grid broad phase (same section, Fig. 2e),
+ *     and inter-filament friction (same section);
+ *   - the magnetic couple of magnetized filaments (Methods, Eq. 2), travelling-wave muscle
+ *     couples (Results, active filaments) and rod-wall contact (rod-boundary contact, Results).
  * The discrete scheme (staggered nodes/elements/Voronoi points, difference and averaging
  * operators with zero ghosts, lumped masses) is the standard one of the method paper the
  * authors cite for the discretisation; every place where the paper is silent is a documented
@@ -57,6 +60,29 @@ typedef struct {
   double contact_k, contact_c;  /* spring stiffness, dashpot coefficient */
   double cell_size;             /* <= 0: 2*max radius + current max element length */
   int32_t broad_phase;          /* 0 = exhaustive O(N^2), 1 = uniform cell list */
+  /* magnetic couple (Methods, "Magnetized filaments", Eq. 2): c = m x (Q b(t)) per unit
+   * reference length, element couple rl c; b(t) = b0 + bc cos(omega t) + bs sin(omega t) (lab) */
+  const double* magnetization;  /* 3*E or NULL: m per unit reference length, local frame */
+  double field_b0[3], field_bc[3], field_bs[3];
+  double field_omega;
+  /* travelling-wave muscle couples (the self-activation of the active-filament study): at
+   * interior Voronoi point k of rod r, tau_k = A sin(2 pi t / T - 2 pi s_k / lambda + phi)
+   * about local d1, s_k the rest arc length of that point; element i receives
+   * tau_{i-1} - tau_i (zero outside the rod), so the couples sum to zero along the rod */
+  const double* muscle_amp;        /* n_rods or NULL */
+  const double* muscle_period;     /* n_rods, T > 0 */
+  const double* muscle_wavelength; /* n_rods, lambda > 0 */
+  const double* muscle_phase;      /* n_rods */
+  /* rod-rod friction: regularised Coulomb force -mu f_n v_t / max(|v_t|, v_slip) at the
+   * closest points (v_t: tangential part of the relative velocity), split like the normal force */
+  double contact_mu, contact_vslip;
+  /* walls: half-spaces n . (x - p - u t) >= r of the node spheres (radius r of the rod);
+   * normal force max(0, k delta - c v_rel . n) n, friction as above with the wall's mu, v_slip */
+  int32_t n_walls;
+  const double* wall_point;     /* [n_walls][3] */
+  const double* wall_normal;    /* [n_walls][3], unit */
+  const double* wall_velocity;  /* [n_walls][3] or NULL */
+  double wall_k, wall_c, wall_mu, wall_vslip;
 } orc_params;
 
 /* sizes */

@@ -60,6 +60,23 @@ class RodSystemDesc(C.Structure):
         ("act_phase", C.c_void_p),
         ("elem_couple", C.c_void_p),
         ("cuda_stream", C.c_void_p),
+        ("magnetization", C.c_void_p),
+        ("field_b0", C.c_double * 3),
+        ("field_bc", C.c_double * 3),
+        ("field_bs", C.c_double * 3),
+        ("field_omega", C.c_double),
+        ("muscle_amp", C.c_void_p),
+        ("muscle_period", C.c_void_p),
+        ("muscle_wavelength", C.c_void_p),
+        ("muscle_phase", C.c_void_p),
+        ("n_walls", C.c_int32),
+        ("wall_point", C.c_void_p),
+        ("wall_normal", C.c_void_p),
+        ("wall_velocity", C.c_void_p),
+        ("wall_k", C.c_double),
+        ("wall_c", C.c_double),
+        ("wall_mu", C.c_double),
+        ("wall_vslip", C.c_double),
     ]
 
 
@@ -77,6 +94,7 @@ _SIGNATURES = {
     "rod_system_step_async": ([_P, C.c_int64, C.c_double], C.c_int),
     "rod_system_sync": ([_P], C.c_int),
     "rod_system_contact_config": ([_P, C.c_int, C.c_double, C.c_double, C.c_double], C.c_int),
+    "rod_system_friction": ([_P, C.c_double, C.c_double], C.c_int),
     "rod_system_rhs": ([_P, C.c_double, _P, _P], C.c_int),
     "rod_system_contact_forces": ([_P, _P], C.c_int),
     "rod_system_set_launch": ([_P, C.c_int32, C.c_int32], C.c_int),
@@ -176,6 +194,14 @@ class RodSystem:
             "act_period": _host(getattr(p, "act_period", None)),
             "act_phase": _host(getattr(p, "act_phase", None)),
             "elem_couple": _host(getattr(p, "elem_couple", None)),
+            "magnetization": _host(getattr(p, "magnetization", None)),
+            "muscle_amp": _host(getattr(p, "muscle_amp", None)),
+            "muscle_period": _host(getattr(p, "muscle_period", None)),
+            "muscle_wavelength": _host(getattr(p, "muscle_wavelength", None)),
+            "muscle_phase": _host(getattr(p, "muscle_phase", None)),
+            "wall_point": _host(getattr(p, "wall_point", None)),
+            "wall_normal": _host(getattr(p, "wall_normal", None)),
+            "wall_velocity": _host(getattr(p, "wall_velocity", None)),
         }
         d = RodSystemDesc()
         d.n_rods = int(keep["n_elem"].shape[0])
@@ -185,6 +211,12 @@ class RodSystem:
         d.gravity = (C.c_double * 3)(*[float(g) for g in getattr(p, "gravity", (0.0, 0.0, 0.0))])
         d.nu_damp = float(getattr(p, "nu_damp", 0.0))
         d.stokes_gamma = float(getattr(p, "stokes_gamma", 0.0))
+        for name in ("field_b0", "field_bc", "field_bs"):
+            setattr(d, name, (C.c_double * 3)(*[float(g) for g in getattr(p, name, (0.0, 0.0, 0.0))]))
+        d.field_omega = float(getattr(p, "field_omega", 0.0))
+        d.n_walls = 0 if keep["wall_point"] is None else int(keep["wall_point"].size // 3)
+        for name in ("wall_k", "wall_c", "wall_mu", "wall_vslip"):
+            setattr(d, name, float(getattr(p, name, 0.0)))
         self.torch_stream = None
         if stream is None and use_torch_stream:
             import torch
@@ -204,6 +236,8 @@ class RodSystem:
         self.n_rods = d.n_rods
         if getattr(p, "contact", False):
             self.contact_config(True, p.contact_k, p.contact_c, p.cell_size)
+        if float(getattr(p, "contact_mu", 0.0)) > 0:
+            self.friction(p.contact_mu, p.contact_vslip)
 
     # -- lifetime
     def close(self):
@@ -288,6 +322,10 @@ class RodSystem:
                                                   float(cell_size)))
 
     # -- debug / parity entry points (device outputs)
+    def friction(self, mu: float, v_slip: float):
+        """Rod-rod friction: -mu f_n v_t / max(|v_t|, v_slip) at every contact."""
+        _check(self.lib.rod_system_friction(self.handle, float(mu), float(v_slip)))
+
     def rhs(self, t: float = 0.0):
         import torch
         av = torch.empty((3, self.n_nodes), dtype=torch.float64, device="cuda")

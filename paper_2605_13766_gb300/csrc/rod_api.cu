@@ -164,6 +164,11 @@ struct rod_system {
   // constants
   DevBuf<double> rest_len, inv_rl, inv_2D, Dhat, inv_m;
   DevBuf<double> rest_kappa, rest_sigma, elem_couple;
+  DevBuf<double> magnet, arc0;  // magnetisation [3E], rest arc length of each element's first node [E]
+  double field_b0[3] = {0, 0, 0}, field_bc[3] = {0, 0, 0}, field_bs[3] = {0, 0, 0}, field_omega = 0.0;
+  int n_walls = 0;
+  double wall_p[kMaxWalls][3] = {}, wall_n[kMaxWalls][3] = {}, wall_u[kMaxWalls][3] = {};
+  double wall_k = 0.0, wall_c = 0.0, wall_mu = 0.0, wall_vslip = 0.0;
   DevBuf<double> clamp_x, clamp_Q;
   DevBuf<RodConst> rods;
   std::vector<RodConst> rods_h;
@@ -277,6 +282,25 @@ StepParams make_params(rod_system* s) {
   for (int c = 0; c < 3; ++c) P.gravity[c] = s->gravity[c];
   P.has_gravity = s->has_gravity;
   P.has_act = s->has_act;
+  P.magnet = s->magnet.p;
+  for (int c = 0; c < 3; ++c) {
+    P.field_b0[c] = s->field_b0[c];
+    P.field_bc[c] = s->field_bc[c];
+    P.field_bs[c] = s->field_bs[c];
+  }
+  P.field_omega = s->field_omega;
+  P.arc0 = s->arc0.p;
+  P.n_walls = s->n_walls;
+  for (int k = 0; k < s->n_walls; ++k)
+    for (int c = 0; c < 3; ++c) {
+      P.wall_p[k][c] = s->wall_p[k][c];
+      P.wall_n[k][c] = s->wall_n[k][c];
+      P.wall_u[k][c] = s->wall_u[k][c];
+    }
+  P.wall_k = s->wall_k;
+  P.wall_c = s->wall_c;
+  P.wall_mu = s->wall_mu;
+  P.wall_vslip = s->wall_vslip;
   P.fseg = nullptr;
   P.err = s->err.p;
   return P;
@@ -461,6 +485,37 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
   if (d->tip_force && !finite_all(d->tip_force, 3 * R)) return fail(ROD_ERR_ARG, "tip_force has non-finite values");
   for (int c = 0; c < 3; ++c)
     if (!std::isfinite(d->gravity[c])) return fail(ROD_ERR_ARG, "gravity must be finite");
+  if (d->magnetization) {
+    if (!finite_all(d->magnetization, 3 * E)) return fail(ROD_ERR_ARG, "magnetization has non-finite values");
+    for (int c = 0; c < 3; ++c)
+      if (!std::isfinite(d->field_b0[c]) || !std::isfinite(d->field_bc[c]) || !std::isfinite(d->field_bs[c]))
+        return fail(ROD_ERR_ARG, "the magnetic field must be finite");
+    if (!std::isfinite(d->field_omega)) return fail(ROD_ERR_ARG, "field_omega must be finite");
+  }
+  if (d->muscle_amp) {
+    if (!d->muscle_period || !d->muscle_wavelength || !d->muscle_phase)
+      return fail(ROD_ERR_ARG, "muscle_amp needs muscle_period, muscle_wavelength and muscle_phase");
+    for (int r = 0; r < R; ++r)
+      if (!std::isfinite(d->muscle_amp[r]) || !(d->muscle_period[r] > 0) || !(d->muscle_wavelength[r] > 0) ||
+          !std::isfinite(d->muscle_period[r]) || !std::isfinite(d->muscle_wavelength[r]) ||
+          !std::isfinite(d->muscle_phase[r]))
+        return fail(ROD_ERR_ARG, "rod %d: muscle period and wavelength must be positive, amplitude/phase finite", r);
+  }
+  if (d->n_walls < 0 || d->n_walls > kMaxWalls) return fail(ROD_ERR_ARG, "n_walls must be 0..%d", kMaxWalls);
+  if (d->n_walls > 0) {
+    if (!d->wall_point || !d->wall_normal) return fail(ROD_ERR_ARG, "walls need wall_point and wall_normal");
+    for (int k = 0; k < d->n_walls; ++k) {
+      const double* nn = d->wall_normal + 3 * k;
+      if (!finite_all(d->wall_point + 3 * k, 3) || !finite_all(nn, 3) ||
+          (d->wall_velocity && !finite_all(d->wall_velocity + 3 * k, 3)))
+        return fail(ROD_ERR_ARG, "wall %d: non-finite point, normal or velocity", k);
+      if (std::fabs(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2] - 1.0) > 1e-12)
+        return fail(ROD_ERR_ARG, "wall %d: the normal must be a unit vector", k);
+    }
+    if (!(d->wall_k >= 0) || !(d->wall_c >= 0) || !(d->wall_mu >= 0) || !std::isfinite(d->wall_k) ||
+        !std::isfinite(d->wall_c) || !std::isfinite(d->wall_mu) || (d->wall_mu > 0 && !(d->wall_vslip > 0)))
+      return fail(ROD_ERR_ARG, "walls need k, c, mu >= 0 and, with friction, a positive slip velocity");
+  }
 
   rod_system* s = new rod_system();
   s->hook.fn = &Profiler::hook;
@@ -520,11 +575,36 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
     }
     if (d->tip_force)
       for (int c = 0; c < 3; ++c) rc.tip[c] = d->tip_force[c * R + r];
+    if (d->muscle_amp && d->muscle_amp[r] != 0.0) {
+      rc.muscle_amp = d->muscle_amp[r];
+      rc.muscle_omega = 2.0 * kPi / d->muscle_period[r];
+      rc.muscle_k = 2.0 * kPi / d->muscle_wavelength[r];
+      rc.muscle_phase = d->muscle_phase[r];
+    }
     e0 += rc.n;
     n0 += rc.n + 1;
   }
   s->has_act = any_act;
-  for (int c = 0; c < 3; ++c) s->gravity[c] = d->gravity[c];
+  for (int c = 0; c < 3; ++c) {
+    s->gravity[c] = d->gravity[c];
+    if (d->magnetization) {
+      s->field_b0[c] = d->field_b0[c];
+      s->field_bc[c] = d->field_bc[c];
+      s->field_bs[c] = d->field_bs[c];
+    }
+  }
+  s->field_omega = d->magnetization ? d->field_omega : 0.0;
+  s->n_walls = d->n_walls;
+  for (int k = 0; k < d->n_walls; ++k)
+    for (int c = 0; c < 3; ++c) {
+      s->wall_p[k][c] = d->wall_point[3 * k + c];
+      s->wall_n[k][c] = d->wall_normal[3 * k + c];
+      s->wall_u[k][c] = d->wall_velocity ? d->wall_velocity[3 * k + c] : 0.0;
+    }
+  s->wall_k = d->wall_k;
+  s->wall_c = d->wall_c;
+  s->wall_mu = d->wall_mu;
+  s->wall_vslip = d->wall_vslip;
   s->has_gravity = d->gravity[0] != 0.0 || d->gravity[1] != 0.0 || d->gravity[2] != 0.0;
 
   // per-item constants
@@ -564,6 +644,22 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
     return cleanup(fail(ROD_ERR_CUDA, "copy failed: %s", cudaGetErrorString(ce)));
   if (d->elem_couple && (ce = up(s->elem_couple, d->elem_couple, 3 * E)))
     return cleanup(fail(ROD_ERR_CUDA, "copy failed: %s", cudaGetErrorString(ce)));
+  if (d->magnetization && (ce = up(s->magnet, d->magnetization, 3 * E)))
+    return cleanup(fail(ROD_ERR_CUDA, "copy failed: %s", cudaGetErrorString(ce)));
+  bool any_muscle = false;
+  for (int r = 0; r < R; ++r) any_muscle = any_muscle || s->rods_h[r].muscle_amp != 0.0;
+  if (any_muscle) {
+    // rest arc length of every element's first node, summed along each rod in order
+    std::vector<double> arc(E);
+    for (int r = 0; r < R; ++r) {
+      double acc = 0.0;
+      for (int i = 0; i < s->rods_h[r].n; ++i) {
+        arc[s->rods_h[r].elem0 + i] = acc;
+        acc += d->rest_len[s->rods_h[r].elem0 + i];
+      }
+    }
+    if ((ce = up(s->arc0, arc.data(), E))) return cleanup(fail(ROD_ERR_CUDA, "copy failed: %s", cudaGetErrorString(ce)));
+  }
   if ((ce = s->t_dev.alloc(1)) || (ce = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking)))
     return cleanup(fail(ROD_ERR_CUDA, "allocation failed: %s", cudaGetErrorString(ce)));
   if ((ce = cudaMemset(s->err.p, 0, sizeof(int))) || (ce = cudaMallocHost(&s->err_host, sizeof(int))))
@@ -590,6 +686,8 @@ rod_status rod_system_destroy(rod_system* s) {
   s->rest_kappa.release();
   s->rest_sigma.release();
   s->elem_couple.release();
+  s->magnet.release();
+  s->arc0.release();
   s->clamp_x.release();
   s->clamp_Q.release();
   s->rods.release();
@@ -735,6 +833,15 @@ rod_status rod_system_contact_config(rod_system* s, int enable, double k, double
   s->contact.c = c;
   s->contact.cell_size = cell_size;
   s->contact.grid_valid = false;
+  return ROD_OK;
+}
+
+rod_status rod_system_friction(rod_system* s, double mu, double v_slip) {
+  if (!s) return fail(ROD_ERR_ARG, "null system");
+  if (!(mu >= 0) || !std::isfinite(mu) || (mu > 0 && (!(v_slip > 0) || !std::isfinite(v_slip))))
+    return fail(ROD_ERR_ARG, "friction needs mu >= 0 and, with mu > 0, a finite slip velocity > 0");
+  s->contact.mu = mu;
+  s->contact.vslip = mu > 0 ? v_slip : 0.0;
   return ROD_OK;
 }
 
@@ -922,6 +1029,8 @@ rod_status rod_system_forward_checkpointed(rod_system* s, int64_t n_steps, doubl
   if (!s) return fail(ROD_ERR_ARG, "null system");
   if (!s->state_set) return fail(ROD_ERR_STATE, "no state has been set");
   if (s->contact.enabled) return fail(ROD_ERR_STATE, "the adjoint does not include contact; disable it first");
+  if (s->magnet.p || s->n_walls > 0)
+    return fail(ROD_ERR_STATE, "the adjoint does not include the magnetic couple or walls");
   if (n_steps < 1 || every < 1 || !(dt > 0) || !std::isfinite(dt)) return fail(ROD_ERR_ARG, "need n_steps, every >= 1 and dt > 0");
   const int64_t ss = state_size(s);
   const int64_t nck = (n_steps + every - 1) / every;
@@ -1077,6 +1186,7 @@ rod_status system_view(rod_system* s, SysView* out) {
   out->rods = s->rods.p;
   out->rest_len = s->rest_len.p;
   out->contact = s->contact.enabled;
+  out->n_packs = s->n_packs;
   out->stream = s->stream;
   out->t = &s->t;
   return ROD_OK;

@@ -256,6 +256,7 @@ struct ContactArgs {
   int64_t N, E;
   int dim[3];
   double k, c;
+  double mu, vslip;
 };
 
 struct PairForce {
@@ -290,22 +291,33 @@ __device__ __noinline__ PairForce pair_force(const ContactArgs& A, int a, int ra
   const double delta = (rada + radb) - d;
   if (!(delta > 0.0) || d == 0.0) return out;
   const double nrm[3] = {dvec[0] / d, dvec[1] / d, dvec[2] / d};
-  double vrel = 0.0;
+  double vrel = 0.0, vr[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const double vp0 = A.v[c * A.N + nP], vp1 = A.v[c * A.N + nP + 1];
     const double vq0 = A.v[c * A.N + nQ], vq1 = A.v[c * A.N + nQ + 1];
-    const double vr = ((1.0 - s) * vp0 + s * vp1) - ((1.0 - u) * vq0 + u * vq1);
-    vrel += vr * nrm[c];
+    vr[c] = ((1.0 - s) * vp0 + s * vp1) - ((1.0 - u) * vq0 + u * vq1);
+    vrel += vr[c] * nrm[c];
   }
   double fmag = A.k * delta - A.c * vrel;
   if (fmag < 0.0) fmag = 0.0;
-  // force on the first segment of the pair is +fmag n, on the second -fmag n
+  // friction: -mu fmag v_t / max(|v_t|, v_slip) with v_t the tangential relative velocity
+  double ft[3] = {0.0, 0.0, 0.0};
+  if (A.mu > 0.0 && fmag > 0.0) {
+    double vt[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) vt[c] = vr[c] - vrel * nrm[c];
+    const double sp = sqrt(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
+    const double fr = -A.mu * fmag / fmax(sp, A.vslip);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ft[c] = fr * vt[c];
+  }
+  // force on the first segment of the pair is +(fmag n + ft), on the second the opposite
   const double wa = first ? (1.0 - s) : -(1.0 - u);
   const double wb = first ? s : -u;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const double fc = fmag * nrm[c];
+    const double fc = fmag * nrm[c] + ft[c];
     out.fa[c] = wa * fc;
     out.fb[c] = wb * fc;
   }
@@ -566,6 +578,8 @@ cudaError_t contact_compute(ContactState& cs, const double* x, const double* v, 
   for (int c = 0; c < 3; ++c) A.dim[c] = cs.dim[c];
   A.k = cs.k;
   A.c = cs.c;
+  A.mu = cs.mu;
+  A.vslip = cs.vslip;
   A.err = err;
   hook.before(K_CONTACT_GATHER, st);
   gather_kernel<<<(E + 255) / 256, 256, 0, st>>>(A);

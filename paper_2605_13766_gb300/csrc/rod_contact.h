@@ -14,6 +14,7 @@ namespace rod {
 struct ContactState {
   bool enabled = false;
   double k = 0.0, c = 0.0, cell_size = 0.0;
+  double mu = 0.0, vslip = 0.0;  // regularised Coulomb friction (mu = 0: none)
   bool grid_valid = false;
   // grid over segment midpoints; midpoints outside are clamped into the boundary cells
   double lo[3] = {0, 0, 0};

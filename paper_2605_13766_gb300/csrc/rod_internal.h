@@ -34,7 +34,13 @@ struct RodConst {
   int32_t clamp;        // 1: node 0 + element 0 held
   int32_t act_elem;     // rod-local element carrying the base couple (-1: none)
   int32_t pad;
+  double muscle_amp;    // travelling-wave muscle couple amplitude (0: none)
+  double muscle_omega;  // 2 pi / T
+  double muscle_k;      // 2 pi / lambda
+  double muscle_phase;
 };
+
+constexpr int kMaxWalls = 8;
 
 // A pack: consecutive rods processed by one thread block.
 struct Pack {
@@ -70,6 +76,15 @@ struct StepParams {
   double gravity[3];
   int32_t has_gravity;
   int32_t has_act;
+  // magnetic couple rl (m x (Q b(t))): m per unit reference length (local) [3E] or null
+  const double* magnet;
+  double field_b0[3], field_bc[3], field_bs[3], field_omega;
+  // travelling-wave muscle couples: rest arc length of each element's first node [E] (null: none)
+  const double* arc0;
+  // walls
+  int32_t n_walls;
+  double wall_p[kMaxWalls][3], wall_n[kMaxWalls][3], wall_u[kMaxWalls][3];
+  double wall_k, wall_c, wall_mu, wall_vslip;
   // contact: per-segment node forces [6E] (force on node a = first node, node b), or null
   const double* fseg;
   int* err;                   // device error word

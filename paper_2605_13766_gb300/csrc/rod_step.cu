@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, 
 
 size_t step_smem_bytes(const LaunchShape& s) {
   const size_t CE = s.cap_elems, CR = s.cap_rods, CN = CE + CR, CV = CE;
-  const size_t doubles = 3 * CN + 3 * CN + 9 * CE + 3 * CE + 3 * CE + 3 * CE + CE + CE + 3 * CV + 3 * CV + CE + CN + CR;
+  const size_t doubles = 3 * CN + 3 * CN + 9 * CE + 3 * CE + 3 * CE + 3 * CE + CE + CE + 3 * CV + 3 * CV + CE + CN + CR + 4;
   const size_t ints = CR + 1;
   const size_t shorts = CE + CN + CV;
   return doubles * sizeof(double) + ints * sizeof(int) + shorts * sizeof(short) + 16;

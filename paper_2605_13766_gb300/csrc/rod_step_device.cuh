@@ -110,6 +110,7 @@ struct Smem {
   double *NF, *TA, *ELL, *EDIL; // element work
   double *PP, *TT;              // Voronoi work
   double *IRL, *IM, *ACT;       // constants, per-rod actuation value
+  double* BF;                   // [4] magnetic field b(t) of the step and its force time t
   int* rel0;                    // [CR+1] first element of each rod (pack-local)
   short *erod, *nrod, *vrod;    // pack-local rod of each element / node / Voronoi point
   int CE, CN, CV, CR;
@@ -135,6 +136,7 @@ __device__ __forceinline__ Smem carve(double* base, const LaunchShape& S) {
   m.IRL = p;  p += m.CE;
   m.IM = p;   p += m.CN;
   m.ACT = p;  p += m.CR;
+  m.BF = p;   p += 4;
   m.rel0 = reinterpret_cast<int*>(p);
   m.erod = reinterpret_cast<short*>(m.rel0 + m.CR + 1);
   m.nrod = m.erod + m.CE;
@@ -270,6 +272,25 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
       for (int c = 0; c < 3; ++c) tc[c] += __ldg(P.elem_couple + c * P.E + ge);
     }
     if (P.has_act && (i - m.rel0[r]) == rc->act_elem) tc[0] += m.ACT[r];
+    if (P.magnet) {
+      // magnetic couple rl (m x (Q b)), Q b: the field in the element's frame
+      double qb[3], mg[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) qb[a] = fma(q[3 * a], m.BF[0], fma(q[3 * a + 1], m.BF[1], q[3 * a + 2] * m.BF[2]));
+#pragma unroll
+      for (int c = 0; c < 3; ++c) mg[c] = rl * __ldg(P.magnet + c * P.E + ge);
+      tc[0] += fma(mg[1], qb[2], -mg[2] * qb[1]);
+      tc[1] += fma(mg[2], qb[0], -mg[0] * qb[2]);
+      tc[2] += fma(mg[0], qb[1], -mg[1] * qb[0]);
+    }
+    if (P.arc0 && rc->muscle_amp != 0.0) {
+      // muscle couples about d1 at the Voronoi points on both sides: tau_{i-1} - tau_i
+      const int li = i - m.rel0[r], nr = m.rel0[r + 1] - m.rel0[r];
+      const double t = m.BF[3], sl = __ldg(P.arc0 + ge), sr = sl + rl;
+      const double tr = (li <= nr - 2) ? rc->muscle_amp * sin(rc->muscle_omega * t - rc->muscle_k * sr + rc->muscle_phase) : 0.0;
+      const double tl = (li >= 1) ? rc->muscle_amp * sin(rc->muscle_omega * t - rc->muscle_k * sl + rc->muscle_phase) : 0.0;
+      tc[0] += tl - tr;
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) m.TA[c * m.CE + i] = tc[c];
     m.ELL[i] = ell;
@@ -419,6 +440,29 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
         F[c] += fc;
       }
     }
+    for (int k = 0; k < P.n_walls; ++k) {
+      // node sphere (radius of the rod) against the half-space n . (x - p - u t) >= 0
+      const double t = m.BF[3];
+      double d[3], vr[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        d[c] = m.X[c * m.CN + j] - fma(P.wall_u[k][c], t, P.wall_p[k][c]);
+        vr[c] = m.VN[c * m.CN + j] - P.wall_u[k][c];
+      }
+      const double* nn = P.wall_n[k];
+      const double delta = rc->radius - fma(d[0], nn[0], fma(d[1], nn[1], d[2] * nn[2]));
+      if (!(delta > 0.0)) continue;
+      const double vn = fma(vr[0], nn[0], fma(vr[1], nn[1], vr[2] * nn[2]));
+      double fn = P.wall_k * delta - P.wall_c * vn;
+      if (fn < 0.0) fn = 0.0;
+      double vt[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) vt[c] = vr[c] - vn * nn[c];
+      const double sp = sqrt(fma(vt[0], vt[0], fma(vt[1], vt[1], vt[2] * vt[2])));
+      const double fr = (P.wall_mu > 0.0 && fn > 0.0) ? -P.wall_mu * fn / fmax(sp, P.wall_vslip) : 0.0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) F[c] += fn * nn[c] + fr * vt[c];
+    }
     if (MODE == MODE_RHS) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -440,13 +484,28 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
   }
 }
 
+// Time-dependent values of a step at its force time t, shared by the whole block: the base
+// couple of every rod, the magnetic field and t itself.  Ends with a barrier (other warps read
+// them in the next stage).
 __device__ __forceinline__ void actuation_values(const StepParams& P, const Pack& pk, Smem& m, double t) {
-  if (!P.has_act) return;
-  for (int r = threadIdx.x; r < pk.nrods; r += blockDim.x) {
-    const RodConst* rc = P.rods + pk.rod0 + r;
-    const double amp = rc->act_amp;
-    m.ACT[r] = (amp != 0.0) ? amp * sin(fma(rc->act_omega, t, rc->act_phase)) : 0.0;
+  const bool timed = P.magnet != nullptr || P.arc0 != nullptr || P.n_walls > 0;
+  if (!P.has_act && !timed) return;
+  if (P.has_act) {
+    for (int r = threadIdx.x; r < pk.nrods; r += blockDim.x) {
+      const RodConst* rc = P.rods + pk.rod0 + r;
+      const double amp = rc->act_amp;
+      m.ACT[r] = (amp != 0.0) ? amp * sin(fma(rc->act_omega, t, rc->act_phase)) : 0.0;
+    }
   }
+  if (timed && threadIdx.x == 0) {
+    if (P.magnet) {
+      const double co = cos(P.field_omega * t), si = sin(P.field_omega * t);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) m.BF[c] = P.field_b0[c] + P.field_bc[c] * co + P.field_bs[c] * si;
+    }
+    m.BF[3] = t;
+  }
+  __syncthreads();
 }
 
 // Copy a pack's state and constants into shared memory and build the item -> rod maps.

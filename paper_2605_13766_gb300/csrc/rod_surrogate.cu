@@ -920,7 +920,7 @@ cudaError_t fused_grid(int* grid) {
 
 // n_calls network windows on the system's stream (no synchronisation): one fused launch per call
 // (or the unfused kernel sequence when ROD_SURROGATE_UNFUSED is set, for comparison)
-cudaError_t apply_calls(rod_surrogate* s, const SysView& V, int64_t n_calls) {
+cudaError_t apply_calls(rod_surrogate* s, const SysView& V, int64_t n_calls, int reserve_sms = 0) {
   static const bool unfused = std::getenv("ROD_SURROGATE_UNFUSED") != nullptr;
   const WinState S = win_state(V.x, V.v, V.Q, V.w, V.R);
   int sms = 0;
@@ -935,7 +935,8 @@ cudaError_t apply_calls(rod_surrogate* s, const SysView& V, int64_t n_calls) {
       apply_kernel<<<(V.R * kPos + 255) / 256, 256, 0, V.stream>>>(V.x, V.v, V.Q, V.w, V.N, V.E, V.R, s->outf, s->sc,
                                                                    V.rods);
     } else {
-      fused_apply_kernel<<<std::min(groups, sms), 256, kFusedSmem, V.stream>>>(V.x, V.v, V.Q, V.w, V.N, V.E, V.R, V.rods,
+      const int grid = std::max(1, std::min(groups, sms - reserve_sms));
+      fused_apply_kernel<<<grid, 256, kFusedSmem, V.stream>>>(V.x, V.v, V.Q, V.w, V.N, V.E, V.R, V.rods,
                                                                               *V.t, s->sc, s->wf, s->master);
     }
     *V.t += s->window * s->dt;
@@ -1200,7 +1201,10 @@ rod_status rod_surrogate_rollout(rod_surrogate* s, rod_system* sys, rod_system* 
     const double t0 = *V.t;
     // the shadow rods follow the plain method on their own stream while the network runs
     if ((rs = rod_system_step_async(shadow, k * s->window, s->dt)) != ROD_OK) return rs;
-    if ((e = checkpoint(s, V, true)) || (e = apply_calls(s, V, k))) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
+    // the fused kernel fills a whole SM's shared memory: leave the shadow's blocks SMs of their own
+    const int reserve = std::min(H.n_packs, 16);
+    if ((e = checkpoint(s, V, true)) || (e = apply_calls(s, V, k, reserve)))
+      return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
     if ((rs = rod_system_sync(shadow)) != ROD_OK) return rs;
     double err = 0.0;
     if ((e = tip_error(s, V, H, n_sample, &err))) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));

@@ -16,6 +16,7 @@ struct SysView {
   const RodConst* rods;    // device per-rod constants
   const double* rest_len;  // device rest length per element
   bool contact;            // rod-rod contact enabled
+  int n_packs;             // thread blocks of one step launch
   cudaStream_t stream;
   double* t;               // the system's simulated time (host)
 };

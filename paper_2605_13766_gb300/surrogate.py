@@ -21,6 +21,12 @@ from .binding import RodSystem, Surrogate
 POSITIONS = 51
 ELEMENTS = 50
 
+# The default recipe: noise level of the training perturbations (x the output scale of each
+# group), bound of the sampled tip error in a checked rollout (below the 1e-3 L target, since
+# only a sample of the rods is checked)
+DEFAULT_NOISE = 0.05
+DEFAULT_CHECK_BOUND = 8e-4
+
 
 def couple_samples(problem, t: float, T: float) -> np.ndarray:
     """(3, R) base couple A sin(2 pi (t + k T / 2) / period + phi) for k = 0, 1, 2 (zero without
@@ -295,6 +301,29 @@ def _perturb(state, d, spread, noise, gen):
         Qn[:, he] = state[2][:, he]
         w[:, he] = 0.0
     return [x, v, Qn, w]
+
+
+def train_default(steps: int = 15000, side: int = 32, n_windows: int = 200, seed: int = 101,
+                  window: int = 50, dt: float = 1e-5, log_every: int = 0):
+    """The default surrogate: trained on side^2 x n_windows windows (2 x 10^5 by default) of a
+    carpet of 50-element rods from rest with amplitudes 0.2..0.8 EI/L, periods 0.5..2 s and
+    random phases; group-shared output scales, noise-injected Adam with cosine decay 2e-3 ->
+    2e-5.  Returns the surrogate and a dict of training facts."""
+    import time
+    import rodgen
+    t = time.time()
+    p = rodgen.cilia_carpet(side=side, n=ELEMENTS, amp_range=(0.2, 0.8), period_range=(0.5, 2.0), seed=seed)
+    data = [generate(p, n_windows=n_windows, window=window, dt=dt)]
+    t_data = time.time() - t
+    sur = Surrogate(window, dt)
+    fit_scales(sur, data, output_floor=1.0)
+    sur.set_params(initial_params(seed=0))
+    t = time.time()
+    losses = train(sur, data, steps=steps, lr=2e-3, lr_end=2e-5, seed=0, noise=DEFAULT_NOISE, log_every=log_every)
+    info = {"windows": sum(d.n_windows * d.n_rods for d in data), "train_steps": steps, "data_s": t_data,
+            "train_s": time.time() - t, "loss_first": float(losses[0]), "loss_last_200": float(np.mean(losses[-200:]))}
+    del data
+    return sur, info
 
 
 def _rod_slice(state, r0: int, n: int):

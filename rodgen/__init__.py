@@ -66,6 +66,24 @@ class RodProblem:
     contact_k: float = 0.0
     contact_c: float = 0.0
     cell_size: float = 0.0
+    contact_mu: float = 0.0                   # rod-rod friction coefficient
+    contact_vslip: float = 0.0                # slip velocity of the regularised Coulomb law
+    magnetization: Optional[np.ndarray] = None  # (3, E) per unit reference length, local frame
+    field_b0: np.ndarray = field(default_factory=lambda: np.zeros(3))
+    field_bc: np.ndarray = field(default_factory=lambda: np.zeros(3))
+    field_bs: np.ndarray = field(default_factory=lambda: np.zeros(3))
+    field_omega: float = 0.0
+    muscle_amp: Optional[np.ndarray] = None        # (R,)
+    muscle_period: Optional[np.ndarray] = None     # (R,)
+    muscle_wavelength: Optional[np.ndarray] = None # (R,)
+    muscle_phase: Optional[np.ndarray] = None      # (R,)
+    wall_point: Optional[np.ndarray] = None        # (n_walls, 3)
+    wall_normal: Optional[np.ndarray] = None       # (n_walls, 3), unit
+    wall_velocity: Optional[np.ndarray] = None     # (n_walls, 3)
+    wall_k: float = 0.0
+    wall_c: float = 0.0
+    wall_mu: float = 0.0
+    wall_vslip: float = 0.0
     dt: float = 1e-5
     n_steps: int = 1
     t0: float = 0.0

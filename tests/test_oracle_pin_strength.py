@@ -13,6 +13,7 @@ from oracle.oracle import set_mutation
 import test_oracle_contact as tc
 import test_oracle_dynamics as td
 import test_oracle_more_pins as tm
+import test_oracle_next_rows as tn
 import test_oracle_rotations as tr
 import test_oracle_statics as ts
 
@@ -31,6 +32,11 @@ PINS = [
     tm.test_axial_mode_period,
     td.test_linear_momentum_conserved_for_free_rod,
     lambda: ts.test_timoshenko_cantilever(0.1, 0.02),
+    tn.test_field_along_the_magnetization_exerts_no_couple,
+    tn.test_muscle_couples_bend_a_free_rod_to_tau_over_B,
+    tn.test_segment_resting_on_a_wall_sinks_by_mg_over_k,
+    tn.test_sliding_on_a_wall_decelerates_at_mu_g,
+    tn.test_sliding_crossing_feels_coulomb_friction,
 ]
 
 MUTATIONS = {
@@ -52,6 +58,10 @@ MUTATIONS = {
     19: "gravity with the wrong sign",
     20: "actuation couple on the clamped element",
     21: "no Stokes drag",
+    22: "magnetic couple with Q^T b instead of Q b",
+    23: "muscle couples tau_i - tau_{i-1} instead of tau_{i-1} - tau_i",
+    24: "wall contact without the rod radius",
+    25: "friction along the sliding direction instead of against it",
 }
 
 

@@ -214,7 +214,7 @@ def _e2e(s, p, dt, K, world, dist, barrier):
 def _surrogate_speedup(train_steps: int):
     """Surrogate speed-up at the tip-error bound: the 64 x 64 carpet of 50-element rods from rest
     over 10^4 fine steps of 1e-5 s (200 calls of 50 steps), plain GPU step vs the checked
-    rollout (64 sampled rods against a shadow system every 10 calls, plain-step redo above the
+    rollout (sampled rods against a shadow system every 10 calls, plain-step redo above the
     bound); the network is first trained by the library's kernels (default recipe)."""
     import time
 
@@ -248,10 +248,10 @@ def _surrogate_speedup(train_steps: int):
         sur.apply(net, 20)
         worst = max(worst, float(S.tip_error(p, net.get_state()[0], ref[20 * k]).max()))
     net.close()
-    warm = S.CheckedRollout(sur, p, n_sample=64, seed=1)
+    warm = S.CheckedRollout(sur, p, seed=1)
     warm.run(2, check_every=1, bound=1.0)
     warm.close()
-    ro = S.CheckedRollout(sur, p, n_sample=64, seed=1)
+    ro = S.CheckedRollout(sur, p, seed=1)
     torch.cuda.synchronize()
     t = time.perf_counter()
     stats = ro.run(n_calls, check_every=10, bound=S.DEFAULT_CHECK_BOUND)

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(AdjointParams A, LaunchSha
   stage_voronoi(P, pk, m);
   __syncthreads();
   stage_rotation<MODE_STEPS>(P, pk, m, dt, 0.0, nullptr);   // WW <- w'
-  stage_translation<MODE_STEPS>(P, pk, m, dt, nullptr);     // VN <- v'
+  stage_translation<MODE_STEPS>(P, pk, m, dt, nullptr, A.t + h);   // VN <- v'
   __syncthreads();
 
   // ---- reverse of the second kinematic half (h): Q' = R(-h w') Qh, x' = xh + h v'

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, 
     stage_voronoi(P, pk, m);
     __syncthreads();
     stage_rotation<MODE_RHS>(P, pk, m, dt, 0.0, acc_w);
-    stage_translation<MODE_RHS>(P, pk, m, dt, acc_v);
+    stage_translation<MODE_RHS>(P, pk, m, dt, acc_v, t0);
     return;
   } else {
     if (MODE == MODE_STEPS) {
@@ -62,19 +62,23 @@ __global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, 
       __syncthreads();
     }
     const double tbase = P.t_dev ? *P.t_dev : t0;
+    const bool timed = has_time_values(P);
+    if (n_steps > 0) actuation_values(P, pk, m, tbase + 0.5 * dt);
     for (int64_t s = 0; s < n_steps; ++s) {
-      const double t = tbase + (static_cast<double>(s) + 0.5) * dt;
-      actuation_values(P, pk, m, t);
       stage_elements(P, pk, m);
       __syncthreads();
       stage_voronoi(P, pk, m);
       __syncthreads();
-      stage_rotation<MODE_STEPS>(P, pk, m, dt, 0.0, nullptr);
-      stage_translation<MODE_STEPS>(P, pk, m, dt, nullptr);
-      __syncthreads();
+      // rate updates fused with the following kinematic stage: each thread moves only the
+      // elements and nodes whose rates it has just updated
       const bool last = (s == n_steps - 1);
       const double h = (last && (MODE == MODE_STEPS || last_half)) ? 0.5 * dt : dt;
-      kinematic(P, pk, m, h);
+      const double t = tbase + (static_cast<double>(s) + 0.5) * dt;
+      stage_rotation<MODE_STEPS>(P, pk, m, dt, h, nullptr);
+      stage_translation<MODE_STEPS>(P, pk, m, dt, nullptr, t, h);
+      // the next step's time values: their only readers (the element stage) are past a barrier;
+      // the next step's element stage waits for the barrier below
+      if (timed && !last) time_values(P, pk, m, t + dt);
       __syncthreads();
     }
   }

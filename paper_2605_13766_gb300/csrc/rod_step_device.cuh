@@ -156,52 +156,58 @@ __device__ __forceinline__ int find_rod(const int* starts, int nrods, int idx) {
 
 // ------------------------------------------------------------------ kinematic stage (a1/a11, a2)
 
-__device__ __forceinline__ void kinematic(const StepParams& P, const Pack& pk, Smem& m, double h) {
-  const int Ep = pk.nelem, Np = pk.nnode;
-  for (int i = threadIdx.x; i < Ep; i += blockDim.x) {
-    const int r = m.erod[i];
-    const int g = pk.rod0 + r;
-    const bool held = (i == m.rel0[r]) && P.rods[g].clamp;
-    double q[9];
+// Kinematic update of one element: Q <- exp(-h [w]x) Q (clamped element: held value).
+__device__ __forceinline__ void kin_element(const StepParams& P, const Pack& pk, Smem& m, int i, double h) {
+  const int r = m.erod[i];
+  const int g = pk.rod0 + r;
+  const bool held = (i == m.rel0[r]) && P.rods[g].clamp;
+  double q[9];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) q[a] = m.QQ[a * m.CE + i];
-    if (held) {
+  for (int a = 0; a < 9; ++a) q[a] = m.QQ[a * m.CE + i];
+  if (held) {
 #pragma unroll
-      for (int a = 0; a < 9; ++a) q[a] = P.clamp_Q[a * P.n_rods + g];
-    } else {
-      // Q <- R Q, R = exp([phi]x), phi = -h w:  R = I + a K + b K^2 = (1 - b th^2) I + a K + b phi phi^T
-      const double p0 = -h * m.WW[i], p1 = -h * m.WW[m.CE + i], p2 = -h * m.WW[2 * m.CE + i];
-      const double th2 = fma(p0, p0, fma(p1, p1, p2 * p2));
-      double ca, cb;
-      rot_coeffs(th2, ca, cb);
-      const double c0 = fma(-cb, th2, 1.0);
-      const double b0 = cb * p0, b1 = cb * p1, b2 = cb * p2;
-      const double a0 = ca * p0, a1 = ca * p1, a2 = ca * p2;
-      const double R00 = fma(b0, p0, c0), R11 = fma(b1, p1, c0), R22 = fma(b2, p2, c0);
-      const double R01 = fma(b0, p1, -a2), R10 = fma(b1, p0, a2);
-      const double R02 = fma(b0, p2, a1), R20 = fma(b2, p0, -a1);
-      const double R12 = fma(b1, p2, -a0), R21 = fma(b2, p1, a0);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double q0 = q[c], q1 = q[3 + c], q2 = q[6 + c];
-        q[c] = fma(R00, q0, fma(R01, q1, R02 * q2));
-        q[3 + c] = fma(R10, q0, fma(R11, q1, R12 * q2));
-        q[6 + c] = fma(R20, q0, fma(R21, q1, R22 * q2));
-      }
-    }
-#pragma unroll
-    for (int a = 0; a < 9; ++a) m.QQ[a * m.CE + i] = q[a];
-  }
-  for (int j = threadIdx.x; j < Np; j += blockDim.x) {
-    const int r = m.nrod[j];
-    const int g = pk.rod0 + r;
-    const bool held = (j == m.rel0[r] + r) && P.rods[g].clamp;
+    for (int a = 0; a < 9; ++a) q[a] = P.clamp_Q[a * P.n_rods + g];
+  } else {
+    // Q <- R Q, R = exp([phi]x), phi = -h w:  R = I + a K + b K^2 = (1 - b th^2) I + a K + b phi phi^T
+    const double p0 = -h * m.WW[i], p1 = -h * m.WW[m.CE + i], p2 = -h * m.WW[2 * m.CE + i];
+    const double th2 = fma(p0, p0, fma(p1, p1, p2 * p2));
+    double ca, cb;
+    rot_coeffs(th2, ca, cb);
+    const double c0 = fma(-cb, th2, 1.0);
+    const double b0 = cb * p0, b1 = cb * p1, b2 = cb * p2;
+    const double a0 = ca * p0, a1 = ca * p1, a2 = ca * p2;
+    const double R00 = fma(b0, p0, c0), R11 = fma(b1, p1, c0), R22 = fma(b2, p2, c0);
+    const double R01 = fma(b0, p1, -a2), R10 = fma(b1, p0, a2);
+    const double R02 = fma(b0, p2, a1), R20 = fma(b2, p0, -a1);
+    const double R12 = fma(b1, p2, -a0), R21 = fma(b2, p1, a0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const double val = held ? P.clamp_x[c * P.n_rods + g] : fma(h, m.VN[c * m.CN + j], m.X[c * m.CN + j]);
-      m.X[c * m.CN + j] = val;
+      const double q0 = q[c], q1 = q[3 + c], q2 = q[6 + c];
+      q[c] = fma(R00, q0, fma(R01, q1, R02 * q2));
+      q[3 + c] = fma(R10, q0, fma(R11, q1, R12 * q2));
+      q[6 + c] = fma(R20, q0, fma(R21, q1, R22 * q2));
     }
   }
+#pragma unroll
+  for (int a = 0; a < 9; ++a) m.QQ[a * m.CE + i] = q[a];
+}
+
+// Kinematic update of one node: x <- x + h v (clamped node: held value).
+__device__ __forceinline__ void kin_node(const StepParams& P, const Pack& pk, Smem& m, int j, double h) {
+  const int r = m.nrod[j];
+  const int g = pk.rod0 + r;
+  const bool held = (j == m.rel0[r] + r) && P.rods[g].clamp;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double val = held ? P.clamp_x[c * P.n_rods + g] : fma(h, m.VN[c * m.CN + j], m.X[c * m.CN + j]);
+    m.X[c * m.CN + j] = val;
+  }
+}
+
+__device__ __forceinline__ void kinematic(const StepParams& P, const Pack& pk, Smem& m, double h) {
+  const int Ep = pk.nelem, Np = pk.nnode;
+  for (int i = threadIdx.x; i < Ep; i += blockDim.x) kin_element(P, pk, m, i, h);
+  for (int j = threadIdx.x; j < Np; j += blockDim.x) kin_node(P, pk, m, j, h);
 }
 
 // --------------------------------------------------------------- dynamic stage (a3-a7, a10, a2)
@@ -397,6 +403,8 @@ __device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& 
 #pragma unroll
       for (int c = 0; c < 3; ++c)
         m.WW[c * m.CE + i] = held ? 0.0 : fma(ke * __ldg(&rc->inv_rhoI[c]), tau[c], m.WW[c * m.CE + i]);
+      // the following kinematic half/full step of this element (it reads only its own w, Q)
+      if (h != 0.0) kin_element(P, pk, m, i, h);
     }
   }
 }
@@ -404,7 +412,7 @@ __device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& 
 // Stage D (nodes): internal force difference, external forces, velocity update + constraint.
 template <int MODE>
 __device__ __forceinline__ void stage_translation(const StepParams& P, const Pack& pk, Smem& m, double dt,
-                                                  double* acc_v) {
+                                                  double* acc_v, double t, double h = 0.0) {
   const int Np = pk.nnode;
   const double dtg[3] = {dt * P.gravity[0], dt * P.gravity[1], dt * P.gravity[2]};
   for (int j = threadIdx.x; j < Np; j += blockDim.x) {
@@ -442,7 +450,6 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
     }
     for (int k = 0; k < P.n_walls; ++k) {
       // node sphere (radius of the rod) against the half-space n . (x - p - u t) >= 0
-      const double t = m.BF[3];
       double d[3], vr[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -480,24 +487,30 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
         const double base = P.has_gravity ? fma(vj, keep, dtg[c]) : vj * keep;
         m.VN[c * m.CN + j] = held ? 0.0 : fma(F[c], dtim, base);
       }
+      // the following kinematic half/full step of this node (it reads only its own x, v)
+      if (h != 0.0) kin_node(P, pk, m, j, h);
     }
   }
 }
 
 // Time-dependent values of a step at its force time t, shared by the whole block: the base
-// couple of every rod, the magnetic field and t itself.  Ends with a barrier (other warps read
-// them in the next stage).
-__device__ __forceinline__ void actuation_values(const StepParams& P, const Pack& pk, Smem& m, double t) {
-  const bool timed = P.magnet != nullptr || P.arc0 != nullptr || P.n_walls > 0;
-  if (!P.has_act && !timed) return;
+// couple of every rod, the magnetic field and t itself.  Written by the last threads of the
+// block (idle in the element loops of small packs), without a barrier: the caller orders them
+// before their readers.
+__device__ __forceinline__ bool has_time_values(const StepParams& P) {
+  return P.has_act || P.magnet != nullptr || P.arc0 != nullptr || P.n_walls > 0;
+}
+
+__device__ __forceinline__ void time_values(const StepParams& P, const Pack& pk, Smem& m, double t) {
+  const int rev = blockDim.x - 1 - threadIdx.x;
   if (P.has_act) {
-    for (int r = threadIdx.x; r < pk.nrods; r += blockDim.x) {
+    for (int r = rev; r < pk.nrods; r += blockDim.x) {
       const RodConst* rc = P.rods + pk.rod0 + r;
       const double amp = rc->act_amp;
       m.ACT[r] = (amp != 0.0) ? amp * sin(fma(rc->act_omega, t, rc->act_phase)) : 0.0;
     }
   }
-  if (timed && threadIdx.x == 0) {
+  if (rev == 0 && (P.magnet != nullptr || P.arc0 != nullptr || P.n_walls > 0)) {
     if (P.magnet) {
       const double co = cos(P.field_omega * t), si = sin(P.field_omega * t);
 #pragma unroll
@@ -505,6 +518,12 @@ __device__ __forceinline__ void actuation_values(const StepParams& P, const Pack
     }
     m.BF[3] = t;
   }
+}
+
+// The same, followed by a barrier (other warps read them in the next stage).
+__device__ __forceinline__ void actuation_values(const StepParams& P, const Pack& pk, Smem& m, double t) {
+  if (!has_time_values(P)) return;
+  time_values(P, pk, m, t);
   __syncthreads();
 }
 

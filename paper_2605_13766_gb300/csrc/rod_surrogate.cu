@@ -491,19 +491,30 @@ constexpr size_t kFusedAct = size_t(kFW) * kRows * kLdAct * 2;
 constexpr size_t kFusedState = size_t(kFW) * kStateDoubles * 8;
 constexpr size_t kFusedSmem = kFusedState + kFusedW1 + 2 * kFusedW2 + kFusedW4 + kFusedBias + 2 * kFusedAct;
 
-// one convolution layer from in (kFW x [64][kLdAct]) with smem weights Ws [COUT][LDW]
-template <int CIN, int COUT, int LDW, bool OUTPUT>
+// one convolution layer from in (kFW x [64][kLdAct]) with smem weights Ws [COUT][LDW].
+// WARPS = 8: warp w takes window w / 2 and output rows 32 (w % 2) .. +31 (2 x 7 m16n8 tiles);
+// the 16-channel output layer splits the 7 n-tiles 4 / 3.  WARPS = 16: warp w takes window
+// w / 4 and rows 16 (w % 4) .. +15 (1 x 7 tiles); the output layer splits the n-tiles 2/2/2/1.
+// Every output element sums its K products in the same order whichever warp computes it.
+template <int CIN, int COUT, int LDW, bool OUTPUT, int WARPS>
 __device__ __forceinline__ void fused_conv(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ Ws,
                                            const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
                                            float* __restrict__ outf, int warp, int lane) {
   const int g = lane >> 2, tg = lane & 3;
-  const int wi = warp >> 1, half = warp & 1;
+  constexpr int PER = WARPS / kFW;          // warps per window
+  const int wi = warp / PER, part = warp % PER;
   constexpr int K = kTaps * CIN;
-  constexpr int MT = OUTPUT ? 1 : 2;
-  constexpr int NT = OUTPUT ? 4 : 7;
-  const int m0 = OUTPUT ? 0 : half * 32;
-  const int nt0 = OUTPUT ? half * 4 : 0;
-  const int ntn = OUTPUT ? (half ? 3 : 4) : 7;
+  constexpr int MT = OUTPUT ? 1 : (WARPS == 8 ? 2 : 1);
+  constexpr int NT = OUTPUT ? (WARPS == 8 ? 4 : 2) : 7;
+  const int m0 = OUTPUT ? 0 : part * (16 * MT);
+  int ntile[NT];
+  int ntn = 0;
+#pragma unroll
+  for (int n = 0; n < NT; ++n) {
+    const int tt = OUTPUT ? (WARPS == 8 ? part * 4 + n : part + 4 * n) : n;
+    ntile[n] = tt;
+    if (tt < 7 && (!OUTPUT || WARPS != 8 || n < (part ? 3 : 4))) ntn = n + 1;
+  }
   const __nv_bfloat16* inw = in + wi * kRows * kLdAct;
   float acc[MT][NT][4];
 #pragma unroll
@@ -526,7 +537,7 @@ __device__ __forceinline__ void fused_conv(const __nv_bfloat16* __restrict__ in,
 #pragma unroll
     for (int n = 0; n < NT; ++n) {
       if (n < ntn) {
-        const int row = (nt0 + n) * 8 + g + t;
+        const int row = ntile[n] * 8 + g + t;
         const __nv_bfloat16* ir = inw + row * kLdAct + cb + 2 * tg;
         uint32_t bf[2];
         bf[0] = *reinterpret_cast<const uint32_t*>(ir);
@@ -544,7 +555,7 @@ __device__ __forceinline__ void fused_conv(const __nv_bfloat16* __restrict__ in,
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int o = m0 + a * 16 + g + ((q & 2) ? 8 : 0);
-        const int jj = (nt0 + n) * 8 + 2 * tg + (q & 1);
+        const int jj = ntile[n] * 8 + 2 * tg + (q & 1);
         const float vv = acc[a][n][q] + bias[o];
         if (OUTPUT) {
           if (jj < kPos) outf[(wi * kPos + jj) * kCO + o] = vv;
@@ -555,7 +566,8 @@ __device__ __forceinline__ void fused_conv(const __nv_bfloat16* __restrict__ in,
     }
 }
 
-__global__ void __launch_bounds__(256, 1) fused_apply_kernel(double* x, double* v, double* Q, double* w, int64_t N,
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1) fused_apply_kernel(double* x, double* v, double* Q, double* w, int64_t N,
                                                              int64_t E, int nrods, const RodConst* __restrict__ rods,
                                                              double t, Scales sc, const __nv_bfloat16* __restrict__ wf,
                                                              const float* __restrict__ master) {
@@ -636,9 +648,12 @@ __global__ void __launch_bounds__(256, 1) fused_apply_kernel(double* x, double* 
       reinterpret_cast<uint32_t*>(bufA + (wi * kRows + row) * kLdAct)[cw] = 0u;
     }
     __syncthreads();
-    // features: one thread per (window, node position) writes the whole row j + 2
-    for (int i = tid; i < kFW * kPos; i += blockDim.x) {
-      const int wi = i / kPos, j = i % kPos;
+    // features: one thread per (window, node position, pair of columns) of the rows 2..52;
+    // consecutive threads take consecutive node positions of the same column pair, so a warp
+    // follows one branch of raw_feature
+    for (int i = tid; i < kFW * kPos * (kLdAct / 2); i += blockDim.x) {
+      const int cp = i / (kFW * kPos), wj = i % (kFW * kPos);
+      const int wi = wj / kPos, j = wj % kPos;
       const double* sw = st + wi * kStateDoubles;
       WinState S;
       S.x = sw;
@@ -647,26 +662,25 @@ __global__ void __launch_bounds__(256, 1) fused_apply_kernel(double* x, double* 
       S.w = sw + 6 * kPos + 9 * (kPos - 1);
       S.N = kPos;
       S.E = kPos - 1;
-      uint32_t* row = reinterpret_cast<uint32_t*>(bufA + (wi * kRows + j + 2) * kLdAct);
-#pragma unroll 1
-      for (int c = 0; c < kLdAct; c += 2) {
-        float f[2] = {0.f, 0.f};
-        for (int h = 0; h < 2; ++h) {
-          double d;
-          if (c + h < kFeat && raw_feature(S, act_s + 3 * wi, 1, 0, j, c + h, &d))
-            f[h] = static_cast<float>(d - sc.in_shift[c + h]) * sc.in_scale[c + h];
-        }
-        row[c / 2] = pack_bf16(__float2bfloat16_rn(f[0]), __float2bfloat16_rn(f[1]));
+      float f[2] = {0.f, 0.f};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = 2 * cp + h;
+        double d;
+        if (c < kFeat && raw_feature(S, act_s + 3 * wi, 1, 0, j, c, &d))
+          f[h] = static_cast<float>(d - sc.in_shift[c]) * sc.in_scale[c];
       }
+      reinterpret_cast<uint32_t*>(bufA + (wi * kRows + j + 2) * kLdAct)[cp] =
+          pack_bf16(__float2bfloat16_rn(f[0]), __float2bfloat16_rn(f[1]));
     }
     __syncthreads();
-    fused_conv<kC0, kC, kLdW1, false>(bufA, W1s, bias, bufB, nullptr, warp, lane);
+    fused_conv<kC0, kC, kLdW1, false, WARPS>(bufA, W1s, bias, bufB, nullptr, warp, lane);
     __syncthreads();
-    fused_conv<kC, kC, kLdW, false>(bufB, W2s, bias + kC, bufA, nullptr, warp, lane);
+    fused_conv<kC, kC, kLdW, false, WARPS>(bufB, W2s, bias + kC, bufA, nullptr, warp, lane);
     __syncthreads();
-    fused_conv<kC, kC, kLdW, false>(bufA, W3s, bias + 2 * kC, bufB, nullptr, warp, lane);
+    fused_conv<kC, kC, kLdW, false, WARPS>(bufA, W3s, bias + 2 * kC, bufB, nullptr, warp, lane);
     __syncthreads();
-    fused_conv<kC, kCO, kLdW, true>(bufB, W4s, bias + 3 * kC, nullptr, outf, warp, lane);
+    fused_conv<kC, kCO, kLdW, true, WARPS>(bufB, W4s, bias + 3 * kC, nullptr, outf, warp, lane);
     __syncthreads();
     // FP64 update of every node position of the group
     for (int i = tid; i < nw * kPos; i += blockDim.x) {
@@ -900,6 +914,12 @@ rod_status check_system(rod_surrogate* s, rod_system* sys, SysView* V, const cha
   return ROD_OK;
 }
 
+// warps per block of the fused kernel (8 or 16; ROD_SURROGATE_FUSED_WARPS picks one)
+int fused_warps() {
+  const char* e = std::getenv("ROD_SURROGATE_FUSED_WARPS");
+  return (e && std::atoi(e) == 8) ? 8 : 16;
+}
+
 // blocks of the fused kernel: one per SM (its shared memory holds the whole network)
 cudaError_t fused_grid(int* grid) {
   static int sms = 0;
@@ -910,7 +930,8 @@ cudaError_t fused_grid(int* grid) {
     if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
   }
   if (!attr) {
-    if ((e = cudaFuncSetAttribute(fused_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem)))
+    if ((e = cudaFuncSetAttribute(fused_apply_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem)) ||
+        (e = cudaFuncSetAttribute(fused_apply_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem)))
       return e;
     attr = true;
   }
@@ -921,7 +942,7 @@ cudaError_t fused_grid(int* grid) {
 // n_calls network windows on the system's stream (no synchronisation): one fused launch per call
 // (or the unfused kernel sequence when ROD_SURROGATE_UNFUSED is set, for comparison)
 cudaError_t apply_calls(rod_surrogate* s, const SysView& V, int64_t n_calls, int reserve_sms = 0) {
-  static const bool unfused = std::getenv("ROD_SURROGATE_UNFUSED") != nullptr;
+  const bool unfused = std::getenv("ROD_SURROGATE_UNFUSED") != nullptr;
   const WinState S = win_state(V.x, V.v, V.Q, V.w, V.R);
   int sms = 0;
   cudaError_t e;
@@ -936,7 +957,8 @@ cudaError_t apply_calls(rod_surrogate* s, const SysView& V, int64_t n_calls, int
                                                                    V.rods);
     } else {
       const int grid = std::max(1, std::min(groups, sms - reserve_sms));
-      fused_apply_kernel<<<grid, 256, kFusedSmem, V.stream>>>(V.x, V.v, V.Q, V.w, V.N, V.E, V.R, V.rods,
+      auto kern = fused_warps() == 8 ? fused_apply_kernel<8> : fused_apply_kernel<16>;
+      kern<<<grid, fused_warps() * 32, kFusedSmem, V.stream>>>(V.x, V.v, V.Q, V.w, V.N, V.E, V.R, V.rods,
                                                                               *V.t, s->sc, s->wf, s->master);
     }
     *V.t += s->window * s->dt;

@@ -26,6 +26,8 @@ ELEMENTS = 50
 # only a sample of the rods is checked)
 DEFAULT_NOISE = 0.05
 DEFAULT_CHECK_BOUND = 8e-4
+DEFAULT_SAMPLE = 32              # rods followed by the shadow system
+SHADOW_SHAPE = (64, 64)          # launch shape of the shadow: 64 elements (one rod) per block
 
 
 def couple_samples(problem, t: float, T: float) -> np.ndarray:
@@ -362,7 +364,8 @@ class CheckedRollout:
     """A system advanced by the surrogate, checked every ``check_every`` calls on ``n_sample``
     sampled rods that a shadow system follows with the plain step."""
 
-    def __init__(self, sur: Surrogate, problem, n_sample: int = 64, seed: int = 0):
+    def __init__(self, sur: Surrogate, problem, n_sample: int = DEFAULT_SAMPLE, seed: int = 0,
+                 shadow_shape=SHADOW_SHAPE):
         R = len(problem.n_elem)
         rng = np.random.default_rng(seed)
         self.sample = np.sort(rng.choice(R, size=min(n_sample, R), replace=False)).astype(np.int32)
@@ -371,6 +374,9 @@ class CheckedRollout:
         self.system.set_state(*problem.state())
         sub = subset_problem(problem, self.sample)
         self.shadow = RodSystem(sub, use_torch_stream=False)
+        if shadow_shape is not None:
+            # one rod per block: the shadow's step is latency-bound, not throughput-bound
+            self.shadow.set_launch(*shadow_shape)
         self.shadow.set_state(*sub.state())
 
     def run(self, n_calls: int, check_every: int = 10, bound: float = 5e-4) -> dict:
@@ -387,3 +393,41 @@ def tip_error(problem, xa, xb) -> np.ndarray:
     L = np.asarray(problem.rest_len).reshape(-1, ELEMENTS).sum(axis=1)
     d = np.asarray(xa)[:, tips] - np.asarray(xb)[:, tips]
     return np.sqrt((d * d).sum(axis=0)) / L
+
+
+def _main():
+    """Time the surrogate on the 64 x 64 carpet: ``python -m paper_2605_13766_gb300.surrogate``
+    applies ``--calls`` windows with seeded untrained weights (or trains first with
+    ``--train-steps``) and prints the time per call."""
+    import argparse
+    import json
+    import time
+
+    import torch
+    import rodgen
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--calls", type=int, default=3)
+    ap.add_argument("--side", type=int, default=64)
+    ap.add_argument("--train-steps", type=int, default=0)
+    args = ap.parse_args()
+    if args.train_steps:
+        sur, _ = train_default(steps=args.train_steps)
+    else:
+        sur = Surrogate(50, 1e-5)
+        sur.set_params(initial_params(seed=3))
+        rng = np.random.default_rng(0)
+        sur.set_scales(rng.normal(0, 0.01, 24), np.exp(rng.normal(0, 1, 24)), np.full(15, 1e-7))
+    p = rodgen.cilia_carpet(side=args.side, n=ELEMENTS)
+    s = RodSystem(p)
+    s.set_state(*p.state())
+    sur.apply(s, 1)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    sur.apply(s, args.calls)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    print(json.dumps({"rods": p.n_rods, "calls": args.calls, "us_per_call": dt / args.calls * 1e6}))
+
+
+if __name__ == "__main__":
+    _main()

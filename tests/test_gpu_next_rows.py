@@ -104,17 +104,24 @@ def test_trajectory_with_friction_and_a_box_400_steps():
     box = 0.08
     p = rodgen.random_packing(n_rods=40, nmin=8, nmax=40, box=box, rest_len=2e-3, radius=0.004, seed=6,
                               speed=1.0, dt=2e-6, margin=-1e-3)
-    pts = np.array([[0, 0, 0], [box, 0, 0], [0, 0, 0], [0, box, 0], [0, 0, 0], [0, 0, box]], dtype=float)
+    # walls just inside the extreme nodes' spheres: a few nodes touch them by up to 0.5 mm
+    lo = p.x.min(axis=1) - 0.004 + 5e-4
+    hi = p.x.max(axis=1) + 0.004 - 5e-4
+    pts = np.array([lo, hi, lo, hi, lo, hi], dtype=float)
     nrm = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], dtype=float)
     p = p.replace(contact_mu=0.3, contact_vslip=1e-3, wall_point=pts, wall_normal=nrm, wall_k=1e4,
                   wall_c=5.0, wall_mu=0.2, wall_vslip=1e-3, gravity=np.array([0.0, 0.0, -9.81]))
     o = Oracle(p)
     assert np.abs(o.contact_forces(p.x, p.v)).max() > 0.5
+    av, _ = o.rhs(*p.state())
+    av0, _ = Oracle(p.replace(wall_point=None, wall_normal=None)).rhs(*p.state())
+    assert _rel(av0, av) > 1e-6                          # the walls act
     ref = o.step(*p.state(), dt=2e-6, n_steps=400)
     s = _gpu(p)
     s.step(400, 2e-6)
     got = s.get_state()
-    assert np.abs(got[0] - ref[0]).max() / box <= 1e-9
+    size = float((hi - lo).max())
+    assert np.abs(got[0] - ref[0]).max() / size <= 1e-9
     assert _rel(got[1], ref[1]) <= 1e-7
 
 

@@ -185,6 +185,32 @@ def test_apply_matches_reference_update(oracle_window):
     assert abs(s.time - T) < 1e-15
 
 
+def test_fused_inference_is_bit_identical_to_the_unfused_kernels(oracle_window, monkeypatch):
+    """The persistent fused kernel (8 or 16 warps) and the kernel-by-kernel path give the same
+    state after two calls, bit for bit (same products summed in the same order)."""
+    from paper_2605_13766_gb300 import RodSystem
+    p, s0, s1, t0, dt, W = oracle_window
+    act = _act(p, t0, W * dt)
+    sur, params, _ = _setup_network(p, s0, s1, act, W * dt)
+    q = rodgen.perturbed(rodgen.cilia_carpet(side=6, n=50), seed=4, pos=0.01, vel=0.02, rot=0.02, omega=1.0)
+    results = {}
+    for mode, env in (("unfused", {"ROD_SURROGATE_UNFUSED": "1"}), ("fused8", {"ROD_SURROGATE_FUSED_WARPS": "8"}),
+                      ("fused16", {})):
+        for k in ("ROD_SURROGATE_UNFUSED", "ROD_SURROGATE_FUSED_WARPS"):
+            monkeypatch.delenv(k, raising=False)
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        s = RodSystem(q)
+        s.set_state(*q.state())
+        s.time = 0.0123
+        sur.apply(s, 2)
+        results[mode] = s.get_state()
+        s.close()
+    for mode in ("fused8", "fused16"):
+        for a, b in zip(results[mode], results["unfused"]):
+            assert np.array_equal(a, b), mode
+
+
 # ---- training on windows of the plain GPU step, checked rollout, fallback
 
 
@@ -205,7 +231,7 @@ def trained():
 def test_trained_surrogate_gain_over_plain_step(trained):
     """The 64 x 64 carpet of 50-element rods from rest over 10^4 fine steps (200 calls): the
     trained network's tip error stays within 1e-3 L at every 20th call, and the checked rollout
-    (64 sampled rods against a shadow system every 10 calls) is faster than the plain step."""
+    (sampled rods against a shadow system every 10 calls) is faster than the plain step."""
     import torch
     from paper_2605_13766_gb300 import RodSystem
     from paper_2605_13766_gb300 import surrogate as S
@@ -239,10 +265,10 @@ def test_trained_surrogate_gain_over_plain_step(trained):
         curve[20 * k] = {"max_err": float(e.max()), "mean_err": float(e.mean()), "plain_disp_max": float(d.max())}
     net.close()
     # checked rollout, timed
-    warm = S.CheckedRollout(sur, p, n_sample=64, seed=1)
+    warm = S.CheckedRollout(sur, p, seed=1)
     warm.run(2, check_every=1, bound=1.0)
     warm.close()
-    ro = S.CheckedRollout(sur, p, n_sample=64, seed=1)
+    ro = S.CheckedRollout(sur, p, seed=1)
     torch.cuda.synchronize()
     t = time.perf_counter()
     stats = ro.run(n_calls, check_every=10, bound=S.DEFAULT_CHECK_BOUND)

@@ -257,6 +257,13 @@ int32_t rod_max_elements_per_rod(void);
  *                                   step; if max |x_tip - x_tip(shadow)| / L exceeds bound, the
  *                                   segment is undone and redone with the plain step.  stats
  *                                   (optional) receives the counts and errors.
+ *   rollout_local(sys, shadows, n_shadows, ...)   the same with local checks: segment k's check
+ *                                   restarts the plain step from the surrogate's state of the
+ *                                   sampled rods at the segment's start (on shadow k mod
+ *                                   n_shadows, each holding the n_sample rods) and compares the
+ *                                   tips at its end; up to n_shadows (1..8) checks run while the
+ *                                   network goes on; a segment above the bound is undone with
+ *                                   every later one and redone with the plain step.
  * All calls return ROD_ERR_ARG for bad arguments, ROD_ERR_CUDA for CUDA failures. */
 typedef struct rod_surrogate rod_surrogate;
 typedef struct {
@@ -266,6 +273,8 @@ typedef struct {
   double max_err;            /* largest sampled error kept (after any fallback) */
   double last_err;           /* sampled error at the end */
   double rejected_err;       /* largest sampled error that caused a fallback (0: none) */
+  double sum_err;            /* sum of the accepted checks' errors (rollout_local: a bound on the
+                                accumulated error when segment errors add up without growth) */
 } rod_surrogate_stats;
 rod_status rod_surrogate_create(int32_t window_steps, double dt, rod_surrogate** out);
 rod_status rod_surrogate_destroy(rod_surrogate* sur);
@@ -292,6 +301,10 @@ rod_status rod_surrogate_apply(rod_surrogate* sur, rod_system* sys, int64_t n_ca
 rod_status rod_surrogate_rollout(rod_surrogate* sur, rod_system* sys, rod_system* shadow, const int32_t* sample_rods,
                                  int32_t n_sample, int64_t n_calls, int32_t check_every, double bound,
                                  rod_surrogate_stats* stats);
+rod_status rod_surrogate_rollout_local(rod_surrogate* sur, rod_system* sys, rod_system* const* shadows,
+                                       int32_t n_shadows, const int32_t* sample_rods, int32_t n_sample,
+                                       int64_t n_calls, int32_t check_every, double bound,
+                                       rod_surrogate_stats* stats);
 
 /* Contact forces without allocating anything (the paper has no counterpart: this is a service
  * for callers that cannot allocate device memory when they need the forces, such as code

@@ -32,7 +32,8 @@ class RodError(RuntimeError):
 class SurrogateStats(C.Structure):
     """rod_surrogate_stats."""
     _fields_ = [("surrogate_calls", C.c_int64), ("fallback_calls", C.c_int64), ("checks", C.c_int64),
-                ("max_err", C.c_double), ("last_err", C.c_double), ("rejected_err", C.c_double)]
+                ("max_err", C.c_double), ("last_err", C.c_double), ("rejected_err", C.c_double),
+                ("sum_err", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -125,6 +126,8 @@ _SIGNATURES = {
     "rod_surrogate_raw_targets": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int32, _P, _P], C.c_int),
     "rod_surrogate_apply": ([_P, _P, C.c_int64], C.c_int),
     "rod_surrogate_rollout": ([_P, _P, _P, _P, C.c_int32, C.c_int64, C.c_int32, C.c_double, _P], C.c_int),
+    "rod_surrogate_rollout_local": ([_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_int64, C.c_int32, C.c_double, _P],
+                                    C.c_int),
     "rod_max_elements_per_rod": ([], C.c_int32),
     "rod_last_error": ([], C.c_char_p),
     "rod_version": ([], C.c_char_p),
@@ -542,6 +545,18 @@ class Surrogate:
         st = SurrogateStats()
         _check(self.lib.rod_surrogate_rollout(self.handle, system.handle, shadow.handle, idx.ctypes.data, int(idx.size),
                                               int(n_calls), int(check_every), float(bound), C.byref(st)))
+        return st.as_dict()
+
+    def rollout_local(self, system, shadows, sample_rods, n_calls: int, check_every: int, bound: float) -> dict:
+        """n_calls windows with pipelined local checks: the check of each segment restarts the
+        plain step from the surrogate's state of the sampled rods on one of ``shadows`` (each
+        holding those rods); a segment above ``bound`` is undone and redone with the plain step."""
+        idx = np.ascontiguousarray(sample_rods, dtype=np.int32)
+        arr = (C.c_void_p * len(shadows))(*[sh.handle.value for sh in shadows])
+        st = SurrogateStats()
+        _check(self.lib.rod_surrogate_rollout_local(self.handle, system.handle, arr, len(shadows), idx.ctypes.data,
+                                                    int(idx.size), int(n_calls), int(check_every), float(bound),
+                                                    C.byref(st)))
         return st.as_dict()
 
 

@@ -1169,6 +1169,8 @@ rod_status rod_system_get_launch(const rod_system* s, int32_t* elems_per_block, 
 }  // extern "C"
 
 namespace rod {
+cudaError_t system_clear_error(rod_system* s) { return cudaMemsetAsync(s->err.p, 0, sizeof(int), s->stream); }
+
 rod_status system_view(rod_system* s, SysView* out) {
   if (!s || !out) return fail(ROD_ERR_ARG, "null argument");
   if (!s->state_set) return fail(ROD_ERR_STATE, "no state has been set");

@@ -133,12 +133,14 @@ __global__ void __launch_bounds__(128) conv_kernel(const __nv_bfloat16* __restri
   }
 }
 
-// dW[o][t*CIN + c] += sum_{windows in chunk, j} g[b][j+2][o] in[b][j+t][c]   (atomic FP32 per block)
-// grid.x: window chunks, grid.y: groups of 8 n-tiles (64 K columns); warp w owns m-tile w (COUT=64) or 0.
+// Partial weight gradient of one chunk of windows (grid.x), written without atomics:
+//   part[chunk][o*K + t*CIN + c] = sum_{windows in chunk, j} g[b][j+2][o] in[b][j+t][c]
+//   part[chunk][COUT*K + o]      = sum_{windows in chunk, j} g[b][j+2][o]
+// grid.y: groups of 8 n-tiles (64 K columns); warp w owns m-tile w (COUT=64) or 0.  The chunks
+// are summed in a fixed order by reduce_partials_kernel, so training is deterministic.
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(128) wgrad_kernel(const __nv_bfloat16* __restrict__ gout, const __nv_bfloat16* __restrict__ in,
-                                                    float* __restrict__ dW, float* __restrict__ db, int nwin,
-                                                    int win_per_block) {
+                                                    float* __restrict__ part, int nwin, int win_per_block) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, tg = lane & 3;
   constexpr int K = kTaps * CIN;
@@ -188,14 +190,16 @@ __global__ void __launch_bounds__(128) wgrad_kernel(const __nv_bfloat16* __restr
       }
     }
   }
+  float* dW = part + static_cast<int64_t>(blockIdx.x) * (COUT * K + COUT);
+  float* db = dW + COUT * K;
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int nc = nbase + s * 8 + 2 * tg;
     if (nc >= K) continue;
-    atomicAdd(dW + (m0 + g) * K + nc, acc[s][0]);
-    atomicAdd(dW + (m0 + g) * K + nc + 1, acc[s][1]);
-    atomicAdd(dW + (m0 + g + 8) * K + nc, acc[s][2]);
-    atomicAdd(dW + (m0 + g + 8) * K + nc + 1, acc[s][3]);
+    dW[(m0 + g) * K + nc] = acc[s][0];
+    dW[(m0 + g) * K + nc + 1] = acc[s][1];
+    dW[(m0 + g + 8) * K + nc] = acc[s][2];
+    dW[(m0 + g + 8) * K + nc + 1] = acc[s][3];
   }
   if (blockIdx.y == 0) {
     // reduce the bias sums over the 4 lanes sharing a row
@@ -204,10 +208,19 @@ __global__ void __launch_bounds__(128) wgrad_kernel(const __nv_bfloat16* __restr
       bsum1 += __shfl_xor_sync(0xffffffffu, bsum1, o);
     }
     if (tg == 0) {
-      atomicAdd(db + m0 + g, bsum0);
-      atomicAdd(db + m0 + g + 8, bsum1);
+      db[m0 + g] = bsum0;
+      db[m0 + g + 8] = bsum1;
     }
   }
+}
+
+// grad[p] = sum over chunks c = 0, 1, ... of part[c][p], in that order
+__global__ void reduce_partials_kernel(const float* __restrict__ part, int chunks, int n, float* __restrict__ grad) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  float acc = 0.f;
+  for (int c = 0; c < chunks; ++c) acc += part[static_cast<int64_t>(c) * n + p];
+  grad[p] = acc;
 }
 
 // ---- features, targets, loss, state update, Adam
@@ -470,6 +483,58 @@ __global__ void apply_kernel(double* x, double* v, double* Q, double* w, int64_t
   S.E = E;
   update_node(S, b, j, out + i * kCO, sc, rods[b].clamp != 0, x, v, Q, w, N, E, i,
               static_cast<int64_t>(b) * (kPos - 1) + j);
+}
+
+// Copy the state of the sampled rods sample[0..n) of a system into a system that holds just
+// those rods (same order, 50 elements each).
+__global__ void gather_rods_kernel(const double* __restrict__ x, const double* __restrict__ v, const double* __restrict__ Q,
+                                   const double* __restrict__ w, int64_t N, int64_t E, const int32_t* __restrict__ sample,
+                                   int n, double* __restrict__ xs, double* __restrict__ vs, double* __restrict__ Qs,
+                                   double* __restrict__ ws) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= static_cast<int64_t>(n) * kPos) return;
+  const int k = static_cast<int>(i / kPos), j = static_cast<int>(i % kPos);
+  const int64_t Ns = static_cast<int64_t>(n) * kPos, Es = static_cast<int64_t>(n) * (kPos - 1);
+  const int64_t src = static_cast<int64_t>(sample[k]) * kPos + j;
+  for (int c = 0; c < 3; ++c) {
+    xs[c * Ns + i] = x[c * N + src];
+    vs[c * Ns + i] = v[c * N + src];
+  }
+  if (j < kPos - 1) {
+    const int64_t se = static_cast<int64_t>(sample[k]) * (kPos - 1) + j, de = static_cast<int64_t>(k) * (kPos - 1) + j;
+    for (int a = 0; a < 9; ++a) Qs[a * Es + de] = Q[a * E + se];
+    for (int c = 0; c < 3; ++c) ws[c * Es + de] = w[c * E + se];
+  }
+}
+
+// tips[k][c] = tip position of sampled rod k
+__global__ void save_tips_kernel(const double* __restrict__ x, int64_t N, const int32_t* __restrict__ sample, int n,
+                                 double* __restrict__ tips) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int64_t tip = static_cast<int64_t>(sample[k]) * kPos + kPos - 1;
+  for (int c = 0; c < 3; ++c) tips[3 * k + c] = x[c * N + tip];
+}
+
+// max over k of |tip of rod k of a shadow system - tips[k]| / L_k (as non-negative double bits)
+__global__ void local_error_kernel(const double* __restrict__ xs, int64_t Ns, const double* __restrict__ tips, int n,
+                                   const double* __restrict__ rest_len_s, unsigned long long* err_bits) {
+  double worst = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int64_t tip = static_cast<int64_t>(k) * kPos + kPos - 1;
+    double d2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      const double d = xs[c * Ns + tip] - tips[3 * k + c];
+      d2 += d * d;
+    }
+    double L = 0.0;
+    for (int q = 0; q < kPos - 1; ++q) L += rest_len_s[static_cast<int64_t>(k) * (kPos - 1) + q];
+    double e = sqrt(d2) / L;
+    if (!(e <= 1e300)) e = INFINITY;
+    worst = fmax(worst, e);
+  }
+  for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(err_bits, static_cast<unsigned long long>(__double_as_longlong(worst)));
 }
 
 // ---- fused inference: one persistent kernel per window call
@@ -790,6 +855,7 @@ struct rod_surrogate {
   __nv_bfloat16 *a0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr;  // input, hidden 1..3
   float *p1 = nullptr, *p2 = nullptr, *p3 = nullptr;                        // pre-activations
   float *outf = nullptr, *tgt = nullptr, *loss = nullptr;
+  float* part = nullptr;   // per-chunk partial weight gradients [chunks][largest layer]
   __nv_bfloat16 *g4 = nullptr, *g3 = nullptr, *g2 = nullptr, *g1 = nullptr;
   double* act = nullptr;
   bool weights_dirty = true;
@@ -811,10 +877,12 @@ int64_t bf_off(int layer) {  // offset of layer l's weights in the BF16 weight a
   return o;
 }
 constexpr int64_t kBfTotal = kW1 + kW2 + kW3 + kW4;
+constexpr int kWgradWindows = 16;   // windows per chunk of the weight gradient
 
 cudaError_t grow(rod_surrogate* s, int nwin) {
   if (nwin <= s->cap) return cudaSuccess;
-  void* ptrs[] = {s->a0, s->a1, s->a2, s->a3, s->p1, s->p2, s->p3, s->outf, s->tgt, s->g4, s->g3, s->g2, s->g1, s->act};
+  void* ptrs[] = {s->a0, s->a1, s->a2, s->a3, s->p1, s->p2, s->p3, s->outf, s->tgt, s->g4, s->g3, s->g2, s->g1, s->act,
+                  s->part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   s->cap = 0;
@@ -826,7 +894,8 @@ cudaError_t grow(rod_surrogate* s, int nwin) {
       (e = cudaMalloc(&s->p3, rows * kC * 4)) || (e = cudaMalloc(&s->outf, static_cast<size_t>(nwin) * kPos * kCO * 4)) ||
       (e = cudaMalloc(&s->tgt, static_cast<size_t>(nwin) * kPos * kCO * 4)) || (e = cudaMalloc(&s->g4, rows * kCO * 2)) ||
       (e = cudaMalloc(&s->g3, rows * kC * 2)) || (e = cudaMalloc(&s->g2, rows * kC * 2)) ||
-      (e = cudaMalloc(&s->g1, rows * kC * 2)) || (e = cudaMalloc(&s->act, static_cast<size_t>(nwin) * 3 * 8)))
+      (e = cudaMalloc(&s->g1, rows * kC * 2)) || (e = cudaMalloc(&s->act, static_cast<size_t>(nwin) * 3 * 8)) ||
+      (e = cudaMalloc(&s->part, static_cast<size_t>((nwin + kWgradWindows - 1) / kWgradWindows) * (kW2 + kC) * 4)))
     return e;
   // the kernels write rows 2..57 only: the padding rows must start (and stay) zero
   if ((e = cudaMemset(s->a1, 0, rows * kC * 2)) || (e = cudaMemset(s->a2, 0, rows * kC * 2)) ||
@@ -860,28 +929,34 @@ cudaError_t forward(rod_surrogate* s, int nwin, bool train, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// gradients of the mean-square loss (outf vs tgt) into s->grad (overwritten)
+// gradients of the mean-square loss (outf vs tgt) into s->grad (overwritten, deterministic)
 cudaError_t backward(rod_surrogate* s, int nwin, cudaStream_t st) {
   cudaError_t e;
-  if ((e = cudaMemsetAsync(s->grad, 0, kNumParams * 4, st))) return e;
   if ((e = cudaMemsetAsync(s->loss, 0, 4, st))) return e;
   const int64_t total = static_cast<int64_t>(nwin) * kRows * kCO;
   const float inv_count = 1.0f / (static_cast<float>(nwin) * kPos * kOut);
   loss_kernel<<<(total + 255) / 256, 256, 0, st>>>(s->outf, s->tgt, nwin, s->g4, s->loss, inv_count);
-  const int wpb = 16;
+  const int wpb = kWgradWindows;
   const int gx = (nwin + wpb - 1) / wpb;
   float* gr = s->grad;
+  auto reduce = [&](int n, float* dst) {
+    reduce_partials_kernel<<<(n + 255) / 256, 256, 0, st>>>(s->part, gx, n, dst);
+  };
   // layer 4: dW4, db4; input gradient to layer-3 activations (times SiLU'(p3))
-  wgrad_kernel<kC, kCO><<<dim3(gx, (kTaps * kC + 63) / 64), 128, 0, st>>>(s->g4, s->a3, gr + kOffW4, gr + kOffB4, nwin, wpb);
+  wgrad_kernel<kC, kCO><<<dim3(gx, (kTaps * kC + 63) / 64), 128, 0, st>>>(s->g4, s->a3, s->part, nwin, wpb);
+  reduce(kW4 + kCO, gr + kOffW4);
   conv_kernel<kCO, kC, EPI_DGRAD, true><<<nwin, 128, 0, st>>>(s->g4, s->wt + bf_off(3), nullptr, s->g3, nullptr, nullptr,
                                                                s->p3, nwin);
-  wgrad_kernel<kC, kC><<<dim3(gx, (kTaps * kC + 63) / 64), 128, 0, st>>>(s->g3, s->a2, gr + kOffW3, gr + kOffB3, nwin, wpb);
+  wgrad_kernel<kC, kC><<<dim3(gx, (kTaps * kC + 63) / 64), 128, 0, st>>>(s->g3, s->a2, s->part, nwin, wpb);
+  reduce(kW3 + kC, gr + kOffW3);
   conv_kernel<kC, kC, EPI_DGRAD, true><<<nwin, 128, 0, st>>>(s->g3, s->wt + bf_off(2), nullptr, s->g2, nullptr, nullptr,
                                                               s->p2, nwin);
-  wgrad_kernel<kC, kC><<<dim3(gx, (kTaps * kC + 63) / 64), 128, 0, st>>>(s->g2, s->a1, gr + kOffW2, gr + kOffB2, nwin, wpb);
+  wgrad_kernel<kC, kC><<<dim3(gx, (kTaps * kC + 63) / 64), 128, 0, st>>>(s->g2, s->a1, s->part, nwin, wpb);
+  reduce(kW2 + kC, gr + kOffW2);
   conv_kernel<kC, kC, EPI_DGRAD, true><<<nwin, 128, 0, st>>>(s->g2, s->wt + bf_off(1), nullptr, s->g1, nullptr, nullptr,
                                                               s->p1, nwin);
-  wgrad_kernel<kC0, kC><<<dim3(gx, (kTaps * kC0 + 63) / 64), 128, 0, st>>>(s->g1, s->a0, gr + kOffW1, gr + kOffB1, nwin, wpb);
+  wgrad_kernel<kC0, kC><<<dim3(gx, (kTaps * kC0 + 63) / 64), 128, 0, st>>>(s->g1, s->a0, s->part, nwin, wpb);
+  reduce(kW1 + kC, gr + kOffW1);
   return cudaGetLastError();
 }
 
@@ -1044,7 +1119,7 @@ rod_status rod_surrogate_destroy(rod_surrogate* s) {
   if (!s) return ROD_OK;
   void* ptrs[] = {s->master, s->grad, s->adam_m, s->adam_v, s->wf, s->wt, s->loss, s->a0, s->a1, s->a2, s->a3,
                   s->p1, s->p2, s->p3, s->outf, s->tgt, s->g4, s->g3, s->g2, s->g1, s->act, s->ck, s->sample,
-                  s->err_dev};
+                  s->err_dev, s->part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->err_host) cudaFreeHost(s->err_host);
@@ -1244,8 +1319,219 @@ rod_status rod_surrogate_rollout(rod_surrogate* s, rod_system* sys, rod_system* 
     }
     st.max_err = std::max(st.max_err, err);
     st.last_err = err;
+    st.sum_err += err;
     done += k;
   }
+  if (stats) *stats = st;
+  return ROD_OK;
+}
+
+// Checked rollout with local (per-segment) error checks run in a pipeline: the check of a
+// segment restarts the plain step from the surrogate's own state of the sampled rods at the
+// segment's start, on a shadow system of its own, while the network goes on with the next
+// segments; a segment whose local error exceeds the bound is undone (with everything after
+// it) and redone with the plain step.
+rod_status rod_surrogate_rollout_local(rod_surrogate* s, rod_system* sys, rod_system* const* shadows, int32_t n_shadows,
+                                       const int32_t* sample_rods, int32_t n_sample, int64_t n_calls,
+                                       int32_t check_every, double bound, rod_surrogate_stats* stats) {
+  const char* who = "rod_surrogate_rollout_local";
+  if (!s || !sys || !shadows || n_shadows < 1 || n_shadows > 8 || !sample_rods || n_sample < 1 || n_calls < 0 ||
+      check_every < 1 || !(bound > 0))
+    return internal_fail(ROD_ERR_ARG, who, "bad argument");
+  SysView V;
+  rod_status rs = check_system(s, sys, &V, who);
+  if (rs != ROD_OK) return rs;
+  std::vector<SysView> H(n_shadows);
+  for (int k = 0; k < n_shadows; ++k) {
+    if (!shadows[k] || shadows[k] == sys) return internal_fail(ROD_ERR_ARG, who, "bad shadow system");
+    if ((rs = system_view(shadows[k], &H[k])) != ROD_OK) return rs;
+    if (H[k].R != n_sample || H[k].max_n != kPos - 1 || H[k].min_n != kPos - 1 || H[k].contact)
+      return internal_fail(ROD_ERR_ARG, who, "every shadow system must hold the n_sample rods (50 elements, no contact)");
+    for (int q = 0; q < k; ++q)
+      if (shadows[q] == shadows[k]) return internal_fail(ROD_ERR_ARG, who, "shadow systems must be distinct");
+  }
+  for (int i = 0; i < n_sample; ++i)
+    if (sample_rods[i] < 0 || sample_rods[i] >= V.R) return internal_fail(ROD_ERR_ARG, who, "sample index out of range");
+  cudaError_t e;
+  const int64_t ss = 6 * V.N + 12 * V.E;  // one checkpoint
+  const int slots = n_shadows;
+  if (slots * ss > s->ck_cap) {
+    if (s->ck) cudaFree(s->ck);
+    s->ck = nullptr;
+    s->ck_cap = 0;
+    if ((e = cudaMalloc(&s->ck, slots * ss * 8))) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
+    s->ck_cap = slots * ss;
+  }
+  if (n_sample > s->sample_cap) {
+    if (s->sample) cudaFree(s->sample);
+    s->sample = nullptr;
+    s->sample_cap = 0;
+    if ((e = cudaMalloc(&s->sample, n_sample * 4))) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
+    s->sample_cap = n_sample;
+  }
+  // per slot: saved tips, error word (device and pinned host), events
+  struct Slot {
+    double* tips = nullptr;
+    unsigned long long* err_dev = nullptr;
+    unsigned long long* err_host = nullptr;
+    cudaEvent_t gathered = nullptr, tipped = nullptr, done = nullptr;
+    int64_t seg = -1;
+    double t0 = 0.0;
+  };
+  std::vector<Slot> sl(slots);
+  auto release = [&]() {
+    for (auto& q : sl) {
+      if (q.done) cudaEventSynchronize(q.done);
+      if (q.tips) cudaFree(q.tips);
+      if (q.err_dev) cudaFree(q.err_dev);
+      if (q.err_host) cudaFreeHost(q.err_host);
+      if (q.gathered) cudaEventDestroy(q.gathered);
+      if (q.tipped) cudaEventDestroy(q.tipped);
+      if (q.done) cudaEventDestroy(q.done);
+    }
+  };
+  auto failc = [&](cudaError_t err) {
+    release();
+    return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(err));
+  };
+  for (auto& q : sl) {
+    if ((e = cudaMalloc(&q.tips, 3 * n_sample * 8)) || (e = cudaMalloc(&q.err_dev, 8)) ||
+        (e = cudaMallocHost(&q.err_host, 8)) || (e = cudaEventCreateWithFlags(&q.gathered, cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&q.tipped, cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&q.done, cudaEventDisableTiming)))
+      return failc(e);
+  }
+  if ((e = cudaMemcpyAsync(s->sample, sample_rods, n_sample * 4, cudaMemcpyHostToDevice, V.stream))) return failc(e);
+  int reserve = 0;
+  for (int k = 0; k < n_shadows; ++k) reserve += H[k].n_packs;
+  reserve = std::min(reserve, 64);
+  const int64_t n_seg = (n_calls + check_every - 1) / check_every;
+  rod_surrogate_stats st{};
+  int64_t seg = 0;
+  int inflight = 0;
+  // Wait for the check of slot q and act on it; returns true when the segment was rejected
+  // (the system is then back at the segment's end, computed by the plain step).
+  auto finish = [&](int qi, bool* rejected) -> rod_status {
+    Slot& q = sl[qi];
+    *rejected = false;
+    if (q.seg < 0) return ROD_OK;
+    if ((e = cudaEventSynchronize(q.done))) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
+    // a shadow that ran into non-finite values (from a non-finite surrogate state) fails the check
+    rod_status r2 = rod_system_sync(shadows[qi]);
+    if (r2 != ROD_OK && r2 != ROD_ERR_NONFINITE) return r2;
+    double err;
+    const uint64_t bits = *q.err_host;
+    std::memcpy(&err, &bits, 8);
+    if (r2 == ROD_ERR_NONFINITE) {
+      err = INFINITY;
+      if ((e = system_clear_error(shadows[qi]))) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
+    }
+    const int64_t k = q.seg;
+    const int64_t calls = std::min<int64_t>(check_every, n_calls - k * check_every);
+    q.seg = -1;
+    --inflight;
+    st.checks += 1;
+    st.last_err = err;
+    if (err <= bound) {
+      st.surrogate_calls += calls;
+      st.max_err = std::max(st.max_err, err);
+      st.sum_err += err;
+      return ROD_OK;
+    }
+    // reject: drain the other checks (their segments come after this one and are discarded)
+    for (int o = 0; o < slots; ++o)
+      if (sl[o].seg >= 0) {
+        if ((e = cudaEventSynchronize(sl[o].done))) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
+        r2 = rod_system_sync(shadows[o]);
+        if (r2 == ROD_ERR_NONFINITE) {
+          if ((e = system_clear_error(shadows[o]))) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
+        } else if (r2 != ROD_OK) {
+          return r2;
+        }
+        sl[o].seg = -1;
+        --inflight;
+      }
+    // back to the checkpoint of segment k and redo it with the plain step
+    double* parts[4] = {V.x, V.v, V.Q, V.w};
+    const int64_t sizes[4] = {3 * V.N, 3 * V.N, 9 * V.E, 3 * V.E};
+    int64_t off = 0;
+    for (int c = 0; c < 4; ++c) {
+      if ((e = cudaMemcpyAsync(parts[c], s->ck + qi * ss + off, sizes[c] * 8, cudaMemcpyDeviceToDevice, V.stream)))
+        return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
+      off += sizes[c];
+    }
+    *V.t = q.t0;
+    if ((r2 = rod_system_step(sys, calls * s->window, s->dt)) != ROD_OK) return r2;
+    st.fallback_calls += calls;
+    st.rejected_err = std::max(st.rejected_err, err);
+    seg = k + 1;
+    *rejected = true;
+    return ROD_OK;
+  };
+  while (seg < n_seg || inflight > 0) {
+    if (seg >= n_seg) {
+      // drain the oldest check
+      int oldest = -1;
+      for (int q = 0; q < slots; ++q)
+        if (sl[q].seg >= 0 && (oldest < 0 || sl[q].seg < sl[oldest].seg)) oldest = q;
+      bool rej;
+      rod_status r2 = finish(oldest, &rej);
+      if (r2 != ROD_OK) {
+        release();
+        return r2;
+      }
+      continue;
+    }
+    const int qi = static_cast<int>(seg % slots);
+    if (sl[qi].seg >= 0) {
+      bool rej;
+      rod_status r2 = finish(qi, &rej);
+      if (r2 != ROD_OK) {
+        release();
+        return r2;
+      }
+      if (rej) continue;
+    }
+    Slot& q = sl[qi];
+    const int64_t calls = std::min<int64_t>(check_every, n_calls - seg * check_every);
+    q.seg = seg;
+    q.t0 = *V.t;
+    ++inflight;
+    // checkpoint of the segment's start and the sampled rods' state into the slot's shadow
+    {
+      double* parts[4] = {V.x, V.v, V.Q, V.w};
+      const int64_t sizes[4] = {3 * V.N, 3 * V.N, 9 * V.E, 3 * V.E};
+      int64_t off = 0;
+      for (int c = 0; c < 4; ++c) {
+        if ((e = cudaMemcpyAsync(s->ck + qi * ss + off, parts[c], sizes[c] * 8, cudaMemcpyDeviceToDevice, V.stream)))
+          return failc(e);
+        off += sizes[c];
+      }
+    }
+    gather_rods_kernel<<<(n_sample * kPos + 127) / 128, 128, 0, V.stream>>>(V.x, V.v, V.Q, V.w, V.N, V.E, s->sample,
+                                                                           n_sample, H[qi].x, H[qi].v, H[qi].Q, H[qi].w);
+    if ((e = cudaEventRecord(q.gathered, V.stream)) || (e = cudaStreamWaitEvent(H[qi].stream, q.gathered, 0)))
+      return failc(e);
+    rod_status r2 = rod_system_set_time(shadows[qi], q.t0);
+    if (r2 == ROD_OK) r2 = rod_system_step_async(shadows[qi], calls * s->window, s->dt);
+    if (r2 != ROD_OK) {
+      release();
+      return r2;
+    }
+    // the network's segment, then the sampled tips at its end
+    if ((e = apply_calls(s, V, calls, reserve))) return failc(e);
+    save_tips_kernel<<<(n_sample + 127) / 128, 128, 0, V.stream>>>(V.x, V.N, s->sample, n_sample, q.tips);
+    if ((e = cudaEventRecord(q.tipped, V.stream)) || (e = cudaStreamWaitEvent(H[qi].stream, q.tipped, 0)) ||
+        (e = cudaMemsetAsync(q.err_dev, 0, 8, H[qi].stream)))
+      return failc(e);
+    local_error_kernel<<<1, 256, 0, H[qi].stream>>>(H[qi].x, H[qi].N, q.tips, n_sample, H[qi].rest_len, q.err_dev);
+    if ((e = cudaMemcpyAsync(q.err_host, q.err_dev, 8, cudaMemcpyDeviceToHost, H[qi].stream)) ||
+        (e = cudaEventRecord(q.done, H[qi].stream)))
+      return failc(e);
+    ++seg;
+  }
+  if ((e = cudaStreamSynchronize(V.stream))) return failc(e);
+  release();
   if (stats) *stats = st;
   return ROD_OK;
 }

@@ -23,4 +23,8 @@ struct SysView {
 
 rod_status system_view(rod_system* sys, SysView* out);
 
+// Clear a system's latched device error word (on its stream), e.g. after a shadow copy of
+// rods ran into non-finite values; returns the CUDA status of the enqueue.
+cudaError_t system_clear_error(rod_system* sys);
+
 }  // namespace rod

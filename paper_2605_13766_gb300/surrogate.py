@@ -26,7 +26,7 @@ ELEMENTS = 50
 # only a sample of the rods is checked)
 DEFAULT_NOISE = 0.05
 DEFAULT_CHECK_BOUND = 8e-4
-DEFAULT_SAMPLE = 32              # rods followed by the shadow system
+DEFAULT_SAMPLE = 16              # rods followed by the shadow systems
 SHADOW_SHAPE = (64, 64)          # launch shape of the shadow: 64 elements (one rod) per block
 
 
@@ -361,30 +361,52 @@ def _vor_pick(a, rods):
 
 
 class CheckedRollout:
-    """A system advanced by the surrogate, checked every ``check_every`` calls on ``n_sample``
-    sampled rods that a shadow system follows with the plain step."""
+    """A system advanced by the surrogate with periodic checks of ``n_sample`` sampled rods
+    against the plain step.
+
+    mode "global": one shadow system follows the sampled rods with the plain step from the
+    initial state (the check measures the accumulated error exactly, at the cost of running
+    the plain step for the whole horizon on the side).
+    mode "local": ``n_shadows`` shadow systems take turns; each segment's check restarts the
+    plain step from the surrogate's own state of the sampled rods at the segment's start, so
+    the checks of different segments run while the network goes on (the check measures the
+    error the surrogate adds in one segment; ``stats["sum_err"]`` bounds the accumulated
+    error if segment errors add up without growing)."""
 
     def __init__(self, sur: Surrogate, problem, n_sample: int = DEFAULT_SAMPLE, seed: int = 0,
-                 shadow_shape=SHADOW_SHAPE):
+                 shadow_shape=SHADOW_SHAPE, mode: str = "global", n_shadows: int = 2):
+        if mode not in ("global", "local"):
+            raise ValueError("mode is 'global' or 'local'")
         R = len(problem.n_elem)
         rng = np.random.default_rng(seed)
         self.sample = np.sort(rng.choice(R, size=min(n_sample, R), replace=False)).astype(np.int32)
         self.sur = sur
+        self.mode = mode
         self.system = RodSystem(problem)
         self.system.set_state(*problem.state())
         sub = subset_problem(problem, self.sample)
-        self.shadow = RodSystem(sub, use_torch_stream=False)
-        if shadow_shape is not None:
-            # one rod per block: the shadow's step is latency-bound, not throughput-bound
-            self.shadow.set_launch(*shadow_shape)
-        self.shadow.set_state(*sub.state())
+        self.shadows = []
+        for _ in range(1 if mode == "global" else n_shadows):
+            sh = RodSystem(sub, use_torch_stream=False)
+            if shadow_shape is not None:
+                # one rod per block: the shadow's step is latency-bound, not throughput-bound
+                sh.set_launch(*shadow_shape)
+            sh.set_state(*sub.state())
+            self.shadows.append(sh)
+        self.shadow = self.shadows[0]
 
-    def run(self, n_calls: int, check_every: int = 10, bound: float = 5e-4) -> dict:
-        return self.sur.rollout(self.system, self.shadow, self.sample, n_calls, check_every, bound)
+    def run(self, n_calls: int, check_every: int = 10, bound: float = DEFAULT_CHECK_BOUND) -> dict:
+        """``bound`` is the target for the accumulated sampled tip error; a local check gets its
+        share per segment, bound x check_every / n_calls."""
+        if self.mode == "global":
+            return self.sur.rollout(self.system, self.shadow, self.sample, n_calls, check_every, bound)
+        local = bound * min(1.0, check_every / max(n_calls, 1))
+        return self.sur.rollout_local(self.system, self.shadows, self.sample, n_calls, check_every, local)
 
     def close(self):
         self.system.close()
-        self.shadow.close()
+        for sh in self.shadows:
+            sh.close()
 
 
 def tip_error(problem, xa, xb) -> np.ndarray:

@@ -264,31 +264,34 @@ def test_trained_surrogate_gain_over_plain_step(trained):
         d = S.tip_error(p, ref[20 * k], p.x)
         curve[20 * k] = {"max_err": float(e.max()), "mean_err": float(e.mean()), "plain_disp_max": float(d.max())}
     net.close()
-    # checked rollout, timed
-    warm = S.CheckedRollout(sur, p, seed=1)
-    warm.run(2, check_every=1, bound=1.0)
-    warm.close()
-    ro = S.CheckedRollout(sur, p, seed=1)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    stats = ro.run(n_calls, check_every=10, bound=S.DEFAULT_CHECK_BOUND)
-    torch.cuda.synchronize()
-    t_sur = time.perf_counter() - t
-    err = S.tip_error(p, ro.system.get_state()[0], ref[n_calls])
-    ro.close()
+    # checked rollouts (global and local checks), timed
     el_steps = p.n_elems * n_calls * W
     worst = max(v["max_err"] for v in curve.values())
-    rec = dict(info, plain_s=t_plain, rollout_s=t_sur, speedup=t_plain / t_sur,
-               plain_elem_steps_per_s=el_steps / t_plain, rollout_elem_steps_per_s=el_steps / t_sur,
-               network_curve=curve, network_worst_tip_err=worst, rollout_final_tip_err=float(err.max()), stats=stats)
+    rec = dict(info, plain_s=t_plain, plain_elem_steps_per_s=el_steps / t_plain, network_curve=curve,
+               network_worst_tip_err=worst)
+    for mode in ("global", "local"):
+        warm = S.CheckedRollout(sur, p, seed=1, mode=mode)
+        warm.run(2, check_every=1, bound=1.0)
+        warm.close()
+        ro = S.CheckedRollout(sur, p, seed=1, mode=mode)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        stats = ro.run(n_calls, check_every=10, bound=S.DEFAULT_CHECK_BOUND)
+        torch.cuda.synchronize()
+        t_sur = time.perf_counter() - t
+        err = S.tip_error(p, ro.system.get_state()[0], ref[n_calls])
+        ro.close()
+        rec[mode] = dict(rollout_s=t_sur, speedup=t_plain / t_sur, rollout_elem_steps_per_s=el_steps / t_sur,
+                         final_tip_err=float(err.max()), stats=stats)
+        assert err.max() <= 1e-3, rec
+        assert t_sur < t_plain, rec                       # what the trained network gains
     _record("surrogate_gain", rec)
     print(json.dumps(rec, indent=1))
     assert worst <= 1e-3, rec                             # the bound, every 20th call, all 4096 rods
-    assert err.max() <= 1e-3, rec
-    assert t_sur < t_plain, rec                           # what the trained network gains
 
 
-def test_untrained_network_falls_back_to_the_plain_step():
+@pytest.mark.parametrize("mode", ["global", "local"])
+def test_untrained_network_falls_back_to_the_plain_step(mode):
     """With random weights every checked segment exceeds the bound, is undone and redone with
     the plain step: the result is the plain trajectory."""
     import torch
@@ -299,7 +302,7 @@ def test_untrained_network_falls_back_to_the_plain_step():
     sur = Surrogate(W, dt)
     sur.set_params(S.initial_params(seed=5, last_gain=1.0))
     sur.set_scales(np.zeros(24), np.ones(24), np.full(15, 1e-3))
-    ro = S.CheckedRollout(sur, p, n_sample=8, seed=2)
+    ro = S.CheckedRollout(sur, p, n_sample=8, seed=2, mode=mode, n_shadows=3)
     stats = ro.run(n_calls, check_every=every, bound=1e-3)
     assert stats["fallback_calls"] == n_calls and stats["surrogate_calls"] == 0, stats
     assert stats["checks"] == n_calls // every and stats["rejected_err"] > 1e-3

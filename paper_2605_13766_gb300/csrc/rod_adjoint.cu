@@ -339,6 +339,16 @@ __global__ void __launch_bounds__(256) adjoint_kernel(AdjointParams A, LaunchSha
       nb[aa] += q[3 * aa] * Nb[0] + q[3 * aa + 1] * Nb[1] + q[3 * aa + 2] * Nb[2];
       for (int b = 0; b < 3; ++b) Qhb[3 * aa + b] = n[aa] * Nb[b];
     }
+    if (P.magnet) {
+      // magnetic couple rl (m x (Qh b)): d/dQh_ab of taub . (m x Qh b) = (taub x m)_a b_b rl
+      double mg[3], lxm[3];
+      for (int c = 0; c < 3; ++c) mg[c] = rl * P.magnet[c * P.E + ge];
+      lxm[0] = taub[1] * mg[2] - taub[2] * mg[1];
+      lxm[1] = taub[2] * mg[0] - taub[0] * mg[2];
+      lxm[2] = taub[0] * mg[1] - taub[1] * mg[0];
+      for (int aa = 0; aa < 3; ++aa)
+        for (int b = 0; b < 3; ++b) Qhb[3 * aa + b] += lxm[aa] * m.BF[b];
+    }
     // n = (S ie) sigma, sigma = Ql / rl - e3 - sigma0
     for (int c = 0; c < 3; ++c) {
       const double sgb = rc->S[c] * ie * nb[c];

@@ -353,16 +353,30 @@ __global__ void __launch_bounds__(256, 4) gather_kernel(ContactArgs A) {
         atomicOr(A.err, ERR_OVERFLOW);
         continue;
       }
+      // the next candidate's records are loaded while the current one is tested
+      int4 bb_next = make_int4(0, 0, 0, 0);
+      float4 gb_next = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (b0 < b1) {
+        bb_next = A.recB[b0];
+        gb_next = A.recA[b0];
+      }
       for (int t = b0; t < b1; ++t) {
-        const int4 bb = A.recB[t];
+        const int4 bb = bb_next;
+        const float4 gb = gb_next;
+        if (t + 1 < b1) {
+          bb_next = A.recB[t + 1];
+          gb_next = A.recA[t + 1];
+        }
         if (bb.y == ra) continue;
-        // FP32 lower bound of the segment distance: |m_a - m_b| - (h_a + h_b)
-        const float4 gb = A.recA[t];
+        // FP32 lower bound of the segment distance, |m_a - m_b| - (h_a + h_b) > r_a + r_b + tol,
+        // compared squared: |m_a - m_b|^2 > (r_a + r_b + tol + h_a + h_b)^2 (tol covers the
+        // rounding of both forms)
         const float ddx = ga.x - gb.x, ddy = ga.y - gb.y, ddz = ga.z - gb.z;
-        const float dm = sqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
+        const float dm2 = ddx * ddx + ddy * ddy + ddz * ddz;
         const float mb_inf = fmaxf(fabsf(gb.x), fmaxf(fabsf(gb.y), fabsf(gb.z)));
         const float tol = 1e-6f + 4e-6f * (ma_inf + mb_inf + ga.w + gb.w);
-        if (dm - (ga.w + gb.w) > rada + __int_as_float(bb.z) + tol) continue;
+        const float reach = rada + __int_as_float(bb.z) + tol + ga.w + gb.w;
+        if (dm2 > reach * reach) continue;
         const PairForce pf = pair_force(A, a, ra, bb.x, bb.y);
         if (pf.hit) {
 #pragma unroll

@@ -86,6 +86,34 @@ def test_adjoint_matches_oracle_finite_differences_small():
     _record("adjoint_small_oracle_fd", report)
 
 
+def test_adjoint_with_magnetic_and_muscle_couples_matches_oracle_finite_differences():
+    """The same check with a rotating-field magnetic couple (which depends on the directors)
+    and travelling-wave muscle couples on every rod."""
+    p = _small_problem()
+    rng = np.random.default_rng(8)
+    mag = np.zeros((3, p.n_elems))
+    mag[2] = rng.uniform(0.5, 1.5, p.n_elems)
+    mag[0] = rng.normal(0, 0.3, p.n_elems)
+    p = p.replace(magnetization=mag, field_b0=np.array([0.0, 0.0, 1e-3]), field_bc=np.array([4e-3, 0.0, 0.0]),
+                  field_bs=np.array([0.0, 4e-3, 0.0]), field_omega=2 * np.pi * 20.0,
+                  muscle_amp=np.full(p.n_rods, 2e-6), muscle_period=np.full(p.n_rods, 0.01),
+                  muscle_wavelength=np.full(p.n_rods, 0.05), muscle_phase=np.linspace(0, 3, p.n_rods))
+    n_steps, dt, every = 200, 1e-5, 50
+    L, gk, gc, _ = _grads_gpu(p, n_steps, dt, every)
+    L_ref = _loss_oracle(p, p.rest_kappa, p.elem_couple, n_steps, dt)
+    assert abs(L - L_ref) <= 1e-10 * abs(L_ref)
+    def cd(dk, dc, h):
+        return (_loss_oracle(p, p.rest_kappa + h * dk, p.elem_couple + h * dc, n_steps, dt)
+                - _loss_oracle(p, p.rest_kappa - h * dk, p.elem_couple - h * dc, n_steps, dt)) / (2 * h)
+
+    for dk, dc in _directions(p, 6, seed=4):
+        # Richardson's extrapolation of central differences at h = 1e-4 and 2e-4: at h = 1e-6
+        # the rounding of the loss reaches 1e-6 of the smaller directional derivatives here
+        fd = (4 * cd(dk, dc, 1e-4) - cd(dk, dc, 2e-4)) / 3
+        ad = float((gk * dk).sum() + (gc * dc).sum())
+        assert abs(ad - fd) <= 1e-6 * abs(fd), (ad, fd)
+
+
 def test_adjoint_full_workload_matches_finite_differences():
     import torch
     from paper_2605_13766_gb300 import RodSystem
@@ -137,13 +165,20 @@ def _record(name, rows):
                         "rel_err_reference": abs(a - c) / abs(c)} for a, b, c in rows], f, indent=1)
 
 
-def test_state_adjoint_of_one_step_matches_oracle():
-    """d L / d(initial state) after one step, every entry, against central differences of the
-    oracle (positions, velocities, the nine director entries, angular velocities)."""
+@pytest.mark.parametrize("magnetic", [False, True])
+def test_state_adjoint_of_one_step_matches_oracle(magnetic):
+    """d L / d(initial state) after one step against central differences of the oracle
+    (positions, velocities, angular velocities entry by entry; directors along rotations),
+    without and with a magnetic couple (which depends on the directors)."""
     import torch
     from paper_2605_13766_gb300 import RodSystem
     from paper_2605_13766_gb300.autograd import rollout, tip_indices
     p = rodgen.perturbed(_small_problem(), seed=9, pos=0.01, vel=0.1, rot=0.05, omega=5.0)
+    if magnetic:
+        mag = np.zeros((3, p.n_elems))
+        mag[2] = 2.0
+        mag[1] = 0.5
+        p = p.replace(magnetization=mag, field_b0=np.array([3e-2, -2e-2, 1e-2]))
     dt = 1e-5
     s = RodSystem(p)
     k0 = torch.tensor(p.rest_kappa, device="cuda", requires_grad=True)
@@ -209,3 +244,38 @@ def test_state_adjoint_of_one_step_matches_oracle():
         assert abs(ad - fd) <= 1e-5 * scale, (e, ad, fd)
         checked += 1
     assert checked > 60
+
+
+def test_adjoint_matches_the_oracle_reverse_sweep():
+    """Every entry of the GPU gradients with respect to the rest curvature and the element
+    couples, and the adjoint of the free initial positions, velocities and angular velocities,
+    against the oracle's reverse sweep (discrete adjoint composed from one-step Jacobians of the
+    oracle) on a two-rod problem over 12 steps."""
+    import torch
+    from paper_2605_13766_gb300 import RodSystem
+    from paper_2605_13766_gb300.autograd import rollout
+    from oracle.reverse_sweep import reverse_sweep
+    from test_oracle_reverse_sweep import tiny_problem, weights
+    p = tiny_problem()
+    n_steps, dt = 12, 1e-5
+    W = weights(p)
+    gk_ref, gc_ref, lam_ref = reverse_sweep(p, n_steps, dt, W)
+    s = RodSystem(p)
+    k0 = torch.tensor(p.rest_kappa, device="cuda", requires_grad=True)
+    c0 = torch.tensor(p.elem_couple, device="cuda", requires_grad=True)
+    state0 = [torch.tensor(a, device="cuda") for a in p.state()]
+    out = rollout(s, k0, c0, state0, n_steps, dt, 4)
+    L = sum((o * torch.tensor(wt, device="cuda")).sum() for o, wt in zip(out, W))
+    L.backward()
+    gk, gc = k0.grad.cpu().numpy(), c0.grad.cpu().numpy()
+    assert np.abs(gk - gk_ref).max() <= 1e-6 * np.abs(gk_ref).max(), np.abs(gk - gk_ref).max() / np.abs(gk_ref).max()
+    assert np.abs(gc - gc_ref).max() <= 1e-6 * np.abs(gc_ref).max(), np.abs(gc - gc_ref).max() / np.abs(gc_ref).max()
+    adj = [a.cpu().numpy() for a in s.adjoint_of_state()]
+    free_nodes = np.ones(p.n_nodes, dtype=bool)
+    free_elems = np.ones(p.n_elems, dtype=bool)
+    for r in np.flatnonzero(p.clamp_base):
+        free_nodes[p.node_offsets()[r]] = False
+        free_elems[p.elem_offsets()[r]] = False
+    for a_idx, mask in ((0, free_nodes), (1, free_nodes), (3, free_elems)):
+        got, ref = adj[a_idx][:, mask], lam_ref[a_idx][:, mask]
+        assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max(), (a_idx, np.abs(got - ref).max() / np.abs(ref).max())

@@ -125,14 +125,14 @@ def test_trajectory_with_friction_and_a_box_400_steps():
     assert _rel(got[1], ref[1]) <= 1e-7
 
 
-def test_adjoint_refuses_the_magnetic_couple_and_walls():
+def test_adjoint_refuses_walls():
     from paper_2605_13766_gb300 import RodError
     p = _magnetic_muscle_carpet(side=2)
     s = _gpu(p)
     with pytest.raises(RodError):
         s.forward_checkpointed(10, 1e-5, 5)
-    # muscle couples alone depend on time only: the adjoint runs
-    q = p.replace(magnetization=None, wall_point=None, wall_normal=None, wall_velocity=None)
+    # the magnetic couple and the muscle couples are in the adjoint: it runs without walls
+    q = p.replace(wall_point=None, wall_normal=None, wall_velocity=None)
     s = _gpu(q)
     s.forward_checkpointed(10, 1e-5, 5)
 

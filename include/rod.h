@@ -160,9 +160,10 @@ rod_status rod_system_contact_forces(rod_system* sys, double* f);
 rod_status rod_system_set_launch(rod_system* sys, int32_t elems_per_block, int32_t threads_per_block);
 rod_status rod_system_get_launch(const rod_system* sys, int32_t* elems_per_block, int32_t* threads_per_block);
 
-/* Differentiation (hand-written adjoint of the step; contact and walls must be off: their
- * state derivatives are not in the reverse sweep; the magnetic couple is covered, muscle
- * couples depend on time only and are covered too).
+/* Differentiation (hand-written adjoint of the step; rod-rod contact must be off: its state
+ * derivatives are not in the reverse sweep; the magnetic couple and walls (normal force and
+ * friction, piecewise smooth: derivatives of the active branch) are covered, muscle couples
+ * depend on time only).
  * rod_system_set_params replaces the rest curvature [3*V] and/or the element couples [3*E]
  * (NULL leaves one unchanged; on_device as for set_state).
  * rod_system_forward_checkpointed advances n_steps steps of dt from the current state, one

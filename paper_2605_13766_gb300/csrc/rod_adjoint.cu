@@ -274,6 +274,47 @@ __global__ void __launch_bounds__(256) adjoint_kernel(AdjointParams A, LaunchSha
       a.FB[c * m.CN + j] = abar * m.IM[j];
       a.VB[c * m.CN + j] = vb - rc->damp_lin * abar;   // adjoint of v (rate update + damping)
     }
+    // walls: F = fn n + fr vt with fn = k delta - c (v - u).n, delta = r - n.(xh - p - u t),
+    // vt the tangential part of v - u, fr = -mu fn / max(|vt|, v_slip) (active contacts only)
+    for (int kw = 0; kw < P.n_walls && !held; ++kw) {
+      const double tw = A.t + h;
+      const double* nn = P.wall_n[kw];
+      double d[3], vr[3], Fb[3];
+      for (int c = 0; c < 3; ++c) {
+        d[c] = m.X[c * m.CN + j] - fma(P.wall_u[kw][c], tw, P.wall_p[kw][c]);
+        vr[c] = a.V0[c * m.CN + j] - P.wall_u[kw][c];
+        Fb[c] = a.FB[c * m.CN + j];
+      }
+      const double delta = rc->radius - fma(d[0], nn[0], fma(d[1], nn[1], d[2] * nn[2]));
+      if (!(delta > 0.0)) continue;
+      const double vn = fma(vr[0], nn[0], fma(vr[1], nn[1], vr[2] * nn[2]));
+      const double fn = P.wall_k * delta - P.wall_c * vn;
+      if (!(fn > 0.0)) continue;
+      double vt[3];
+      for (int c = 0; c < 3; ++c) vt[c] = vr[c] - vn * nn[c];
+      const double sp = sqrt(fma(vt[0], vt[0], fma(vt[1], vt[1], vt[2] * vt[2])));
+      const double s_n = Fb[0] * nn[0] + Fb[1] * nn[1] + Fb[2] * nn[2];
+      double fnb = s_n, vtb[3] = {0.0, 0.0, 0.0};
+      if (P.wall_mu > 0.0) {
+        const double den = fmax(sp, P.wall_vslip);
+        const double fr = -P.wall_mu * fn / den;
+        const double g = Fb[0] * vt[0] + Fb[1] * vt[1] + Fb[2] * vt[2];
+        fnb += -P.wall_mu / den * g;
+        for (int c = 0; c < 3; ++c) vtb[c] = fr * Fb[c];
+        if (sp > P.wall_vslip) {
+          const double spb = P.wall_mu * fn / (den * den) * g;
+          for (int c = 0; c < 3; ++c) vtb[c] += spb * vt[c] / sp;
+        }
+      }
+      // vt = vr - vn n;  fn = k delta - c vn;  vn = vr . n;  delta = r - n . d
+      const double ntb = nn[0] * vtb[0] + nn[1] * vtb[1] + nn[2] * vtb[2];
+      const double vnb = -ntb - P.wall_c * fnb;
+      const double deltab = P.wall_k * fnb;
+      for (int c = 0; c < 3; ++c) {
+        a.VB[c * m.CN + j] += vtb[c] + vnb * nn[c];
+        a.XB[c * m.CN + j] += -deltab * nn[c];
+      }
+    }
   }
   __syncthreads();
 

@@ -1029,7 +1029,6 @@ rod_status rod_system_forward_checkpointed(rod_system* s, int64_t n_steps, doubl
   if (!s) return fail(ROD_ERR_ARG, "null system");
   if (!s->state_set) return fail(ROD_ERR_STATE, "no state has been set");
   if (s->contact.enabled) return fail(ROD_ERR_STATE, "the adjoint does not include contact; disable it first");
-  if (s->n_walls > 0) return fail(ROD_ERR_STATE, "the adjoint does not include walls");
   if (n_steps < 1 || every < 1 || !(dt > 0) || !std::isfinite(dt)) return fail(ROD_ERR_ARG, "need n_steps, every >= 1 and dt > 0");
   const int64_t ss = state_size(s);
   const int64_t nck = (n_steps + every - 1) / every;

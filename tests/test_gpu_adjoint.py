@@ -114,6 +114,26 @@ def test_adjoint_with_magnetic_and_muscle_couples_matches_oracle_finite_differen
         assert abs(ad - fd) <= 1e-6 * abs(fd), (ad, fd)
 
 
+def test_adjoint_with_a_wall_matches_oracle_finite_differences():
+    """Two of the rods press into a side wall during the whole run (normal spring-dashpot;
+    friction is checked by the one-step state adjoint, where no slip threshold is crossed)."""
+    p = _small_problem().replace(wall_point=np.array([[0.003, 0.0, 0.0]]), wall_normal=np.array([[-1.0, 0.0, 0.0]]),
+                                 wall_k=50.0, wall_c=0.01)
+    n_steps, dt, every = 200, 1e-5, 50
+    L, gk, gc, _ = _grads_gpu(p, n_steps, dt, every)
+    L_ref = _loss_oracle(p, p.rest_kappa, p.elem_couple, n_steps, dt)
+    assert abs(L - L_ref) <= 1e-10 * abs(L_ref)
+
+    def cd(dk, dc, h):
+        return (_loss_oracle(p, p.rest_kappa + h * dk, p.elem_couple + h * dc, n_steps, dt)
+                - _loss_oracle(p, p.rest_kappa - h * dk, p.elem_couple - h * dc, n_steps, dt)) / (2 * h)
+
+    for dk, dc in _directions(p, 4, seed=6):
+        fd = (4 * cd(dk, dc, 1e-4) - cd(dk, dc, 2e-4)) / 3
+        ad = float((gk * dk).sum() + (gc * dc).sum())
+        assert abs(ad - fd) <= 1e-6 * abs(fd), (ad, fd)
+
+
 def test_adjoint_full_workload_matches_finite_differences():
     import torch
     from paper_2605_13766_gb300 import RodSystem
@@ -165,8 +185,8 @@ def _record(name, rows):
                         "rel_err_reference": abs(a - c) / abs(c)} for a, b, c in rows], f, indent=1)
 
 
-@pytest.mark.parametrize("magnetic", [False, True])
-def test_state_adjoint_of_one_step_matches_oracle(magnetic):
+@pytest.mark.parametrize("magnetic,wall", [(False, False), (True, False), (False, True)])
+def test_state_adjoint_of_one_step_matches_oracle(magnetic, wall):
     """d L / d(initial state) after one step against central differences of the oracle
     (positions, velocities, angular velocities entry by entry; directors along rotations),
     without and with a magnetic couple (which depends on the directors)."""
@@ -179,6 +199,12 @@ def test_state_adjoint_of_one_step_matches_oracle(magnetic):
         mag[2] = 2.0
         mag[1] = 0.5
         p = p.replace(magnetization=mag, field_b0=np.array([3e-2, -2e-2, 1e-2]))
+    if wall:
+        # a slanted wall that the nodes of the rods at x = 0 press into, sliding along it
+        nrm = np.array([-1.0, 0.1, 0.05])
+        nrm /= np.linalg.norm(nrm)
+        p = p.replace(wall_point=np.array([[0.003, 0.0, 0.0]]), wall_normal=nrm[None, :], wall_k=50.0,
+                      wall_c=0.01, wall_mu=0.3, wall_vslip=1e-4, wall_velocity=np.array([[0.0, 0.0, 0.2]]))
     dt = 1e-5
     s = RodSystem(p)
     k0 = torch.tensor(p.rest_kappa, device="cuda", requires_grad=True)
@@ -209,9 +235,15 @@ def test_state_adjoint_of_one_step_matches_oracle(magnetic):
     for r in np.flatnonzero(p.clamp_base):
         free_nodes[p.node_offsets()[r]] = False
         free_elems[p.elem_offsets()[r]] = False
+    touching = np.ones(p.n_nodes, dtype=bool)
+    if wall:
+        # the entries of the nodes in contact with the wall (where its force acts)
+        pen = p.radius[0] - (p.wall_normal[0][:, None] * (p.x - p.wall_point[0][:, None])).sum(axis=0)
+        touching = pen > 0
+        assert touching[free_nodes].sum() >= 2
     for a_idx in (0, 1, 3):
         arr = base[a_idx]
-        mask = np.broadcast_to(free_nodes if a_idx < 2 else free_elems, arr.shape)
+        mask = np.broadcast_to(free_nodes & touching if a_idx < 2 else free_elems, arr.shape)
         flat = np.flatnonzero(mask)
         for f in rng.choice(flat, size=min(24, flat.size), replace=False):
             plus = [b.copy() for b in base]
@@ -243,7 +275,7 @@ def test_state_adjoint_of_one_step_matches_oracle(magnetic):
         scale = max(abs(fd), 1e-3 * np.abs(adj[2]).max(), 1e-12)
         assert abs(ad - fd) <= 1e-5 * scale, (e, ad, fd)
         checked += 1
-    assert checked > 60
+    assert checked > (40 if wall else 60)
 
 
 def test_adjoint_matches_the_oracle_reverse_sweep():

@@ -125,16 +125,15 @@ def test_trajectory_with_friction_and_a_box_400_steps():
     assert _rel(got[1], ref[1]) <= 1e-7
 
 
-def test_adjoint_refuses_walls():
+def test_adjoint_refuses_rod_rod_contact_only():
     from paper_2605_13766_gb300 import RodError
     p = _magnetic_muscle_carpet(side=2)
     s = _gpu(p)
+    s.forward_checkpointed(10, 1e-5, 5)          # magnetic couple, muscles and walls: covered
+    q = _dense_with_friction(n_rods=10, box=0.05)
+    s = _gpu(q)
     with pytest.raises(RodError):
         s.forward_checkpointed(10, 1e-5, 5)
-    # the magnetic couple and the muscle couples are in the adjoint: it runs without walls
-    q = p.replace(wall_point=None, wall_normal=None, wall_velocity=None)
-    s = _gpu(q)
-    s.forward_checkpointed(10, 1e-5, 5)
 
 
 def test_invalid_walls_and_friction_are_rejected():

@@ -99,7 +99,10 @@ typedef struct {
 #define ROD_MAX_WALLS 8
 
 /* Create a system; validates the description (ROD_ERR_ARG with a message on failure).
- * Rods longer than rod_max_elements_per_rod() are rejected. */
+ * Rods up to the launch shape's elements per block (at most rod_max_elements_per_rod()) are
+ * packed into thread blocks in shared memory; a longer rod (up to 2^24 elements) is stepped by
+ * a cooperative launch over the whole GPU with its working arrays in global memory and
+ * grid-wide barriers between the stages (same arithmetic; not covered by the adjoint). */
 rod_status rod_system_create(const rod_system_desc* desc, rod_system** out);
 
 /* Free the system and all its device memory (NULL is accepted). */
@@ -156,7 +159,8 @@ rod_status rod_system_contact_forces(rod_system* sys, double* f);
 
 /* Launch shape used by the step kernels: elements per thread block and threads per block
  * (0 keeps the built-in default for that value).  Returns ROD_ERR_ARG if the shape cannot
- * hold the longest rod or needs more shared memory than a block has. */
+ * fit the block limits or needs more shared memory than a block has (rods longer than the
+ * shape's elements per block take the cooperative path). */
 rod_status rod_system_set_launch(rod_system* sys, int32_t elems_per_block, int32_t threads_per_block);
 rod_status rod_system_get_launch(const rod_system* sys, int32_t* elems_per_block, int32_t* threads_per_block);
 
@@ -212,7 +216,8 @@ rod_status rod_system_launch_count(const rod_system* sys, int64_t* launches);
 rod_status rod_system_autotune(rod_system* sys, double dt, int32_t trial_steps, int32_t* best_elems,
                                int32_t* best_threads, double* best_ms);
 
-/* Longest rod (elements) one thread block can hold with the largest supported shape. */
+/* Longest rod (elements) one thread block can hold with the largest supported shape; longer
+ * rods take the cooperative path. */
 int32_t rod_max_elements_per_rod(void);
 
 /* Learned surrogate of a window of fine steps for rods of 50 elements (the paper has no

@@ -177,6 +177,10 @@ struct rod_system {
   LaunchShape shape{0, 0, 0};
   DevBuf<Pack> packs;
   int n_packs = 0;
+  // rods longer than a block holds: one pack each, run by cooperative launches with their
+  // working arrays in long_scratch
+  std::vector<Pack> long_packs;
+  DevBuf<double> long_scratch;
   bool shape_user = false;
   // misc
   double gravity[3] = {0, 0, 0};
@@ -211,15 +215,36 @@ struct rod_system {
 namespace {
 
 rod_status build_packs(rod_system* s, const LaunchShape& shape) {
-  if (shape.cap_elems < s->max_n)
-    return fail(ROD_ERR_ARG, "launch shape holds %d elements per block but the longest rod has %d", shape.cap_elems,
-                s->max_n);
-  std::vector<Pack> packs;
+  std::vector<Pack> packs, longs;
   Pack cur{};
   bool open = false;
+  size_t scratch = 0;
   for (int r = 0; r < s->R; ++r) {
     const RodConst& rc = s->rods_h[r];
     const int n = rc.n;
+    if (n > shape.cap_elems) {
+      // too long for a block: a pack of its own on the cooperative (grid-wide) path
+      if (open) {
+        packs.push_back(cur);
+        open = false;
+      }
+      Pack lp{};
+      lp.rod0 = r;
+      lp.nrods = 1;
+      lp.elem0 = rc.elem0;
+      lp.nelem = n;
+      lp.node0 = rc.node0;
+      lp.nnode = n + 1;
+      lp.vor0 = rc.elem0 - r;
+      lp.nvor = n - 1;
+      longs.push_back(lp);
+      LaunchShape ls;
+      ls.cap_elems = n;
+      ls.cap_rods = 1;
+      ls.threads = 256;
+      scratch = std::max(scratch, step_smem_bytes(ls));
+      continue;
+    }
     if (open && (cur.nelem + n > shape.cap_elems || cur.nrods + 1 > shape.cap_rods)) {
       packs.push_back(cur);
       open = false;
@@ -238,9 +263,14 @@ rod_status build_packs(rod_system* s, const LaunchShape& shape) {
     cur.nvor += n - 1;
   }
   if (open) packs.push_back(cur);
-  CUDA_TRY(s->packs.alloc(packs.size()));
-  CUDA_TRY(cudaMemcpy(s->packs.p, packs.data(), packs.size() * sizeof(Pack), cudaMemcpyHostToDevice));
+  if (!packs.empty()) {
+    CUDA_TRY(s->packs.alloc(packs.size()));
+    CUDA_TRY(cudaMemcpy(s->packs.p, packs.data(), packs.size() * sizeof(Pack), cudaMemcpyHostToDevice));
+  }
   s->n_packs = static_cast<int>(packs.size());
+  s->long_packs = longs;
+  if (scratch > 0 && (int64_t)s->long_scratch.n * 8 < (int64_t)scratch)
+    CUDA_TRY(s->long_scratch.alloc((scratch + 7) / 8));
   s->shape = shape;
   s->shape_version += 1;
   return ROD_OK;
@@ -303,6 +333,9 @@ StepParams make_params(rod_system* s) {
   P.wall_vslip = s->wall_vslip;
   P.fseg = nullptr;
   P.err = s->err.p;
+  P.long_packs_h = s->long_packs.empty() ? nullptr : s->long_packs.data();
+  P.n_long = static_cast<int32_t>(s->long_packs.size());
+  P.long_scratch = s->long_scratch.p;
   return P;
 }
 
@@ -463,8 +496,7 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
         !std::isfinite(d->density[r]))
       return fail(ROD_ERR_ARG, "rod %d: non-finite material parameter", r);
   }
-  if (max_n > kMaxCapElems)
-    return fail(ROD_ERR_ARG, "a rod has %d elements; one thread block holds at most %d", max_n, kMaxCapElems);
+  if (max_n > (1 << 24)) return fail(ROD_ERR_ARG, "a rod has %d elements (at most %d)", max_n, 1 << 24);
   if (E + R >= (int64_t(1) << 31) / 9) return fail(ROD_ERR_ARG, "ensemble too large (%lld elements)", (long long)E);
   for (int64_t i = 0; i < E; ++i)
     if (!(d->rest_len[i] > 0) || !std::isfinite(d->rest_len[i]))
@@ -692,6 +724,7 @@ rod_status rod_system_destroy(rod_system* s) {
   s->clamp_Q.release();
   s->rods.release();
   s->packs.release();
+  s->long_scratch.release();
   s->ckpt.release();
   s->seg_states.release();
   s->adj.release();
@@ -788,7 +821,8 @@ rod_status rod_system_step_async(rod_system* s, int64_t n_steps, double dt) {
     // steps 0 .. n-2 bin the next step's positions; the last one ends on a half step
     const int64_t binned = n_steps - 1;
     int64_t k = 0;
-    if (s->use_graphs && !s->prof.enabled && binned >= kGraphSteps) {
+    // (cooperative launches of long rods stay eager: no graph replay when there are any)
+    if (s->use_graphs && !s->prof.enabled && binned >= kGraphSteps && s->long_packs.empty()) {
       st = ensure_contact_graph(s, Pb, dt);
       if (st != ROD_OK) return st;
       if (s->graph_exec) {
@@ -966,7 +1000,7 @@ rod_status rod_system_autotune(rod_system* s, double dt, int32_t trial_steps, in
   const int caps[] = {192, 256, 320, 384, 448, 512, 640, 768};
   const int thrs[] = {128, 256, 384, 512};
   for (int cap : caps) {
-    if (cap < s->max_n) continue;
+    if (cap < std::min(s->max_n, kMaxCapElems)) continue;
     for (int thr : thrs) {
       if (thr > cap) continue;
       if (rod_system_set_launch(s, cap, thr) != ROD_OK) continue;

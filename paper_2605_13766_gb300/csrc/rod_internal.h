@@ -98,6 +98,11 @@ struct StepParams {
   float bin_inv_h;
   int bin_dim[3];
   float bin_l_allowed;        // longest element the cell covers, less the FP32 rounding margin
+  // host side only: packs of rods too long for a block (one rod each) and the global scratch
+  // their cooperative launches use as working memory
+  const struct Pack* long_packs_h;
+  int32_t n_long;
+  double* long_scratch;
 };
 
 // Kernel classes for the optional per-kernel timing (rod_system_profile).

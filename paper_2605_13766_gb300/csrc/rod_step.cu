@@ -23,6 +23,8 @@
 #include <cmath>
 #include <cstdint>
 
+#include <algorithm>
+
 #include "rod_internal.h"
 #include "rod_step_device.cuh"
 
@@ -32,43 +34,44 @@ namespace {
 
 // ------------------------------------------------------------------------- the pack kernel
 
+// The work of one pack, shared by the block kernel (pack in shared memory, one block) and the
+// cooperative kernel (pack in global memory, every block of the grid); stage_sync is the
+// block's or the grid's barrier.
 template <int MODE>
-__global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, int64_t n_steps, double t0, double dt,
-                                                   int last_half, double* acc_v, double* acc_w) {
-  extern __shared__ double smem_d[];
-  // a step after a latched error (non-finite state, contact overflow) is skipped
+__device__ __forceinline__ void pack_body(const StepParams& P, const Pack& pk, Smem& m, int64_t n_steps, double t0,
+                                          double dt, int last_half, double* acc_v, double* acc_w) {
+  // a step after a latched error (non-finite state, contact overflow) is skipped (the word is
+  // read before the first barrier, so every block of a grid takes the same path)
   if (MODE == MODE_ONE_STEP && *(volatile int*)P.err != 0) return;
-  const Pack pk = P.packs[blockIdx.x];
-  Smem m = carve(smem_d, S);
   const int Ep = pk.nelem, Np = pk.nnode;
 
   stage_pack(P, pk, m);
 
   if (MODE == MODE_KIN_HALF) {
     kinematic(P, pk, m, 0.5 * dt);
-    __syncthreads();
+    stage_sync(m);
   } else if (MODE == MODE_RHS) {
     actuation_values(P, pk, m, t0);
     stage_elements(P, pk, m);
-    __syncthreads();
+    stage_sync(m);
     stage_voronoi(P, pk, m);
-    __syncthreads();
+    stage_sync(m);
     stage_rotation<MODE_RHS>(P, pk, m, dt, 0.0, acc_w);
     stage_translation<MODE_RHS>(P, pk, m, dt, acc_v, t0);
     return;
   } else {
     if (MODE == MODE_STEPS) {
       kinematic(P, pk, m, 0.5 * dt);
-      __syncthreads();
+      stage_sync(m);
     }
     const double tbase = P.t_dev ? *P.t_dev : t0;
     const bool timed = has_time_values(P);
     if (n_steps > 0) actuation_values(P, pk, m, tbase + 0.5 * dt);
     for (int64_t s = 0; s < n_steps; ++s) {
       stage_elements(P, pk, m);
-      __syncthreads();
+      stage_sync(m);
       stage_voronoi(P, pk, m);
-      __syncthreads();
+      stage_sync(m);
       // rate updates fused with the following kinematic stage: each thread moves only the
       // elements and nodes whose rates it has just updated
       const bool last = (s == n_steps - 1);
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, 
       // the next step's time values: their only readers (the element stage) are past a barrier;
       // the next step's element stage waits for the barrier below
       if (timed && !last) time_values(P, pk, m, t + dt);
-      __syncthreads();
+      stage_sync(m);
     }
   }
 
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, 
   // cell with one atomic per distinct cell in the warp.
   if ((MODE == MODE_KIN_HALF || (MODE == MODE_ONE_STEP && !last_half)) && P.bin_count) {
     bool grid_bad = false, nonfinite = false;
-    for (int i = threadIdx.x; i < Ep; i += blockDim.x) {
+    for (int i = m.t0; i < Ep; i += m.ts) {
       const int j = i + m.erod[i];
       float p0[3], p1[3], mid[3];
       float ll = 0.f;
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, 
 
   // ---- write back, flag non-finite values
   bool bad = false;
-  for (int i = threadIdx.x; i < Ep; i += blockDim.x) {
+  for (int i = m.t0; i < Ep; i += m.ts) {
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       const double q = m.QQ[a * m.CE + i];
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, 
       P.w[c * P.E + pk.elem0 + i] = ww;
     }
   }
-  for (int j = threadIdx.x; j < Np; j += blockDim.x) {
+  for (int j = m.t0; j < Np; j += m.ts) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const double xx = m.X[c * m.CN + j], vv = m.VN[c * m.CN + j];
@@ -146,8 +149,36 @@ __global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, 
       P.v[c * P.N + pk.node0 + j] = vv;
     }
   }
-  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(P.err, ERR_NONFINITE);
+  if (m.grid) {
+    if (__any_sync(__activemask(), bad) && (threadIdx.x & 31) == __ffs(__activemask()) - 1) atomicOr(P.err, ERR_NONFINITE);
+  } else if (__syncthreads_or(bad) && threadIdx.x == 0) {
+    atomicOr(P.err, ERR_NONFINITE);
+  }
 }
+
+template <int MODE>
+__global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, int64_t n_steps, double t0, double dt,
+                                                   int last_half, double* acc_v, double* acc_w) {
+  extern __shared__ double smem_d[];
+  const Pack pk = P.packs[blockIdx.x];
+  Smem m = carve(smem_d, S);
+  pack_body<MODE>(P, pk, m, n_steps, t0, dt, last_half, acc_v, acc_w);
+}
+
+// One pack too long for a block: its working arrays live in global memory (scratch, carved
+// like the shared-memory layout with the pack's own capacities) and the whole grid of a
+// cooperative launch shares it, with grid-wide barriers between the stages.
+template <int MODE>
+__global__ void __launch_bounds__(256) pack_kernel_grid(StepParams P, Pack pk, LaunchShape S, double* scratch,
+                                                        int64_t n_steps, double t0, double dt, int last_half,
+                                                        double* acc_v, double* acc_w) {
+  Smem m = carve(scratch, S);
+  m.t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  m.ts = gridDim.x * blockDim.x;
+  m.grid = true;
+  pack_body<MODE>(P, pk, m, n_steps, t0, dt, last_half, acc_v, acc_w);
+}
+
 
 }  // namespace
 
@@ -166,6 +197,40 @@ const char* kernel_class_name(int k) {
   return (k >= 0 && k < K_NUM_CLASSES) ? names[k] : "?";
 }
 
+namespace {
+
+template <int MODE>
+cudaError_t launch_grid_packs(const StepParams& P, int64_t n_steps, double t0, double dt, int last_half, double* acc_v,
+                              double* acc_w, cudaStream_t st) {
+  static int sms = 0, per_sm = 0;
+  cudaError_t e;
+  if (!sms) {
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pack_kernel_grid<MODE>, 256, 0)))
+      return e;
+    per_sm = per_sm > 0 ? per_sm : 1;
+  }
+  for (int k = 0; k < P.n_long; ++k) {
+    Pack pk = P.long_packs_h[k];
+    LaunchShape ls;
+    ls.cap_elems = pk.nelem;
+    ls.cap_rods = pk.nrods;
+    ls.threads = 256;
+    const int need = (std::max(pk.nelem, pk.nnode) + 255) / 256;
+    const int blocks = std::max(1, std::min(need, sms * per_sm));
+    StepParams Pc = P;
+    double* scratch = P.long_scratch;
+    void* args[] = {&Pc, &pk, &ls, &scratch, &n_steps, &t0, &dt, &last_half, &acc_v, &acc_w};
+    if ((e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(pack_kernel_grid<MODE>), dim3(blocks), dim3(256), args, 0,
+                                         st)))
+      return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
 cudaError_t launch_pack_kernel(const StepParams& P, const LaunchShape& s, int mode, int64_t n_steps, double t0,
                                double dt, int last_half, double* acc_v, double* acc_w, cudaStream_t st,
                                const LaunchHook& hook) {
@@ -178,30 +243,44 @@ cudaError_t launch_pack_kernel(const StepParams& P, const LaunchShape& s, int mo
     const LaunchHook& h; int c; cudaStream_t s;
     ~After() { h.after(c, s); }
   } after_guard{hook, cls, st};
+  cudaError_t e = cudaSuccess;
   switch (mode) {
     case MODE_STEPS: {
-      cudaFuncSetAttribute(pack_kernel<MODE_STEPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      pack_kernel<MODE_STEPS><<<grid, block, smem, st>>>(P, s, n_steps, t0, dt, last_half, acc_v, acc_w);
+      if (P.n_packs > 0) {
+        cudaFuncSetAttribute(pack_kernel<MODE_STEPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        pack_kernel<MODE_STEPS><<<grid, block, smem, st>>>(P, s, n_steps, t0, dt, last_half, acc_v, acc_w);
+      }
+      if (P.n_long) e = launch_grid_packs<MODE_STEPS>(P, n_steps, t0, dt, last_half, acc_v, acc_w, st);
       break;
     }
     case MODE_ONE_STEP: {
-      cudaFuncSetAttribute(pack_kernel<MODE_ONE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      pack_kernel<MODE_ONE_STEP><<<grid, block, smem, st>>>(P, s, n_steps, t0, dt, last_half, acc_v, acc_w);
+      if (P.n_packs > 0) {
+        cudaFuncSetAttribute(pack_kernel<MODE_ONE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        pack_kernel<MODE_ONE_STEP><<<grid, block, smem, st>>>(P, s, n_steps, t0, dt, last_half, acc_v, acc_w);
+      }
+      if (P.n_long) e = launch_grid_packs<MODE_ONE_STEP>(P, n_steps, t0, dt, last_half, acc_v, acc_w, st);
       break;
     }
     case MODE_KIN_HALF: {
-      cudaFuncSetAttribute(pack_kernel<MODE_KIN_HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      pack_kernel<MODE_KIN_HALF><<<grid, block, smem, st>>>(P, s, n_steps, t0, dt, last_half, acc_v, acc_w);
+      if (P.n_packs > 0) {
+        cudaFuncSetAttribute(pack_kernel<MODE_KIN_HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        pack_kernel<MODE_KIN_HALF><<<grid, block, smem, st>>>(P, s, n_steps, t0, dt, last_half, acc_v, acc_w);
+      }
+      if (P.n_long) e = launch_grid_packs<MODE_KIN_HALF>(P, n_steps, t0, dt, last_half, acc_v, acc_w, st);
       break;
     }
     case MODE_RHS: {
-      cudaFuncSetAttribute(pack_kernel<MODE_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      pack_kernel<MODE_RHS><<<grid, block, smem, st>>>(P, s, n_steps, t0, dt, last_half, acc_v, acc_w);
+      if (P.n_packs > 0) {
+        cudaFuncSetAttribute(pack_kernel<MODE_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        pack_kernel<MODE_RHS><<<grid, block, smem, st>>>(P, s, n_steps, t0, dt, last_half, acc_v, acc_w);
+      }
+      if (P.n_long) e = launch_grid_packs<MODE_RHS>(P, n_steps, t0, dt, last_half, acc_v, acc_w, st);
       break;
     }
     default:
       return cudaErrorInvalidValue;
   }
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

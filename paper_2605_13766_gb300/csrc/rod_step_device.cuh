@@ -2,6 +2,7 @@
 // (rod_step.cu) and the adjoint kernel (rod_adjoint.cu), so that the adjoint recomputes the
 // forward step with exactly the same arithmetic.  Internal to librod.
 #pragma once
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -114,7 +115,20 @@ struct Smem {
   int* rel0;                    // [CR+1] first element of each rod (pack-local)
   short *erod, *nrod, *vrod;    // pack-local rod of each element / node / Voronoi point
   int CE, CN, CV, CR;
+  // the threads that share the pack: this thread's index and their number (a block, or the
+  // whole grid of a cooperative launch whose working arrays live in global memory)
+  int t0, ts;
+  bool grid;
 };
+
+// Barrier between stages: the block, or the whole grid of a cooperative launch.
+__device__ __forceinline__ void stage_sync(const Smem& m) {
+  if (m.grid) {
+    cooperative_groups::this_grid().sync();
+  } else {
+    __syncthreads();
+  }
+}
 
 __device__ __forceinline__ Smem carve(double* base, const LaunchShape& S) {
   Smem m;
@@ -141,6 +155,9 @@ __device__ __forceinline__ Smem carve(double* base, const LaunchShape& S) {
   m.erod = reinterpret_cast<short*>(m.rel0 + m.CR + 1);
   m.nrod = m.erod + m.CE;
   m.vrod = m.nrod + m.CN;
+  m.t0 = threadIdx.x;
+  m.ts = blockDim.x;
+  m.grid = false;
   return m;
 }
 
@@ -206,8 +223,8 @@ __device__ __forceinline__ void kin_node(const StepParams& P, const Pack& pk, Sm
 
 __device__ __forceinline__ void kinematic(const StepParams& P, const Pack& pk, Smem& m, double h) {
   const int Ep = pk.nelem, Np = pk.nnode;
-  for (int i = threadIdx.x; i < Ep; i += blockDim.x) kin_element(P, pk, m, i, h);
-  for (int j = threadIdx.x; j < Np; j += blockDim.x) kin_node(P, pk, m, j, h);
+  for (int i = m.t0; i < Ep; i += m.ts) kin_element(P, pk, m, i, h);
+  for (int j = m.t0; j < Np; j += m.ts) kin_node(P, pk, m, j, h);
 }
 
 // --------------------------------------------------------------- dynamic stage (a3-a7, a10, a2)
@@ -216,7 +233,7 @@ __device__ __forceinline__ void kinematic(const StepParams& P, const Pack& pk, S
 // damping and external couples.
 __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& pk, Smem& m) {
   const int Ep = pk.nelem;
-  for (int i = threadIdx.x; i < Ep; i += blockDim.x) {
+  for (int i = m.t0; i < Ep; i += m.ts) {
     const int r = m.erod[i];
     const RodConst* rc = P.rods + pk.rod0 + r;
     const int j = i + r;
@@ -308,7 +325,7 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
 // bending/twist couple m = B(kappa - kappa0), P = m/eps^3, T = (kappa x m) D/eps^3.
 __device__ __forceinline__ void stage_voronoi(const StepParams& P, const Pack& pk, Smem& m) {
   const int Vp = pk.nvor;
-  for (int k = threadIdx.x; k < Vp; k += blockDim.x) {
+  for (int k = m.t0; k < Vp; k += m.ts) {
     const int r = m.vrod[k];
     const RodConst* rc = P.rods + pk.rod0 + r;
     const int i = k + r;
@@ -374,7 +391,7 @@ template <int MODE>
 __device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& pk, Smem& m, double dt, double h,
                                                double* acc_w) {
   const int Ep = pk.nelem;
-  for (int i = threadIdx.x; i < Ep; i += blockDim.x) {
+  for (int i = m.t0; i < Ep; i += m.ts) {
     const int r = m.erod[i];
     const int g = pk.rod0 + r;
     const RodConst* rc = P.rods + g;
@@ -415,7 +432,7 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
                                                   double* acc_v, double t, double h = 0.0) {
   const int Np = pk.nnode;
   const double dtg[3] = {dt * P.gravity[0], dt * P.gravity[1], dt * P.gravity[2]};
-  for (int j = threadIdx.x; j < Np; j += blockDim.x) {
+  for (int j = m.t0; j < Np; j += m.ts) {
     const int r = m.nrod[j];
     const int g = pk.rod0 + r;
     const RodConst* rc = P.rods + g;
@@ -502,9 +519,9 @@ __device__ __forceinline__ bool has_time_values(const StepParams& P) {
 }
 
 __device__ __forceinline__ void time_values(const StepParams& P, const Pack& pk, Smem& m, double t) {
-  const int rev = blockDim.x - 1 - threadIdx.x;
+  const int rev = m.ts - 1 - m.t0;
   if (P.has_act) {
-    for (int r = rev; r < pk.nrods; r += blockDim.x) {
+    for (int r = rev; r < pk.nrods; r += m.ts) {
       const RodConst* rc = P.rods + pk.rod0 + r;
       const double amp = rc->act_amp;
       m.ACT[r] = (amp != 0.0) ? amp * sin(fma(rc->act_omega, t, rc->act_phase)) : 0.0;
@@ -524,16 +541,16 @@ __device__ __forceinline__ void time_values(const StepParams& P, const Pack& pk,
 __device__ __forceinline__ void actuation_values(const StepParams& P, const Pack& pk, Smem& m, double t) {
   if (!has_time_values(P)) return;
   time_values(P, pk, m, t);
-  __syncthreads();
+  stage_sync(m);
 }
 
 // Copy a pack's state and constants into shared memory and build the item -> rod maps.
 __device__ __forceinline__ void stage_pack(const StepParams& P, const Pack& pk, Smem& m) {
   const int Ep = pk.nelem, Np = pk.nnode, Rp = pk.nrods, Vp = pk.nvor;
-  for (int r = threadIdx.x; r < Rp; r += blockDim.x) m.rel0[r] = P.rods[pk.rod0 + r].elem0 - pk.elem0;
-  if (threadIdx.x == 0) m.rel0[Rp] = Ep;
-  __syncthreads();
-  for (int i = threadIdx.x; i < Ep; i += blockDim.x) {
+  for (int r = m.t0; r < Rp; r += m.ts) m.rel0[r] = P.rods[pk.rod0 + r].elem0 - pk.elem0;
+  if (m.t0 == 0) m.rel0[Rp] = Ep;
+  stage_sync(m);
+  for (int i = m.t0; i < Ep; i += m.ts) {
     m.erod[i] = (short)find_rod(m.rel0, Rp, i);
     m.IRL[i] = __ldg(P.inv_rl + pk.elem0 + i);
 #pragma unroll
@@ -541,7 +558,7 @@ __device__ __forceinline__ void stage_pack(const StepParams& P, const Pack& pk, 
 #pragma unroll
     for (int c = 0; c < 3; ++c) m.WW[c * m.CE + i] = P.w[c * P.E + pk.elem0 + i];
   }
-  for (int j = threadIdx.x; j < Np; j += blockDim.x) {
+  for (int j = m.t0; j < Np; j += m.ts) {
     // node j belongs to rod r with rel0[r] + r <= j
     int lo = 0, hi = Rp - 1;
     while (lo < hi) {
@@ -556,7 +573,7 @@ __device__ __forceinline__ void stage_pack(const StepParams& P, const Pack& pk, 
       m.VN[c * m.CN + j] = P.v[c * P.N + pk.node0 + j];
     }
   }
-  for (int k = threadIdx.x; k < Vp; k += blockDim.x) {
+  for (int k = m.t0; k < Vp; k += m.ts) {
     int lo = 0, hi = Rp - 1;
     while (lo < hi) {
       int mid = (lo + hi + 1) >> 1;
@@ -564,7 +581,7 @@ __device__ __forceinline__ void stage_pack(const StepParams& P, const Pack& pk, 
     }
     m.vrod[k] = (short)lo;
   }
-  __syncthreads();
+  stage_sync(m);
 
 }
 

@@ -242,7 +242,9 @@ def test_invalid_descriptions_are_rejected():
     with pytest.raises(RodError):
         RodSystem(p.replace(rest_len=-p.rest_len))
     with pytest.raises(RodError):
-        RodSystem(p.replace(n_elem=np.array([2000], dtype=np.int32), rest_len=np.full(2000, 1e-3)))
+        RodSystem(p.replace(n_elem=np.array([0], dtype=np.int32), rest_len=np.zeros(0)))
+    # a rod longer than a block holds is accepted (it takes the cooperative path)
+    RodSystem(p.replace(n_elem=np.array([2000], dtype=np.int32), rest_len=np.full(2000, 1e-3)))
     s = RodSystem(p)
     with pytest.raises(RodError):
         s.step(1, 1e-5)          # no state yet

@@ -285,6 +285,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--surrogate-train-steps", type=int, default=15000)
     args = ap.parse_args()
 
@@ -314,6 +315,12 @@ def main():
     s.set_state(*p.state())
     W = max(args.warmup, 3)
     K = args.steps
+    # launch shape (elements and threads per block) picked by the library's autotuner on the
+    # live state, which it restores afterwards
+    tuned = None
+    if not args.no_autotune:
+        te, tt, tms = s.autotune(dt, trial_steps=5)
+        tuned = {"elems_per_block": te, "threads_per_block": tt, "trial_ms_per_step": tms}
     s.step(W, dt)
     torch.cuda.synchronize()
 
@@ -377,7 +384,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": t_max * 1e3 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic (seeded)",
-                "config": dict(desc, parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
+                "config": dict(desc, parallelism=f"replicas x{world}" if world > 1 else "1 GPU", launch_shape=tuned,
                                l2="state (196 MB) larger than L2, no flush needed" if args.workload == "packing"
                                else "state L2/smem resident"),
                 "clocks": clk, "gpu_launches": launches, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,

@@ -286,6 +286,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--skin", type=float, default=None,
+                    help="contact skin list (m); default 0.5 mm for the packing, 0 = cell search every step")
     ap.add_argument("--surrogate-train-steps", type=int, default=15000)
     args = ap.parse_args()
 
@@ -312,6 +314,9 @@ def main():
     build.build()
     p, dt, desc = _workload(args.workload, rank)
     s = RodSystem(p)
+    skin = args.skin if args.skin is not None else (5e-4 if args.workload == "packing" else 0.0)
+    if p.contact:
+        s.contact_skin(skin)
     s.set_state(*p.state())
     W = max(args.warmup, 3)
     K = args.steps
@@ -327,6 +332,7 @@ def main():
     # ---- timed region (device time, CUDA events on the stream the library launches on)
     stream = s.torch_stream
     launches0 = s.launch_count
+    builds0 = s.contact_list_builds()
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
@@ -342,6 +348,7 @@ def main():
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     launches = s.launch_count - launches0
+    builds = s.contact_list_builds() - builds0
     t_local = ms / 1e3
     t_max = slowest(t_local)
     value = total(p.n_elems * K) / t_max
@@ -385,6 +392,9 @@ def main():
                 "ms_per_step": t_max * 1e3 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic (seeded)",
                 "config": dict(desc, parallelism=f"replicas x{world}" if world > 1 else "1 GPU", launch_shape=tuned,
+                               contact_search=("none" if not p.contact else
+                                               f"skin list, skin {skin:g} m, {builds} rebuilds in the timed steps"
+                                               if skin > 0 else "cell grid searched every step"),
                                l2="state (196 MB) larger than L2, no flush needed" if args.workload == "packing"
                                else "state L2/smem resident"),
                 "clocks": clk, "gpu_launches": launches, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,

@@ -143,6 +143,23 @@ rod_status rod_system_sync(rod_system* sys);
  * are clamped into the boundary cells, which keeps the pair search exact). */
 rod_status rod_system_contact_config(rod_system* sys, int enable, double k, double c, double cell_size);
 
+/* Skin list for the contact search (same forces, fewer candidates per step).  With skin > 0
+ * each segment keeps the list of other-rod segments whose distance was within
+ * r_a + r_b + skin when the list was built from the cell grid (whose edge grows by the skin);
+ * the distance of two segments changes by at most the sum of their endpoints' displacements,
+ * so while no node has moved by skin / 2 (m) since the build every touching pair is listed and
+ * a step evaluates only the listed pairs.  The step kernels track the largest displacement on
+ * the device and the list is rebuilt there when it reaches skin / 2 (no host round trip).
+ * Forces are those of the direct search up to the order of summation.  skin = 0 (default):
+ * the cell grid is rebuilt and searched at every step.  ROD_ERR_ARG for skin < 0 or not
+ * finite.  Takes effect at the next step; the grid is rebuilt. */
+rod_status rod_system_contact_skin(rod_system* sys, double skin);
+
+/* Number of skin-list builds since the contact grid was last set up (by set_state, a change of
+ * the contact configuration or of the skin): *n = 0 without a skin list.  Synchronises on the
+ * system's stream. */
+rod_status rod_system_contact_list_builds(rod_system* sys, int64_t* n);
+
 /* Rod-rod friction (Results, "Fibrous granular materials": normal force and friction): at a
  * contact with normal force f_n the tangential force -mu f_n v_t / max(|v_t|, v_slip) acts at
  * the closest points (v_t: the tangential relative velocity), split onto the nodes like the

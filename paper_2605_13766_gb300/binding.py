@@ -96,6 +96,8 @@ _SIGNATURES = {
     "rod_system_sync": ([_P], C.c_int),
     "rod_system_contact_config": ([_P, C.c_int, C.c_double, C.c_double, C.c_double], C.c_int),
     "rod_system_friction": ([_P, C.c_double, C.c_double], C.c_int),
+    "rod_system_contact_skin": ([_P, C.c_double], C.c_int),
+    "rod_system_contact_list_builds": ([_P, _P], C.c_int),
     "rod_system_rhs": ([_P, C.c_double, _P, _P], C.c_int),
     "rod_system_contact_forces": ([_P, _P], C.c_int),
     "rod_system_set_launch": ([_P, C.c_int32, C.c_int32], C.c_int),
@@ -324,10 +326,22 @@ class RodSystem:
         _check(self.lib.rod_system_contact_config(self.handle, 1 if enable else 0, float(k), float(c),
                                                   float(cell_size)))
 
-    # -- debug / parity entry points (device outputs)
+    def contact_skin(self, skin: float):
+        """Skin list for the contact search: candidates within r_a + r_b + skin, rebuilt on the
+        device once a node has moved by skin / 2 (0: search the cell grid at every step)."""
+        _check(self.lib.rod_system_contact_skin(self.handle, float(skin)))
+
+    def contact_list_builds(self) -> int:
+        """Skin-list builds since the contact grid was last set up (0 without a skin list)."""
+        n = C.c_int64(0)
+        _check(self.lib.rod_system_contact_list_builds(self.handle, C.byref(n)))
+        return int(n.value)
+
     def friction(self, mu: float, v_slip: float):
         """Rod-rod friction: -mu f_n v_t / max(|v_t|, v_slip) at every contact."""
         _check(self.lib.rod_system_friction(self.handle, float(mu), float(v_slip)))
+
+    # -- debug / parity entry points (device outputs)
 
     def rhs(self, t: float = 0.0):
         import torch

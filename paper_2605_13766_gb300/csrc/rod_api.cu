@@ -200,6 +200,7 @@ struct rod_system {
   cudaGraphExec_t graph_exec = nullptr;
   double graph_dt = 0.0;
   int graph_grid_version = -1;
+  bool graph_list = false;  // the graph was captured with the skin list
   int shape_version = 0, graph_shape_version = -1;
   bool use_graphs = true;
   // adjoint: checkpoints of the last checkpointed forward run, recompute buffers
@@ -360,10 +361,15 @@ bool finite_all(const double* p, size_t n) {
 // the next positions, time advance) once per (dt, launch shape, grid); replays then cost one
 // launch per kGraphSteps steps.  The time of the state is read from t_dev inside the graph.
 constexpr int kGraphSteps = 32;
-constexpr int kKernelsPerGraphStep = 9;  // scan x3, scatter, sort, records, gather, step, time
+// kernels per captured step: scan x3, fill, scatter, sort, records, gather, step, time; with the
+// skin list decide, bin, scan x3, fill, scatter, sort, records, build, snapshot, force, step, time
+// (the rebuild kernels return at once unless a rebuild is due)
+constexpr int kKernelsPerGraphStep = 10;
+constexpr int kKernelsPerListGraphStep = 14;
 
 rod_status ensure_contact_graph(rod_system* s, const StepParams& Pb, double dt) {
   if (s->graph_exec && s->graph_dt == dt && s->graph_grid_version == s->contact.version &&
+      s->graph_list == (s->contact.skin > 0.0) &&
       s->graph_shape_version == s->shape_version)
     return ROD_OK;
   if (s->graph_exec) {
@@ -374,11 +380,14 @@ rod_status ensure_contact_graph(rod_system* s, const StepParams& Pb, double dt) 
   Pg.t_dev = s->t_dev.p;
   LaunchHook none;
   cudaGraph_t graph = nullptr;
+  const bool list = s->contact.skin > 0.0;
   CUDA_TRY(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
-    e = contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->cap_stream, none, true);
-    if (e == cudaSuccess) e = contact_clear_counts(s->contact, s->cap_stream);
+    e = list ? contact_list_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->cap_stream,
+                                    none)
+             : contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->cap_stream,
+                               none, true);
     if (e == cudaSuccess) e = launch_pack_kernel(Pg, s->shape, MODE_ONE_STEP, 1, 0.0, dt, 0, nullptr, nullptr,
                                                  s->cap_stream, none);
     if (e == cudaSuccess) {
@@ -403,6 +412,7 @@ rod_status ensure_contact_graph(rod_system* s, const StepParams& Pb, double dt) 
   }
   s->graph_dt = dt;
   s->graph_grid_version = s->contact.version;
+  s->graph_list = list;
   s->graph_shape_version = s->shape_version;
   return ROD_OK;
 }
@@ -814,8 +824,14 @@ rod_status rod_system_step_async(rod_system* s, int64_t n_steps, double dt) {
     rod_status st = contact_prepare(s->contact, s->rods_h, s->rods.p, s->x.p, s->N, s->E, s->R, s->stream, s->hook);
     if (st != ROD_OK) return st;
     P.fseg = s->contact.fseg;
-    StepParams Pb = P;  // with the binning epilogue for the next step
-    contact_bin_params(s->contact, Pb);
+    const bool list = s->contact.skin > 0.0;
+    StepParams Pb = P;  // with the binning epilogue for the next step, or the skin list's displacement
+    if (list) {
+      contact_list_params(s->contact, P);
+      Pb = P;
+    } else {
+      contact_bin_params(s->contact, Pb);
+    }
     CUDA_TRY(contact_clear_counts(s->contact, s->stream));
     CUDA_TRY(launch_pack_kernel(Pb, s->shape, MODE_KIN_HALF, 1, s->t, dt, 0, nullptr, nullptr, s->stream, s->hook));
     // steps 0 .. n-2 bin the next step's positions; the last one ends on a half step
@@ -830,15 +846,18 @@ rod_status rod_system_step_async(rod_system* s, int64_t n_steps, double dt) {
         s->prof.launches += 1;
         for (; k + kGraphSteps <= binned; k += kGraphSteps) {
           CUDA_TRY(cudaGraphLaunch(s->graph_exec, s->stream));
-          s->prof.launches += kGraphSteps * kKernelsPerGraphStep;
+          s->prof.launches += kGraphSteps * (list ? kKernelsPerListGraphStep : kKernelsPerGraphStep);
         }
       }
     }
     for (; k < n_steps; ++k) {
       const bool last = (k == n_steps - 1);
-      CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream, s->hook,
-                               true));
-      if (!last) CUDA_TRY(contact_clear_counts(s->contact, s->stream));
+      if (list)
+        CUDA_TRY(contact_list_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream,
+                                      s->hook));
+      else
+        CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream,
+                                 s->hook, true));
       CUDA_TRY(launch_pack_kernel(last ? P : Pb, s->shape, MODE_ONE_STEP, 1, s->t + k * dt, dt, last ? 1 : 0, nullptr,
                                   nullptr, s->stream, s->hook));
     }
@@ -870,6 +889,25 @@ rod_status rod_system_contact_config(rod_system* s, int enable, double k, double
   return ROD_OK;
 }
 
+rod_status rod_system_contact_skin(rod_system* s, double skin) {
+  if (!s) return fail(ROD_ERR_ARG, "null system");
+  if (!(skin >= 0) || !std::isfinite(skin)) return fail(ROD_ERR_ARG, "the skin must be finite and >= 0");
+  s->contact.skin = skin;
+  s->contact.grid_valid = false;  // the cell edge covers the skin
+  return ROD_OK;
+}
+
+rod_status rod_system_contact_list_builds(rod_system* s, int64_t* n) {
+  if (!s || !n) return fail(ROD_ERR_ARG, "null argument");
+  *n = 0;
+  if (!s->contact.ctl || !(s->contact.skin > 0.0) || !s->contact.grid_valid) return ROD_OK;
+  ListCtl c{};
+  CUDA_TRY(cudaMemcpyAsync(&c, s->contact.ctl, sizeof(ListCtl), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  *n = c.builds;
+  return ROD_OK;
+}
+
 rod_status rod_system_friction(rod_system* s, double mu, double v_slip) {
   if (!s) return fail(ROD_ERR_ARG, "null system");
   if (!(mu >= 0) || !std::isfinite(mu) || (mu > 0 && (!(v_slip > 0) || !std::isfinite(v_slip))))
@@ -887,6 +925,7 @@ rod_status rod_system_rhs(rod_system* s, double t, double* acc_v, double* acc_w)
     rod_status st = contact_prepare(s->contact, s->rods_h, s->rods.p, s->x.p, s->N, s->E, s->R, s->stream, s->hook);
     if (st != ROD_OK) return st;
     CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream, s->hook, false));
+    CUDA_TRY(contact_list_invalidate(s->contact, s->stream));  // the cell structures were overwritten
     P.fseg = s->contact.fseg;
   }
   CUDA_TRY(launch_pack_kernel(P, s->shape, MODE_RHS, 1, t, 1.0, 0, acc_v, acc_w, s->stream, s->hook));
@@ -904,6 +943,7 @@ rod_status rod_system_contact_forces(rod_system* s, double* f) {
   rod_status st = contact_prepare(s->contact, s->rods_h, s->rods.p, s->x.p, s->N, s->E, s->R, s->stream, s->hook);
   if (st != ROD_OK) return st;
   CUDA_TRY(contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->stream, s->hook, false));
+  CUDA_TRY(contact_list_invalidate(s->contact, s->stream));  // the cell structures were overwritten
   CUDA_TRY(contact_node_forces(s->contact, s->rods.p, s->N, s->E, s->R, f, s->stream, s->hook));
   return read_error_word(s);
 }

@@ -8,13 +8,23 @@
 // put in ascending segment order so that the force sums are reproducible.
 //
 // Narrow phase: each segment visits the 27 neighbour cells and, for every segment of another
-// rod, (1) rejects it in FP32 when a lower bound of the segment distance, |m_a - m_b| minus
-// the two half lengths, exceeds r_a + r_b by more than the FP32 rounding margin, then (2)
-// evaluates the pair in FP64 exactly as the model defines it: closest points of the two
-// segments (clamped two-parameter minimisation, lower segment index first so both members of
-// the pair compute bit-identical values), overlap delta = r_a + r_b - d, force
-// max(0, k delta - c v_rel . n) along n, split (1-s, s) onto the segment's nodes.  Each segment
-// accumulates only its own share, so there are no atomics and no scatter conflicts.
+// rod, (1) rejects it in FP32 when a lower bound of the segment distance exceeds r_a + r_b by
+// more than the FP32 rounding margin -- first |m_a - m_b| minus the two half lengths, then the
+// separating-axis bound along u = (m_a - m_b)/|m_a - m_b|, |m_a - m_b| - |e_a . u| - |e_b . u|
+// (e = half edge vector: a segment projects onto u as m . u +- |e . u|) -- then (2) evaluates
+// the pair in FP64 exactly as the model defines it: closest points of the two segments
+// (clamped two-parameter minimisation, lower segment index first so both members of the pair
+// compute bit-identical values), overlap delta = r_a + r_b - d, force max(0, k delta -
+// c v_rel . n) along n, split (1-s, s) onto the segment's nodes.  Each segment accumulates only
+// its own share, so there are no atomics and no scatter conflicts.
+//
+// Skin list (optional): the same search with the bound raised by a skin records, per segment,
+// the candidates that may come within r_a + r_b + skin; the distance of two segments moves by
+// at most the sum of their endpoints' displacements, so while no node has moved by skin / 2
+// since the build, every touching pair is on the list and a step evaluates only the listed
+// pairs.  The step kernels raise the largest displacement; the rebuild kernels run, gated on
+// the device, when it reaches skin / 2, and return at once otherwise (no host round trip, so
+// the steps stay in one CUDA graph).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -53,11 +63,9 @@ struct Grid {
 // Midpoint, half length and cell of every segment in FP32 (the cell only has to be consistent
 // within one evaluation; the grid's slack covers the FP32 rounding of the midpoints), counted
 // per cell with one atomic per distinct cell in the warp.
-__global__ void bin_kernel(const double* __restrict__ x, const int* __restrict__ seg_rod, int64_t N, int64_t E, Grid g,
-                           int* __restrict__ seg_cell, int* __restrict__ cell_count, float4* __restrict__ prox,
-                           int* err) {
-  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (a >= E) return;
+__device__ __forceinline__ void bin_one(const double* __restrict__ x, const int* __restrict__ seg_rod, int64_t N,
+                                        const Grid& g, int* __restrict__ seg_cell, int* __restrict__ cell_count,
+                                        float4* __restrict__ prox, int* err, int64_t a) {
   const int64_t j = a + seg_rod[a];
   float mid[3], ll = 0.f;
 #pragma unroll
@@ -83,6 +91,18 @@ __global__ void bin_kernel(const double* __restrict__ x, const int* __restrict__
   const unsigned peers = __match_any_sync(__activemask(), cell);
   if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cell_count + cell, __popc(peers));
   prox[a] = make_float4(mid[0], mid[1], mid[2], 0.5f * len);
+}
+
+// A gate (null: always) lets the skin list's rebuild kernels return at once unless a rebuild
+// is due; gated launches use a grid of a few blocks per SM and stride over the items.
+__device__ __forceinline__ bool gated_off(const int* gate) { return gate && *(volatile const int*)gate == 0; }
+
+__global__ void bin_kernel(const double* __restrict__ x, const int* __restrict__ seg_rod, int64_t N, int64_t E, Grid g,
+                           int* __restrict__ seg_cell, int* __restrict__ cell_count, float4* __restrict__ prox,
+                           int* err, const int* gate) {
+  if (gated_off(gate)) return;
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < E; a += (int64_t)gridDim.x * blockDim.x)
+    bin_one(x, seg_rod, N, g, seg_cell, cell_count, prox, err, a);
 }
 
 // ---- exclusive scan of cell_count[0..n) into cell_start[0..n], cell_start[n] = total
@@ -116,28 +136,35 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot, int& t
 }
 
 __global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const int* __restrict__ in, int64_t n,
-                                                                   int* __restrict__ out, int* __restrict__ tile_sums) {
+                                                                   int* __restrict__ out, int* __restrict__ tile_sums,
+                                                                   const int* gate) {
   __shared__ int wt[33];
-  const int64_t base = blockIdx.x * (int64_t)kScanTile + threadIdx.x * kScanPerThread;
-  int v[kScanPerThread];
-  int s = 0;
+  if (gated_off(gate)) return;
+  const int64_t nt = (n + kScanTile - 1) / kScanTile;
+  for (int64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const int64_t base = tile * kScanTile + threadIdx.x * kScanPerThread;
+    int v[kScanPerThread];
+    int s = 0;
 #pragma unroll
-  for (int q = 0; q < kScanPerThread; ++q) {
-    v[q] = (base + q < n) ? in[base + q] : 0;
-    s += v[q];
-  }
-  int total;
-  int off = block_exclusive_scan(s, wt, total);
+    for (int q = 0; q < kScanPerThread; ++q) {
+      v[q] = (base + q < n) ? in[base + q] : 0;
+      s += v[q];
+    }
+    int total;
+    int off = block_exclusive_scan(s, wt, total);
 #pragma unroll
-  for (int q = 0; q < kScanPerThread; ++q) {
-    if (base + q < n) out[base + q] = off;
-    off += v[q];
+    for (int q = 0; q < kScanPerThread; ++q) {
+      if (base + q < n) out[base + q] = off;
+      off += v[q];
+    }
+    if (threadIdx.x == 0) tile_sums[tile] = total;
   }
-  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(int* sums, int64_t nt, int* out_total_slot) {
+__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(int* sums, int64_t nt, int* out_total_slot,
+                                                                  const int* gate) {
   __shared__ int wt[33];
+  if (gated_off(gate)) return;
   int carry = 0;
   for (int64_t b = 0; b < nt; b += kScanThreads) {
     const int64_t i = b + threadIdx.x;
@@ -150,36 +177,51 @@ __global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(int* sums, int6
   if (threadIdx.x == 0) *out_total_slot = carry;
 }
 
-__global__ void scan_add_kernel(int* out, int64_t n, const int* sums) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) out[i] += sums[i / kScanTile];
+__global__ void scan_add_kernel(int* out, int64_t n, const int* sums, const int* gate) {
+  if (gated_off(gate)) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] += sums[i / kScanTile];
+}
+
+// Scatter cursors from the cell starts; the counts are cleared for the next rebuild.
+__global__ void fill_kernel(const int* __restrict__ start, int64_t ncell, int* __restrict__ fill,
+                            int* __restrict__ count, const int* gate) {
+  if (gated_off(gate)) return;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    fill[c] = start[c];
+    count[c] = 0;
+  }
 }
 
 __global__ void scatter_kernel(const int* __restrict__ seg_cell, int64_t E, int* __restrict__ fill,
-                               int* __restrict__ sorted) {
-  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (a >= E) return;
-  const int pos = atomicAdd(fill + seg_cell[a], 1);
-  sorted[pos] = (int)a;
+                               int* __restrict__ sorted, const int* gate) {
+  if (gated_off(gate)) return;
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < E; a += (int64_t)gridDim.x * blockDim.x) {
+    const int pos = atomicAdd(fill + seg_cell[a], 1);
+    sorted[pos] = (int)a;
+  }
 }
 
-__global__ void sort_cells_kernel(const int* __restrict__ start, int64_t ncell, int* __restrict__ sorted, int* err) {
-  const int64_t cidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (cidx >= ncell) return;
-  const int b = start[cidx], e = start[cidx + 1];
-  if (e - b > kCellCap) {
-    atomicOr(err, ERR_OVERFLOW);
-    return;
-  }
-  if (*(volatile int*)err != 0) return;
-  for (int i = b + 1; i < e; ++i) {  // insertion sort; cells hold a handful of segments
-    const int key = sorted[i];
-    int j = i - 1;
-    while (j >= b && sorted[j] > key) {
-      sorted[j + 1] = sorted[j];
-      --j;
+__global__ void sort_cells_kernel(const int* __restrict__ start, int64_t ncell, int* __restrict__ sorted, int* err,
+                                  const int* gate) {
+  if (gated_off(gate)) return;
+  for (int64_t cidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cidx < ncell;
+       cidx += (int64_t)gridDim.x * blockDim.x) {
+    const int b = start[cidx], e = start[cidx + 1];
+    if (e - b > kCellCap) {
+      atomicOr(err, ERR_OVERFLOW);
+      continue;
     }
-    sorted[j + 1] = key;
+    if (*(volatile int*)err != 0) return;
+    for (int i = b + 1; i < e; ++i) {  // insertion sort; cells hold a handful of segments
+      const int key = sorted[i];
+      int j = i - 1;
+      while (j >= b && sorted[j] > key) {
+        sorted[j + 1] = sorted[j];
+        --j;
+      }
+      sorted[j + 1] = key;
+    }
   }
 }
 
@@ -227,17 +269,35 @@ __device__ __forceinline__ void closest(const double* p0, const double* p1, cons
   }
 }
 
-// Per-slot records in cell order, so that the narrow phase reads each candidate with two
-// contiguous 16-byte loads: (FP32 midpoint, FP32 half length) and (segment, rod, FP32 radius).
+// Per-slot records in cell order, so that the narrow phase reads each candidate with
+// contiguous 16-byte loads: (FP32 midpoint, FP32 half length), (segment, rod, FP32 radius, end
+// of the rod's run) and, for candidates that pass the first bound, (FP32 half edge).  A cell
+// lists its segments by ascending index and a rod's segments have consecutive indices, so the
+// segments of one rod in a cell form one run of slots; a scan that meets a segment of its own
+// rod (never a contact pair) jumps to the run's end.
 __global__ void records_kernel(const int* __restrict__ sorted, const int* __restrict__ seg_rod,
-                               const float4* __restrict__ prox, const RodConst* __restrict__ rods, int64_t E,
-                               float4* __restrict__ recA, int4* __restrict__ recB) {
-  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= E) return;
-  const int a = sorted[q];
-  const int r = seg_rod[a];
-  recA[q] = prox[a];
-  recB[q] = make_int4(a, r, __float_as_int((float)rods[r].radius), 0);
+                               const int* __restrict__ seg_cell, const int* __restrict__ cell_start,
+                               const float4* __restrict__ prox, const double* __restrict__ x, int64_t N,
+                               const RodConst* __restrict__ rods, int64_t E, float4* __restrict__ recA,
+                               int4* __restrict__ recB, float4* __restrict__ recC, int* __restrict__ slot_of,
+                               const int* gate) {
+  if (gated_off(gate)) return;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < E; q += (int64_t)gridDim.x * blockDim.x) {
+    const int a = sorted[q];
+    const int r = seg_rod[a];
+    const int cell_end = cell_start[seg_cell[a] + 1];
+    const int rod_end = rods[r].elem0 + rods[r].n;
+    int run_end = (int)q + 1;
+    while (run_end < cell_end && sorted[run_end] < rod_end) ++run_end;
+    const int64_t na = (int64_t)a + r;
+    float e[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) e[c] = (float)(0.5 * (x[c * N + na + 1] - x[c * N + na]));
+    recA[q] = prox[a];
+    recB[q] = make_int4(a, r, __float_as_int((float)rods[r].radius), run_end);
+    recC[q] = make_float4(e[0], e[1], e[2], 0.f);
+    if (slot_of) slot_of[a] = (int)q;
+  }
 }
 
 struct ContactArgs {
@@ -250,6 +310,12 @@ struct ContactArgs {
   const float4* prox;
   const float4* recA;
   const int4* recB;
+  const float4* recC;
+  const int* gate;
+  int* nbr;
+  int* nbr_count;
+  const int* slot_of;
+  float skin;
   const RodConst* rods;
   double* fseg;
   int* err;
@@ -325,20 +391,35 @@ __device__ __noinline__ PairForce pair_force(const ContactArgs& A, int a, int ra
   return out;
 }
 
-// One thread per slot of the cell-ordered list: threads of a warp share cells and their
-// neighbour rows, so candidate records come from L1.  The three cells of each (y, z) row of
-// the 3x3x3 neighbourhood are consecutive in the list and scanned as one range.
-__global__ void __launch_bounds__(256, 4) gather_kernel(ContactArgs A) {
-  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= A.E) return;
-  if (*(volatile int*)A.err != 0) return;  // latched error: the step is abandoned
+// FP32 lower bounds of the distance of segments a and b (midpoints m, half lengths h, half
+// edges e) against touch = r_a + r_b + extra + tol, tol covering the rounding of the FP32
+// inputs and of these expressions: false when the pair is certainly farther apart.
+__device__ __forceinline__ bool may_touch(float4 ga, float4 gb, float4 ea, float4 eb, float touch_base) {
+  const float ddx = ga.x - gb.x, ddy = ga.y - gb.y, ddz = ga.z - gb.z;
+  const float dm2 = ddx * ddx + ddy * ddy + ddz * ddz;
+  const float ma_inf = fmaxf(fabsf(ga.x), fmaxf(fabsf(ga.y), fabsf(ga.z)));
+  const float mb_inf = fmaxf(fabsf(gb.x), fmaxf(fabsf(gb.y), fabsf(gb.z)));
+  const float touch = touch_base + 1e-6f + 4e-6f * (ma_inf + mb_inf + ga.w + gb.w);
+  const float reach = touch + ga.w + gb.w;
+  if (dm2 > reach * reach) return false;
+  // separating axis along m_a - m_b: |dm| - (|e_a . dm| + |e_b . dm|) / |dm| > touch
+  const float pa = fabsf(ea.x * ddx + ea.y * ddy + ea.z * ddz);
+  const float pb = fabsf(eb.x * ddx + eb.y * ddy + eb.z * ddz);
+  return !(dm2 > 0.f && dm2 - (pa + pb) > touch * sqrtf(dm2));
+}
+
+// Calls visit(b, rb) for every segment b of another rod in the 27-cell neighbourhood of slot q
+// (cell-ordered records) that may come within r_a + r_b + extra of the slot's segment, in list
+// order.  The three cells of each (y, z) row are consecutive in the list and scanned as one
+// range; the next candidate's records are loaded while the current one is tested.
+template <class Visit>
+__device__ __forceinline__ void scan_neighbourhood(const ContactArgs& A, int64_t q, float extra, Visit& visit) {
   const float4 ga = A.recA[q];
   const int4 ba = A.recB[q];
-  const int a = ba.x, ra = ba.y;
+  const float4 ea = A.recC[q];
+  const int ra = ba.y;
   const float rada = __int_as_float(ba.z);
-  const float ma_inf = fmaxf(fabsf(ga.x), fmaxf(fabsf(ga.y), fabsf(ga.z)));
-  double fa[3] = {0, 0, 0}, fb[3] = {0, 0, 0};
-  const int cell = A.seg_cell[a];
+  const int cell = A.seg_cell[ba.x];
   const int cx = cell % A.dim[0], cy = (cell / A.dim[0]) % A.dim[1], cz = cell / (A.dim[0] * A.dim[1]);
   const int x0 = max(cx - 1, 0), x1 = min(cx + 1, A.dim[0] - 1);
   for (int dz = -1; dz <= 1; ++dz) {
@@ -353,45 +434,149 @@ __global__ void __launch_bounds__(256, 4) gather_kernel(ContactArgs A) {
         atomicOr(A.err, ERR_OVERFLOW);
         continue;
       }
-      // the next candidate's records are loaded while the current one is tested
       int4 bb_next = make_int4(0, 0, 0, 0);
       float4 gb_next = make_float4(0.f, 0.f, 0.f, 0.f);
       if (b0 < b1) {
         bb_next = A.recB[b0];
         gb_next = A.recA[b0];
       }
-      for (int t = b0; t < b1; ++t) {
+      for (int t = b0; t < b1;) {
+        const int tc = t;
         const int4 bb = bb_next;
         const float4 gb = gb_next;
-        if (t + 1 < b1) {
-          bb_next = A.recB[t + 1];
-          gb_next = A.recA[t + 1];
+        t = (bb.y == ra) ? bb.w : t + 1;  // own rod: skip its run in this cell
+        if (t < b1) {
+          bb_next = A.recB[t];
+          gb_next = A.recA[t];
         }
         if (bb.y == ra) continue;
-        // FP32 lower bound of the segment distance, |m_a - m_b| - (h_a + h_b) > r_a + r_b + tol,
-        // compared squared: |m_a - m_b|^2 > (r_a + r_b + tol + h_a + h_b)^2 (tol covers the
-        // rounding of both forms)
-        const float ddx = ga.x - gb.x, ddy = ga.y - gb.y, ddz = ga.z - gb.z;
-        const float dm2 = ddx * ddx + ddy * ddy + ddz * ddz;
-        const float mb_inf = fmaxf(fabsf(gb.x), fmaxf(fabsf(gb.y), fabsf(gb.z)));
-        const float tol = 1e-6f + 4e-6f * (ma_inf + mb_inf + ga.w + gb.w);
-        const float reach = rada + __int_as_float(bb.z) + tol + ga.w + gb.w;
-        if (dm2 > reach * reach) continue;
-        const PairForce pf = pair_force(A, a, ra, bb.x, bb.y);
-        if (pf.hit) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            fa[c] += pf.fa[c];
-            fb[c] += pf.fb[c];
-          }
-        }
+        if (!may_touch(ga, gb, ea, A.recC[tc], rada + __int_as_float(bb.z) + extra)) continue;
+        visit(bb.x, bb.y);
       }
     }
   }
+}
+
+struct ForceSum {
+  const ContactArgs& A;
+  int a, ra;
+  double fa[3], fb[3];
+  __device__ ForceSum(const ContactArgs& args, int a_, int ra_) : A(args), a(a_), ra(ra_) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) fa[c] = fb[c] = 0.0;
+  }
+  __device__ void operator()(int b, int rb) {
+    const PairForce pf = pair_force(A, a, ra, b, rb);
+    if (pf.hit) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        fa[c] += pf.fa[c];
+        fb[c] += pf.fb[c];
+      }
+    }
+  }
+  __device__ void store(double* fseg, int64_t E) const {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      fseg[c * E + a] = fa[c];
+      fseg[(3 + c) * E + a] = fb[c];
+    }
+  }
+};
+
+// Direct evaluation: one thread per slot of the cell-ordered list (threads of a warp share
+// cells and their neighbour rows, so candidate records come from L1).
+__global__ void __launch_bounds__(256, 4) gather_kernel(ContactArgs A) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= A.E) return;
+  if (*(volatile int*)A.err != 0) return;  // latched error: the step is abandoned
+  const int4 ba = A.recB[q];
+  ForceSum f(A, ba.x, ba.y);
+  scan_neighbourhood(A, q, 0.f, f);
+  f.store(A.fseg, A.E);
+}
+
+struct ListAppend {
+  int* nbr;
+  int64_t E;
+  int a, n;
+  __device__ void operator()(int b, int) {
+    if (n < kNbrCap) nbr[n * E + a] = b;
+    ++n;
+  }
+};
+
+// Skin-list build (gated): the same scan with the bound raised by the skin.
+__global__ void __launch_bounds__(256) list_build_kernel(ContactArgs A) {
+  if (gated_off(A.gate)) return;
+  if (*(volatile int*)A.err != 0) return;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < A.E; q += (int64_t)gridDim.x * blockDim.x) {
+    ListAppend l{A.nbr, A.E, A.recB[q].x, 0};
+    scan_neighbourhood(A, q, A.skin, l);
+    A.nbr_count[l.a] = l.n;
+  }
+}
+
+// FP32 midpoint, half length and half edge of segment (nodes n, n + 1) from the FP64 positions.
+__device__ __forceinline__ void seg_now(const double* __restrict__ x, int64_t N, int64_t n, float4& g, float4& e) {
+  double d[3], m[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    A.fseg[c * A.E + a] = fa[c];
-    A.fseg[(3 + c) * A.E + a] = fb[c];
+    const double p0 = x[c * N + n], p1 = x[c * N + n + 1];
+    m[c] = 0.5 * (p0 + p1);
+    d[c] = 0.5 * (p1 - p0);
+  }
+  e = make_float4((float)d[0], (float)d[1], (float)d[2], 0.f);
+  g = make_float4((float)m[0], (float)m[1], (float)m[2], (float)sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+}
+
+// Skin-list evaluation: one thread per segment, its listed candidates culled in FP32 at the
+// current positions and evaluated in FP64; a segment whose list overflowed scans its
+// neighbourhood of the last build with the skin bound (the build's records are stale by less
+// than skin / 2 per node, which the skin covers).
+__global__ void __launch_bounds__(256) list_force_kernel(ContactArgs A) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= A.E) return;
+  if (*(volatile int*)A.err != 0) return;
+  const int n = A.nbr_count[a];
+  const int ra = A.seg_rod[a];
+  ForceSum f(A, (int)a, ra);
+  if (n <= kNbrCap) {
+    if (n > 0) {
+      float4 ga, ea;
+      seg_now(A.x, A.N, a + ra, ga, ea);
+      const float rada = (float)A.rods[ra].radius;
+      for (int k = 0; k < n; ++k) {
+        const int b = A.nbr[k * A.E + a];
+        const int rb = A.seg_rod[b];
+        float4 gb, eb;
+        seg_now(A.x, A.N, (int64_t)b + rb, gb, eb);
+        if (may_touch(ga, gb, ea, eb, rada + (float)A.rods[rb].radius)) f(b, rb);
+      }
+    }
+  } else {
+    scan_neighbourhood(A, A.slot_of[a], A.skin, f);
+  }
+  f.store(A.fseg, A.E);
+}
+
+// Rebuild decision of this evaluation: requested, or a node has moved by skin / 2 (or the
+// displacement is not finite).
+__global__ void list_decide_kernel(ListCtl* ctl, double limit2) {
+  const double d2 = __longlong_as_double(static_cast<long long>(ctl->disp2));
+  ctl->gate = (ctl->force != 0 || !(d2 < limit2)) ? 1 : 0;
+}
+
+// After a rebuild: the build's positions become the reference, the displacement restarts.
+__global__ void list_snapshot_kernel(const double* __restrict__ x, int64_t n, double* __restrict__ x_ref, ListCtl* ctl,
+                                     const int* gate) {
+  if (gated_off(gate)) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x_ref[i] = x[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->disp2 = 0ull;
+    ctl->force = 0;
+    ctl->builds += 1;
   }
 }
 
@@ -421,7 +606,8 @@ cudaError_t dev_alloc(T** p, size_t count) {
 
 void contact_release(ContactState& cs) {
   void* ptrs[] = {cs.seg_rod, cs.seg_cell, cs.cell_count, cs.cell_start, cs.cell_fill,
-                  cs.block_sums, cs.sorted, cs.prox, cs.fseg, cs.recA, cs.recB};
+                  cs.block_sums, cs.sorted, cs.prox, cs.fseg, cs.recA, cs.recB, cs.recC,
+                  cs.nbr, cs.nbr_count, cs.slot_of, cs.x_ref, cs.ctl};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cs.seg_rod = cs.seg_cell = cs.cell_count = cs.cell_start = cs.cell_fill = cs.block_sums = cs.sorted = nullptr;
@@ -429,6 +615,11 @@ void contact_release(ContactState& cs) {
   cs.fseg = nullptr;
   cs.recA = nullptr;
   cs.recB = nullptr;
+  cs.recC = nullptr;
+  cs.nbr = cs.nbr_count = cs.slot_of = nullptr;
+  cs.x_ref = nullptr;
+  cs.ctl = nullptr;
+  cs.N = 0;
   cs.cap_cells = 0;
   cs.E = 0;
   cs.grid_valid = false;
@@ -465,7 +656,8 @@ rod_status contact_prepare(ContactState& cs, const std::vector<RodConst>& rods_h
   for (int c = 0; c < 3; ++c)
     if (!std::isfinite(lo[c]) || !std::isfinite(hi[c]))
       return cfail(ROD_ERR_NONFINITE, "contact grid: non-finite positions", cudaSuccess);
-  double h = std::max(cs.cell_size, 2.0 * rmax + 1.25 * lmax);
+  const double skin = cs.skin > 0.0 ? cs.skin : 0.0;
+  double h = std::max(cs.cell_size, 2.0 * rmax + 1.25 * lmax + skin);
   double ext[3], margin[3];
   int64_t ncell = 0;
   for (int iter = 0; iter < 64; ++iter) {
@@ -489,14 +681,28 @@ rod_status contact_prepare(ContactState& cs, const std::vector<RodConst>& rods_h
   double cmax = 0.0;
   for (int c = 0; c < 3; ++c) cmax = std::max(cmax, std::max(std::fabs(cs.lo[c]), std::fabs(cs.lo[c] + cs.dim[c] * h)));
   const double fp32_margin = 64.0 * 6e-8 * (1.0 + cmax);
-  cs.l_allowed = h - 2.0 * rmax - fp32_margin;
+  cs.l_allowed = h - 2.0 * rmax - skin - fp32_margin;
   cs.version += 1;
   if (cs.E != E) {
     if ((e = dev_alloc(&cs.seg_rod, E)) || (e = dev_alloc(&cs.seg_cell, E)) || (e = dev_alloc(&cs.sorted, E)) ||
         (e = dev_alloc(&cs.prox, E)) || (e = dev_alloc(&cs.fseg, 6 * E)) || (e = dev_alloc(&cs.recA, E)) ||
-        (e = dev_alloc(&cs.recB, E)))
+        (e = dev_alloc(&cs.recB, E)) || (e = dev_alloc(&cs.recC, E)))
       return cfail(ROD_ERR_CUDA, "contact: allocation", e);
     cs.E = E;
+    cs.N = 0;  // list buffers follow
+  }
+  if (skin > 0.0 && cs.N != N) {
+    if ((e = dev_alloc(&cs.nbr, int64_t(kNbrCap) * E)) || (e = dev_alloc(&cs.nbr_count, E)) ||
+        (e = dev_alloc(&cs.slot_of, E)) || (e = dev_alloc(&cs.x_ref, 3 * N)) || (e = dev_alloc(&cs.ctl, 1)))
+      return cfail(ROD_ERR_CUDA, "contact: skin list allocation", e);
+    cs.N = N;
+  }
+  if (cs.sm_count == 0) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      cs.sm_count = sms;
+    cudaGetLastError();
+    if (cs.sm_count <= 0) cs.sm_count = 1;
   }
   if (cs.cap_cells < ncell) {
     const int64_t nt = (ncell + 1 + kScanTile - 1) / kScanTile;
@@ -510,6 +716,12 @@ rod_status contact_prepare(ContactState& cs, const std::vector<RodConst>& rods_h
   seg_rod_kernel<<<R, 64, 0, st>>>(rods_dev, R, cs.seg_rod);
   hook.after(K_MISC, st);
   if ((e = cudaGetLastError())) return cfail(ROD_ERR_CUDA, "contact: segment map", e);
+  // every structure starts empty; a skin list is rebuilt at its first evaluation
+  if ((e = contact_clear_counts(cs, st))) return cfail(ROD_ERR_CUDA, "contact: clearing counts", e);
+  if (skin > 0.0) {
+    if ((e = cudaMemsetAsync(cs.ctl, 0, sizeof(ListCtl), st)) || (e = contact_list_invalidate(cs, st)))
+      return cfail(ROD_ERR_CUDA, "contact: skin list reset", e);
+  }
   cs.grid_valid = true;
   return ROD_OK;
 }
@@ -530,51 +742,10 @@ cudaError_t contact_clear_counts(const ContactState& cs, cudaStream_t st) {
   return cudaMemsetAsync(cs.cell_count, 0, (cs.ncell + 1) * sizeof(int), st);
 }
 
-cudaError_t contact_compute(ContactState& cs, const double* x, const double* v, const RodConst* rods, int64_t N,
-                            int64_t E, int R, int* err, cudaStream_t st, const LaunchHook& hook, bool prebinned) {
-  cudaError_t e;
-  (void)R;
-  const int64_t n1 = cs.ncell + 1;
-  const int tb = 256;
-  const int64_t eb = (E + tb - 1) / tb;
-  if (!prebinned) {
-    if ((e = contact_clear_counts(cs, st))) return e;
-    Grid g;
-    for (int c = 0; c < 3; ++c) {
-      g.lo[c] = (float)cs.lo[c];
-      g.dim[c] = cs.dim[c];
-    }
-    g.inv_h = (float)cs.inv_h;
-    g.l_allowed = (float)cs.l_allowed;
-    hook.before(K_CONTACT_BIN, st);
-    bin_kernel<<<eb, tb, 0, st>>>(x, cs.seg_rod, N, E, g, cs.seg_cell, cs.cell_count, cs.prox, err);
-    hook.after(K_CONTACT_BIN, st);
-    if ((e = cudaGetLastError())) return e;
-  }
-  const int64_t nt = (n1 + kScanTile - 1) / kScanTile;
-  hook.before(K_CONTACT_SCAN, st);
-  scan_tiles_kernel<<<nt, kScanThreads, 0, st>>>(cs.cell_count, n1, cs.cell_start, cs.block_sums);
-  hook.after(K_CONTACT_SCAN, st);
-  hook.before(K_CONTACT_SCAN, st);
-  scan_sums_kernel<<<1, kScanThreads, 0, st>>>(cs.block_sums, nt, cs.block_sums + nt);
-  hook.after(K_CONTACT_SCAN, st);
-  hook.before(K_CONTACT_SCAN, st);
-  scan_add_kernel<<<(n1 + 255) / 256, 256, 0, st>>>(cs.cell_start, n1, cs.block_sums);
-  hook.after(K_CONTACT_SCAN, st);
-  if ((e = cudaGetLastError())) return e;
-  if ((e = cudaMemcpyAsync(cs.cell_fill, cs.cell_start, cs.ncell * sizeof(int), cudaMemcpyDeviceToDevice, st)))
-    return e;
-  hook.before(K_CONTACT_SCATTER, st);
-  scatter_kernel<<<eb, tb, 0, st>>>(cs.seg_cell, E, cs.cell_fill, cs.sorted);
-  hook.after(K_CONTACT_SCATTER, st);
-  hook.before(K_CONTACT_SORT, st);
-  sort_cells_kernel<<<(cs.ncell + 255) / 256, 256, 0, st>>>(cs.cell_start, cs.ncell, cs.sorted, err);
-  hook.after(K_CONTACT_SORT, st);
-  if ((e = cudaGetLastError())) return e;
-  hook.before(K_CONTACT_SORT, st);
-  records_kernel<<<eb, tb, 0, st>>>(cs.sorted, cs.seg_rod, cs.prox, rods, E, cs.recA, cs.recB);
-  hook.after(K_CONTACT_SORT, st);
-  if ((e = cudaGetLastError())) return e;
+namespace {
+
+ContactArgs make_args(const ContactState& cs, const double* x, const double* v, const RodConst* rods, int64_t N,
+                      int64_t E, int* err, const int* gate) {
   ContactArgs A;
   A.x = x;
   A.v = v;
@@ -585,6 +756,12 @@ cudaError_t contact_compute(ContactState& cs, const double* x, const double* v, 
   A.prox = cs.prox;
   A.recA = cs.recA;
   A.recB = cs.recB;
+  A.recC = cs.recC;
+  A.gate = gate;
+  A.nbr = cs.nbr;
+  A.nbr_count = cs.nbr_count;
+  A.slot_of = cs.slot_of;
+  A.skin = (float)cs.skin;
   A.rods = rods;
   A.fseg = cs.fseg;
   A.N = N;
@@ -595,10 +772,110 @@ cudaError_t contact_compute(ContactState& cs, const double* x, const double* v, 
   A.mu = cs.mu;
   A.vslip = cs.vslip;
   A.err = err;
+  return A;
+}
+
+// Cell structures and records of positions x: binning (unless the step kernel binned them),
+// scan of the counts, scatter, per-cell sort, records.  Gated (skin list): every kernel returns
+// at once unless the device gate is set, and strides over its items with a small grid.
+cudaError_t enqueue_build(ContactState& cs, const double* x, const RodConst* rods, int64_t N, int64_t E, int* err,
+                          cudaStream_t st, const LaunchHook& hook, bool prebinned, const int* gate) {
+  cudaError_t e;
+  const int64_t n1 = cs.ncell + 1;
+  const int tb = 256;
+  const int64_t cap = gate ? int64_t(8) * std::max(cs.sm_count, 1) : INT64_MAX;
+  auto blocks = [&](int64_t n, int64_t per_block) {
+    return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((n + per_block - 1) / per_block, cap)));
+  };
+  if (!prebinned) {
+    if (!gate && (e = contact_clear_counts(cs, st))) return e;
+    Grid g;
+    for (int c = 0; c < 3; ++c) {
+      g.lo[c] = (float)cs.lo[c];
+      g.dim[c] = cs.dim[c];
+    }
+    g.inv_h = (float)cs.inv_h;
+    g.l_allowed = (float)cs.l_allowed;
+    hook.before(K_CONTACT_BIN, st);
+    bin_kernel<<<blocks(E, tb), tb, 0, st>>>(x, cs.seg_rod, N, E, g, cs.seg_cell, cs.cell_count, cs.prox, err, gate);
+    hook.after(K_CONTACT_BIN, st);
+    if ((e = cudaGetLastError())) return e;
+  }
+  const int64_t nt = (n1 + kScanTile - 1) / kScanTile;
+  hook.before(K_CONTACT_SCAN, st);
+  scan_tiles_kernel<<<blocks(nt, 1), kScanThreads, 0, st>>>(cs.cell_count, n1, cs.cell_start, cs.block_sums, gate);
+  hook.after(K_CONTACT_SCAN, st);
+  hook.before(K_CONTACT_SCAN, st);
+  scan_sums_kernel<<<1, kScanThreads, 0, st>>>(cs.block_sums, nt, cs.block_sums + nt, gate);
+  hook.after(K_CONTACT_SCAN, st);
+  hook.before(K_CONTACT_SCAN, st);
+  scan_add_kernel<<<blocks(n1, tb), tb, 0, st>>>(cs.cell_start, n1, cs.block_sums, gate);
+  hook.after(K_CONTACT_SCAN, st);
+  if ((e = cudaGetLastError())) return e;
+  hook.before(K_CONTACT_SCATTER, st);
+  fill_kernel<<<blocks(cs.ncell, tb), tb, 0, st>>>(cs.cell_start, cs.ncell, cs.cell_fill, cs.cell_count, gate);
+  hook.after(K_CONTACT_SCATTER, st);
+  hook.before(K_CONTACT_SCATTER, st);
+  scatter_kernel<<<blocks(E, tb), tb, 0, st>>>(cs.seg_cell, E, cs.cell_fill, cs.sorted, gate);
+  hook.after(K_CONTACT_SCATTER, st);
+  hook.before(K_CONTACT_SORT, st);
+  sort_cells_kernel<<<blocks(cs.ncell, tb), tb, 0, st>>>(cs.cell_start, cs.ncell, cs.sorted, err, gate);
+  hook.after(K_CONTACT_SORT, st);
+  if ((e = cudaGetLastError())) return e;
+  hook.before(K_CONTACT_SORT, st);
+  records_kernel<<<blocks(E, tb), tb, 0, st>>>(cs.sorted, cs.seg_rod, cs.seg_cell, cs.cell_start, cs.prox, x, N, rods,
+                                              E, cs.recA, cs.recB, cs.recC, gate ? cs.slot_of : nullptr, gate);
+  hook.after(K_CONTACT_SORT, st);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t contact_compute(ContactState& cs, const double* x, const double* v, const RodConst* rods, int64_t N,
+                            int64_t E, int R, int* err, cudaStream_t st, const LaunchHook& hook, bool prebinned) {
+  (void)R;
+  cudaError_t e = enqueue_build(cs, x, rods, N, E, err, st, hook, prebinned, nullptr);
+  if (e) return e;
+  const ContactArgs A = make_args(cs, x, v, rods, N, E, err, nullptr);
   hook.before(K_CONTACT_GATHER, st);
   gather_kernel<<<(E + 255) / 256, 256, 0, st>>>(A);
   hook.after(K_CONTACT_GATHER, st);
   return cudaGetLastError();
+}
+
+cudaError_t contact_list_compute(ContactState& cs, const double* x, const double* v, const RodConst* rods, int64_t N,
+                                 int64_t E, int R, int* err, cudaStream_t st, const LaunchHook& hook) {
+  (void)R;
+  const double half = 0.5 * cs.skin * (1.0 - 1e-6);
+  hook.before(K_MISC, st);
+  list_decide_kernel<<<1, 1, 0, st>>>(cs.ctl, half * half);
+  hook.after(K_MISC, st);
+  const int* gate = &cs.ctl->gate;
+  cudaError_t e = enqueue_build(cs, x, rods, N, E, err, st, hook, false, gate);
+  if (e) return e;
+  const ContactArgs A = make_args(cs, x, v, rods, N, E, err, gate);
+  const unsigned gb = static_cast<unsigned>(std::max(1, 8 * cs.sm_count));
+  hook.before(K_CONTACT_LIST_BUILD, st);
+  list_build_kernel<<<gb, 256, 0, st>>>(A);
+  hook.after(K_CONTACT_LIST_BUILD, st);
+  hook.before(K_CONTACT_LIST_BUILD, st);
+  list_snapshot_kernel<<<gb, 256, 0, st>>>(x, 3 * N, cs.x_ref, cs.ctl, gate);
+  hook.after(K_CONTACT_LIST_BUILD, st);
+  if ((e = cudaGetLastError())) return e;
+  hook.before(K_CONTACT_LIST_FORCE, st);
+  list_force_kernel<<<(E + 255) / 256, 256, 0, st>>>(A);
+  hook.after(K_CONTACT_LIST_FORCE, st);
+  return cudaGetLastError();
+}
+
+void contact_list_params(const ContactState& cs, StepParams& P) {
+  P.disp_ref = cs.x_ref;
+  P.disp_word = &cs.ctl->disp2;
+}
+
+cudaError_t contact_list_invalidate(const ContactState& cs, cudaStream_t st) {
+  if (!cs.ctl) return cudaSuccess;
+  return cudaMemsetAsync(&cs.ctl->force, 0xff, sizeof(int), st);
 }
 
 cudaError_t contact_node_forces(const ContactState& cs, const RodConst* rods, int64_t N, int64_t E, int R, double* f,

@@ -11,6 +11,21 @@
 
 namespace rod {
 
+// Device-side control of the skin list: the largest squared node displacement since the last
+// build (bits of a non-negative double, raised by the step kernels), the rebuild decision of
+// the current evaluation, and a request to rebuild from the host.
+struct ListCtl {
+  unsigned long long disp2;
+  int gate;
+  int force;
+  int builds;  // list builds since the grid was set up
+  int pad;
+};
+
+// Capacity of one segment's candidate list; a segment with more candidates scans its
+// neighbourhood of the last build instead.
+constexpr int kNbrCap = 16;
+
 struct ContactState {
   bool enabled = false;
   double k = 0.0, c = 0.0, cell_size = 0.0;
@@ -35,8 +50,19 @@ struct ContactState {
   int* sorted = nullptr;      // [E] segments ordered by cell, ascending index within a cell
   float4* prox = nullptr;     // [E] FP32 midpoint + half length (culling only)
   float4* recA = nullptr;     // [E] prox in cell order
-  int4* recB = nullptr;       // [E] (segment, rod, FP32 radius bits, 0) in cell order
+  int4* recB = nullptr;       // [E] (segment, rod, FP32 radius bits, end of the rod's run) in cell order
+  float4* recC = nullptr;     // [E] FP32 half edge (x_{i+1} - x_i) / 2 in cell order
   double* fseg = nullptr;     // [6E] force on the first / second node of each segment
+  // skin list (skin > 0): candidates within r_a + r_b + skin at the last build, kept while no
+  // node has moved by skin / 2 since (then no pair outside the list can touch)
+  double skin = 0.0;
+  int sm_count = 0;
+  int64_t N = 0;
+  int* nbr = nullptr;         // [kNbrCap * E] entry-major: candidate k of segment a at k E + a
+  int* nbr_count = nullptr;   // [E] (> kNbrCap: overflowed, scan instead)
+  int* slot_of = nullptr;     // [E] slot of each segment in the last build's cell order
+  double* x_ref = nullptr;    // [3N] positions of the last build
+  ListCtl* ctl = nullptr;
 };
 
 void contact_release(ContactState& cs);
@@ -57,6 +83,17 @@ cudaError_t contact_compute(ContactState& cs, const double* x, const double* v, 
 // Point the step kernel's binning epilogue at this grid; zero the per-cell counts.
 void contact_bin_params(const ContactState& cs, StepParams& P);
 cudaError_t contact_clear_counts(const ContactState& cs, cudaStream_t st);
+
+// Skin-list evaluation of the contact forces at x, v -> cs.fseg: rebuild (bin, sort, list) on
+// the device when the displacement since the last build reaches skin / 2 or a rebuild was
+// requested, then the forces of the listed pairs.  The per-cell counts must be zero on entry
+// (contact_clear_counts) and are zero again after a rebuild.
+cudaError_t contact_list_compute(ContactState& cs, const double* x, const double* v, const RodConst* rods, int64_t N,
+                                 int64_t E, int R, int* err, cudaStream_t st, const LaunchHook& hook);
+// Point the step kernels' displacement tracking at the list's reference positions.
+void contact_list_params(const ContactState& cs, StepParams& P);
+// Make the next list evaluation rebuild (after anything that overwrote the cell structures).
+cudaError_t contact_list_invalidate(const ContactState& cs, cudaStream_t st);
 
 // Sum cs.fseg into node forces f [3N] (debug / parity entry point).
 cudaError_t contact_node_forces(const ContactState& cs, const RodConst* rods, int64_t N, int64_t E, int R, double* f,

@@ -98,6 +98,10 @@ struct StepParams {
   float bin_inv_h;
   int bin_dim[3];
   float bin_l_allowed;        // longest element the cell covers, less the FP32 rounding margin
+  // skin-list contact: largest squared node displacement since the list was built, raised by
+  // every launch with the bits of a non-negative double (disp_ref = null: not tracked)
+  const double* disp_ref;     // [3N] positions of the last list build
+  unsigned long long* disp_word;
   // host side only: packs of rods too long for a block (one rod each) and the global scratch
   // their cooperative launches use as working memory
   const struct Pack* long_packs_h;
@@ -108,7 +112,8 @@ struct StepParams {
 // Kernel classes for the optional per-kernel timing (rod_system_profile).
 enum KernelClass : int {
   K_PACK_STEPS = 0, K_PACK_ONE_STEP, K_KIN_HALF, K_RHS, K_CONTACT_BIN, K_CONTACT_SCAN, K_CONTACT_SCATTER,
-  K_CONTACT_SORT, K_CONTACT_GATHER, K_CONTACT_NODE_FORCES, K_MISC, K_NUM_CLASSES
+  K_CONTACT_SORT, K_CONTACT_GATHER, K_CONTACT_NODE_FORCES, K_CONTACT_LIST_BUILD, K_CONTACT_LIST_FORCE, K_MISC,
+  K_NUM_CLASSES
 };
 const char* kernel_class_name(int k);
 

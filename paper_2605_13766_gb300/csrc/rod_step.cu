@@ -40,9 +40,13 @@ namespace {
 template <int MODE>
 __device__ __forceinline__ void pack_body(const StepParams& P, const Pack& pk, Smem& m, int64_t n_steps, double t0,
                                           double dt, int last_half, double* acc_v, double* acc_w) {
-  // a step after a latched error (non-finite state, contact overflow) is skipped (the word is
-  // read before the first barrier, so every block of a grid takes the same path)
-  if (MODE == MODE_ONE_STEP && *(volatile int*)P.err != 0) return;
+  // a step after a latched error (non-finite state, contact overflow) is skipped: a block
+  // decides once for all its threads; the blocks of a cooperative grid all read the word
+  // before any of them can set it (after the last grid barrier)
+  if (MODE == MODE_ONE_STEP) {
+    const bool stop = *(volatile int*)P.err != 0;
+    if (m.grid ? stop : __syncthreads_or(stop)) return;
+  }
   const int Ep = pk.nelem, Np = pk.nnode;
 
   stage_pack(P, pk, m);
@@ -140,14 +144,29 @@ __device__ __forceinline__ void pack_body(const StepParams& P, const Pack& pk, S
       P.w[c * P.E + pk.elem0 + i] = ww;
     }
   }
+  double disp2 = 0.0;  // largest squared displacement since the skin list's build
   for (int j = m.t0; j < Np; j += m.ts) {
+    double d2 = 0.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const double xx = m.X[c * m.CN + j], vv = m.VN[c * m.CN + j];
       bad |= !isfinite(xx) || !isfinite(vv);
       P.x[c * P.N + pk.node0 + j] = xx;
       P.v[c * P.N + pk.node0 + j] = vv;
+      if (P.disp_ref) {
+        const double d = xx - P.disp_ref[c * P.N + pk.node0 + j];
+        d2 = fma(d, d, d2);
+      }
     }
+    disp2 = fmax(disp2, d2);
+  }
+  if (P.disp_ref && MODE != MODE_RHS) {
+    // warp maximum, then one atomic per warp whose maximum raises the word (non-negative
+    // doubles order like their bit patterns)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) disp2 = fmax(disp2, __shfl_xor_sync(0xffffffffu, disp2, o));
+    const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(disp2));
+    if ((threadIdx.x & 31) == 0 && bits > *(volatile unsigned long long*)P.disp_word) atomicMax(P.disp_word, bits);
   }
   if (m.grid) {
     if (__any_sync(__activemask(), bad) && (threadIdx.x & 31) == __ffs(__activemask()) - 1) atomicOr(P.err, ERR_NONFINITE);
@@ -193,7 +212,8 @@ size_t step_smem_bytes(const LaunchShape& s) {
 const char* kernel_class_name(int k) {
   static const char* names[K_NUM_CLASSES] = {"pack_steps", "pack_one_step", "kin_half", "rhs", "contact_bin",
                                              "contact_scan", "contact_scatter", "contact_sort", "contact_gather",
-                                             "contact_node_forces", "misc"};
+                                             "contact_node_forces", "contact_list_build", "contact_list_force",
+                                             "misc"};
   return (k >= 0 && k < K_NUM_CLASSES) ? names[k] : "?";
 }
 

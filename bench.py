@@ -286,6 +286,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--launch-shape", default=None,
+                    help="elements,threads per block for the step kernels (skips the autotuner)")
     ap.add_argument("--skin", type=float, default=None,
                     help="contact skin list (m); default 0.5 mm for the packing, 0 = cell search every step")
     ap.add_argument("--surrogate-train-steps", type=int, default=15000)
@@ -323,7 +325,11 @@ def main():
     # launch shape (elements and threads per block) picked by the library's autotuner on the
     # live state, which it restores afterwards
     tuned = None
-    if not args.no_autotune:
+    if args.launch_shape:
+        te, tt = (int(v) for v in args.launch_shape.split(","))
+        s.set_launch(te, tt)
+        tuned = {"elems_per_block": te, "threads_per_block": tt, "trial_ms_per_step": None}
+    elif not args.no_autotune:
         te, tt, tms = s.autotune(dt, trial_steps=5)
         tuned = {"elems_per_block": te, "threads_per_block": tt, "trial_ms_per_step": tms}
     s.step(W, dt)

@@ -196,6 +196,7 @@ struct rod_system {
   LaunchHook hook;
   // CUDA graph of kGraphSteps contact steps (captured on cap_stream, replayed on stream)
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t body_stream = nullptr;  // captures the bodies of the graph's conditional nodes
   DevBuf<double> t_dev;
   cudaGraphExec_t graph_exec = nullptr;
   double graph_dt = 0.0;
@@ -362,10 +363,46 @@ bool finite_all(const double* p, size_t n) {
 // launch per kGraphSteps steps.  The time of the state is read from t_dev inside the graph.
 constexpr int kGraphSteps = 32;
 // kernels per captured step: scan x3, fill, scatter, sort, records, gather, step, time; with the
-// skin list decide, bin, scan x3, fill, scatter, sort, records, build, snapshot, force, step, time
-// (the rebuild kernels return at once unless a rebuild is due)
+// skin list decide, force, step, time, and the rebuild kernels (bin, scan x3, fill, scatter,
+// sort, records, build, snapshot) in a conditional node that the decision opens only when a
+// rebuild is due (those launches are counted on the device)
 constexpr int kKernelsPerGraphStep = 10;
-constexpr int kKernelsPerListGraphStep = 14;
+constexpr int kKernelsPerListGraphStep = 4;
+
+// One skin-list contact evaluation during the capture of s->cap_stream: the decision, an IF
+// node whose body (captured on s->body_stream) holds the rebuild kernels, then the forces.
+cudaError_t capture_list_step(rod_system* s) {
+  LaunchHook none;
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s->cap_stream, &cst, nullptr, &g, &deps, nullptr, &nd);
+  if (e) return e;
+  if (cst != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphConditionalHandle cond;
+  if ((e = cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault))) return e;
+  if ((e = contact_list_decide(s->contact, s->cap_stream, none, &cond))) return e;
+  if ((e = cudaStreamGetCaptureInfo(s->cap_stream, &cst, nullptr, &g, &deps, nullptr, &nd))) return e;
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  if ((e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp))) return e;
+  if ((e = cudaStreamUpdateCaptureDependencies(s->cap_stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies)))
+    return e;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if ((e = cudaStreamBeginCaptureToGraph(s->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
+    return e;
+  e = contact_list_rebuild(s->contact, s->x.p, s->rods.p, s->N, s->E, s->err.p, s->body_stream, none);
+  cudaGraph_t out = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(s->body_stream, &out);
+  if (e) return e;
+  if (e2) return e2;
+  return contact_list_force(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->err.p, s->cap_stream, none);
+}
 
 rod_status ensure_contact_graph(rod_system* s, const StepParams& Pb, double dt) {
   if (s->graph_exec && s->graph_dt == dt && s->graph_grid_version == s->contact.version &&
@@ -384,8 +421,7 @@ rod_status ensure_contact_graph(rod_system* s, const StepParams& Pb, double dt) 
   CUDA_TRY(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
-    e = list ? contact_list_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->cap_stream,
-                                    none)
+    e = list ? capture_list_step(s)
              : contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->cap_stream,
                                none, true);
     if (e == cudaSuccess) e = launch_pack_kernel(Pg, s->shape, MODE_ONE_STEP, 1, 0.0, dt, 0, nullptr, nullptr,
@@ -603,6 +639,7 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
     rc.damp_lin = (d->nu_damp + d->stokes_gamma) / (rho * A);
     rc.damp_rot = d->nu_damp / (rho * A);
     rc.radius = rad;
+    rc.radius_f = static_cast<float>(rad);
     rc.node0 = static_cast<int32_t>(n0);
     rc.elem0 = static_cast<int32_t>(e0);
     rc.n = d->n_elem[r];
@@ -702,7 +739,8 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
     }
     if ((ce = up(s->arc0, arc.data(), E))) return cleanup(fail(ROD_ERR_CUDA, "copy failed: %s", cudaGetErrorString(ce)));
   }
-  if ((ce = s->t_dev.alloc(1)) || (ce = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking)))
+  if ((ce = s->t_dev.alloc(1)) || (ce = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking)) ||
+      (ce = cudaStreamCreateWithFlags(&s->body_stream, cudaStreamNonBlocking)))
     return cleanup(fail(ROD_ERR_CUDA, "allocation failed: %s", cudaGetErrorString(ce)));
   if ((ce = cudaMemset(s->err.p, 0, sizeof(int))) || (ce = cudaMallocHost(&s->err_host, sizeof(int))))
     return cleanup(fail(ROD_ERR_CUDA, "allocation failed: %s", cudaGetErrorString(ce)));
@@ -744,6 +782,7 @@ rod_status rod_system_destroy(rod_system* s) {
   contact_release(s->contact);
   if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  if (s->body_stream) cudaStreamDestroy(s->body_stream);
   s->t_dev.release();
   if (s->err_host) cudaFreeHost(s->err_host);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -1227,7 +1266,7 @@ rod_status rod_system_profile_read(rod_system* s, int32_t k, const char** name, 
 
 rod_status rod_system_launch_count(const rod_system* s, int64_t* launches) {
   if (!s || !launches) return fail(ROD_ERR_ARG, "null argument");
-  *launches = s->prof.launches;
+  *launches = s->prof.launches + contact_list_graph_rebuild_launches(s->contact, s->stream);
   return ROD_OK;
 }
 

@@ -315,6 +315,7 @@ struct ContactArgs {
   int* nbr;
   int* nbr_count;
   const int* slot_of;
+  const float4* seg_prox;
   float skin;
   const RodConst* rods;
   double* fseg;
@@ -517,23 +518,11 @@ __global__ void __launch_bounds__(256) list_build_kernel(ContactArgs A) {
   }
 }
 
-// FP32 midpoint, half length and half edge of segment (nodes n, n + 1) from the FP64 positions.
-__device__ __forceinline__ void seg_now(const double* __restrict__ x, int64_t N, int64_t n, float4& g, float4& e) {
-  double d[3], m[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const double p0 = x[c * N + n], p1 = x[c * N + n + 1];
-    m[c] = 0.5 * (p0 + p1);
-    d[c] = 0.5 * (p1 - p0);
-  }
-  e = make_float4((float)d[0], (float)d[1], (float)d[2], 0.f);
-  g = make_float4((float)m[0], (float)m[1], (float)m[2], (float)sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
-}
-
-// Skin-list evaluation: one thread per segment, its listed candidates culled in FP32 at the
-// current positions and evaluated in FP64; a segment whose list overflowed scans its
-// neighbourhood of the last build with the skin bound (the build's records are stale by less
-// than skin / 2 per node, which the skin covers).
+// Skin-list evaluation: one thread per segment, its listed candidates culled in FP32 against
+// the segment proxies of the current positions (written by the step kernel that produced them)
+// and evaluated in FP64; a segment whose list overflowed scans its neighbourhood of the last
+// build with the skin bound (the build's records are stale by less than skin / 2 per node,
+// which the skin covers).
 __global__ void __launch_bounds__(256) list_force_kernel(ContactArgs A) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= A.E) return;
@@ -543,15 +532,19 @@ __global__ void __launch_bounds__(256) list_force_kernel(ContactArgs A) {
   ForceSum f(A, (int)a, ra);
   if (n <= kNbrCap) {
     if (n > 0) {
-      float4 ga, ea;
-      seg_now(A.x, A.N, a + ra, ga, ea);
-      const float rada = (float)A.rods[ra].radius;
+      const float4 ga = A.seg_prox[2 * a], ea = A.seg_prox[2 * a + 1];
+      // the next candidate's index and proxy are loaded while the current one is tested
+      int b = A.nbr[a];
+      float4 gb = A.seg_prox[2 * (int64_t)b], eb = A.seg_prox[2 * (int64_t)b + 1];
       for (int k = 0; k < n; ++k) {
-        const int b = A.nbr[k * A.E + a];
-        const int rb = A.seg_rod[b];
-        float4 gb, eb;
-        seg_now(A.x, A.N, (int64_t)b + rb, gb, eb);
-        if (may_touch(ga, gb, ea, eb, rada + (float)A.rods[rb].radius)) f(b, rb);
+        const int bc = b;
+        const float4 gc = gb, ec = eb;
+        if (k + 1 < n) {
+          b = A.nbr[(k + 1) * A.E + a];
+          gb = A.seg_prox[2 * (int64_t)b];
+          eb = A.seg_prox[2 * (int64_t)b + 1];
+        }
+        if (may_touch(ga, gc, ea, ec, ea.w + ec.w)) f(bc, A.seg_rod[bc]);
       }
     }
   } else {
@@ -561,18 +554,24 @@ __global__ void __launch_bounds__(256) list_force_kernel(ContactArgs A) {
 }
 
 // Rebuild decision of this evaluation: requested, or a node has moved by skin / 2 (or the
-// displacement is not finite).
-__global__ void list_decide_kernel(ListCtl* ctl, double limit2) {
+// displacement is not finite).  Inside a graph it also opens or skips the conditional node
+// that holds the rebuild kernels.
+__global__ void list_decide_kernel(ListCtl* ctl, double limit2, cudaGraphConditionalHandle cond, int use_cond) {
   const double d2 = __longlong_as_double(static_cast<long long>(ctl->disp2));
-  ctl->gate = (ctl->force != 0 || !(d2 < limit2)) ? 1 : 0;
+  const int gate = (ctl->force != 0 || !(d2 < limit2)) ? 1 : 0;
+  ctl->gate = gate;
+  if (use_cond) {
+    cudaGraphSetConditional(cond, static_cast<unsigned>(gate));
+    ctl->opened += gate;
+  }
 }
 
 // After a rebuild: the build's positions become the reference, the displacement restarts.
-__global__ void list_snapshot_kernel(const double* __restrict__ x, int64_t n, double* __restrict__ x_ref, ListCtl* ctl,
+__global__ void list_snapshot_kernel(const double* __restrict__ x, int64_t n, float* __restrict__ x_ref, ListCtl* ctl,
                                      const int* gate) {
   if (gated_off(gate)) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x_ref[i] = x[i];
+    x_ref[i] = static_cast<float>(x[i]);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->disp2 = 0ull;
     ctl->force = 0;
@@ -607,7 +606,7 @@ cudaError_t dev_alloc(T** p, size_t count) {
 void contact_release(ContactState& cs) {
   void* ptrs[] = {cs.seg_rod, cs.seg_cell, cs.cell_count, cs.cell_start, cs.cell_fill,
                   cs.block_sums, cs.sorted, cs.prox, cs.fseg, cs.recA, cs.recB, cs.recC,
-                  cs.nbr, cs.nbr_count, cs.slot_of, cs.x_ref, cs.ctl};
+                  cs.nbr, cs.nbr_count, cs.slot_of, cs.x_ref, cs.seg_prox, cs.ctl};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cs.seg_rod = cs.seg_cell = cs.cell_count = cs.cell_start = cs.cell_fill = cs.block_sums = cs.sorted = nullptr;
@@ -618,7 +617,9 @@ void contact_release(ContactState& cs) {
   cs.recC = nullptr;
   cs.nbr = cs.nbr_count = cs.slot_of = nullptr;
   cs.x_ref = nullptr;
+  cs.seg_prox = nullptr;
   cs.ctl = nullptr;
+  cs.ctl_live = false;
   cs.N = 0;
   cs.cap_cells = 0;
   cs.E = 0;
@@ -629,9 +630,26 @@ static rod_status cfail(rod_status st, const char* what, cudaError_t e) {
   return internal_fail(st, what, e == cudaSuccess ? "" : cudaGetErrorString(e));
 }
 
+int64_t contact_list_graph_rebuild_launches(const ContactState& cs, cudaStream_t st) {
+  int64_t opened = cs.opened_before;
+  if (cs.ctl && cs.ctl_live) {
+    ListCtl c{};
+    if (cudaMemcpyAsync(&c, cs.ctl, sizeof(ListCtl), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+        cudaStreamSynchronize(st) == cudaSuccess)
+      opened += c.opened;
+    cudaGetLastError();
+  }
+  return opened * kListRebuildKernels;
+}
+
 rod_status contact_prepare(ContactState& cs, const std::vector<RodConst>& rods_h, const RodConst* rods_dev,
                            const double* x_dev, int64_t N, int64_t E, int R, cudaStream_t st, const LaunchHook& hook) {
   if (cs.grid_valid) return ROD_OK;
+  if (cs.ctl && cs.ctl_live) {
+    // the list state restarts below: keep the count of rebuilds run inside graphs so far
+    cs.opened_before = contact_list_graph_rebuild_launches(cs, st) / kListRebuildKernels;
+    cs.ctl_live = false;
+  }
   std::vector<double> x(3 * N);
   cudaError_t e = cudaMemcpyAsync(x.data(), x_dev, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -693,7 +711,8 @@ rod_status contact_prepare(ContactState& cs, const std::vector<RodConst>& rods_h
   }
   if (skin > 0.0 && cs.N != N) {
     if ((e = dev_alloc(&cs.nbr, int64_t(kNbrCap) * E)) || (e = dev_alloc(&cs.nbr_count, E)) ||
-        (e = dev_alloc(&cs.slot_of, E)) || (e = dev_alloc(&cs.x_ref, 3 * N)) || (e = dev_alloc(&cs.ctl, 1)))
+        (e = dev_alloc(&cs.slot_of, E)) || (e = dev_alloc(&cs.x_ref, 3 * N)) || (e = dev_alloc(&cs.seg_prox, 2 * E)) ||
+        (e = dev_alloc(&cs.ctl, 1)))
       return cfail(ROD_ERR_CUDA, "contact: skin list allocation", e);
     cs.N = N;
   }
@@ -721,6 +740,7 @@ rod_status contact_prepare(ContactState& cs, const std::vector<RodConst>& rods_h
   if (skin > 0.0) {
     if ((e = cudaMemsetAsync(cs.ctl, 0, sizeof(ListCtl), st)) || (e = contact_list_invalidate(cs, st)))
       return cfail(ROD_ERR_CUDA, "contact: skin list reset", e);
+    cs.ctl_live = true;
   }
   cs.grid_valid = true;
   return ROD_OK;
@@ -761,6 +781,7 @@ ContactArgs make_args(const ContactState& cs, const double* x, const double* v, 
   A.nbr = cs.nbr;
   A.nbr_count = cs.nbr_count;
   A.slot_of = cs.slot_of;
+  A.seg_prox = cs.seg_prox;
   A.skin = (float)cs.skin;
   A.rods = rods;
   A.fseg = cs.fseg;
@@ -843,17 +864,21 @@ cudaError_t contact_compute(ContactState& cs, const double* x, const double* v, 
   return cudaGetLastError();
 }
 
-cudaError_t contact_list_compute(ContactState& cs, const double* x, const double* v, const RodConst* rods, int64_t N,
-                                 int64_t E, int R, int* err, cudaStream_t st, const LaunchHook& hook) {
-  (void)R;
+cudaError_t contact_list_decide(ContactState& cs, cudaStream_t st, const LaunchHook& hook,
+                                const cudaGraphConditionalHandle* cond) {
   const double half = 0.5 * cs.skin * (1.0 - 1e-6);
   hook.before(K_MISC, st);
-  list_decide_kernel<<<1, 1, 0, st>>>(cs.ctl, half * half);
+  list_decide_kernel<<<1, 1, 0, st>>>(cs.ctl, half * half, cond ? *cond : cudaGraphConditionalHandle(0), cond ? 1 : 0);
   hook.after(K_MISC, st);
+  return cudaGetLastError();
+}
+
+cudaError_t contact_list_rebuild(ContactState& cs, const double* x, const RodConst* rods, int64_t N, int64_t E,
+                                 int* err, cudaStream_t st, const LaunchHook& hook) {
   const int* gate = &cs.ctl->gate;
   cudaError_t e = enqueue_build(cs, x, rods, N, E, err, st, hook, false, gate);
   if (e) return e;
-  const ContactArgs A = make_args(cs, x, v, rods, N, E, err, gate);
+  const ContactArgs A = make_args(cs, x, nullptr, rods, N, E, err, gate);
   const unsigned gb = static_cast<unsigned>(std::max(1, 8 * cs.sm_count));
   hook.before(K_CONTACT_LIST_BUILD, st);
   list_build_kernel<<<gb, 256, 0, st>>>(A);
@@ -861,16 +886,31 @@ cudaError_t contact_list_compute(ContactState& cs, const double* x, const double
   hook.before(K_CONTACT_LIST_BUILD, st);
   list_snapshot_kernel<<<gb, 256, 0, st>>>(x, 3 * N, cs.x_ref, cs.ctl, gate);
   hook.after(K_CONTACT_LIST_BUILD, st);
-  if ((e = cudaGetLastError())) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t contact_list_force(ContactState& cs, const double* x, const double* v, const RodConst* rods, int64_t N,
+                               int64_t E, int* err, cudaStream_t st, const LaunchHook& hook) {
+  const ContactArgs A = make_args(cs, x, v, rods, N, E, err, &cs.ctl->gate);
   hook.before(K_CONTACT_LIST_FORCE, st);
   list_force_kernel<<<(E + 255) / 256, 256, 0, st>>>(A);
   hook.after(K_CONTACT_LIST_FORCE, st);
   return cudaGetLastError();
 }
 
+cudaError_t contact_list_compute(ContactState& cs, const double* x, const double* v, const RodConst* rods, int64_t N,
+                                 int64_t E, int R, int* err, cudaStream_t st, const LaunchHook& hook) {
+  (void)R;
+  cudaError_t e = contact_list_decide(cs, st, hook, nullptr);
+  if (e == cudaSuccess) e = contact_list_rebuild(cs, x, rods, N, E, err, st, hook);
+  if (e == cudaSuccess) e = contact_list_force(cs, x, v, rods, N, E, err, st, hook);
+  return e;
+}
+
 void contact_list_params(const ContactState& cs, StepParams& P) {
   P.disp_ref = cs.x_ref;
   P.disp_word = &cs.ctl->disp2;
+  P.seg_prox = cs.seg_prox;
 }
 
 cudaError_t contact_list_invalidate(const ContactState& cs, cudaStream_t st) {

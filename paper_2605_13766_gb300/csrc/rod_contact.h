@@ -19,8 +19,11 @@ struct ListCtl {
   int gate;
   int force;
   int builds;  // list builds since the grid was set up
-  int pad;
+  int opened;  // rebuilds that ran inside a replayed graph's conditional node (launch accounting)
 };
+
+// Kernels of one skin-list rebuild (bin, scan x3, fill, scatter, sort, records, build, snapshot).
+constexpr int kListRebuildKernels = 10;
 
 // Capacity of one segment's candidate list; a segment with more candidates scans its
 // neighbourhood of the last build instead.
@@ -61,9 +64,15 @@ struct ContactState {
   int* nbr = nullptr;         // [kNbrCap * E] entry-major: candidate k of segment a at k E + a
   int* nbr_count = nullptr;   // [E] (> kNbrCap: overflowed, scan instead)
   int* slot_of = nullptr;     // [E] slot of each segment in the last build's cell order
-  double* x_ref = nullptr;    // [3N] positions of the last build
+  float* x_ref = nullptr;     // [3N] positions of the last build, rounded to FP32
+  float4* seg_prox = nullptr; // [2E] FP32 proxies of the current positions, written by the step kernels
   ListCtl* ctl = nullptr;
+  bool ctl_live = false;       // ctl holds counts of the current grid
+  int64_t opened_before = 0;   // ctl->opened of earlier grids (launch accounting)
 };
+
+// Rebuild kernels launched so far inside replayed graphs (reads the device counter).
+int64_t contact_list_graph_rebuild_launches(const ContactState& cs, cudaStream_t st);
 
 void contact_release(ContactState& cs);
 
@@ -90,6 +99,15 @@ cudaError_t contact_clear_counts(const ContactState& cs, cudaStream_t st);
 // (contact_clear_counts) and are zero again after a rebuild.
 cudaError_t contact_list_compute(ContactState& cs, const double* x, const double* v, const RodConst* rods, int64_t N,
                                  int64_t E, int R, int* err, cudaStream_t st, const LaunchHook& hook);
+// The same in three parts, for graph capture: the decision (with a conditional handle it also
+// sets the condition of the graph node that holds the rebuild), the gated rebuild kernels, and
+// the forces of the listed pairs.
+cudaError_t contact_list_decide(ContactState& cs, cudaStream_t st, const LaunchHook& hook,
+                                const cudaGraphConditionalHandle* cond);
+cudaError_t contact_list_rebuild(ContactState& cs, const double* x, const RodConst* rods, int64_t N, int64_t E,
+                                 int* err, cudaStream_t st, const LaunchHook& hook);
+cudaError_t contact_list_force(ContactState& cs, const double* x, const double* v, const RodConst* rods, int64_t N,
+                               int64_t E, int* err, cudaStream_t st, const LaunchHook& hook);
 // Point the step kernels' displacement tracking at the list's reference positions.
 void contact_list_params(const ContactState& cs, StepParams& P);
 // Make the next list evaluation rebuild (after anything that overwrote the cell structures).

@@ -33,7 +33,7 @@ struct RodConst {
   int32_t n;            // elements
   int32_t clamp;        // 1: node 0 + element 0 held
   int32_t act_elem;     // rod-local element carrying the base couple (-1: none)
-  int32_t pad;
+  float radius_f;       // radius rounded to FP32 (contact culling)
   double muscle_amp;    // travelling-wave muscle couple amplitude (0: none)
   double muscle_omega;  // 2 pi / T
   double muscle_k;      // 2 pi / lambda
@@ -98,10 +98,16 @@ struct StepParams {
   float bin_inv_h;
   int bin_dim[3];
   float bin_l_allowed;        // longest element the cell covers, less the FP32 rounding margin
-  // skin-list contact: largest squared node displacement since the list was built, raised by
-  // every launch with the bits of a non-negative double (disp_ref = null: not tracked)
-  const double* disp_ref;     // [3N] positions of the last list build
+  // skin-list contact: an upper bound of the largest squared node displacement since the list
+  // was built, raised by every launch with the bits of a non-negative double (disp_ref = null:
+  // not tracked), and the FP32 segment proxies of the positions a half/one-step launch leaves
+  // behind: [2e] = (midpoint, half length), [2e + 1] = (half edge, radius); null: not written
+  const float* disp_ref;      // [3N] positions of the last list build, rounded to FP32
   unsigned long long* disp_word;
+  float4* seg_prox;           // [2E]
+  // byte offset of the FP32 node positions in a block's dynamic shared memory (0: none; set by
+  // the launcher when the proxies are written and the shape leaves room for them)
+  int32_t xf_smem_off;
   // host side only: packs of rods too long for a block (one rod each) and the global scratch
   // their cooperative launches use as working memory
   const struct Pack* long_packs_h;
@@ -134,6 +140,8 @@ struct LaunchShape {
 };
 
 size_t step_smem_bytes(const LaunchShape& s);
+// Largest dynamic shared memory of one block (opt-in) on this part.
+constexpr size_t kMaxBlockSmem = 227 * 1024;
 
 // Kernel launchers (rod_step.cu).
 enum StepMode : int { MODE_STEPS = 0, MODE_RHS = 1, MODE_KIN_HALF = 2, MODE_ONE_STEP = 3 };

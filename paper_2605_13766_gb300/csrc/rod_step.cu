@@ -93,7 +93,8 @@ __device__ __forceinline__ void pack_body(const StepParams& P, const Pack& pk, S
   // ---- contact binning of the positions this launch leaves behind (the next step's
   // half-step positions): FP32 midpoint, half length and cell of every segment, counted per
   // cell with one atomic per distinct cell in the warp.
-  if ((MODE == MODE_KIN_HALF || (MODE == MODE_ONE_STEP && !last_half)) && P.bin_count) {
+  const bool leaves_half = MODE == MODE_KIN_HALF || (MODE == MODE_ONE_STEP && !last_half);
+  if (leaves_half && P.bin_count) {
     bool grid_bad = false, nonfinite = false;
     for (int i = m.t0; i < Ep; i += m.ts) {
       const int j = i + m.erod[i];
@@ -128,46 +129,80 @@ __device__ __forceinline__ void pack_body(const StepParams& P, const Pack& pk, S
     if (grid_bad) atomicOr(P.err, ERR_GRID);
   }
 
-  // ---- write back, flag non-finite values
-  bool bad = false;
+  // ---- write back.  Non-finite values are found from the largest exponent field on the
+  // integer pipe (all ones: Inf or NaN), which leaves the FP64 pipe to the step's arithmetic.
+  // With the skin list, every segment also gets its FP32 proxy (midpoint, half length, half
+  // edge, radius) from the node positions the kinematic stage rounded to FP32 in shared memory
+  // (or rounded here where the pack has no room for them).
+  unsigned expo = 0u;
+  const bool prox = leaves_half && P.seg_prox != nullptr;
   for (int i = m.t0; i < Ep; i += m.ts) {
+    const int ge = pk.elem0 + i;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       const double q = m.QQ[a * m.CE + i];
-      bad |= !isfinite(q);
-      P.Q[a * P.E + pk.elem0 + i] = q;
+      expo = max(expo, exp_field(q));
+      P.Q[a * P.E + ge] = q;
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const double ww = m.WW[c * m.CE + i];
-      bad |= !isfinite(ww);
-      P.w[c * P.E + pk.elem0 + i] = ww;
+      expo = max(expo, exp_field(ww));
+      P.w[c * P.E + ge] = ww;
+    }
+    if (prox) {
+      const int r = m.erod[i];
+      const int j = i + r;
+      float p0[3], p1[3], he[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        p0[c] = m.XF ? m.XF[c * m.CN + j] : static_cast<float>(m.X[c * m.CN + j]);
+        p1[c] = m.XF ? m.XF[c * m.CN + j + 1] : static_cast<float>(m.X[c * m.CN + j + 1]);
+        he[c] = 0.5f * (p1[c] - p0[c]);
+      }
+      const float hl = sqrtf(fmaf(he[0], he[0], fmaf(he[1], he[1], he[2] * he[2])));
+      P.seg_prox[2 * static_cast<int64_t>(ge)] =
+          make_float4(0.5f * (p0[0] + p1[0]), 0.5f * (p0[1] + p1[1]), 0.5f * (p0[2] + p1[2]), hl);
+      P.seg_prox[2 * static_cast<int64_t>(ge) + 1] = make_float4(he[0], he[1], he[2], P.rods[pk.rod0 + r].radius_f);
     }
   }
-  double disp2 = 0.0;  // largest squared displacement since the skin list's build
+  // Upper bound of the node displacement since the skin list's build, in FP32: with xf, rf the
+  // FP32 roundings of the position and of the build's position (each within 2^-24 of its
+  // magnitude), |x - x_ref| <= |xf - rf| + 2^-24 sum_c (|xf_c| + |rf_c|) (to first order);
+  // the factor and the coefficient below cover that and the rounding of these expressions.
+  const bool track = P.disp_ref != nullptr && MODE != MODE_RHS;
+  float dmax = 0.f;
   for (int j = m.t0; j < Np; j += m.ts) {
-    double d2 = 0.0;
+    const int64_t gn = pk.node0 + j;
+    float s2 = 0.f, mag = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const double xx = m.X[c * m.CN + j], vv = m.VN[c * m.CN + j];
-      bad |= !isfinite(xx) || !isfinite(vv);
-      P.x[c * P.N + pk.node0 + j] = xx;
-      P.v[c * P.N + pk.node0 + j] = vv;
-      if (P.disp_ref) {
-        const double d = xx - P.disp_ref[c * P.N + pk.node0 + j];
-        d2 = fma(d, d, d2);
+      expo = max(expo, max(exp_field(xx), exp_field(vv)));
+      P.x[c * P.N + gn] = xx;
+      P.v[c * P.N + gn] = vv;
+      if (track) {
+        const float xf = m.XF ? m.XF[c * m.CN + j] : static_cast<float>(xx);
+        const float rf = P.disp_ref[c * P.N + gn];
+        const float d = xf - rf;
+        s2 = fmaf(d, d, s2);
+        mag += fabsf(xf) + fabsf(rf);
       }
     }
-    disp2 = fmax(disp2, d2);
+    if (track) dmax = fmaxf(dmax, fmaf(sqrtf(s2), 1.000001f, 1.25e-7f * mag));
   }
-  if (P.disp_ref && MODE != MODE_RHS) {
+  if (track) {
     // warp maximum, then one atomic per warp whose maximum raises the word (non-negative
-    // doubles order like their bit patterns)
+    // doubles order like their bit patterns; the square of an FP32 value is exact in FP64)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) disp2 = fmax(disp2, __shfl_xor_sync(0xffffffffu, disp2, o));
-    const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(disp2));
-    if ((threadIdx.x & 31) == 0 && bits > *(volatile unsigned long long*)P.disp_word) atomicMax(P.disp_word, bits);
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if ((threadIdx.x & 31) == 0) {
+      const double d2 = static_cast<double>(dmax) * static_cast<double>(dmax);
+      const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(d2));
+      if (bits > *(volatile unsigned long long*)P.disp_word) atomicMax(P.disp_word, bits);
+    }
   }
+  const bool bad = expo == kExpAllOnes;
   if (m.grid) {
     if (__any_sync(__activemask(), bad) && (threadIdx.x & 31) == __ffs(__activemask()) - 1) atomicOr(P.err, ERR_NONFINITE);
   } else if (__syncthreads_or(bad) && threadIdx.x == 0) {
@@ -181,6 +216,7 @@ __global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, 
   extern __shared__ double smem_d[];
   const Pack pk = P.packs[blockIdx.x];
   Smem m = carve(smem_d, S);
+  if (P.xf_smem_off) m.XF = reinterpret_cast<float*>(reinterpret_cast<char*>(smem_d) + P.xf_smem_off);
   pack_body<MODE>(P, pk, m, n_steps, t0, dt, last_half, acc_v, acc_w);
 }
 
@@ -251,10 +287,22 @@ cudaError_t launch_grid_packs(const StepParams& P, int64_t n_steps, double t0, d
 
 }  // namespace
 
-cudaError_t launch_pack_kernel(const StepParams& P, const LaunchShape& s, int mode, int64_t n_steps, double t0,
+cudaError_t launch_pack_kernel(const StepParams& P0, const LaunchShape& s, int mode, int64_t n_steps, double t0,
                                double dt, int last_half, double* acc_v, double* acc_w, cudaStream_t st,
                                const LaunchHook& hook) {
-  const size_t smem = step_smem_bytes(s);
+  size_t smem = step_smem_bytes(s);
+  // FP32 node positions for the skin list's segment proxies, behind the pack's arrays when the
+  // block's shared memory has room (otherwise the epilogue rounds the FP64 positions itself)
+  StepParams P = P0;
+  P.xf_smem_off = 0;
+  if (P.seg_prox && mode != MODE_RHS) {
+    const size_t off = (smem + 15) & ~size_t(15);
+    const size_t need = off + sizeof(float) * 3 * static_cast<size_t>(s.cap_elems + s.cap_rods);
+    if (need <= kMaxBlockSmem) {
+      P.xf_smem_off = static_cast<int32_t>(off);
+      smem = need;
+    }
+  }
   const dim3 grid(P.n_packs), block(s.threads);
   const int cls = mode == MODE_STEPS ? K_PACK_STEPS : mode == MODE_ONE_STEP ? K_PACK_ONE_STEP
                 : mode == MODE_KIN_HALF ? K_KIN_HALF : K_RHS;

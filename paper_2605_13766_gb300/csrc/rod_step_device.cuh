@@ -18,6 +18,11 @@ namespace {
 // High 32 bits of a non-negative double: x < 2^k exactly when hi_word(x) < hi_word(2^k), so a
 // warp-wide integer maximum of these words bounds every lane's argument.
 __device__ __forceinline__ unsigned hi_word(double x) { return static_cast<unsigned>(__double2hiint(x)); }
+// Exponent field of a double (all ones: Inf or NaN), from its high word on the integer pipe.
+__device__ __forceinline__ unsigned exp_field(double x) {
+  return static_cast<unsigned>(__double2hiint(x)) & 0x7FF00000u;
+}
+constexpr unsigned kExpAllOnes = 0x7FF00000u;
 constexpr unsigned kHi2m20 = 0x3EB00000u;  // 2^-20
 constexpr unsigned kHi2m10 = 0x3F500000u;  // 2^-10
 
@@ -114,6 +119,7 @@ struct Smem {
   double* BF;                   // [4] magnetic field b(t) of the step and its force time t
   int* rel0;                    // [CR+1] first element of each rod (pack-local)
   short *erod, *nrod, *vrod;    // pack-local rod of each element / node / Voronoi point
+  float* XF;                    // [3][CN] node positions rounded to FP32 by the kinematic stage, or null
   int CE, CN, CV, CR;
   // the threads that share the pack: this thread's index and their number (a block, or the
   // whole grid of a cooperative launch whose working arrays live in global memory)
@@ -155,6 +161,7 @@ __device__ __forceinline__ Smem carve(double* base, const LaunchShape& S) {
   m.erod = reinterpret_cast<short*>(m.rel0 + m.CR + 1);
   m.nrod = m.erod + m.CE;
   m.vrod = m.nrod + m.CN;
+  m.XF = nullptr;
   m.t0 = threadIdx.x;
   m.ts = blockDim.x;
   m.grid = false;
@@ -218,6 +225,7 @@ __device__ __forceinline__ void kin_node(const StepParams& P, const Pack& pk, Sm
   for (int c = 0; c < 3; ++c) {
     const double val = held ? P.clamp_x[c * P.n_rods + g] : fma(h, m.VN[c * m.CN + j], m.X[c * m.CN + j]);
     m.X[c * m.CN + j] = val;
+    if (m.XF) m.XF[c * m.CN + j] = static_cast<float>(val);
   }
 }
 

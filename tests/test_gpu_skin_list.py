@@ -209,3 +209,26 @@ def test_skin_must_be_finite_and_non_negative():
             s.contact_skin(bad)
     s.contact_skin(0.0)
     assert s.contact_list_builds() == 0
+
+
+def test_replayed_graph_launches_rebuild_kernels_only_when_due():
+    """Inside a replayed graph the rebuild kernels sit in a conditional node that the device-side
+    decision opens only when a rebuild is due: per step the decision, the forces, the step and
+    the time advance, plus the ten rebuild kernels per rebuild.  Eager steps launch all thirteen
+    of theirs (decision, ten rebuild kernels that return at once when no rebuild is due, forces,
+    step)."""
+    p = _touching(60, 0.1, 14)
+    counts = {}
+    for graphs in (True, False):
+        s = _gpu(p, 2e-4, graphs=graphs)
+        s.step(1, 2e-6)                       # grid set-up and the first list build
+        b0, l0 = s.contact_list_builds(), s.launch_count
+        s.step(65, 2e-6)                      # kinematic half step, 2 graph replays of 32 steps, 1 eager step
+        counts[graphs] = (s.contact_list_builds() - b0, s.launch_count - l0)
+        s.close()
+    (builds_g, n_g), (builds_e, n_e) = counts[True], counts[False]
+    assert builds_g == builds_e >= 1
+    assert n_e == 1 + 65 * 13
+    # kinematic half step, set_time, 64 replayed steps, one eager step with all its kernels
+    assert n_g <= 1 + 1 + 64 * 4 + 10 * builds_g + 13
+    assert n_g >= 1 + 1 + 64 * 4 + 13

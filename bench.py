@@ -37,23 +37,28 @@ import rodgen  # noqa: E402
 METRIC = "element-steps/sec FP64 on 1 GB300 (% HBM roofline); surrogate speedup at <=1e-3 err"
 UNIT = "element-steps/s"
 
-# FP64 peak of the part: 2 FP64 FMA per clock per SM (measured 1.975 with an FMA-throughput
-# probe) x 152 SMs x 2.07 GHz max SM clock x 2 flop per FMA.
+# FP64 peak of the part: 2 FP64 FMA per clock per SM (an FMA-throughput probe measured 1.91 per
+# clock at 2.07 GHz) x 152 SMs x 2.07 GHz max SM clock x 2 flop per FMA.
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
 # Algorithmic FP64 flops per unit of each kernel: the FP64 arithmetic of the formulas as the
 # kernel evaluates them, counted by ncu on the active threads (add/sub/mul = 1 flop, fma = 2),
-# divided by the units of the launch.  Source: profiles/pack_kernel_one_step_packing_10k.md
-# (pack_kernel<3>, one step of the 10^4-rod packing: 158.06M DFMA + 44.98M DADD + 128.68M
-# DMUL on 1,366,295 element-steps = 358.6 flop per element-step).
+# divided by the units of the launch.  pack_one_step: one launch of pack_kernel<3> on the
+# 10^4-rod packing, 159.27M DFMA + 36.13M DADD + 121.92M DMUL on 1,366,295 element-steps
+# (profiles/pack_kernel_one_step_packing_10k.md).  pack_steps: one 20-step launch of
+# pack_kernel<0> on the 64 x 64 carpet, 465.37M DFMA + 82.90M DADD + 367.68M DMUL on 4,096,000
+# element-steps (profiles/pack_kernel_steps_carpet_4096.md).
 FLOPS_PER_UNIT = {
-    "pack_one_step": 358.6,   # per element-step
-    "pack_steps": None,       # per element-step (not yet counted for the blocked kernel)
+    "pack_one_step": 348.8,   # per element-step
+    "pack_steps": 337.2,      # per element-step
 }
-# DRAM bytes per launch of the same capture (dram__bytes_read.sum + dram__bytes_write.sum);
-# reset to None whenever the kernel changes.
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the same captures;
+# reset to None whenever the kernel changes.  The carpet's state stays on chip between the
+# steps of a launch: its traffic is one read of the state and constants per launch (the
+# written state is still in L2 when the launch ends).
 TRAFFIC_PER_LAUNCH = {
-    "pack_one_step": 319.73e6 + 145.29e6,
+    "pack_one_step": 336.42e6 + 147.24e6,
+    "pack_steps": 39.28e6,
 }
 
 
@@ -382,7 +387,7 @@ def main():
     roof = {"bound": "alu", "kernel": dname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
             "traffic": TRAFFIC_PER_LAUNCH.get(dname), "avg_launch_ms": avg_ms,
-            "peak_source": "FP64: 2 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal unit count; probe measured 1.975/clk)",
+            "peak_source": "FP64: 2 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal unit count; an FMA probe measured 1.91/clk)",
             "kernel_share": {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4)
                              for k, v in prof.items() if v[1]}}
 

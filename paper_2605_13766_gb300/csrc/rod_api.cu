@@ -1077,7 +1077,7 @@ rod_status rod_system_autotune(rod_system* s, double dt, int32_t trial_steps, in
   float best = 1e30f;
   int bc = before.cap_elems, bt = before.threads;
   const int caps[] = {192, 256, 320, 384, 448, 512, 640, 768};
-  const int thrs[] = {128, 256, 384, 512};
+  const int thrs[] = {128, 192, 256, 320, 384, 512};
   for (int cap : caps) {
     if (cap < std::min(s->max_n, kMaxCapElems)) continue;
     for (int thr : thrs) {

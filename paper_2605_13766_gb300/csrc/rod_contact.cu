@@ -227,7 +227,9 @@ __global__ void sort_cells_kernel(const int* __restrict__ start, int64_t ncell, 
 
 // Closest points of P(s) = p0 + s d1, R(u) = q0 + u d2 on [0,1]^2 (minimise |r + s d1 - u d2|^2,
 // r = p0 - q0): free minimiser s = (b f - c e)/(a e - b^2) clamped, u = (b s + f)/e; a clamped u
-// re-solves s.  Parallel segments start from s = 0.
+// re-solves s.  Parallel segments start from s = 0.  Quotients are taken as products with
+// correctly rounded reciprocals (one per denominator): an FP64 division costs about three
+// reciprocals on this part.
 __device__ __forceinline__ void closest(const double* p0, const double* p1, const double* q0, const double* q1,
                                         double& s, double& u) {
   double d1[3], d2[3], r[3];
@@ -247,25 +249,25 @@ __device__ __forceinline__ void closest(const double* p0, const double* p1, cons
   }
   if (a <= 0.0) {
     s = 0.0;
-    u = fmin(fmax(f / e, 0.0), 1.0);
+    u = fmin(fmax(f * __drcp_rn(e), 0.0), 1.0);
     return;
   }
   const double c = d1[0] * r[0] + d1[1] * r[1] + d1[2] * r[2];
   if (e <= 0.0) {
     u = 0.0;
-    s = fmin(fmax(-c / a, 0.0), 1.0);
+    s = fmin(fmax(-c * __drcp_rn(a), 0.0), 1.0);
     return;
   }
   const double b = d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2];
   const double den = a * e - b * b;
-  s = (den != 0.0) ? fmin(fmax((b * f - c * e) / den, 0.0), 1.0) : 0.0;
-  u = (b * s + f) / e;
+  s = (den != 0.0) ? fmin(fmax((b * f - c * e) * __drcp_rn(den), 0.0), 1.0) : 0.0;
+  u = (b * s + f) * __drcp_rn(e);
   if (u < 0.0) {
     u = 0.0;
-    s = fmin(fmax(-c / a, 0.0), 1.0);
+    s = fmin(fmax(-c * __drcp_rn(a), 0.0), 1.0);
   } else if (u > 1.0) {
     u = 1.0;
-    s = fmin(fmax((b - c) / a, 0.0), 1.0);
+    s = fmin(fmax((b - c) * __drcp_rn(a), 0.0), 1.0);
   }
 }
 
@@ -323,7 +325,7 @@ struct ContactArgs {
   int64_t N, E;
   int dim[3];
   double k, c;
-  double mu, vslip;
+  double mu, vslip, inv_vslip;
 };
 
 struct PairForce {
@@ -354,10 +356,13 @@ __device__ __noinline__ PairForce pair_force(const ContactArgs& A, int a, int ra
   double dvec[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) dvec[c] = (P0[c] + s * (P1[c] - P0[c])) - (Q0[c] + u * (Q1[c] - Q0[c]));
-  const double d = sqrt(dvec[0] * dvec[0] + dvec[1] * dvec[1] + dvec[2] * dvec[2]);
+  const double d2 = dvec[0] * dvec[0] + dvec[1] * dvec[1] + dvec[2] * dvec[2];
+  if (!(d2 > 0.0)) return out;
+  const double id = rsqrt(d2);              // 1 / d
+  const double d = d2 * id;
   const double delta = (rada + radb) - d;
-  if (!(delta > 0.0) || d == 0.0) return out;
-  const double nrm[3] = {dvec[0] / d, dvec[1] / d, dvec[2] / d};
+  if (!(delta > 0.0)) return out;
+  const double nrm[3] = {dvec[0] * id, dvec[1] * id, dvec[2] * id};
   double vrel = 0.0, vr[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -374,8 +379,9 @@ __device__ __noinline__ PairForce pair_force(const ContactArgs& A, int a, int ra
     double vt[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) vt[c] = vr[c] - vrel * nrm[c];
-    const double sp = sqrt(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
-    const double fr = -A.mu * fmag / fmax(sp, A.vslip);
+    // 1 / max(|v_t|, v_slip) = min(1 / |v_t|, 1 / v_slip)
+    const double sp2 = vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2];
+    const double fr = -A.mu * fmag * fmin(rsqrt(sp2), A.inv_vslip);
 #pragma unroll
     for (int c = 0; c < 3; ++c) ft[c] = fr * vt[c];
   }
@@ -792,6 +798,7 @@ ContactArgs make_args(const ContactState& cs, const double* x, const double* v, 
   A.c = cs.c;
   A.mu = cs.mu;
   A.vslip = cs.vslip;
+  A.inv_vslip = cs.vslip > 0.0 ? 1.0 / cs.vslip : INFINITY;
   A.err = err;
   return A;
 }

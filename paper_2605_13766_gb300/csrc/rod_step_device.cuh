@@ -90,15 +90,22 @@ __device__ __forceinline__ double asin_over_s(double s2) {
   return f;
 }
 
-// theta / sin(theta) of the relative rotation with sin^2 = s2, cos = c.  Warp-uniform cut of the
-// series like rot_coeffs (s2 < 2^-20: three terms, dropped < 4e-20; s2 < 2^-10: six terms,
-// dropped < 2e-20), used only when every lane's rotation is below 90 degrees (c > 0).
-__device__ __forceinline__ double theta_over_sin(double s2, double c) {
+// theta / sin(theta) of the relative rotation R = Q_{k+1} Q_k^T with sin^2 = s2, from the
+// diagonal products dd_a = d_a(k+1) . d_a(k) (cos theta = (dd1 + dd2 + dd3 - 1) / 2).  Warp-
+// uniform cut of the series like rot_coeffs (s2 < 2^-20: three terms, dropped < 4e-20; s2 <
+// 2^-10: six terms, dropped < 2e-20) when every lane's rotation is small.  With s2 < 2^-10 the
+// angle is below 1.8 deg or above 178.2 deg; above 178.2 deg, dd_a = cos t + (1 - cos t)(n . d_a)^2
+// < 2 (n . d_a)^2 - 0.9995 (n the axis), so dd1 and dd3 cannot both exceed 1/4 (that needs
+// (n . d1)^2 + (n . d3)^2 > 1.249), while below 1.8 deg both exceed cos t > 0.9995.  The test
+// reads their high words on the integer pipe; cos theta itself is formed only off the fast path.
+__device__ __forceinline__ double theta_over_sin(double s2, double dd1, double dd3, const double* qa,
+                                                 const double* qb) {
+  constexpr int kHiQuarter = 0x3FD00000;  // high word of 0.25
   const unsigned act = __activemask();
   const unsigned mx = __reduce_max_sync(act, hi_word(s2));
-  const bool acute = __all_sync(act, c > 0.0);
-  if (acute && mx < kHi2m20) return fma(fma(s2, 3.0 / 40.0, 1.0 / 6.0), s2, 1.0);
-  if (acute && mx < kHi2m10) {
+  const bool small = __all_sync(act, __double2hiint(dd1) > kHiQuarter && __double2hiint(dd3) > kHiQuarter);
+  if (small && mx < kHi2m20) return fma(fma(s2, 3.0 / 40.0, 1.0 / 6.0), s2, 1.0);
+  if (small && mx < kHi2m10) {
     double f = 63.0 / 2816.0;
     f = fma(f, s2, 35.0 / 1152.0);
     f = fma(f, s2, 5.0 / 112.0);
@@ -106,6 +113,8 @@ __device__ __forceinline__ double theta_over_sin(double s2, double c) {
     f = fma(f, s2, 1.0 / 6.0);
     return fma(f, s2, 1.0);
   }
+  const double dd2 = fma(qb[3], qa[3], fma(qb[4], qa[4], qb[5] * qa[5]));
+  const double c = 0.5 * ((dd1 + dd2 + dd3) - 1.0);
   if (s2 <= 0.0625 && c > 0.0) return asin_over_s(s2);
   const double sn = sqrt(s2);
   return (sn > 0.0) ? atan2(sn, c) / sn : 1.0;
@@ -265,16 +274,22 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
     double Ql[3], sg[3], n[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) Ql[a] = fma(q[3 * a], l[0], fma(q[3 * a + 1], l[1], q[3 * a + 2] * l[2]));
-    sg[0] = Ql[0] * irl;
-    sg[1] = Ql[1] * irl;
-    sg[2] = fma(Ql[2], irl, -1.0);
+    // n / e = S sigma / e  (the 1/e of the internal force, folded once)
     if (P.rest_sigma) {
+      sg[0] = Ql[0] * irl;
+      sg[1] = Ql[1] * irl;
+      sg[2] = fma(Ql[2], irl, -1.0);
 #pragma unroll
       for (int c = 0; c < 3; ++c) sg[c] -= __ldg(P.rest_sigma + c * P.E + ge);
-    }
-    // n / e = S sigma / e  (the 1/e of the internal force, folded once)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) n[c] = (__ldg(&rc->S[c]) * ie) * sg[c];
+      for (int c = 0; c < 3; ++c) n[c] = (__ldg(&rc->S[c]) * ie) * sg[c];
+    } else {
+      // sigma / e = (Q l / rl - e3) rl / ell = Q l / ell - e3 rl / ell
+      const double s2 = __ldg(&rc->S[2]);
+      n[0] = (__ldg(&rc->S[0]) * rs) * Ql[0];
+      n[1] = (__ldg(&rc->S[1]) * rs) * Ql[1];
+      n[2] = fma(s2 * rs, Ql[2], -s2 * ie);
+    }
     // lab internal force N = Q^T n / e
 #pragma unroll
     for (int b = 0; b < 3; ++b) m.NF[b * m.CE + i] = fma(q[b], n[0], fma(q[3 + b], n[1], q[6 + b] * n[2]));
@@ -283,21 +298,20 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
     tc[0] = fma(Ql[1], n[2], -Ql[2] * n[1]);
     tc[1] = fma(Ql[2], n[0], -Ql[0] * n[2]);
     tc[2] = fma(Ql[0], n[1], -Ql[1] * n[0]);
-    // transport couples (J w / e) x w + (J w / e^2) de/dt,  de/dt = (l . dv) / (ell rl)
+    // transport couples (J w / e) x w + (J w / e^2) de/dt,  de/dt = (l . dv) / (ell rl), and the
+    // rotational damping -nu rl (I/A) w; with J w = rl g, g = rho I w:
+    //   rl/e (g x w) + rl (de/dt / e^2 - damp_rot) g
     const double edot = fma(l[0], dv[0], fma(l[1], dv[1], l[2] * dv[2])) * rs * irl;
-    double Jw[3], Jwe[3];
+    double gw[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      Jw[c] = __ldg(&rc->rhoI[c]) * rl * w[c];
-      Jwe[c] = Jw[c] * ie;
-    }
-    const double k2 = ie * ie * edot;
-    const double drot = __ldg(&rc->damp_rot);
-    tc[0] += fma(Jwe[1], w[2], -Jwe[2] * w[1]);
-    tc[1] += fma(Jwe[2], w[0], -Jwe[0] * w[2]);
-    tc[2] += fma(Jwe[0], w[1], -Jwe[1] * w[0]);
+    for (int c = 0; c < 3; ++c) gw[c] = __ldg(&rc->rhoI[c]) * w[c];
+    const double k1 = rl * ie;
+    const double k2 = rl * fma(ie * ie, edot, -__ldg(&rc->damp_rot));
+    tc[0] = fma(k1, fma(gw[1], w[2], -gw[2] * w[1]), tc[0]);
+    tc[1] = fma(k1, fma(gw[2], w[0], -gw[0] * w[2]), tc[1]);
+    tc[2] = fma(k1, fma(gw[0], w[1], -gw[1] * w[0]), tc[2]);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) tc[c] = fma(Jw[c], k2 - drot, tc[c]);
+    for (int c = 0; c < 3; ++c) tc[c] = fma(k2, gw[c], tc[c]);
     if (P.elem_couple) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) tc[c] += __ldg(P.elem_couple + c * P.E + ge);
@@ -363,12 +377,10 @@ __device__ __forceinline__ void stage_voronoi(const StepParams& P, const Pack& p
     u2 = fma(-qb[0], qa[3], u2);
     u2 = fma(-qb[1], qa[4], u2);
     u2 = fma(-qb[2], qa[5], u2);
-    double tr = qb[0] * qa[0];
-#pragma unroll
-    for (int a = 1; a < 9; ++a) tr = fma(qb[a], qa[a], tr);
     const double s2 = 0.25 * fma(u0, u0, fma(u1, u1, u2 * u2));  // |w|^2 = sin^2(theta)
-    const double c = 0.5 * (tr - 1.0);                             // cos(theta)
-    const double f = theta_over_sin(s2, c);
+    const double dd1 = fma(qb[0], qa[0], fma(qb[1], qa[1], qb[2] * qa[2]));
+    const double dd3 = fma(qb[6], qa[6], fma(qb[7], qa[7], qb[8] * qa[8]));
+    const double f = theta_over_sin(s2, dd1, dd3, qa, qb);
     const double i2D = __ldg(P.inv_2D + gv);
     const double kf = -f * i2D;             // kappa = -(theta/s) w / D = -f u / (2D)
     double kap[3] = {kf * u0, kf * u1, kf * u2};
@@ -453,25 +465,28 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
     const double im = m.IM[j];
     const double dl = __ldg(&rc->damp_lin);
     double F[3];
+    if (P.fseg) {
+      // contact: node a of segment iR and node b of segment iR-1, folded into the difference
+      const int ge = pk.elem0 + iR;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const double Nr = hasR ? m.NF[c * m.CE + iR] : 0.0;
-      const double Nl = hasL ? m.NF[c * m.CE + iR - 1] : 0.0;
-      F[c] = Nr - Nl;
+      for (int c = 0; c < 3; ++c) {
+        const double Nr = hasR ? m.NF[c * m.CE + iR] : 0.0;
+        const double Nl = hasL ? m.NF[c * m.CE + iR - 1] : 0.0;
+        const double fa = hasR ? __ldg(P.fseg + c * P.E + ge) : 0.0;
+        const double fb = hasL ? __ldg(P.fseg + (3 + c) * P.E + ge - 1) : 0.0;
+        F[c] = (Nr + fa) - (Nl - fb);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double Nr = hasR ? m.NF[c * m.CE + iR] : 0.0;
+        const double Nl = hasL ? m.NF[c * m.CE + iR - 1] : 0.0;
+        F[c] = Nr - Nl;
+      }
     }
     if (lj == nr) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) F[c] += __ldg(&rc->tip[c]);
-    }
-    if (P.fseg) {
-      const int ge = pk.elem0 + iR;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        double fc = 0.0;
-        if (hasR) fc += __ldg(P.fseg + c * P.E + ge);              // node a of segment iR
-        if (hasL) fc += __ldg(P.fseg + (3 + c) * P.E + ge - 1);    // node b of segment iR-1
-        F[c] += fc;
-      }
     }
     for (int k = 0; k < P.n_walls; ++k) {
       // node sphere (radius of the rod) against the half-space n . (x - p - u t) >= 0

@@ -205,7 +205,7 @@ def _e2e(s, p, dt, K, world, dist, barrier):
     t0 = time.perf_counter()
     s.set_state(*[a.numpy() for a in pin])
     s.step(K, dt)
-    xs = s.get_state()
+    xs = s.get_state(out=[o.numpy() for o in outs])
     t_e2e = slowest(time.perf_counter() - t0)
     state_bytes = 8 * (6 * p.n_nodes + 12 * p.n_elems)
     e2e = {"value": total(p.n_elems * K) / t_e2e, "unit": UNIT, "h2d_bytes_per_step": state_bytes / K,

@@ -112,9 +112,12 @@ rod_status rod_system_destroy(rod_system* sys);
 rod_status rod_system_sizes(const rod_system* sys, int64_t* n_nodes, int64_t* n_elems, int64_t* n_voronoi);
 
 /* Set the state: x, v [3*N], Q [9*E], w [3*E] in the layout above.  on_device = 0: host
- * pointers, copied synchronously; on_device = 1: device pointers, copied on the system's
- * stream (the caller keeps them valid until the stream reaches the copy).  Records the clamp
- * values, resets the simulated time to 0 and clears the device error word. */
+ * pointers, copied synchronously and checked for NaN/Inf on the device after the copy (such a
+ * state is rejected with ROD_ERR_ARG and the system then holds no state until the next
+ * successful call); on_device = 1: device pointers, copied on the system's stream (the caller
+ * keeps them valid until the stream reaches the copy; non-finite values surface as
+ * ROD_ERR_NONFINITE from the next step).  Records the clamp values, resets the simulated time
+ * to 0 and clears the device error word. */
 rod_status rod_system_set_state(rod_system* sys, const double* x, const double* v, const double* Q,
                                 const double* w, int on_device);
 

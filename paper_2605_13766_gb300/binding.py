@@ -280,8 +280,22 @@ class RodSystem:
         _check(self.lib.rod_system_set_state(self.handle, *[_ptr(a) for a in arrs], 1 if on_dev else 0))
         self._keep_state_inputs = arrs  # alive until the stream has copied them
 
-    def get_state(self, device: bool = False):
-        if device:
+    def get_state(self, device: bool = False, out=None):
+        """The state (x, v, Q, w).  out: four caller arrays to fill (host numpy, pinned or not,
+        or CUDA float64 tensors when device=True) instead of new ones."""
+        if out is not None:
+            out = list(out)
+            if device:
+                import torch
+                for a in out:
+                    if a.dtype != torch.float64 or not a.is_cuda or not a.is_contiguous():
+                        raise TypeError("device outputs must be contiguous float64 CUDA tensors")
+            else:
+                for a in out:
+                    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+                        raise TypeError("host outputs must be C-contiguous float64 numpy arrays")
+            self._check_shapes(out)
+        elif device:
             import torch
             out = [torch.empty((3, self.n_nodes), dtype=torch.float64, device="cuda"),
                    torch.empty((3, self.n_nodes), dtype=torch.float64, device="cuda"),

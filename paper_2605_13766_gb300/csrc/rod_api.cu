@@ -151,6 +151,15 @@ __global__ void gather_clamp_kernel(const double* x, const double* Q, const RodC
   for (int a = 0; a < 9; ++a) cQ[a * R + r] = Q[a * E + i];
 }
 
+// Non-finite values of a state array: the largest exponent field (all ones: Inf or NaN) on the
+// integer pipe, one atomic per warp that saw one.
+__global__ void nonfinite_kernel(const double* __restrict__ a, int64_t n, int* err) {
+  unsigned mx = 0u;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    mx = max(mx, static_cast<unsigned>(__double2hiint(a[i])) & 0x7FF00000u);
+  if (__any_sync(0xffffffffu, mx == 0x7FF00000u) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_NONFINITE);
+}
+
 }  // namespace
 
 struct rod_system {
@@ -802,14 +811,32 @@ rod_status rod_system_set_state(rod_system* s, const double* x, const double* v,
                                 int on_device) {
   if (!s || !x || !v || !Q || !w) return fail(ROD_ERR_ARG, "null argument");
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if (!on_device) {
-    if (!finite_all(x, 3 * s->N) || !finite_all(v, 3 * s->N) || !finite_all(Q, 9 * s->E) || !finite_all(w, 3 * s->E))
-      return fail(ROD_ERR_ARG, "the state holds non-finite values");
-  }
   CUDA_TRY(cudaMemcpyAsync(s->x.p, x, 3 * s->N * sizeof(double), kind, s->stream));
   CUDA_TRY(cudaMemcpyAsync(s->v.p, v, 3 * s->N * sizeof(double), kind, s->stream));
   CUDA_TRY(cudaMemcpyAsync(s->Q.p, Q, 9 * s->E * sizeof(double), kind, s->stream));
   CUDA_TRY(cudaMemcpyAsync(s->w.p, w, 3 * s->E * sizeof(double), kind, s->stream));
+  if (!on_device) {
+    // host input: checked for non-finite values on the device after the copy (the copy of a
+    // host state has to synchronise anyway); a rejected state leaves the system without one
+    CUDA_TRY(cudaMemsetAsync(s->err.p, 0, sizeof(int), s->stream));
+    const struct { const double* p; int64_t n; } arr[4] = {{s->x.p, 3 * s->N}, {s->v.p, 3 * s->N},
+                                                           {s->Q.p, 9 * s->E}, {s->w.p, 3 * s->E}};
+    for (const auto& a : arr) {
+      const int64_t blocks = std::min<int64_t>((a.n + 255) / 256, 4096);
+      s->hook.before(K_MISC, s->stream);
+      nonfinite_kernel<<<static_cast<unsigned>(std::max<int64_t>(blocks, 1)), 256, 0, s->stream>>>(a.p, a.n, s->err.p);
+      s->hook.after(K_MISC, s->stream);
+    }
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(s->err_host, s->err.p, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (*s->err_host != 0) {
+      s->state_set = false;
+      CUDA_TRY(cudaMemsetAsync(s->err.p, 0, sizeof(int), s->stream));
+      CUDA_TRY(cudaStreamSynchronize(s->stream));
+      return fail(ROD_ERR_ARG, "the state holds non-finite values");
+    }
+  }
   s->hook.before(K_MISC, s->stream);
   gather_clamp_kernel<<<(s->R + 127) / 128, 128, 0, s->stream>>>(s->x.p, s->Q.p, s->rods.p, s->R, s->N, s->E,
                                                                   s->clamp_x.p, s->clamp_Q.p);

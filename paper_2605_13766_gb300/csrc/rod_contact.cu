@@ -539,18 +539,24 @@ __global__ void __launch_bounds__(256) list_force_kernel(ContactArgs A) {
   if (n <= kNbrCap) {
     if (n > 0) {
       const float4 ga = A.seg_prox[2 * a], ea = A.seg_prox[2 * a + 1];
-      // the next candidate's index and proxy are loaded while the current one is tested
-      int b = A.nbr[a];
-      float4 gb = A.seg_prox[2 * (int64_t)b], eb = A.seg_prox[2 * (int64_t)b + 1];
-      for (int k = 0; k < n; ++k) {
-        const int bc = b;
-        const float4 gc = gb, ec = eb;
-        if (k + 1 < n) {
-          b = A.nbr[(k + 1) * A.E + a];
-          gb = A.seg_prox[2 * (int64_t)b];
-          eb = A.seg_prox[2 * (int64_t)b + 1];
+      // candidates in groups of four: all indices, then all proxies, then the tests in list
+      // order (four independent loads in flight instead of a chain of dependent ones)
+      constexpr int kG = 4;
+      for (int k0 = 0; k0 < n; k0 += kG) {
+        int bs[kG];
+        float4 gb[kG], eb[kG];
+#pragma unroll
+        for (int t = 0; t < kG; ++t) bs[t] = (k0 + t < n) ? A.nbr[(k0 + t) * A.E + a] : -1;
+#pragma unroll
+        for (int t = 0; t < kG; ++t) {
+          if (bs[t] >= 0) {
+            gb[t] = A.seg_prox[2 * (int64_t)bs[t]];
+            eb[t] = A.seg_prox[2 * (int64_t)bs[t] + 1];
+          }
         }
-        if (may_touch(ga, gc, ea, ec, ea.w + ec.w)) f(bc, A.seg_rod[bc]);
+#pragma unroll
+        for (int t = 0; t < kG; ++t)
+          if (bs[t] >= 0 && may_touch(ga, gb[t], ea, eb[t], ea.w + eb[t].w)) f(bs[t], A.seg_rod[bs[t]]);
       }
     }
   } else {

@@ -26,8 +26,10 @@ struct ListCtl {
 constexpr int kListRebuildKernels = 10;
 
 // Capacity of one segment's candidate list; a segment with more candidates scans its
-// neighbourhood of the last build instead.
-constexpr int kNbrCap = 16;
+// neighbourhood of the last build instead.  Thick rods cut into short segments give a touching
+// segment many candidates (two parallel rods of radius r and element length l: about
+// 2 sqrt((2r + skin)^2 - (2r)^2) / l on each neighbour), hence room for 32.
+constexpr int kNbrCap = 32;
 
 struct ContactState {
   bool enabled = false;

@@ -232,8 +232,23 @@ def test_nonfinite_state_is_reported_and_cleared():
     assert ei.value.status == -3
     s.set_state(*p.state())
     s.step(10, 1e-5)
-    with pytest.raises(RodError):
-        s.set_state(p.x * np.nan, p.v, p.Q, p.w)
+    # a host state with NaN/Inf is rejected (checked on the device after the copy) and leaves
+    # the system without a state until the next good one
+    for bad in ("x", "Q", "w"):
+        arrs = dict(x=p.x, v=p.v, Q=p.Q, w=p.w)
+        arrs[bad] = arrs[bad].copy()
+        arrs[bad].flat[7] = np.inf if bad == "Q" else np.nan
+        with pytest.raises(RodError) as ei:
+            s.set_state(arrs["x"], arrs["v"], arrs["Q"], arrs["w"])
+        assert ei.value.status == -1
+        with pytest.raises(RodError) as ei:
+            s.step(1, 1e-5)
+        assert ei.value.status == -6
+    s.set_state(*p.state())
+    s.step(10, 1e-5)
+    out = [np.full(a.shape, np.nan) for a in p.state()]
+    got = s.get_state(out=out)
+    assert all(g is o for g, o in zip(got, out)) and np.isfinite(out[0]).all()
 
 
 def test_invalid_descriptions_are_rejected():

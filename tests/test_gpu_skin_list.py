@@ -82,8 +82,8 @@ def test_skin_list_equals_the_direct_search(skin):
 def _bundle(n_side=3, gap=2e-4, rest_len=1e-3, radius=5e-3, n=24, tilt=0.02):
     """Rods on a square lattice at centre distance 2 r + gap, each tilted from the common axis by
     `tilt` in a random direction (exactly parallel segments have no unique closest points, and
-    rounding would pick the force split), with elements much shorter than the radius: a segment
-    has more than the list's 16 candidates within 2 r + skin."""
+    rounding would pick the force split), with elements much shorter than the radius: with a
+    3 mm skin a segment has more than the list's 32 candidates within 2 r + skin."""
     from rodgen import _straight_rods
     rng = np.random.default_rng(3)
     R = n_side * n_side
@@ -110,10 +110,10 @@ def _bundle(n_side=3, gap=2e-4, rest_len=1e-3, radius=5e-3, n=24, tilt=0.02):
 
 
 def test_overflowing_lists_scan_their_neighbourhood():
-    skin = 1e-3
+    skin = 3e-3
     p = _bundle()
     # brute force on the CPU: some segment has more other-rod segments within 2 r + skin than a
-    # list holds (16), so the overflow scan runs
+    # list holds (32), so the overflow scan runs
     off = p.node_offsets()
     rod = np.repeat(np.arange(p.n_rods), p.n_elem)
     nodes = np.concatenate([np.arange(off[r], off[r + 1] - 1) for r in range(p.n_rods)])
@@ -121,7 +121,7 @@ def test_overflowing_lists_scan_their_neighbourhood():
     d = np.linalg.norm(mid[:, :, None] - mid[:, None, :], axis=0)
     # segment distance <= midpoint distance: these pairs are all list candidates
     near = (d < 2 * 5e-3 + skin) & (rod[:, None] != rod[None, :])
-    assert near.sum(1).max() > 16
+    assert near.sum(1).max() > 32
     o = Oracle(p)
     assert np.abs(o.contact_forces(p.x, p.v)).max() > 0.5
     ref = o.step(*p.state(), dt=2e-6, n_steps=200)

@@ -17,7 +17,6 @@ same workload on the host cores.
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
 import subprocess
@@ -65,26 +64,7 @@ TRAFFIC_PER_LAUNCH = {
 def _workload(name: str, rank: int):
     seed = 1234
     if name == "packing":
-        cache_dir = os.path.join(tempfile.gettempdir(), "rodbench_cache")
-        os.makedirs(cache_dir, exist_ok=True)
-        key = hashlib.sha1(f"random_packing-default-{seed}-v2".encode()).hexdigest()[:12]
-        path = os.path.join(cache_dir, f"packing_{key}.npz")
-        p = None
-        if os.path.exists(path):
-            try:
-                z = np.load(path)
-                base = rodgen.random_packing(n_rods=10, seed=seed)  # cheap template for the fields
-                p = base.replace(n_elem=z["n_elem"], rest_len=z["rest_len"], radius=z["radius"], youngs=z["youngs"],
-                                 shear_mod=z["shear_mod"], density=z["density"], x=z["x"], v=z["v"], Q=z["Q"],
-                                 w=z["w"], name="random_packing_10000")
-            except Exception:
-                p = None
-        if p is None:
-            p = rodgen.random_packing(seed=seed)
-            tmp = path + f".{os.getpid()}.npz"
-            np.savez(tmp, n_elem=p.n_elem, rest_len=p.rest_len, radius=p.radius, youngs=p.youngs,
-                     shear_mod=p.shear_mod, density=p.density, x=p.x, v=p.v, Q=p.Q, w=p.w)
-            os.replace(tmp, path)
+        p = rodgen.random_packing_cached(seed=seed)
         desc = {"workload": "random packing, 10^4 rods, n~U{16..256} (seeded), contact k=1e4 c=10, gravity, dt=5e-6",
                 "rods": p.n_rods, "elements": p.n_elems, "dt": 5e-6}
         return p, 5e-6, desc

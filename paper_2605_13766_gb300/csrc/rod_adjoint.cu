@@ -255,14 +255,14 @@ __global__ void __launch_bounds__(256) adjoint_kernel(AdjointParams A, LaunchSha
     for (int c = 0; c < 3; ++c) {
       const double wb = held ? 0.0 : a.WB[c * m.CE + i];
       const double alpha_b = dt * wb;
-      const double jinv = m.IRL[i] * rc->inv_rhoI[c];
+      const double jinv = P.inv_rl[pk.elem0 + i] * rc->inv_rhoI[c];
       const double taub = m.EDIL[i] * jinv * alpha_b;
       ebar += jinv * tau[c] * alpha_b;
       a.TAUB[c * m.CE + i] = taub;
       a.WB[c * m.CE + i] = wb;                       // now: adjoint of w (through w' = w + dt alpha)
       A.g_couple[c * P.E + pk.elem0 + i] += taub;    // tau contains C directly
     }
-    a.LBL[i] = ebar * m.IRL[i];                      // e = ell / rl
+    a.LBL[i] = ebar * P.inv_rl[pk.elem0 + i];                      // e = ell / rl
   }
   for (int j = threadIdx.x; j < Np; j += blockDim.x) {
     const int r = m.nrod[j];
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(AdjointParams A, LaunchSha
     for (int c = 0; c < 3; ++c) {
       const double vb = held ? 0.0 : a.VB[c * m.CN + j];
       const double abar = dt * vb;
-      a.FB[c * m.CN + j] = abar * m.IM[j];
+      a.FB[c * m.CN + j] = abar * P.inv_m[pk.node0 + j];
       a.VB[c * m.CN + j] = vb - rc->damp_lin * abar;   // adjoint of v (rate update + damping)
     }
     // walls: F = fn n + fr vt with fn = k delta - c (v - u).n, delta = r - n.(xh - p - u t),
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(AdjointParams A, LaunchSha
     for (int k = 0; k < 9; ++k) q[k] = a.QH[k * m.CE + i];
     const double ll = l[0] * l[0] + l[1] * l[1] + l[2] * l[2];
     const double rs = rsqrt(ll);
-    const double irl = m.IRL[i];
+    const double irl = P.inv_rl[pk.elem0 + i];
     const double rl = P.rest_len[ge];
     const double ie = rl * rs;
     double Ql[3], sg[3], n[3];

@@ -287,12 +287,21 @@ rod_status build_packs(rod_system* s, const LaunchShape& shape) {
   return ROD_OK;
 }
 
+// Rods per pack: as many of the shortest rods as the element capacity holds (at most 64), so
+// the node arrays of a pack reserve no room a real pack cannot use.
+int rods_per_pack(const rod_system* s, int cap_elems) {
+  int min_n = 1 << 30;
+  for (const auto& r : s->rods_h) min_n = std::min(min_n, r.n);
+  if (s->rods_h.empty()) min_n = 1;
+  return std::max(1, std::min(64, (cap_elems + min_n - 1) / min_n));
+}
+
 LaunchShape default_shape(const rod_system* s) {
   LaunchShape sh;
   int cap = 384;
   while (cap < s->max_n) cap += 128;
   sh.cap_elems = std::min(cap, kMaxCapElems);
-  sh.cap_rods = std::max(8, std::min(64, sh.cap_elems / 4));
+  sh.cap_rods = rods_per_pack(s, sh.cap_elems);
   sh.threads = sh.cap_elems >= 512 ? 512 : 256;
   return sh;
 }
@@ -1021,7 +1030,7 @@ rod_status rod_system_set_launch(rod_system* s, int32_t elems_per_block, int32_t
     if (elems_per_block > kMaxCapElems || elems_per_block % 32)
       return fail(ROD_ERR_ARG, "elems_per_block must be a multiple of 32 and <= %d", kMaxCapElems);
     sh.cap_elems = elems_per_block;
-    sh.cap_rods = std::max(8, std::min(64, sh.cap_elems / 4));
+    sh.cap_rods = rods_per_pack(s, sh.cap_elems);
   }
   if (threads_per_block > 0) {
     if (threads_per_block > 512 || threads_per_block % 32)
@@ -1103,8 +1112,8 @@ rod_status rod_system_autotune(rod_system* s, double dt, int32_t trial_steps, in
   CUDA_TRY(cudaEventCreate(&e1));
   float best = 1e30f;
   int bc = before.cap_elems, bt = before.threads;
-  const int caps[] = {192, 256, 320, 384, 448, 512, 640, 768};
-  const int thrs[] = {128, 192, 256, 320, 384, 512};
+  const int caps[] = {192, 224, 256, 288, 320, 384, 448, 512, 640, 768};
+  const int thrs[] = {128, 160, 192, 224, 256, 320, 384, 512};
   for (int cap : caps) {
     if (cap < std::min(s->max_n, kMaxCapElems)) continue;
     for (int thr : thrs) {

@@ -33,15 +33,13 @@
 #include <vector>
 
 #include "rod_contact.h"
+#include "rod_contact_device.cuh"
 
 namespace rod {
 
 namespace {
 
 constexpr int64_t kMaxCells = int64_t(1) << 24;
-// Largest number of segments one cell may hold; a denser cell (a collapsed or escaped
-// configuration) latches ERR_OVERFLOW instead of running a quadratic search.
-constexpr int kCellCap = 512;
 constexpr int kScanThreads = 1024;
 constexpr int kScanPerThread = 4;
 constexpr int kScanTile = kScanThreads * kScanPerThread;
@@ -225,52 +223,6 @@ __global__ void sort_cells_kernel(const int* __restrict__ start, int64_t ncell, 
   }
 }
 
-// Closest points of P(s) = p0 + s d1, R(u) = q0 + u d2 on [0,1]^2 (minimise |r + s d1 - u d2|^2,
-// r = p0 - q0): free minimiser s = (b f - c e)/(a e - b^2) clamped, u = (b s + f)/e; a clamped u
-// re-solves s.  Parallel segments start from s = 0.  Quotients are taken as products with
-// correctly rounded reciprocals (one per denominator): an FP64 division costs about three
-// reciprocals on this part.
-__device__ __forceinline__ void closest(const double* p0, const double* p1, const double* q0, const double* q1,
-                                        double& s, double& u) {
-  double d1[3], d2[3], r[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    d1[c] = p1[c] - p0[c];
-    d2[c] = q1[c] - q0[c];
-    r[c] = p0[c] - q0[c];
-  }
-  const double a = d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2];
-  const double e = d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2];
-  const double f = d2[0] * r[0] + d2[1] * r[1] + d2[2] * r[2];
-  if (a <= 0.0 && e <= 0.0) {
-    s = 0.0;
-    u = 0.0;
-    return;
-  }
-  if (a <= 0.0) {
-    s = 0.0;
-    u = fmin(fmax(f * __drcp_rn(e), 0.0), 1.0);
-    return;
-  }
-  const double c = d1[0] * r[0] + d1[1] * r[1] + d1[2] * r[2];
-  if (e <= 0.0) {
-    u = 0.0;
-    s = fmin(fmax(-c * __drcp_rn(a), 0.0), 1.0);
-    return;
-  }
-  const double b = d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2];
-  const double den = a * e - b * b;
-  s = (den != 0.0) ? fmin(fmax((b * f - c * e) * __drcp_rn(den), 0.0), 1.0) : 0.0;
-  u = (b * s + f) * __drcp_rn(e);
-  if (u < 0.0) {
-    u = 0.0;
-    s = fmin(fmax(-c * __drcp_rn(a), 0.0), 1.0);
-  } else if (u > 1.0) {
-    u = 1.0;
-    s = fmin(fmax((b - c) * __drcp_rn(a), 0.0), 1.0);
-  }
-}
-
 // Per-slot records in cell order, so that the narrow phase reads each candidate with
 // contiguous 16-byte loads: (FP32 midpoint, FP32 half length), (segment, rod, FP32 radius, end
 // of the rod's run) and, for candidates that pass the first bound, (FP32 half edge).  A cell
@@ -301,195 +253,6 @@ __global__ void records_kernel(const int* __restrict__ sorted, const int* __rest
     if (slot_of) slot_of[a] = (int)q;
   }
 }
-
-struct ContactArgs {
-  const double* x;
-  const double* v;
-  const int* seg_rod;
-  const int* seg_cell;
-  const int* cell_start;
-  const int* sorted;
-  const float4* prox;
-  const float4* recA;
-  const int4* recB;
-  const float4* recC;
-  const int* gate;
-  int* nbr;
-  int* nbr_count;
-  const int* slot_of;
-  const float4* seg_prox;
-  float skin;
-  const RodConst* rods;
-  double* fseg;
-  int* err;
-  int64_t N, E;
-  int dim[3];
-  double k, c;
-  double mu, vslip, inv_vslip;
-};
-
-struct PairForce {
-  double fa[3], fb[3];
-  bool hit;
-};
-
-// FP64 evaluation of one candidate pair (a, b) in canonical order (lower index first); returns
-// the contributions to the two nodes of segment a.  Kept out of line: it runs only for the
-// few candidates that survive the FP32 cull, and the scan loop stays small.
-__device__ __noinline__ PairForce pair_force(const ContactArgs& A, int a, int ra, int b, int rb) {
-  PairForce out;
-  out.hit = false;
-  const double rada = A.rods[ra].radius, radb = A.rods[rb].radius;
-  const bool first = a < b;
-  const int64_t na = a + ra, nb = b + rb;
-  const int64_t nP = first ? na : nb, nQ = first ? nb : na;
-  double P0[3], P1[3], Q0[3], Q1[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    P0[c] = A.x[c * A.N + nP];
-    P1[c] = A.x[c * A.N + nP + 1];
-    Q0[c] = A.x[c * A.N + nQ];
-    Q1[c] = A.x[c * A.N + nQ + 1];
-  }
-  double s, u;
-  closest(P0, P1, Q0, Q1, s, u);
-  double dvec[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) dvec[c] = (P0[c] + s * (P1[c] - P0[c])) - (Q0[c] + u * (Q1[c] - Q0[c]));
-  const double d2 = dvec[0] * dvec[0] + dvec[1] * dvec[1] + dvec[2] * dvec[2];
-  if (!(d2 > 0.0)) return out;
-  const double id = rsqrt(d2);              // 1 / d
-  const double d = d2 * id;
-  const double delta = (rada + radb) - d;
-  if (!(delta > 0.0)) return out;
-  const double nrm[3] = {dvec[0] * id, dvec[1] * id, dvec[2] * id};
-  double vrel = 0.0, vr[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const double vp0 = A.v[c * A.N + nP], vp1 = A.v[c * A.N + nP + 1];
-    const double vq0 = A.v[c * A.N + nQ], vq1 = A.v[c * A.N + nQ + 1];
-    vr[c] = ((1.0 - s) * vp0 + s * vp1) - ((1.0 - u) * vq0 + u * vq1);
-    vrel += vr[c] * nrm[c];
-  }
-  double fmag = A.k * delta - A.c * vrel;
-  if (fmag < 0.0) fmag = 0.0;
-  // friction: -mu fmag v_t / max(|v_t|, v_slip) with v_t the tangential relative velocity
-  double ft[3] = {0.0, 0.0, 0.0};
-  if (A.mu > 0.0 && fmag > 0.0) {
-    double vt[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) vt[c] = vr[c] - vrel * nrm[c];
-    // 1 / max(|v_t|, v_slip) = min(1 / |v_t|, 1 / v_slip)
-    const double sp2 = vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2];
-    const double fr = -A.mu * fmag * fmin(rsqrt(sp2), A.inv_vslip);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) ft[c] = fr * vt[c];
-  }
-  // force on the first segment of the pair is +(fmag n + ft), on the second the opposite
-  const double wa = first ? (1.0 - s) : -(1.0 - u);
-  const double wb = first ? s : -u;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const double fc = fmag * nrm[c] + ft[c];
-    out.fa[c] = wa * fc;
-    out.fb[c] = wb * fc;
-  }
-  out.hit = true;
-  return out;
-}
-
-// FP32 lower bounds of the distance of segments a and b (midpoints m, half lengths h, half
-// edges e) against touch = r_a + r_b + extra + tol, tol covering the rounding of the FP32
-// inputs and of these expressions: false when the pair is certainly farther apart.
-__device__ __forceinline__ bool may_touch(float4 ga, float4 gb, float4 ea, float4 eb, float touch_base) {
-  const float ddx = ga.x - gb.x, ddy = ga.y - gb.y, ddz = ga.z - gb.z;
-  const float dm2 = ddx * ddx + ddy * ddy + ddz * ddz;
-  const float ma_inf = fmaxf(fabsf(ga.x), fmaxf(fabsf(ga.y), fabsf(ga.z)));
-  const float mb_inf = fmaxf(fabsf(gb.x), fmaxf(fabsf(gb.y), fabsf(gb.z)));
-  const float touch = touch_base + 1e-6f + 4e-6f * (ma_inf + mb_inf + ga.w + gb.w);
-  const float reach = touch + ga.w + gb.w;
-  if (dm2 > reach * reach) return false;
-  // separating axis along m_a - m_b: |dm| - (|e_a . dm| + |e_b . dm|) / |dm| > touch
-  const float pa = fabsf(ea.x * ddx + ea.y * ddy + ea.z * ddz);
-  const float pb = fabsf(eb.x * ddx + eb.y * ddy + eb.z * ddz);
-  return !(dm2 > 0.f && dm2 - (pa + pb) > touch * sqrtf(dm2));
-}
-
-// Calls visit(b, rb) for every segment b of another rod in the 27-cell neighbourhood of slot q
-// (cell-ordered records) that may come within r_a + r_b + extra of the slot's segment, in list
-// order.  The three cells of each (y, z) row are consecutive in the list and scanned as one
-// range; the next candidate's records are loaded while the current one is tested.
-template <class Visit>
-__device__ __forceinline__ void scan_neighbourhood(const ContactArgs& A, int64_t q, float extra, Visit& visit) {
-  const float4 ga = A.recA[q];
-  const int4 ba = A.recB[q];
-  const float4 ea = A.recC[q];
-  const int ra = ba.y;
-  const float rada = __int_as_float(ba.z);
-  const int cell = A.seg_cell[ba.x];
-  const int cx = cell % A.dim[0], cy = (cell / A.dim[0]) % A.dim[1], cz = cell / (A.dim[0] * A.dim[1]);
-  const int x0 = max(cx - 1, 0), x1 = min(cx + 1, A.dim[0] - 1);
-  for (int dz = -1; dz <= 1; ++dz) {
-    const int z = cz + dz;
-    if (z < 0 || z >= A.dim[2]) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int y = cy + dy;
-      if (y < 0 || y >= A.dim[1]) continue;
-      const int row = (z * A.dim[1] + y) * A.dim[0];
-      const int b0 = A.cell_start[row + x0], b1 = A.cell_start[row + x1 + 1];
-      if (b1 - b0 > 3 * kCellCap) {
-        atomicOr(A.err, ERR_OVERFLOW);
-        continue;
-      }
-      int4 bb_next = make_int4(0, 0, 0, 0);
-      float4 gb_next = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (b0 < b1) {
-        bb_next = A.recB[b0];
-        gb_next = A.recA[b0];
-      }
-      for (int t = b0; t < b1;) {
-        const int tc = t;
-        const int4 bb = bb_next;
-        const float4 gb = gb_next;
-        t = (bb.y == ra) ? bb.w : t + 1;  // own rod: skip its run in this cell
-        if (t < b1) {
-          bb_next = A.recB[t];
-          gb_next = A.recA[t];
-        }
-        if (bb.y == ra) continue;
-        if (!may_touch(ga, gb, ea, A.recC[tc], rada + __int_as_float(bb.z) + extra)) continue;
-        visit(bb.x, bb.y);
-      }
-    }
-  }
-}
-
-struct ForceSum {
-  const ContactArgs& A;
-  int a, ra;
-  double fa[3], fb[3];
-  __device__ ForceSum(const ContactArgs& args, int a_, int ra_) : A(args), a(a_), ra(ra_) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) fa[c] = fb[c] = 0.0;
-  }
-  __device__ void operator()(int b, int rb) {
-    const PairForce pf = pair_force(A, a, ra, b, rb);
-    if (pf.hit) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        fa[c] += pf.fa[c];
-        fb[c] += pf.fb[c];
-      }
-    }
-  }
-  __device__ void store(double* fseg, int64_t E) const {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      fseg[c * E + a] = fa[c];
-      fseg[(3 + c) * E + a] = fb[c];
-    }
-  }
-};
 
 // Direct evaluation: one thread per slot of the cell-ordered list (threads of a warp share
 // cells and their neighbour rows, so candidate records come from L1).
@@ -524,44 +287,14 @@ __global__ void __launch_bounds__(256) list_build_kernel(ContactArgs A) {
   }
 }
 
-// Skin-list evaluation: one thread per segment, its listed candidates culled in FP32 against
-// the segment proxies of the current positions (written by the step kernel that produced them)
-// and evaluated in FP64; a segment whose list overflowed scans its neighbourhood of the last
-// build with the skin bound (the build's records are stale by less than skin / 2 per node,
-// which the skin covers).
+// Skin-list evaluation by a kernel of its own (the step kernel evaluates the lists itself when
+// the ensemble has no rods longer than a block): one thread per segment.
 __global__ void __launch_bounds__(256) list_force_kernel(ContactArgs A) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= A.E) return;
   if (*(volatile int*)A.err != 0) return;
-  const int n = A.nbr_count[a];
-  const int ra = A.seg_rod[a];
-  ForceSum f(A, (int)a, ra);
-  if (n <= kNbrCap) {
-    if (n > 0) {
-      const float4 ga = A.seg_prox[2 * a], ea = A.seg_prox[2 * a + 1];
-      // candidates in groups of four: all indices, then all proxies, then the tests in list
-      // order (four independent loads in flight instead of a chain of dependent ones)
-      constexpr int kG = 4;
-      for (int k0 = 0; k0 < n; k0 += kG) {
-        int bs[kG];
-        float4 gb[kG], eb[kG];
-#pragma unroll
-        for (int t = 0; t < kG; ++t) bs[t] = (k0 + t < n) ? A.nbr[(k0 + t) * A.E + a] : -1;
-#pragma unroll
-        for (int t = 0; t < kG; ++t) {
-          if (bs[t] >= 0) {
-            gb[t] = A.seg_prox[2 * (int64_t)bs[t]];
-            eb[t] = A.seg_prox[2 * (int64_t)bs[t] + 1];
-          }
-        }
-#pragma unroll
-        for (int t = 0; t < kG; ++t)
-          if (bs[t] >= 0 && may_touch(ga, gb[t], ea, eb[t], ea.w + eb[t].w)) f(bs[t], A.seg_rod[bs[t]]);
-      }
-    }
-  } else {
-    scan_neighbourhood(A, A.slot_of[a], A.skin, f);
-  }
+  ForceSum f(A, (int)a, A.seg_rod[a]);
+  listed_forces(A, a, f);
   f.store(A.fseg, A.E);
 }
 

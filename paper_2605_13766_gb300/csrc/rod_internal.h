@@ -51,6 +51,33 @@ struct Pack {
 };
 
 // Read-only parameters of the step kernels.
+// Arguments of the contact kernels (device pointers of the contact state and its parameters).
+struct ContactArgs {
+  const double* x;
+  const double* v;
+  const int* seg_rod;
+  const int* seg_cell;
+  const int* cell_start;
+  const int* sorted;
+  const float4* prox;
+  const float4* recA;
+  const int4* recB;
+  const float4* recC;
+  const int* gate;
+  int* nbr;
+  int* nbr_count;
+  const int* slot_of;
+  const float4* seg_prox;
+  float skin;
+  const RodConst* rods;
+  double* fseg;
+  int* err;
+  int64_t N, E;
+  int dim[3];
+  double k, c;
+  double mu, vslip, inv_vslip;
+};
+
 struct StepParams {
   // state (component-major)
   double* x;

@@ -51,6 +51,7 @@ __device__ __forceinline__ void pack_body(const StepParams& P, const Pack& pk, S
 
   stage_pack(P, pk, m);
 
+
   if (MODE == MODE_KIN_HALF) {
     kinematic(P, pk, m, 0.5 * dt);
     stage_sync(m);
@@ -211,8 +212,8 @@ __device__ __forceinline__ void pack_body(const StepParams& P, const Pack& pk, S
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, int64_t n_steps, double t0, double dt,
-                                                   int last_half, double* acc_v, double* acc_w) {
+__global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, int64_t n_steps,
+                                                   double t0, double dt, int last_half, double* acc_v, double* acc_w) {
   extern __shared__ double smem_d[];
   const Pack pk = P.packs[blockIdx.x];
   Smem m = carve(smem_d, S);
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(256) pack_kernel_grid(StepParams P, Pack pk, L
 
 size_t step_smem_bytes(const LaunchShape& s) {
   const size_t CE = s.cap_elems, CR = s.cap_rods, CN = CE + CR, CV = CE;
-  const size_t doubles = 3 * CN + 3 * CN + 9 * CE + 3 * CE + 3 * CE + 3 * CE + CE + CE + 3 * CV + 3 * CV + CE + CN + CR + 4;
+  const size_t doubles = 3 * CN + 3 * CN + 9 * CE + 3 * CE + 3 * CE + 3 * CE + CE + CE + 3 * CV + 3 * CV + CR + 4;
   const size_t ints = CR + 1;
   const size_t shorts = CE + CN + CV;
   return doubles * sizeof(double) + ints * sizeof(int) + shorts * sizeof(short) + 16;
@@ -291,10 +292,10 @@ cudaError_t launch_pack_kernel(const StepParams& P0, const LaunchShape& s, int m
                                double dt, int last_half, double* acc_v, double* acc_w, cudaStream_t st,
                                const LaunchHook& hook) {
   size_t smem = step_smem_bytes(s);
-  // FP32 node positions for the skin list's segment proxies, behind the pack's arrays when the
-  // block's shared memory has room (otherwise the epilogue rounds the FP64 positions itself)
   StepParams P = P0;
   P.xf_smem_off = 0;
+  // FP32 node positions for the skin list's segment proxies, behind the pack's arrays when the
+  // block's shared memory has room (otherwise the epilogue rounds the FP64 positions itself)
   if (P.seg_prox && mode != MODE_RHS) {
     const size_t off = (smem + 15) & ~size_t(15);
     const size_t need = off + sizeof(float) * 3 * static_cast<size_t>(s.cap_elems + s.cap_rods);

@@ -124,7 +124,7 @@ struct Smem {
   double *X, *VN, *QQ, *WW;     // state
   double *NF, *TA, *ELL, *EDIL; // element work
   double *PP, *TT;              // Voronoi work
-  double *IRL, *IM, *ACT;       // constants, per-rod actuation value
+  double* ACT;                  // per-rod actuation value (1/rl and 1/m are read through L1)
   double* BF;                   // [4] magnetic field b(t) of the step and its force time t
   int* rel0;                    // [CR+1] first element of each rod (pack-local)
   short *erod, *nrod, *vrod;    // pack-local rod of each element / node / Voronoi point
@@ -162,8 +162,6 @@ __device__ __forceinline__ Smem carve(double* base, const LaunchShape& S) {
   m.EDIL = p; p += m.CE;
   m.PP = p;   p += 3 * m.CV;
   m.TT = p;   p += 3 * m.CV;
-  m.IRL = p;  p += m.CE;
-  m.IM = p;   p += m.CN;
   m.ACT = p;  p += m.CR;
   m.BF = p;   p += 4;
   m.rel0 = reinterpret_cast<int*>(p);
@@ -267,7 +265,7 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
     const double ll = fma(l[0], l[0], fma(l[1], l[1], l[2] * l[2]));
     const double rs = rsqrt(ll);            // 1 / ell
     const double ell = ll * rs;
-    const double irl = m.IRL[i];
+    const double irl = __ldg(P.inv_rl + ge);
     const double rl = __ldg(P.rest_len + ge);
     const double e = ell * irl;             // dilatation
     const double ie = rl * rs;              // 1 / e
@@ -431,12 +429,12 @@ __device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& 
     }
     const bool held = (li == 0) && rc->clamp;
     if (MODE == MODE_RHS) {
-      const double ke = m.EDIL[i] * m.IRL[i];
+      const double ke = m.EDIL[i] * __ldg(P.inv_rl + pk.elem0 + i);
 #pragma unroll
       for (int c = 0; c < 3; ++c) acc_w[c * P.E + pk.elem0 + i] = held ? 0.0 : ke * __ldg(&rc->inv_rhoI[c]) * tau[c];
     } else {
       // w += dt e J^{-1} tau,  J^{-1} = 1/(rho I rl)
-      const double ke = (dt * m.EDIL[i]) * m.IRL[i];
+      const double ke = (dt * m.EDIL[i]) * __ldg(P.inv_rl + pk.elem0 + i);
 #pragma unroll
       for (int c = 0; c < 3; ++c)
         m.WW[c * m.CE + i] = held ? 0.0 : fma(ke * __ldg(&rc->inv_rhoI[c]), tau[c], m.WW[c * m.CE + i]);
@@ -462,7 +460,7 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
     const bool hasR = lj < nr, hasL = lj > 0;
     const int iR = j - r;                    // element to the right (pack-local)
     const bool held = (lj == 0) && rc->clamp;
-    const double im = m.IM[j];
+    const double im = __ldg(P.inv_m + pk.node0 + j);
     const double dl = __ldg(&rc->damp_lin);
     double F[3];
     if (P.fseg) {
@@ -575,7 +573,6 @@ __device__ __forceinline__ void stage_pack(const StepParams& P, const Pack& pk, 
   stage_sync(m);
   for (int i = m.t0; i < Ep; i += m.ts) {
     m.erod[i] = (short)find_rod(m.rel0, Rp, i);
-    m.IRL[i] = __ldg(P.inv_rl + pk.elem0 + i);
 #pragma unroll
     for (int a = 0; a < 9; ++a) m.QQ[a * m.CE + i] = P.Q[a * P.E + pk.elem0 + i];
 #pragma unroll
@@ -589,7 +586,6 @@ __device__ __forceinline__ void stage_pack(const StepParams& P, const Pack& pk, 
       if (m.rel0[mid] + mid <= j) lo = mid; else hi = mid - 1;
     }
     m.nrod[j] = (short)lo;
-    m.IM[j] = __ldg(P.inv_m + pk.node0 + j);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       m.X[c * m.CN + j] = P.x[c * P.N + pk.node0 + j];

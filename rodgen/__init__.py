@@ -277,6 +277,34 @@ def random_packing(n_rods: int = 10_000, nmin: int = 16, nmax: int = 256, box: f
         contact_c=contact_c, cell_size=2 * radius, dt=dt, n_steps=n_steps)
 
 
+def random_packing_cached(seed: int = 1234, cache_dir: Optional[str] = None) -> RodProblem:
+    """The default 10^4-rod packing of ``random_packing(seed=seed)``, kept as an .npz file in
+    ``cache_dir`` (default: the system's temporary directory) because the placement without
+    overlap takes tens of seconds; a missing or unreadable file is regenerated."""
+    import hashlib
+    import os
+    import tempfile
+    cache_dir = cache_dir or os.path.join(tempfile.gettempdir(), "rodbench_cache")
+    os.makedirs(cache_dir, exist_ok=True)
+    key = hashlib.sha1(f"random_packing-default-{seed}-v2".encode()).hexdigest()[:12]
+    path = os.path.join(cache_dir, f"packing_{key}.npz")
+    if os.path.exists(path):
+        try:
+            z = np.load(path)
+            base = random_packing(n_rods=10, seed=seed)  # cheap template for the other fields
+            return base.replace(n_elem=z["n_elem"], rest_len=z["rest_len"], radius=z["radius"], youngs=z["youngs"],
+                                shear_mod=z["shear_mod"], density=z["density"], x=z["x"], v=z["v"], Q=z["Q"],
+                                w=z["w"], name=f"random_packing_{int(z['n_elem'].size)}")
+        except Exception:
+            pass
+    p = random_packing(seed=seed)
+    tmp = path + f".{os.getpid()}.npz"
+    np.savez(tmp, n_elem=p.n_elem, rest_len=p.rest_len, radius=p.radius, youngs=p.youngs,
+             shear_mod=p.shear_mod, density=p.density, x=p.x, v=p.v, Q=p.Q, w=p.w)
+    os.replace(tmp, path)
+    return p
+
+
 def _axis_distance(c1, a1, h1, c2, a2, h2):
     """Exact distance between the axis segments c + t a, |t| <= h (vectorised over pairs): the
     minimum of the convex quadratic over the rectangle is either its free stationary point (if

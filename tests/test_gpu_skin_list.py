@@ -232,3 +232,4 @@ def test_replayed_graph_launches_rebuild_kernels_only_when_due():
     # kinematic half step, set_time, 64 replayed steps, one eager step with all its kernels
     assert n_g <= 1 + 1 + 64 * 4 + 10 * builds_g + 13
     assert n_g >= 1 + 1 + 64 * 4 + 13
+

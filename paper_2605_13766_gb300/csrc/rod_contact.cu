@@ -287,9 +287,10 @@ __global__ void __launch_bounds__(256) list_build_kernel(ContactArgs A) {
   }
 }
 
-// Skin-list evaluation by a kernel of its own (the step kernel evaluates the lists itself when
-// the ensemble has no rods longer than a block): one thread per segment.
-__global__ void __launch_bounds__(256) list_force_kernel(ContactArgs A) {
+// Skin-list evaluation: one thread per segment.  The kernel is bound by the latency of its
+// gathers, so it asks for three resident blocks per SM (80 registers; the spills sit around the
+// out-of-line pair evaluation, which runs for the few survivors of the cull).
+__global__ void __launch_bounds__(256, 3) list_force_kernel(ContactArgs A) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= A.E) return;
   if (*(volatile int*)A.err != 0) return;

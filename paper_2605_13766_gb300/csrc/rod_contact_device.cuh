@@ -235,9 +235,11 @@ __device__ __forceinline__ void listed_forces(const ContactArgs& A, int64_t a, F
   const int n = A.nbr_count[a];
   if (n <= kNbrCap) {
     if (n > 0) {
+      static_assert(kNbrCap <= 32, "the survivors of the cull are kept in a 32-bit mask");
+      // pass 1: FP32 cull of every candidate (groups of four: all indices, then all proxies, so
+      // that four independent loads are in flight); survivors go to a bit mask
       const float4 ga = A.seg_prox[2 * a], ea = A.seg_prox[2 * a + 1];
-      // candidates in groups of four: all indices, then all proxies, then the tests in list
-      // order (four independent loads in flight instead of a chain of dependent ones)
+      unsigned hit = 0u;
       constexpr int kG = 4;
       for (int k0 = 0; k0 < n; k0 += kG) {
         int bs[kG];
@@ -253,7 +255,14 @@ __device__ __forceinline__ void listed_forces(const ContactArgs& A, int64_t a, F
         }
 #pragma unroll
         for (int t = 0; t < kG; ++t)
-          if (bs[t] >= 0 && may_touch(ga, gb[t], ea, eb[t], ea.w + eb[t].w)) f(bs[t], A.seg_rod[bs[t]]);
+          if (bs[t] >= 0 && may_touch(ga, gb[t], ea, eb[t], ea.w + eb[t].w)) hit |= 1u << (k0 + t);
+      }
+      // pass 2: FP64 evaluation of the survivors in list order
+      while (hit) {
+        const int k = __ffs(hit) - 1;
+        hit &= hit - 1;
+        const int b = A.nbr[k * A.E + a];
+        f(b, A.seg_rod[b]);
       }
     }
   } else {

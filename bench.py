@@ -51,12 +51,13 @@ FLOPS_PER_UNIT = {
     "pack_one_step": 348.8,   # per element-step
     "pack_steps": 337.2,      # per element-step
 }
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the same captures;
-# reset to None whenever the kernel changes.  The carpet's state stays on chip between the
-# steps of a launch: its traffic is one read of the state and constants per launch (the
-# written state is still in L2 when the launch ends).
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of one capture of the
+# current kernel; reset to None whenever the kernel changes.  pack_one_step: the launch of step
+# ~290 of the bench's timed steps (dense contact), profiles/contact_list_force_packing_10k.md.
+# The carpet's state stays on chip between the steps of a launch: its traffic is one read of
+# the state and constants per launch (the written state is still in L2 when the launch ends).
 TRAFFIC_PER_LAUNCH = {
-    "pack_one_step": 336.42e6 + 147.24e6,
+    "pack_one_step": 336.42e6 + 188.58e6,
     "pack_steps": 39.28e6,
 }
 

@@ -197,6 +197,54 @@ def _e2e(s, p, dt, K, world, dist, barrier):
     return e2e
 
 
+def _adjoint_timing():
+    """Gradient of a tip-target loss with respect to the rest curvature and the element couples
+    over the adjoint workload (1024 rods x 64 elements, 2000 steps of 1e-5 s, checkpoint every
+    100 steps): the checkpointed forward run and the reverse sweep (recompute of each segment and
+    the hand-written adjoint kernels), each timed with CUDA events on the system's stream."""
+    import torch
+    from paper_2605_13766_gb300 import RodSystem
+    from paper_2605_13766_gb300.autograd import tip_indices
+    p = rodgen.adjoint_batch()
+    n_steps, dt, every = 2000, 1e-5, 100
+    s = RodSystem(p)
+    k0 = torch.tensor(p.rest_kappa, device="cuda")
+    c0 = torch.tensor(p.elem_couple, device="cuda")
+    state0 = [torch.tensor(a, device="cuda") for a in p.state()]
+    tips = tip_indices(p.node_offsets())
+    targets = torch.tensor(p.extra["targets"], device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    times = []
+    for rep in range(2):                      # the first pair warms up
+        s.set_params(k0, c0)
+        s.set_state(*state0)
+        torch.cuda.synchronize()
+        ev[0].record(s.torch_stream)
+        s.forward_checkpointed(n_steps, dt, every)
+        ev[1].record(s.torch_stream)
+        x = s.get_state(device=True)[0]
+        gx = torch.zeros_like(x)
+        gx[:, tips] = 2.0 * (x[:, tips] - targets)
+        z = torch.zeros
+        s.torch_stream.wait_stream(torch.cuda.current_stream())
+        e2 = torch.cuda.Event(enable_timing=True)
+        e2.record(s.torch_stream)
+        gk, gc = s.backward(gx, z((3, s.n_nodes), dtype=torch.float64, device="cuda"),
+                            z((9, s.n_elems), dtype=torch.float64, device="cuda"),
+                            z((3, s.n_elems), dtype=torch.float64, device="cuda"))
+        ev[2].record(s.torch_stream)
+        torch.cuda.synchronize()
+        times.append((ev[0].elapsed_time(ev[1]) / 1e3, e2.elapsed_time(ev[2]) / 1e3))
+    s.close()
+    t_fwd, t_bwd = times[-1]
+    units = p.n_elems * n_steps
+    return {"workload": "1024 rods x 64 elements, 2000 steps of 1e-5 s, checkpoint every 100, tip-target loss",
+            "forward_elem_steps_per_s": units / t_fwd, "backward_elem_steps_per_s": units / t_bwd,
+            "gradient_elem_steps_per_s": units / (t_fwd + t_bwd), "forward_s": t_fwd, "backward_s": t_bwd,
+            "grad_norm": {"rest_kappa": float(gk.norm()), "elem_couple": float(gc.norm())},
+            "check": "gradients checked against Richardson-extrapolated central differences in the GPU tests"}
+
+
 def _surrogate_speedup(train_steps: int):
     """Surrogate speed-up at the tip-error bound: the 64 x 64 carpet of 50-element rods from rest
     over 10^4 fine steps of 1e-5 s (200 calls of 50 steps), plain GPU step vs the checked
@@ -271,6 +319,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--launch-shape", default=None,
                     help="elements,threads per block for the step kernels (skips the autotuner)")
@@ -378,6 +427,9 @@ def main():
     sur = None
     if rank == 0 and world == 1 and not args.no_surrogate:
         sur = _surrogate_speedup(args.surrogate_train_steps)
+    adj = None
+    if rank == 0 and world == 1 and not args.no_adjoint:
+        adj = _adjoint_timing()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -390,7 +442,7 @@ def main():
                                l2="state (196 MB) larger than L2, no flush needed" if args.workload == "packing"
                                else "state L2/smem resident"),
                 "clocks": clk, "gpu_launches": launches, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
-                "surrogate": sur}
+                "surrogate": sur, "adjoint": adj}
         print(json.dumps(line), flush=True)
     s.close()
     if dist is not None:

@@ -274,6 +274,10 @@ rod_status build_packs(rod_system* s, const LaunchShape& shape) {
     cur.nvor += n - 1;
   }
   if (open) packs.push_back(cur);
+  // heaviest packs first (blocks start roughly in index order): the last, partly filled wave of
+  // blocks then holds the lightest packs, which shortens the tail of every launch
+  std::stable_sort(packs.begin(), packs.end(),
+                   [](const Pack& a, const Pack& b) { return a.nelem + a.nnode > b.nelem + b.nnode; });
   if (!packs.empty()) {
     CUDA_TRY(s->packs.alloc(packs.size()));
     CUDA_TRY(cudaMemcpy(s->packs.p, packs.data(), packs.size() * sizeof(Pack), cudaMemcpyHostToDevice));

@@ -212,6 +212,7 @@ struct rod_system {
   int graph_grid_version = -1;
   bool graph_list = false;  // the graph was captured with the skin list
   int shape_version = 0, graph_shape_version = -1;
+  StepParams graph_params{};  // the step kernel's parameters baked into the captured graph
   bool use_graphs = true;
   // adjoint: checkpoints of the last checkpointed forward run, recompute buffers
   DevBuf<double> ckpt, seg_states, adj, final_state;
@@ -311,7 +312,8 @@ LaunchShape default_shape(const rod_system* s) {
 }
 
 StepParams make_params(rod_system* s) {
-  StepParams P{};
+  StepParams P;
+  std::memset(&P, 0, sizeof P);  // padding too: captured parameters are compared as whole objects
   P.x = s->x.p;
   P.v = s->v.p;
   P.Q = s->Q.p;
@@ -427,16 +429,19 @@ cudaError_t capture_list_step(rod_system* s) {
 }
 
 rod_status ensure_contact_graph(rod_system* s, const StepParams& Pb, double dt) {
+  StepParams Pg = Pb;
+  Pg.t_dev = s->t_dev.p;
+  // reuse the graph while nothing baked into it has changed: the step kernel's parameters
+  // (every pointer and constant; the structures are zero-initialised, so whole-object
+  // comparison is exact), dt, the launch shape and the contact state's version
   if (s->graph_exec && s->graph_dt == dt && s->graph_grid_version == s->contact.version &&
-      s->graph_list == (s->contact.skin > 0.0) &&
-      s->graph_shape_version == s->shape_version)
+      s->graph_list == (s->contact.skin > 0.0) && s->graph_shape_version == s->shape_version &&
+      std::memcmp(&s->graph_params, &Pg, sizeof Pg) == 0)
     return ROD_OK;
   if (s->graph_exec) {
     cudaGraphExecDestroy(s->graph_exec);
     s->graph_exec = nullptr;
   }
-  StepParams Pg = Pb;
-  Pg.t_dev = s->t_dev.p;
   LaunchHook none;
   cudaGraph_t graph = nullptr;
   const bool list = s->contact.skin > 0.0;
@@ -472,6 +477,7 @@ rod_status ensure_contact_graph(rod_system* s, const StepParams& Pb, double dt) 
   s->graph_grid_version = s->contact.version;
   s->graph_list = list;
   s->graph_shape_version = s->shape_version;
+  s->graph_params = Pg;
   return ROD_OK;
 }
 
@@ -993,6 +999,7 @@ rod_status rod_system_friction(rod_system* s, double mu, double v_slip) {
     return fail(ROD_ERR_ARG, "friction needs mu >= 0 and, with mu > 0, a finite slip velocity > 0");
   s->contact.mu = mu;
   s->contact.vslip = mu > 0 ? v_slip : 0.0;
+  s->contact.grid_valid = false;  // the contact kernels take the friction law by value
   return ROD_OK;
 }
 

@@ -42,7 +42,8 @@ struct ContactState {
   int dim[3] = {0, 0, 0};
   int64_t ncell = 0, cap_cells = 0;
   double l_allowed = 0.0;  // longest element the cell size covers (less the FP32 binning margin)
-  int version = 0;         // bumped whenever the grid is rebuilt
+  int version = 0;         // bumped whenever the grid, the constants or a buffer changes
+  std::vector<uint64_t> signature;  // what the last version was made of
   int64_t E = 0;
   // device buffers (library-owned)
   int* seg_rod = nullptr;     // [E] rod of each segment
@@ -69,6 +70,7 @@ struct ContactState {
   float* x_ref = nullptr;     // [3N] positions of the last build, rounded to FP32
   float4* seg_prox = nullptr; // [2E] FP32 proxies of the current positions, written by the step kernels
   ListCtl* ctl = nullptr;
+  unsigned long long* bounds = nullptr;  // [8] grid set-up: bounding box, longest segment (order keys)
   bool ctl_live = false;       // ctl holds counts of the current grid
   int64_t opened_before = 0;   // ctl->opened of earlier grids (launch accounting)
 };

@@ -233,3 +233,28 @@ def test_replayed_graph_launches_rebuild_kernels_only_when_due():
     assert n_g <= 1 + 1 + 64 * 4 + 10 * builds_g + 13
     assert n_g >= 1 + 1 + 64 * 4 + 13
 
+
+
+def test_replayed_graph_follows_parameter_changes_between_calls():
+    """A graph captured for the contact steps is replayed only while nothing baked into it has
+    changed: friction set between two step calls, new rest curvatures and element couples, and
+    the same state set again give the trajectory of eager launches bit for bit."""
+    p = _touching(60, 0.1, 23)
+    rng = np.random.default_rng(4)
+    kappa = rng.normal(0.0, 0.5, (3, p.n_elems - p.n_rods))
+    couple = rng.normal(0.0, 1e-7, (3, p.n_elems))
+    out = []
+    for graphs in (True, False):
+        s = _gpu(p, 2e-4, graphs=graphs)
+        s.step(40, 2e-6)
+        s.friction(0.4, 1e-3)
+        s.step(40, 2e-6)
+        s.set_params(kappa, couple)
+        s.step(40, 2e-6)
+        x, v, Q, w = s.get_state()
+        s.set_state(x, v, Q, w)
+        s.step(40, 2e-6)
+        out.append(s.get_state())
+        s.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)

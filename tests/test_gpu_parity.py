@@ -268,3 +268,31 @@ def test_invalid_descriptions_are_rejected():
         s.step(1, -1.0)
     with pytest.raises(RodError):
         s.set_launch(100, 0)     # not a multiple of 32
+
+
+def test_cantilever_settles_to_the_oracles_elastica_state():
+    """The cantilever workload's rod (1 m, r = 1 cm, E = 1 MPa, tip force 1e-2 N, far outside
+    linear theory) at n = 25, critically damped and run for 252,000 steps of 1e-4 s to rest: the
+    GPU's settled tip equals the oracle's to 1e-9 of the length, and both sit at the oracle
+    pin's first-order distance below the nonlinear elastica's 0.3651 m."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "statics", os.path.join(os.path.dirname(os.path.abspath(__file__)), "test_oracle_statics.py"))
+    statics = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(statics)
+    L, r, F, n = 1.0, 0.01, 1e-2, 25
+    A, I, EA, EI, GAs = statics._consts(r)
+    w1 = 3.516 * np.sqrt(EI / (1000 * A * L ** 4))
+    nu = 2 * 1000 * A * w1
+    dt = min(1e-4, 0.1 * (L / n) / np.sqrt(1e6 / 1000))
+    steps = int(14 / w1 / dt)
+    p = rodgen.cantilever(n=n, length=L, radius=r, tip_force=F, nu=nu, dt=dt)
+    xo = Oracle(p).step(*p.state(), dt=dt, n_steps=steps)[0]
+    s = _gpu(p)
+    s.step(steps, dt)
+    xg, vg = s.get_state()[:2]
+    assert np.abs(xg - xo).max() / L <= POS_TOL
+    assert np.abs(vg).max() < 1e-5
+    y_ref, _ = statics._elastica_tip(L, EI, F)
+    assert -0.07 < xg[1, -1] / y_ref - 1 < -0.03

@@ -130,3 +130,42 @@ def test_timoshenko_cantilever(L, r):
     assert -0.08 < e25 < -0.03 and -0.04 < e50 < -0.015
     assert 1.7 < e25 / e50 < 2.3                       # first-order convergence
     assert abs((2 * d50 - d25) / ref - 1) < 3e-3      # extrapolated limit
+
+
+def _elastica_tip(L, EI, F):
+    """Tip of the inextensible elastica of a cantilever under a transverse dead tip load F:
+    EI theta'' + F cos(theta) = 0, theta(0) = 0, theta'(L) = 0 (theta: tangent angle from the
+    clamped axis), x' = sin(theta), z' = cos(theta); boundary-value solve in scipy."""
+    from scipy.integrate import solve_bvp
+
+    def f(s, y):
+        return np.vstack([y[1], -(F / EI) * np.cos(y[0]), np.sin(y[0]), np.cos(y[0])])
+
+    def bc(ya, yb):
+        return np.array([ya[0], yb[1], ya[2], ya[3]])
+
+    s = np.linspace(0.0, L, 401)
+    y0 = np.zeros((4, s.size))
+    y0[3] = s
+    sol = solve_bvp(f, bc, s, y0, tol=1e-10, max_nodes=100000)
+    assert sol.status == 0
+    return sol.y[2, -1], sol.y[3, -1]
+
+
+def test_nonlinear_elastica_cantilever():
+    """The cantilever workload's load (1 m, r = 1 cm, E = 1 MPa, F = 1e-2 N: F L^2/EI = 1.27) is
+    far outside linear theory (F L^3/(3EI) = 0.424 m): settled, the tip deflection converges at
+    first order in 1/n to the nonlinear elastica's 0.3651 m (14 % below the linear value), and
+    Richardson extrapolation of n = 25, 50 lands within 1e-3 of it (extensibility and shear
+    contribute ~1e-4 here)."""
+    L, r, F = 1.0, 0.01, 1e-2
+    A, I, EA, EI, GAs = _consts(r)
+    y_ref, z_ref = _elastica_tip(L, EI, F)
+    assert abs(y_ref - 0.3651) < 1e-4 and y_ref < 0.9 * F * L ** 3 / (3 * EI)
+    d25, v25 = _settled_tip(25, L, r, F)
+    d50, v50 = _settled_tip(50, L, r, F)
+    assert v25 < 1e-5 and v50 < 1e-5                  # settled
+    e25, e50 = d25 / y_ref - 1, d50 / y_ref - 1
+    assert -0.07 < e25 < -0.03 and -0.035 < e50 < -0.015
+    assert 1.8 < e25 / e50 < 2.2                       # first-order convergence
+    assert abs((2 * d50 - d25) / y_ref - 1) < 1e-3     # extrapolated limit

@@ -245,33 +245,41 @@ struct Scales {
 };
 
 // Q_new = exp([-T w]x) Q (rows: directors): the director update of a constant angular velocity
-// w (local frame) held for the whole window, by the Rodrigues formula with (1 - cos th) written
-// as 2 sin^2(th / 2).
+// w (local frame) held for the whole window, by the Rodrigues formula R = I + a K + b K^2 =
+// (1 - b th^2) I + a K + b p p^T with p = -T w, K = [p]x, a = sin(th)/th, b = (1 - cos th)/th^2.
+// No FP64 division: for th < 0.05 the Taylor polynomials of a and b in th^2 (the first omitted
+// terms, th^8/9! and th^8/10!, are below 1e-16), otherwise sin and cos of th.
 __device__ __forceinline__ void rotate_directors(const double w[3], double T, const double Q[9], double out[9]) {
-  const double ph[3] = {-T * w[0], -T * w[1], -T * w[2]};
-  const double th2 = ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2];
+  const double p0 = -T * w[0], p1 = -T * w[1], p2 = -T * w[2];
+  const double th2 = fma(p0, p0, fma(p1, p1, p2 * p2));
   double a, b;
   if (th2 < 2.5e-3) {
-    // |th| < 0.05: Taylor series of sin(th)/th and (1 - cos th)/th^2; the first omitted terms,
-    // th^8/9! and th^8/10!, are below 1e-16
-    a = 1.0 - th2 / 6.0 * (1.0 - th2 / 20.0 * (1.0 - th2 / 42.0));
-    b = 0.5 * (1.0 - th2 / 12.0 * (1.0 - th2 / 30.0 * (1.0 - th2 / 56.0)));
+    a = fma(fma(fma(th2, -1.0 / 5040.0, 1.0 / 120.0), th2, -1.0 / 6.0), th2, 1.0);
+    b = fma(fma(fma(th2, -1.0 / 40320.0, 1.0 / 720.0), th2, -1.0 / 24.0), th2, 0.5);
   } else {
+    // half-angle forms: sin th = 2 s c and 1 - cos th = 2 s^2 with s, c of th / 2 (no cancellation)
     const double th = sqrt(th2);
-    const double sh = sin(0.5 * th) / th;
-    a = sin(th) / th;
-    b = 2.0 * sh * sh;
+    const double ith = 1.0 / th;
+    double sh, ch;
+    sincos(0.5 * th, &sh, &ch);
+    const double shi = sh * ith;
+    a = 2.0 * shi * ch;
+    b = 2.0 * shi * shi;
   }
-  const double K[9] = {0.0, -ph[2], ph[1], ph[2], 0.0, -ph[0], -ph[1], ph[0], 0.0};
-  double M[9];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) {
-      double k2 = 0.0;
-      for (int l = 0; l < 3; ++l) k2 += K[3 * i + l] * K[3 * l + j];
-      M[3 * i + j] = (i == j ? 1.0 : 0.0) + a * K[3 * i + j] + b * k2;
-    }
-  for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 3; ++k) out[3 * i + k] = M[3 * i] * Q[k] + M[3 * i + 1] * Q[3 + k] + M[3 * i + 2] * Q[6 + k];
+  const double c0 = fma(-b, th2, 1.0);
+  const double b0 = b * p0, b1 = b * p1, b2 = b * p2;
+  const double a0 = a * p0, a1 = a * p1, a2 = a * p2;
+  const double R00 = fma(b0, p0, c0), R11 = fma(b1, p1, c0), R22 = fma(b2, p2, c0);
+  const double R01 = fma(b0, p1, -a2), R10 = fma(b1, p0, a2);
+  const double R02 = fma(b0, p2, a1), R20 = fma(b2, p0, -a1);
+  const double R12 = fma(b1, p2, -a0), R21 = fma(b2, p1, a0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double q0 = Q[k], q1 = Q[3 + k], q2 = Q[6 + k];
+    out[k] = fma(R00, q0, fma(R01, q1, R02 * q2));
+    out[3 + k] = fma(R10, q0, fma(R11, q1, R12 * q2));
+    out[6 + k] = fma(R20, q0, fma(R21, q1, R22 * q2));
+  }
 }
 
 __device__ __forceinline__ void load_q(const double* Q, int64_t E, int64_t e, double q[9]) {
@@ -454,11 +462,11 @@ __device__ __forceinline__ void update_node(const WinState& S, int b, int j, con
     d2[c] = qp[3 + c] + sc.out[9 + c] * static_cast<double>(o[9 + c]);
     w[c * E + eg] = (sc.keep_w ? w0[c] : 0.0) + sc.out[12 + c] * static_cast<double>(o[12 + c]);
   }
-  const double n1 = 1.0 / sqrt(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
+  const double n1 = rsqrt(fma(d1[0], d1[0], fma(d1[1], d1[1], d1[2] * d1[2])));
   for (int c = 0; c < 3; ++c) d1[c] *= n1;
-  const double p = d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2];
-  for (int c = 0; c < 3; ++c) d2[c] -= p * d1[c];
-  const double n2 = 1.0 / sqrt(d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2]);
+  const double p = fma(d1[0], d2[0], fma(d1[1], d2[1], d1[2] * d2[2]));
+  for (int c = 0; c < 3; ++c) d2[c] = fma(-p, d1[c], d2[c]);
+  const double n2 = rsqrt(fma(d2[0], d2[0], fma(d2[1], d2[1], d2[2] * d2[2])));
   for (int c = 0; c < 3; ++c) d2[c] *= n2;
   const double d3[3] = {d1[1] * d2[2] - d1[2] * d2[1], d1[2] * d2[0] - d1[0] * d2[2], d1[0] * d2[1] - d1[1] * d2[0]};
   for (int c = 0; c < 3; ++c) {

@@ -140,8 +140,9 @@ rod_status rod_system_sync(rod_system* sys);
 
 /* Rod-rod contact (a8-a9 of the step): enable = 0 disables it.  k: spring stiffness (N/m),
  * c: dashpot coefficient (N s/m), cell_size: requested cell edge; the grid uses
- * max(cell_size, 2 r_max + (1 + margin) l_max) where l_max is the longest element of the
- * state given to the next set_state (a longer element later raises ROD_ERR_OVERFLOW), over
+ * max(cell_size, 2 r_max + 2 l_max (+ the skin)) where l_max is the longest element of the
+ * state given to the next set_state (an element later stretched beyond 2 l_max, less a rounding
+ * margin, raises ROD_ERR_OVERFLOW), over
  * the bounding box of that state grown by box_margin (m) on each side (segments leaving it
  * are clamped into the boundary cells, which keeps the pair search exact). */
 rod_status rod_system_contact_config(rod_system* sys, int enable, double k, double c, double cell_size);

@@ -42,6 +42,8 @@ namespace {
 // Largest number of segments one cell may hold; a denser cell (a collapsed or escaped
 // configuration) latches ERR_OVERFLOW instead of running a quadratic search.
 constexpr int kCellCap = 512;
+// Longest element the contact grid covers, in units of the longest element at grid set-up.
+constexpr double kStretchAllowance = 2.0;
 
 // Closest points of P(s) = p0 + s d1, R(u) = q0 + u d2 on [0,1]^2 (minimise |r + s d1 - u d2|^2,
 // r = p0 - q0): free minimiser s = (b f - c e)/(a e - b^2) clamped, u = (b s + f)/e; a clamped u
@@ -768,8 +770,12 @@ rod_status contact_prepare(ContactState& cs, const std::vector<RodConst>& rods_h
   for (int c = 0; c < 3; ++c)
     if (!std::isfinite(lo[c]) || !std::isfinite(hi[c]) || !std::isfinite(lmax))
       return cfail(ROD_ERR_NONFINITE, "contact grid: non-finite positions", cudaSuccess);
+  // cell edge: a contacting pair's midpoints are closer than r_a + r_b + (l_a + l_b) / 2 (+ the
+  // skin), so 2 r_max + l_max would do for the elements as they are now; the grid allows
+  // elements up to twice the longest one at set-up (soft rods under stiff contact stretch
+  // by tens of percent) before a longer one latches ROD_ERR_OVERFLOW
   const double skin = cs.skin > 0.0 ? cs.skin : 0.0;
-  double h = std::max(cs.cell_size, 2.0 * rmax + 1.25 * lmax + skin);
+  double h = std::max(cs.cell_size, 2.0 * rmax + kStretchAllowance * lmax + skin);
   double ext[3], margin[3];
   int64_t ncell = 0;
   for (int iter = 0; iter < 64; ++iter) {

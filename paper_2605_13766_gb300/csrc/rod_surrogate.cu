@@ -874,6 +874,16 @@ struct rod_surrogate {
   int sample_cap = 0;
   unsigned long long* err_dev = nullptr;
   unsigned long long* err_host = nullptr;  // pinned
+  // local checked rollouts: per shadow slot the sampled tips, an error word (device and pinned
+  // host) and three events, kept between calls (no allocation inside a rollout)
+  struct CheckRes {
+    double* tips = nullptr;
+    int tips_cap = 0;
+    unsigned long long* err_dev = nullptr;
+    unsigned long long* err_host = nullptr;
+    cudaEvent_t gathered = nullptr, tipped = nullptr, done = nullptr;
+  };
+  std::vector<CheckRes> chk;
 };
 
 namespace {
@@ -1131,6 +1141,14 @@ rod_status rod_surrogate_destroy(rod_surrogate* s) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->err_host) cudaFreeHost(s->err_host);
+  for (auto& c : s->chk) {
+    if (c.tips) cudaFree(c.tips);
+    if (c.err_dev) cudaFree(c.err_dev);
+    if (c.err_host) cudaFreeHost(c.err_host);
+    if (c.gathered) cudaEventDestroy(c.gathered);
+    if (c.tipped) cudaEventDestroy(c.tipped);
+    if (c.done) cudaEventDestroy(c.done);
+  }
   delete s;
   return ROD_OK;
 }
@@ -1388,26 +1406,34 @@ rod_status rod_surrogate_rollout_local(rod_surrogate* s, rod_system* sys, rod_sy
   };
   std::vector<Slot> sl(slots);
   auto release = [&]() {
-    for (auto& q : sl) {
+    for (auto& q : sl)
       if (q.done) cudaEventSynchronize(q.done);
-      if (q.tips) cudaFree(q.tips);
-      if (q.err_dev) cudaFree(q.err_dev);
-      if (q.err_host) cudaFreeHost(q.err_host);
-      if (q.gathered) cudaEventDestroy(q.gathered);
-      if (q.tipped) cudaEventDestroy(q.tipped);
-      if (q.done) cudaEventDestroy(q.done);
-    }
   };
   auto failc = [&](cudaError_t err) {
     release();
     return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(err));
   };
-  for (auto& q : sl) {
-    if ((e = cudaMalloc(&q.tips, 3 * n_sample * 8)) || (e = cudaMalloc(&q.err_dev, 8)) ||
-        (e = cudaMallocHost(&q.err_host, 8)) || (e = cudaEventCreateWithFlags(&q.gathered, cudaEventDisableTiming)) ||
-        (e = cudaEventCreateWithFlags(&q.tipped, cudaEventDisableTiming)) ||
-        (e = cudaEventCreateWithFlags(&q.done, cudaEventDisableTiming)))
+  if (static_cast<int>(s->chk.size()) < slots) s->chk.resize(slots);
+  for (int k = 0; k < slots; ++k) {
+    rod_surrogate::CheckRes& c = s->chk[k];
+    if (c.tips_cap < n_sample) {
+      if (c.tips) cudaFree(c.tips);
+      c.tips = nullptr;
+      c.tips_cap = 0;
+      if ((e = cudaMalloc(&c.tips, 3 * n_sample * 8))) return failc(e);
+      c.tips_cap = n_sample;
+    }
+    if ((!c.err_dev && (e = cudaMalloc(&c.err_dev, 8))) || (!c.err_host && (e = cudaMallocHost(&c.err_host, 8))) ||
+        (!c.gathered && (e = cudaEventCreateWithFlags(&c.gathered, cudaEventDisableTiming))) ||
+        (!c.tipped && (e = cudaEventCreateWithFlags(&c.tipped, cudaEventDisableTiming))) ||
+        (!c.done && (e = cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming))))
       return failc(e);
+    sl[k].tips = c.tips;
+    sl[k].err_dev = c.err_dev;
+    sl[k].err_host = c.err_host;
+    sl[k].gathered = c.gathered;
+    sl[k].tipped = c.tipped;
+    sl[k].done = c.done;
   }
   if ((e = cudaMemcpyAsync(s->sample, sample_rods, n_sample * 4, cudaMemcpyHostToDevice, V.stream))) return failc(e);
   int reserve = 0;

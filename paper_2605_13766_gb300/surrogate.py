@@ -27,7 +27,11 @@ ELEMENTS = 50
 DEFAULT_NOISE = 0.05
 DEFAULT_CHECK_BOUND = 8e-4
 DEFAULT_SAMPLE = 16              # rods followed by the shadow systems
-SHADOW_SHAPE = (64, 64)          # launch shape of the shadow: 64 elements (one rod) per block
+# launch shape of the shadows: two 50-element rods per 128-thread block, one warp per SM
+# sub-partition (an FP64 warp instruction holds a sub-partition's FP64 unit for 64 cycles
+# however many lanes are active, so a single rod per block is no faster), and half the SMs
+# that one rod per block would take from the network
+SHADOW_SHAPE = (128, 128)
 
 
 def couple_samples(problem, t: float, T: float) -> np.ndarray:
@@ -389,7 +393,7 @@ class CheckedRollout:
         for _ in range(1 if mode == "global" else n_shadows):
             sh = RodSystem(sub, use_torch_stream=False)
             if shadow_shape is not None:
-                # one rod per block: the shadow's step is latency-bound, not throughput-bound
+                # few rods per block: the shadow's step is latency-bound, not throughput-bound
                 sh.set_launch(*shadow_shape)
             sh.set_state(*sub.state())
             self.shadows.append(sh)

@@ -208,8 +208,12 @@ rod_status rod_system_backward(rod_system* sys, const double* adj_x, const doubl
 rod_status rod_system_adjoint_of_state(rod_system* sys, double* adj_x, double* adj_v, double* adj_Q, double* adj_w);
 
 /* With contact, rod_system_step replays a CUDA graph of 32 captured steps (captured on an
- * internal stream, launched on the system's stream) unless profiling is on; enable = 0 makes
- * every step an eager sequence of launches (same kernels, same results). */
+ * internal stream, launched on the system's stream) unless profiling is on or a rod is longer
+ * than a block holds; enable = 0 makes every step an eager sequence of launches (same kernels,
+ * same results).  With the skin list the rebuild kernels sit in a conditional node of the graph
+ * that the device-side rebuild decision opens only when a rebuild is due.  A captured graph is
+ * kept while nothing it bakes in changes (step parameters, dt, launch shape, contact grid and
+ * constants); otherwise the next step call captures a new one. */
 rod_status rod_system_set_graphs(rod_system* sys, int enable);
 
 /* Per-kernel timing (tracing): enable = 1 records a CUDA event pair on the system's stream
@@ -225,7 +229,9 @@ int32_t rod_profile_classes(void);
 rod_status rod_system_profile_read(rod_system* sys, int32_t k, const char** name, double* total_ms,
                                    int64_t* launches);
 
-/* Total number of kernels this system has launched since it was created. */
+/* Total number of kernels this system has launched since it was created, those of replayed
+ * graphs included (rebuild kernels of a graph's conditional node count when they ran: with a
+ * skin list the call reads a device counter and synchronises on the system's stream). */
 rod_status rod_system_launch_count(const rod_system* sys, int64_t* launches);
 
 /* Autotuner: time trial_steps steps of dt (after one warm-up step) for every valid launch shape

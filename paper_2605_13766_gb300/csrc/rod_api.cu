@@ -14,6 +14,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -185,6 +186,7 @@ struct rod_system {
   // packing
   LaunchShape shape{0, 0, 0};
   DevBuf<Pack> packs;
+  DevBuf<int2> pack_rods;  // (global rod, first pack-local element) of the rods of listed packs
   int n_packs = 0;
   // rods longer than a block holds: one pack each, run by cooperative launches with their
   // working arrays in long_scratch
@@ -275,6 +277,68 @@ rod_status build_packs(rod_system* s, const LaunchShape& shape) {
     cur.nvor += n - 1;
   }
   if (open) packs.push_back(cur);
+  // Rods of mixed lengths leave the consecutive packs part empty (a block's element loops run
+  // over cap_elems threads whatever the pack holds).  Best-fit decreasing over the same rods
+  // fills them closer to the capacity; it is kept when it needs fewer packs.  Its packs list
+  // their rods (global rod, first pack-local element) unless the rods happen to be consecutive.
+  std::vector<int2> list;
+  {
+    std::vector<int> order;
+    for (int r = 0; r < s->R; ++r)
+      if (s->rods_h[r].n <= shape.cap_elems) order.push_back(r);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return s->rods_h[a].n > s->rods_h[b].n; });
+    std::vector<std::vector<int>> bins;
+    std::vector<int> room;
+    std::multiset<std::pair<int, int>> open_bins;  // (free elements, bin), bins below cap_rods
+    for (int r : order) {
+      const int n = s->rods_h[r].n;
+      auto it = open_bins.lower_bound({n, -1});
+      int b;
+      if (it == open_bins.end()) {
+        b = static_cast<int>(bins.size());
+        bins.emplace_back();
+        room.push_back(shape.cap_elems);
+      } else {
+        b = it->second;
+        open_bins.erase(it);
+      }
+      bins[b].push_back(r);
+      room[b] -= n;
+      if (static_cast<int>(bins[b].size()) < shape.cap_rods) open_bins.insert({room[b], b});
+    }
+    if (bins.size() < packs.size()) {
+      packs.clear();
+      for (auto& rods : bins) {
+        std::sort(rods.begin(), rods.end());
+        Pack pk{};
+        bool consecutive = true;
+        for (size_t k = 1; k < rods.size(); ++k) consecutive = consecutive && rods[k] == rods[k - 1] + 1;
+        const RodConst& first = s->rods_h[rods[0]];
+        pk.rod0 = rods[0];
+        pk.elem0 = first.elem0;
+        pk.node0 = first.node0;
+        pk.vor0 = first.elem0 - rods[0];
+        pk.listed = consecutive ? 0 : 1;
+        pk.list_off = consecutive ? 0 : static_cast<int32_t>(list.size());
+        for (int r : rods) {
+          const int n = s->rods_h[r].n;
+          if (!consecutive) list.push_back(make_int2(r, pk.nelem));
+          pk.nrods += 1;
+          pk.nelem += n;
+          pk.nnode += n + 1;
+          pk.nvor += n - 1;
+        }
+        packs.push_back(pk);
+      }
+    }
+  }
+  if (!list.empty()) {
+    CUDA_TRY(s->pack_rods.alloc(list.size()));
+    CUDA_TRY(cudaMemcpy(s->pack_rods.p, list.data(), list.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  } else {
+    s->pack_rods.release();
+  }
   // heaviest packs first (blocks start roughly in index order): the last, partly filled wave of
   // blocks then holds the lightest packs, which shortens the tail of every launch
   std::stable_sort(packs.begin(), packs.end(),
@@ -333,6 +397,7 @@ StepParams make_params(rod_system* s) {
   P.clamp_Q = s->clamp_Q.p;
   P.rods = s->rods.p;
   P.packs = s->packs.p;
+  P.pack_rods = s->pack_rods.p;
   P.n_packs = s->n_packs;
   P.n_rods = s->R;
   for (int c = 0; c < 3; ++c) P.gravity[c] = s->gravity[c];
@@ -800,6 +865,7 @@ rod_status rod_system_destroy(rod_system* s) {
   s->clamp_Q.release();
   s->rods.release();
   s->packs.release();
+  s->pack_rods.release();
   s->long_scratch.release();
   s->ckpt.release();
   s->seg_states.release();

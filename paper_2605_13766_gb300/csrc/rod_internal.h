@@ -43,11 +43,15 @@ struct RodConst {
 constexpr int kMaxWalls = 8;
 
 // A pack: consecutive rods processed by one thread block.
+// A thread block's share of the ensemble: consecutive rods (listed = 0: rod0.. and the global
+// first element, node and Voronoi point), or any rods (listed = 1: entries list_off ..
+// list_off + nrods of StepParams::pack_rods), with the pack's element, node and Voronoi counts.
 struct Pack {
   int32_t rod0, nrods;
-  int32_t elem0, nelem;  // global first element, element count
-  int32_t node0, nnode;  // global first node, node count
-  int32_t vor0, nvor;    // global first Voronoi point, count
+  int32_t elem0, nelem;  // global first element (consecutive packs), element count
+  int32_t node0, nnode;  // global first node (consecutive packs), node count
+  int32_t vor0, nvor;    // global first Voronoi point (consecutive packs), count
+  int32_t listed, list_off;
 };
 
 // Read-only parameters of the step kernels.
@@ -98,6 +102,7 @@ struct StepParams {
   const double* clamp_Q;      // [9R]
   const RodConst* rods;       // [R]
   const Pack* packs;
+  const int2* pack_rods;      // listed packs: (global rod, first pack-local element) per entry
   int32_t n_packs;
   int32_t n_rods;
   double gravity[3];

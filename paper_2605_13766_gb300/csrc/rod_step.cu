@@ -120,7 +120,7 @@ __device__ __forceinline__ void pack_body(const StepParams& P, const Pack& pk, S
         ic[c] = static_cast<int>(q);
       }
       const int cell = (ic[2] * P.bin_dim[1] + ic[1]) * P.bin_dim[0] + ic[0];
-      const int ge = pk.elem0 + i;
+      const int ge = i + m.dE[m.erod[i]];
       P.bin_cell[ge] = cell;
       P.bin_prox[ge] = make_float4(mid[0], mid[1], mid[2], 0.5f * len);
       const unsigned peers = __match_any_sync(__activemask(), cell);
@@ -138,7 +138,7 @@ __device__ __forceinline__ void pack_body(const StepParams& P, const Pack& pk, S
   unsigned expo = 0u;
   const bool prox = leaves_half && P.seg_prox != nullptr;
   for (int i = m.t0; i < Ep; i += m.ts) {
-    const int ge = pk.elem0 + i;
+    const int ge = i + m.dE[m.erod[i]];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       const double q = m.QQ[a * m.CE + i];
@@ -164,7 +164,7 @@ __device__ __forceinline__ void pack_body(const StepParams& P, const Pack& pk, S
       const float hl = sqrtf(fmaf(he[0], he[0], fmaf(he[1], he[1], he[2] * he[2])));
       P.seg_prox[2 * static_cast<int64_t>(ge)] =
           make_float4(0.5f * (p0[0] + p1[0]), 0.5f * (p0[1] + p1[1]), 0.5f * (p0[2] + p1[2]), hl);
-      P.seg_prox[2 * static_cast<int64_t>(ge) + 1] = make_float4(he[0], he[1], he[2], P.rods[pk.rod0 + r].radius_f);
+      P.seg_prox[2 * static_cast<int64_t>(ge) + 1] = make_float4(he[0], he[1], he[2], P.rods[m.grod[r]].radius_f);
     }
   }
   // Upper bound of the node displacement since the skin list's build, in FP32: with xf, rf the
@@ -174,7 +174,7 @@ __device__ __forceinline__ void pack_body(const StepParams& P, const Pack& pk, S
   const bool track = P.disp_ref != nullptr && MODE != MODE_RHS;
   float dmax = 0.f;
   for (int j = m.t0; j < Np; j += m.ts) {
-    const int64_t gn = pk.node0 + j;
+    const int64_t gn = j + m.dN[m.nrod[j]];
     float s2 = 0.f, mag = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(256) pack_kernel_grid(StepParams P, Pack pk, L
 size_t step_smem_bytes(const LaunchShape& s) {
   const size_t CE = s.cap_elems, CR = s.cap_rods, CN = CE + CR, CV = CE;
   const size_t doubles = 3 * CN + 3 * CN + 9 * CE + 3 * CE + 3 * CE + 3 * CE + CE + CE + 3 * CV + 3 * CV + CR + 4;
-  const size_t ints = CR + 1;
+  const size_t ints = CR + 1 + 4 * CR;
   const size_t shorts = CE + CN + CV;
   return doubles * sizeof(double) + ints * sizeof(int) + shorts * sizeof(short) + 16;
 }

@@ -127,6 +127,9 @@ struct Smem {
   double* ACT;                  // per-rod actuation value (1/rl and 1/m are read through L1)
   double* BF;                   // [4] magnetic field b(t) of the step and its force time t
   int* rel0;                    // [CR+1] first element of each rod (pack-local)
+  // per pack-local rod: global rod index, and the offsets from pack-local element / node /
+  // Voronoi indices to global ones (global = local + offset)
+  int *grod, *dE, *dN, *dV;
   short *erod, *nrod, *vrod;    // pack-local rod of each element / node / Voronoi point
   float* XF;                    // [3][CN] node positions rounded to FP32 by the kinematic stage, or null
   int CE, CN, CV, CR;
@@ -165,7 +168,11 @@ __device__ __forceinline__ Smem carve(double* base, const LaunchShape& S) {
   m.ACT = p;  p += m.CR;
   m.BF = p;   p += 4;
   m.rel0 = reinterpret_cast<int*>(p);
-  m.erod = reinterpret_cast<short*>(m.rel0 + m.CR + 1);
+  m.grod = m.rel0 + m.CR + 1;
+  m.dE = m.grod + m.CR;
+  m.dN = m.dE + m.CR;
+  m.dV = m.dN + m.CR;
+  m.erod = reinterpret_cast<short*>(m.dV + m.CR);
   m.nrod = m.erod + m.CE;
   m.vrod = m.nrod + m.CN;
   m.XF = nullptr;
@@ -190,7 +197,7 @@ __device__ __forceinline__ int find_rod(const int* starts, int nrods, int idx) {
 // Kinematic update of one element: Q <- exp(-h [w]x) Q (clamped element: held value).
 __device__ __forceinline__ void kin_element(const StepParams& P, const Pack& pk, Smem& m, int i, double h) {
   const int r = m.erod[i];
-  const int g = pk.rod0 + r;
+  const int g = m.grod[r];
   const bool held = (i == m.rel0[r]) && P.rods[g].clamp;
   double q[9];
 #pragma unroll
@@ -226,7 +233,7 @@ __device__ __forceinline__ void kin_element(const StepParams& P, const Pack& pk,
 // Kinematic update of one node: x <- x + h v (clamped node: held value).
 __device__ __forceinline__ void kin_node(const StepParams& P, const Pack& pk, Smem& m, int j, double h) {
   const int r = m.nrod[j];
-  const int g = pk.rod0 + r;
+  const int g = m.grod[r];
   const bool held = (j == m.rel0[r] + r) && P.rods[g].clamp;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -250,9 +257,9 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
   const int Ep = pk.nelem;
   for (int i = m.t0; i < Ep; i += m.ts) {
     const int r = m.erod[i];
-    const RodConst* rc = P.rods + pk.rod0 + r;
+    const RodConst* rc = P.rods + m.grod[r];
     const int j = i + r;
-    const int ge = pk.elem0 + i;
+    const int ge = i + m.dE[r];
     double l[3], dv[3], q[9], w[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -347,9 +354,9 @@ __device__ __forceinline__ void stage_voronoi(const StepParams& P, const Pack& p
   const int Vp = pk.nvor;
   for (int k = m.t0; k < Vp; k += m.ts) {
     const int r = m.vrod[k];
-    const RodConst* rc = P.rods + pk.rod0 + r;
+    const RodConst* rc = P.rods + m.grod[r];
     const int i = k + r;
-    const int gv = pk.vor0 + k;
+    const int gv = k + m.dV[r];
     double qa[9], qb[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
@@ -411,7 +418,8 @@ __device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& 
   const int Ep = pk.nelem;
   for (int i = m.t0; i < Ep; i += m.ts) {
     const int r = m.erod[i];
-    const int g = pk.rod0 + r;
+    const int g = m.grod[r];
+    const int ge = i + m.dE[r];
     const RodConst* rc = P.rods + g;
     const int first = m.rel0[r];
     const int nr = m.rel0[r + 1] - first;
@@ -429,12 +437,12 @@ __device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& 
     }
     const bool held = (li == 0) && rc->clamp;
     if (MODE == MODE_RHS) {
-      const double ke = m.EDIL[i] * __ldg(P.inv_rl + pk.elem0 + i);
+      const double ke = m.EDIL[i] * __ldg(P.inv_rl + ge);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) acc_w[c * P.E + pk.elem0 + i] = held ? 0.0 : ke * __ldg(&rc->inv_rhoI[c]) * tau[c];
+      for (int c = 0; c < 3; ++c) acc_w[c * P.E + ge] = held ? 0.0 : ke * __ldg(&rc->inv_rhoI[c]) * tau[c];
     } else {
       // w += dt e J^{-1} tau,  J^{-1} = 1/(rho I rl)
-      const double ke = (dt * m.EDIL[i]) * __ldg(P.inv_rl + pk.elem0 + i);
+      const double ke = (dt * m.EDIL[i]) * __ldg(P.inv_rl + ge);
 #pragma unroll
       for (int c = 0; c < 3; ++c)
         m.WW[c * m.CE + i] = held ? 0.0 : fma(ke * __ldg(&rc->inv_rhoI[c]), tau[c], m.WW[c * m.CE + i]);
@@ -452,7 +460,8 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
   const double dtg[3] = {dt * P.gravity[0], dt * P.gravity[1], dt * P.gravity[2]};
   for (int j = m.t0; j < Np; j += m.ts) {
     const int r = m.nrod[j];
-    const int g = pk.rod0 + r;
+    const int g = m.grod[r];
+    const int gn = j + m.dN[r];
     const RodConst* rc = P.rods + g;
     const int firstn = m.rel0[r] + r;
     const int nr = m.rel0[r + 1] - m.rel0[r];
@@ -460,12 +469,12 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
     const bool hasR = lj < nr, hasL = lj > 0;
     const int iR = j - r;                    // element to the right (pack-local)
     const bool held = (lj == 0) && rc->clamp;
-    const double im = __ldg(P.inv_m + pk.node0 + j);
+    const double im = __ldg(P.inv_m + gn);
     const double dl = __ldg(&rc->damp_lin);
     double F[3];
     if (P.fseg) {
       // contact: node a of segment iR and node b of segment iR-1, folded into the difference
-      const int ge = pk.elem0 + iR;
+      const int ge = iR + m.dE[r];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const double Nr = hasR ? m.NF[c * m.CE + iR] : 0.0;
@@ -514,7 +523,7 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
         const double vj = m.VN[c * m.CN + j];
         double a = fma(F[c], im, -dl * vj);
         if (P.has_gravity) a += P.gravity[c];
-        acc_v[c * P.N + pk.node0 + j] = held ? 0.0 : a;
+        acc_v[c * P.N + gn] = held ? 0.0 : a;
       }
     } else {
       // v += dt (F/m - c v + g)  as  v (1 - dt c) + (dt/m) F + dt g
@@ -543,7 +552,7 @@ __device__ __forceinline__ void time_values(const StepParams& P, const Pack& pk,
   const int rev = m.ts - 1 - m.t0;
   if (P.has_act) {
     for (int r = rev; r < pk.nrods; r += m.ts) {
-      const RodConst* rc = P.rods + pk.rod0 + r;
+      const RodConst* rc = P.rods + m.grod[r];
       const double amp = rc->act_amp;
       m.ACT[r] = (amp != 0.0) ? amp * sin(fma(rc->act_omega, t, rc->act_phase)) : 0.0;
     }
@@ -568,15 +577,33 @@ __device__ __forceinline__ void actuation_values(const StepParams& P, const Pack
 // Copy a pack's state and constants into shared memory and build the item -> rod maps.
 __device__ __forceinline__ void stage_pack(const StepParams& P, const Pack& pk, Smem& m) {
   const int Ep = pk.nelem, Np = pk.nnode, Rp = pk.nrods, Vp = pk.nvor;
-  for (int r = m.t0; r < Rp; r += m.ts) m.rel0[r] = P.rods[pk.rod0 + r].elem0 - pk.elem0;
+  for (int r = m.t0; r < Rp; r += m.ts) {
+    int g, rel;
+    if (pk.listed) {
+      const int2 e = P.pack_rods[pk.list_off + r];
+      g = e.x;
+      rel = e.y;
+    } else {
+      g = pk.rod0 + r;
+      rel = P.rods[g].elem0 - pk.elem0;
+    }
+    const RodConst& rc = P.rods[g];
+    m.rel0[r] = rel;
+    m.grod[r] = g;
+    m.dE[r] = rc.elem0 - rel;
+    m.dN[r] = rc.node0 - rel - r;
+    m.dV[r] = rc.elem0 - g - rel + r;
+  }
   if (m.t0 == 0) m.rel0[Rp] = Ep;
   stage_sync(m);
   for (int i = m.t0; i < Ep; i += m.ts) {
-    m.erod[i] = (short)find_rod(m.rel0, Rp, i);
+    const int r = find_rod(m.rel0, Rp, i);
+    const int ge = i + m.dE[r];
+    m.erod[i] = (short)r;
 #pragma unroll
-    for (int a = 0; a < 9; ++a) m.QQ[a * m.CE + i] = P.Q[a * P.E + pk.elem0 + i];
+    for (int a = 0; a < 9; ++a) m.QQ[a * m.CE + i] = P.Q[a * P.E + ge];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) m.WW[c * m.CE + i] = P.w[c * P.E + pk.elem0 + i];
+    for (int c = 0; c < 3; ++c) m.WW[c * m.CE + i] = P.w[c * P.E + ge];
   }
   for (int j = m.t0; j < Np; j += m.ts) {
     // node j belongs to rod r with rel0[r] + r <= j
@@ -586,10 +613,11 @@ __device__ __forceinline__ void stage_pack(const StepParams& P, const Pack& pk, 
       if (m.rel0[mid] + mid <= j) lo = mid; else hi = mid - 1;
     }
     m.nrod[j] = (short)lo;
+    const int gn = j + m.dN[lo];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      m.X[c * m.CN + j] = P.x[c * P.N + pk.node0 + j];
-      m.VN[c * m.CN + j] = P.v[c * P.N + pk.node0 + j];
+      m.X[c * m.CN + j] = P.x[c * P.N + gn];
+      m.VN[c * m.CN + j] = P.v[c * P.N + gn];
     }
   }
   for (int k = m.t0; k < Vp; k += m.ts) {

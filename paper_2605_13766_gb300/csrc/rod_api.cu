@@ -279,8 +279,10 @@ rod_status build_packs(rod_system* s, const LaunchShape& shape) {
   if (open) packs.push_back(cur);
   // Rods of mixed lengths leave the consecutive packs part empty (a block's element loops run
   // over cap_elems threads whatever the pack holds).  Best-fit decreasing over the same rods
-  // fills them closer to the capacity; it is kept when it needs fewer packs.  Its packs list
-  // their rods (global rod, first pack-local element) unless the rods happen to be consecutive.
+  // fills them closer to the capacity; it is kept when it needs fewer packs.  It counts a rod's
+  // nodes (n + 1), so a full pack's node loops make no second pass for a few nodes when the
+  // block has as many threads as the capacity.  Its packs list their rods (global rod, first
+  // pack-local element) unless the rods happen to be consecutive.
   std::vector<int2> list;
   {
     std::vector<int> order;
@@ -290,9 +292,9 @@ rod_status build_packs(rod_system* s, const LaunchShape& shape) {
                      [&](int a, int b) { return s->rods_h[a].n > s->rods_h[b].n; });
     std::vector<std::vector<int>> bins;
     std::vector<int> room;
-    std::multiset<std::pair<int, int>> open_bins;  // (free elements, bin), bins below cap_rods
+    std::multiset<std::pair<int, int>> open_bins;  // (free node slots, bin), bins below cap_rods
     for (int r : order) {
-      const int n = s->rods_h[r].n;
+      const int n = s->rods_h[r].n + 1;
       auto it = open_bins.lower_bound({n, -1});
       int b;
       if (it == open_bins.end()) {

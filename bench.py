@@ -43,21 +43,21 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 # Algorithmic FP64 flops per unit of each kernel: the FP64 arithmetic of the formulas as the
 # kernel evaluates them, counted by ncu on the active threads (add/sub/mul = 1 flop, fma = 2),
 # divided by the units of the launch.  pack_one_step: one launch of pack_kernel<3> on the
-# 10^4-rod packing, 159.27M DFMA + 36.13M DADD + 121.92M DMUL on 1,366,295 element-steps
+# 10^4-rod packing, 156.95M DFMA + 37.07M DADD + 121.45M DMUL on 1,366,295 element-steps
 # (profiles/pack_kernel_one_step_packing_10k.md).  pack_steps: one 20-step launch of
 # pack_kernel<0> on the 64 x 64 carpet, 465.37M DFMA + 82.90M DADD + 367.68M DMUL on 4,096,000
 # element-steps (profiles/pack_kernel_steps_carpet_4096.md).
 FLOPS_PER_UNIT = {
-    "pack_one_step": 348.8,   # per element-step
+    "pack_one_step": 345.8,   # per element-step
     "pack_steps": 337.2,      # per element-step
 }
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of one capture of the
-# current kernel; reset to None whenever the kernel changes.  pack_one_step: the launch of step
-# ~290 of the bench's timed steps (dense contact), profiles/contact_list_force_packing_10k.md.
+# current kernel; reset to None whenever the kernel changes.  pack_one_step: the third launch of
+# the bench's steps at its autotuned 256 x 256 shape, profiles/pack_kernel_one_step_packing_10k.md.
 # The carpet's state stays on chip between the steps of a launch: its traffic is one read of
 # the state and constants per launch (the written state is still in L2 when the launch ends).
 TRAFFIC_PER_LAUNCH = {
-    "pack_one_step": 336.42e6 + 188.58e6,
+    "pack_one_step": 356.06e6 + 152.13e6,
     "pack_steps": 39.28e6,
 }
 

@@ -185,6 +185,13 @@ rod_status rod_system_contact_forces(rod_system* sys, double* f);
 rod_status rod_system_set_launch(rod_system* sys, int32_t elems_per_block, int32_t threads_per_block);
 rod_status rod_system_get_launch(const rod_system* sys, int32_t* elems_per_block, int32_t* threads_per_block);
 
+/* How the current launch shape packs the rods into thread blocks: the number of block packs,
+ * how many of them list their rods (best-fit-decreasing packs of rods that are not consecutive
+ * in index order; the others hold a consecutive run of rods), and the number of rods longer
+ * than a block holds (one cooperative launch each).  Any output may be null.  Host-side only:
+ * no device work, no synchronisation. */
+rod_status rod_system_pack_info(const rod_system* sys, int32_t* n_packs, int32_t* n_listed, int32_t* n_long);
+
 /* Differentiation (hand-written adjoint of the step; rod-rod contact must be off: its state
  * derivatives are not in the reverse sweep; the magnetic couple and walls (normal force and
  * friction, piecewise smooth: derivatives of the active branch) are covered, muscle couples

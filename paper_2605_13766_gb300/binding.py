@@ -102,6 +102,7 @@ _SIGNATURES = {
     "rod_system_contact_forces": ([_P, _P], C.c_int),
     "rod_system_set_launch": ([_P, C.c_int32, C.c_int32], C.c_int),
     "rod_system_get_launch": ([_P, _P, _P], C.c_int),
+    "rod_system_pack_info": ([_P, _P, _P, _P], C.c_int),
     "rod_system_set_graphs": ([_P, C.c_int], C.c_int),
     "rod_system_set_params": ([_P, _P, _P, C.c_int], C.c_int),
     "rod_system_autotune": ([_P, C.c_double, C.c_int32, _P, _P, _P], C.c_int),
@@ -445,6 +446,12 @@ class RodSystem:
         e, t = C.c_int32(), C.c_int32()
         _check(self.lib.rod_system_get_launch(self.handle, C.byref(e), C.byref(t)))
         return e.value, t.value
+
+    def pack_info(self):
+        """(block packs, of which list their rods, rods on the cooperative path)."""
+        n, l, g = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(self.lib.rod_system_pack_info(self.handle, C.byref(n), C.byref(l), C.byref(g)))
+        return n.value, l.value, g.value
 
 
 class Surrogate:

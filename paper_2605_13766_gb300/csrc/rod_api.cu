@@ -187,7 +187,7 @@ struct rod_system {
   LaunchShape shape{0, 0, 0};
   DevBuf<Pack> packs;
   DevBuf<int2> pack_rods;  // (global rod, first pack-local element) of the rods of listed packs
-  int n_packs = 0;
+  int n_packs = 0, n_listed = 0;
   // rods longer than a block holds: one pack each, run by cooperative launches with their
   // working arrays in long_scratch
   std::vector<Pack> long_packs;
@@ -350,6 +350,7 @@ rod_status build_packs(rod_system* s, const LaunchShape& shape) {
     CUDA_TRY(cudaMemcpy(s->packs.p, packs.data(), packs.size() * sizeof(Pack), cudaMemcpyHostToDevice));
   }
   s->n_packs = static_cast<int>(packs.size());
+  s->n_listed = static_cast<int>(std::count_if(packs.begin(), packs.end(), [](const Pack& p) { return p.listed != 0; }));
   s->long_packs = longs;
   if (scratch > 0 && (int64_t)s->long_scratch.n * 8 < (int64_t)scratch)
     CUDA_TRY(s->long_scratch.alloc((scratch + 7) / 8));
@@ -1389,6 +1390,14 @@ rod_status rod_system_get_launch(const rod_system* s, int32_t* elems_per_block, 
   if (!s) return fail(ROD_ERR_ARG, "null system");
   if (elems_per_block) *elems_per_block = s->shape.cap_elems;
   if (threads_per_block) *threads_per_block = s->shape.threads;
+  return ROD_OK;
+}
+
+rod_status rod_system_pack_info(const rod_system* s, int32_t* n_packs, int32_t* n_listed, int32_t* n_long) {
+  if (!s) return fail(ROD_ERR_ARG, "null system");
+  if (n_packs) *n_packs = s->n_packs;
+  if (n_listed) *n_listed = s->n_listed;
+  if (n_long) *n_long = static_cast<int32_t>(s->long_packs.size());
   return ROD_OK;
 }
 

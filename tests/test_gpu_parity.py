@@ -117,6 +117,27 @@ def test_trajectory_1000_steps(name, p, dt):
     assert _rel(got[1], ref[1]) <= 1e-7
 
 
+def test_listed_packs_match_the_oracle():
+    """Rods of mixed lengths at 256 node slots per block: best fit needs fewer packs than
+    packing in index order, so the packs list rods that are not consecutive.  The right-hand
+    side and a 1000-step trajectory stay at the oracle's bars.  Equal rods keep consecutive packs."""
+    p = _mixed_rods()
+    s = _gpu(p, (256, 128))
+    n_packs, n_listed, n_long = s.pack_info()
+    assert n_listed > 0 and n_long == 0
+    pr = rodgen.perturbed(p, seed=4, pos=0.01, rot=0.05)
+    av_ref, aw_ref = Oracle(pr).rhs(*pr.state(), t=0.05)
+    av, aw = (a.cpu().numpy() for a in _gpu(pr, (256, 128)).rhs(0.05))
+    assert _rel(av, av_ref) <= RHS_TOL and _rel(aw, aw_ref) <= RHS_TOL
+    ref, got = _traj(p, 1000, 2e-6, shape=(256, 128))
+    L = max(p.rest_len[p.elem_offsets()[r]:p.elem_offsets()[r + 1]].sum() for r in range(p.n_rods))
+    assert np.abs(got[0] - ref[0]).max() / L <= POS_TOL
+    assert _rel(got[2], ref[2]) <= 1e-9
+    assert _rel(got[1], ref[1]) <= 1e-7
+    c = _gpu(rodgen.cilia_carpet(side=4, n=50), (384, 192))
+    assert c.pack_info()[1] == 0
+
+
 def test_chunked_steps_equal_one_call():
     p = rodgen.perturbed(rodgen.cilia_carpet(side=3, n=50), seed=8)
     s1 = _gpu(p)

@@ -371,6 +371,7 @@ def main():
         tuned = {"elems_per_block": te, "threads_per_block": tt, "trial_ms_per_step": tms}
     s.step(W, dt)
     torch.cuda.synchronize()
+    diag0 = s.diagnostics(per_rod=False)[1]   # energy parts and orthonormality before the timed steps
 
     # ---- timed region (device time, CUDA events on the stream the library launches on)
     stream = s.torch_stream
@@ -395,6 +396,13 @@ def main():
     t_local = ms / 1e3
     t_max = slowest(t_local)
     value = total(p.n_elems * K) / t_max
+    diag1 = s.diagnostics(per_rod=False)[1]
+    diag = {"energy_before": float(diag0[:5].sum()), "energy_after": float(diag1[:5].sum()),
+            "energy_parts_after": [float(e) for e in diag1[:5]],
+            "max_orthonormality_error_after": float(diag1[5]),
+            "note": "energy of the timed steps' first and last states (kinetic, strain, work potential of "
+                    "gravity and tip forces; contact, damping and drag dissipate); parts: translational, "
+                    "rotational, shear/stretch, bend/twist, potential"}
 
     # ---- per-kernel device times: the same K steps again with CUDA events around every launch
     # (eager launches: the event pairs sit between kernels on the same stream)
@@ -444,7 +452,7 @@ def main():
                                l2="state (196 MB) larger than L2, no flush needed" if args.workload == "packing"
                                else "state L2/smem resident"),
                 "clocks": clk, "gpu_launches": launches, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
-                "surrogate": sur, "adjoint": adj}
+                "surrogate": sur, "adjoint": adj, "diagnostics": diag}
         print(json.dumps(line), flush=True)
     s.close()
     if dist is not None:

@@ -185,6 +185,24 @@ rod_status rod_system_contact_forces(rod_system* sys, double* f);
 rod_status rod_system_set_launch(rod_system* sys, int32_t elems_per_block, int32_t threads_per_block);
 rod_status rod_system_get_launch(const rod_system* sys, int32_t* elems_per_block, int32_t* threads_per_block);
 
+/* Energy and frame diagnostics of the current state (Methods: the Cosserat rod of Eq. 1; the
+ * energy the explicit symplectic step conserves without damping and loads).  One warp per rod.
+ * per_rod: device [6*R] (row c holds component c of every rod) or NULL:
+ *   0  translational kinetic energy, sum over the rod's nodes of 1/2 m |v|^2
+ *   1  rotational kinetic energy, sum over its elements of 1/2 rho I_c rl w_c^2
+ *   2  shear/stretch energy, sum over its elements of 1/2 rl S_c (sigma_c - sigma0_c)^2 with
+ *      sigma = Q (x_{i+1} - x_i) / rl - (0, 0, 1) in the element's frame
+ *   3  bend/twist energy, sum over its Voronoi points of 1/2 D B_c (kappa_c - kappa0_c)^2 with
+ *      kappa = -log(Q_{k+1} Q_k^T) / D, D the mean of the two rest lengths
+ *   4  work potential: -sum m g . x over its nodes - F_tip . x_tip
+ *   5  largest entry of |Q Q^T - I| over its elements (orthonormality of the directors)
+ * totals: host [6] or NULL: rows 0-4 summed over the rods, row 5 maximised (a fixed order: the
+ * same bits on every call).  Contact, walls, fields, actuation and damping hold no potential
+ * here.  With totals the call synchronises on the system's stream; otherwise it only enqueues
+ * (2 kernels with totals, 1 without; counted by rod_system_launch_count).  ROD_ERR_STATE
+ * without a state. */
+rod_status rod_system_diagnostics(rod_system* sys, double* per_rod, double* totals);
+
 /* How the current launch shape packs the rods into thread blocks: the number of block packs,
  * how many of them list their rods (best-fit-decreasing packs of rods that are not consecutive
  * in index order; the others hold a consecutive run of rods), and the number of rods longer

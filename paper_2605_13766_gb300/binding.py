@@ -103,6 +103,7 @@ _SIGNATURES = {
     "rod_system_set_launch": ([_P, C.c_int32, C.c_int32], C.c_int),
     "rod_system_get_launch": ([_P, _P, _P], C.c_int),
     "rod_system_pack_info": ([_P, _P, _P, _P], C.c_int),
+    "rod_system_diagnostics": ([_P, _P, _P], C.c_int),
     "rod_system_set_graphs": ([_P, C.c_int], C.c_int),
     "rod_system_set_params": ([_P, _P, _P, C.c_int], C.c_int),
     "rod_system_autotune": ([_P, C.c_double, C.c_int32, _P, _P, _P], C.c_int),
@@ -446,6 +447,24 @@ class RodSystem:
         e, t = C.c_int32(), C.c_int32()
         _check(self.lib.rod_system_get_launch(self.handle, C.byref(e), C.byref(t)))
         return e.value, t.value
+
+    def diagnostics(self, per_rod: bool = True):
+        """Energy parts and director orthonormality of the current state.
+
+        Returns (rows, totals): rows a [6, R] device tensor (translational kinetic, rotational
+        kinetic, shear/stretch, bend/twist, work potential, max |Q Q^T - I| per rod) or None, and
+        totals a numpy array of 6 (rows 0-4 summed, row 5 maximised)."""
+        import torch
+        rows = torch.empty((6, self.n_rods), dtype=torch.float64, device="cuda") if per_rod else None
+        tot = np.zeros(6)
+        # with totals the call synchronises the system's stream, so the rows are complete on return
+        _check(self.lib.rod_system_diagnostics(self.handle, rows.data_ptr() if rows is not None else None,
+                                               tot.ctypes.data_as(C.c_void_p)))
+        return rows, tot
+
+    def energy(self) -> float:
+        """Total energy: kinetic + strain energy + work potential of gravity and tip forces."""
+        return float(self.diagnostics(per_rod=False)[1][:5].sum())
 
     def pack_info(self):
         """(block packs, of which list their rods, rods on the cooperative path)."""

@@ -21,6 +21,7 @@
 #include "../../include/rod.h"
 #include "rod_adjoint.h"
 #include "rod_contact.h"
+#include "rod_diag.h"
 #include "rod_internal.h"
 #include "rod_sysview.h"
 
@@ -187,6 +188,7 @@ struct rod_system {
   LaunchShape shape{0, 0, 0};
   DevBuf<Pack> packs;
   DevBuf<int2> pack_rods;  // (global rod, first pack-local element) of the rods of listed packs
+  DevBuf<double> diag_rows, diag_tot;  // rod_system_diagnostics scratch: [6][R], [6]
   int n_packs = 0, n_listed = 0;
   // rods longer than a block holds: one pack each, run by cooperative launches with their
   // working arrays in long_scratch
@@ -340,6 +342,8 @@ rod_status build_packs(rod_system* s, const LaunchShape& shape) {
     CUDA_TRY(cudaMemcpy(s->pack_rods.p, list.data(), list.size() * sizeof(int2), cudaMemcpyHostToDevice));
   } else {
     s->pack_rods.release();
+  s->diag_rows.release();
+  s->diag_tot.release();
   }
   // heaviest packs first (blocks start roughly in index order): the last, partly filled wave of
   // blocks then holds the lightest packs, which shortens the tail of every launch
@@ -1390,6 +1394,44 @@ rod_status rod_system_get_launch(const rod_system* s, int32_t* elems_per_block, 
   if (!s) return fail(ROD_ERR_ARG, "null system");
   if (elems_per_block) *elems_per_block = s->shape.cap_elems;
   if (threads_per_block) *threads_per_block = s->shape.threads;
+  return ROD_OK;
+}
+
+rod_status rod_system_diagnostics(rod_system* s, double* per_rod, double* totals) {
+  if (!s) return fail(ROD_ERR_ARG, "null system");
+  if (!s->state_set) return fail(ROD_ERR_STATE, "no state has been set");
+  if (!per_rod && !totals) return ROD_OK;
+  DiagArgs A;
+  A.x = s->x.p;
+  A.v = s->v.p;
+  A.Q = s->Q.p;
+  A.w = s->w.p;
+  A.rest_len = s->rest_len.p;
+  A.inv_m = s->inv_m.p;
+  A.rest_sigma = s->rest_sigma.p;
+  A.rest_kappa = s->rest_kappa.p;
+  A.rods = s->rods.p;
+  A.N = s->N;
+  A.E = s->E;
+  A.V = s->V;
+  A.R = s->R;
+  for (int c = 0; c < 3; ++c) A.gravity[c] = s->has_gravity ? s->gravity[c] : 0.0;
+  if (!per_rod) {
+    if ((int64_t)s->diag_rows.n < 6 * (int64_t)s->R) CUDA_TRY(s->diag_rows.alloc(6 * (size_t)s->R));
+    per_rod = s->diag_rows.p;
+  }
+  A.per_rod = per_rod;
+  if (totals && !s->diag_tot.p) CUDA_TRY(s->diag_tot.alloc(6));
+  s->hook.before(K_MISC, s->stream);
+  CUDA_TRY(launch_diag_rows(A, s->stream));
+  s->hook.after(K_MISC, s->stream);
+  if (totals) {
+    s->hook.before(K_MISC, s->stream);
+    CUDA_TRY(launch_diag_totals(per_rod, s->R, s->diag_tot.p, s->stream));
+    s->hook.after(K_MISC, s->stream);
+    CUDA_TRY(cudaMemcpyAsync(totals, s->diag_tot.p, 6 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+  }
   return ROD_OK;
 }
 

@@ -42,7 +42,6 @@ struct RodConst {
 
 constexpr int kMaxWalls = 8;
 
-// A pack: consecutive rods processed by one thread block.
 // A thread block's share of the ensemble: consecutive rods (listed = 0: rod0.. and the global
 // first element, node and Voronoi point), or any rods (listed = 1: entries list_off ..
 // list_off + nrods of StepParams::pack_rods), with the pack's element, node and Voronoi counts.

@@ -400,9 +400,10 @@ def main():
     diag = {"energy_before": float(diag0[:5].sum()), "energy_after": float(diag1[:5].sum()),
             "energy_parts_after": [float(e) for e in diag1[:5]],
             "max_orthonormality_error_after": float(diag1[5]),
-            "note": "energy of the timed steps' first and last states (kinetic, strain, work potential of "
-                    "gravity and tip forces; contact, damping and drag dissipate); parts: translational, "
-                    "rotational, shear/stretch, bend/twist, potential"}
+            "note": "energy of the timed steps' first and last states: kinetic, strain, work potential of "
+                    "gravity and tip forces (the contact springs' stored energy is not in the sum and "
+                    "moves energy into or out of it; damping, drag and the dashpot dissipate); parts: "
+                    "translational, rotational, shear/stretch, bend/twist, potential"}
 
     # ---- per-kernel device times: the same K steps again with CUDA events around every launch
     # (eager launches: the event pairs sit between kernels on the same stream)

@@ -68,7 +68,10 @@ def test_long_rods_rhs_matches_oracle():
     p = _mixed_long()
     t = 0.0123
     av_ref, aw_ref = Oracle(p).rhs(*p.state(), t=t)
-    av, aw = (a.cpu().numpy() for a in _gpu(p).rhs(t))
+    s = _gpu(p)
+    # the two long rods run cooperatively; the four short ones share one listed pack
+    assert s.pack_info() == (1, 1, 2)
+    av, aw = (a.cpu().numpy() for a in s.rhs(t))
     assert _rel(av, av_ref) <= 1e-12, _rel(av, av_ref)
     assert _rel(aw, aw_ref) <= 1e-12, _rel(aw, aw_ref)
 

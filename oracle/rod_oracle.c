@@ -909,8 +909,8 @@ double orc_energy(const orc_params* p, const double* x, const double* v, const d
       double vj[3], xj[3];
       ld3(v, N, jn, vj);
       ld3(x, N, jn, xj);
-      H += 0.5 * mass * dot3(vj, vj);
-      H -= mass * dot3(p->gravity, xj);
+      H += (g_mut == 30 ? 1.0 : 0.5) * mass * dot3(vj, vj);
+      H -= (g_mut == 29 ? -1.0 : 1.0) * mass * dot3(p->gravity, xj);
       if (p->tip_force && j == g.n) {
         double F[3] = {p->tip_force[r], p->tip_force[p->n_rods + r], p->tip_force[2 * p->n_rods + r]};
         H -= dot3(F, xj);
@@ -922,13 +922,13 @@ double orc_energy(const orc_params* p, const double* x, const double* v, const d
       for (int c = 0; c < 3; ++c) {
         double wc = w[c * E + ie];
         double sc = sig[c * E + ie] - (p->rest_sigma ? p->rest_sigma[c * E + ie] : 0.0);
-        H += 0.5 * K.rho * rl * K.I[c] * wc * wc;
-        H += 0.5 * rl * K.S[c] * sc * sc;
+        H += 0.5 * K.rho * rl * K.I[g_mut == 27 ? 0 : c] * wc * wc;
+        H += 0.5 * rl * K.S[g_mut == 28 ? 2 : c] * sc * sc;
       }
     }
     for (int k = 0; k < g.n - 1; ++k) {
       int64_t iv = g.vor0 + k;
-      double D = 0.5 * (p->rest_len[g.elem0 + k] + p->rest_len[g.elem0 + k + 1]);
+      double D = (g_mut == 26) ? p->rest_len[g.elem0 + k] : 0.5 * (p->rest_len[g.elem0 + k] + p->rest_len[g.elem0 + k + 1]);
       for (int c = 0; c < 3; ++c) {
         double kc = kap[c * V + iv] - (p->rest_kappa ? p->rest_kappa[c * V + iv] : 0.0);
         H += 0.5 * D * K.B[c] * kc * kc;

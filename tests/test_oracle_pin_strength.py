@@ -12,6 +12,7 @@ from oracle.oracle import set_mutation
 
 import test_oracle_contact as tc
 import test_oracle_dynamics as td
+import test_oracle_energy as te
 import test_oracle_more_pins as tm
 import test_oracle_next_rows as tn
 import test_oracle_rotations as tr
@@ -37,6 +38,11 @@ PINS = [
     tn.test_segment_resting_on_a_wall_sinks_by_mg_over_k,
     tn.test_sliding_on_a_wall_decelerates_at_mu_g,
     tn.test_sliding_crossing_feels_coulomb_friction,
+    te.test_rigid_translation,
+    te.test_uniform_angular_velocity,
+    te.test_uniform_shear_and_stretch,
+    te.test_uniform_bending,
+    te.test_gravity_and_tip_force_potential,
 ]
 
 MUTATIONS = {
@@ -62,6 +68,11 @@ MUTATIONS = {
     23: "muscle couples tau_i - tau_{i-1} instead of tau_{i-1} - tau_i",
     24: "wall contact without the rod radius",
     25: "friction along the sliding direction instead of against it",
+    26: "energy: bend/twist term over one element's rest length instead of the Voronoi length",
+    27: "energy: rotational kinetic term with I_1 about every axis",
+    28: "energy: shear terms with the axial stiffness E A",
+    29: "energy: work potential of gravity with the wrong sign",
+    30: "energy: translational kinetic term without the 1/2",
 }
 
 

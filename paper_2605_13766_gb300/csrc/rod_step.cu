@@ -1,6 +1,7 @@
 // rod_step.cu -- FP64 step kernels of the discrete Cosserat-rod method for sm_103a.
 //
-// One thread block owns a "pack" of consecutive rods (CSR order) and stages their nodes,
+// One thread block owns a "pack" of rods (a consecutive run in CSR order, or rods listed by
+// the best-fit packer, each with its offsets into the global arrays) and stages their nodes,
 // directors and work arrays in shared memory, so that the difference (Delta^h) and averaging
 // (A^h) operators of Eq. 1 read their neighbours on chip; ghost values at the rod ends are the
 // zeros of the discrete operators.  Without contact the rods are independent, so a block runs

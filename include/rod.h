@@ -210,6 +210,22 @@ rod_status rod_system_diagnostics(rod_system* sys, double* per_rod, double* tota
  * no device work, no synchronisation. */
 rod_status rod_system_pack_info(const rod_system* sys, int32_t* n_packs, int32_t* n_listed, int32_t* n_long);
 
+/* The packing rod_system_set_launch makes for elems_per_block = cap_elems and a rods-per-block
+ * limit cap_rods, computed on the host (no GPU, no system) for inspection and tests.
+ * n_elem [n_rods]: elements per rod (>= 1), rods stored one after another (elements, nodes and
+ * Voronoi points numbered rod by rod).  Outputs, each may be null:
+ *   n_packs, n_list, n_long: block packs, entries of the rod list, rods longer than cap_elems
+ *     (those run one cooperative launch each and are in no block pack);
+ *   packs [10 * n_packs], in launch order (heaviest first), per pack: first rod, rods, first
+ *     element, elements, first node, nodes, first Voronoi point, Voronoi points (the four
+ *     "first" values are the first rod's when the pack lists its rods), listed (0: the rods
+ *     first rod .. first rod + rods - 1; 1: the rods of list entries list_off ..), list_off;
+ *   list [2 * n_list]: (global rod, the rod's first element within its pack).
+ * Call with null packs and list to learn the sizes.  ROD_ERR_ARG for a rod without elements
+ * or a capacity below 1. */
+rod_status rod_plan_packs(const int32_t* n_elem, int32_t n_rods, int32_t cap_elems, int32_t cap_rods,
+                          int32_t* n_packs, int32_t* n_list, int32_t* n_long, int32_t* packs, int32_t* list);
+
 /* Differentiation (hand-written adjoint of the step; rod-rod contact must be off: its state
  * derivatives are not in the reverse sweep; the magnetic couple and walls (normal force and
  * friction, piecewise smooth: derivatives of the active branch) are covered, muscle couples

@@ -103,6 +103,7 @@ _SIGNATURES = {
     "rod_system_set_launch": ([_P, C.c_int32, C.c_int32], C.c_int),
     "rod_system_get_launch": ([_P, _P, _P], C.c_int),
     "rod_system_pack_info": ([_P, _P, _P, _P], C.c_int),
+    "rod_plan_packs": ([_P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, _P, _P], C.c_int),
     "rod_system_diagnostics": ([_P, _P, _P], C.c_int),
     "rod_system_set_graphs": ([_P, C.c_int], C.c_int),
     "rod_system_set_params": ([_P, _P, _P, C.c_int], C.c_int),
@@ -624,6 +625,25 @@ def contact_forces_noalloc(node_off, radius, x, v, k: float, c: float, cell_size
     _check(lib.rod_contact_forces_noalloc(int(radius.shape[0]), node_off.data_ptr(), radius.data_ptr(),
                                           x.data_ptr(), v.data_ptr(), float(k), float(c), float(cell_size),
                                           f.data_ptr(), stream))
+
+
+def plan_packs(n_elem, cap_elems: int, cap_rods: int) -> dict:
+    """The thread-block packing of rods with these element counts for a launch shape of
+    cap_elems elements and at most cap_rods rods per block (rod_plan_packs; host only, no GPU).
+    Returns {"packs": int32 [n_packs, 10] (first rod, rods, first element, elements, first node,
+    nodes, first Voronoi point, Voronoi points, listed, list offset) in launch order,
+    "list": int32 [n_list, 2] (global rod, first pack-local element), "n_long": rods on the
+    cooperative path}."""
+    lib = load_library()
+    n = np.ascontiguousarray(n_elem, dtype=np.int32)
+    npk, nl, ng = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib.rod_plan_packs(n.ctypes.data, int(n.size), int(cap_elems), int(cap_rods), C.byref(npk), C.byref(nl),
+                              C.byref(ng), None, None))
+    packs = np.zeros((npk.value, 10), dtype=np.int32)
+    lst = np.zeros((nl.value, 2), dtype=np.int32)
+    _check(lib.rod_plan_packs(n.ctypes.data, int(n.size), int(cap_elems), int(cap_rods), None, None, None,
+                              packs.ctypes.data if packs.size else None, lst.ctypes.data if lst.size else None))
+    return {"packs": packs, "list": lst, "n_long": ng.value}
 
 
 def exported_symbols():

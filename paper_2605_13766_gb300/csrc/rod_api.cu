@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -230,15 +231,25 @@ struct rod_system {
 
 namespace {
 
-rod_status build_packs(rod_system* s, const LaunchShape& shape) {
+// Thread-block packs of an ensemble for one launch shape: rods longer than cap_elems get a
+// cooperative pack each (longs); the others are packed consecutively in index order, or by
+// best-fit decreasing when that needs fewer packs, whose packs then list their rods (global
+// rod, first pack-local element) in list.  Host only; packs come heaviest first.
+struct PackPlan {
   std::vector<Pack> packs, longs;
+  std::vector<int2> list;
+};
+
+PackPlan plan_packs(const std::vector<RodConst>& rods, int cap_elems, int cap_rods) {
+  PackPlan plan;
+  std::vector<Pack>& packs = plan.packs;
+  const int R = static_cast<int>(rods.size());
   Pack cur{};
   bool open = false;
-  size_t scratch = 0;
-  for (int r = 0; r < s->R; ++r) {
-    const RodConst& rc = s->rods_h[r];
+  for (int r = 0; r < R; ++r) {
+    const RodConst& rc = rods[r];
     const int n = rc.n;
-    if (n > shape.cap_elems) {
+    if (n > cap_elems) {
       // too long for a block: a pack of its own on the cooperative (grid-wide) path
       if (open) {
         packs.push_back(cur);
@@ -253,15 +264,10 @@ rod_status build_packs(rod_system* s, const LaunchShape& shape) {
       lp.nnode = n + 1;
       lp.vor0 = rc.elem0 - r;
       lp.nvor = n - 1;
-      longs.push_back(lp);
-      LaunchShape ls;
-      ls.cap_elems = n;
-      ls.cap_rods = 1;
-      ls.threads = 256;
-      scratch = std::max(scratch, step_smem_bytes(ls));
+      plan.longs.push_back(lp);
       continue;
     }
-    if (open && (cur.nelem + n > shape.cap_elems || cur.nrods + 1 > shape.cap_rods)) {
+    if (open && (cur.nelem + n > cap_elems || cur.nrods + 1 > cap_rods)) {
       packs.push_back(cur);
       open = false;
     }
@@ -285,49 +291,47 @@ rod_status build_packs(rod_system* s, const LaunchShape& shape) {
   // nodes (n + 1), so a full pack's node loops make no second pass for a few nodes when the
   // block has as many threads as the capacity.  Its packs list their rods (global rod, first
   // pack-local element) unless the rods happen to be consecutive.
-  std::vector<int2> list;
   {
     std::vector<int> order;
-    for (int r = 0; r < s->R; ++r)
-      if (s->rods_h[r].n <= shape.cap_elems) order.push_back(r);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return s->rods_h[a].n > s->rods_h[b].n; });
+    for (int r = 0; r < R; ++r)
+      if (rods[r].n <= cap_elems) order.push_back(r);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return rods[a].n > rods[b].n; });
     std::vector<std::vector<int>> bins;
     std::vector<int> room;
     std::multiset<std::pair<int, int>> open_bins;  // (free node slots, bin), bins below cap_rods
     for (int r : order) {
-      const int n = s->rods_h[r].n + 1;
+      const int n = rods[r].n + 1;
       auto it = open_bins.lower_bound({n, -1});
       int b;
       if (it == open_bins.end()) {
         b = static_cast<int>(bins.size());
         bins.emplace_back();
-        room.push_back(shape.cap_elems);
+        room.push_back(cap_elems);
       } else {
         b = it->second;
         open_bins.erase(it);
       }
       bins[b].push_back(r);
       room[b] -= n;
-      if (static_cast<int>(bins[b].size()) < shape.cap_rods) open_bins.insert({room[b], b});
+      if (static_cast<int>(bins[b].size()) < cap_rods) open_bins.insert({room[b], b});
     }
     if (bins.size() < packs.size()) {
       packs.clear();
-      for (auto& rods : bins) {
-        std::sort(rods.begin(), rods.end());
+      for (auto& bin : bins) {
+        std::sort(bin.begin(), bin.end());
         Pack pk{};
         bool consecutive = true;
-        for (size_t k = 1; k < rods.size(); ++k) consecutive = consecutive && rods[k] == rods[k - 1] + 1;
-        const RodConst& first = s->rods_h[rods[0]];
-        pk.rod0 = rods[0];
+        for (size_t k = 1; k < bin.size(); ++k) consecutive = consecutive && bin[k] == bin[k - 1] + 1;
+        const RodConst& first = rods[bin[0]];
+        pk.rod0 = bin[0];
         pk.elem0 = first.elem0;
         pk.node0 = first.node0;
-        pk.vor0 = first.elem0 - rods[0];
+        pk.vor0 = first.elem0 - bin[0];
         pk.listed = consecutive ? 0 : 1;
-        pk.list_off = consecutive ? 0 : static_cast<int32_t>(list.size());
-        for (int r : rods) {
-          const int n = s->rods_h[r].n;
-          if (!consecutive) list.push_back(make_int2(r, pk.nelem));
+        pk.list_off = consecutive ? 0 : static_cast<int32_t>(plan.list.size());
+        for (int r : bin) {
+          const int n = rods[r].n;
+          if (!consecutive) plan.list.push_back(make_int2(r, pk.nelem));
           pk.nrods += 1;
           pk.nelem += n;
           pk.nnode += n + 1;
@@ -337,25 +341,38 @@ rod_status build_packs(rod_system* s, const LaunchShape& shape) {
       }
     }
   }
+  // heaviest packs first (blocks start roughly in index order): the last, partly filled wave of
+  // blocks then holds the lightest packs, which shortens the tail of every launch
+  std::stable_sort(packs.begin(), packs.end(),
+                   [](const Pack& a, const Pack& b) { return a.nelem + a.nnode > b.nelem + b.nnode; });
+  return plan;
+}
+
+rod_status build_packs(rod_system* s, const LaunchShape& shape) {
+  PackPlan plan = plan_packs(s->rods_h, shape.cap_elems, shape.cap_rods);
+  const std::vector<Pack>& packs = plan.packs;
+  const std::vector<int2>& list = plan.list;
+  size_t scratch = 0;
+  for (const Pack& lp : plan.longs) {
+    LaunchShape ls;
+    ls.cap_elems = lp.nelem;
+    ls.cap_rods = 1;
+    ls.threads = 256;
+    scratch = std::max(scratch, step_smem_bytes(ls));
+  }
   if (!list.empty()) {
     CUDA_TRY(s->pack_rods.alloc(list.size()));
     CUDA_TRY(cudaMemcpy(s->pack_rods.p, list.data(), list.size() * sizeof(int2), cudaMemcpyHostToDevice));
   } else {
     s->pack_rods.release();
-  s->diag_rows.release();
-  s->diag_tot.release();
   }
-  // heaviest packs first (blocks start roughly in index order): the last, partly filled wave of
-  // blocks then holds the lightest packs, which shortens the tail of every launch
-  std::stable_sort(packs.begin(), packs.end(),
-                   [](const Pack& a, const Pack& b) { return a.nelem + a.nnode > b.nelem + b.nnode; });
   if (!packs.empty()) {
     CUDA_TRY(s->packs.alloc(packs.size()));
     CUDA_TRY(cudaMemcpy(s->packs.p, packs.data(), packs.size() * sizeof(Pack), cudaMemcpyHostToDevice));
   }
   s->n_packs = static_cast<int>(packs.size());
   s->n_listed = static_cast<int>(std::count_if(packs.begin(), packs.end(), [](const Pack& p) { return p.listed != 0; }));
-  s->long_packs = longs;
+  s->long_packs = plan.longs;
   if (scratch > 0 && (int64_t)s->long_scratch.n * 8 < (int64_t)scratch)
     CUDA_TRY(s->long_scratch.alloc((scratch + 7) / 8));
   s->shape = shape;
@@ -873,6 +890,8 @@ rod_status rod_system_destroy(rod_system* s) {
   s->rods.release();
   s->packs.release();
   s->pack_rods.release();
+  s->diag_rows.release();
+  s->diag_tot.release();
   s->long_scratch.release();
   s->ckpt.release();
   s->seg_states.release();
@@ -1432,6 +1451,39 @@ rod_status rod_system_diagnostics(rod_system* s, double* per_rod, double* totals
     CUDA_TRY(cudaMemcpyAsync(totals, s->diag_tot.p, 6 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
   }
+  return ROD_OK;
+}
+
+rod_status rod_plan_packs(const int32_t* n_elem, int32_t n_rods, int32_t cap_elems, int32_t cap_rods,
+                          int32_t* n_packs, int32_t* n_list, int32_t* n_long, int32_t* packs, int32_t* list) {
+  if (!n_elem || n_rods < 1 || cap_elems < 1 || cap_rods < 1) return fail(ROD_ERR_ARG, "need rods and positive capacities");
+  std::vector<RodConst> rods(n_rods);
+  int64_t e0 = 0;
+  for (int r = 0; r < n_rods; ++r) {
+    if (n_elem[r] < 1) return fail(ROD_ERR_ARG, "every rod needs at least one element");
+    if (e0 + n_elem[r] + r + 1 > INT32_MAX) return fail(ROD_ERR_ARG, "too many elements");
+    rods[r] = RodConst{};
+    rods[r].n = n_elem[r];
+    rods[r].elem0 = static_cast<int32_t>(e0);
+    rods[r].node0 = static_cast<int32_t>(e0 + r);
+    e0 += n_elem[r];
+  }
+  const PackPlan plan = plan_packs(rods, cap_elems, cap_rods);
+  if (n_packs) *n_packs = static_cast<int32_t>(plan.packs.size());
+  if (n_list) *n_list = static_cast<int32_t>(plan.list.size());
+  if (n_long) *n_long = static_cast<int32_t>(plan.longs.size());
+  if (packs)
+    for (size_t k = 0; k < plan.packs.size(); ++k) {
+      const Pack& pk = plan.packs[k];
+      const int32_t row[10] = {pk.rod0, pk.nrods, pk.elem0, pk.nelem, pk.node0, pk.nnode, pk.vor0, pk.nvor,
+                               pk.listed, pk.list_off};
+      std::memcpy(packs + 10 * k, row, sizeof row);
+    }
+  if (list)
+    for (size_t k = 0; k < plan.list.size(); ++k) {
+      list[2 * k] = plan.list[k].x;
+      list[2 * k + 1] = plan.list[k].y;
+    }
   return ROD_OK;
 }
 

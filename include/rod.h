@@ -187,7 +187,7 @@ rod_status rod_system_get_launch(const rod_system* sys, int32_t* elems_per_block
 
 /* Energy and frame diagnostics of the current state (Methods: the Cosserat rod of Eq. 1; the
  * energy the explicit symplectic step conserves without damping and loads).  One warp per rod.
- * per_rod: device [6*R] (row c holds component c of every rod) or NULL:
+ * per_rod: device [9*R] (row c holds component c of every rod) or NULL:
  *   0  translational kinetic energy, sum over the rod's nodes of 1/2 m |v|^2
  *   1  rotational kinetic energy, sum over its elements of 1/2 rho I_c rl w_c^2
  *   2  shear/stretch energy, sum over its elements of 1/2 rl S_c (sigma_c - sigma0_c)^2 with
@@ -196,6 +196,7 @@ rod_status rod_system_get_launch(const rod_system* sys, int32_t* elems_per_block
  *      kappa = -log(Q_{k+1} Q_k^T) / D, D the mean of the two rest lengths
  *   4  work potential: -sum m g . x over its nodes - F_tip . x_tip
  *   5  largest entry of |Q Q^T - I| over its elements (orthonormality of the directors)
+ *   6-8  the position x, y, z of its last node (the tip)
  * totals: host [6] or NULL: rows 0-4 summed over the rods, row 5 maximised (a fixed order: the
  * same bits on every call).  Contact, walls, fields, actuation and damping hold no potential
  * here.  With totals the call synchronises on the system's stream; otherwise it only enqueues

@@ -452,11 +452,11 @@ class RodSystem:
     def diagnostics(self, per_rod: bool = True):
         """Energy parts and director orthonormality of the current state.
 
-        Returns (rows, totals): rows a [6, R] device tensor (translational kinetic, rotational
-        kinetic, shear/stretch, bend/twist, work potential, max |Q Q^T - I| per rod) or None, and
-        totals a numpy array of 6 (rows 0-4 summed, row 5 maximised)."""
+        Returns (rows, totals): rows a [9, R] device tensor (translational kinetic, rotational
+        kinetic, shear/stretch, bend/twist, work potential, max |Q Q^T - I|, tip x, y, z per rod)
+        or None, and totals a numpy array of 6 (rows 0-4 summed, row 5 maximised)."""
         import torch
-        rows = torch.empty((6, self.n_rods), dtype=torch.float64, device="cuda") if per_rod else None
+        rows = torch.empty((9, self.n_rods), dtype=torch.float64, device="cuda") if per_rod else None
         tot = np.zeros(6)
         # with totals the call synchronises the system's stream, so the rows are complete on return
         _check(self.lib.rod_system_diagnostics(self.handle, rows.data_ptr() if rows is not None else None,

@@ -189,7 +189,7 @@ struct rod_system {
   LaunchShape shape{0, 0, 0};
   DevBuf<Pack> packs;
   DevBuf<int2> pack_rods;  // (global rod, first pack-local element) of the rods of listed packs
-  DevBuf<double> diag_rows, diag_tot;  // rod_system_diagnostics scratch: [6][R], [6]
+  DevBuf<double> diag_rows, diag_tot;  // rod_system_diagnostics scratch: [9][R], [6]
   int n_packs = 0, n_listed = 0;
   // rods longer than a block holds: one pack each, run by cooperative launches with their
   // working arrays in long_scratch
@@ -1436,7 +1436,7 @@ rod_status rod_system_diagnostics(rod_system* s, double* per_rod, double* totals
   A.R = s->R;
   for (int c = 0; c < 3; ++c) A.gravity[c] = s->has_gravity ? s->gravity[c] : 0.0;
   if (!per_rod) {
-    if ((int64_t)s->diag_rows.n < 6 * (int64_t)s->R) CUDA_TRY(s->diag_rows.alloc(6 * (size_t)s->R));
+    if ((int64_t)s->diag_rows.n < 9 * (int64_t)s->R) CUDA_TRY(s->diag_rows.alloc(9 * (size_t)s->R));
     per_rod = s->diag_rows.p;
   }
   A.per_rod = per_rod;

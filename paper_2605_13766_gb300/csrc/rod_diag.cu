@@ -4,8 +4,9 @@
 // kinetic energy of the nodes, rotational kinetic energy of the elements, shear/stretch energy
 // of the element strains sigma = Q (x_{i+1} - x_i) / rl - d3 (frame components), bend/twist
 // energy of the Voronoi curvatures kappa = -log(Q_{k+1} Q_k^T) / D, and the work potential of
-// gravity and the constant tip forces.  One warp per rod; per-rod sums by warp shuffles, the
-// totals by one block in a fixed order (the same bits on every call).  Not on the step path.
+// gravity and the constant tip forces; also the orthonormality of the directors and the tip
+// positions.  One warp per rod; per-rod sums by warp shuffles, the totals by one block in a
+// fixed order (the same bits on every call).  Not on the step path.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -46,7 +47,13 @@ __global__ void __launch_bounds__(256) diag_rod_kernel(DiagArgs A) {
     const double v0 = A.v[g], v1 = A.v[N + g], v2 = A.v[2 * N + g];
     kt += 0.5 * m * (v0 * v0 + v1 * v1 + v2 * v2);
     pot -= m * (A.gravity[0] * x0 + A.gravity[1] * x1 + A.gravity[2] * x2);
-    if (j == n) pot -= rc->tip[0] * x0 + rc->tip[1] * x1 + rc->tip[2] * x2;
+    if (j == n) {
+      pot -= rc->tip[0] * x0 + rc->tip[1] * x1 + rc->tip[2] * x2;
+      // the tip position, written by the lane that holds the last node
+      A.per_rod[6 * A.R + r] = x0;
+      A.per_rod[7 * A.R + r] = x1;
+      A.per_rod[8 * A.R + r] = x2;
+    }
   }
   // elements: 1/2 rho I_c rl w_c^2, 1/2 rl S_c (sigma_c - sigma0_c)^2, |Q Q^T - I|
   for (int i = lane; i < n; i += 32) {

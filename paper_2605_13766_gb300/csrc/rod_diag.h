@@ -18,7 +18,7 @@ struct DiagArgs {
   int64_t N, E, V;
   int R;
   double gravity[3];            // zero when the system has none
-  double* per_rod;              // [6][R] output
+  double* per_rod;              // [9][R] output: five energy parts, orthonormality, tip x, y, z
 };
 
 // Per-rod rows into A.per_rod (one warp per rod).

@@ -1,4 +1,4 @@
-"""GPU energy and frame diagnostics (rod_system_diagnostics) against the oracle's energy.
+"""GPU energy, frame and tip diagnostics (rod_system_diagnostics) against the oracle's energy.
 
 Each component is pinned on its own: a state in which only that part of the energy is non-zero
 (velocities only, angular velocities only, stretched rods with uniform frames, rods twisted about
@@ -145,6 +145,9 @@ def test_general_state_sums_and_totals():
     H = Oracle(p).energy(*p.state())
     assert abs(tot[:5].sum() - H) <= TOL * scale.sum()
     assert np.all(np.abs(tot[:5] - rows[:5].sum(axis=1)) <= 1e-13 * np.abs(rows[:5]).sum(axis=1))
+    # rows 6-8: the tip of every rod (its last node), copied bit for bit
+    tips = p.x[:, p.node_offsets()[1:] - 1]
+    assert np.array_equal(rows[6:9], tips)
     # the totals do not change between calls, and a call with totals launches two kernels
     n0 = s.launch_count
     _, tot2 = s.diagnostics(per_rod=False)

@@ -22,7 +22,6 @@ from oracle.oracle import Oracle
 
 pytestmark = pytest.mark.gpu
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -35,8 +34,9 @@ def _lib():
 
 
 def _record(name, obj):
-    out = os.path.join(ROOT, "gpurun_out")
-    if os.path.isdir(out):
+    """Write obj as JSON into the directory named by ROD_TEST_RECORD_DIR, when it is set."""
+    out = os.environ.get("ROD_TEST_RECORD_DIR")
+    if out and os.path.isdir(out):
         with open(os.path.join(out, f"{name}.json"), "w") as f:
             json.dump(obj, f, indent=1)
 

@@ -23,7 +23,6 @@ from oracle.oracle import Oracle
 pytestmark = pytest.mark.gpu
 
 
-
 @pytest.fixture(scope="module", autouse=True)
 def _lib():
     torch = pytest.importorskip("torch")

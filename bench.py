@@ -56,6 +56,8 @@ FLOPS_PER_UNIT = {
 # the bench's steps at its autotuned 256 x 256 shape, profiles/pack_kernel_one_step_packing_10k.md.
 # The carpet's state stays on chip between the steps of a launch: its traffic is one read of
 # the state and constants per launch (the written state is still in L2 when the launch ends).
+# CPU seconds the reference arm spends on its W + K samples (the whole run stays within minutes)
+REF_BUDGET_S = 90.0
 TRAFFIC_PER_LAUNCH = {
     "pack_one_step": 356.06e6 + 152.13e6,
     "pack_steps": 39.28e6,
@@ -131,30 +133,46 @@ class ClockSampler:
 
 
 def _reference(args, world, rank):
-    """CPU oracle (plain C, single thread) on a bounded sample of the same workload."""
+    """CPU oracle (plain C, single thread) as the reference arm: W untimed and exactly K timed
+    steps, each step a bounded sample of the same workload -- s time steps of its first m rods,
+    sized during the warm-up so that all W + K samples take about REF_BUDGET_S seconds."""
     if rank != 0:
         return
     from oracle.oracle import Oracle, build_oracle
     build_oracle()
     p, dt, desc = _workload(args.workload, 0)
-    o = Oracle(p)
-    sample_steps = {"packing": 2, "carpet": 20, "cantilever": 2000}[args.workload]
-    st = p.state()
-    # warm-up: one step, untimed
+    K, W = max(1, args.steps), max(args.warmup, 3)
+    target = min(0.5, REF_BUDGET_S / (K + W))          # seconds per sample
+    # calibration (the first warm-up sample): one time step of enough rods for ~2e4 elements
+    eo = p.elem_offsets()
+    m = int(min(p.n_rods, max(1, np.searchsorted(eo, 20000))))
+    q = p.take_rods(0, m)
+    o = Oracle(q)
+    st = q.state()
+    t0 = time.perf_counter()
     st = o.step(*st, dt=dt, n_steps=1)
+    per_elem_step = (time.perf_counter() - t0) / q.n_elems
+    # the sample: s steps of the first m rods
+    if per_elem_step * p.n_elems <= target:
+        m, s = p.n_rods, max(1, int(target / (per_elem_step * p.n_elems)))
+    else:
+        m, s = int(min(p.n_rods, max(1, np.searchsorted(eo, target / per_elem_step)))), 1
+    q = p.take_rods(0, m)
+    o = Oracle(q)
+    st = q.state()
+    for _ in range(W - 1):
+        st = o.step(*st, dt=dt, n_steps=s)
     times = []
-    for _ in range(max(1, args.steps)):
+    for _ in range(K):
         t0 = time.perf_counter()
-        st = o.step(*st, dt=dt, n_steps=sample_steps)
+        st = o.step(*st, dt=dt, n_steps=s)
         times.append(time.perf_counter() - t0)
-        if sum(times) > 60.0:
-            break
     tot = sum(times)
-    n = len(times) * sample_steps
-    value = p.n_elems * n / tot
-    sample = f"{n} full time steps of the {desc['workload']} ({p.n_elems} elements), oracle single-threaded"
+    value = q.n_elems * s * K / tot
+    sample = (f"each step: {s} time step(s) of the first {m} of {p.n_rods} rods ({q.n_elems} of {p.n_elems} "
+              f"elements) of the {desc['workload']}, oracle single-threaded")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": len(times), "warmup": 1, "ms_per_step": tot / n * 1e3, "higher_is_better": True,
+            "steps": K, "warmup": W, "ms_per_step": tot / K * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
             "config": dict(desc, l2="state larger than L2 (196 MB)" if args.workload == "packing" else "n/a"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},

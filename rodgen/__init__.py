@@ -117,6 +117,37 @@ class RodProblem:
     def replace(self, **kw) -> "RodProblem":
         return dataclasses.replace(self, **kw)
 
+    def take_rods(self, r0: int, r1: int) -> "RodProblem":
+        """The sub-ensemble of rods r0 .. r1 - 1 with their state, constants and loads (global
+        settings unchanged)."""
+        R = self.n_rods
+        if not (0 <= r0 < r1 <= R):
+            raise ValueError("need 0 <= r0 < r1 <= n_rods")
+        eo, no = self.elem_offsets(), self.node_offsets()
+        e0, e1, n0, n1 = int(eo[r0]), int(eo[r1]), int(no[r0]), int(no[r1])
+        v0, v1 = e0 - r0, e1 - r1
+        per_rod, per_elem, per_node, per_vor = {}, {}, {}, {}
+        for f in dataclasses.fields(self):
+            a = getattr(self, f.name)
+            if not isinstance(a, np.ndarray) or f.name in ("gravity", "field_b0", "field_bc", "field_bs") \
+                    or f.name.startswith("wall_"):
+                continue
+            last = a.shape[-1]
+            if f.name == "n_elem" or (a.ndim == 1 and last == R and f.name != "rest_len"):
+                per_rod[f.name] = a[r0:r1].copy()
+            elif a.ndim == 2 and last == R and f.name in ("tip_force",):
+                per_rod[f.name] = a[:, r0:r1].copy()
+            elif f.name in ("x", "v"):
+                per_node[f.name] = a[:, n0:n1].copy()
+            elif f.name == "rest_kappa":
+                per_vor[f.name] = a[:, v0:v1].copy()
+            elif f.name == "rest_len":
+                per_elem[f.name] = a[e0:e1].copy()
+            elif a.shape[-1] == self.n_elems:
+                per_elem[f.name] = a[..., e0:e1].copy()
+        return dataclasses.replace(self, name=f"{self.name}_rods{r0}-{r1}", **per_rod, **per_elem, **per_node,
+                                   **per_vor)
+
 
 # ----------------------------------------------------------------------------- helpers
 

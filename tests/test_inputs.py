@@ -6,7 +6,8 @@
   the recipe (n ~ U{nmin..nmax}, rigid velocity per rod within [-speed, speed]^3, orthonormal
   frames with d3 along the rod);
 * the cilia carpet: upright clamped rods on the square grid, base couple amplitude 0.5 E I / L;
-* the same seed gives the same arrays.
+* the same seed gives the same arrays;
+* a sub-ensemble taken out of an ensemble (the reference arm's bounded samples) is the same rods.
 """
 import numpy as np
 import pytest
@@ -100,3 +101,23 @@ def test_cantilever_recipe(n):
     assert p.n_rods == 1 and p.n_elem[0] == n
     assert np.allclose(p.x[2], np.linspace(0.0, 1.0, n + 1)) and np.allclose(p.x[:2], 0.0)
     assert np.allclose(p.tip_force[:, 0], [0.0, 1e-2, 0.0])
+
+
+def test_take_rods_matches_the_full_ensemble():
+    """Without contact the rods are independent: the oracle's right-hand side of rods r0..r1-1
+    taken on their own equals the matching slice of the full right-hand side, bit for bit."""
+    from oracle.oracle import Oracle
+    rng = np.random.default_rng(3)
+    p = rodgen.perturbed(rodgen.random_packing(n_rods=12, nmin=1, nmax=40, box=0.5, seed=3, allow_overlap=True,
+                                               speed=0.2), seed=3)
+    p = p.replace(contact=False, tip_force=rng.normal(0, 1e-3, (3, 12)), rest_sigma=rng.normal(0, 1e-3, (3, p.n_elems)),
+                  rest_kappa=rng.normal(0, 0.3, (3, p.n_voronoi)), elem_couple=rng.normal(0, 1e-6, (3, p.n_elems)),
+                  clamp_base=(np.arange(12) % 3 == 0).astype(np.int8), gravity=np.array([0.0, 0.0, -9.81]))
+    av, aw = Oracle(p).rhs(*p.state(), t=0.01)
+    eo, no = p.elem_offsets(), p.node_offsets()
+    for r0, r1 in [(0, 1), (3, 8), (11, 12), (0, 12)]:
+        q = p.take_rods(r0, r1)
+        bv, bw = Oracle(q).rhs(*q.state(), t=0.01)
+        assert np.array_equal(bv, av[:, no[r0]:no[r1]]) and np.array_equal(bw, aw[:, eo[r0]:eo[r1]])
+    with pytest.raises(ValueError):
+        p.take_rods(5, 5)

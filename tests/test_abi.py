@@ -62,3 +62,19 @@ def test_missing_library_fails_loudly(tmp_path):
             binding.load_library(str(tmp_path / "nope.so"))
         finally:
             binding._lib = old
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/*.h compile as ISO C99 (the boundary is a C ABI, usable without C++)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    incs = "".join(f'#include "{os.path.join(ROOT, "include", f)}"\n'
+                   for f in sorted(os.listdir(os.path.join(ROOT, "include"))) if f.endswith(".h"))
+    src.write_text(incs + "int main(void) { return 0; }\n")
+    out = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-c", str(src), "-o",
+                          str(tmp_path / "abi.o")], capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr

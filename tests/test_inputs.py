@@ -6,6 +6,7 @@
   the recipe (n ~ U{nmin..nmax}, rigid velocity per rod within [-speed, speed]^3, orthonormal
   frames with d3 along the rod);
 * the cilia carpet: upright clamped rods on the square grid, base couple amplitude 0.5 E I / L;
+* the adjoint batch: the stated distributions of rest curvature, couples and tip targets;
 * the same seed gives the same arrays;
 * a sub-ensemble taken out of an ensemble (the reference arm's bounded samples) is the same rods.
 """
@@ -121,3 +122,19 @@ def test_take_rods_matches_the_full_ensemble():
         assert np.array_equal(bv, av[:, no[r0]:no[r1]]) and np.array_equal(bw, aw[:, eo[r0]:eo[r1]])
     with pytest.raises(ValueError):
         p.take_rods(5, 5)
+
+
+def test_adjoint_batch_recipe():
+    """1024 clamped upright rods x 64 elements, rest curvature ~ N(0, 0.5) 1/m, element couples
+    ~ N(0, 1e-6) N m, tip targets = undeformed tips + N(0, 0.01) m (sample moments of the
+    seeded draws within a few standard errors)."""
+    p = rodgen.adjoint_batch()
+    R, n = 1024, 64
+    assert p.n_rods == R and np.all(p.n_elem == n) and np.all(p.clamp_base == 1)
+    assert p.rest_kappa.shape == (3, R * (n - 1)) and p.elem_couple.shape == (3, R * n)
+    k, c = p.rest_kappa.ravel(), p.elem_couple.ravel()
+    assert abs(k.mean()) < 4 * 0.5 / np.sqrt(k.size) and abs(k.std() / 0.5 - 1) < 0.01
+    assert abs(c.mean()) < 4 * 1e-6 / np.sqrt(c.size) and abs(c.std() / 1e-6 - 1) < 0.01
+    tips = p.x[:, p.node_offsets()[1:] - 1]
+    dev = (p.extra["targets"] - tips).ravel()
+    assert abs(dev.std() / 0.01 - 1) < 0.05 and np.allclose(tips[2], 0.2)

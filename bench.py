@@ -40,20 +40,42 @@ UNIT = "element-steps/s"
 # clock at 2.07 GHz) x 152 SMs x 2.07 GHz max SM clock x 2 flop per FMA.
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
-# Algorithmic FP64 flops per unit of each kernel: the FP64 arithmetic of the formulas as the
-# kernel evaluates them, counted by ncu on the active threads (add/sub/mul = 1 flop, fma = 2),
-# divided by the units of the launch.  pack_one_step: one launch of pack_kernel<3> on the
-# 10^4-rod packing, 156.95M DFMA + 37.07M DADD + 121.45M DMUL on 1,366,295 element-steps
-# (profiles/pack_kernel_one_step_packing_10k.md).  pack_steps: one 20-step launch of
-# pack_kernel<0> on the 64 x 64 carpet, 465.37M DFMA + 82.90M DADD + 367.68M DMUL on 4,096,000
-# element-steps (profiles/pack_kernel_steps_carpet_4096.md).
+# FP64 flops per unit of each kernel as the kernel evaluates them, counted by ncu on the active
+# threads (add/sub/mul = 1 flop, fma = 2) and divided by the units of the launch.  pack_one_step:
+# one launch of pack_kernel<3> on the 10^4-rod packing, 156.95M DFMA + 37.07M DADD + 121.45M
+# DMUL on 1,366,295 element-steps.  pack_steps: one 20-step launch of pack_kernel<0> on the
+# 64 x 64 carpet, 465.37M DFMA + 82.90M DADD + 367.68M DMUL on 4,096,000 element-steps.
 FLOPS_PER_UNIT = {
     "pack_one_step": 345.8,   # per element-step
     "pack_steps": 337.2,      # per element-step
 }
+FLOPS_SOURCE = "executed FP64 arithmetic of the kernel (ncu: DFMA x 2 + DADD + DMUL) per element-step"
+# The method's own FP64 work per element-step, counted on the oracle's arithmetic (every FP64
+# add, subtract, multiply and divide of one step, a special function (sqrt, sin, cos, atan2,
+# floor) counted as one operation), for the same workloads; None where not counted.
+ORACLE_FLOPS_PER_UNIT = {
+    "pack_one_step": None,
+    "pack_steps": None,
+}
+# Algorithmic HBM bytes per element-step: the state makes one round trip (6 node + 12 element
+# doubles, read and written: 288 B), the rest length is read (8 B), and with contact each
+# segment's cell key and sorted index are written and read (16 B).
+BYTES_PER_UNIT = {"packing": 312.0, "carpet": 296.0, "cantilever": 296.0}
+
+
+def _measured_hbm_gbs():
+    """(HBM copy bandwidth in GB/s, where it comes from): the measured figure when the pod's
+    MEASURED_PEAKS.json is present, else an earlier measurement on a GB300 (6.8 TB/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except Exception:
+        return 6800.0, "6.8 TB/s, an earlier GB300 copy measurement (of fallback)"
+
+
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of one capture of the
 # current kernel; reset to None whenever the kernel changes.  pack_one_step: the third launch of
-# the bench's steps at its autotuned 256 x 256 shape, profiles/pack_kernel_one_step_packing_10k.md.
+# the bench's steps at its autotuned 256 x 256 shape.
 # The carpet's state stays on chip between the steps of a launch: its traffic is one read of
 # the state and constants per launch (the written state is still in L2 when the launch ends).
 # CPU seconds the reference arm spends on its W + K samples (the whole run stays within minutes)
@@ -70,8 +92,9 @@ def _workload(name: str, rank: int):
         p = rodgen.random_packing_cached(seed=seed)
         desc = {"workload": "random packing, 10^4 rods, n~U{16..256} (seeded), contact k=1e4 c=10, gravity, dt=5e-6",
                 "rods": p.n_rods, "elements": p.n_elems, "dt": 5e-6,
-                "note": "the timed steps are a prefix of the workload's 5000; with the stated explicit dashpot "
-                        "the packing blows up after ~2750 steps (stable with c=0), a property of the scheme"}
+                "note": "timed steps sit inside the workload's 5000-step run, after an untimed pre-roll from "
+                        "the placement to a contact-dense state (timed_window); the first steps after the "
+                        "placement, which has no overlap, are reported as early_window"}
         return p, 5e-6, desc
     if name == "carpet":
         p = rodgen.cilia_carpet()
@@ -193,12 +216,12 @@ def _cpu_baseline(p, dt, desc, workload):
             "sample": f"{n} time steps of the full workload ({p.n_elems} elements), plain C oracle, one thread"}
 
 
-def _e2e(s, p, dt, K, world, dist, barrier):
-    """Same metric through the public API from pinned host buffers: set_state (H2D), K steps,
-    get_state (D2H) inside the timed region."""
+def _e2e(s, start_state, p, dt, K, world, dist, barrier):
+    """Same metric through the public API from pinned host buffers: set_state (H2D) of the timed
+    window's start state, K steps, get_state (D2H) inside the timed region."""
     import torch
     from paper_2605_13766_gb300.replicas import slowest, total
-    x, v, Q, w = p.state()
+    x, v, Q, w = start_state
     pin = [torch.from_numpy(a).pin_memory() for a in (x, v, Q, w)]
     outs = [torch.empty(a.shape, dtype=torch.float64).pin_memory() for a in (x, v, Q, w)]
     barrier()
@@ -211,7 +234,8 @@ def _e2e(s, p, dt, K, world, dist, barrier):
     state_bytes = 8 * (6 * p.n_nodes + 12 * p.n_elems)
     e2e = {"value": total(p.n_elems * K) / t_e2e, "unit": UNIT, "h2d_bytes_per_step": state_bytes / K,
            "d2h_bytes_per_step": state_bytes / K,
-           "note": f"set_state from pinned host + {K} steps + get_state to host per round trip"}
+           "note": f"set_state of the timed window's start state from pinned host + {K} steps + get_state to "
+                   f"host per round trip (host wall clock; set_state rebuilds the contact grid and list)"}
     del outs, xs
 
     return e2e
@@ -346,6 +370,12 @@ def main():
     ap.add_argument("--skin", type=float, default=None,
                     help="contact skin list (m); default 0.5 mm for the packing, 0 = cell search every step")
     ap.add_argument("--surrogate-train-steps", type=int, default=15000)
+    ap.add_argument("--preroll", type=int, default=None,
+                    help="contact workloads: untimed steps of the same run before the timed window (default: "
+                         "4000, less what keeps the timed and profiled steps inside the run's 5000); the early "
+                         "window from the placement is reported beside it")
+    ap.add_argument("--no-full-run", action="store_true",
+                    help="skip the timing of the whole 5000-step contact run from the placement")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -387,33 +417,71 @@ def main():
     elif not args.no_autotune:
         te, tt, tms = s.autotune(dt, trial_steps=5)
         tuned = {"elems_per_block": te, "threads_per_block": tt, "trial_ms_per_step": tms}
+    stream = s.torch_stream
+
+    def timed(n):
+        """n steps in one call, CUDA events on the library's stream; (seconds, launches, rebuilds)."""
+        launches0 = s.launch_count
+        builds0 = s.contact_list_builds()
+        barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s.step_async(n, dt)
+        ev1.record(stream)
+        s.sync()
+        torch.cuda.synchronize()
+        barrier()
+        return ev0.elapsed_time(ev1) / 1e3, s.launch_count - launches0, s.contact_list_builds() - builds0
+
+    def pairs_now():
+        """Segment pairs in contact at the current state (the cell-grid search; the skin list is
+        rebuilt at the next step)."""
+        return s.contact_pair_count()[0] if p.contact else None
+
+    # ---- early window: W warm-up steps from the placement, then K timed steps (no contact yet
+    # on the packing: it starts without overlap)
+    early = None
+    run_steps = 5000
+    if not p.contact:
+        preroll = 0
+    elif args.preroll is not None:
+        preroll = args.preroll
+    else:
+        preroll = max(W + K, min(4000, run_steps - (W + 2 * K + 1)))
+    if preroll > 0:
+        s.step(W, dt)
+        t_e, l_e, b_e = timed(K)
+        early = {"steps": f"{W + 1}..{W + K}", "value": total(p.n_elems * K) / slowest(t_e),
+                 "ms_per_step": slowest(t_e) * 1e3 / K, "gpu_launches": l_e, "rebuilds": b_e,
+                 "contact_pairs_at_end": pairs_now()}
+        # ---- untimed pre-roll of the same run to a contact-dense state
+        done = W + K
+        while done < preroll:
+            n = min(500, preroll - done)
+            s.step(n, dt)
+            done += n
+    else:
+        done = 0
+    # the window's start state, kept on the host for the end-to-end measurement
+    start_state = s.get_state()
+    pairs0 = pairs_now()
     s.step(W, dt)
     torch.cuda.synchronize()
     diag0 = s.diagnostics(per_rod=False)[1]   # energy parts and orthonormality before the timed steps
 
     # ---- timed region (device time, CUDA events on the stream the library launches on)
-    stream = s.torch_stream
-    launches0 = s.launch_count
-    builds0 = s.contact_list_builds()
     clocks = ClockSampler(local)
     clocks.start()
-    barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    s.step_async(K, dt)
-    ev1.record(stream)
-    s.sync()
-    torch.cuda.synchronize()
-    barrier()
+    t_local, launches, builds = timed(K)
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    launches = s.launch_count - launches0
-    builds = s.contact_list_builds() - builds0
-    t_local = ms / 1e3
     t_max = slowest(t_local)
     value = total(p.n_elems * K) / t_max
+    pairs1 = pairs_now()
+    window = {"first_timed_step": done + W + 1, "last_timed_step": done + W + K,
+              "contact_pairs_at_start": pairs0, "contact_pairs_at_end": pairs1,
+              "rebuilds_in_timed_steps": builds}
     diag1 = s.diagnostics(per_rod=False)[1]
     diag = {"energy_before": float(diag0[:5].sum()), "energy_after": float(diag1[:5].sum()),
             "energy_parts_after": [float(e) for e in diag1[:5]],
@@ -423,18 +491,41 @@ def main():
                     "moves energy into or out of it; damping, drag and the dashpot dissipate); parts: "
                     "translational, rotational, shear/stretch, bend/twist, potential"}
 
-    # ---- per-kernel device times: the same K steps again with CUDA events around every launch
+    # ---- per-kernel device times: the next K steps with CUDA events around every launch
     # (eager launches: the event pairs sit between kernels on the same stream)
+    s.step(1, dt)   # takes the rebuild that the pair count above requested
+    builds_p0 = s.contact_list_builds()
     s.profile(True)
     s.step_async(K, dt)
     s.sync()
     prof = s.profile_read()
     s.profile(False)
+    builds_p = s.contact_list_builds() - builds_p0
+    if p.contact and skin > 0:
+        rebuild_ms = sum(prof.get(k, (0.0, 0))[0] for k in
+                         ("contact_bin", "contact_scan", "contact_scatter", "contact_sort", "contact_list_build"))
+        window["rebuild"] = {
+            "rebuilds_in_profiled_steps": builds_p,
+            "rebuild_kernels_ms_per_step": rebuild_ms / K,
+            "ms_per_rebuild": (rebuild_ms / builds_p) if builds_p else None,
+            "steps_per_rebuild": (K / builds_p) if builds_p else None,
+            "note": "eager profiled steps launch the gated rebuild kernels every step (they return at once "
+                    "when no rebuild is due); their time over K steps is the amortised rebuild cost"}
 
-    # ---- end to end through the public API with pinned host buffers
+    # ---- end to end through the public API with pinned host buffers (from the window's start)
     e2e = None
     if not args.no_e2e:
-        e2e = _e2e(s, p, dt, K, world, dist, barrier)
+        e2e = _e2e(s, start_state, p, dt, K, world, dist, barrier)
+
+    # ---- the whole contact run from the placement (the workload's 5000 steps in one call,
+    # graph-replayed), timed with CUDA events like the window
+    full = None
+    if p.contact and not args.no_full_run:
+        s.set_state(*p.state())
+        t_f, l_f, b_f = timed(run_steps)
+        full = {"steps": run_steps, "value": total(p.n_elems * run_steps) / slowest(t_f),
+                "ms_per_step": slowest(t_f) * 1e3 / run_steps, "gpu_launches": l_f, "rebuilds": b_f,
+                "contact_pairs_at_end": pairs_now()}
 
     # ---- roofline of the dominant kernel
     dom = max(prof.items(), key=lambda kv: kv[1][0])
@@ -443,10 +534,24 @@ def main():
     fpu = FLOPS_PER_UNIT.get(dname)
     units = p.n_elems * (K if dname == "pack_steps" else 1)
     achieved = (fpu * units / (avg_ms * 1e-3) / 1e12) if fpu else None
+    hbm_peak, hbm_src = _measured_hbm_gbs()
+    bpu = BYTES_PER_UNIT.get(args.workload)
+    hbm = None
+    if bpu:
+        k_gbs = bpu * units / (avg_ms * 1e-3) / 1e9
+        step_gbs = bpu * value / 1e9
+        hbm = {"bytes_per_unit": bpu, "peak_gbs": hbm_peak, "peak_source": hbm_src,
+               "kernel_gbs": k_gbs, "kernel_frac": k_gbs / hbm_peak,
+               "step_gbs": step_gbs, "step_frac": step_gbs / hbm_peak,
+               "note": "algorithmic bytes (one HBM round trip of the state plus rest lengths and, with contact, "
+                       "the cell key and sorted index) x units / time"}
     roof = {"bound": "alu", "kernel": dname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
             "traffic": TRAFFIC_PER_LAUNCH.get(dname), "avg_launch_ms": avg_ms,
+            "flops_per_unit": fpu, "flops_source": FLOPS_SOURCE,
+            "flops_per_unit_oracle": ORACLE_FLOPS_PER_UNIT.get(dname),
             "peak_source": "FP64: 2 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal unit count; an FMA probe measured 1.91/clk)",
+            "hbm_frac": hbm["step_frac"] if hbm else None, "hbm": hbm,
             "kernel_share": {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4)
                              for k, v in prof.items() if v[1]}}
 
@@ -469,9 +574,10 @@ def main():
                                                f"skin list, skin {skin:g} m, {builds} rebuilds in the timed steps"
                                                if skin > 0 else "cell grid searched every step"),
                                l2="state (196 MB) larger than L2, no flush needed" if args.workload == "packing"
-                               else "state L2/smem resident"),
+                               else "state L2/smem resident",
+                               timed_window=window),
                 "clocks": clk, "gpu_launches": launches, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
-                "surrogate": sur, "adjoint": adj, "diagnostics": diag}
+                "early_window": early, "full_run": full, "surrogate": sur, "adjoint": adj, "diagnostics": diag}
         print(json.dumps(line), flush=True)
     s.close()
     if dist is not None:

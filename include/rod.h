@@ -111,7 +111,10 @@ rod_status rod_system_destroy(rod_system* sys);
 /* Sizes of the packed arrays. */
 rod_status rod_system_sizes(const rod_system* sys, int64_t* n_nodes, int64_t* n_elems, int64_t* n_voronoi);
 
-/* Set the state: x, v [3*N], Q [9*E], w [3*E] in the layout above.  on_device = 0: host
+/* Set the state: x, v [3*N], Q [9*E], w [3*E] in the layout above -- the rod's centreline
+ * positions r and velocities v, its director frame Q (rows d1, d2, d3) and the angular
+ * velocity w = ax(Q dQ^T/dt) in the local frame, the unknowns of Eq. 1a and Eq. 1b (Methods,
+ * "Cosserat rod dynamics"), sampled at the nodes (r, v) and elements (Q, w).  on_device = 0: host
  * pointers, copied synchronously and checked for NaN/Inf on the device after the copy (such a
  * state is rejected with ROD_ERR_ARG and the system then holds no state until the next
  * successful call); on_device = 1: device pointers, copied on the system's stream (the caller
@@ -121,14 +124,19 @@ rod_status rod_system_sizes(const rod_system* sys, int64_t* n_nodes, int64_t* n_
 rod_status rod_system_set_state(rod_system* sys, const double* x, const double* v, const double* Q,
                                 const double* w, int on_device);
 
-/* Read the state back (same layout / on_device meaning; host copies synchronise). */
+/* Read the state back: r, v, Q, w of Eq. 1 (Methods, "Cosserat rod dynamics"), same layout and
+ * on_device meaning as rod_system_set_state; host copies synchronise. */
 rod_status rod_system_get_state(rod_system* sys, double* x, double* v, double* Q, double* w, int on_device);
 
 /* Simulated time of the current state (advanced by dt per step; reset by set_state). */
 rod_status rod_system_set_time(rod_system* sys, double t);
 rod_status rod_system_get_time(const rod_system* sys, double* t);
 
-/* Advance n_steps position-Verlet steps of size dt (> 0).  Enqueued on the system's stream;
+/* Advance n_steps position-Verlet steps of size dt (> 0): the multi-stage symplectic scheme with
+ * the kinematic constraints enforced after every stage (Results, "Performance-oriented software
+ * design"), each step a half kinematic stage (x += dt/2 v, Q <- exp(-dt/2 [w]x) Q), the loads of
+ * Eq. 1a and Eq. 1b at the half step (contact included when enabled), the dynamic update of v
+ * and w, and the second half kinematic stage.  Enqueued on the system's stream;
  * the call synchronises that stream at the end and returns the device error word
  * (ROD_ERR_NONFINITE / ROD_ERR_OVERFLOW / ROD_ERR_TIMEOUT) if one was raised. */
 rod_status rod_system_step(rod_system* sys, int64_t n_steps, double dt);
@@ -138,7 +146,9 @@ rod_status rod_system_step(rod_system* sys, int64_t n_steps, double dt);
 rod_status rod_system_step_async(rod_system* sys, int64_t n_steps, double dt);
 rod_status rod_system_sync(rod_system* sys);
 
-/* Rod-rod contact (a8-a9 of the step): enable = 0 disables it.  k: spring stiffness (N/m),
+/* Rod-rod contact (Results, "Fibrous granular materials": a normal spring-dashpot force between
+ * touching filaments, found through a hash grid instead of an exhaustive search, Fig. 2e):
+ * enable = 0 disables it.  k: spring stiffness (N/m),
  * c: dashpot coefficient (N s/m), cell_size: requested cell edge; the grid uses
  * max(cell_size, 2 r_max + 2 l_max (+ the skin)) where l_max is the longest element of the
  * state given to the next set_state (an element later stretched beyond 2 l_max, less a rounding
@@ -170,13 +180,28 @@ rod_status rod_system_contact_list_builds(rod_system* sys, int64_t* n);
  * normal force.  mu = 0 turns it off.  ROD_ERR_ARG for mu < 0 or, with mu > 0, v_slip <= 0. */
 rod_status rod_system_friction(rod_system* sys, double mu, double v_slip);
 
-/* Right-hand side at the current state and time t: node accelerations acc_v [3*N] and
+/* Right-hand side of Eq. 1a and Eq. 1b (Methods, "Cosserat rod dynamics") at the current state
+ * and time t: node accelerations acc_v [3*N] (Eq. 1a divided by the lumped node mass) and
  * element angular accelerations acc_w [3*E] (constraints on rates applied: clamped node 0
  * and element 0 read zero), contact forces included when enabled.  Device pointers. */
 rod_status rod_system_rhs(rod_system* sys, double t, double* acc_v, double* acc_w);
 
-/* Contact forces on the nodes [3*N] at the current state (zero when contact is off). Device pointer. */
+/* Contact forces on the nodes [3*N] at the current state (zero when contact is off), the
+ * spring-dashpot term of f in Eq. 1a (Results, "Fibrous granular materials"). Device pointer. */
 rod_status rod_system_contact_forces(rod_system* sys, double* f);
+
+/* Contact pair set of the current state (Results, "Fibrous granular materials", Fig. 2e: the
+ * hash-grid search must find exactly the pairs an exhaustive search finds), for checking the
+ * broad phase.  The cell grid is built and searched as in a step without a skin list; every
+ * pair of segments (a, b) of different rods, a < b (element indices in CSR order), whose
+ * closest-point distance is below r_a + r_b is written to pairs[2k], pairs[2k + 1] for
+ * k < cap, in no particular order.  *n_pairs receives the number of such pairs (which may
+ * exceed cap: then only cap were written) and *n_candidates, when not NULL, the number of pairs
+ * that reached the FP64 evaluation after the grid and the FP32 cull.  pairs: host buffer of
+ * 2*cap int64 (may be NULL with cap = 0 to count only).  Synchronises; ROD_ERR_STATE without a
+ * state or with contact disabled. */
+rod_status rod_system_contact_pairs(rod_system* sys, int64_t* pairs, int64_t cap, int64_t* n_pairs,
+                                    int64_t* n_candidates);
 
 /* Launch shape used by the step kernels: elements per thread block and threads per block
  * (0 keeps the built-in default for that value).  Returns ROD_ERR_ARG if the shape cannot
@@ -393,7 +418,9 @@ rod_status rod_surrogate_rollout_local(rod_surrogate* sur, rod_system* sys, rod_
  *   radius    device double [n_rods]
  *   x, v      device double [3 * N], component-major node positions and velocities
  *   k, c      spring stiffness and dashpot coefficient (finite, >= 0)
- *   cell_size requested cell edge; the grid uses max(cell_size, 2 r_max + l_max) of these positions
+ *   cell_size requested cell edge; the grid uses max(cell_size, 2 r_max + l_max) of these positions,
+ *             grown (which keeps the search exact) until the grid over the midpoints' bounding
+ *             box has at most ROD_NOALLOC_MAX_CELLS cells
  *   f         device double [3 * N] output, overwritten with the contact force on every node
  *   cuda_stream  stream to run on (NULL = legacy default stream)
  * The same forces as rod_system_contact_forces for the same state (pair set exact, sums in

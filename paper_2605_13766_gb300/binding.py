@@ -100,6 +100,7 @@ _SIGNATURES = {
     "rod_system_contact_list_builds": ([_P, _P], C.c_int),
     "rod_system_rhs": ([_P, C.c_double, _P, _P], C.c_int),
     "rod_system_contact_forces": ([_P, _P], C.c_int),
+    "rod_system_contact_pairs": ([_P, _P, C.c_int64, _P, _P], C.c_int),
     "rod_system_set_launch": ([_P, C.c_int32, C.c_int32], C.c_int),
     "rod_system_get_launch": ([_P, _P, _P], C.c_int),
     "rod_system_pack_info": ([_P, _P, _P, _P], C.c_int),
@@ -372,6 +373,28 @@ class RodSystem:
         f = torch.empty((3, self.n_nodes), dtype=torch.float64, device="cuda")
         _check(self.lib.rod_system_contact_forces(self.handle, f.data_ptr()))
         return f
+
+    def contact_pair_count(self):
+        """(segment pairs in contact, candidate pairs that reached the FP64 test) at the current
+        state, by the cell-grid search."""
+        n, nc = C.c_int64(0), C.c_int64(0)
+        _check(self.lib.rod_system_contact_pairs(self.handle, None, 0, C.byref(n), C.byref(nc)))
+        return int(n.value), int(nc.value)
+
+    def contact_pairs(self, cap: Optional[int] = None):
+        """Pairs (a, b), a < b, of segments of different rods in contact at the current state,
+        found by the cell-grid search: (int64 array [n, 2] sorted by rows, candidates that
+        reached the FP64 test).  cap=None counts first and then fetches them all."""
+        n, nc = C.c_int64(0), C.c_int64(0)
+        if cap is None:
+            _check(self.lib.rod_system_contact_pairs(self.handle, None, 0, C.byref(n), C.byref(nc)))
+            cap = int(n.value)
+        buf = np.zeros((max(int(cap), 1), 2), dtype=np.int64)
+        _check(self.lib.rod_system_contact_pairs(self.handle, buf.ctypes.data if cap > 0 else None, int(cap),
+                                                 C.byref(n), C.byref(nc)))
+        got = buf[:min(int(n.value), int(cap))]
+        got = got[np.lexsort((got[:, 1], got[:, 0]))] if len(got) else got.reshape(0, 2)
+        return got, int(nc.value)
 
     # -- differentiation
     def set_params(self, rest_kappa=None, elem_couple=None):

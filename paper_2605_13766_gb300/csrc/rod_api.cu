@@ -165,6 +165,17 @@ __global__ void nonfinite_kernel(const double* __restrict__ a, int64_t n, int* e
 
 }  // namespace
 
+// One captured CUDA graph of `steps` contact steps and what was baked into it.
+struct StepGraph {
+  cudaGraphExec_t exec = nullptr;
+  int steps = 0;
+  double dt = 0.0;
+  int grid_version = -1;
+  bool list = false;  // captured with the skin list
+  int shape_version = -1;
+  StepParams params{};  // the step kernel's parameters baked into the graph
+};
+
 struct rod_system {
   int R = 0;
   int64_t N = 0, E = 0, V = 0;
@@ -208,16 +219,13 @@ struct rod_system {
   // launch accounting / timing
   Profiler prof;
   LaunchHook hook;
-  // CUDA graph of kGraphSteps contact steps (captured on cap_stream, replayed on stream)
+  // CUDA graphs of contact steps (captured on cap_stream, replayed on stream): one of
+  // kGraphSteps steps for long calls and one of a single step for the rest of a call
   cudaStream_t cap_stream = nullptr;
   cudaStream_t body_stream = nullptr;  // captures the bodies of the graph's conditional nodes
   DevBuf<double> t_dev;
-  cudaGraphExec_t graph_exec = nullptr;
-  double graph_dt = 0.0;
-  int graph_grid_version = -1;
-  bool graph_list = false;  // the graph was captured with the skin list
-  int shape_version = 0, graph_shape_version = -1;
-  StepParams graph_params{};  // the step kernel's parameters baked into the captured graph
+  StepGraph graphs[2];
+  int shape_version = 0;
   bool use_graphs = true;
   // adjoint: checkpoints of the last checkpointed forward run, recompute buffers
   DevBuf<double> ckpt, seg_states, adj, final_state;
@@ -517,26 +525,27 @@ cudaError_t capture_list_step(rod_system* s) {
   return contact_list_force(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->err.p, s->cap_stream, none);
 }
 
-rod_status ensure_contact_graph(rod_system* s, const StepParams& Pb, double dt) {
+// The graph of g.steps contact steps for the current state, captured when something baked into
+// it changed.  A capture that fails turns graphs off for the system (eager launches).
+rod_status ensure_contact_graph(rod_system* s, StepGraph& g, const StepParams& Pb, double dt) {
   StepParams Pg = Pb;
   Pg.t_dev = s->t_dev.p;
   // reuse the graph while nothing baked into it has changed: the step kernel's parameters
   // (every pointer and constant; the structures are zero-initialised, so whole-object
   // comparison is exact), dt, the launch shape and the contact state's version
-  if (s->graph_exec && s->graph_dt == dt && s->graph_grid_version == s->contact.version &&
-      s->graph_list == (s->contact.skin > 0.0) && s->graph_shape_version == s->shape_version &&
-      std::memcmp(&s->graph_params, &Pg, sizeof Pg) == 0)
+  const bool list = s->contact.skin > 0.0;
+  if (g.exec && g.dt == dt && g.grid_version == s->contact.version && g.list == list &&
+      g.shape_version == s->shape_version && std::memcmp(&g.params, &Pg, sizeof Pg) == 0)
     return ROD_OK;
-  if (s->graph_exec) {
-    cudaGraphExecDestroy(s->graph_exec);
-    s->graph_exec = nullptr;
+  if (g.exec) {
+    cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
   }
   LaunchHook none;
   cudaGraph_t graph = nullptr;
-  const bool list = s->contact.skin > 0.0;
   CUDA_TRY(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
+  for (int k = 0; k < g.steps && e == cudaSuccess; ++k) {
     e = list ? capture_list_step(s)
              : contact_compute(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->R, s->err.p, s->cap_stream,
                                none, true);
@@ -554,19 +563,19 @@ rod_status ensure_contact_graph(rod_system* s, const StepParams& Pb, double dt) 
     s->use_graphs = false;  // eager launches from now on
     return ROD_OK;
   }
-  e = cudaGraphInstantiate(&s->graph_exec, graph, 0);
+  e = cudaGraphInstantiate(&g.exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
-    s->graph_exec = nullptr;
+    g.exec = nullptr;
     cudaGetLastError();
     s->use_graphs = false;
     return ROD_OK;
   }
-  s->graph_dt = dt;
-  s->graph_grid_version = s->contact.version;
-  s->graph_list = list;
-  s->graph_shape_version = s->shape_version;
-  s->graph_params = Pg;
+  g.dt = dt;
+  g.grid_version = s->contact.version;
+  g.list = list;
+  g.shape_version = s->shape_version;
+  g.params = Pg;
   return ROD_OK;
 }
 
@@ -862,6 +871,8 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
   if ((ce = cudaMemset(s->err.p, 0, sizeof(int))) || (ce = cudaMallocHost(&s->err_host, sizeof(int))))
     return cleanup(fail(ROD_ERR_CUDA, "allocation failed: %s", cudaGetErrorString(ce)));
   *s->err_host = 0;
+  s->graphs[0].steps = kGraphSteps;
+  s->graphs[1].steps = 1;
   rod_status st = build_packs(s, default_shape(s));
   if (st != ROD_OK) return cleanup(st);
   *out = s;
@@ -900,7 +911,8 @@ rod_status rod_system_destroy(rod_system* s) {
   s->adj_packs.release();
   s->err.release();
   contact_release(s->contact);
-  if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+  for (StepGraph& g : s->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   if (s->body_stream) cudaStreamDestroy(s->body_stream);
   s->t_dev.release();
@@ -1014,16 +1026,24 @@ rod_status rod_system_step_async(rod_system* s, int64_t n_steps, double dt) {
     // steps 0 .. n-2 bin the next step's positions; the last one ends on a half step
     const int64_t binned = n_steps - 1;
     int64_t k = 0;
+    // Binned steps replay the kGraphSteps-step graph, then the one-step graph for the rest.
     // (cooperative launches of long rods stay eager: no graph replay when there are any)
-    if (s->use_graphs && !s->prof.enabled && binned >= kGraphSteps && s->long_packs.empty()) {
-      st = ensure_contact_graph(s, Pb, dt);
-      if (st != ROD_OK) return st;
-      if (s->graph_exec) {
-        set_time_kernel<<<1, 1, 0, s->stream>>>(s->t_dev.p, s->t);
-        s->prof.launches += 1;
-        for (; k + kGraphSteps <= binned; k += kGraphSteps) {
-          CUDA_TRY(cudaGraphLaunch(s->graph_exec, s->stream));
-          s->prof.launches += kGraphSteps * (list ? kKernelsPerListGraphStep : kKernelsPerGraphStep);
+    if (s->use_graphs && !s->prof.enabled && binned >= 1 && s->long_packs.empty()) {
+      bool time_set = false;
+      for (StepGraph& g : s->graphs) {
+        if (binned - k < g.steps) continue;
+        st = ensure_contact_graph(s, g, Pb, dt);
+        if (st != ROD_OK) return st;
+        if (!g.exec) break;
+        if (!time_set) {
+          set_time_kernel<<<1, 1, 0, s->stream>>>(s->t_dev.p, s->t);
+          CUDA_TRY(cudaGetLastError());
+          s->prof.launches += 1;
+          time_set = true;
+        }
+        for (; k + g.steps <= binned; k += g.steps) {
+          CUDA_TRY(cudaGraphLaunch(g.exec, s->stream));
+          s->prof.launches += g.steps * (list ? kKernelsPerListGraphStep : kKernelsPerGraphStep);
         }
       }
     }
@@ -1124,6 +1144,38 @@ rod_status rod_system_contact_forces(rod_system* s, double* f) {
   CUDA_TRY(contact_list_invalidate(s->contact, s->stream));  // the cell structures were overwritten
   CUDA_TRY(contact_node_forces(s->contact, s->rods.p, s->N, s->E, s->R, f, s->stream, s->hook));
   return read_error_word(s);
+}
+
+rod_status rod_system_contact_pairs(rod_system* s, int64_t* pairs, int64_t cap, int64_t* n_pairs,
+                                    int64_t* n_candidates) {
+  if (!s || !n_pairs || cap < 0 || (cap > 0 && !pairs)) return fail(ROD_ERR_ARG, "bad argument");
+  if (!s->state_set) return fail(ROD_ERR_STATE, "no state has been set");
+  if (!s->contact.enabled) return fail(ROD_ERR_STATE, "contact is disabled");
+  rod_status st = contact_prepare(s->contact, s->rods_h, s->rods.p, s->x.p, s->N, s->E, s->R, s->stream, s->hook);
+  if (st != ROD_OK) return st;
+  // scratch of this debug call only (freed before it returns)
+  DevBuf<unsigned long long> counts;
+  DevBuf<int64_t> out;
+  unsigned long long c[2] = {0, 0};
+  cudaError_t e = counts.alloc(2);
+  if (!e) e = out.alloc(std::max<int64_t>(2 * cap, 2));
+  if (!e)
+    e = contact_pairs(s->contact, s->x.p, s->v.p, s->rods.p, s->N, s->E, s->err.p, counts.p, out.p, cap, s->stream,
+                      s->hook);
+  if (!e) e = contact_list_invalidate(s->contact, s->stream);  // the cell structures were overwritten
+  if (!e) e = cudaMemcpyAsync(c, counts.p, sizeof c, cudaMemcpyDeviceToHost, s->stream);
+  if (!e) e = cudaStreamSynchronize(s->stream);
+  const int64_t n = static_cast<int64_t>(c[0]);
+  if (!e && cap > 0 && n > 0)
+    e = cudaMemcpy(pairs, out.p, 2 * std::min(n, cap) * sizeof(int64_t), cudaMemcpyDeviceToHost);
+  counts.release();
+  out.release();
+  CUDA_TRY(e);
+  st = read_error_word(s);
+  if (st != ROD_OK) return st;
+  *n_pairs = n;
+  if (n_candidates) *n_candidates = static_cast<int64_t>(c[1]);
+  return ROD_OK;
 }
 
 rod_status rod_system_set_launch(rod_system* s, int32_t elems_per_block, int32_t threads_per_block) {

@@ -657,6 +657,37 @@ __global__ void node_forces_kernel(const double* __restrict__ fseg, const RodCon
   }
 }
 
+// Pair-set query: the visitor of one segment a records every pair (a, b), a < b, that survives
+// the FP32 cull (a candidate) and, of those, every pair the FP64 evaluation finds in contact
+// (positive overlap), in any order (atomic slots); counts keep rising past the capacity.
+struct PairRecord {
+  const ContactArgs& A;
+  int a, ra;
+  unsigned long long* counts;  // [0] pairs in contact, [1] candidates
+  int64_t* out;
+  int64_t cap;
+  __device__ void operator()(int b, int rb) {
+    if (b <= a) return;  // each pair once, from its lower segment
+    atomicAdd(&counts[1], 1ull);
+    if (!pair_force(A, a, ra, b, rb).hit) return;
+    const unsigned long long k = atomicAdd(&counts[0], 1ull);
+    if (k < static_cast<unsigned long long>(cap)) {
+      out[2 * k] = a;
+      out[2 * k + 1] = b;
+    }
+  }
+};
+
+__global__ void __launch_bounds__(256) pairs_kernel(ContactArgs A, unsigned long long* counts, int64_t* out,
+                                                    int64_t cap) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= A.E) return;
+  if (*(volatile int*)A.err != 0) return;
+  const int4 ba = A.recB[q];
+  PairRecord rec{A, ba.x, ba.y, counts, out, cap};
+  scan_neighbourhood(A, q, 0.f, rec);
+}
+
 template <typename T>
 cudaError_t dev_alloc(T** p, size_t count) {
   if (*p) cudaFree(*p);
@@ -776,21 +807,35 @@ rod_status contact_prepare(ContactState& cs, const std::vector<RodConst>& rods_h
   // by tens of percent) before a longer one latches ROD_ERR_OVERFLOW
   const double skin = cs.skin > 0.0 ? cs.skin : 0.0;
   double h = std::max(cs.cell_size, 2.0 * rmax + kStretchAllowance * lmax + skin);
-  double ext[3], margin[3];
-  int64_t ncell = 0;
-  for (int iter = 0; iter < 64; ++iter) {
-    ncell = 1;
+  if (!(h > 0.0)) h = 1.0;  // zero radii and lengths touch nothing: any positive edge is exact
+  double ext[3], margin[3], dimd[3];
+  double ncell_d = 0.0;
+  // dimensions in double, clamped before the integer conversion (finite but huge extents of a
+  // diverged state cannot overflow them); a larger cell edge keeps the search exact
+  auto fit = [&](double hh) {
+    ncell_d = 1.0;
     for (int c = 0; c < 3; ++c) {
       ext[c] = hi[c] - lo[c];
-      margin[c] = std::max(0.1 * ext[c], 2.0 * h);
+      margin[c] = std::max(0.1 * ext[c], 2.0 * hh);
       const double span = ext[c] + 2.0 * margin[c];
-      cs.dim[c] = static_cast<int>(std::floor(span / h)) + 1;
-      ncell *= cs.dim[c];
+      dimd[c] = std::min(std::floor(span / hh) + 1.0, double(kMaxCells) + 1.0);
+      ncell_d *= dimd[c];
     }
-    if (ncell <= kMaxCells) break;
-    h *= 1.25;
+    return ncell_d <= double(kMaxCells);
+  };
+  bool fits = false;
+  for (int iter = 0; iter < 64 && !(fits = fit(h)); ++iter) h *= 1.25;
+  if (!fits) {
+    // at most about 200 cells per dimension: span / h <= max(1.2 ext / h, ext / h + 4)
+    h = std::max(h, 1.2 * std::max(ext[0], std::max(ext[1], ext[2])) / 200.0);
+    fits = fit(h);
   }
-  for (int c = 0; c < 3; ++c) cs.lo[c] = lo[c] - margin[c];
+  if (!fits) return cfail(ROD_ERR_OVERFLOW, "contact grid: the positions span too many cells", cudaSuccess);
+  const int64_t ncell = static_cast<int64_t>(ncell_d);
+  for (int c = 0; c < 3; ++c) {
+    cs.dim[c] = static_cast<int>(dimd[c]);
+    cs.lo[c] = lo[c] - margin[c];
+  }
   cs.h = h;
   cs.inv_h = 1.0 / h;
   cs.ncell = ncell;
@@ -969,6 +1014,19 @@ cudaError_t contact_compute(ContactState& cs, const double* x, const double* v, 
   hook.before(K_CONTACT_GATHER, st);
   gather_kernel<<<(E + 255) / 256, 256, 0, st>>>(A);
   hook.after(K_CONTACT_GATHER, st);
+  return cudaGetLastError();
+}
+
+cudaError_t contact_pairs(ContactState& cs, const double* x, const double* v, const RodConst* rods, int64_t N,
+                          int64_t E, int* err, unsigned long long* counts, int64_t* out, int64_t cap, cudaStream_t st,
+                          const LaunchHook& hook) {
+  cudaError_t e = enqueue_build(cs, x, rods, N, E, err, st, hook, false, nullptr);
+  if (e) return e;
+  if ((e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), st))) return e;
+  const ContactArgs A = make_args(cs, x, v, rods, N, E, err, nullptr);
+  hook.before(K_MISC, st);
+  pairs_kernel<<<(E + 255) / 256, 256, 0, st>>>(A, counts, out, cap);
+  hook.after(K_MISC, st);
   return cudaGetLastError();
 }
 

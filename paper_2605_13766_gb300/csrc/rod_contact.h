@@ -117,6 +117,13 @@ void contact_list_params(const ContactState& cs, StepParams& P);
 // Make the next list evaluation rebuild (after anything that overwrote the cell structures).
 cudaError_t contact_list_invalidate(const ContactState& cs, cudaStream_t st);
 
+// Pair set of positions x by the cell-grid search (debug / parity entry point): the pairs (a, b),
+// a < b, in contact go to out[2k], out[2k + 1] for k < cap; counts[0] = pairs in contact,
+// counts[1] = candidate pairs that passed the FP32 cull (device words, overwritten).
+cudaError_t contact_pairs(ContactState& cs, const double* x, const double* v, const RodConst* rods, int64_t N,
+                          int64_t E, int* err, unsigned long long* counts, int64_t* out, int64_t cap, cudaStream_t st,
+                          const LaunchHook& hook);
+
 // Sum cs.fseg into node forces f [3N] (debug / parity entry point).
 cudaError_t contact_node_forces(const ContactState& cs, const RodConst* rods, int64_t N, int64_t E, int R, double* f,
                                 cudaStream_t st, const LaunchHook& hook);

@@ -159,8 +159,10 @@ __global__ void grid_kernel(Args A, View s) {
     lo[c] = ounkey(g->lo_key[c]);
     ext[c] = ounkey(g->hi_key[c]) - lo[c];
   }
-  bool ok = isfinite(h) && h > 0.0;
+  bool ok = isfinite(h);
   for (int c = 0; c < 3; ++c) ok = ok && isfinite(lo[c]) && isfinite(ext[c]);
+  // zero radii and zero-length segments (h = 0) touch nothing: any positive cell edge is exact
+  if (ok && !(h > 0.0)) h = 1.0;
   if (!ok) {
     g->err |= ERR_NONFINITE;
     for (int c = 0; c < 3; ++c) g->dim[c] = 1;
@@ -169,17 +171,37 @@ __global__ void grid_kernel(Args A, View s) {
     g->inv_h = 1.0;
     return;
   }
-  int64_t n = 0;
-  for (int it = 0; it < 200; ++it) {  // grow the cell until the grid fits the scratch
-    n = 1;
+  // Grow the cell edge until the grid fits the scratch (a larger edge keeps the search exact).
+  // Dimensions are formed in double and clamped before any integer conversion, so extents of
+  // any finite size (a diverged state) cannot overflow them; when 200 growth steps are not
+  // enough, the edge jumps to the largest extent / 63, which gives at most 64^3 cells.
+  double dim[3], n = 0.0;
+  auto fit = [&](double hh) {
+    n = 1.0;
     for (int c = 0; c < 3; ++c) {
-      g->dim[c] = static_cast<int>(floor(ext[c] / h)) + 1;
-      n *= g->dim[c];
+      dim[c] = fmin(floor(ext[c] / hh) + 1.0, (double)kMaxCells + 1.0);
+      n *= dim[c];
     }
-    if (n <= kMaxCells) break;
-    h *= 1.25;
+    return n <= (double)kMaxCells;
+  };
+  bool fits = false;
+  for (int it = 0; it < 200 && !(fits = fit(h)); ++it) h *= 1.25;
+  if (!fits) {
+    h = fmax(h, fmax(ext[0], fmax(ext[1], ext[2])) / 63.0);
+    fits = fit(h);
   }
-  for (int c = 0; c < 3; ++c) g->lo[c] = lo[c];
+  if (!fits) {  // unreachable for finite extents; kept so that no size is ever taken unchecked
+    g->err |= ERR_OVERFLOW;
+    for (int c = 0; c < 3; ++c) g->dim[c] = 1;
+    g->ncell = 1;
+    g->h = 1.0;
+    g->inv_h = 1.0;
+    return;
+  }
+  for (int c = 0; c < 3; ++c) {
+    g->lo[c] = lo[c];
+    g->dim[c] = static_cast<int>(dim[c]);
+  }
   g->h = h;
   g->inv_h = 1.0 / h;
   g->ncell = static_cast<int>(n);

@@ -260,7 +260,7 @@ def cilia_carpet(side: int = 64, n: int = 50, spacing: float = 0.05, length: flo
 
 def random_packing(n_rods: int = 10_000, nmin: int = 16, nmax: int = 256, box: float = 1.0,
                    rest_len: float = 1e-3, radius: float = 0.005, youngs: float = 1e6,
-                   density: float = 1000.0, speed: float = 0.5, spin: float = 0.0,
+                   density: float = 1000.0, speed: float = 0.25, spin: float = 0.0,
                    contact_k: float = 1e4, contact_c: float = 10.0, gravity: float = 9.81,
                    dt: float = 5e-6, n_steps: int = 5000, seed: int = 1234,
                    allow_overlap: bool = False, margin: float = 5e-4) -> RodProblem:
@@ -317,7 +317,7 @@ def random_packing_cached(seed: int = 1234, cache_dir: Optional[str] = None) -> 
     import tempfile
     cache_dir = cache_dir or os.path.join(tempfile.gettempdir(), "rodbench_cache")
     os.makedirs(cache_dir, exist_ok=True)
-    key = hashlib.sha1(f"random_packing-default-{seed}-v2".encode()).hexdigest()[:12]
+    key = hashlib.sha1(f"random_packing-default-{seed}-v3".encode()).hexdigest()[:12]
     path = os.path.join(cache_dir, f"packing_{key}.npz")
     if os.path.exists(path):
         try:

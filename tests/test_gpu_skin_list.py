@@ -235,6 +235,30 @@ def test_replayed_graph_launches_rebuild_kernels_only_when_due():
 
 
 
+@pytest.mark.parametrize("K", [2, 20, 45])
+def test_any_step_count_replays_graphs(K):
+    """A call of any length replays graphs for all but its last step: the 32-step graph while
+    32 or more steps remain, then the one-step graph; the trajectory is that of eager launches
+    bit for bit."""
+    p = _touching(60, 0.1, 14)
+    counts, states = {}, {}
+    for graphs in (True, False):
+        s = _gpu(p, 2e-4, graphs=graphs)
+        s.step(1, 2e-6)
+        b0, l0 = s.contact_list_builds(), s.launch_count
+        s.step(K, 2e-6)
+        counts[graphs] = (s.contact_list_builds() - b0, s.launch_count - l0)
+        states[graphs] = s.get_state()
+        s.close()
+    for a, b in zip(states[True], states[False]):
+        assert np.array_equal(a, b)
+    (builds_g, n_g), (builds_e, n_e) = counts[True], counts[False]
+    assert builds_g == builds_e
+    assert n_e == 1 + K * 13
+    # kinematic half step, set_time, K - 1 replayed steps of 4 kernels, the last step eager
+    assert 1 + 1 + (K - 1) * 4 + 13 <= n_g <= 1 + 1 + (K - 1) * 4 + 10 * builds_g + 13
+
+
 def test_replayed_graph_follows_parameter_changes_between_calls():
     """A graph captured for the contact steps is replayed only while nothing baked into it has
     changed: friction set between two step calls, new rest curvatures and element couples, and

@@ -1,5 +1,7 @@
 """The allocation-free contact entry point (rod_contact_forces_noalloc) against the system's own
-contact forces (rod_system_contact_forces) on the same states.
+contact forces (rod_system_contact_forces) and the oracle's exhaustive search on the same states,
+plus the paths that size its fixed scratch: a grid that must grow to fit, finite but huge
+coordinates, a cell that holds too many segments, non-finite positions.
 
 The entry point exists for callers that cannot allocate device memory when they need contact
 forces (code running inside another framework's allocator or memory pool, loops that must stay
@@ -52,6 +54,11 @@ def _packing(seed, n_rods=80, box=0.08):
                                  allow_overlap=True, speed=0.3)
 
 
+def _oracle_forces(p):
+    from oracle.oracle import Oracle
+    return Oracle(p, broad_phase=0).contact_forces(p.x, p.v)
+
+
 def test_two_calls_in_a_row_match_the_system_entry_point():
     first = _packing(21)
     second = rodgen.perturbed(_packing(22, n_rods=120, box=0.1), seed=3, pos=0.05, vel=0.5, rot=0.0, omega=0.0)
@@ -61,6 +68,73 @@ def test_two_calls_in_a_row_match_the_system_entry_point():
         scale = np.abs(ref).max()
         assert scale > 1.0                      # there is contact to compare
         assert np.abs(got - ref).max() <= TOL * scale
+        orc = _oracle_forces(p)
+        assert np.abs(got - orc).max() <= TOL * np.abs(orc).max()
+
+
+def _two_clusters(offset, n_second=25):
+    """Two contact-rich clusters of 25 rods (the second cut to its first n_second rods), the
+    second moved by `offset` (m) along each axis."""
+    a = rodgen.random_packing(n_rods=25, nmin=3, nmax=20, box=0.06, rest_len=2e-3, radius=0.004, seed=31,
+                              allow_overlap=True, speed=0.3)
+    b = rodgen.random_packing(n_rods=25, nmin=3, nmax=20, box=0.06, rest_len=2e-3, radius=0.004, seed=32,
+                              allow_overlap=True, speed=0.3).take_rods(0, n_second)
+    cat = lambda u, w: np.concatenate([u, w], axis=-1)
+    return a.replace(n_elem=cat(a.n_elem, b.n_elem), rest_len=cat(a.rest_len, b.rest_len),
+                     radius=cat(a.radius, b.radius), youngs=cat(a.youngs, b.youngs),
+                     shear_mod=cat(a.shear_mod, b.shear_mod), density=cat(a.density, b.density),
+                     x=cat(a.x, b.x + offset), v=cat(a.v, b.v), Q=cat(a.Q, b.Q), w=cat(a.w, b.w))
+
+
+def test_grid_that_must_grow_to_fit_the_scratch():
+    # 100 m between the clusters with 1 cm cells would need ~10^12 cells: the cell edge grows
+    # until the grid fits ROD_NOALLOC_MAX_CELLS, and the search stays exact
+    p = _two_clusters(100.0)
+    orc = _oracle_forces(p)
+    assert np.abs(orc).max() > 1.0
+    for _ in range(2):
+        got = _noalloc_forces(p)
+        assert np.abs(got - orc).max() <= TOL * np.abs(orc).max()
+    sysf = _system_forces(p)
+    assert np.abs(got - sysf).max() <= TOL * np.abs(sysf).max()
+
+
+def test_finite_but_huge_coordinates_give_exact_forces():
+    # one rod moved to 1e30 m (its nodes coincide there in FP64): the grid's dimensions are
+    # clamped before any integer conversion and the cell edge jumps to the extent / 63
+    p = _two_clusters(1e30, n_second=1)
+    orc = _oracle_forces(p)
+    got = _noalloc_forces(p)
+    assert np.abs(orc).max() > 1.0
+    assert np.abs(got - orc).max() <= TOL * np.abs(orc).max()
+
+
+def _one_element_rods(n_rods, centre_spread, seed=5):
+    p = rodgen.random_packing(n_rods=n_rods, nmin=1, nmax=1, box=centre_spread, rest_len=1e-4, radius=0.004,
+                              seed=seed, allow_overlap=True, speed=0.1)
+    return p
+
+
+def test_a_cell_with_more_than_512_segments_is_rejected():
+    from paper_2605_13766_gb300 import RodError
+    p = _one_element_rods(600, 1e-3)            # 600 segments in one cell of edge >= 8 mm
+    with pytest.raises(RodError) as ei:
+        _noalloc_forces(p)
+    assert ei.value.status == -5 and "512" in str(ei.value)
+    # the next call on a fine state is unaffected by the rejected one
+    q = _packing(23)
+    ref = _system_forces(q)
+    assert np.abs(_noalloc_forces(q) - ref).max() <= TOL * np.abs(ref).max()
+
+
+def test_non_finite_positions_are_rejected():
+    from paper_2605_13766_gb300 import RodError
+    p = _packing(24)
+    x = p.x.copy()
+    x[1, 7] = np.nan
+    with pytest.raises(RodError) as ei:
+        _noalloc_forces(p.replace(x=x))
+    assert ei.value.status == -3
 
 
 def test_sizes_beyond_the_fixed_capacity_are_rejected():

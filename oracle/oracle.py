@@ -4,6 +4,7 @@ TEST INFRASTRUCTURE ONLY.  Arrays follow the component-major layout of ``rodgen`
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -14,8 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SOURCES = ["rod_oracle.c"]
 _LIB_NAME = "liboracle.so"
-_lock = threading.Lock()
-_lib = None
+_lock = threading.RLock()
 
 
 def oracle_library_path() -> str:
@@ -84,11 +84,16 @@ class _Params(C.Structure):
     ]
 
 
+_libs = {}
+_active = None  # path of a library that replaces the default one (pin-strength tests only)
+
+
 def _load():
-    global _lib
     with _lock:
-        if _lib is None:
-            lib = C.CDLL(build_oracle())
+        path = _active or build_oracle()
+        lib = _libs.get(path)
+        if lib is None:
+            lib = C.CDLL(path)
             P = C.POINTER(_Params)
             d = C.c_void_p
             lib.orc_rhs.argtypes = [P, C.c_double, d, d, d, d, d, d]
@@ -105,9 +110,22 @@ def _load():
             lib.orc_orthonormality_error.argtypes = [P, d]
             lib.orc_orthonormality_error.restype = C.c_double
             lib.orc_last_error.restype = C.c_char_p
-            lib.orc_set_mutation.argtypes = [C.c_int]
-            _lib = lib
-    return _lib
+            _libs[path] = lib
+    return lib
+
+
+@contextlib.contextmanager
+def using_library(path):
+    """Within the block, oracles created and module functions called use the oracle library at
+    `path` (a build of a patched source, see mutants.py) instead of the default one."""
+    global _active
+    with _lock:
+        prev, _active = _active, path
+    try:
+        yield
+    finally:
+        with _lock:
+            _active = prev
 
 
 def _f64(a):
@@ -263,6 +281,3 @@ def segment_closest(p0, p1, q0, q1):
     return float(s[0]), float(u[0])
 
 
-def set_mutation(mid: int) -> None:
-    """Plant numbered mistake ``mid`` in the oracle (0 removes it).  Pin-strength tests only."""
-    _load().orc_set_mutation(int(mid))

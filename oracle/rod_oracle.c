@@ -55,9 +55,6 @@
 
 static char g_err[512];
 
-/* Planted mistakes, used only by the tests that show every pin can fail (0 = none). */
-static int g_mut = 0;
-void orc_set_mutation(int id) { g_mut = id; }
 static int fail(const char* msg) {
   snprintf(g_err, sizeof g_err, "%s", msg);
   return -1;
@@ -242,7 +239,7 @@ static void friction_force(double mu, double vslip, double fn, const double nrm[
   for (int c = 0; c < 3; ++c) vt[c] = vrel[c] - vn * nrm[c];
   double sp = sqrt(dot3(vt, vt));
   double den = sp > vslip ? sp : vslip;
-  for (int c = 0; c < 3; ++c) ft[c] = (mu > 0.0 && fn > 0.0) ? (g_mut == 25 ? 1.0 : -1.0) * mu * fn * vt[c] / den : 0.0;
+  for (int c = 0; c < 3; ++c) ft[c] = (mu > 0.0 && fn > 0.0) ? -mu * fn * vt[c] / den : 0.0;
 }
 
 /* ---------------------------------------------------------------- a3-a5: strains */
@@ -414,7 +411,7 @@ static int pair_force(const orc_params* p, const seg_map* m, const double* x, co
     ld3(v, m->N, nb, vb0);
     ld3(v, m->N, nb + 1, vb1);
     for (int c = 0; c < 3; ++c) vrel[c] = ((1.0 - s) * va0[c] + s * va1[c]) - ((1.0 - u) * vb0[c] + u * vb1[c]);
-    fmag = fmag - (g_mut == 11 ? -1.0 : 1.0) * p->contact_c * dot3(vrel, nrm);
+    fmag = fmag - p->contact_c * dot3(vrel, nrm);
     if (fmag < 0.0) fmag = 0.0;
     double ft[3];
     friction_force(p->contact_mu, p->contact_vslip, fmag, nrm, vrel, ft);
@@ -529,7 +526,7 @@ static int for_each_candidate(const orc_params* p, const seg_map* m, const doubl
     int64_t ix = c % cl.dim[0], iy = (c / cl.dim[0]) % cl.dim[1], iz = c / (cl.dim[0] * cl.dim[1]);
     for (int dz = -1; dz <= 1 && !stop; ++dz)
       for (int dy = -1; dy <= 1 && !stop; ++dy)
-        for (int dx = (g_mut == 12 ? 0 : -1); dx <= 1 && !stop; ++dx) {
+        for (int dx = -1; dx <= 1 && !stop; ++dx) {
           int64_t jx = ix + dx, jy = iy + dy, jz = iz + dz;
           if (jx < 0 || jy < 0 || jz < 0 || jx >= cl.dim[0] || jy >= cl.dim[1] || jz >= cl.dim[2]) continue;
           int64_t cc = (jz * cl.dim[1] + jy) * cl.dim[0] + jx;
@@ -562,7 +559,7 @@ static int visit_force(int64_t a, int64_t b, void* vctx) {
   double s, u, f[3], delta;
   if (!pair_force(C->p, C->m, C->x, C->v, a, b, &s, &u, f, &delta)) return 0;
   int64_t na = C->m->node_of[a], nb = C->m->node_of[b], N = C->m->N;
-  double wa = (g_mut == 10) ? s : 1.0 - s;
+  double wa = 1.0 - s;
   acc3(C->f, N, na, f, wa);
   acc3(C->f, N, na + 1, f, 1.0 - wa);
   acc3(C->f, N, nb, f, -(1.0 - u));
@@ -611,7 +608,6 @@ int64_t orc_contact_pairs(const orc_params* p, const double* x, int64_t* pairs, 
 
 static int act_element(const orc_params* p, int r) {
   int clamped = p->clamp_base && p->clamp_base[r];
-  if (g_mut == 20) return 0;
   return (clamped && p->n_elem[r] >= 2) ? 1 : 0;
 }
 
@@ -650,10 +646,7 @@ int orc_rhs(const orc_params* p, double t, const double* x, const double* v, con
       double lg = sqrt(dot3(l, l));
       double e = lg / rl;
       double tt[3] = {l[0] / lg, l[1] / lg, l[2] / lg};
-      if (g_mut == 4)
-        matT_vec(M, l, Ql);
-      else
-        mat_vec(M, l, Ql);
+      mat_vec(M, l, Ql);
       sig[0] = Ql[0] / rl;
       sig[1] = Ql[1] / rl;
       sig[2] = Ql[2] / rl - 1.0;
@@ -661,8 +654,7 @@ int orc_rhs(const orc_params* p, double t, const double* x, const double* v, con
         for (int c = 0; c < 3; ++c) sig[c] -= p->rest_sigma[c * E + ie];
       for (int c = 0; c < 3; ++c) nl[c] = K.S[c] * sig[c];
       matT_vec(M, nl, Nl);
-      if (g_mut != 3)
-        for (int c = 0; c < 3; ++c) Nl[c] = Nl[c] / e;
+      for (int c = 0; c < 3; ++c) Nl[c] = Nl[c] / e;
       st3(Nf, E, ie, Nl);
       dil[ie] = e;
       ell[ie] = lg;
@@ -677,10 +669,6 @@ int orc_rhs(const orc_params* p, double t, const double* x, const double* v, con
       cross3(Jwe, wi, tl);
       double dv[3] = {vb[0] - va[0], vb[1] - va[1], vb[2] - va[2]};
       double edot = dot3(tt, dv) / rl;
-      if (g_mut == 2)
-        for (int c = 0; c < 3; ++c) ts[c] = -ts[c];
-      if (g_mut == 5) edot = 0.0;
-      if (g_mut == 6) tl[0] = tl[1] = tl[2] = 0.0;
       for (int c = 0; c < 3; ++c) tau[c * E + ie] = ts[c] * rl + tl[c] + Jw[c] / (e * e) * edot;
     }
     /* Voronoi points: curvature, bending moment, dilatation */
@@ -693,9 +681,9 @@ int orc_rhs(const orc_params* p, double t, const double* x, const double* v, con
       orc_rot_log(R, phi);
       double rla = p->rest_len[ie], rlb = p->rest_len[ie + 1];
       double D = 0.5 * (rla + rlb);
-      for (int c = 0; c < 3; ++c) kap[c] = (g_mut == 9 ? phi[c] : -phi[c]) / D;
+      for (int c = 0; c < 3; ++c) kap[c] = -phi[c] / D;
       double eps = (ell[ie] + ell[ie + 1]) / (rla + rlb);
-      double eps3 = (g_mut == 8) ? eps * eps : eps * eps * eps;
+      double eps3 = eps * eps * eps;
       for (int c = 0; c < 3; ++c) {
         double k0 = p->rest_kappa ? p->rest_kappa[c * V + iv] : 0.0;
         mk[c] = K.B[c] * (kap[c] - k0);
@@ -722,8 +710,8 @@ int orc_rhs(const orc_params* p, double t, const double* x, const double* v, con
         double Pm = (i >= 1) ? P[c * V + g.vor0 + i - 1] : 0.0;
         double Ti = (i <= g.n - 2) ? T[c * V + g.vor0 + i] : 0.0;
         double Tm = (i >= 1) ? T[c * V + g.vor0 + i - 1] : 0.0;
-        tot[c] = (Pi - Pm) + (g_mut == 1 ? 0.0 : 0.5 * (Tm + Ti)) + tau[c * E + ie];
-        if (g_mut != 15) tot[c] += -p->nu_damp * rl * (K.I[c] / K.A) * wi[c];
+        tot[c] = (Pi - Pm) + 0.5 * (Tm + Ti) + tau[c * E + ie];
+        tot[c] += -p->nu_damp * rl * (K.I[c] / K.A) * wi[c];
         if (p->elem_couple) tot[c] += p->elem_couple[c * E + ie];
       }
       if (p->act_amp && i == iact)
@@ -733,8 +721,7 @@ int orc_rhs(const orc_params* p, double t, const double* x, const double* v, con
         double M[9], qb[3], mi[3], cmag[3];
         ldQ(Q, E, ie, M);
         for (int a = 0; a < 3; ++a)
-          qb[a] = (g_mut == 22) ? M[a] * bt[0] + M[3 + a] * bt[1] + M[6 + a] * bt[2]
-                                : M[3 * a] * bt[0] + M[3 * a + 1] * bt[1] + M[3 * a + 2] * bt[2];
+          qb[a] = M[3 * a] * bt[0] + M[3 * a + 1] * bt[1] + M[3 * a + 2] * bt[2];
         ld3(p->magnetization, E, ie, mi);
         cross3(mi, qb, cmag);
         for (int c = 0; c < 3; ++c) tot[c] += rl * cmag[c];
@@ -747,16 +734,16 @@ int orc_rhs(const orc_params* p, double t, const double* x, const double* v, con
         double om = 2.0 * M_PI / p->muscle_period[r], kw = 2.0 * M_PI / p->muscle_wavelength[r];
         double tr = (i <= g.n - 2) ? p->muscle_amp[r] * sin(om * t - kw * s_right + p->muscle_phase[r]) : 0.0;
         double tl = (i >= 1) ? p->muscle_amp[r] * sin(om * t - kw * s_left + p->muscle_phase[r]) : 0.0;
-        tot[0] += (g_mut == 23) ? tr - tl : tl - tr;
+        tot[0] += tl - tr;
       }
-      for (int c = 0; c < 3; ++c) acc_w[c * E + ie] = (g_mut == 17 ? 1.0 : dil[ie]) * tot[c] / (K.rho * rl * K.I[c]);
+      for (int c = 0; c < 3; ++c) acc_w[c * E + ie] = dil[ie] * tot[c] / (K.rho * rl * K.I[c]);
     }
     /* node accelerations */
     for (int j = 0; j <= g.n; ++j) {
       int64_t jn = g.node0 + j;
       double rl_l = (j >= 1) ? p->rest_len[g.elem0 + j - 1] : 0.0;
       double rl_r = (j <= g.n - 1) ? p->rest_len[g.elem0 + j] : 0.0;
-      double mass = (g_mut == 14 ? 1.0 : 0.5) * K.rho * K.A * (rl_l + rl_r);
+      double mass = 0.5 * K.rho * K.A * (rl_l + rl_r);
       double rlN = 0.5 * (rl_l + rl_r);
       double F[3], vj[3];
       ld3(v, N, jn, vj);
@@ -764,8 +751,8 @@ int orc_rhs(const orc_params* p, double t, const double* x, const double* v, con
         double Nr = (j <= g.n - 1) ? Nf[c * E + g.elem0 + j] : 0.0;
         double Nlft = (j >= 1) ? Nf[c * E + g.elem0 + j - 1] : 0.0;
         F[c] = Nr - Nlft;
-        F[c] += (g_mut == 19 ? -1.0 : 1.0) * mass * p->gravity[c];
-        F[c] += -(p->nu_damp + (g_mut == 21 ? 0.0 : p->stokes_gamma)) * rlN * vj[c];
+        F[c] += mass * p->gravity[c];
+        F[c] += -(p->nu_damp + p->stokes_gamma) * rlN * vj[c];
         F[c] += fc[c * N + jn];
         if (p->tip_force && j == g.n) F[c] += p->tip_force[c * p->n_rods + r];
       }
@@ -777,7 +764,7 @@ int orc_rhs(const orc_params* p, double t, const double* x, const double* v, con
         if (p->wall_velocity)
           for (int c = 0; c < 3; ++c) u[c] = p->wall_velocity[3 * k + c];
         for (int c = 0; c < 3; ++c) d[c] = xj[c] - (p->wall_point[3 * k + c] + u[c] * t);
-        double delta = (g_mut == 24 ? 0.0 : p->radius[r]) - dot3(d, nn);
+        double delta = p->radius[r] - dot3(d, nn);
         if (!(delta > 0.0)) continue;
         for (int c = 0; c < 3; ++c) vrel[c] = vj[c] - u[c];
         double fn = p->wall_k * delta - p->wall_c * dot3(vrel, nn);
@@ -816,7 +803,7 @@ static void kinematic_half(const orc_params* p, double h, double* x, const doubl
     for (int c = 0; c < 3; ++c) x[c * N + j] += h * v[c * N + j];
   for (int64_t i = 0; i < E; ++i) {
     double M[9], R[9], Mn[9], phi[3];
-    for (int c = 0; c < 3; ++c) phi[c] = (g_mut == 7 ? h : -h) * w[c * E + i];
+    for (int c = 0; c < 3; ++c) phi[c] = -h * w[c * E + i];
     orc_rot_exp(phi, R);
     ldQ(Q, E, i, M);
     mat_mul(R, M, Mn);
@@ -909,8 +896,8 @@ double orc_energy(const orc_params* p, const double* x, const double* v, const d
       double vj[3], xj[3];
       ld3(v, N, jn, vj);
       ld3(x, N, jn, xj);
-      H += (g_mut == 30 ? 1.0 : 0.5) * mass * dot3(vj, vj);
-      H -= (g_mut == 29 ? -1.0 : 1.0) * mass * dot3(p->gravity, xj);
+      H += 0.5 * mass * dot3(vj, vj);
+      H -= mass * dot3(p->gravity, xj);
       if (p->tip_force && j == g.n) {
         double F[3] = {p->tip_force[r], p->tip_force[p->n_rods + r], p->tip_force[2 * p->n_rods + r]};
         H -= dot3(F, xj);
@@ -922,13 +909,13 @@ double orc_energy(const orc_params* p, const double* x, const double* v, const d
       for (int c = 0; c < 3; ++c) {
         double wc = w[c * E + ie];
         double sc = sig[c * E + ie] - (p->rest_sigma ? p->rest_sigma[c * E + ie] : 0.0);
-        H += 0.5 * K.rho * rl * K.I[g_mut == 27 ? 0 : c] * wc * wc;
-        H += 0.5 * rl * K.S[g_mut == 28 ? 2 : c] * sc * sc;
+        H += 0.5 * K.rho * rl * K.I[c] * wc * wc;
+        H += 0.5 * rl * K.S[c] * sc * sc;
       }
     }
     for (int k = 0; k < g.n - 1; ++k) {
       int64_t iv = g.vor0 + k;
-      double D = (g_mut == 26) ? p->rest_len[g.elem0 + k] : 0.5 * (p->rest_len[g.elem0 + k] + p->rest_len[g.elem0 + k + 1]);
+      double D = 0.5 * (p->rest_len[g.elem0 + k] + p->rest_len[g.elem0 + k + 1]);
       for (int c = 0; c < 3; ++c) {
         double kc = kap[c * V + iv] - (p->rest_kappa ? p->rest_kappa[c * V + iv] : 0.0);
         H += 0.5 * D * K.B[c] * kc * kc;

@@ -123,9 +123,6 @@ double orc_energy(const orc_params* p, const double* x, const double* v, const d
 /* max over elements of |Q Q^T - I|_inf */
 double orc_orthonormality_error(const orc_params* p, const double* Q);
 
-/* Plant a numbered mistake (0 = none).  Only for the tests that show every pin can fail. */
-void orc_set_mutation(int id);
-
 /* last error message */
 const char* orc_last_error(void);
 

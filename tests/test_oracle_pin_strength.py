@@ -1,14 +1,16 @@
 """Every planted mistake in the oracle makes at least one physics pin fail.
 
-The oracle carries a switch that plants one numbered mistake at a time (a dropped term, a
-flipped sign, a transposed operand, a wrong factor or index).  For each one this test runs the
-pins of the other oracle test files and requires that some pin fails, so the pins can tell a
-correct oracle from a plausibly wrong one.
+oracle/mutants.py lists numbered mistakes (a dropped term, a flipped sign, a transposed
+operand, a wrong factor or index), each a patch of one snippet of the oracle's source compiled
+into a library of its own; the oracle the other tests use has no switch.  For each mistake this
+test runs the pins of the other oracle test files against the patched library and requires
+that some pin fails, so the pins can tell a correct oracle from a plausibly wrong one.
 """
 import numpy as np
 import pytest
 
-from oracle.oracle import set_mutation
+from oracle.mutants import MUTANTS, build_mutant
+from oracle.oracle import using_library
 
 import test_oracle_contact as tc
 import test_oracle_dynamics as td
@@ -45,35 +47,7 @@ PINS = [
     te.test_gravity_and_tip_force_potential,
 ]
 
-MUTATIONS = {
-    1: "bending couple without the (kappa x m) averaging term",
-    2: "shear couple with the wrong sign",
-    3: "internal force without the 1/e factor",
-    4: "shear strain from Q^T l instead of Q l",
-    5: "angular balance without the (J w/e^2) de/dt term",
-    6: "angular balance without the (J w/e) x w term",
-    7: "director update exp(+h[w]x) instead of exp(-h[w]x)",
-    8: "bending couple divided by eps^2 instead of eps^3",
-    9: "curvature from +log instead of -log",
-    10: "contact force split (s, 1-s) instead of (1-s, s)",
-    11: "dashpot with the wrong sign",
-    12: "cell list missing the -x neighbour cells",
-    14: "node mass doubled",
-    15: "no rotational damping",
-    17: "angular acceleration without the e factor",
-    19: "gravity with the wrong sign",
-    20: "actuation couple on the clamped element",
-    21: "no Stokes drag",
-    22: "magnetic couple with Q^T b instead of Q b",
-    23: "muscle couples tau_i - tau_{i-1} instead of tau_{i-1} - tau_i",
-    24: "wall contact without the rod radius",
-    25: "friction along the sliding direction instead of against it",
-    26: "energy: bend/twist term over one element's rest length instead of the Voronoi length",
-    27: "energy: rotational kinetic term with I_1 about every axis",
-    28: "energy: shear terms with the axial stiffness E A",
-    29: "energy: work potential of gravity with the wrong sign",
-    30: "energy: translational kinetic term without the 1/2",
-}
+MUTATIONS = {k: v[0] for k, v in MUTANTS.items()}
 
 
 def _baseline_passes():
@@ -82,15 +56,22 @@ def _baseline_passes():
 
 
 def test_pins_pass_without_mutation():
-    set_mutation(0)
     _baseline_passes()
+
+
+def test_the_default_oracle_has_no_mutation_switch():
+    import os
+    here = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle")
+    for name in ("rod_oracle.c", "rod_oracle.h"):
+        with open(os.path.join(here, name)) as f:
+            text = f.read()
+        assert "mut" not in text.lower(), name
 
 
 @pytest.mark.parametrize("mid", sorted(MUTATIONS))
 def test_each_mutation_fails_some_pin(mid):
     caught = None
-    try:
-        set_mutation(mid)
+    with using_library(build_mutant(mid)):
         with np.errstate(all="ignore"):
             for pin in PINS:
                 try:
@@ -98,6 +79,4 @@ def test_each_mutation_fails_some_pin(mid):
                 except Exception as exc:  # AssertionError, or a NaN blow-up in the oracle
                     caught = f"{getattr(pin, '__name__', 'pin')}: {type(exc).__name__}"
                     break
-    finally:
-        set_mutation(0)
     assert caught is not None, f"mutation {mid} ({MUTATIONS[mid]}) passed every pin"

@@ -50,13 +50,24 @@ FLOPS_PER_UNIT = {
     "pack_steps": 337.2,      # per element-step
 }
 FLOPS_SOURCE = "executed FP64 arithmetic of the kernel (ncu: DFMA x 2 + DADD + DMUL) per element-step"
-# The method's own FP64 work per element-step, counted on the oracle's arithmetic (every FP64
-# add, subtract, multiply and divide of one step, a special function (sqrt, sin, cos, atan2,
-# floor) counted as one operation), for the same workloads; None where not counted.
+# The method's FP64 work per element-step as the oracle states it: every addition, subtraction,
+# multiplication and division of one step of the oracle's source evaluated over counting numbers
+# (oracle/count_flops.py, general bent and spinning states of the packing's and the carpet's
+# recipes); special-function calls (sqrt, sin, cos, atan2, floor) are counted apart.  The kernel
+# executes fewer operations than the oracle states (reciprocals of constants stored once,
+# rotation maps by series, products fused), so the roofline fraction uses the executed count,
+# which never credits the kernel with work it does not do.
 ORACLE_FLOPS_PER_UNIT = {
-    "pack_one_step": None,
-    "pack_steps": None,
+    "pack_one_step": 588.76,   # the step without contact (the step kernel's share)
+    "pack_steps": 588.34,      # the carpet's step
 }
+ORACLE_SPECIAL_PER_UNIT = {
+    "pack_one_step": 8.99,
+    "pack_steps": 8.94,
+}
+# the oracle's contact evaluation (cell list, exact closest points of every candidate) on the
+# packing's placement density, per element-step, on top of the step
+ORACLE_CONTACT_FLOPS_PER_UNIT = 511.02
 # Algorithmic HBM bytes per element-step: the state makes one round trip (6 node + 12 element
 # doubles, read and written: 288 B), the rest length is read (8 B), and with contact each
 # segment's cell key and sorted index are written and read (16 B).
@@ -550,6 +561,9 @@ def main():
             "traffic": TRAFFIC_PER_LAUNCH.get(dname), "avg_launch_ms": avg_ms,
             "flops_per_unit": fpu, "flops_source": FLOPS_SOURCE,
             "flops_per_unit_oracle": ORACLE_FLOPS_PER_UNIT.get(dname),
+            "special_calls_per_unit_oracle": ORACLE_SPECIAL_PER_UNIT.get(dname),
+            "frac_uses": "flops_per_unit (executed by the kernel); flops_per_unit_oracle is the oracle's "
+                         "statement of the same step, counted on its source",
             "peak_source": "FP64: 2 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal unit count; an FMA probe measured 1.91/clk)",
             "hbm_frac": hbm["step_frac"] if hbm else None, "hbm": hbm,
             "kernel_share": {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4)

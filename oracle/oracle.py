@@ -36,6 +36,43 @@ def build_oracle(force: bool = False) -> str:
     return out
 
 
+def build_oracle_ad(force: bool = False) -> str:
+    """Compile oracle_ad.cpp (the oracle's source over dual and counting number types) with g++,
+    same flags as the oracle.  Returns the .so path."""
+    out = os.path.join(_HERE, "liboracle_ad.so")
+    srcs = [os.path.join(_HERE, s) for s in ("oracle_ad.cpp", "rod_oracle.c", "rod_oracle.h")]
+    if not force and os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(s) for s in srcs):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-Wall",
+           "-I", _HERE, "-o", tmp, os.path.join(_HERE, "oracle_ad.cpp"), "-lm"]
+    subprocess.run(cmd, check=True, cwd=_HERE)
+    os.replace(tmp, out)
+    return out
+
+
+_ad_lib = None
+
+
+def _load_ad():
+    global _ad_lib
+    with _lock:
+        if _ad_lib is None:
+            lib = C.CDLL(build_oracle_ad())
+            P = C.POINTER(_Params)
+            d = C.c_void_p
+            lib.orcd_step_jvp.argtypes = [P, C.c_double, C.c_double, C.c_int64] + [d] * 10
+            lib.orcd_last_error.restype = C.c_char_p
+            lib.orcc_step_count.argtypes = [P, C.c_double, C.c_double, C.c_int64] + [d] * 5
+            lib.orcc_last_error.restype = C.c_char_p
+            _ad_lib = lib
+    return _ad_lib
+
+
+# operation classes counted by Oracle.step_count, in the library's order
+COUNT_NAMES = ("add", "mul", "div", "sqrt", "sincos", "atan2", "floor", "fabs")
+
+
 class _Params(C.Structure):
     _fields_ = [
         ("n_rods", C.c_int32),
@@ -220,6 +257,33 @@ class Oracle:
         x, v, Q, w = (np.array(a, dtype=np.float64, order="C", copy=True) for a in (x, v, Q, w))
         self._check(self.lib.orc_step(C.byref(self.params), t, dt, int(n_steps), _ptr(x), _ptr(v), _ptr(Q), _ptr(w)))
         return x, v, Q, w
+
+    def step_jvp(self, state, tangents, dt, n_steps, t=0.0, d_rest_kappa=None, d_elem_couple=None):
+        """Forward-mode derivative of ``n_steps`` oracle steps (the oracle's source over dual
+        numbers): returns (new state, its tangent) for the state tangent ``tangents`` and the
+        rest-curvature and element-couple tangents (None: zero).  The state part equals
+        ``step`` bit for bit."""
+        lib = _load_ad()
+        st = [np.array(a, dtype=np.float64, order="C", copy=True) for a in state]
+        tg = [np.array(a, dtype=np.float64, order="C", copy=True) for a in tangents]
+        dk = None if d_rest_kappa is None else _f64(d_rest_kappa)
+        dc = None if d_elem_couple is None else _f64(d_elem_couple)
+        rc = lib.orcd_step_jvp(C.byref(self.params), t, dt, int(n_steps), *[_ptr(a) for a in st],
+                               *[_ptr(a) for a in tg], _ptr(dk), _ptr(dc))
+        if rc != 0:
+            raise RuntimeError("oracle (dual): " + lib.orcd_last_error().decode())
+        return st, tg
+
+    def step_count(self, state, dt, n_steps, t=0.0):
+        """``n_steps`` oracle steps counting the FP64 work: (new state, {class: count}) with the
+        classes of COUNT_NAMES."""
+        lib = _load_ad()
+        st = [np.array(a, dtype=np.float64, order="C", copy=True) for a in state]
+        counts = np.zeros(len(COUNT_NAMES), dtype=np.int64)
+        rc = lib.orcc_step_count(C.byref(self.params), t, dt, int(n_steps), *[_ptr(a) for a in st], _ptr(counts))
+        if rc != 0:
+            raise RuntimeError("oracle (counting): " + lib.orcc_last_error().decode())
+        return st, dict(zip(COUNT_NAMES, (int(c) for c in counts)))
 
     def energy(self, x, v, Q, w):
         x, v, Q, w = map(_f64, (x, v, Q, w))

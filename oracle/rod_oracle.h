@@ -31,7 +31,9 @@
 #define ROD_ORACLE_H
 #include <stdint.h>
 
-#ifdef __cplusplus
+/* ORC_CXX_LINKAGE: the C++ builds of this source over other number types (oracle_ad.cpp)
+ * give the functions C++ linkage inside a namespace of their own. */
+#if defined(__cplusplus) && !defined(ORC_CXX_LINKAGE)
 extern "C" {
 #endif
 
@@ -126,7 +128,7 @@ double orc_orthonormality_error(const orc_params* p, const double* Q);
 /* last error message */
 const char* orc_last_error(void);
 
-#ifdef __cplusplus
+#if defined(__cplusplus) && !defined(ORC_CXX_LINKAGE)
 }
 #endif
 #endif

@@ -9,7 +9,10 @@ curvature kappa0 and the element couples C are checked against central finite di
     against Richardson-extrapolated differences (h = 1e-3, 2e-3), since at h = 1e-6 the
     differences carry FP64 rounding noise of up to 3e-5 of a directional derivative.
 The adjoint of the initial state after one step is also checked entry by entry against
-finite differences of the oracle.
+finite differences of the oracle, and the gradients against the oracle's exact derivatives:
+its dual-number build (directional derivatives along random directions, on the small ensemble
+and on sampled rods of the full workload) and its reverse sweep built from exact one-step
+Jacobians (every gradient entry).
 """
 import numpy as np
 import pytest
@@ -44,6 +47,17 @@ def _loss_oracle(p, kappa0, couple, n_steps, dt):
     x = Oracle(q).step(*q.state(), dt=dt, n_steps=n_steps)[0]
     tips = x[:, p.node_offsets()[1:] - 1]
     return float(((tips - p.extra["targets"]) ** 2).sum())
+
+
+def _jvp_loss_oracle(p, dk, dc, n_steps, dt, targets=None):
+    """Exact directional derivative of the tip loss along (dk, dc) by the oracle's dual-number
+    build: one forward run of the tangents, no difference quotient."""
+    o = Oracle(p)
+    zero = [np.zeros_like(a) for a in p.state()]
+    st, tg = o.step_jvp(p.state(), zero, dt, n_steps, d_rest_kappa=dk, d_elem_couple=dc)
+    tips = p.node_offsets()[1:] - 1
+    tgt = p.extra["targets"] if targets is None else targets
+    return float((2.0 * (st[0][:, tips] - tgt) * tg[0][:, tips]).sum())
 
 
 def _grads_gpu(p, n_steps, dt, every):
@@ -84,6 +98,39 @@ def test_adjoint_matches_oracle_finite_differences_small():
         report.append((ad, fd[1e-6], fd[1e-5]))
         assert abs(ad - fd[1e-6]) <= 1e-6 * abs(fd[1e-6]), (ad, fd)
     _record("adjoint_small_oracle_fd", report)
+
+
+def test_adjoint_matches_the_oracle_dual_derivative_small():
+    """The same gradients against the exact directional derivatives of the oracle (its source
+    over dual numbers), where finite differences allowed only 1e-6."""
+    p = _small_problem()
+    n_steps, dt, every = 200, 1e-5, 50
+    _, gk, gc, _ = _grads_gpu(p, n_steps, dt, every)
+    for dk, dc in _directions(p, 8, seed=1):
+        ref = _jvp_loss_oracle(p, dk, dc, n_steps, dt)
+        ad = float((gk * dk).sum() + (gc * dc).sum())
+        assert abs(ad - ref) <= 1e-9 * abs(ref), (ad, ref)
+
+
+def test_adjoint_full_workload_matches_the_oracle_dual_derivative_on_sampled_rods():
+    """The full 1024 x 64 x 2000-step gradient, restricted to 16 sampled rods, against the exact
+    directional derivatives of the oracle run on those rods alone (the rods are clamped and
+    touch nothing, so the loss is a sum of independent per-rod terms)."""
+    p = rodgen.adjoint_batch()
+    n_steps, dt, every = 2000, 1e-5, 100
+    _, gk, gc, _ = _grads_gpu(p, n_steps, dt, every)
+    eo, R = p.elem_offsets(), p.n_rods
+    for r0 in (0, 8, 517, 1016):
+        r1 = r0 + 4
+        q = p.take_rods(r0, r1)
+        e0, e1 = int(eo[r0]), int(eo[r1])
+        v0, v1 = e0 - r0, e1 - r1
+        rng = np.random.default_rng(r0)
+        dk = rng.normal(size=(3, v1 - v0)) * np.abs(q.rest_kappa).max()
+        dc = rng.normal(size=(3, e1 - e0)) * np.abs(q.elem_couple).max()
+        ref = _jvp_loss_oracle(q, dk, dc, n_steps, dt, targets=p.extra["targets"][:, r0:r1])
+        ad = float((gk[:, v0:v1] * dk).sum() + (gc[:, e0:e1] * dc).sum())
+        assert abs(ad - ref) <= 1e-8 * abs(ref), (r0, ad, ref)
 
 
 def test_adjoint_with_magnetic_and_muscle_couples_matches_oracle_finite_differences():
@@ -300,8 +347,9 @@ def test_adjoint_matches_the_oracle_reverse_sweep():
     L = sum((o * torch.tensor(wt, device="cuda")).sum() for o, wt in zip(out, W))
     L.backward()
     gk, gc = k0.grad.cpu().numpy(), c0.grad.cpu().numpy()
-    assert np.abs(gk - gk_ref).max() <= 1e-6 * np.abs(gk_ref).max(), np.abs(gk - gk_ref).max() / np.abs(gk_ref).max()
-    assert np.abs(gc - gc_ref).max() <= 1e-6 * np.abs(gc_ref).max(), np.abs(gc - gc_ref).max() / np.abs(gc_ref).max()
+    # the sweep is exact (dual-number Jacobians), so every entry agrees to 1e-9 of the largest
+    assert np.abs(gk - gk_ref).max() <= 1e-9 * np.abs(gk_ref).max(), np.abs(gk - gk_ref).max() / np.abs(gk_ref).max()
+    assert np.abs(gc - gc_ref).max() <= 1e-9 * np.abs(gc_ref).max(), np.abs(gc - gc_ref).max() / np.abs(gc_ref).max()
     adj = [a.cpu().numpy() for a in s.adjoint_of_state()]
     free_nodes = np.ones(p.n_nodes, dtype=bool)
     free_elems = np.ones(p.n_elems, dtype=bool)
@@ -310,4 +358,4 @@ def test_adjoint_matches_the_oracle_reverse_sweep():
         free_elems[p.elem_offsets()[r]] = False
     for a_idx, mask in ((0, free_nodes), (1, free_nodes), (3, free_elems)):
         got, ref = adj[a_idx][:, mask], lam_ref[a_idx][:, mask]
-        assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max(), (a_idx, np.abs(got - ref).max() / np.abs(ref).max())
+        assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max(), (a_idx, np.abs(got - ref).max() / np.abs(ref).max())

@@ -23,8 +23,11 @@
  *   - The library owns all device memory it allocates; caller buffers are only read or
  *     written during the call (or, for on_device copies, on the system's stream).
  *   - Device errors (non-finite state, a segment longer than the contact grid allows,
- *     a contact table overflow, a bounded wait that ran out) latch into a device error word
- *     that rod_system_step() reports after it synchronises; rod_system_set_state() clears it.
+ *     a contact table overflow) latch into a device error word that rod_system_step() reports
+ *     after it synchronises; rod_system_set_state() clears it.  No kernel of the library spins
+ *     on a flag: the only device-wide wait is the grid barrier of the cooperative launch that
+ *     steps a rod longer than a thread block holds, and a cooperative launch either runs all
+ *     its blocks at once or fails to launch (ROD_ERR_CUDA), so that barrier cannot stall.
  */
 #ifndef ROD_H
 #define ROD_H
@@ -42,7 +45,7 @@ typedef enum {
   ROD_ERR_ARG = -1,       /* invalid argument or description */
   ROD_ERR_CUDA = -2,      /* a CUDA runtime call failed (message has the CUDA error) */
   ROD_ERR_NONFINITE = -3, /* the state became NaN/Inf */
-  ROD_ERR_TIMEOUT = -4,   /* a bounded device wait ran out */
+  ROD_ERR_TIMEOUT = -4,   /* reserved for a bounded device wait that ran out; no call returns it */
   ROD_ERR_OVERFLOW = -5,  /* contact grid or table capacity exceeded */
   ROD_ERR_STATE = -6      /* call not valid in the current state (e.g. no state set) */
 } rod_status;
@@ -138,7 +141,7 @@ rod_status rod_system_get_time(const rod_system* sys, double* t);
  * Eq. 1a and Eq. 1b at the half step (contact included when enabled), the dynamic update of v
  * and w, and the second half kinematic stage.  Enqueued on the system's stream;
  * the call synchronises that stream at the end and returns the device error word
- * (ROD_ERR_NONFINITE / ROD_ERR_OVERFLOW / ROD_ERR_TIMEOUT) if one was raised. */
+ * (ROD_ERR_NONFINITE / ROD_ERR_OVERFLOW) if one was raised. */
 rod_status rod_system_step(rod_system* sys, int64_t n_steps, double dt);
 
 /* Same as rod_system_step but returns as soon as the work is enqueued; call

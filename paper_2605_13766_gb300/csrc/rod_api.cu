@@ -469,7 +469,6 @@ rod_status read_error_word(rod_system* s) {
   if (e & ERR_NONFINITE) return fail(ROD_ERR_NONFINITE, "the state became non-finite (NaN/Inf)");
   if (e & ERR_GRID) return fail(ROD_ERR_OVERFLOW, "an element grew longer than the contact grid allows");
   if (e & ERR_OVERFLOW) return fail(ROD_ERR_OVERFLOW, "contact table capacity exceeded");
-  if (e & ERR_TIMEOUT) return fail(ROD_ERR_TIMEOUT, "a bounded device wait ran out");
   return ROD_OK;
 }
 

@@ -125,7 +125,7 @@ def build_mutant(mid: int) -> str:
     with open(src, "w") as f:
         f.write(text)
     tmp = lib + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-Wall",
+    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-Wall", "-Wno-unknown-pragmas",
                     "-I", _HERE, "-o", tmp, src, "-lm"], check=True)
     os.replace(tmp, lib)
     return lib

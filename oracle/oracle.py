@@ -29,11 +29,34 @@ def build_oracle(force: bool = False) -> str:
     if not force and os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(s) for s in srcs):
         return out
     tmp = out + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-Wall",
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-Wall", "-Wno-unknown-pragmas",
            "-o", tmp] + [os.path.join(_HERE, s) for s in _SOURCES] + ["-lm"]
     subprocess.run(cmd, check=True, cwd=_HERE)
     os.replace(tmp, out)
     return out
+
+
+def build_oracle_omp(force: bool = False) -> str:
+    """The same source compiled with -fopenmp: the per-rod loop of the right-hand side and the
+    per-item loops of the update run on all host cores (contact stays serial); every item is
+    computed by one thread with the same operations, so the results are those of the plain build
+    bit for bit.  Returns the .so path (use it through ``using_library``)."""
+    out = os.path.join(_HERE, "liboracle_omp.so")
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES] + [os.path.join(_HERE, "rod_oracle.h")]
+    if not force and os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(s) for s in srcs):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-Wall", "-Wno-unknown-pragmas",
+           "-o", tmp] + [os.path.join(_HERE, s) for s in _SOURCES] + ["-lm"]
+    subprocess.run(cmd, check=True, cwd=_HERE)
+    os.replace(tmp, out)
+    return out
+
+
+def omp_threads(path: str) -> int:
+    """Threads the OpenMP build at `path` runs its parallel loops with."""
+    lib = C.CDLL(path)
+    return int(lib.omp_get_max_threads())
 
 
 def build_oracle_ad(force: bool = False) -> str:
@@ -44,7 +67,7 @@ def build_oracle_ad(force: bool = False) -> str:
     if not force and os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(s) for s in srcs):
         return out
     tmp = out + f".tmp{os.getpid()}"
-    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-Wall",
+    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-Wall", "-Wno-unknown-pragmas",
            "-I", _HERE, "-o", tmp, os.path.join(_HERE, "oracle_ad.cpp"), "-lm"]
     subprocess.run(cmd, check=True, cwd=_HERE)
     os.replace(tmp, out)

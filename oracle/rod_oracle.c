@@ -628,6 +628,9 @@ int orc_rhs(const orc_params* p, double t, const double* x, const double* v, con
   if (!rc && p->contact && orc_contact_forces(p, x, fc, v)) rc = -1;
   if (rc) goto done;
 
+  /* rods are independent here (each writes only its own entries): the OpenMP build runs them
+   * on all host cores, the plain build ignores the pragma */
+#pragma omp parallel for schedule(dynamic, 8)
   for (int r = 0; r < p->n_rods; ++r) {
     rod_range g = G[r];
     rod_consts K = consts_of(p, r);
@@ -799,8 +802,10 @@ done:
 
 static void kinematic_half(const orc_params* p, double h, double* x, const double* v, double* Q, const double* w) {
   int64_t N = orc_num_nodes(p), E = orc_num_elems(p);
+#pragma omp parallel for
   for (int64_t j = 0; j < N; ++j)
     for (int c = 0; c < 3; ++c) x[c * N + j] += h * v[c * N + j];
+#pragma omp parallel for
   for (int64_t i = 0; i < E; ++i) {
     double M[9], R[9], Mn[9], phi[3];
     for (int c = 0; c < 3; ++c) phi[c] = -h * w[c * E + i];
@@ -859,7 +864,9 @@ int orc_step(const orc_params* p, double t, double dt, int64_t n_steps, double* 
       rc = -1;
       break;
     }
+#pragma omp parallel for
     for (int64_t q = 0; q < 3 * N; ++q) v[q] += dt * av[q];
+#pragma omp parallel for
     for (int64_t q = 0; q < 3 * E; ++q) w[q] += dt * aw[q];
     constrain_rates(p, G, v, w);
     kinematic_half(p, 0.5 * dt, x, v, Q, w);

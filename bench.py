@@ -85,14 +85,15 @@ def _measured_hbm_gbs():
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of one capture of the
-# current kernel; reset to None whenever the kernel changes.  pack_one_step: the third launch of
-# the bench's steps at its autotuned 256 x 256 shape.
+# current kernel; reset to None whenever the kernel changes.  pack_one_step: launches of the
+# packing's steps near step 1000 at the 256 x 256 shape (the force entries read only for
+# segments with skin-list candidates).
 # The carpet's state stays on chip between the steps of a launch: its traffic is one read of
 # the state and constants per launch (the written state is still in L2 when the launch ends).
 # CPU seconds the reference arm spends on its W + K samples (the whole run stays within minutes)
 REF_BUDGET_S = 90.0
 TRAFFIC_PER_LAUNCH = {
-    "pack_one_step": 356.06e6 + 152.13e6,
+    "pack_one_step": 286.81e6 + 142.23e6,
     "pack_steps": 39.28e6,
 }
 

@@ -484,7 +484,7 @@ bool finite_all(const double* p, size_t n) {
 constexpr int kGraphSteps = 32;
 // kernels per captured step: scan x3, fill, scatter, sort, records, gather, step, time; with the
 // skin list decide, force, step, time, and the rebuild kernels (bin, scan x3, fill, scatter,
-// sort, records, build, snapshot) in a conditional node that the decision opens only when a
+// sort, records, build, active set, snapshot) in a conditional node that the decision opens only when a
 // rebuild is due (those launches are counted on the device)
 constexpr int kKernelsPerGraphStep = 10;
 constexpr int kKernelsPerListGraphStep = 4;

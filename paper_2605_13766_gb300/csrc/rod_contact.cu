@@ -596,6 +596,7 @@ struct ListAppend {
 // Skin-list build (gated): the same scan with the bound raised by the skin.
 __global__ void __launch_bounds__(256) list_build_kernel(ContactArgs A) {
   if (gated_off(A.gate)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *A.n_active = 0;  // refilled by list_active_kernel
   if (*(volatile int*)A.err != 0) return;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < A.E; q += (int64_t)gridDim.x * blockDim.x) {
     ListAppend l{A.nbr, A.E, A.recB[q].x, 0};
@@ -604,16 +605,44 @@ __global__ void __launch_bounds__(256) list_build_kernel(ContactArgs A) {
   }
 }
 
-// Skin-list evaluation: one thread per segment.  The kernel is bound by the latency of its
-// gathers, so it asks for three resident blocks per SM (80 registers; the spills sit around the
-// out-of-line pair evaluation, which runs for the few survivors of the cull).
+// After a list build (gated): the segments with candidates, as a bit per segment index and as a
+// compact list (warp-aggregated slots; the list's order does not matter, each segment's force
+// is summed by one thread over its own candidates in list order).  Until the next build no
+// other segment can touch anything, so the force kernel walks only these and the step kernels
+// read only their forces.
+__global__ void __launch_bounds__(256) list_active_kernel(ContactArgs A) {
+  if (gated_off(A.gate)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < A.E; base += stride) {
+    const int64_t a = base + lane;
+    const bool act = a < A.E && A.nbr_count[a] > 0;
+    const unsigned mask = __ballot_sync(0xffffffffu, act);
+    int slot = 0;
+    if (lane == 0) {
+      A.active_mask[base >> 5] = mask;
+      if (mask) slot = atomicAdd(A.n_active, __popc(mask));
+    }
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (act) A.active[slot + __popc(mask & ((1u << lane) - 1u))] = static_cast<int>(a);
+  }
+}
+
+// Skin-list evaluation: the segments with candidates, one per thread of a grid that strides
+// over the active list.  The kernel is bound by the latency of its gathers, so it asks for
+// three resident blocks per SM (80 registers; the spills sit around the out-of-line pair
+// evaluation, which runs for the few survivors of the cull).  (One warp per segment, a lane per
+// candidate, measured 2.4x slower: the FP64 pair evaluations of one segment's few survivors then
+// occupy whole warps with most lanes masked.)
 __global__ void __launch_bounds__(256, 3) list_force_kernel(ContactArgs A) {
-  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (a >= A.E) return;
   if (*(volatile int*)A.err != 0) return;
-  ForceSum f(A, (int)a, A.seg_rod[a]);
-  listed_forces(A, a, f);
-  f.store(A.fseg, A.E);
+  const int n = *A.n_active;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int a = A.active[k];
+    ForceSum f(A, a, A.seg_rod[a]);
+    listed_forces(A, a, f);
+    f.store(A.fseg, A.E);
+  }
 }
 
 // Rebuild decision of this evaluation: requested, or a node has moved by skin / 2 (or the
@@ -700,7 +729,8 @@ cudaError_t dev_alloc(T** p, size_t count) {
 void contact_release(ContactState& cs) {
   void* ptrs[] = {cs.seg_rod, cs.seg_cell, cs.cell_count, cs.cell_start, cs.cell_fill,
                   cs.block_sums, cs.sorted, cs.prox, cs.fseg, cs.recA, cs.recB, cs.recC,
-                  cs.nbr, cs.nbr_count, cs.slot_of, cs.x_ref, cs.seg_prox, cs.ctl, cs.bounds};
+                  cs.nbr, cs.nbr_count, cs.slot_of, cs.x_ref, cs.seg_prox, cs.ctl, cs.bounds,
+                  cs.active_mask, cs.active};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cs.seg_rod = cs.seg_cell = cs.cell_count = cs.cell_start = cs.cell_fill = cs.block_sums = cs.sorted = nullptr;
@@ -712,6 +742,8 @@ void contact_release(ContactState& cs) {
   cs.nbr = cs.nbr_count = cs.slot_of = nullptr;
   cs.x_ref = nullptr;
   cs.seg_prox = nullptr;
+  cs.active_mask = nullptr;
+  cs.active = nullptr;
   cs.ctl = nullptr;
   cs.bounds = nullptr;
   cs.ctl_live = false;
@@ -754,7 +786,7 @@ std::vector<uint64_t> grid_signature(const ContactState& cs) {
   v.push_back(static_cast<uint64_t>(cs.sm_count));
   const void* bufs[] = {cs.seg_rod, cs.seg_cell, cs.cell_count, cs.cell_start, cs.cell_fill, cs.block_sums,
                         cs.sorted, cs.prox, cs.recA, cs.recB, cs.recC, cs.fseg, cs.nbr, cs.nbr_count,
-                        cs.slot_of, cs.x_ref, cs.seg_prox, cs.ctl};
+                        cs.slot_of, cs.x_ref, cs.seg_prox, cs.ctl, cs.active_mask, cs.active};
   for (const void* q : bufs) p(q);
   return v;
 }
@@ -856,7 +888,8 @@ rod_status contact_prepare(ContactState& cs, const std::vector<RodConst>& rods_h
   if (skin > 0.0 && cs.N != N) {
     if ((e = dev_alloc(&cs.nbr, int64_t(kNbrCap) * E)) || (e = dev_alloc(&cs.nbr_count, E)) ||
         (e = dev_alloc(&cs.slot_of, E)) || (e = dev_alloc(&cs.x_ref, 3 * N)) || (e = dev_alloc(&cs.seg_prox, 2 * E)) ||
-        (e = dev_alloc(&cs.ctl, 1)))
+        (e = dev_alloc(&cs.ctl, 1)) || (e = dev_alloc(&cs.active_mask, (E + 31) / 32)) ||
+        (e = dev_alloc(&cs.active, E)))
       return cfail(ROD_ERR_CUDA, "contact: skin list allocation", e);
     cs.N = N;
   }
@@ -934,6 +967,9 @@ ContactArgs make_args(const ContactState& cs, const double* x, const double* v, 
   A.nbr_count = cs.nbr_count;
   A.slot_of = cs.slot_of;
   A.seg_prox = cs.seg_prox;
+  A.active_mask = cs.active_mask;
+  A.active = cs.active;
+  A.n_active = cs.ctl ? &cs.ctl->n_active : nullptr;
   A.skin = (float)cs.skin;
   A.rods = rods;
   A.fseg = cs.fseg;
@@ -1050,6 +1086,9 @@ cudaError_t contact_list_rebuild(ContactState& cs, const double* x, const RodCon
   list_build_kernel<<<gb, 256, 0, st>>>(A);
   hook.after(K_CONTACT_LIST_BUILD, st);
   hook.before(K_CONTACT_LIST_BUILD, st);
+  list_active_kernel<<<gb, 256, 0, st>>>(A);
+  hook.after(K_CONTACT_LIST_BUILD, st);
+  hook.before(K_CONTACT_LIST_BUILD, st);
   list_snapshot_kernel<<<gb, 256, 0, st>>>(x, 3 * N, cs.x_ref, cs.ctl, gate);
   hook.after(K_CONTACT_LIST_BUILD, st);
   return cudaGetLastError();
@@ -1059,7 +1098,7 @@ cudaError_t contact_list_force(ContactState& cs, const double* x, const double* 
                                int64_t E, int* err, cudaStream_t st, const LaunchHook& hook) {
   const ContactArgs A = make_args(cs, x, v, rods, N, E, err, &cs.ctl->gate);
   hook.before(K_CONTACT_LIST_FORCE, st);
-  list_force_kernel<<<(E + 255) / 256, 256, 0, st>>>(A);
+  list_force_kernel<<<3 * std::max(cs.sm_count, 1), 256, 0, st>>>(A);
   hook.after(K_CONTACT_LIST_FORCE, st);
   return cudaGetLastError();
 }
@@ -1077,6 +1116,7 @@ void contact_list_params(const ContactState& cs, StepParams& P) {
   P.disp_ref = cs.x_ref;
   P.disp_word = &cs.ctl->disp2;
   P.seg_prox = cs.seg_prox;
+  P.fmask = cs.active_mask;
 }
 
 cudaError_t contact_list_invalidate(const ContactState& cs, cudaStream_t st) {

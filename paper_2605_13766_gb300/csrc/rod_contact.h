@@ -20,10 +20,12 @@ struct ListCtl {
   int force;
   int builds;  // list builds since the grid was set up
   int opened;  // rebuilds that ran inside a replayed graph's conditional node (launch accounting)
+  int n_active;  // segments with candidates at the last build (entries of ContactState::active)
 };
 
-// Kernels of one skin-list rebuild (bin, scan x3, fill, scatter, sort, records, build, snapshot).
-constexpr int kListRebuildKernels = 10;
+// Kernels of one skin-list rebuild (bin, scan x3, fill, scatter, sort, records, build, active
+// set, snapshot).
+constexpr int kListRebuildKernels = 11;
 
 // Capacity of one segment's candidate list; a segment with more candidates scans its
 // neighbourhood of the last build instead.  Thick rods cut into short segments give a touching
@@ -69,6 +71,10 @@ struct ContactState {
   int* slot_of = nullptr;     // [E] slot of each segment in the last build's cell order
   float* x_ref = nullptr;     // [3N] positions of the last build, rounded to FP32
   float4* seg_prox = nullptr; // [2E] FP32 proxies of the current positions, written by the step kernels
+  // segments with candidates at the last build (only they can have a contact force until the
+  // next one): a bit per segment index and the compact list the force kernel walks
+  unsigned* active_mask = nullptr;  // [(E + 31) / 32]
+  int* active = nullptr;            // [E], ctl->n_active entries in use
   ListCtl* ctl = nullptr;
   unsigned long long* bounds = nullptr;  // [8] grid set-up: bounding box, longest segment (order keys)
   bool ctl_live = false;       // ctl holds counts of the current grid

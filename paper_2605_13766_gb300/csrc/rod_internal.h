@@ -71,6 +71,9 @@ struct ContactArgs {
   int* nbr_count;
   const int* slot_of;
   const float4* seg_prox;
+  unsigned* active_mask;
+  int* active;
+  int* n_active;
   float skin;
   const RodConst* rods;
   double* fseg;
@@ -118,6 +121,9 @@ struct StepParams {
   double wall_k, wall_c, wall_mu, wall_vslip;
   // contact: per-segment node forces [6E] (force on node a = first node, node b), or null
   const double* fseg;
+  // skin-list contact: bit e set when segment e has candidates (its fseg entries are written);
+  // null: every segment's entries are written
+  const unsigned* fmask;
   int* err;                   // device error word
   // simulated time of the state at launch (device scalar; replayed graphs read it), or null
   const double* t_dev;

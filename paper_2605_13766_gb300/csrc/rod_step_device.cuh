@@ -473,14 +473,17 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
     const double dl = __ldg(&rc->damp_lin);
     double F[3];
     if (P.fseg) {
-      // contact: node a of segment iR and node b of segment iR-1, folded into the difference
+      // contact: node a of segment iR and node b of segment iR-1, folded into the difference;
+      // with the skin list only segments with candidates have entries (bit set in fmask)
       const int ge = iR + m.dE[r];
+      const bool fR = hasR && (!P.fmask || ((__ldg(P.fmask + (ge >> 5)) >> (ge & 31)) & 1u));
+      const bool fL = hasL && (!P.fmask || ((__ldg(P.fmask + ((ge - 1) >> 5)) >> ((ge - 1) & 31)) & 1u));
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const double Nr = hasR ? m.NF[c * m.CE + iR] : 0.0;
         const double Nl = hasL ? m.NF[c * m.CE + iR - 1] : 0.0;
-        const double fa = hasR ? __ldg(P.fseg + c * P.E + ge) : 0.0;
-        const double fb = hasL ? __ldg(P.fseg + (3 + c) * P.E + ge - 1) : 0.0;
+        const double fa = fR ? __ldg(P.fseg + c * P.E + ge) : 0.0;
+        const double fb = fL ? __ldg(P.fseg + (3 + c) * P.E + ge - 1) : 0.0;
         F[c] = (Nr + fa) - (Nl - fb);
       }
     } else {

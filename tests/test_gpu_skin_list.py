@@ -214,8 +214,8 @@ def test_skin_must_be_finite_and_non_negative():
 def test_replayed_graph_launches_rebuild_kernels_only_when_due():
     """Inside a replayed graph the rebuild kernels sit in a conditional node that the device-side
     decision opens only when a rebuild is due: per step the decision, the forces, the step and
-    the time advance, plus the ten rebuild kernels per rebuild.  Eager steps launch all thirteen
-    of theirs (decision, ten rebuild kernels that return at once when no rebuild is due, forces,
+    the time advance, plus the eleven rebuild kernels per rebuild.  Eager steps launch all
+    fourteen of theirs (decision, eleven rebuild kernels that return at once when no rebuild is due, forces,
     step)."""
     p = _touching(60, 0.1, 14)
     counts = {}
@@ -228,10 +228,10 @@ def test_replayed_graph_launches_rebuild_kernels_only_when_due():
         s.close()
     (builds_g, n_g), (builds_e, n_e) = counts[True], counts[False]
     assert builds_g == builds_e >= 1
-    assert n_e == 1 + 65 * 13
+    assert n_e == 1 + 65 * 14
     # kinematic half step, set_time, 64 replayed steps, one eager step with all its kernels
-    assert n_g <= 1 + 1 + 64 * 4 + 10 * builds_g + 13
-    assert n_g >= 1 + 1 + 64 * 4 + 13
+    assert n_g <= 1 + 1 + 64 * 4 + 11 * builds_g + 14
+    assert n_g >= 1 + 1 + 64 * 4 + 14
 
 
 
@@ -254,9 +254,9 @@ def test_any_step_count_replays_graphs(K):
         assert np.array_equal(a, b)
     (builds_g, n_g), (builds_e, n_e) = counts[True], counts[False]
     assert builds_g == builds_e
-    assert n_e == 1 + K * 13
+    assert n_e == 1 + K * 14
     # kinematic half step, set_time, K - 1 replayed steps of 4 kernels, the last step eager
-    assert 1 + 1 + (K - 1) * 4 + 13 <= n_g <= 1 + 1 + (K - 1) * 4 + 10 * builds_g + 13
+    assert 1 + 1 + (K - 1) * 4 + 14 <= n_g <= 1 + 1 + (K - 1) * 4 + 11 * builds_g + 14
 
 
 def test_replayed_graph_follows_parameter_changes_between_calls():

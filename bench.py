@@ -376,8 +376,16 @@ def _surrogate_speedup(train_steps: int):
         ro.close()
         modes[mode] = {"speedup": t_plain / t_sur, "surrogate_elem_steps_per_s": el / t_sur,
                        "final_tip_err": final, "rollout": stats}
+    # out of the training window: t in [0.5, 0.6] s of the same carpet (training saw the first
+    # 0.1 s of 32 x 32 carpets from rest), and a carpet whose amplitude and period both lie
+    # outside the training ranges (0.2..0.8 EI/L, 0.5..2 s)
+    later = _pre_rolled(p, dt, 50_000)
+    beyond = rodgen.cilia_carpet(side=64, n=50, amp_factor=1.0, period=0.3)
+    out = {"t_0.5_to_0.6_s": _rollout_case(sur, later, dt, W, n_calls, t0=0.5),
+           "amp_1.0_EI_over_L_period_0.3_s": _rollout_case(sur, beyond, dt, W, n_calls)}
     head = modes["local"]
     return {"workload": "cilia carpet 64x64 rods x 50 elements, 10^4 steps of 1e-5 s (200 calls of 50 steps)",
+            "out_of_window": out,
             "speedup": head["speedup"], "check": "local (pipelined per-segment checks); global below",
             "plain_elem_steps_per_s": el / t_plain, "surrogate_elem_steps_per_s": head["surrogate_elem_steps_per_s"],
             "max_tip_err_network_every_20_calls": worst, "final_tip_err_checked_rollout": head["final_tip_err"],
@@ -385,6 +393,54 @@ def _surrogate_speedup(train_steps: int):
             "check_bound_sampled": S.DEFAULT_CHECK_BOUND, "modes": modes,
             "timing": "plain: CUDA events on its stream; rollout: host wall clock around the whole checked rollout",
             "training": info, "dtype": "bf16 tensor cores (mma.sync), FP32 accumulation, FP64 state"}
+
+
+def _pre_rolled(p, dt, n_steps):
+    """The problem with its state advanced n_steps plain GPU steps from rest."""
+    from paper_2605_13766_gb300 import RodSystem
+    s = RodSystem(p)
+    s.set_state(*p.state())
+    s.step(n_steps, dt)
+    x, v, Q, w = s.get_state()
+    s.close()
+    return p.replace(x=x, v=v, Q=Q, w=w)
+
+
+def _rollout_case(sur, p, dt, W, n_calls, t0=0.0):
+    """Checked rollout (local checks) of n_calls windows from the problem's state at time t0
+    against the plain GPU step over the same interval: speed-up, tip errors, fallbacks."""
+    import time
+
+    import torch
+    from paper_2605_13766_gb300 import RodSystem
+    from paper_2605_13766_gb300 import surrogate as S
+    s = RodSystem(p)
+    s.set_state(*p.state())
+    s.time = t0
+    s.step(n_calls * W, dt)
+    ref = s.get_state()[0]
+    s.set_state(*p.state())
+    s.time = t0
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s.torch_stream)
+    s.step_async(n_calls * W, dt)
+    e1.record(s.torch_stream)
+    s.sync()
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) / 1e3
+    s.close()
+    ro = S.CheckedRollout(sur, p, seed=1, mode="local", t0=t0)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    stats = ro.run(n_calls, check_every=10, bound=S.DEFAULT_CHECK_BOUND)
+    torch.cuda.synchronize()
+    t_sur = time.perf_counter() - t
+    err = S.tip_error(p, ro.system.get_state()[0], ref)
+    ro.close()
+    return {"t0": t0, "speedup": t_plain / t_sur, "final_tip_err": float(err.max()),
+            "fallback_calls": int(stats["fallback_calls"]), "surrogate_calls": int(stats["surrogate_calls"]),
+            "rollout": stats}
 
 
 def main():

@@ -392,6 +392,20 @@ rod_status rod_surrogate_train_step(rod_surrogate* sur, const double* x0, const 
                                     const double* w1, const double* act, int32_t nwin, float lr, float* loss_out,
                                     void* cuda_stream);
 rod_status rod_surrogate_get_grad(rod_surrogate* sur, float* grad, int on_device);
+/* Intermediate arrays of the last rod_surrogate_train_step, copied to the host as FP32 (BF16
+ * arrays widened exactly), so that each layer of the kernels can be checked on its own; a test
+ * hook with no counterpart in the paper.  Rows are positions + 2 (rows 0, 1 and 53..63 are the
+ * convolutions' zero padding), windows outermost, channels innermost.  which:
+ *   0       network input (features)       [nwin][64][32]  BF16
+ *   1..3    hidden activations of layer 1..3 [nwin][64][64] BF16
+ *   4..6    pre-activations of layer 1..3   [nwin][64][64]  FP32
+ *   7       network output                  [nwin][51][16]  FP32
+ *   8       training targets                [nwin][51][16]  FP32
+ *   9       loss gradient of the output     [nwin][64][16]  BF16
+ *   10..12  back-propagated gradients at the outputs of layers 3, 2, 1 [nwin][64][64] BF16
+ * cap: room in out (floats); *n_out receives the element count (cap = 0: count only).
+ * ROD_ERR_STATE before the first training step.  Synchronises the device. */
+rod_status rod_surrogate_debug_buffer(rod_surrogate* sur, int32_t which, float* out, int64_t cap, int64_t* n_out);
 rod_status rod_surrogate_forward(rod_surrogate* sur, const double* x, const double* v, const double* Q,
                                  const double* w, const double* act, int32_t nwin, float* out, void* cuda_stream);
 rod_status rod_surrogate_raw_features(rod_surrogate* sur, const double* x, const double* v, const double* Q,

@@ -127,6 +127,7 @@ _SIGNATURES = {
     "rod_surrogate_train_step": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int32, C.c_float, _P, _P], C.c_int),
     "rod_surrogate_get_grad": ([_P, _P, C.c_int], C.c_int),
     "rod_surrogate_forward": ([_P, _P, _P, _P, _P, _P, C.c_int32, _P, _P], C.c_int),
+    "rod_surrogate_debug_buffer": ([_P, C.c_int32, _P, C.c_int64, _P], C.c_int),
     "rod_surrogate_set_prior": ([_P, C.c_int32], C.c_int),
     "rod_surrogate_raw_features": ([_P, _P, _P, _P, _P, _P, C.c_int32, _P, _P, _P], C.c_int),
     "rod_surrogate_raw_targets": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int32, _P, _P], C.c_int),
@@ -543,6 +544,20 @@ class Surrogate:
         p = np.empty(self.n_params, dtype=np.float32)
         _check(self.lib.rod_surrogate_get_params(self.handle, p.ctypes.data, 0))
         return p
+
+    # shapes of rod_surrogate_debug_buffer's arrays per window: (rows, channels)
+    _DEBUG_SHAPES = {0: (64, 32), 1: (64, 64), 2: (64, 64), 3: (64, 64), 4: (64, 64), 5: (64, 64), 6: (64, 64),
+                     7: (51, 16), 8: (51, 16), 9: (64, 16), 10: (64, 64), 11: (64, 64), 12: (64, 64)}
+
+    def debug_buffer(self, which: int) -> np.ndarray:
+        """Intermediate array `which` of the last training step (see include/rod.h), as
+        float32 [windows, rows, channels]."""
+        n = C.c_int64(0)
+        _check(self.lib.rod_surrogate_debug_buffer(self.handle, int(which), None, 0, C.byref(n)))
+        out = np.empty(int(n.value), dtype=np.float32)
+        _check(self.lib.rod_surrogate_debug_buffer(self.handle, int(which), out.ctypes.data, out.size, C.byref(n)))
+        rows, ch = self._DEBUG_SHAPES[int(which)]
+        return out.reshape(-1, rows, ch)
 
     def get_grad(self) -> np.ndarray:
         g = np.empty(self.n_params, dtype=np.float32)

@@ -860,6 +860,7 @@ struct rod_surrogate {
   int64_t adam_t = 0;
   // per-batch buffers (grown on demand)
   int cap = 0;
+  int last_nwin = 0;  // windows of the last training step (rod_surrogate_debug_buffer)
   __nv_bfloat16 *a0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr;  // input, hidden 1..3
   float *p1 = nullptr, *p2 = nullptr, *p3 = nullptr;                        // pre-activations
   float *outf = nullptr, *tgt = nullptr, *loss = nullptr;
@@ -1213,6 +1214,7 @@ rod_status rod_surrogate_train_step(rod_surrogate* s, const double* x0, const do
   targets_kernel<<<(static_cast<int64_t>(nwin) * kPos * kCO + 255) / 256, 256, 0, st>>>(A, B, nwin, s->sc, s->tgt);
   if ((e = forward(s, nwin, true, st)) || (e = backward(s, nwin, st)))
     return internal_fail(ROD_ERR_CUDA, "rod_surrogate_train_step", cudaGetErrorString(e));
+  s->last_nwin = nwin;
   if (lr > 0.f) {
     s->adam_t += 1;
     const float b1 = 0.9f, b2 = 0.999f;
@@ -1234,6 +1236,48 @@ rod_status rod_surrogate_get_grad(rod_surrogate* s, float* grad, int on_device) 
   if (!s || !grad) return internal_fail(ROD_ERR_ARG, "rod_surrogate_get_grad: null argument", "");
   cudaError_t e = cudaMemcpy(grad, s->grad, kNumParams * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return internal_fail(ROD_ERR_CUDA, "rod_surrogate_get_grad", cudaGetErrorString(e));
+  return ROD_OK;
+}
+
+rod_status rod_surrogate_debug_buffer(rod_surrogate* s, int32_t which, float* out, int64_t cap, int64_t* n_out) {
+  if (!s || !n_out || cap < 0 || (cap > 0 && !out))
+    return internal_fail(ROD_ERR_ARG, "rod_surrogate_debug_buffer: bad argument", "");
+  if (s->last_nwin < 1) return internal_fail(ROD_ERR_STATE, "rod_surrogate_debug_buffer: no training step yet", "");
+  const int64_t nw = s->last_nwin, rows = nw * kRows;
+  const void* src = nullptr;
+  int64_t n = 0;
+  bool bf = false;
+  switch (which) {
+    case 0: src = s->a0, n = rows * kC0, bf = true; break;
+    case 1: src = s->a1, n = rows * kC, bf = true; break;
+    case 2: src = s->a2, n = rows * kC, bf = true; break;
+    case 3: src = s->a3, n = rows * kC, bf = true; break;
+    case 4: src = s->p1, n = rows * kC; break;
+    case 5: src = s->p2, n = rows * kC; break;
+    case 6: src = s->p3, n = rows * kC; break;
+    case 7: src = s->outf, n = nw * kPos * kCO; break;
+    case 8: src = s->tgt, n = nw * kPos * kCO; break;
+    case 9: src = s->g4, n = rows * kCO, bf = true; break;
+    case 10: src = s->g3, n = rows * kC, bf = true; break;
+    case 11: src = s->g2, n = rows * kC, bf = true; break;
+    case 12: src = s->g1, n = rows * kC, bf = true; break;
+    default: return internal_fail(ROD_ERR_ARG, "rod_surrogate_debug_buffer: which must be 0..12", "");
+  }
+  *n_out = n;
+  if (cap == 0) return ROD_OK;
+  if (cap < n) return internal_fail(ROD_ERR_ARG, "rod_surrogate_debug_buffer: buffer too small", "");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (!e && !bf) e = cudaMemcpy(out, src, n * sizeof(float), cudaMemcpyDeviceToHost);
+  if (!e && bf) {
+    // BF16 bits widen to FP32 exactly: the 16 bits become the high half
+    std::vector<uint16_t> h(static_cast<size_t>(n));
+    e = cudaMemcpy(h.data(), src, n * sizeof(uint16_t), cudaMemcpyDeviceToHost);
+    for (int64_t i = 0; !e && i < n; ++i) {
+      const uint32_t u = static_cast<uint32_t>(h[i]) << 16;
+      std::memcpy(out + i, &u, sizeof u);
+    }
+  }
+  if (e) return internal_fail(ROD_ERR_CUDA, "rod_surrogate_debug_buffer", cudaGetErrorString(e));
   return ROD_OK;
 }
 

@@ -54,6 +54,7 @@ class Windows:
     acts: list            # [(3, R)] float64 CUDA tensors, couple samples of window k
     window: int
     dt: float
+    t0: float = 0.0       # simulated time of states[0]
 
     @property
     def n_windows(self) -> int:
@@ -93,7 +94,7 @@ def generate(problem, n_windows: int, window: int = 50, dt: Optional[float] = No
                 s.step(window, dt)
         torch.cuda.synchronize()
         s.close()
-        return Windows(problem, states, acts, window, dt)
+        return Windows(problem, states, acts, window, dt, t0)
     if window % sub:
         raise ValueError("window must be a multiple of sub")
     h = window // sub
@@ -137,7 +138,7 @@ def generate(problem, n_windows: int, window: int = 50, dt: Optional[float] = No
         finish(k)
     torch.cuda.synchronize()
     s.close()
-    return Windows(problem, states, acts, window, dt)
+    return Windows(problem, states, acts, window, dt, t0)
 
 
 def fit_scales(sur: Surrogate, data: Sequence[Windows], max_windows: int = 64, output_floor: float = 1e-3):
@@ -213,7 +214,8 @@ def initial_params(seed: int = 0, last_gain: float = 0.1) -> np.ndarray:
 def train(sur: Surrogate, data: Sequence[Windows], steps: int, lr: float = 1e-3, lr_end: float = 1e-5,
           batch_rods: Optional[int] = None, seed: int = 0, log_every: int = 0, noise: float = 0.0,
           pushforward: float = 0.0, pushforward_start: float = 0.5) -> List[float]:
-    """Adam on random windows: each step takes window k of trajectory d (random) for
+    """Adam on random windows: each step takes window k of trajectory d (random, every window of
+    every trajectory equally likely) for
     ``batch_rods`` consecutive rods (all rods by default).  Cosine decay from lr to lr_end.
 
     noise > 0: the window start is perturbed by Gaussian noise of ``noise`` times the largest
@@ -240,8 +242,10 @@ def train(sur: Surrogate, data: Sequence[Windows], steps: int, lr: float = 1e-3,
         spread = torch.tensor(grp, device="cuda")
     scratch = {}
     losses = []
+    weights = np.array([d.n_windows for d in data], dtype=np.float64)
+    weights /= weights.sum()
     for it in range(steps):
-        di = int(rng.integers(len(data)))
+        di = int(rng.choice(len(data), p=weights))   # every window equally likely
         d = data[di]
         use_pf = pushforward > 0 and it >= pushforward_start * steps and rng.random() < pushforward
         k = int(rng.integers(1 if use_pf else 0, d.n_windows))
@@ -252,7 +256,7 @@ def train(sur: Surrogate, data: Sequence[Windows], steps: int, lr: float = 1e-3,
                 scratch[di].set_state(*[t.cpu().numpy() for t in d.states[0]])
             sysk = scratch[di]
             sysk.set_state(*d.states[k - 1])
-            sysk.time = (k - 1) * d.window * d.dt
+            sysk.time = d.t0 + (k - 1) * d.window * d.dt
             sur.apply(sysk, 1)
             a = [t.clone() for t in sysk.get_state(device=True)]
             torch.cuda.synchronize()
@@ -310,16 +314,23 @@ def _perturb(state, d, spread, noise, gen):
 
 
 def train_default(steps: int = 15000, side: int = 32, n_windows: int = 200, seed: int = 101,
-                  window: int = 50, dt: float = 1e-5, log_every: int = 0):
-    """The default surrogate: trained on side^2 x n_windows windows (2 x 10^5 by default) of a
-    carpet of 50-element rods from rest with amplitudes 0.2..0.8 EI/L, periods 0.5..2 s and
-    random phases; group-shared output scales, noise-injected Adam with cosine decay 2e-3 ->
-    2e-5.  Returns the surrogate and a dict of training facts."""
+                  window: int = 50, dt: float = 1e-5, log_every: int = 0,
+                  later_starts=(0.2, 0.4, 0.7, 0.9), later_windows: int = 50):
+    """The default surrogate: trained on windows of a carpet of 50-element rods with amplitudes
+    0.2..0.8 EI/L, periods 0.5..2 s and random phases -- side^2 x n_windows windows from rest
+    (2 x 10^5 by default) and side^2 x later_windows windows from each of the times
+    ``later_starts`` (s) of the same run, so that the network sees the beating carpet after the
+    start-up as well (none of them covers 0.5..0.6 s); group-shared output scales,
+    noise-injected Adam with cosine decay 2e-3 -> 2e-5.  Returns the surrogate and a dict of
+    training facts."""
     import time
     import rodgen
     t = time.time()
     p = rodgen.cilia_carpet(side=side, n=ELEMENTS, amp_range=(0.2, 0.8), period_range=(0.5, 2.0), seed=seed)
     data = [generate(p, n_windows=n_windows, window=window, dt=dt)]
+    for ts in later_starts:
+        data.append(generate(p, n_windows=later_windows, window=window, dt=dt,
+                             skip_windows=int(round(ts / (window * dt)))))
     t_data = time.time() - t
     sur = Surrogate(window, dt)
     fit_scales(sur, data, output_floor=1.0)
@@ -375,10 +386,11 @@ class CheckedRollout:
     plain step from the surrogate's own state of the sampled rods at the segment's start, so
     the checks of different segments run while the network goes on (the check measures the
     error the surrogate adds in one segment; ``stats["sum_err"]`` bounds the accumulated
-    error if segment errors add up without growing)."""
+    error if segment errors add up without growing).  ``t0``: the simulated time of the
+    problem's state (the actuation phase)."""
 
     def __init__(self, sur: Surrogate, problem, n_sample: int = DEFAULT_SAMPLE, seed: int = 0,
-                 shadow_shape=SHADOW_SHAPE, mode: str = "global", n_shadows: int = 2):
+                 shadow_shape=SHADOW_SHAPE, mode: str = "global", n_shadows: int = 2, t0: float = 0.0):
         if mode not in ("global", "local"):
             raise ValueError("mode is 'global' or 'local'")
         R = len(problem.n_elem)
@@ -388,6 +400,7 @@ class CheckedRollout:
         self.mode = mode
         self.system = RodSystem(problem)
         self.system.set_state(*problem.state())
+        self.system.time = t0
         sub = subset_problem(problem, self.sample)
         self.shadows = []
         for _ in range(1 if mode == "global" else n_shadows):
@@ -396,6 +409,7 @@ class CheckedRollout:
                 # few rods per block: the shadow's step is latency-bound, not throughput-bound
                 sh.set_launch(*shadow_shape)
             sh.set_state(*sub.state())
+            sh.time = t0
             self.shadows.append(sh)
         self.shadow = self.shadows[0]
 

@@ -4,9 +4,11 @@ network (oracle side), then training, the checked rollout and the fallback.
 Parity cases use windows of the CPU oracle (3 x 3 carpet of 50-element rods, bent by 400 steps
 of actuation, then one window of 50 steps).  Tolerances:
   * unscaled features and targets (FP64 on both sides): 1e-12 of each channel's magnitude;
-  * network output, loss and gradient: the reference rounds to BF16 at every point the kernels
-    store BF16, so what remains is FP32 versus FP64 accumulation and the rare BF16 rounding it
-    flips: 2e-3 (output, norm-wise), 2e-3 (loss), 2e-2 (gradient per layer, norm-wise);
+  * network output, loss and gradient of the whole network against the reference, which rounds
+    to BF16 at every point the kernels store BF16 (an end-to-end cross-check; the element-wise
+    parity of every layer is in test_gpu_surrogate_layers.py): what remains is FP32 versus FP64
+    accumulation and the rare BF16 rounding it flips, which then propagates through the later
+    layers: 2e-3 (output, norm-wise), 2e-3 (loss), 2e-2 (gradient per layer, norm-wise);
   * state update (FP64 on both sides, same network outputs): 1e-12.
 """
 import json
@@ -283,10 +285,65 @@ def test_trained_surrogate_gain_over_plain_step(trained):
         rec[mode] = dict(rollout_s=t_sur, speedup=t_plain / t_sur, rollout_elem_steps_per_s=el_steps / t_sur,
                          final_tip_err=float(err.max()), stats=stats)
         assert err.max() <= 1e-3, rec
-        assert t_sur < t_plain, rec                       # what the trained network gains
+        # what the trained network gains: at least 10x the plain step with the pipelined local
+        # checks; the global check follows sampled rods with sequential plain steps on a shadow
+        # system, which bounds it near 9x, so it must only beat the plain step
+        assert t_plain / t_sur >= (10.0 if mode == "local" else 1.0), rec
+    assert worst <= 1e-3, rec                             # the bound, every 20th call, all 4096 rods
+    # out of the training window: t in [0.5, 0.6] s of the same carpet (no training window
+    # covers it), and a carpet whose amplitude and period lie outside the training ranges,
+    # where the checks must take over (fallbacks) and keep the bound
+    later = _advanced(p, dt, 50_000)
+    rec["t_0.5_to_0.6_s"] = _checked_case(sur, later, dt, W, n_calls, t0=0.5)
+    assert rec["t_0.5_to_0.6_s"]["final_tip_err"] <= 1e-3, rec
+    assert rec["t_0.5_to_0.6_s"]["speedup"] >= 10.0, rec
+    beyond = rodgen.cilia_carpet(side=64, n=50, amp_factor=1.0, period=0.3)
+    rec["amp_1.0_period_0.3"] = _checked_case(sur, beyond, dt, W, n_calls)
+    assert rec["amp_1.0_period_0.3"]["final_tip_err"] <= 1e-3, rec
+    assert rec["amp_1.0_period_0.3"]["fallback_calls"] > 0, rec
     _record("surrogate_gain", rec)
     print(json.dumps(rec, indent=1))
-    assert worst <= 1e-3, rec                             # the bound, every 20th call, all 4096 rods
+
+
+def _advanced(p, dt, n_steps):
+    from paper_2605_13766_gb300 import RodSystem
+    s = RodSystem(p)
+    s.set_state(*p.state())
+    s.step(n_steps, dt)
+    x, v, Q, w = s.get_state()
+    s.close()
+    return p.replace(x=x, v=v, Q=Q, w=w)
+
+
+def _checked_case(sur, p, dt, W, n_calls, t0=0.0):
+    """Checked rollout with local checks from the problem's state at time t0 against the plain
+    GPU step over the same interval (wall clock around each, after a synchronisation)."""
+    import torch
+    from paper_2605_13766_gb300 import RodSystem
+    from paper_2605_13766_gb300 import surrogate as S
+    s = RodSystem(p)
+    s.set_state(*p.state())
+    s.time = t0
+    s.step(W, dt)                                           # warm-up
+    s.set_state(*p.state())
+    s.time = t0
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    s.step(n_calls * W, dt)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t
+    ref = s.get_state()[0]
+    s.close()
+    ro = S.CheckedRollout(sur, p, seed=1, mode="local", t0=t0)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    stats = ro.run(n_calls, check_every=10, bound=S.DEFAULT_CHECK_BOUND)
+    torch.cuda.synchronize()
+    t_sur = time.perf_counter() - t
+    err = S.tip_error(p, ro.system.get_state()[0], ref)
+    ro.close()
+    return {"speedup": t_plain / t_sur, "final_tip_err": float(err.max()),
+            "fallback_calls": int(stats["fallback_calls"]), "surrogate_calls": int(stats["surrogate_calls"])}
 
 
 @pytest.mark.parametrize("mode", ["global", "local"])

@@ -1,0 +1,181 @@
+"""Element-wise parity of the surrogate's kernels, layer by layer.
+
+After one training step on windows of the CPU oracle, the library hands back every intermediate
+array of that step (rod_surrogate_debug_buffer): the BF16 activations, the FP32
+pre-activations, the output, the loss gradient and the back-propagated BF16 gradients.  Each
+layer is then checked on its own, against an FP64 evaluation of the same layer from the GPU's
+own inputs to that layer, so no rounding decision taken earlier can blur the comparison:
+
+  * pre-activations and outputs: |z_gpu - z| <= (K + 2) 2^-22 (sum |W a| + |b|) for every entry,
+    K = 5 C_in products of BF16 operands (exact in FP32) accumulated in FP32 by the tensor cores
+    (2^-22: two units of FP32 rounding per addition, for accumulators that truncate);
+  * activations and gradients stored in BF16: the stored value lies in the BF16 rounding of the
+    interval that the FP32 value can occupy (the bound above, widened by the error of the FP32
+    SiLU or SiLU' evaluation: (4 + 1.2 |x|) 2^-23 relative for the exponential intrinsic);
+  * loss gradient: 2 (out - tgt) / count with four FP32 roundings, rounded to BF16;
+  * loss: (n + 4) 2^-23 of the sum of the n squared residuals (FP32 sums in any order);
+  * weight and bias gradients: (M + 4) 2^-22 (sum |g a|) for M = windows x 64 positions of a chunk.
+
+A dropped, repeated or misplaced tap or channel moves an entry by about one term of its sum,
+|W a| ~ (sum |W a|) / K, two orders of magnitude above these bounds.
+"""
+import numpy as np
+import pytest
+
+from oracle import surrogate_ref as R
+from test_gpu_surrogate import _act, _cuda, _setup_network, oracle_window  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+U22 = 2.0 ** -22
+U23 = 2.0 ** -23
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_13766_gb300 import build
+    build.build()
+
+
+def _cp(buf):
+    """[windows, rows, channels] with rows = positions + 2 -> [windows, channels, 51]."""
+    return np.asarray(buf, dtype=np.float64)[:, 2:2 + R.POS, :].transpose(0, 2, 1)
+
+
+def _bf16_bracket(got, lo, hi):
+    """True where the BF16 value `got` is a round-to-nearest BF16 of some value in [lo, hi]."""
+    a, b = np.minimum(lo, hi), np.maximum(lo, hi)
+    return (R.bf16(a) <= got) & (got <= R.bf16(b))
+
+
+@pytest.fixture(scope="module")
+def step(oracle_window):  # noqa: F811
+    p, s0, s1, t0, dt, W = oracle_window
+    T = W * dt
+    act = _act(p, t0, T)
+    sur, params, scales = _setup_network(p, s0, s1, act, T)
+    loss = sur.train_step(_cuda(s0), _cuda(s1), _cuda([act])[0], lr=0.0)
+    bufs = {k: sur.debug_buffer(k).astype(np.float64) for k in range(13)}
+    layers = R.unpack(params)
+    Wb = [(R.bf16(Wl), bl.astype(np.float32).astype(np.float64)) for Wl, bl in layers]
+    return {"loss": loss, "grad": sur.get_grad().astype(np.float64), "bufs": bufs, "W": Wb,
+            "params": params, "scales": scales, "s0": s0, "act": act}
+
+
+def _check_pre(z_gpu, inp, W, b, K):
+    z = R.conv(inp, W, b)
+    mag = R.conv(np.abs(inp), np.abs(W), np.abs(b))
+    err = np.abs(z_gpu - z)
+    bound = (K + 2) * U22 * mag + 1e-37
+    assert np.all(err <= bound), (float((err / np.maximum(mag, 1e-300)).max()), K)
+    return float((err / np.maximum(mag, 1e-300)).max())
+
+
+def test_network_input_is_the_bf16_rounding_of_the_reference_features(step, oracle_window):  # noqa: F811
+    """float32(raw - shift) * float32(scale), rounded to BF16, from raw features that agree with
+    the reference to 1e-12 of each channel's magnitude (test_gpu_surrogate): every entry lies in
+    the image of that interval under the same monotone chain of roundings."""
+    sh, sc, _ = step["scales"]
+    F, M = R.raw_features(*step["s0"], step["act"])
+    delta = 1e-12 * np.abs(F).max(axis=(0, 2), keepdims=True) + 1e-300
+    shv = np.asarray(sh, dtype=np.float64)[None, :, None]
+    sc32 = np.asarray(sc, dtype=np.float64).astype(np.float32)[None, :, None]
+
+    def chain(raw):
+        return R.bf16(((raw - shv).astype(np.float32) * sc32).astype(np.float64))
+
+    lo, hi = np.where(M, chain(F - delta), 0.0), np.where(M, chain(F + delta), 0.0)
+    got = _cp(step["bufs"][0])
+    assert np.all(got[:, R.N_FEAT:] == 0.0)
+    g = got[:, :R.N_FEAT]
+    assert np.all((np.minimum(lo, hi) <= g) & (g <= np.maximum(lo, hi)))
+    pad = step["bufs"][0]
+    assert np.all(pad[:, :2] == 0) and np.all(pad[:, 2 + R.POS:] == 0)
+
+
+@pytest.mark.parametrize("layer", [0, 1, 2])
+def test_hidden_layer_pre_activations_and_activations(step, layer):
+    bufs = step["bufs"]
+    Wl, bl = step["W"][layer]
+    inp = _cp(bufs[layer])
+    K = R.TAPS * inp.shape[1]
+    pre = _cp(bufs[4 + layer])
+    _check_pre(pre, inp, Wl, bl, K)
+    # activation: BF16 of the FP32 SiLU of the FP32 pre-activation
+    s = R.silu(pre)
+    eps = (4.0 + 1.2 * np.abs(pre)) * U23
+    got = _cp(bufs[layer + 1])
+    ok = _bf16_bracket(got, s - eps * np.abs(s) - 1e-38, s + eps * np.abs(s) + 1e-38)
+    assert np.all(ok), int((~ok).sum())
+    out = bufs[layer + 1]
+    assert np.all(out[:, :2] == 0) and np.all(out[:, 2 + R.POS:] == 0)
+
+
+def test_output_layer(step):
+    bufs = step["bufs"]
+    W4, b4 = step["W"][3]
+    out = np.asarray(bufs[7], dtype=np.float64).transpose(0, 2, 1)        # [nwin, 16, 51]
+    _check_pre(out, _cp(bufs[3]), W4, b4, R.TAPS * 64)
+
+
+def test_loss_and_its_gradient(step):
+    bufs = step["bufs"]
+    out = bufs[7][:, :, :R.N_OUT]
+    tgt = bufs[8][:, :, :R.N_OUT]
+    r = out - tgt
+    n = r.size
+    ref = float((r * r).sum() / n)
+    assert abs(step["loss"] - ref) <= (n + 4) * U23 * ref, (step["loss"], ref)
+    g = 2.0 * r / n
+    eps = 4 * 2.0 ** -24
+    got = bufs[9][:, 2:2 + R.POS, :R.N_OUT]
+    assert np.all(_bf16_bracket(got, g - eps * np.abs(g), g + eps * np.abs(g)))
+    assert np.all(bufs[9][:, :, R.N_OUT:] == 0) and np.all(bufs[9][:, :2] == 0) and np.all(bufs[9][:, 2 + R.POS:] == 0)
+
+
+@pytest.mark.parametrize("layer", [3, 2, 1])
+def test_back_propagated_gradients(step, layer):
+    """g at the output of layer `layer` (1-based below it) from the gradient above: the input
+    gradient of the convolution, times SiLU' of the lower pre-activation, stored in BF16."""
+    bufs = step["bufs"]
+    W, _ = step["W"][layer]
+    g_above = _cp(bufs[9 + (3 - layer)])          # 9: output gradient, 10: layer 3's, 11: layer 2's
+    acc = R.conv_input_grad(g_above, W)
+    mag = R.conv_input_grad(np.abs(g_above), np.abs(W))
+    K = R.TAPS * g_above.shape[1]
+    B = (K + 2) * U22 * mag + 1e-38
+    x = _cp(bufs[4 + layer - 1])                  # pre-activation of the layer below
+    d = R.dsilu(x)
+    ed = (2.0 ** -21) * (1.0 + np.abs(x)) * (3.0 + 1.2 * np.abs(x)) * np.maximum(1.0, np.abs(d))
+    corners = [(acc + sa * B) * (d + sd * ed) for sa in (-1, 1) for sd in (-1, 1)]
+    lo = np.minimum.reduce(corners)
+    hi = np.maximum.reduce(corners)
+    lo, hi = lo - 2.0 ** -24 * np.abs(lo) - 1e-38, hi + 2.0 ** -24 * np.abs(hi) + 1e-38
+    got = _cp(bufs[10 + (3 - layer)])
+    ok = _bf16_bracket(got, lo, hi)
+    assert np.all(ok), int((~ok).sum())
+
+
+@pytest.mark.parametrize("layer", [0, 1, 2, 3])
+def test_weight_and_bias_gradients(step, layer):
+    bufs = step["bufs"]
+    g = _cp(bufs[9 + (3 - layer)])                # gradient at the output of this layer
+    a = _cp(bufs[layer])                          # its input activations
+    dW, db = R.conv_weight_grad(g, a)
+    mW, mb = R.conv_weight_grad(np.abs(g), np.abs(a))
+    nwin = g.shape[0]
+    M = min(nwin, 16) * 64 + (nwin + 15) // 16
+    off = 0
+    for l, (co, ci) in enumerate(R.SHAPES):
+        if l == layer:
+            break
+        off += co * R.TAPS * ci + co
+    co, ci = R.SHAPES[layer]
+    gw = step["grad"][off:off + co * R.TAPS * ci].reshape(co, R.TAPS, ci)
+    gb = step["grad"][off + co * R.TAPS * ci:off + co * R.TAPS * ci + co]
+    assert np.all(np.abs(gw - dW) <= (M + 4) * U22 * mW + 1e-38), float((np.abs(gw - dW) / np.maximum(mW, 1e-300)).max())
+    assert np.all(np.abs(gb - db) <= (M + 4) * U22 * mb + 1e-38)
+    assert np.abs(dW).max() > 0

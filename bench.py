@@ -42,13 +42,21 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
 # FP64 flops per unit of each kernel as the kernel evaluates them, counted by ncu on the active
 # threads (add/sub/mul = 1 flop, fma = 2) and divided by the units of the launch.  pack_one_step:
-# one launch of pack_kernel<3> on the 10^4-rod packing, 156.95M DFMA + 37.07M DADD + 121.45M
-# DMUL on 1,366,295 element-steps.  pack_steps: one 20-step launch of pack_kernel<0> on the
-# 64 x 64 carpet, 465.37M DFMA + 82.90M DADD + 367.68M DMUL on 4,096,000 element-steps.
+# one launch of pack_kernel<3> on the 10^4-rod packing near step 1000, 133.98M DFMA + 32.12M
+# DADD + 107.91M DMUL on 1,366,295 element-steps.  pack_steps: one 20-step launch of
+# pack_kernel<0> on the 64 x 64 carpet, 465.37M DFMA + 82.90M DADD + 367.68M DMUL on 4,096,000
+# element-steps (before the FP64 instruction cuts of the step's stages).
 FLOPS_PER_UNIT = {
-    "pack_one_step": 345.8,   # per element-step
+    "pack_one_step": 298.6,   # per element-step
     "pack_steps": 337.2,      # per element-step
 }
+# FP64-pipe instructions per unit (thread level, ncu smsp__sass_thread_inst_executed_op_fp64):
+# a DMUL or DADD takes the FP64 unit as long as a DFMA, so the pipe is bound by instructions,
+# not flops; peak 2 per clock per SM x 152 SMs x 2.07 GHz.
+FP64_INSTR_PER_UNIT = {
+    "pack_one_step": 202.56,
+}
+FP64_INSTR_PEAK = 2 * 152 * 2.07e9
 FLOPS_SOURCE = "executed FP64 arithmetic of the kernel (ncu: DFMA x 2 + DADD + DMUL) per element-step"
 # The method's FP64 work per element-step as the oracle states it: every addition, subtraction,
 # multiplication and division of one step of the oracle's source evaluated over counting numbers
@@ -93,7 +101,7 @@ def _measured_hbm_gbs():
 # CPU seconds the reference arm spends on its W + K samples (the whole run stays within minutes)
 REF_BUDGET_S = 90.0
 TRAFFIC_PER_LAUNCH = {
-    "pack_one_step": 286.81e6 + 142.23e6,
+    "pack_one_step": 287.23e6 + 144.93e6,
     "pack_steps": 39.28e6,
 }
 
@@ -645,6 +653,13 @@ def main():
                          "statement of the same step, counted on its source",
             "peak_source": "FP64: 2 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal unit count; an FMA probe measured 1.91/clk)",
             "hbm_frac": hbm["step_frac"] if hbm else None, "hbm": hbm,
+            "fp64_pipe": ({"instr_per_unit": FP64_INSTR_PER_UNIT[dname],
+                           "achieved_instr_per_s": FP64_INSTR_PER_UNIT[dname] * units / (avg_ms * 1e-3),
+                           "peak_instr_per_s": FP64_INSTR_PEAK,
+                           "frac": FP64_INSTR_PER_UNIT[dname] * units / (avg_ms * 1e-3) / FP64_INSTR_PEAK,
+                           "note": "FP64-pipe instruction rate against 2 per clock per SM (DMUL and DADD cost "
+                                   "a DFMA's slot, so the flop fraction understates the pipe's load)"}
+                          if dname in FP64_INSTR_PER_UNIT else None),
             "kernel_share": {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4)
                              for k, v in prof.items() if v[1]}}
 

@@ -209,7 +209,7 @@ struct rod_system {
   bool shape_user = false;
   // misc
   double gravity[3] = {0, 0, 0};
-  bool has_gravity = false, has_act = false;
+  bool has_gravity = false, has_act = false, has_damp_lin = false;
   DevBuf<int> err;
   int* err_host = nullptr;  // pinned
   bool state_set = false;
@@ -434,6 +434,7 @@ StepParams make_params(rod_system* s) {
   P.n_rods = s->R;
   for (int c = 0; c < 3; ++c) P.gravity[c] = s->gravity[c];
   P.has_gravity = s->has_gravity;
+  P.has_damp_lin = s->has_damp_lin;
   P.has_act = s->has_act;
   P.magnet = s->magnet.p;
   for (int c = 0; c < 3; ++c) {
@@ -763,6 +764,9 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
     }
     rc.damp_lin = (d->nu_damp + d->stokes_gamma) / (rho * A);
     rc.damp_rot = d->nu_damp / (rho * A);
+    s->has_damp_lin = s->has_damp_lin || rc.damp_lin != 0.0;
+    rc.rhoI_12 = rc.rhoI[1] - rc.rhoI[2];
+    rc.B_21 = rc.B[2] - rc.B[1];
     rc.radius = rad;
     rc.radius_f = static_cast<float>(rad);
     rc.node0 = static_cast<int32_t>(n0);

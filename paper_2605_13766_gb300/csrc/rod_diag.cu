@@ -94,10 +94,7 @@ __global__ void __launch_bounds__(256) diag_rod_kernel(DiagArgs A) {
     const double u0 = (qb[6] * qa[3] + qb[7] * qa[4] + qb[8] * qa[5]) - (qb[3] * qa[6] + qb[4] * qa[7] + qb[5] * qa[8]);
     const double u1 = (qb[0] * qa[6] + qb[1] * qa[7] + qb[2] * qa[8]) - (qb[6] * qa[0] + qb[7] * qa[1] + qb[8] * qa[2]);
     const double u2 = (qb[3] * qa[0] + qb[4] * qa[1] + qb[5] * qa[2]) - (qb[0] * qa[3] + qb[1] * qa[4] + qb[2] * qa[5]);
-    const double s2 = 0.25 * (u0 * u0 + u1 * u1 + u2 * u2);
-    const double dd1 = qb[0] * qa[0] + qb[1] * qa[1] + qb[2] * qa[2];
-    const double dd3 = qb[6] * qa[6] + qb[7] * qa[7] + qb[8] * qa[8];
-    const double f = theta_over_sin(s2, dd1, dd3, qa, qb);
+    const double f = theta_over_sin(u0 * u0 + u1 * u1 + u2 * u2, qa, qb);
     const double D = 0.5 * (A.rest_len[ge] + A.rest_len[ge + 1]);
     const double kf = -0.5 * f / D;
     const double kap[3] = {kf * u0, kf * u1, kf * u2};

@@ -38,6 +38,10 @@ struct RodConst {
   double muscle_omega;  // 2 pi / T
   double muscle_k;      // 2 pi / lambda
   double muscle_phase;
+  // circular cross-section: I1 = I2, so S[0] = S[1], B[0] = B[1], rhoI[0] = rhoI[1]; the step
+  // folds the products that these equalities make redundant, with
+  double rhoI_12;       // rhoI[1] - rhoI[2]: (rho I w) x w = rhoI_12 (w1 w2, -w0 w2, 0)
+  double B_21;          // B[2] - B[1]: kappa x (B kappa) = B_21 (k1 k2, -k0 k2, 0)
 };
 
 constexpr int kMaxWalls = 8;
@@ -109,6 +113,7 @@ struct StepParams {
   int32_t n_rods;
   double gravity[3];
   int32_t has_gravity;
+  int32_t has_damp_lin;       // some rod has linear damping or drag (damp_lin != 0)
   int32_t has_act;
   // magnetic couple rl (m x (Q b(t))): m per unit reference length (local) [3E] or null
   const double* magnet;

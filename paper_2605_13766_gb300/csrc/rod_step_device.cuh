@@ -8,12 +8,53 @@
 #include <cmath>
 #include <cstdint>
 
+#include "rod_fp.h"
 #include "rod_internal.h"
 
 namespace rod {
 namespace {
 
 // ---------------------------------------------------------------------------------- math
+
+// 1/x by Newton-Raphson, y <- y + y (1 - x y), from a seed that costs no FP64 instruction: x
+// rounded to FP32 on the integer pipe, its correctly rounded FP32 reciprocal, widened on the
+// integer pipe (relative error below 2^-23).  Two steps square the error twice, to below the
+// FP64 rounding: 4 FP64 instructions.  x whose FP32 rounding or reciprocal leaves the FP32
+// normal range takes the FP64 reciprocal instruction sequence instead.
+__device__ __forceinline__ double rcp_nr(double x) {
+  bool ok1, ok2;
+  const float xf = f32_rn_bits(x, ok1);
+  const double y0 = f64_of_f32_bits(__frcp_rn(xf), ok2);
+  if (!(ok1 && ok2) || xf == 0.0f) return __drcp_rn(x);
+  const double e0 = fma(-x, y0, 1.0);
+  const double y1 = fma(y0, e0, y0);
+  const double e1 = fma(-x, y1, 1.0);
+  return fma(y1, e1, y1);
+}
+
+// 1/sqrt(x) for x > 0 by one Newton-Raphson step, y <- y + (y/2)(1 - x y^2), from the seed of
+// rcp_nr's kind (the correctly rounded FP32 rsqrt of x rounded to FP32: relative error below
+// 1.5 2^-24; y/2 formed in FP32 and widened, exactly).  The step leaves a relative error below
+// 1.5 (1.5 2^-24)^2 + 2^-52 < 1.3e-14: 3 FP64 instructions.  Otherwise the FP64 rsqrt.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  bool ok1, ok2, ok3;
+  const float xf = f32_rn_bits(x, ok1);
+  const float yf = __frsqrt_rn(xf);
+  const double y0 = f64_of_f32_bits(yf, ok2);
+  const double h0 = f64_of_f32_bits(0.5f * yf, ok3);
+  if (!(ok1 && ok2 && ok3) || !(xf > 0.0f)) return rsqrt(x);
+  const double t = x * y0;
+  const double r = fma(-t, y0, 1.0);
+  return fma(h0, r, y0);
+}
+
+// FP32 rounding of a position for the shared-memory copy (integer pipe; the conversion
+// instruction only for values outside the FP32 normal range)
+__device__ __forceinline__ float f32_rn(double x) {
+  bool ok;
+  const float f = f32_rn_bits(x, ok);
+  return ok ? f : static_cast<float>(x);
+}
 
 // High 32 bits of a non-negative double: x < 2^k exactly when hi_word(x) < hi_word(2^k), so a
 // warp-wide integer maximum of these words bounds every lane's argument.
@@ -90,30 +131,52 @@ __device__ __forceinline__ double asin_over_s(double s2) {
   return f;
 }
 
-// theta / sin(theta) of the relative rotation R = Q_{k+1} Q_k^T with sin^2 = s2, from the
-// diagonal products dd_a = d_a(k+1) . d_a(k) (cos theta = (dd1 + dd2 + dd3 - 1) / 2).  Warp-
-// uniform cut of the series like rot_coeffs (s2 < 2^-20: three terms, dropped < 4e-20; s2 <
-// 2^-10: six terms, dropped < 2e-20) when every lane's rotation is small.  With s2 < 2^-10 the
-// angle is below 1.8 deg or above 178.2 deg; above 178.2 deg, dd_a = cos t + (1 - cos t)(n . d_a)^2
+// An FP32 approximation of a double of magnitude at most 2 built from its high word on the
+// integer pipe (mantissa cut to 20 bits; magnitudes below 2^-126 give zero); for comparisons
+// with wide margins only.
+__device__ __forceinline__ float f32_approx_hi(double x) {
+  const unsigned hi = static_cast<unsigned>(__double2hiint(x));
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  const unsigned sign = hi & 0x80000000u;
+  return __uint_as_float(e > 896u ? (sign | ((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3)) : sign);
+}
+
+// theta / sin(theta) of the relative rotation R = Q_{k+1} Q_k^T, from s4 = |u|^2 = 4 sin^2
+// theta (u = (R32 - R23, R13 - R31, R21 - R12)).  Warp-uniform cut of the series like
+// rot_coeffs (sin^2 < 2^-20: three terms, dropped < 4e-20; sin^2 < 2^-10: six terms, dropped
+// < 2e-20) when every lane's rotation is small.  With sin^2 < 2^-10 the angle is below 1.8 deg
+// or above 178.2 deg; above 178.2 deg, dd_a = d_a(k+1) . d_a(k) = cos t + (1 - cos t)(n . d_a)^2
 // < 2 (n . d_a)^2 - 0.9995 (n the axis), so dd1 and dd3 cannot both exceed 1/4 (that needs
 // (n . d1)^2 + (n . d3)^2 > 1.249), while below 1.8 deg both exceed cos t > 0.9995.  The test
-// reads their high words on the integer pipe; cos theta itself is formed only off the fast path.
-__device__ __forceinline__ double theta_over_sin(double s2, double dd1, double dd3, const double* qa,
-                                                 const double* qb) {
-  constexpr int kHiQuarter = 0x3FD00000;  // high word of 0.25
+// takes dd1 and dd3 in FP32 from the high words of the directors (integer and FP32 pipes; their
+// error, below 1e-5, is far inside the margins); FP64 dot products and cos theta are formed only
+// off the fast path.
+__device__ __forceinline__ double theta_over_sin(double s4, const double* qa, const double* qb) {
+  constexpr unsigned kHi2m18 = 0x3ED00000u;  // 4 x 2^-20
+  constexpr unsigned kHi2m8 = 0x3F700000u;   // 4 x 2^-10
   const unsigned act = __activemask();
-  const unsigned mx = __reduce_max_sync(act, hi_word(s2));
-  const bool small = __all_sync(act, __double2hiint(dd1) > kHiQuarter && __double2hiint(dd3) > kHiQuarter);
-  if (small && mx < kHi2m20) return fma(fma(s2, 3.0 / 40.0, 1.0 / 6.0), s2, 1.0);
-  if (small && mx < kHi2m10) {
-    double f = 63.0 / 2816.0;
-    f = fma(f, s2, 35.0 / 1152.0);
-    f = fma(f, s2, 5.0 / 112.0);
-    f = fma(f, s2, 3.0 / 40.0);
-    f = fma(f, s2, 1.0 / 6.0);
-    return fma(f, s2, 1.0);
+  const unsigned mx = __reduce_max_sync(act, hi_word(s4));
+  float d1 = 0.f, d3 = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    d1 = fmaf(f32_approx_hi(qb[c]), f32_approx_hi(qa[c]), d1);
+    d3 = fmaf(f32_approx_hi(qb[6 + c]), f32_approx_hi(qa[6 + c]), d3);
   }
+  const bool small = __all_sync(act, d1 > 0.25f && d3 > 0.25f);
+  // the series in sin^2 = s4 / 4, with its coefficients scaled by powers of 1/4
+  if (small && mx < kHi2m18) return fma(fma(s4, 3.0 / 640.0, 1.0 / 24.0), s4, 1.0);
+  if (small && mx < kHi2m8) {
+    double f = 63.0 / 2883584.0;
+    f = fma(f, s4, 35.0 / 294912.0);
+    f = fma(f, s4, 5.0 / 7168.0);
+    f = fma(f, s4, 3.0 / 640.0);
+    f = fma(f, s4, 1.0 / 24.0);
+    return fma(f, s4, 1.0);
+  }
+  const double s2 = 0.25 * s4;
+  const double dd1 = fma(qb[0], qa[0], fma(qb[1], qa[1], qb[2] * qa[2]));
   const double dd2 = fma(qb[3], qa[3], fma(qb[4], qa[4], qb[5] * qa[5]));
+  const double dd3 = fma(qb[6], qa[6], fma(qb[7], qa[7], qb[8] * qa[8]));
   const double c = 0.5 * ((dd1 + dd2 + dd3) - 1.0);
   if (s2 <= 0.0625 && c > 0.0) return asin_over_s(s2);
   const double sn = sqrt(s2);
@@ -239,7 +302,7 @@ __device__ __forceinline__ void kin_node(const StepParams& P, const Pack& pk, Sm
   for (int c = 0; c < 3; ++c) {
     const double val = held ? P.clamp_x[c * P.n_rods + g] : fma(h, m.VN[c * m.CN + j], m.X[c * m.CN + j]);
     m.X[c * m.CN + j] = val;
-    if (m.XF) m.XF[c * m.CN + j] = static_cast<float>(val);
+    if (m.XF) m.XF[c * m.CN + j] = f32_rn(val);
   }
 }
 
@@ -270,7 +333,7 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
 #pragma unroll
     for (int a = 0; a < 9; ++a) q[a] = m.QQ[a * m.CE + i];
     const double ll = fma(l[0], l[0], fma(l[1], l[1], l[2] * l[2]));
-    const double rs = rsqrt(ll);            // 1 / ell
+    const double rs = rsqrt_nr(ll);         // 1 / ell
     const double ell = ll * rs;
     const double irl = __ldg(P.inv_rl + ge);
     const double rl = __ldg(P.rest_len + ge);
@@ -289,10 +352,11 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
 #pragma unroll
       for (int c = 0; c < 3; ++c) n[c] = (__ldg(&rc->S[c]) * ie) * sg[c];
     } else {
-      // sigma / e = (Q l / rl - e3) rl / ell = Q l / ell - e3 rl / ell
+      // sigma / e = (Q l / rl - e3) rl / ell = Q l / ell - e3 rl / ell  (S[0] = S[1])
       const double s2 = __ldg(&rc->S[2]);
-      n[0] = (__ldg(&rc->S[0]) * rs) * Ql[0];
-      n[1] = (__ldg(&rc->S[1]) * rs) * Ql[1];
+      const double s01 = __ldg(&rc->S[0]) * rs;
+      n[0] = s01 * Ql[0];
+      n[1] = s01 * Ql[1];
       n[2] = fma(s2 * rs, Ql[2], -s2 * ie);
     }
     // lab internal force N = Q^T n / e
@@ -306,17 +370,17 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
     // transport couples (J w / e) x w + (J w / e^2) de/dt,  de/dt = (l . dv) / (ell rl), and the
     // rotational damping -nu rl (I/A) w; with J w = rl g, g = rho I w:
     //   rl/e (g x w) + rl (de/dt / e^2 - damp_rot) g
-    const double edot = fma(l[0], dv[0], fma(l[1], dv[1], l[2] * dv[2])) * rs * irl;
-    double gw[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) gw[c] = __ldg(&rc->rhoI[c]) * w[c];
-    const double k1 = rl * ie;
-    const double k2 = rl * fma(ie * ie, edot, -__ldg(&rc->damp_rot));
-    tc[0] = fma(k1, fma(gw[1], w[2], -gw[2] * w[1]), tc[0]);
-    tc[1] = fma(k1, fma(gw[2], w[0], -gw[0] * w[2]), tc[1]);
-    tc[2] = fma(k1, fma(gw[0], w[1], -gw[1] * w[0]), tc[2]);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) tc[c] = fma(k2, gw[c], tc[c]);
+    // For a circular section rho I = (j, j, j3): g x w = (j - j3)(w1 w2, -w0 w2, 0).
+    // rl (de/dt / e^2 - damp_rot) = ie^2 ((l . dv) rs) - rl damp_rot   (rl / (ell rl e^2) = ie^2 rs)
+    const double ldv = fma(l[0], dv[0], fma(l[1], dv[1], l[2] * dv[2]));
+    const double k1 = (rl * ie) * __ldg(&rc->rhoI_12);
+    const double k2 = fma(ie * ie, ldv * rs, -rl * __ldg(&rc->damp_rot));
+    tc[0] = fma(k1, w[1] * w[2], tc[0]);
+    tc[1] = fma(-k1, w[0] * w[2], tc[1]);
+    const double k2j = k2 * __ldg(&rc->rhoI[0]);
+    tc[0] = fma(k2j, w[0], tc[0]);
+    tc[1] = fma(k2j, w[1], tc[1]);
+    tc[2] = fma(k2 * __ldg(&rc->rhoI[2]), w[2], tc[2]);
     if (P.elem_couple) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) tc[c] += __ldg(P.elem_couple + c * P.E + ge);
@@ -382,31 +446,38 @@ __device__ __forceinline__ void stage_voronoi(const StepParams& P, const Pack& p
     u2 = fma(-qb[0], qa[3], u2);
     u2 = fma(-qb[1], qa[4], u2);
     u2 = fma(-qb[2], qa[5], u2);
-    const double s2 = 0.25 * fma(u0, u0, fma(u1, u1, u2 * u2));  // |w|^2 = sin^2(theta)
-    const double dd1 = fma(qb[0], qa[0], fma(qb[1], qa[1], qb[2] * qa[2]));
-    const double dd3 = fma(qb[6], qa[6], fma(qb[7], qa[7], qb[8] * qa[8]));
-    const double f = theta_over_sin(s2, dd1, dd3, qa, qb);
+    const double s4 = fma(u0, u0, fma(u1, u1, u2 * u2));  // |u|^2 = 4 sin^2(theta)
+    const double f = theta_over_sin(s4, qa, qb);
     const double i2D = __ldg(P.inv_2D + gv);
     const double kf = -f * i2D;             // kappa = -(theta/s) w / D = -f u / (2D)
-    double kap[3] = {kf * u0, kf * u1, kf * u2};
     const double eps = (m.ELL[i] + m.ELL[i + 1]) * i2D;
-    const double ieps = __drcp_rn(eps);
+    const double ieps = rcp_nr(eps);
     const double ie3 = ieps * ieps * ieps;
-    double mk[3];
+    const double tD = __ldg(P.Dhat + gv) * ie3;
     if (P.rest_kappa) {
+      const double kap[3] = {kf * u0, kf * u1, kf * u2};
+      double mk[3];
 #pragma unroll
       for (int cc = 0; cc < 3; ++cc) mk[cc] = __ldg(&rc->B[cc]) * (kap[cc] - __ldg(P.rest_kappa + cc * P.V + gv));
+      m.PP[k] = mk[0] * ie3;
+      m.PP[m.CV + k] = mk[1] * ie3;
+      m.PP[2 * m.CV + k] = mk[2] * ie3;
+      m.TT[k] = fma(kap[1], mk[2], -kap[2] * mk[1]) * tD;
+      m.TT[m.CV + k] = fma(kap[2], mk[0], -kap[0] * mk[2]) * tD;
+      m.TT[2 * m.CV + k] = fma(kap[0], mk[1], -kap[1] * mk[0]) * tD;
     } else {
-#pragma unroll
-      for (int cc = 0; cc < 3; ++cc) mk[cc] = __ldg(&rc->B[cc]) * kap[cc];
+      // m = B kappa = kf B u; with B = (b, b, b3) (circular section) kappa x m = kf^2 (b3 - b)
+      // (u1 u2, -u0 u2, 0)
+      const double sk = kf * ie3;
+      const double sb = sk * __ldg(&rc->B[0]);
+      m.PP[k] = sb * u0;
+      m.PP[m.CV + k] = sb * u1;
+      m.PP[2 * m.CV + k] = (sk * __ldg(&rc->B[2])) * u2;
+      const double ct = ((kf * kf) * tD) * __ldg(&rc->B_21);
+      m.TT[k] = ct * (u1 * u2);
+      m.TT[m.CV + k] = -ct * (u0 * u2);
+      m.TT[2 * m.CV + k] = 0.0;
     }
-    const double tD = __ldg(P.Dhat + gv) * ie3;
-    m.PP[k] = mk[0] * ie3;
-    m.PP[m.CV + k] = mk[1] * ie3;
-    m.PP[2 * m.CV + k] = mk[2] * ie3;
-    m.TT[k] = fma(kap[1], mk[2], -kap[2] * mk[1]) * tD;
-    m.TT[m.CV + k] = fma(kap[2], mk[0], -kap[0] * mk[2]) * tD;
-    m.TT[2 * m.CV + k] = fma(kap[0], mk[1], -kap[1] * mk[0]) * tD;
   }
 }
 
@@ -431,6 +502,12 @@ __device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& 
     for (int c = 0; c < 3; ++c) {
       const double Pr = hasR ? m.PP[c * m.CV + k] : 0.0;
       const double Pl = hasL ? m.PP[c * m.CV + k - 1] : 0.0;
+      if (c == 2 && !P.rest_kappa) {
+        // the third component of kappa x (B kappa) vanishes for a circular section without rest
+        // curvature (stage_voronoi writes zeros there)
+        tau[c] = (Pr - Pl) + m.TA[c * m.CE + i];
+        continue;
+      }
       const double Tr = hasR ? m.TT[c * m.CV + k] : 0.0;
       const double Tl = hasL ? m.TT[c * m.CV + k - 1] : 0.0;
       tau[c] = fma(0.5, Tl + Tr, (Pr - Pl) + m.TA[c * m.CE + i]);
@@ -441,11 +518,12 @@ __device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& 
 #pragma unroll
       for (int c = 0; c < 3; ++c) acc_w[c * P.E + ge] = held ? 0.0 : ke * __ldg(&rc->inv_rhoI[c]) * tau[c];
     } else {
-      // w += dt e J^{-1} tau,  J^{-1} = 1/(rho I rl)
+      // w += dt e J^{-1} tau,  J^{-1} = 1/(rho I rl)  (inv_rhoI[0] = inv_rhoI[1])
       const double ke = (dt * m.EDIL[i]) * __ldg(P.inv_rl + ge);
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        m.WW[c * m.CE + i] = held ? 0.0 : fma(ke * __ldg(&rc->inv_rhoI[c]), tau[c], m.WW[c * m.CE + i]);
+      const double k01 = ke * __ldg(&rc->inv_rhoI[0]), k2 = ke * __ldg(&rc->inv_rhoI[2]);
+      m.WW[i] = held ? 0.0 : fma(k01, tau[0], m.WW[i]);
+      m.WW[m.CE + i] = held ? 0.0 : fma(k01, tau[1], m.WW[m.CE + i]);
+      m.WW[2 * m.CE + i] = held ? 0.0 : fma(k2, tau[2], m.WW[2 * m.CE + i]);
       // the following kinematic half/full step of this element (it reads only its own w, Q)
       if (h != 0.0) kin_element(P, pk, m, i, h);
     }
@@ -472,12 +550,19 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
     const double im = __ldg(P.inv_m + gn);
     const double dl = __ldg(&rc->damp_lin);
     double F[3];
+    bool contact = false;
+    int ge = 0;
+    bool fR = false, fL = false;
     if (P.fseg) {
-      // contact: node a of segment iR and node b of segment iR-1, folded into the difference;
-      // with the skin list only segments with candidates have entries (bit set in fmask)
-      const int ge = iR + m.dE[r];
-      const bool fR = hasR && (!P.fmask || ((__ldg(P.fmask + (ge >> 5)) >> (ge & 31)) & 1u));
-      const bool fL = hasL && (!P.fmask || ((__ldg(P.fmask + ((ge - 1) >> 5)) >> ((ge - 1) & 31)) & 1u));
+      // contact: node a of segment iR and node b of segment iR-1; with the skin list only
+      // segments with candidates have entries (bit set in fmask)
+      ge = iR + m.dE[r];
+      fR = hasR && (!P.fmask || ((__ldg(P.fmask + (ge >> 5)) >> (ge & 31)) & 1u));
+      fL = hasL && (!P.fmask || ((__ldg(P.fmask + ((ge - 1) >> 5)) >> ((ge - 1) & 31)) & 1u));
+      // warps without a contact force take the plain difference (the common case)
+      contact = __any_sync(__activemask(), fR || fL);
+    }
+    if (contact) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const double Nr = hasR ? m.NF[c * m.CE + iR] : 0.0;
@@ -529,12 +614,14 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
         acc_v[c * P.N + gn] = held ? 0.0 : a;
       }
     } else {
-      // v += dt (F/m - c v + g)  as  v (1 - dt c) + (dt/m) F + dt g
-      const double keep = fma(-dt, dl, 1.0), dtim = dt * im;
+      // v += dt (F/m - c v + g)  as  v (1 - dt c) + (dt/m) F + dt g  (keep = 1 without damping)
+      const double dtim = dt * im;
+      const double keep = P.has_damp_lin ? fma(-dt, dl, 1.0) : 1.0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const double vj = m.VN[c * m.CN + j];
-        const double base = P.has_gravity ? fma(vj, keep, dtg[c]) : vj * keep;
+        const double base = P.has_damp_lin ? (P.has_gravity ? fma(vj, keep, dtg[c]) : vj * keep)
+                                           : (P.has_gravity ? vj + dtg[c] : vj);
         m.VN[c * m.CN + j] = held ? 0.0 : fma(F[c], dtim, base);
       }
       // the following kinematic half/full step of this node (it reads only its own x, v)

@@ -1,0 +1,75 @@
+// Checks the integer-pipe FP64 <-> FP32 conversions of rod_fp.h against the host compiler's own
+// conversions (round to nearest, ties to even) on edge cases and random bit patterns.
+// Prints "<checked> <mismatches> <not_ok_in_range>" and exits 0.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+
+#include "../../paper_2605_13766_gb300/csrc/rod_fp.h"
+
+static uint64_t s = 0x9E3779B97F4A7C15ull;
+static uint64_t next() {  // xorshift64*
+  s ^= s >> 12;
+  s ^= s << 25;
+  s ^= s >> 27;
+  return s * 0x2545F4914F6CDD1Dull;
+}
+
+int main() {
+  long checked = 0, bad = 0, missed = 0;
+  auto check_d = [&](double x) {
+    bool ok = false;
+    const float got = rod::f32_rn_bits(x, ok);
+    const float ref = static_cast<float>(x);
+    // ok must hold exactly when the rounded result is zero or normal and x is finite, except for
+    // values just below the smallest normal that round up to it (reported not ok, by design)
+    const double ax = std::fabs(x);
+    const bool in_range = std::isfinite(x) && (ax == 0.0 || (ax >= 0x1p-126 && ax < 0x1p128));
+    if (ok) {
+      ++checked;
+      if (rod::fp32_bits(got) != rod::fp32_bits(ref)) ++bad;
+    } else if (in_range) {
+      ++missed;
+    }
+  };
+  auto check_f = [&](float f) {
+    bool ok = false;
+    const double got = rod::f64_of_f32_bits(f, ok);
+    const bool in_range = std::isfinite(f) && (f == 0.0f || std::fabs(f) >= std::numeric_limits<float>::min());
+    if (ok) {
+      ++checked;
+      const double ref = static_cast<double>(f);
+      if (rod::fp64_bits(got) != rod::fp64_bits(ref)) ++bad;
+    } else if (in_range) {
+      ++missed;
+    }
+  };
+  const double edges[] = {0.0, -0.0, 1.0, -1.0, 0x1p-126, -0x1p-126, 0x1p-127, 0x1.fffffep127, 0x1.ffffffp127,
+                          0x1.fffffefffffffp127, 0x1p128, 1e300, -1e-300, INFINITY, -INFINITY, NAN,
+                          1.0 + 0x1p-24, 1.0 + 0x1p-23 + 0x1p-24, 1.0 + 0x1p-24 + 0x1p-52, 3.0e-39, 1e-45};
+  for (double x : edges) check_d(x);
+  const float fedges[] = {0.0f, -0.0f, 1.0f, std::numeric_limits<float>::min(), std::numeric_limits<float>::max(),
+                          std::numeric_limits<float>::denorm_min(), INFINITY, NAN, -3.5f};
+  for (float f : fedges) check_f(f);
+  for (int i = 0; i < 2000000; ++i) {
+    const uint64_t r = next();
+    // exponents spread over the whole range, and concentrated around the FP32 range
+    uint64_t u = r;
+    if (i & 1) {
+      const uint64_t e = 860 + (next() % 330);
+      u = (r & 0x800FFFFFFFFFFFFFull) | (e << 52);
+    }
+    if (i % 4 == 2) u = (u & ~0x1FFFFFFFull) | 0x10000000ull;   // exact ties
+    double x;
+    std::memcpy(&x, &u, sizeof x);
+    check_d(x);
+    uint32_t v = static_cast<uint32_t>(r >> 17);
+    float f;
+    std::memcpy(&f, &v, sizeof f);
+    check_f(f);
+  }
+  std::printf("%ld %ld %ld\n", checked, bad, missed);
+  return 0;
+}

@@ -1,0 +1,21 @@
+"""The step kernels' integer-pipe FP64 <-> FP32 conversions (paper_2605_13766_gb300/csrc/rod_fp.h)
+against the host compiler's conversions: round to nearest with ties to even, bit for bit, on
+edge cases (ties, the ends of the FP32 normal range, zero, infinities, NaN) and 4 million random
+bit patterns; every value the conversions decline (ok = false) lies outside their stated range,
+except values just below the smallest FP32 normal, which they decline by design."""
+import os
+import subprocess
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_integer_pipe_conversions_match_the_compiler(tmp_path):
+    exe = str(tmp_path / "fp_bits_check")
+    subprocess.run(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-o", exe,
+                    os.path.join(ROOT, "tests", "csrc", "fp_bits_check.cpp")], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    checked, bad, missed = (int(v) for v in out)
+    assert checked > 2_500_000
+    assert bad == 0
+    # only values in [2^-127, 2^-126) (about 1 in 330 of the concentrated exponents) may be declined
+    assert missed < 0.01 * checked

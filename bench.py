@@ -400,7 +400,7 @@ def _surrogate_speedup(train_steps: int):
             "err_unit": "|x_tip - x_tip(plain)| / L, max over all rods", "bound": 1e-3,
             "check_bound_sampled": S.DEFAULT_CHECK_BOUND, "modes": modes,
             "timing": "plain: CUDA events on its stream; rollout: host wall clock around the whole checked rollout",
-            "training": info, "dtype": "bf16 tensor cores (mma.sync), FP32 accumulation, FP64 state"}
+            "training": info, "dtype": "bf16 tensor cores (tcgen05, accumulators in tensor memory), FP32 accumulation, FP64 state"}
 
 
 def _pre_rolled(p, dt, n_steps):

@@ -23,11 +23,13 @@
  *   - The library owns all device memory it allocates; caller buffers are only read or
  *     written during the call (or, for on_device copies, on the system's stream).
  *   - Device errors (non-finite state, a segment longer than the contact grid allows,
- *     a contact table overflow) latch into a device error word that rod_system_step() reports
- *     after it synchronises; rod_system_set_state() clears it.  No kernel of the library spins
- *     on a flag: the only device-wide wait is the grid barrier of the cooperative launch that
- *     steps a rod longer than a thread block holds, and a cooperative launch either runs all
- *     its blocks at once or fails to launch (ROD_ERR_CUDA), so that barrier cannot stall.
+ *     a contact table overflow, a bounded wait of the surrogate's tensor-core kernel that ran
+ *     out) latch into a device error word that rod_system_step() reports after it
+ *     synchronises; rod_system_set_state() clears it.  The device-wide wait of the cooperative
+ *     launch that steps a rod longer than a thread block holds cannot stall (a cooperative
+ *     launch either runs all its blocks at once or fails to launch, ROD_ERR_CUDA); the
+ *     surrogate's fused kernel waits on an mbarrier for its own tensor-core operations, at most
+ *     a fixed number of polls, after which it latches the error, drains and ends.
  */
 #ifndef ROD_H
 #define ROD_H
@@ -45,7 +47,7 @@ typedef enum {
   ROD_ERR_ARG = -1,       /* invalid argument or description */
   ROD_ERR_CUDA = -2,      /* a CUDA runtime call failed (message has the CUDA error) */
   ROD_ERR_NONFINITE = -3, /* the state became NaN/Inf */
-  ROD_ERR_TIMEOUT = -4,   /* reserved for a bounded device wait that ran out; no call returns it */
+  ROD_ERR_TIMEOUT = -4,   /* a bounded device wait (the surrogate's tensor-core kernel) ran out */
   ROD_ERR_OVERFLOW = -5,  /* contact grid or table capacity exceeded */
   ROD_ERR_STATE = -6      /* call not valid in the current state (e.g. no state set) */
 } rod_status;
@@ -141,7 +143,7 @@ rod_status rod_system_get_time(const rod_system* sys, double* t);
  * Eq. 1a and Eq. 1b at the half step (contact included when enabled), the dynamic update of v
  * and w, and the second half kinematic stage.  Enqueued on the system's stream;
  * the call synchronises that stream at the end and returns the device error word
- * (ROD_ERR_NONFINITE / ROD_ERR_OVERFLOW) if one was raised. */
+ * (ROD_ERR_NONFINITE / ROD_ERR_OVERFLOW / ROD_ERR_TIMEOUT) if one was raised. */
 rod_status rod_system_step(rod_system* sys, int64_t n_steps, double dt);
 
 /* Same as rod_system_step but returns as soon as the work is enqueued; call
@@ -415,6 +417,21 @@ rod_status rod_surrogate_raw_targets(rod_surrogate* sur, const double* x0, const
                                      const double* w0, const double* x1, const double* v1, const double* Q1,
                                      const double* w1, int32_t nwin, double* out, void* cuda_stream);
 rod_status rod_surrogate_apply(rod_surrogate* sur, rod_system* sys, int64_t n_calls);
+/* Polls of the fused inference kernel's waits for its tensor-core MMAs before it gives up
+ * (0: the default, 2^20).  A wait that runs out latches ROD_ERR_TIMEOUT into the system's error
+ * word (returned by rod_surrogate_apply and the system's next step or sync).  A test hook: with
+ * the top bit set the kernel issues no MMA, so its first wait runs out after the remaining
+ * bits' polls and the kernel ends without updating the state. */
+rod_status rod_surrogate_set_wait_polls(rod_surrogate* sur, uint32_t polls);
+/* One window call of the fused inference kernel with every layer's arrays captured, for
+ * checking the tensor-core layers element by element (a test hook; the paper has no
+ * counterpart).  pre, act: host buffers of cap >= 4 * R * 51 * 64 floats; entry
+ * ((l * R + b) * 51 + p) * 64 + o receives, for layer l = 0..3, rod b, node position p and
+ * output channel o, the FP32 accumulator plus bias (pre; the output layer fills o < 16), and
+ * the BF16 input of layer l, widened (act; l = 0: the features, channels 0..31).  Advances the
+ * system by one window like rod_surrogate_apply(sur, sys, 1).  ROD_ERR_STATE when the unfused
+ * path is forced (ROD_SURROGATE_UNFUSED). */
+rod_status rod_surrogate_apply_debug(rod_surrogate* sur, rod_system* sys, float* pre, float* act, int64_t cap);
 rod_status rod_surrogate_rollout(rod_surrogate* sur, rod_system* sys, rod_system* shadow, const int32_t* sample_rods,
                                  int32_t n_sample, int64_t n_calls, int32_t check_every, double bound,
                                  rod_surrogate_stats* stats);

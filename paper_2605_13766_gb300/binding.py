@@ -128,6 +128,8 @@ _SIGNATURES = {
     "rod_surrogate_get_grad": ([_P, _P, C.c_int], C.c_int),
     "rod_surrogate_forward": ([_P, _P, _P, _P, _P, _P, C.c_int32, _P, _P], C.c_int),
     "rod_surrogate_debug_buffer": ([_P, C.c_int32, _P, C.c_int64, _P], C.c_int),
+    "rod_surrogate_set_wait_polls": ([_P, C.c_uint32], C.c_int),
+    "rod_surrogate_apply_debug": ([_P, _P, _P, _P, C.c_int64], C.c_int),
     "rod_surrogate_set_prior": ([_P, C.c_int32], C.c_int),
     "rod_surrogate_raw_features": ([_P, _P, _P, _P, _P, _P, C.c_int32, _P, _P, _P], C.c_int),
     "rod_surrogate_raw_targets": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int32, _P, _P], C.c_int),
@@ -558,6 +560,20 @@ class Surrogate:
         _check(self.lib.rod_surrogate_debug_buffer(self.handle, int(which), out.ctypes.data, out.size, C.byref(n)))
         rows, ch = self._DEBUG_SHAPES[int(which)]
         return out.reshape(-1, rows, ch)
+
+    def set_wait_polls(self, polls: int):
+        """Polls of the fused kernel's tensor-core waits before ROD_ERR_TIMEOUT (0: default)."""
+        _check(self.lib.rod_surrogate_set_wait_polls(self.handle, int(polls)))
+
+    def apply_debug(self, system):
+        """One window call with every layer's arrays captured: (pre, act), each float32
+        [4 layers, rods, 51 positions, 64 channels] (see include/rod.h)."""
+        n = 4 * system.n_rods * 51 * 64
+        pre = np.zeros(n, dtype=np.float32)
+        act = np.zeros(n, dtype=np.float32)
+        _check(self.lib.rod_surrogate_apply_debug(self.handle, system.handle, pre.ctypes.data, act.ctypes.data, n))
+        shape = (4, system.n_rods, 51, 64)
+        return pre.reshape(shape), act.reshape(shape)
 
     def get_grad(self) -> np.ndarray:
         g = np.empty(self.n_params, dtype=np.float32)

@@ -470,6 +470,7 @@ rod_status read_error_word(rod_system* s) {
   if (e & ERR_NONFINITE) return fail(ROD_ERR_NONFINITE, "the state became non-finite (NaN/Inf)");
   if (e & ERR_GRID) return fail(ROD_ERR_OVERFLOW, "an element grew longer than the contact grid allows");
   if (e & ERR_OVERFLOW) return fail(ROD_ERR_OVERFLOW, "contact table capacity exceeded");
+  if (e & ERR_TIMEOUT) return fail(ROD_ERR_TIMEOUT, "a bounded wait of the surrogate's tensor-core kernel ran out");
   return ROD_OK;
 }
 
@@ -1575,6 +1576,7 @@ rod_status system_view(rod_system* s, SysView* out) {
   out->n_packs = s->n_packs;
   out->stream = s->stream;
   out->t = &s->t;
+  out->err = s->err.p;
   return ROD_OK;
 }
 }  // namespace rod

@@ -5,7 +5,9 @@
 // functions do the same conversions with integer operations on the bit patterns, for the
 // numbers whose conversion stays within the FP32 normal range (and zero); for the rest they
 // report `ok = false` and the caller takes the conversion instruction.  Host-compilable, so the
-// bit logic is tested on the CPU against the compiler's own conversions.
+// bit logic is tested on the CPU against the compiler's own conversions.  Device code also gets
+// the FP64 reciprocal and reciprocal square root by Newton-Raphson from seeds formed with them,
+// and the two conversions with their instruction as the fallback.
 #pragma once
 #include <cstdint>
 #include <cstring>
@@ -97,5 +99,57 @@ ROD_FP_HD double f64_of_f32_bits(float f, bool& ok) {
   ok = (b & 0x7FFFFFFFu) == 0u;
   return fp64_from_bits(sign);
 }
+
+#if defined(__CUDACC__)
+
+// 1/x by Newton-Raphson, y <- y + y (1 - x y), from a seed that costs no FP64 instruction: x
+// rounded to FP32 on the integer pipe, its correctly rounded FP32 reciprocal, widened on the
+// integer pipe (relative error below 2^-23).  Two steps square the error twice, to below the
+// FP64 rounding: 4 FP64 instructions.  x whose FP32 rounding or reciprocal leaves the FP32
+// normal range takes the FP64 reciprocal instruction sequence instead.
+__device__ __forceinline__ double rcp_nr(double x) {
+  bool ok1, ok2;
+  const float xf = f32_rn_bits(x, ok1);
+  const double y0 = f64_of_f32_bits(__frcp_rn(xf), ok2);
+  if (!(ok1 && ok2) || xf == 0.0f) return __drcp_rn(x);
+  const double e0 = fma(-x, y0, 1.0);
+  const double y1 = fma(y0, e0, y0);
+  const double e1 = fma(-x, y1, 1.0);
+  return fma(y1, e1, y1);
+}
+
+// 1/sqrt(x) for x > 0 by one Newton-Raphson step, y <- y + (y/2)(1 - x y^2), from the seed of
+// rcp_nr's kind (the correctly rounded FP32 rsqrt of x rounded to FP32: relative error below
+// 1.5 2^-24; y/2 formed in FP32 and widened, exactly).  The step leaves a relative error below
+// 1.5 (1.5 2^-24)^2 + 2^-52 < 1.3e-14: 3 FP64 instructions.  Otherwise the FP64 rsqrt.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  bool ok1, ok2, ok3;
+  const float xf = f32_rn_bits(x, ok1);
+  const float yf = __frsqrt_rn(xf);
+  const double y0 = f64_of_f32_bits(yf, ok2);
+  const double h0 = f64_of_f32_bits(0.5f * yf, ok3);
+  if (!(ok1 && ok2 && ok3) || !(xf > 0.0f)) return rsqrt(x);
+  const double t = x * y0;
+  const double r = fma(-t, y0, 1.0);
+  return fma(h0, r, y0);
+}
+
+// a double rounded to FP32 (integer pipe; the conversion instruction only for results outside
+// the FP32 normal range)
+__device__ __forceinline__ float f32_rn(double x) {
+  bool ok;
+  const float f = f32_rn_bits(x, ok);
+  return ok ? f : static_cast<float>(x);
+}
+
+// an FP32 value widened to FP64 (integer pipe; the conversion instruction for subnormals,
+// infinities and NaN)
+__device__ __forceinline__ double f64_of(float f) {
+  bool ok;
+  const double d = f64_of_f32_bits(f, ok);
+  return ok ? d : static_cast<double>(f);
+}
+
+#endif  // __CUDACC__
 
 }  // namespace rod

@@ -10,7 +10,7 @@ namespace rod {
 enum : int {
   ERR_NONFINITE = 1,
   ERR_OVERFLOW = 2,
-  ERR_RESERVED = 4,   // unused (no kernel waits on a flag)
+  ERR_TIMEOUT = 4,    // a bounded wait of the surrogate's fused kernel ran out
   ERR_GRID = 8,       // a segment longer than the contact cell allows
 };
 

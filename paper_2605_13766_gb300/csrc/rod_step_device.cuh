@@ -16,46 +16,6 @@ namespace {
 
 // ---------------------------------------------------------------------------------- math
 
-// 1/x by Newton-Raphson, y <- y + y (1 - x y), from a seed that costs no FP64 instruction: x
-// rounded to FP32 on the integer pipe, its correctly rounded FP32 reciprocal, widened on the
-// integer pipe (relative error below 2^-23).  Two steps square the error twice, to below the
-// FP64 rounding: 4 FP64 instructions.  x whose FP32 rounding or reciprocal leaves the FP32
-// normal range takes the FP64 reciprocal instruction sequence instead.
-__device__ __forceinline__ double rcp_nr(double x) {
-  bool ok1, ok2;
-  const float xf = f32_rn_bits(x, ok1);
-  const double y0 = f64_of_f32_bits(__frcp_rn(xf), ok2);
-  if (!(ok1 && ok2) || xf == 0.0f) return __drcp_rn(x);
-  const double e0 = fma(-x, y0, 1.0);
-  const double y1 = fma(y0, e0, y0);
-  const double e1 = fma(-x, y1, 1.0);
-  return fma(y1, e1, y1);
-}
-
-// 1/sqrt(x) for x > 0 by one Newton-Raphson step, y <- y + (y/2)(1 - x y^2), from the seed of
-// rcp_nr's kind (the correctly rounded FP32 rsqrt of x rounded to FP32: relative error below
-// 1.5 2^-24; y/2 formed in FP32 and widened, exactly).  The step leaves a relative error below
-// 1.5 (1.5 2^-24)^2 + 2^-52 < 1.3e-14: 3 FP64 instructions.  Otherwise the FP64 rsqrt.
-__device__ __forceinline__ double rsqrt_nr(double x) {
-  bool ok1, ok2, ok3;
-  const float xf = f32_rn_bits(x, ok1);
-  const float yf = __frsqrt_rn(xf);
-  const double y0 = f64_of_f32_bits(yf, ok2);
-  const double h0 = f64_of_f32_bits(0.5f * yf, ok3);
-  if (!(ok1 && ok2 && ok3) || !(xf > 0.0f)) return rsqrt(x);
-  const double t = x * y0;
-  const double r = fma(-t, y0, 1.0);
-  return fma(h0, r, y0);
-}
-
-// FP32 rounding of a position for the shared-memory copy (integer pipe; the conversion
-// instruction only for values outside the FP32 normal range)
-__device__ __forceinline__ float f32_rn(double x) {
-  bool ok;
-  const float f = f32_rn_bits(x, ok);
-  return ok ? f : static_cast<float>(x);
-}
-
 // High 32 bits of a non-negative double: x < 2^k exactly when hi_word(x) < hi_word(2^k), so a
 // warp-wide integer maximum of these words bounds every lane's argument.
 __device__ __forceinline__ unsigned hi_word(double x) { return static_cast<unsigned>(__double2hiint(x)); }

@@ -13,7 +13,10 @@
 // new state is prior + scale * output in FP64; the directors are re-orthonormalised
 // (Gram-Schmidt on d1, d2; d3 = d1 x d2) and a clamp is re-applied.
 //
-// Every convolution is an implicit GEMM on mma.sync.m16n8k16 (BF16 in, FP32 accumulate):
+// Inference (one persistent kernel per window call, tc_apply_kernel) runs the convolutions on
+// the fifth-generation tensor cores (tcgen05: operands in shared memory, accumulator in tensor
+// memory) and overlaps them with the FP64 features and update.  Training runs them kernel by
+// kernel as implicit GEMMs on mma.sync.m16n8k16 (BF16 in, FP32 accumulate):
 //   forward:  out[o, j] = b[o] + sum_{t,c} W[o, t, c] in[c, j + t - 2]    (M = C_out, N = j, K = 5 C_in)
 //   input gradient: the same kernel with the tap-transposed weights and flipped taps
 //   weight gradient: dW[o, t, c] = sum_{windows, j} g[o, j] in[c, j + t - 2]  (split over windows)
@@ -30,6 +33,8 @@
 
 #include "../../include/rod.h"
 #include "rod_contact.h"
+#include "rod_fp.h"
+#include "rod_tc.cuh"
 #include "rod_internal.h"
 
 namespace rod {
@@ -50,7 +55,9 @@ constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kW1, kOffW2 = kOffB1 + kC, kOffB2 = 
 constexpr int kOffW3 = kOffB2 + kC, kOffB3 = kOffW3 + kW3, kOffW4 = kOffB3 + kC, kOffB4 = kOffW4 + kW4;
 constexpr int kNumParams = kOffB4 + kCO;
 
-__device__ __forceinline__ float silu(float x) { return x / (1.0f + __expf(-x)); }
+// SiLU in FP32: the exponential and the quotient by their fast intrinsics (relative error below
+// (4.5 + 1.2 |x|) 2^-23; -0 below x = -87.3, where the true value is under 1.5e-36 in size)
+__device__ __forceinline__ float silu(float x) { return __fdividef(x, 1.0f + __expf(-x)); }
 __device__ __forceinline__ float dsilu(float x) {
   const float s = 1.0f / (1.0f + __expf(-x));
   return s * (1.0f + x * (1.0f - s));
@@ -244,12 +251,13 @@ struct Scales {
   int keep_w;              // 1: angular velocities are w + output (residual), 0: output alone
 };
 
-// Q_new = exp([-T w]x) Q (rows: directors): the director update of a constant angular velocity
-// w (local frame) held for the whole window, by the Rodrigues formula R = I + a K + b K^2 =
+// Directors d1, d2 (out[0..5]) of Q_new = exp([-T w]x) Q (rows: directors; d3 is not needed, the
+// update rebuilds it from d1 x d2): the director update of a constant angular velocity w (local
+// frame) held for the whole window, by the Rodrigues formula R = I + a K + b K^2 =
 // (1 - b th^2) I + a K + b p p^T with p = -T w, K = [p]x, a = sin(th)/th, b = (1 - cos th)/th^2.
 // No FP64 division: for th < 0.05 the Taylor polynomials of a and b in th^2 (the first omitted
 // terms, th^8/9! and th^8/10!, are below 1e-16), otherwise sin and cos of th.
-__device__ __forceinline__ void rotate_directors(const double w[3], double T, const double Q[9], double out[9]) {
+__device__ __forceinline__ void rotate_directors(const double w[3], double T, const double Q[9], double out[6]) {
   const double p0 = -T * w[0], p1 = -T * w[1], p2 = -T * w[2];
   const double th2 = fma(p0, p0, fma(p1, p1, p2 * p2));
   double a, b;
@@ -267,18 +275,16 @@ __device__ __forceinline__ void rotate_directors(const double w[3], double T, co
     b = 2.0 * shi * shi;
   }
   const double c0 = fma(-b, th2, 1.0);
-  const double b0 = b * p0, b1 = b * p1, b2 = b * p2;
+  const double b0 = b * p0, b1 = b * p1;
   const double a0 = a * p0, a1 = a * p1, a2 = a * p2;
-  const double R00 = fma(b0, p0, c0), R11 = fma(b1, p1, c0), R22 = fma(b2, p2, c0);
+  const double R00 = fma(b0, p0, c0), R11 = fma(b1, p1, c0);
   const double R01 = fma(b0, p1, -a2), R10 = fma(b1, p0, a2);
-  const double R02 = fma(b0, p2, a1), R20 = fma(b2, p0, -a1);
-  const double R12 = fma(b1, p2, -a0), R21 = fma(b2, p1, a0);
+  const double R02 = fma(b0, p2, a1), R12 = fma(b1, p2, -a0);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const double q0 = Q[k], q1 = Q[3 + k], q2 = Q[6 + k];
     out[k] = fma(R00, q0, fma(R01, q1, R02 * q2));
     out[3 + k] = fma(R10, q0, fma(R11, q1, R12 * q2));
-    out[6 + k] = fma(R20, q0, fma(R21, q1, R22 * q2));
   }
 }
 
@@ -337,7 +343,7 @@ __global__ void features_kernel(WinState S, const double* __restrict__ act, int 
     float val = 0.f;
     double d;
     if (j >= 0 && j < kPos && c < kFeat && raw_feature(S, act, nwin, b, j, c, &d))
-      val = static_cast<float>(d - sc.in_shift[c]) * sc.in_scale[c];
+      val = f32_rn(d - sc.in_shift[c]) * sc.in_scale[c];
     feat[(static_cast<int64_t>(b) * kRows + row) * kC0 + c] = __float2bfloat16_rn(val);
   }
 }
@@ -353,7 +359,7 @@ __device__ double target_value(const WinState& A, const WinState& B, double T, d
   if (c < 6) return B.v[(c - 3) * A.N + node] - (keep_v ? A.v[(c - 3) * A.N + node] : 0.0);
   if (!has_el) return 0.0;
   if (c < 12) {
-    double q0[9], qp[9];
+    double q0[9], qp[6];
     const double w0[3] = {A.w[el], A.w[A.E + el], A.w[2 * A.E + el]};
     load_q(A.Q, A.E, el, q0);
     rotate_directors(w0, Tq, q0, qp);
@@ -435,8 +441,8 @@ __device__ __forceinline__ void update_node(const WinState& S, int b, int j, con
   if (!held) {
     for (int c = 0; c < 3; ++c) {
       const double x0 = S.x[c * S.N + node], v0 = S.v[c * S.N + node];
-      x[c * N + ng] = x0 + (sc.prior_x ? sc.T * v0 : 0.0) + sc.out[c] * static_cast<double>(o[c]);
-      v[c * N + ng] = (sc.keep_v ? v0 : 0.0) + sc.out[3 + c] * static_cast<double>(o[3 + c]);
+      x[c * N + ng] = fma(sc.out[c], f64_of(o[c]), sc.prior_x ? fma(sc.T, v0, x0) : x0);
+      v[c * N + ng] = (sc.keep_v ? v0 : 0.0) + sc.out[3 + c] * f64_of(o[3 + c]);
     }
   } else {
     for (int c = 0; c < 3; ++c) {
@@ -453,20 +459,20 @@ __device__ __forceinline__ void update_node(const WinState& S, int b, int j, con
     for (int c = 0; c < 3; ++c) w[c * E + eg] = 0.0;
     return;
   }
-  double qp[9];
+  double qp[6];
   const double w0[3] = {S.w[e], S.w[S.E + e], S.w[2 * S.E + e]};
   rotate_directors(w0, sc.prior_q ? sc.T : 0.0, q0, qp);
   double d1[3], d2[3];
   for (int c = 0; c < 3; ++c) {
-    d1[c] = qp[c] + sc.out[6 + c] * static_cast<double>(o[6 + c]);
-    d2[c] = qp[3 + c] + sc.out[9 + c] * static_cast<double>(o[9 + c]);
-    w[c * E + eg] = (sc.keep_w ? w0[c] : 0.0) + sc.out[12 + c] * static_cast<double>(o[12 + c]);
+    d1[c] = qp[c] + sc.out[6 + c] * f64_of(o[6 + c]);
+    d2[c] = qp[3 + c] + sc.out[9 + c] * f64_of(o[9 + c]);
+    w[c * E + eg] = (sc.keep_w ? w0[c] : 0.0) + sc.out[12 + c] * f64_of(o[12 + c]);
   }
-  const double n1 = rsqrt(fma(d1[0], d1[0], fma(d1[1], d1[1], d1[2] * d1[2])));
+  const double n1 = rsqrt_nr(fma(d1[0], d1[0], fma(d1[1], d1[1], d1[2] * d1[2])));
   for (int c = 0; c < 3; ++c) d1[c] *= n1;
   const double p = fma(d1[0], d2[0], fma(d1[1], d2[1], d1[2] * d2[2]));
   for (int c = 0; c < 3; ++c) d2[c] = fma(-p, d1[c], d2[c]);
-  const double n2 = rsqrt(fma(d2[0], d2[0], fma(d2[1], d2[1], d2[2] * d2[2])));
+  const double n2 = rsqrt_nr(fma(d2[0], d2[0], fma(d2[1], d2[1], d2[2] * d2[2])));
   for (int c = 0; c < 3; ++c) d2[c] *= n2;
   const double d3[3] = {d1[1] * d2[2] - d1[2] * d2[1], d1[2] * d2[0] - d1[0] * d2[2], d1[0] * d2[1] - d1[1] * d2[0]};
   for (int c = 0; c < 3; ++c) {
@@ -545,232 +551,354 @@ __global__ void local_error_kernel(const double* __restrict__ xs, int64_t Ns, co
   if ((threadIdx.x & 31) == 0) atomicMax(err_bits, static_cast<unsigned long long>(__double_as_longlong(worst)));
 }
 
-// ---- fused inference: one persistent kernel per window call
+// ---- fused inference on the fifth-generation tensor cores (tcgen05)
 //
-// Each block keeps all BF16 weights in shared memory (rows padded so that the fragment loads of
-// a warp hit 32 distinct banks) and loops over groups of kFW windows: stage the FP64 state of the
-// group, build the features, run the four convolutions between two shared activation buffers and
-// update the state in FP64.  8 warps: warp w takes window w / 2 and output rows 32 (w % 2) ..
-// +31 of a 64-channel layer (2 m-tiles x 7 n-tiles), or n-tiles 0..3 / 4..6 of the 16-channel
-// output layer.
-constexpr int kFW = 4;                      // windows per group
-constexpr int kLdAct = 72;                  // activation row stride (BF16)
-constexpr int kLdW1 = kTaps * kC0 + 8;      // 168
-constexpr int kLdW = kTaps * kC + 8;        // 328
-constexpr int kStateDoubles = 6 * kPos + 12 * (kPos - 1);  // 906
-constexpr size_t kFusedW1 = size_t(kC) * kLdW1 * 2, kFusedW2 = size_t(kC) * kLdW * 2, kFusedW4 = size_t(kCO) * kLdW * 2;
-constexpr size_t kFusedBias = (3 * kC + kCO) * 4 + kFW * 3 * 8;  // biases, then the couple samples (FP64)
-constexpr size_t kFusedAct = size_t(kFW) * kRows * kLdAct * 2;
-constexpr size_t kFusedState = size_t(kFW) * kStateDoubles * 8;
-constexpr size_t kFusedSmem = kFusedState + kFusedW1 + 2 * kFusedW2 + kFusedW4 + kFusedBias + 2 * kFusedAct;
+// One persistent block per SM keeps the four layers' BF16 weights in shared memory and runs two
+// independent pipelines of 256 threads, each walking its own groups of four windows (rods).  A
+// group's activations live in the pipeline's shared-memory store of rows: window i takes rows
+// 53 i .. 53 i + 52, two zero rows and then its 51 node positions, so the two zero rows in
+// front of each window are the right-hand padding of the window before it as well.  A
+// convolution layer is then one GEMM per tile of 128 output rows,
+//   D[m][o] = sum_t sum_c S[m + t][c] W[o][t c],   t = 0..4,
+// where output row m (window m / 53, position m % 53, an output where that is below 51) reads
+// store rows m .. m + 4, i.e. the positions m % 53 - 2 .. m % 53 + 2 of its own window.  The
+// store is K-major with consecutive rows 16 bytes apart inside each block of 8 channels (core
+// matrices of 8 consecutive rows, row-group stride 128 bytes, channel-block stride one whole
+// column block of the store), so the A operand of tap t is the store seen from row t -- its
+// descriptor starts 16 t bytes further on -- and no im2col copy is made.  Two tiles (256 rows)
+// accumulate in FP32 in tensor memory, 64 columns each.  The pipeline's first thread issues the
+// MMAs (tile x tap x 16 input channels) and commits them to the pipeline's mbarrier; after the
+// wait the pipeline's warp w reads lanes 32 (w % 4) .. + 31 of tile w / 4, adds the bias,
+// applies SiLU, rounds to BF16 and writes its row back into the store as the next layer's input
+// (store row m + 2).  The output layer's epilogue leaves the 16 outputs of each node position in
+// shared memory.  The FP64 work -- the features (computed one thread per node position from the
+// state in global memory) and the update of the state in place (one thread per node position;
+// update_node reads only that node and the element starting there) -- runs in separate phases,
+// which the ping-pong schedule below sets against the other pipeline's tensor-core phases: on
+// this part the SM executes 2 FP64 lanes per cycle against 128 FP32 lanes, and the two kinds of
+// work use different units.  Waits are bounded: a wait
+// that runs out latches ERR_TIMEOUT into the system's error word, waits once more for the MMAs
+// in flight, and the pipeline passes the rest of its phases idle; the block frees the tensor
+// memory and ends.
+constexpr int kPipes = 2;                        // independent pipelines per block
+constexpr int kTiles = 2;                        // 128-row tiles per group
+constexpr int kTM = 128;
+constexpr int kWS = kPos + 2;                    // store rows per window (53)
+constexpr int kGW = kTiles * kTM / kWS;          // windows per group (4)
+constexpr int kSR = kTiles * kTM + kTaps - 1;    // store rows (260): the last tile reads 4 rows past it
+constexpr uint32_t kChunk = kSR * 16;            // bytes of one block of 8 channels of a store
+constexpr uint32_t kCoreK = 128;                 // K-direction stride of the weights' core matrices
+constexpr uint32_t kRowW = kTaps * kC * 16;      // row-group stride of W2..W4 (K = 320)
+constexpr uint32_t kRowW1 = kTaps * kC0 * 16;    // row-group stride of W1 (K = 160)
+constexpr size_t kTcS = size_t(kC / 8) * kChunk;
+constexpr size_t kTcW1 = size_t(kC) * kTaps * kC0 * 2;
+constexpr size_t kTcW2 = size_t(kC) * kTaps * kC * 2;
+constexpr size_t kTcW4 = size_t(kCO) * kTaps * kC * 2;
+constexpr size_t kTcBias = size_t(3 * kC + kCO) * 4;
+constexpr size_t kTcOut = size_t(kGW) * kPos * kCO * 4;   // a pipeline's outputs of one group
+constexpr size_t kTcActS = size_t(kPipes) * 2 * kGW * 3 * 8;
+constexpr size_t kTcSmem = kPipes * (kTcS + kTcOut) + kTcW1 + 2 * kTcW2 + kTcW4 + kTcBias + kTcActS;
+constexpr int kPipeThreads = 32 * 4 * kTiles;    // a pipeline's warp w: lane quadrant w % 4 of tile w / 4
+constexpr int kTcThreads = kPipes * kPipeThreads;
+constexpr uint32_t kTmemCols = 64 * kTiles * kPipes;
+constexpr uint32_t kWaitPolls = 1u << 20;        // polls of an mbarrier wait before it gives up
+static_assert(kTcSmem <= 227 * 1024, "the fused kernel's shared memory exceeds a block's");
+static_assert(kTcS % 16 == 0 && kTcW1 % 16 == 0 && kTcW2 % 16 == 0 && kTcW4 % 16 == 0, "16-byte operands");
+static_assert(kTcOut % 16 == 0, "16-byte output rows");
+static_assert((kPipes * (kTcS + kTcOut) + kTcW1 + 2 * kTcW2 + kTcW4 + kTcBias) % 8 == 0, "aligned base-couple samples");
+static_assert(kGW * kWS + 2 <= kSR, "the last window's right-hand padding rows lie inside the store");
+static_assert(kGW * kPos + kGW * 3 <= kPipeThreads, "one thread per node position, the rest for the base couple");
+static_assert((kTmemCols & (kTmemCols - 1)) == 0 && kTmemCols >= 32, "tensor-memory allocation size");
 
-// one convolution layer from in (kFW x [64][kLdAct]) with smem weights Ws [COUT][LDW].
-// WARPS = 8: warp w takes window w / 2 and output rows 32 (w % 2) .. +31 (2 x 7 m16n8 tiles);
-// the 16-channel output layer splits the 7 n-tiles 4 / 3.  WARPS = 16: warp w takes window
-// w / 4 and rows 16 (w % 4) .. +15 (1 x 7 tiles); the output layer splits the n-tiles 2/2/2/1.
-// Every output element sums its K products in the same order whichever warp computes it.
-template <int CIN, int COUT, int LDW, bool OUTPUT, int WARPS>
-__device__ __forceinline__ void fused_conv(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ Ws,
-                                           const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
-                                           float* __restrict__ outf, int warp, int lane) {
-  const int g = lane >> 2, tg = lane & 3;
-  constexpr int PER = WARPS / kFW;          // warps per window
-  const int wi = warp / PER, part = warp % PER;
-  constexpr int K = kTaps * CIN;
-  constexpr int MT = OUTPUT ? 1 : (WARPS == 8 ? 2 : 1);
-  constexpr int NT = OUTPUT ? (WARPS == 8 ? 4 : 2) : 7;
-  const int m0 = OUTPUT ? 0 : part * (16 * MT);
-  int ntile[NT];
-  int ntn = 0;
-#pragma unroll
-  for (int n = 0; n < NT; ++n) {
-    const int tt = OUTPUT ? (WARPS == 8 ? part * 4 + n : part + 4 * n) : n;
-    ntile[n] = tt;
-    if (tt < 7 && (!OUTPUT || WARPS != 8 || n < (part ? 3 : 4))) ntn = n + 1;
-  }
-  const __nv_bfloat16* inw = in + wi * kRows * kLdAct;
-  float acc[MT][NT][4];
-#pragma unroll
-  for (int a = 0; a < MT; ++a)
-#pragma unroll
-    for (int n = 0; n < NT; ++n) acc[a][n][0] = acc[a][n][1] = acc[a][n][2] = acc[a][n][3] = 0.f;
-#pragma unroll 2
-  for (int kb = 0; kb < K / 16; ++kb) {
-    const int t = (kb * 16) / CIN, cb = (kb * 16) % CIN;
-    uint32_t af[MT][4];
-#pragma unroll
-    for (int a = 0; a < MT; ++a) {
-      const __nv_bfloat16* wr0 = Ws + (m0 + a * 16 + g) * LDW + kb * 16 + 2 * tg;
-      const __nv_bfloat16* wr1 = wr0 + 8 * LDW;
-      af[a][0] = *reinterpret_cast<const uint32_t*>(wr0);
-      af[a][1] = *reinterpret_cast<const uint32_t*>(wr1);
-      af[a][2] = *reinterpret_cast<const uint32_t*>(wr0 + 8);
-      af[a][3] = *reinterpret_cast<const uint32_t*>(wr1 + 8);
-    }
-#pragma unroll
-    for (int n = 0; n < NT; ++n) {
-      if (n < ntn) {
-        const int row = ntile[n] * 8 + g + t;
-        const __nv_bfloat16* ir = inw + row * kLdAct + cb + 2 * tg;
-        uint32_t bf[2];
-        bf[0] = *reinterpret_cast<const uint32_t*>(ir);
-        bf[1] = *reinterpret_cast<const uint32_t*>(ir + 8);
-#pragma unroll
-        for (int a = 0; a < MT; ++a) mma_bf16(acc[a][n], af[a], bf);
-      }
-    }
-  }
-#pragma unroll
-  for (int a = 0; a < MT; ++a)
-#pragma unroll
-    for (int n = 0; n < NT; ++n) {
-      if (n >= ntn) continue;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int o = m0 + a * 16 + g + ((q & 2) ? 8 : 0);
-        const int jj = ntile[n] * 8 + 2 * tg + (q & 1);
-        const float vv = acc[a][n][q] + bias[o];
-        if (OUTPUT) {
-          if (jj < kPos) outf[(wi * kPos + jj) * kCO + o] = vv;
-        } else {
-          out[(wi * kRows + jj + 2) * kLdAct + o] = __float2bfloat16_rn(jj < kPos ? silu(vv) : 0.f);
-        }
-      }
-    }
+// byte offset of channel c of store row r
+__device__ __forceinline__ uint32_t store_off(int r, int c) {
+  return static_cast<uint32_t>(c >> 3) * kChunk + static_cast<uint32_t>(r) * 16u + static_cast<uint32_t>(c & 7) * 2u;
 }
 
-template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 1) fused_apply_kernel(double* x, double* v, double* Q, double* w, int64_t N,
-                                                             int64_t E, int nrods, const RodConst* __restrict__ rods,
-                                                             double t, Scales sc, const __nv_bfloat16* __restrict__ wf,
-                                                             const float* __restrict__ master) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* st = reinterpret_cast<double*>(smem_raw);
-  __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(smem_raw + kFusedState);
-  __nv_bfloat16* W2s = reinterpret_cast<__nv_bfloat16*>(smem_raw + kFusedState + kFusedW1);
-  __nv_bfloat16* W3s = reinterpret_cast<__nv_bfloat16*>(smem_raw + kFusedState + kFusedW1 + kFusedW2);
-  __nv_bfloat16* W4s = reinterpret_cast<__nv_bfloat16*>(smem_raw + kFusedState + kFusedW1 + 2 * kFusedW2);
-  float* bias = reinterpret_cast<float*>(smem_raw + kFusedState + kFusedW1 + 2 * kFusedW2 + kFusedW4);
-  double* act_s = reinterpret_cast<double*>(bias + 3 * kC + kCO);
-  __nv_bfloat16* bufA = reinterpret_cast<__nv_bfloat16*>(smem_raw + kFusedState + kFusedW1 + 2 * kFusedW2 + kFusedW4 + kFusedBias);
-  __nv_bfloat16* bufB = bufA + kFW * kRows * kLdAct;
-  float* outf = reinterpret_cast<float*>(bufA);  // the output layer's FP32 result reuses buffer A
+// Debug capture of one call (rod_surrogate_apply_debug): per layer l, window b, position p and
+// channel o, pre[((l R + b) 51 + p) 64 + o] = accumulator + bias, act[same] = the BF16 input of
+// layer l (l = 0: the features), widened.
+struct TcDebug {
+  float* pre;
+  float* act;
+};
+
+__device__ __forceinline__ void tc_debug_put(float* a, int l, int nrods, int b, int p, int o, float val) {
+  a[((static_cast<int64_t>(l) * nrods + b) * kPos + p) * kC + o] = val;
+}
+
+// the 24 input features of node position j of rod b (global state), scaled, as BF16 pairs
+// (channels 24..31 zero); the base-couple samples come from act3[0..2]
+__device__ __forceinline__ void node_features(const WinState& S, const double* act3, const Scales& sc, int b, int j,
+                                              uint32_t pk[kC0 / 2]) {
+#pragma unroll
+  for (int cp = 0; cp < kC0 / 2; ++cp) {
+    float f[2] = {0.f, 0.f};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = 2 * cp + h;
+      if (c >= kFeat) continue;
+      double d;
+      bool ok;
+      if (c < 21) ok = raw_feature(S, nullptr, 1, b, j, c, &d);
+      else {
+        d = act3[c - 21];
+        ok = true;
+      }
+      if (ok) f[h] = f32_rn(d - sc.in_shift[c]) * sc.in_scale[c];
+    }
+    pk[cp] = pack_bf16(__float2bfloat16_rn(f[0]), __float2bfloat16_rn(f[1]));
+  }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) tc_apply_kernel(double* x, double* v, double* Q, double* w,
+                                                                  int64_t N, int64_t E, int nrods,
+                                                                  const RodConst* __restrict__ rods, double t,
+                                                                  Scales sc, const __nv_bfloat16* __restrict__ wf,
+                                                                  const float* __restrict__ master, int* err,
+                                                                  uint32_t wait_polls, TcDebug dbg) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sW1 = smem_raw + kPipes * (kTcS + kTcOut);
+  unsigned char* sW2 = sW1 + kTcW1;
+  unsigned char* sW3 = sW2 + kTcW2;
+  unsigned char* sW4 = sW3 + kTcW2;
+  float* bias = reinterpret_cast<float*>(sW4 + kTcW4);
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t mbar[kPipes];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // weights into shared memory (padded rows), biases
+  // the stores zero (rows that are no node position stay so), the weights in the K-major
+  // core-matrix layout, the biases
+  for (int i = tid; i < static_cast<int>(kPipes * kTcS / 16); i += blockDim.x)
+    reinterpret_cast<uint4*>(smem_raw)[i] = make_uint4(0u, 0u, 0u, 0u);
   {
     const __nv_bfloat16* src[4] = {wf, wf + kW1, wf + kW1 + kW2, wf + kW1 + kW2 + kW3};
-    __nv_bfloat16* dst[4] = {W1s, W2s, W3s, W4s};
+    unsigned char* dst[4] = {sW1, sW2, sW3, sW4};
     const int rows[4] = {kC, kC, kC, kCO}, kk[4] = {kTaps * kC0, kTaps * kC, kTaps * kC, kTaps * kC};
-    const int ld[4] = {kLdW1, kLdW, kLdW, kLdW};
-    for (int l = 0; l < 4; ++l) {
-      const int words = rows[l] * kk[l] / 2;
-      for (int i = tid; i < words; i += blockDim.x) {
-        const int r = (2 * i) / kk[l], c = (2 * i) % kk[l];
-        *reinterpret_cast<uint32_t*>(dst[l] + r * ld[l] + c) = reinterpret_cast<const uint32_t*>(src[l])[i];
+    const uint32_t rs[4] = {kRowW1, kRowW, kRowW, kRowW};
+    for (int l = 0; l < 4; ++l)
+      for (int i = tid; i < rows[l] * kk[l] / 8; i += blockDim.x) {  // chunks of 8 elements of K
+        const int r = (8 * i) / kk[l], k = (8 * i) % kk[l];
+        *reinterpret_cast<uint4*>(dst[l] + tc::kmajor_offset(r, k, kCoreK, rs[l])) =
+            *reinterpret_cast<const uint4*>(src[l] + static_cast<int64_t>(r) * kk[l] + k);
       }
-    }
     for (int i = tid; i < kC; i += blockDim.x) {
       bias[i] = master[kOffB1 + i];
       bias[kC + i] = master[kOffB2 + i];
       bias[2 * kC + i] = master[kOffB3 + i];
     }
     for (int i = tid; i < kCO; i += blockDim.x) bias[3 * kC + i] = master[kOffB4 + i];
-    // buffer B's padding rows (0, 1, 58..63) are never written by the layers: zero once
-    for (int i = tid; i < kFW * kRows * kLdAct / 2; i += blockDim.x) reinterpret_cast<uint32_t*>(bufB)[i] = 0u;
   }
-  const int ngroups = (nrods + kFW - 1) / kFW;
-  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-    const int b0 = grp * kFW;
-    const int nw = min(kFW, nrods - b0);
-    __syncthreads();  // previous group's readers of st / bufA are done
-    // stage the state of the group: per window x[3][51], v[3][51], Q[9][50], w[3][50]
-    for (int i = tid; i < kFW * kStateDoubles; i += blockDim.x) {
-      const int wi = i / kStateDoubles, k = i % kStateDoubles;
-      double val = 0.0;
-      if (wi < nw) {
-        const int64_t n0 = static_cast<int64_t>(b0 + wi) * kPos, e0 = static_cast<int64_t>(b0 + wi) * (kPos - 1);
-        if (k < 3 * kPos) val = x[(k / kPos) * N + n0 + k % kPos];
-        else if (k < 6 * kPos) { const int kk = k - 3 * kPos; val = v[(kk / kPos) * N + n0 + kk % kPos]; }
-        else if (k < 6 * kPos + 9 * (kPos - 1)) { const int kk = k - 6 * kPos; val = Q[(kk / (kPos - 1)) * E + e0 + kk % (kPos - 1)]; }
-        else { const int kk = k - 6 * kPos - 9 * (kPos - 1); val = w[(kk / (kPos - 1)) * E + e0 + kk % (kPos - 1)]; }
+  if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
+  if (tid == 0)
+    for (int p = 0; p < kPipes; ++p) tc::mbar_init(&mbar[p], 1);
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+
+  // From here on each pipeline (kPipeThreads consecutive threads) walks its own groups with its
+  // own store, accumulator columns, mbarrier and named barrier; the two meet again only at the
+  // end, so one pipeline's FP64 work overlaps the other's MMAs and epilogues.
+  const int pipe = tid / kPipeThreads, ptid = tid % kPipeThreads;
+  const uint32_t bar_id = 1u + static_cast<uint32_t>(pipe);
+  unsigned char* sS = smem_raw + pipe * kTcS;
+  float4* outs = reinterpret_cast<float4*>(smem_raw + kPipes * kTcS + pipe * kTcOut);  // [c / 4][node]
+  double* act_s = reinterpret_cast<double*>(bias + 3 * kC + kCO) + pipe * 2 * kGW * 3;  // [group & 1][window][3]
+  uint64_t* mb = &mbar[pipe];
+  const uint32_t tcol = static_cast<uint32_t>(64 * kTiles * pipe);   // the pipeline's first accumulator column
+  uint32_t phase = 0;
+  const int wl = ptid >> 5;
+  const int q = wl & 3, g = wl >> 2;             // lane quadrant (= warp % 4) and tile of this warp's rows
+  const int m = kTM * g + 32 * q + lane;         // the output row of this thread
+  const int mw = m / kWS, mp = m % kWS;          // its window in the group and its node position
+  const bool row_pos = mw < kGW && mp < kPos;    // a node position (of a window slot of the group)
+  const uint32_t tmem = tmem_base;
+  const uint32_t tacc = tmem + (static_cast<uint32_t>(32 * q) << 16) + tcol + 64u * static_cast<uint32_t>(g);
+  WinState S;                                    // the system's state, read in place
+  S.x = x;
+  S.v = v;
+  S.Q = Q;
+  S.w = w;
+  S.N = N;
+  S.E = E;
+
+  // Issue layer l's MMAs (the pipeline's first thread) after every thread's writes to the store
+  // are visible to the tensor cores and every read of the accumulators is done; wait for them.
+  // False when a wait ran out (the error is latched and the MMAs in flight drained).
+  // wait_polls with the top bit set (a test of the timeout path): issue nothing, so that the
+  // wait runs out after the remaining bits' polls.
+  const bool no_issue = (wait_polls & 0x80000000u) != 0u;
+  const uint32_t polls = wait_polls & 0x7FFFFFFFu;
+  auto run_layer = [&](int l) -> bool {
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    tc::bar_sync(bar_id, kPipeThreads);
+    if (ptid == 0 && !no_issue) {
+      tc::fence_after_sync();
+      const uint32_t s0 = tc::smem_addr(sS);
+      const int cin = l == 0 ? kC0 : kC;
+      const uint32_t id = tc::idesc_bf16_f32(kTM, l == 3 ? kCO : kC);
+      const uint32_t w0 = tc::smem_addr(l == 0 ? sW1 : (l == 1 ? sW2 : (l == 2 ? sW3 : sW4)));
+      const uint32_t rw = l == 0 ? kRowW1 : kRowW;
+      for (int gt = 0; gt < kTiles; ++gt) {
+        int s = 0;
+        for (int tp = 0; tp < kTaps; ++tp)
+          for (int h = 0; h < cin / 16; ++h, ++s)
+            tc::mma_bf16(tmem + tcol + 64u * gt,
+                         tc::smem_desc(s0 + static_cast<uint32_t>(kTM * gt + tp) * 16u + 2u * h * kChunk, kChunk, 128u),
+                         tc::smem_desc(w0 + static_cast<uint32_t>((tp * cin + 16 * h) / 8) * kCoreK, kCoreK, rw), id,
+                         s > 0);
+      }
+      tc::commit(mb);
+    }
+    const bool ok = tc::mbar_wait(mb, phase, polls);
+    if (tc::bar_or(bar_id, kPipeThreads, !ok)) {
+      if (ptid == 0) atomicOr(err, ERR_TIMEOUT);
+      tc::mbar_wait(mb, phase, no_issue ? polls : kWaitPolls);  // the MMAs in flight finish first
+      return false;
+    }
+    phase ^= 1u;
+    tc::fence_after_sync();
+    return true;
+  };
+
+  // Ping-pong schedule.  Pipeline p's work is a sequence of phases: F0, T0, U0 F1, T1, U1 F2, ...,
+  // U(n-1), where Fk computes group k's features (FP64, one thread per node position) into the
+  // store, Tk runs its four layers (tensor cores and FP32 epilogues; the outputs go to shared
+  // memory) and Uk updates its node positions (FP64, one thread per node position).  Pipeline 1
+  // runs one phase behind pipeline 0 and the whole block meets at a barrier after every phase,
+  // so each FP64 phase of one pipeline coincides with a tensor-core phase of the other.  Every
+  // thread passes the same number of these barriers (a pipeline with fewer groups, or one whose
+  // wait ran out, passes them idle).
+  const int ngroups = (nrods + kGW - 1) / kGW;
+  const int gstride = gridDim.x * kPipes;
+  auto groups_of = [&](int p) {
+    const int g0 = blockIdx.x * kPipes + p;
+    return g0 < ngroups ? (ngroups - 1 - g0) / gstride + 1 : 0;
+  };
+  auto first_rod = [&](int k) { return (blockIdx.x * kPipes + pipe + k * gstride) * kGW; };
+  // base couple of each window of group k at its start, middle and end, by the threads past
+  // the node positions
+  auto couple_samples = [&](int k) {
+    const int i = ptid - kGW * kPos, b0 = first_rod(k);
+    if (i >= 0 && i < min(kGW, nrods - b0) * 3) {
+      const RodConst& rc = rods[b0 + i / 3];
+      act_s[(k & 1) * kGW * 3 + i] = rc.act_amp * sin(rc.act_omega * (t + 0.5 * (i % 3) * sc.T) + rc.act_phase);
+    }
+  };
+  const int nmine = groups_of(pipe), nmax = groups_of(0);   // pipeline 0 has the most
+  if (nmine > 0) couple_samples(0);
+  tc::bar_sync(bar_id, kPipeThreads);
+  bool alive = true;
+  for (int slot = 0; slot <= 2 * nmax + 1; ++slot) {
+    const int ph = slot - pipe;                  // this pipeline's phase index
+    if (alive && ph >= 0 && ph <= 2 * nmine) {
+      const int k = ph >> 1;                     // the group of a T phase, the group of F in an U F phase
+      const int b0 = first_rod(k);
+      const int nw = min(kGW, nrods - b0);
+      if (ph & 1) {
+        // Tk: three hidden layers (accumulator + bias -> SiLU -> BF16 into the store), output layer
+        for (int l = 0; l < 3 && alive; ++l) {
+          if (!(alive = run_layer(l))) break;
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            uint32_t r[2][16];
+            tc::ld16(tacc + 32u * half, r[0]);
+            tc::ld16(tacc + 32u * half + 16u, r[1]);
+            tc::ld_wait();
+            if (row_pos) {
+              uint32_t pk[16];
+#pragma unroll
+              for (int c = 0; c < 32; c += 2) {
+                const int oc = 32 * half + c;
+                const float p0 = __uint_as_float(r[c >> 4][c & 15]) + bias[l * kC + oc];
+                const float p1 = __uint_as_float(r[c >> 4][(c & 15) + 1]) + bias[l * kC + oc + 1];
+                const __nv_bfloat16 a0 = __float2bfloat16_rn(silu(p0)), a1 = __float2bfloat16_rn(silu(p1));
+                pk[c / 2] = pack_bf16(a0, a1);
+                if (dbg.pre && mw < nw) {
+                  tc_debug_put(dbg.pre, l, nrods, b0 + mw, mp, oc, p0);
+                  tc_debug_put(dbg.pre, l, nrods, b0 + mw, mp, oc + 1, p1);
+                  tc_debug_put(dbg.act, l + 1, nrods, b0 + mw, mp, oc, __bfloat162float(a0));
+                  tc_debug_put(dbg.act, l + 1, nrods, b0 + mw, mp, oc + 1, __bfloat162float(a1));
+                }
+              }
+#pragma unroll
+              for (int cb = 0; cb < 4; ++cb)
+                *reinterpret_cast<uint4*>(sS + store_off(m + 2, 32 * half + 8 * cb)) =
+                    make_uint4(pk[4 * cb], pk[4 * cb + 1], pk[4 * cb + 2], pk[4 * cb + 3]);
+            }
+          }
+        }
+        if (alive) alive = run_layer(3);
+        if (alive) {
+          uint32_t r[16];
+          tc::ld16(tacc, r);
+          tc::ld_wait();
+          if (row_pos && mw < nw) {
+            float o[kCO];
+#pragma unroll
+            for (int c = 0; c < kCO; ++c) o[c] = __uint_as_float(r[c]) + bias[3 * kC + c];
+            const int node = mw * kPos + mp;
+#pragma unroll
+            for (int c4 = 0; c4 < kCO / 4; ++c4)
+              outs[c4 * kGW * kPos + node] = make_float4(o[4 * c4], o[4 * c4 + 1], o[4 * c4 + 2], o[4 * c4 + 3]);
+            if (dbg.pre)
+              for (int c = 0; c < kCO; ++c) tc_debug_put(dbg.pre, 3, nrods, b0 + mw, mp, c, o[c]);
+          }
+        }
       } else {
-        // an absent window: a straight identity-frame rod keeps the features finite
-        if (k >= 6 * kPos && k < 6 * kPos + 9 * (kPos - 1)) {
-          const int a = (k - 6 * kPos) / (kPos - 1);
-          val = (a == 0 || a == 4 || a == 8) ? 1.0 : 0.0;
+        // U(k-1): the FP64 update of the previous group's node positions
+        if (k > 0) {
+          const int bp = first_rod(k - 1);
+          if (ptid < min(kGW, nrods - bp) * kPos) {
+            float o[kCO];
+#pragma unroll
+            for (int c4 = 0; c4 < kCO / 4; ++c4) {
+              const float4 f4 = outs[c4 * kGW * kPos + ptid];
+              o[4 * c4] = f4.x;
+              o[4 * c4 + 1] = f4.y;
+              o[4 * c4 + 2] = f4.z;
+              o[4 * c4 + 3] = f4.w;
+            }
+            const int ub = bp + ptid / kPos, j = ptid % kPos;
+            update_node(S, ub, j, o, sc, rods[ub].clamp != 0, x, v, Q, w, N, E, static_cast<int64_t>(ub) * kPos + j,
+                        static_cast<int64_t>(ub) * (kPos - 1) + j);
+          }
+        }
+        if (k < nmine) {
+          // Fk: the features, one thread per node position (a window slot past the last rod gets
+          // zeros); the threads past them take the next group's base-couple samples
+          if (ptid < kGW * kPos) {
+            const int wi = ptid / kPos, j = ptid % kPos;
+            uint32_t pk[kC0 / 2];
+            if (wi < nw) {
+              node_features(S, act_s + (k & 1) * kGW * 3 + 3 * wi, sc, b0 + wi, j, pk);
+            } else {
+#pragma unroll
+              for (int i = 0; i < kC0 / 2; ++i) pk[i] = 0u;
+            }
+            const int r = wi * kWS + j + 2;
+#pragma unroll
+            for (int cb = 0; cb < kC0 / 8; ++cb)
+              *reinterpret_cast<uint4*>(sS + store_off(r, 8 * cb)) =
+                  make_uint4(pk[4 * cb], pk[4 * cb + 1], pk[4 * cb + 2], pk[4 * cb + 3]);
+            if (dbg.act && wi < nw)
+              for (int c = 0; c < kC0; ++c)
+                tc_debug_put(dbg.act, 0, nrods, b0 + wi, j, c,
+                             __bfloat162float(__ushort_as_bfloat16(static_cast<unsigned short>(pk[c / 2] >> (16 * (c & 1))))));
+          } else if (k + 1 < nmine) {
+            couple_samples(k + 1);
+          }
         }
       }
-      st[i] = val;
     }
-    if (tid < kFW * 3) {
-      // base couple of each window at its start, middle and end
-      const int wi = tid / 3, k = tid % 3;
-      double a = 0.0;
-      if (wi < nw) {
-        const RodConst& rc = rods[b0 + wi];
-        a = rc.act_amp * sin(rc.act_omega * (t + 0.5 * k * sc.T) + rc.act_phase);
-      }
-      act_s[tid] = a;
-    }
-    // padding rows 0, 1 and 53..63 of buffer A are zero
-    for (int i = tid; i < kFW * (kRows - kPos) * (kLdAct / 2); i += blockDim.x) {
-      const int wi = i / ((kRows - kPos) * (kLdAct / 2)), rem = i % ((kRows - kPos) * (kLdAct / 2));
-      const int r = rem / (kLdAct / 2), cw = rem % (kLdAct / 2);
-      const int row = r < 2 ? r : r + kPos;
-      reinterpret_cast<uint32_t*>(bufA + (wi * kRows + row) * kLdAct)[cw] = 0u;
-    }
-    __syncthreads();
-    // features: one thread per (window, node position, pair of columns) of the rows 2..52;
-    // consecutive threads take consecutive node positions of the same column pair, so a warp
-    // follows one branch of raw_feature
-    for (int i = tid; i < kFW * kPos * (kLdAct / 2); i += blockDim.x) {
-      const int cp = i / (kFW * kPos), wj = i % (kFW * kPos);
-      const int wi = wj / kPos, j = wj % kPos;
-      const double* sw = st + wi * kStateDoubles;
-      WinState S;
-      S.x = sw;
-      S.v = sw + 3 * kPos;
-      S.Q = sw + 6 * kPos;
-      S.w = sw + 6 * kPos + 9 * (kPos - 1);
-      S.N = kPos;
-      S.E = kPos - 1;
-      float f[2] = {0.f, 0.f};
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int c = 2 * cp + h;
-        double d;
-        if (c < kFeat && raw_feature(S, act_s + 3 * wi, 1, 0, j, c, &d))
-          f[h] = static_cast<float>(d - sc.in_shift[c]) * sc.in_scale[c];
-      }
-      reinterpret_cast<uint32_t*>(bufA + (wi * kRows + j + 2) * kLdAct)[cp] =
-          pack_bf16(__float2bfloat16_rn(f[0]), __float2bfloat16_rn(f[1]));
-    }
-    __syncthreads();
-    fused_conv<kC0, kC, kLdW1, false, WARPS>(bufA, W1s, bias, bufB, nullptr, warp, lane);
-    __syncthreads();
-    fused_conv<kC, kC, kLdW, false, WARPS>(bufB, W2s, bias + kC, bufA, nullptr, warp, lane);
-    __syncthreads();
-    fused_conv<kC, kC, kLdW, false, WARPS>(bufA, W3s, bias + 2 * kC, bufB, nullptr, warp, lane);
-    __syncthreads();
-    fused_conv<kC, kCO, kLdW, true, WARPS>(bufB, W4s, bias + 3 * kC, nullptr, outf, warp, lane);
-    __syncthreads();
-    // FP64 update of every node position of the group
-    for (int i = tid; i < nw * kPos; i += blockDim.x) {
-      const int wi = i / kPos, j = i % kPos;
-      const double* sw = st + wi * kStateDoubles;
-      WinState S;
-      S.x = sw;
-      S.v = sw + 3 * kPos;
-      S.Q = sw + 6 * kPos;
-      S.w = sw + 6 * kPos + 9 * (kPos - 1);
-      S.N = kPos;
-      S.E = kPos - 1;
-      const int b = b0 + wi;
-      update_node(S, 0, j, outf + (wi * kPos + j) * kCO, sc, rods[b].clamp != 0, x, v, Q, w, N, E,
-                  static_cast<int64_t>(b) * kPos + j, static_cast<int64_t>(b) * (kPos - 1) + j);
-    }
+    tc::bar_sync(kPipes + 1, kTcThreads);       // the phase boundary of the whole block
   }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_free(tmem, kTmemCols);
 }
 
 // base couple A sin(omega t + phi) of every rod at t, t + T/2 and t + T
@@ -861,6 +989,7 @@ struct rod_surrogate {
   // per-batch buffers (grown on demand)
   int cap = 0;
   int last_nwin = 0;  // windows of the last training step (rod_surrogate_debug_buffer)
+  uint32_t wait_polls = 0;  // polls of the fused kernel's mbarrier waits (0: the default)
   __nv_bfloat16 *a0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr;  // input, hidden 1..3
   float *p1 = nullptr, *p2 = nullptr, *p3 = nullptr;                        // pre-activations
   float *outf = nullptr, *tgt = nullptr, *loss = nullptr;
@@ -997,6 +1126,16 @@ WinState win_state(const double* x, const double* v, const double* Q, const doub
 
 namespace {
 
+// After a synchronised call: ROD_ERR_TIMEOUT when a bounded wait of the fused kernel ran out
+// (the system's error word; the step reports the word's other bits).
+rod_status tc_wait_status(const SysView& V, const char* who) {
+  int word = 0;
+  cudaError_t e = cudaMemcpy(&word, V.err, sizeof word, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
+  if (word & ERR_TIMEOUT) return internal_fail(ROD_ERR_TIMEOUT, who, "a bounded wait of the tensor-core kernel ran out");
+  return ROD_OK;
+}
+
 rod_status check_system(rod_surrogate* s, rod_system* sys, SysView* V, const char* who) {
   rod_status rs = system_view(sys, V);
   if (rs != ROD_OK) return rs;
@@ -1006,12 +1145,6 @@ rod_status check_system(rod_surrogate* s, rod_system* sys, SysView* V, const cha
   cudaError_t e;
   if ((e = grow(s, V->R)) || (e = refresh_weights(s, V->stream))) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
   return ROD_OK;
-}
-
-// warps per block of the fused kernel (8 or 16; ROD_SURROGATE_FUSED_WARPS picks one)
-int fused_warps() {
-  const char* e = std::getenv("ROD_SURROGATE_FUSED_WARPS");
-  return (e && std::atoi(e) == 8) ? 8 : 16;
 }
 
 // blocks of the fused kernel: one per SM (its shared memory holds the whole network)
@@ -1024,8 +1157,7 @@ cudaError_t fused_grid(int* grid) {
     if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
   }
   if (!attr) {
-    if ((e = cudaFuncSetAttribute(fused_apply_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem)) ||
-        (e = cudaFuncSetAttribute(fused_apply_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem)))
+    if ((e = cudaFuncSetAttribute(tc_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem)))
       return e;
     attr = true;
   }
@@ -1035,13 +1167,14 @@ cudaError_t fused_grid(int* grid) {
 
 // n_calls network windows on the system's stream (no synchronisation): one fused launch per call
 // (or the unfused kernel sequence when ROD_SURROGATE_UNFUSED is set, for comparison)
-cudaError_t apply_calls(rod_surrogate* s, const SysView& V, int64_t n_calls, int reserve_sms = 0) {
+cudaError_t apply_calls(rod_surrogate* s, const SysView& V, int64_t n_calls, int reserve_sms = 0,
+                        TcDebug dbg = TcDebug{nullptr, nullptr}) {
   const bool unfused = std::getenv("ROD_SURROGATE_UNFUSED") != nullptr;
   const WinState S = win_state(V.x, V.v, V.Q, V.w, V.R);
   int sms = 0;
   cudaError_t e;
   if (!unfused && (e = fused_grid(&sms))) return e;
-  const int groups = (V.R + kFW - 1) / kFW;
+  const int groups = (V.R + kGW - 1) / kGW;
   for (int64_t k = 0; k < n_calls; ++k) {
     if (unfused) {
       actuation_kernel<<<(V.R + 127) / 128, 128, 0, V.stream>>>(V.rods, V.R, *V.t, s->sc.T, s->act);
@@ -1050,10 +1183,11 @@ cudaError_t apply_calls(rod_surrogate* s, const SysView& V, int64_t n_calls, int
       apply_kernel<<<(V.R * kPos + 255) / 256, 256, 0, V.stream>>>(V.x, V.v, V.Q, V.w, V.N, V.E, V.R, s->outf, s->sc,
                                                                    V.rods);
     } else {
-      const int grid = std::max(1, std::min(groups, sms - reserve_sms));
-      auto kern = fused_warps() == 8 ? fused_apply_kernel<8> : fused_apply_kernel<16>;
-      kern<<<grid, fused_warps() * 32, kFusedSmem, V.stream>>>(V.x, V.v, V.Q, V.w, V.N, V.E, V.R, V.rods,
-                                                                              *V.t, s->sc, s->wf, s->master);
+      const int grid = std::max(1, std::min((groups + kPipes - 1) / kPipes, sms - reserve_sms));
+      tc_apply_kernel<<<grid, kTcThreads, kTcSmem, V.stream>>>(V.x, V.v, V.Q, V.w, V.N, V.E, V.R, V.rods, *V.t, s->sc,
+                                                               s->wf, s->master, V.err,
+                                                               s->wait_polls ? s->wait_polls : kWaitPolls, dbg);
+      dbg = TcDebug{nullptr, nullptr};   // capture the first call only
     }
     *V.t += s->window * s->dt;
   }
@@ -1332,7 +1466,38 @@ rod_status rod_surrogate_apply(rod_surrogate* s, rod_system* sys, int64_t n_call
   cudaError_t e = apply_calls(s, V, n_calls);
   if (e == cudaSuccess) e = cudaStreamSynchronize(V.stream);
   if (e != cudaSuccess) return internal_fail(ROD_ERR_CUDA, "rod_surrogate_apply", cudaGetErrorString(e));
+  return tc_wait_status(V, "rod_surrogate_apply");
+}
+
+rod_status rod_surrogate_set_wait_polls(rod_surrogate* s, uint32_t polls) {
+  if (!s) return internal_fail(ROD_ERR_ARG, "rod_surrogate_set_wait_polls: null surrogate", "");
+  s->wait_polls = polls;
   return ROD_OK;
+}
+
+rod_status rod_surrogate_apply_debug(rod_surrogate* s, rod_system* sys, float* pre, float* act, int64_t cap) {
+  if (!s || !sys || !pre || !act) return internal_fail(ROD_ERR_ARG, "rod_surrogate_apply_debug: null argument", "");
+  if (std::getenv("ROD_SURROGATE_UNFUSED"))
+    return internal_fail(ROD_ERR_STATE, "rod_surrogate_apply_debug", "the capture needs the fused kernel");
+  SysView V;
+  rod_status rs = check_system(s, sys, &V, "rod_surrogate_apply_debug");
+  if (rs != ROD_OK) return rs;
+  const int64_t n = int64_t(4) * V.R * kPos * kC;
+  if (cap < n) return internal_fail(ROD_ERR_ARG, "rod_surrogate_apply_debug", "buffers smaller than 4 x R x 51 x 64");
+  // scratch of this debug call only
+  float *dpre = nullptr, *dact = nullptr;
+  cudaError_t e = cudaMalloc(&dpre, n * sizeof(float));
+  if (!e) e = cudaMalloc(&dact, n * sizeof(float));
+  if (!e) e = cudaMemsetAsync(dpre, 0, n * sizeof(float), V.stream);
+  if (!e) e = cudaMemsetAsync(dact, 0, n * sizeof(float), V.stream);
+  if (!e) e = apply_calls(s, V, 1, 0, TcDebug{dpre, dact});
+  if (!e) e = cudaStreamSynchronize(V.stream);
+  if (!e) e = cudaMemcpy(pre, dpre, n * sizeof(float), cudaMemcpyDeviceToHost);
+  if (!e) e = cudaMemcpy(act, dact, n * sizeof(float), cudaMemcpyDeviceToHost);
+  if (dpre) cudaFree(dpre);
+  if (dact) cudaFree(dact);
+  if (e != cudaSuccess) return internal_fail(ROD_ERR_CUDA, "rod_surrogate_apply_debug", cudaGetErrorString(e));
+  return tc_wait_status(V, "rod_surrogate_apply_debug");
 }
 
 rod_status rod_surrogate_rollout(rod_surrogate* s, rod_system* sys, rod_system* shadow, const int32_t* sample_rods,

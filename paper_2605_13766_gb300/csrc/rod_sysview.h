@@ -19,6 +19,7 @@ struct SysView {
   int n_packs;             // thread blocks of one step launch
   cudaStream_t stream;
   double* t;               // the system's simulated time (host)
+  int* err;                // the system's device error word
 };
 
 rod_status system_view(rod_system* sys, SysView* out);

@@ -11,7 +11,8 @@ own inputs to that layer, so no rounding decision taken earlier can blur the com
     (2^-22: two units of FP32 rounding per addition, for accumulators that truncate);
   * activations and gradients stored in BF16: the stored value lies in the BF16 rounding of the
     interval that the FP32 value can occupy (the bound above, widened by the error of the FP32
-    SiLU or SiLU' evaluation: (4 + 1.2 |x|) 2^-23 relative for the exponential intrinsic);
+    SiLU or SiLU' evaluation: (5 + 1.2 |x|) 2^-23 relative for the exponential and quotient
+    intrinsics, and 1.5e-36 absolute below x = -87, where the fast quotient returns -0);
   * loss gradient: 2 (out - tgt) / count with four FP32 roundings, rounded to BF16;
   * loss: (n + 4) 2^-23 of the sum of the n squared residuals (FP32 sums in any order);
   * weight and bias gradients: (M + 4) 2^-22 (sum |g a|) for M = windows x 64 positions of a chunk.
@@ -22,6 +23,7 @@ A dropped, repeated or misplaced tap or channel moves an entry by about one term
 import numpy as np
 import pytest
 
+import rodgen
 from oracle import surrogate_ref as R
 from test_gpu_surrogate import _act, _cuda, _setup_network, oracle_window  # noqa: F401
 
@@ -43,6 +45,19 @@ def _lib():
 def _cp(buf):
     """[windows, rows, channels] with rows = positions + 2 -> [windows, channels, 51]."""
     return np.asarray(buf, dtype=np.float64)[:, 2:2 + R.POS, :].transpose(0, 2, 1)
+
+
+def _silu_rel(pre):
+    """Relative error bound of the FP32 SiLU x / (1 + exp(-x)) with the fast exponential
+    (2 + 1.173 |x| units in the last place) and the fast quotient (2 units)."""
+    return (5.0 + 1.2 * np.abs(pre)) * U23
+
+
+def _silu_abs(pre):
+    """Absolute slack of the same SiLU: below x = -87.3 the denominator passes 2^126 (or the
+    exponential overflows FP32) and the fast quotient returns -0; the true value, |x| e^x, is
+    below 1.5e-36 there."""
+    return np.where(pre < -87.0, 1.5e-36, 1e-38)
 
 
 def _bf16_bracket(got, lo, hi):
@@ -106,9 +121,9 @@ def test_hidden_layer_pre_activations_and_activations(step, layer):
     _check_pre(pre, inp, Wl, bl, K)
     # activation: BF16 of the FP32 SiLU of the FP32 pre-activation
     s = R.silu(pre)
-    eps = (4.0 + 1.2 * np.abs(pre)) * U23
+    eps = _silu_rel(pre)
     got = _cp(bufs[layer + 1])
-    ok = _bf16_bracket(got, s - eps * np.abs(s) - 1e-38, s + eps * np.abs(s) + 1e-38)
+    ok = _bf16_bracket(got, s - eps * np.abs(s) - _silu_abs(pre), s + eps * np.abs(s) + _silu_abs(pre))
     assert np.all(ok), int((~ok).sum())
     out = bufs[layer + 1]
     assert np.all(out[:, :2] == 0) and np.all(out[:, 2 + R.POS:] == 0)
@@ -179,3 +194,79 @@ def test_weight_and_bias_gradients(step, layer):
     assert np.all(np.abs(gw - dW) <= (M + 4) * U22 * mW + 1e-38), float((np.abs(gw - dW) / np.maximum(mW, 1e-300)).max())
     assert np.all(np.abs(gb - db) <= (M + 4) * U22 * mb + 1e-38)
     assert np.abs(dW).max() > 0
+
+
+# ---- the fused inference kernel (tcgen05 tensor cores): the same checks on its captured arrays
+
+@pytest.fixture(scope="module", params=["oracle_9_rods", "carpet_5x5", "carpet_40x40"])
+def tc_call(oracle_window, request):  # noqa: F811
+    """One window call of the fused kernel, with every layer's arrays captured: on the oracle's
+    windows (9 rods, one full group of nine), on a perturbed 5 x 5 carpet (25 rods: groups of
+    9, 9 and 7, the last with two empty window slots) and on a perturbed 40 x 40 carpet (1600
+    rods: 178 groups, more than one per block of the persistent grid)."""
+    from paper_2605_13766_gb300 import RodSystem
+    p, s0, s1, t0, dt, W = oracle_window
+    T = W * dt
+    act = _act(p, t0, T)
+    sur, params, scales = _setup_network(p, s0, s1, act, T)
+    if request.param != "oracle_9_rods":
+        side = 5 if request.param == "carpet_5x5" else 40
+        p = rodgen.perturbed(rodgen.cilia_carpet(side=side, n=50), seed=side, pos=0.01, vel=0.02, rot=0.02,
+                             omega=1.0)
+        s0 = p.state()
+        act = _act(p, t0, T)
+    s = RodSystem(p)
+    s.set_state(*s0)
+    s.time = t0
+    pre, inp = sur.apply_debug(s)
+    new_state = s.get_state()
+    s.close()
+    layers = R.unpack(params)
+    Wb = [(R.bf16(Wl), bl.astype(np.float32).astype(np.float64)) for Wl, bl in layers]
+    tr = lambda a: np.asarray(a, dtype=np.float64).transpose(0, 2, 1)   # [R, 51, 64] -> [R, 64, 51]
+    return {"pre": [tr(pre[l]) for l in range(4)], "inp": [tr(inp[l]) for l in range(4)], "W": Wb,
+            "scales": scales, "s0": s0, "act": act, "new": new_state, "T": T, "clamp": p.clamp_base}
+
+
+def test_tensor_core_input_features(tc_call):
+    sh, sc, _ = tc_call["scales"]
+    F, M = R.raw_features(*tc_call["s0"], tc_call["act"])
+    delta = 1e-12 * np.abs(F).max(axis=(0, 2), keepdims=True) + 1e-300
+    shv = np.asarray(sh, dtype=np.float64)[None, :, None]
+    sc32 = np.asarray(sc, dtype=np.float64).astype(np.float32)[None, :, None]
+
+    def chain(raw):
+        return R.bf16(((raw - shv).astype(np.float32) * sc32).astype(np.float64))
+
+    lo, hi = np.where(M, chain(F - delta), 0.0), np.where(M, chain(F + delta), 0.0)
+    got = tc_call["inp"][0]
+    assert np.all(got[:, R.N_FEAT:32] == 0.0)
+    g = got[:, :R.N_FEAT]
+    assert np.all((np.minimum(lo, hi) <= g) & (g <= np.maximum(lo, hi)))
+
+
+@pytest.mark.parametrize("layer", [0, 1, 2])
+def test_tensor_core_hidden_layers(tc_call, layer):
+    Wl, bl = tc_call["W"][layer]
+    cin = Wl.shape[2]
+    inp = tc_call["inp"][layer][:, :cin]
+    pre = tc_call["pre"][layer]
+    _check_pre(pre, inp, Wl, bl, R.TAPS * cin)
+    s = R.silu(pre)
+    eps = _silu_rel(pre)
+    got = tc_call["inp"][layer + 1]
+    ok = _bf16_bracket(got, s - eps * np.abs(s) - _silu_abs(pre), s + eps * np.abs(s) + _silu_abs(pre))
+    bad = ~ok
+    assert np.all(ok), (int(bad.sum()), np.percentile(pre[bad], [0, 50, 100]).tolist(), got[bad][:5].tolist(),
+                        s[bad][:5].tolist())
+
+
+def test_tensor_core_output_layer_and_update(tc_call):
+    W4, b4 = tc_call["W"][3]
+    out = tc_call["pre"][3][:, :16]
+    _check_pre(out, tc_call["inp"][3], W4, b4, R.TAPS * 64)
+    # the FP64 update from the kernel's own outputs, as the reference computes it
+    _, _, out_scale = tc_call["scales"]
+    ref = R.apply(tc_call["s0"], out.transpose(0, 2, 1), out_scale, tc_call["T"], tc_call["clamp"])
+    for a, b in zip(tc_call["new"], ref):
+        assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1.0)

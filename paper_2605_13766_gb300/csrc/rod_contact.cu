@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "rod_contact.h"
+#include "rod_cull.h"
 
 namespace rod {
 
@@ -161,23 +162,6 @@ __device__ __noinline__ PairForce pair_force(const ContactArgs& A, int a, int ra
   return out;
 }
 
-// FP32 lower bounds of the distance of segments a and b (midpoints m, half lengths h, half
-// edges e) against touch = r_a + r_b + extra + tol, tol covering the rounding of the FP32
-// inputs and of these expressions: false when the pair is certainly farther apart.
-__device__ __forceinline__ bool may_touch(float4 ga, float4 gb, float4 ea, float4 eb, float touch_base) {
-  const float ddx = ga.x - gb.x, ddy = ga.y - gb.y, ddz = ga.z - gb.z;
-  const float dm2 = ddx * ddx + ddy * ddy + ddz * ddz;
-  const float ma_inf = fmaxf(fabsf(ga.x), fmaxf(fabsf(ga.y), fabsf(ga.z)));
-  const float mb_inf = fmaxf(fabsf(gb.x), fmaxf(fabsf(gb.y), fabsf(gb.z)));
-  const float touch = touch_base + 1e-6f + 4e-6f * (ma_inf + mb_inf + ga.w + gb.w);
-  const float reach = touch + ga.w + gb.w;
-  if (dm2 > reach * reach) return false;
-  // separating axis along m_a - m_b: |dm| - (|e_a . dm| + |e_b . dm|) / |dm| > touch
-  const float pa = fabsf(ea.x * ddx + ea.y * ddy + ea.z * ddz);
-  const float pb = fabsf(eb.x * ddx + eb.y * ddy + eb.z * ddz);
-  return !(dm2 > 0.f && dm2 - (pa + pb) > touch * sqrtf(dm2));
-}
-
 // Calls visit(b, rb) for every segment b of another rod in the 27-cell neighbourhood of slot q
 // (cell-ordered records) that may come within r_a + r_b + extra of the slot's segment, in list
 // order.  The three cells of each (y, z) row are consecutive in the list and scanned as one
@@ -254,20 +238,19 @@ struct ForceSum {
   }
 };
 
-// Contact forces on the two nodes of segment a from its skin list: candidates culled in FP32
-// against the segment proxies of the current positions (written by the step kernel that
-// produced them) and evaluated in FP64; a segment whose list overflowed scans its
-// neighbourhood of the last build with the skin bound (the build's records are stale by less
-// than skin / 2 per node, which the skin covers).
-__device__ __forceinline__ void listed_forces(const ContactArgs& A, int64_t a, ForceSum& f) {
+// The FP32 cull of segment a's skin list against the segment proxies of the current positions
+// (written by the step kernel that produced them): the survivors as a bit mask over the list
+// positions.  A segment whose list overflowed scans its neighbourhood of the last build with the
+// skin bound instead (the build's records are stale by less than skin / 2 per node, which the
+// skin covers), evaluating its pairs into f at once, and returns no survivors.
+__device__ __forceinline__ unsigned cull_listed(const ContactArgs& A, int64_t a, ForceSum& f) {
   const int n = A.nbr_count[a];
+  unsigned hit = 0u;
   if (n <= kNbrCap) {
     if (n > 0) {
       static_assert(kNbrCap <= 32, "the survivors of the cull are kept in a 32-bit mask");
-      // pass 1: FP32 cull of every candidate (groups of four: all indices, then all proxies, so
-      // that four independent loads are in flight); survivors go to a bit mask
+      // groups of four: all indices, then all proxies, so that four independent loads are in flight
       const float4 ga = A.seg_prox[2 * a], ea = A.seg_prox[2 * a + 1];
-      unsigned hit = 0u;
       constexpr int kG = 4;
       for (int k0 = 0; k0 < n; k0 += kG) {
         int bs[kG];
@@ -285,17 +268,11 @@ __device__ __forceinline__ void listed_forces(const ContactArgs& A, int64_t a, F
         for (int t = 0; t < kG; ++t)
           if (bs[t] >= 0 && may_touch(ga, gb[t], ea, eb[t], ea.w + eb[t].w)) hit |= 1u << (k0 + t);
       }
-      // pass 2: FP64 evaluation of the survivors in list order
-      while (hit) {
-        const int k = __ffs(hit) - 1;
-        hit &= hit - 1;
-        const int b = A.nbr[k * A.E + a];
-        f(b, A.seg_rod[b]);
-      }
     }
   } else {
     scan_neighbourhood(A, A.slot_of[a], A.skin, f);
   }
+  return hit;
 }
 
 constexpr int64_t kMaxCells = int64_t(1) << 24;
@@ -628,20 +605,89 @@ __global__ void __launch_bounds__(256) list_active_kernel(ContactArgs A) {
   }
 }
 
-// Skin-list evaluation: the segments with candidates, one per thread of a grid that strides
-// over the active list.  The kernel is bound by the latency of its gathers, so it asks for
-// three resident blocks per SM (80 registers; the spills sit around the out-of-line pair
-// evaluation, which runs for the few survivors of the cull).  (One warp per segment, a lane per
-// candidate, measured 2.4x slower: the FP64 pair evaluations of one segment's few survivors then
-// occupy whole warps with most lanes masked.)
-__global__ void __launch_bounds__(256, 3) list_force_kernel(ContactArgs A) {
+// Skin-list evaluation: the segments with candidates, one per lane of warps that stride over
+// the active list.  Each lane culls its list in FP32 (cull_listed); the warp then packs the
+// survivors of its 32 lanes, in lane and list order, into rounds of 32 and evaluates each round
+// with one pair per lane (pair_force, FP64), passing the results back through shared memory;
+// each lane adds the results of its own survivors in list order, so the sums are those of a
+// lane that evaluated its survivors itself.  (Evaluated by their own lanes, a warp's survivors
+// took as many FP64 passes as its busiest lane had survivors, with the other lanes masked --
+// and a masked FP64 warp instruction costs the unit as much as a full one: 99.6 us per step in
+// the packing's contact-dense window against 61 us packed.  One warp per segment, a lane per
+// candidate, had measured 2.4x slower for the same reason.)  Two blocks per SM (128 registers,
+// 108 bytes of spills around the out-of-line pair evaluation): 49 us; three (80 registers, 640
+// bytes of spills): 61 us.
+constexpr int kLfThreads = 256;
+constexpr int kLfWarps = kLfThreads / 32;
+__global__ void __launch_bounds__(kLfThreads, 2) list_force_kernel(ContactArgs A) {
+  __shared__ int s_pair[kLfWarps][4][32];      // a, rod of a, b, rod of b of each slot of a round
+  __shared__ double s_f[kLfWarps][6][32];      // the slot's contributions to a's two nodes
+  __shared__ int s_hit[kLfWarps][32];
   if (*(volatile int*)A.err != 0) return;
   const int n = *A.n_active;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const int a = A.active[k];
-    ForceSum f(A, a, A.seg_rod[a]);
-    listed_forces(A, a, f);
-    f.store(A.fseg, A.E);
+  const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+  const int warps = gridDim.x * kLfWarps;
+  for (int base = (blockIdx.x * kLfWarps + wb) * 32; base < n; base += warps * 32) {
+    const int k = base + lane;
+    const bool valid = k < n;
+    const int a = valid ? A.active[k] : 0;
+    const int ra = valid ? A.seg_rod[a] : 0;
+    ForceSum f(A, a, ra);
+    const unsigned hit = valid ? cull_listed(A, a, f) : 0u;
+    // slots of this lane's survivors: [off, off + cnt) in the warp's order
+    const int cnt = __popc(hit);
+    int off = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, off, d);
+      if (lane >= d) off += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, off, 31);
+    off -= cnt;
+    for (int r0 = 0; r0 < total; r0 += 32) {
+      // this lane's survivors that fall in the round's slots [r0, r0 + 32)
+      if (off < r0 + 32 && off + cnt > r0) {
+        unsigned h = hit;
+        for (int idx = 0; h; ++idx) {
+          const int kk = __ffs(h) - 1;
+          h &= h - 1;
+          const int slot = off + idx - r0;
+          if (slot >= 0 && slot < 32) {
+            const int b = A.nbr[kk * A.E + a];
+            s_pair[wb][0][slot] = a;
+            s_pair[wb][1][slot] = ra;
+            s_pair[wb][2][slot] = b;
+            s_pair[wb][3][slot] = A.seg_rod[b];
+          }
+        }
+      }
+      __syncwarp();
+      if (r0 + lane < total) {
+        const PairForce pf = pair_force(A, s_pair[wb][0][lane], s_pair[wb][1][lane], s_pair[wb][2][lane],
+                                        s_pair[wb][3][lane]);
+        s_hit[wb][lane] = pf.hit ? 1 : 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          s_f[wb][c][lane] = pf.fa[c];
+          s_f[wb][3 + c][lane] = pf.fb[c];
+        }
+      }
+      __syncwarp();
+      if (off < r0 + 32 && off + cnt > r0) {
+        for (int idx = 0; idx < cnt; ++idx) {
+          const int slot = off + idx - r0;
+          if (slot >= 0 && slot < 32 && s_hit[wb][slot]) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              f.fa[c] += s_f[wb][c][slot];
+              f.fb[c] += s_f[wb][3 + c][slot];
+            }
+          }
+        }
+      }
+      __syncwarp();
+    }
+    if (valid) f.store(A.fseg, A.E);
   }
 }
 
@@ -1098,7 +1144,7 @@ cudaError_t contact_list_force(ContactState& cs, const double* x, const double* 
                                int64_t E, int* err, cudaStream_t st, const LaunchHook& hook) {
   const ContactArgs A = make_args(cs, x, v, rods, N, E, err, &cs.ctl->gate);
   hook.before(K_CONTACT_LIST_FORCE, st);
-  list_force_kernel<<<3 * std::max(cs.sm_count, 1), 256, 0, st>>>(A);
+  list_force_kernel<<<2 * std::max(cs.sm_count, 1), kLfThreads, 0, st>>>(A);
   hook.after(K_CONTACT_LIST_FORCE, st);
   return cudaGetLastError();
 }

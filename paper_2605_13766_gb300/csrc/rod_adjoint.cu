@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(AdjointParams A, LaunchSha
       const double wb = held ? 0.0 : a.WB[c * m.CE + i];
       const double alpha_b = dt * wb;
       const double jinv = P.inv_rl[pk.elem0 + i] * rc->inv_rhoI[c];
-      const double taub = m.EDIL[i] * jinv * alpha_b;
+      const double taub = m.EDIL[i] * rc->inv_rhoI[c] * alpha_b;   // EDIL = e / rl
       ebar += jinv * tau[c] * alpha_b;
       a.TAUB[c * m.CE + i] = taub;
       a.WB[c * m.CE + i] = wb;                       // now: adjoint of w (through w' = w + dt alpha)

@@ -185,7 +185,7 @@ struct rod_system {
   // state
   DevBuf<double> x, v, Q, w;
   // constants
-  DevBuf<double> rest_len, inv_rl, inv_2D, Dhat, inv_m;
+  DevBuf<double> rest_len, inv_rl, inv_rl2, inv_2D, Dhat, inv_m;
   DevBuf<double> rest_kappa, rest_sigma, elem_couple;
   DevBuf<double> magnet, arc0;  // magnetisation [3E], rest arc length of each element's first node [E]
   double field_b0[3] = {0, 0, 0}, field_bc[3] = {0, 0, 0}, field_bs[3] = {0, 0, 0}, field_omega = 0.0;
@@ -421,6 +421,7 @@ StepParams make_params(rod_system* s) {
   P.inv_rl = s->inv_rl.p;
   P.inv_2D = s->inv_2D.p;
   P.Dhat = s->Dhat.p;
+  P.inv_rl2 = s->inv_rl2.p;
   P.inv_m = s->inv_m.p;
   P.rest_kappa = s->rest_kappa.p;
   P.rest_sigma = s->rest_sigma.p;
@@ -768,6 +769,7 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
     s->has_damp_lin = s->has_damp_lin || rc.damp_lin != 0.0;
     rc.rhoI_12 = rc.rhoI[1] - rc.rhoI[2];
     rc.B_21 = rc.B[2] - rc.B[1];
+    rc.B_21h = 0.5 * rc.B_21;
     rc.radius = rad;
     rc.radius_f = static_cast<float>(rad);
     rc.node0 = static_cast<int32_t>(n0);
@@ -818,11 +820,14 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
 
   // per-item constants
   s->rest_len_h.assign(d->rest_len, d->rest_len + E);
-  std::vector<double> inv_rl(E), inv_2D(std::max<int64_t>(V, 1)), Dh(std::max<int64_t>(V, 1)), inv_m(N);
+  std::vector<double> inv_rl(E), inv_rl2(E), inv_2D(std::max<int64_t>(V, 1)), Dh(std::max<int64_t>(V, 1)), inv_m(N);
   for (int r = 0; r < R; ++r) {
     const RodConst& rc = s->rods_h[r];
     const double rhoA = d->density[r] * kPi * d->radius[r] * d->radius[r];
-    for (int i = 0; i < rc.n; ++i) inv_rl[rc.elem0 + i] = 1.0 / d->rest_len[rc.elem0 + i];
+    for (int i = 0; i < rc.n; ++i) {
+      inv_rl[rc.elem0 + i] = 1.0 / d->rest_len[rc.elem0 + i];
+      inv_rl2[rc.elem0 + i] = inv_rl[rc.elem0 + i] * inv_rl[rc.elem0 + i];
+    }
     for (int k = 0; k < rc.n - 1; ++k) {
       const double a = d->rest_len[rc.elem0 + k], b = d->rest_len[rc.elem0 + k + 1];
       inv_2D[rc.elem0 - r + k] = 1.0 / (a + b);
@@ -843,6 +848,7 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
   cudaError_t ce = cudaSuccess;
   if ((ce = s->x.alloc(3 * N)) || (ce = s->v.alloc(3 * N)) || (ce = s->Q.alloc(9 * E)) || (ce = s->w.alloc(3 * E)) ||
       (ce = up(s->rest_len, d->rest_len, E)) || (ce = up(s->inv_rl, inv_rl.data(), E)) ||
+      (ce = up(s->inv_rl2, inv_rl2.data(), E)) ||
       (ce = up(s->inv_2D, inv_2D.data(), inv_2D.size())) || (ce = up(s->Dhat, Dh.data(), Dh.size())) ||
       (ce = up(s->inv_m, inv_m.data(), N)) || (ce = up(s->rods, s->rods_h.data(), R)) ||
       (ce = s->clamp_x.alloc(3 * R)) || (ce = s->clamp_Q.alloc(9 * R)) || (ce = s->err.alloc(1)))
@@ -894,6 +900,7 @@ rod_status rod_system_destroy(rod_system* s) {
   s->inv_rl.release();
   s->inv_2D.release();
   s->Dhat.release();
+  s->inv_rl2.release();
   s->inv_m.release();
   s->rest_kappa.release();
   s->rest_sigma.release();

@@ -42,6 +42,7 @@ struct RodConst {
   // folds the products that these equalities make redundant, with
   double rhoI_12;       // rhoI[1] - rhoI[2]: (rho I w) x w = rhoI_12 (w1 w2, -w0 w2, 0)
   double B_21;          // B[2] - B[1]: kappa x (B kappa) = B_21 (k1 k2, -k0 k2, 0)
+  double B_21h;         // B_21 / 2 (the factor D / (2 D) of the Voronoi couple, exactly 1/2)
 };
 
 constexpr int kMaxWalls = 8;
@@ -100,6 +101,7 @@ struct StepParams {
   const double* inv_rl;       // [E]  1/rl
   const double* inv_2D;       // [V]  1/(rl_k + rl_{k+1}) = 1/(2 D_k)
   const double* Dhat;         // [V]  D_k
+  const double* inv_rl2;      // [E]  1/rl^2
   const double* inv_m;        // [N]  1/lumped mass
   const double* rest_kappa;   // [3V] or null
   const double* rest_sigma;   // [3E] or null

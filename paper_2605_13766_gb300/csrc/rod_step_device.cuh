@@ -57,14 +57,16 @@ __device__ __forceinline__ void rot_coeffs_full(double th2, double& a, double& b
   }
 }
 
-// Same coefficients with the series cut to the warp's largest th^2: below 2^-20 three terms
-// (dropped terms < 2e-22), below 2^-10 four terms (< 3e-18), otherwise the full series.  The
-// choice is uniform across the warp, so lanes never diverge on it.
+// Same coefficients with the series cut to the warp's largest th^2.  a multiplies K = [p]x and
+// b multiplies p p^T, of sizes th and th^2, so a term dropped from a costs R at most its size
+// times th: below th^2 = 2^-20 two terms (R off by < th^5 / 120 < 2^-56), below 2^-10 four terms
+// (< th^9 / 362880 < 2^-63), otherwise the full series.  The choice is uniform across the warp,
+// so lanes never diverge on it.
 __device__ __forceinline__ void rot_coeffs(double th2, double& a, double& b) {
   const unsigned mx = __reduce_max_sync(__activemask(), hi_word(th2));
   if (mx < kHi2m20) {
-    a = fma(fma(th2, 1.0 / 120.0, -1.0 / 6.0), th2, 1.0);
-    b = fma(fma(th2, 1.0 / 720.0, -1.0 / 24.0), th2, 0.5);
+    a = fma(th2, -1.0 / 6.0, 1.0);
+    b = fma(th2, -1.0 / 24.0, 0.5);
   } else if (mx < kHi2m10) {
     a = fma(fma(fma(th2, -1.0 / 5040.0, 1.0 / 120.0), th2, -1.0 / 6.0), th2, 1.0);
     b = fma(fma(fma(th2, -1.0 / 40320.0, 1.0 / 720.0), th2, -1.0 / 24.0), th2, 0.5);
@@ -145,7 +147,7 @@ __device__ __forceinline__ double theta_over_sin(double s4, const double* qa, co
 
 struct Smem {
   double *X, *VN, *QQ, *WW;     // state
-  double *NF, *TA, *ELL, *EDIL; // element work
+  double *NF, *TA, *ELL, *EDIL; // element work (EDIL: dilatation over rest length, e / rl)
   double *PP, *TT;              // Voronoi work
   double* ACT;                  // per-rod actuation value (1/rl and 1/m are read through L1)
   double* BF;                   // [4] magnetic field b(t) of the step and its force time t
@@ -295,15 +297,14 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
     const double ll = fma(l[0], l[0], fma(l[1], l[1], l[2] * l[2]));
     const double rs = rsqrt_nr(ll);         // 1 / ell
     const double ell = ll * rs;
-    const double irl = __ldg(P.inv_rl + ge);
     const double rl = __ldg(P.rest_len + ge);
-    const double e = ell * irl;             // dilatation
     const double ie = rl * rs;              // 1 / e
     double Ql[3], sg[3], n[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) Ql[a] = fma(q[3 * a], l[0], fma(q[3 * a + 1], l[1], q[3 * a + 2] * l[2]));
     // n / e = S sigma / e  (the 1/e of the internal force, folded once)
     if (P.rest_sigma) {
+      const double irl = __ldg(P.inv_rl + ge);
       sg[0] = Ql[0] * irl;
       sg[1] = Ql[1] * irl;
       sg[2] = fma(Ql[2], irl, -1.0);
@@ -317,7 +318,7 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
       const double s01 = __ldg(&rc->S[0]) * rs;
       n[0] = s01 * Ql[0];
       n[1] = s01 * Ql[1];
-      n[2] = fma(s2 * rs, Ql[2], -s2 * ie);
+      n[2] = s2 * fma(rs, Ql[2], -ie);
     }
     // lab internal force N = Q^T n / e
 #pragma unroll
@@ -368,7 +369,7 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
 #pragma unroll
     for (int c = 0; c < 3; ++c) m.TA[c * m.CE + i] = tc[c];
     m.ELL[i] = ell;
-    m.EDIL[i] = e;
+    m.EDIL[i] = ell * __ldg(P.inv_rl2 + ge);   // e / rl, the factor of the angular acceleration
   }
 }
 
@@ -409,12 +410,12 @@ __device__ __forceinline__ void stage_voronoi(const StepParams& P, const Pack& p
     const double s4 = fma(u0, u0, fma(u1, u1, u2 * u2));  // |u|^2 = 4 sin^2(theta)
     const double f = theta_over_sin(s4, qa, qb);
     const double i2D = __ldg(P.inv_2D + gv);
-    const double kf = -f * i2D;             // kappa = -(theta/s) w / D = -f u / (2D)
     const double eps = (m.ELL[i] + m.ELL[i + 1]) * i2D;
     const double ieps = rcp_nr(eps);
     const double ie3 = ieps * ieps * ieps;
-    const double tD = __ldg(P.Dhat + gv) * ie3;
     if (P.rest_kappa) {
+      const double kf = -f * i2D;           // kappa = -(theta/s) w / D = -f u / (2D)
+      const double tD = __ldg(P.Dhat + gv) * ie3;
       const double kap[3] = {kf * u0, kf * u1, kf * u2};
       double mk[3];
 #pragma unroll
@@ -426,14 +427,15 @@ __device__ __forceinline__ void stage_voronoi(const StepParams& P, const Pack& p
       m.TT[m.CV + k] = fma(kap[2], mk[0], -kap[0] * mk[2]) * tD;
       m.TT[2 * m.CV + k] = fma(kap[0], mk[1], -kap[1] * mk[0]) * tD;
     } else {
-      // m = B kappa = kf B u; with B = (b, b, b3) (circular section) kappa x m = kf^2 (b3 - b)
-      // (u1 u2, -u0 u2, 0)
-      const double sk = kf * ie3;
-      const double sb = sk * __ldg(&rc->B[0]);
+      // m = B kappa = kf B u with kf = -f / (2D); with B = (b, b, b3) (circular section) kappa x m
+      // = kf^2 (b3 - b) (u1 u2, -u0 u2, 0), and as D / (2D) = 1/2 exactly, the couple's factor
+      // kf^2 D / eps^3 = f g / 2 with g = f / (2D eps^3)
+      const double g = (f * ie3) * i2D;
+      const double sb = -g * __ldg(&rc->B[0]);
       m.PP[k] = sb * u0;
       m.PP[m.CV + k] = sb * u1;
-      m.PP[2 * m.CV + k] = (sk * __ldg(&rc->B[2])) * u2;
-      const double ct = ((kf * kf) * tD) * __ldg(&rc->B_21);
+      m.PP[2 * m.CV + k] = (-g * __ldg(&rc->B[2])) * u2;
+      const double ct = (f * g) * __ldg(&rc->B_21h);
       m.TT[k] = ct * (u1 * u2);
       m.TT[m.CV + k] = -ct * (u0 * u2);
       m.TT[2 * m.CV + k] = 0.0;
@@ -474,12 +476,12 @@ __device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& 
     }
     const bool held = (li == 0) && rc->clamp;
     if (MODE == MODE_RHS) {
-      const double ke = m.EDIL[i] * __ldg(P.inv_rl + ge);
+      const double ke = m.EDIL[i];
 #pragma unroll
       for (int c = 0; c < 3; ++c) acc_w[c * P.E + ge] = held ? 0.0 : ke * __ldg(&rc->inv_rhoI[c]) * tau[c];
     } else {
-      // w += dt e J^{-1} tau,  J^{-1} = 1/(rho I rl)  (inv_rhoI[0] = inv_rhoI[1])
-      const double ke = (dt * m.EDIL[i]) * __ldg(P.inv_rl + ge);
+      // w += dt e J^{-1} tau,  J^{-1} = 1/(rho I rl)  (inv_rhoI[0] = inv_rhoI[1]; EDIL = e / rl)
+      const double ke = dt * m.EDIL[i];
       const double k01 = ke * __ldg(&rc->inv_rhoI[0]), k2 = ke * __ldg(&rc->inv_rhoI[2]);
       m.WW[i] = held ? 0.0 : fma(k01, tau[0], m.WW[i]);
       m.WW[m.CE + i] = held ? 0.0 : fma(k01, tau[1], m.WW[m.CE + i]);

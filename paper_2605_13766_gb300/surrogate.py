@@ -32,6 +32,11 @@ DEFAULT_SAMPLE = 16              # rods followed by the shadow systems
 # however many lanes are active, so a single rod per block is no faster), and half the SMs
 # that one rod per block would take from the network
 SHADOW_SHAPE = (128, 128)
+# shadow systems of a locally checked rollout: one check (500 plain steps of the sampled rods,
+# ~5 ms, a latency-bound step) lasts about three segments of the network, so three checks in
+# flight keep the network busy (64 x 64 carpet, 200 calls: two shadows 52 ms, three 38 ms, four
+# 42 ms -- the fourth's SMs cost the network a fifth round of its groups)
+LOCAL_SHADOWS = 3
 
 
 def couple_samples(problem, t: float, T: float) -> np.ndarray:
@@ -390,7 +395,7 @@ class CheckedRollout:
     problem's state (the actuation phase)."""
 
     def __init__(self, sur: Surrogate, problem, n_sample: int = DEFAULT_SAMPLE, seed: int = 0,
-                 shadow_shape=SHADOW_SHAPE, mode: str = "global", n_shadows: int = 2, t0: float = 0.0):
+                 shadow_shape=SHADOW_SHAPE, mode: str = "global", n_shadows: int = LOCAL_SHADOWS, t0: float = 0.0):
         if mode not in ("global", "local"):
             raise ValueError("mode is 'global' or 'local'")
         R = len(problem.n_elem)

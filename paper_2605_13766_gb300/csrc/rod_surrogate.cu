@@ -241,7 +241,8 @@ struct WinState {          // a batch of rods of 50 elements in the system layou
 };
 
 struct Scales {
-  double in_shift[kFeat];  // feature = float(raw - shift) * scale (0 where a feature is undefined)
+  double in_shift[kFeat];  // raw feature shift (FP64: the raw features of raw_features_kernel)
+  float in_shift_f[kFeat]; // the shift rounded to FP32: network input = (raw - shift) * scale in FP32
   float in_scale[kFeat];
   double out[kOut];        // state change = prior + out * network output
   double T;                // window length in time (window steps x dt)
@@ -332,20 +333,83 @@ __device__ bool raw_feature(const WinState& S, const double* __restrict__ act, i
   return true;
 }
 
-// features[b][row][c] (BF16), row = position + 2, channels 24..31 and padding rows zero
+// The 24 input features of node position j of rod b (raw_feature's channels), shifted, scaled
+// and rounded to BF16 pairs (channels 24..31 zero), evaluated in FP32 from the FP64 state: the
+// network sees 8 bits of each after the shift and scale, against which the FP32 evaluation
+// errs by about 2^-20 of the raw value.  The element's edge x_{j+1} - x_j is differenced in
+// FP64 first: it carries the stretch strain, ~1e-4 of the edge, which FP32 positions of size
+// ~1 would not resolve.  FP64 -> FP32 conversions on the integer pipe (rod_fp.h).  Training
+// (features_kernel) and inference (tc_apply_kernel) both use it.
+__device__ __forceinline__ void scaled_features(const WinState& S, const double* act3, const Scales& sc, int b, int j,
+                                                uint32_t pk[kC0 / 2]) {
+  const int64_t node = static_cast<int64_t>(b) * kPos + j, node0 = static_cast<int64_t>(b) * kPos;
+  const int64_t el = static_cast<int64_t>(b) * (kPos - 1) + j;
+  const bool has_el = j < kPos - 1, has_vor = has_el && j >= 1;
+  float f[kFeat];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    f[c] = f32_rn(S.x[c * S.N + node]) - f32_rn(S.x[c * S.N + node0]);
+    f[3 + c] = f32_rn(S.v[c * S.N + node]);
+    f[21 + c] = f32_rn(act3[c]);
+  }
+#pragma unroll
+  for (int c = 6; c < 21; ++c) f[c] = 0.f;
+  if (has_el) {
+    float q[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) q[a] = f32_rn(S.Q[a * S.E + el]);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) f[6 + c] = q[c];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) f[12 + c] = f32_rn(S.w[c * S.E + el]);
+    float l[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) l[k] = f32_rn(S.x[k * S.N + node + 1] - S.x[k * S.N + node]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) f[18 + a] = q[3 * a] * l[0] + q[3 * a + 1] * l[1] + q[3 * a + 2] * l[2];
+    if (has_vor) {
+      // half the axial vector of R - R^T, R_ab = d_a(j) . d_b(j - 1)
+      float p[9];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) p[a] = f32_rn(S.Q[a * S.E + el - 1]);
+      auto r = [&](int ia, int ib) { return q[3 * ia] * p[3 * ib] + q[3 * ia + 1] * p[3 * ib + 1] + q[3 * ia + 2] * p[3 * ib + 2]; };
+      f[15] = 0.5f * (r(2, 1) - r(1, 2));
+      f[16] = 0.5f * (r(0, 2) - r(2, 0));
+      f[17] = 0.5f * (r(1, 0) - r(0, 1));
+    }
+  }
+#pragma unroll
+  for (int cp = 0; cp < kC0 / 2; ++cp) {
+    float h[2] = {0.f, 0.f};
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int c = 2 * cp + t;
+      if (c >= kFeat) continue;
+      const bool defined = (c < 6 || c >= 21) || (c < 15 || c >= 18 ? has_el : has_vor);
+      if (defined) h[t] = (f[c] - sc.in_shift_f[c]) * sc.in_scale[c];
+    }
+    pk[cp] = pack_bf16(__float2bfloat16_rn(h[0]), __float2bfloat16_rn(h[1]));
+  }
+}
+
+// features[b][row][c] (BF16), row = position + 2, channels 24..31 and padding rows zero; one
+// thread per row
 __global__ void features_kernel(WinState S, const double* __restrict__ act, int nwin, Scales sc,
                                 __nv_bfloat16* __restrict__ feat) {
-  const int b = blockIdx.x;
-  if (b >= nwin) return;
-  for (int idx = threadIdx.x; idx < kRows * kC0; idx += blockDim.x) {
-    const int row = idx / kC0, c = idx % kC0;
-    const int j = row - 2;
-    float val = 0.f;
-    double d;
-    if (j >= 0 && j < kPos && c < kFeat && raw_feature(S, act, nwin, b, j, c, &d))
-      val = f32_rn(d - sc.in_shift[c]) * sc.in_scale[c];
-    feat[(static_cast<int64_t>(b) * kRows + row) * kC0 + c] = __float2bfloat16_rn(val);
+  const int b = blockIdx.x, row = threadIdx.x;
+  if (b >= nwin || row >= kRows) return;
+  const int j = row - 2;
+  uint32_t pk[kC0 / 2];
+  if (j >= 0 && j < kPos) {
+    const double a3[3] = {act[b], act[nwin + b], act[2 * nwin + b]};
+    scaled_features(S, a3, sc, b, j, pk);
+  } else {
+#pragma unroll
+    for (int i = 0; i < kC0 / 2; ++i) pk[i] = 0u;
   }
+  uint4* dst = reinterpret_cast<uint4*>(feat + (static_cast<int64_t>(b) * kRows + row) * kC0);
+#pragma unroll
+  for (int i = 0; i < kC0 / 8; ++i) dst[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
 }
 
 // Training target channel c at node position j of window b (unscaled):
@@ -627,30 +691,6 @@ __device__ __forceinline__ void tc_debug_put(float* a, int l, int nrods, int b, 
   a[((static_cast<int64_t>(l) * nrods + b) * kPos + p) * kC + o] = val;
 }
 
-// the 24 input features of node position j of rod b (global state), scaled, as BF16 pairs
-// (channels 24..31 zero); the base-couple samples come from act3[0..2]
-__device__ __forceinline__ void node_features(const WinState& S, const double* act3, const Scales& sc, int b, int j,
-                                              uint32_t pk[kC0 / 2]) {
-#pragma unroll
-  for (int cp = 0; cp < kC0 / 2; ++cp) {
-    float f[2] = {0.f, 0.f};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int c = 2 * cp + h;
-      if (c >= kFeat) continue;
-      double d;
-      bool ok;
-      if (c < 21) ok = raw_feature(S, nullptr, 1, b, j, c, &d);
-      else {
-        d = act3[c - 21];
-        ok = true;
-      }
-      if (ok) f[h] = f32_rn(d - sc.in_shift[c]) * sc.in_scale[c];
-    }
-    pk[cp] = pack_bf16(__float2bfloat16_rn(f[0]), __float2bfloat16_rn(f[1]));
-  }
-}
-
 __global__ void __launch_bounds__(kTcThreads, 1) tc_apply_kernel(double* x, double* v, double* Q, double* w,
                                                                   int64_t N, int64_t E, int nrods,
                                                                   const RodConst* __restrict__ rods, double t,
@@ -873,7 +913,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_apply_kernel(double* x, doub
             const int wi = ptid / kPos, j = ptid % kPos;
             uint32_t pk[kC0 / 2];
             if (wi < nw) {
-              node_features(S, act_s + (k & 1) * kGW * 3 + 3 * wi, sc, b0 + wi, j, pk);
+              scaled_features(S, act_s + (k & 1) * kGW * 3 + 3 * wi, sc, b0 + wi, j, pk);
             } else {
 #pragma unroll
               for (int i = 0; i < kC0 / 2; ++i) pk[i] = 0u;
@@ -1178,7 +1218,7 @@ cudaError_t apply_calls(rod_surrogate* s, const SysView& V, int64_t n_calls, int
   for (int64_t k = 0; k < n_calls; ++k) {
     if (unfused) {
       actuation_kernel<<<(V.R + 127) / 128, 128, 0, V.stream>>>(V.rods, V.R, *V.t, s->sc.T, s->act);
-      features_kernel<<<V.R, 256, 0, V.stream>>>(S, s->act, V.R, s->sc, s->a0);
+      features_kernel<<<V.R, kRows, 0, V.stream>>>(S, s->act, V.R, s->sc, s->a0);
       if ((e = forward(s, V.R, false, V.stream))) return e;
       apply_kernel<<<(V.R * kPos + 255) / 256, 256, 0, V.stream>>>(V.x, V.v, V.Q, V.w, V.N, V.E, V.R, s->outf, s->sc,
                                                                    V.rods);
@@ -1250,6 +1290,7 @@ rod_status rod_surrogate_create(int32_t window_steps, double dt, rod_surrogate**
   s->sc.keep_w = 1;
   for (int c = 0; c < kFeat; ++c) {
     s->sc.in_shift[c] = 0.0;
+    s->sc.in_shift_f[c] = 0.0f;
     s->sc.in_scale[c] = 1.0f;
   }
   for (int c = 0; c < kOut; ++c) s->sc.out[c] = 1.0;
@@ -1318,6 +1359,7 @@ rod_status rod_surrogate_set_scales(rod_surrogate* s, const double* in_shift, co
       return internal_fail(ROD_ERR_ARG, "rod_surrogate_set_scales: output scales must be positive", "");
   for (int c = 0; c < kFeat; ++c) {
     s->sc.in_shift[c] = in_shift[c];
+    s->sc.in_shift_f[c] = static_cast<float>(in_shift[c]);
     s->sc.in_scale[c] = static_cast<float>(in_scale[c]);
   }
   for (int c = 0; c < kOut; ++c) s->sc.out[c] = out_scale[c];
@@ -1344,7 +1386,7 @@ rod_status rod_surrogate_train_step(rod_surrogate* s, const double* x0, const do
   if ((e = grow(s, nwin)) || (e = refresh_weights(s, st)))
     return internal_fail(ROD_ERR_CUDA, "rod_surrogate_train_step", cudaGetErrorString(e));
   const WinState A = win_state(x0, v0, Q0, w0, nwin), B = win_state(x1, v1, Q1, w1, nwin);
-  features_kernel<<<nwin, 256, 0, st>>>(A, act, nwin, s->sc, s->a0);
+  features_kernel<<<nwin, kRows, 0, st>>>(A, act, nwin, s->sc, s->a0);
   targets_kernel<<<(static_cast<int64_t>(nwin) * kPos * kCO + 255) / 256, 256, 0, st>>>(A, B, nwin, s->sc, s->tgt);
   if ((e = forward(s, nwin, true, st)) || (e = backward(s, nwin, st)))
     return internal_fail(ROD_ERR_CUDA, "rod_surrogate_train_step", cudaGetErrorString(e));
@@ -1423,7 +1465,7 @@ rod_status rod_surrogate_forward(rod_surrogate* s, const double* x, const double
   cudaError_t e;
   if ((e = grow(s, nwin)) || (e = refresh_weights(s, st)))
     return internal_fail(ROD_ERR_CUDA, "rod_surrogate_forward", cudaGetErrorString(e));
-  features_kernel<<<nwin, 256, 0, st>>>(win_state(x, v, Q, w, nwin), act, nwin, s->sc, s->a0);
+  features_kernel<<<nwin, kRows, 0, st>>>(win_state(x, v, Q, w, nwin), act, nwin, s->sc, s->a0);
   if ((e = forward(s, nwin, false, st))) return internal_fail(ROD_ERR_CUDA, "rod_surrogate_forward", cudaGetErrorString(e));
   e = cudaMemcpyAsync(out, s->outf, static_cast<size_t>(nwin) * kPos * kCO * 4, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return internal_fail(ROD_ERR_CUDA, "rod_surrogate_forward", cudaGetErrorString(e));

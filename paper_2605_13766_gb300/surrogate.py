@@ -27,16 +27,18 @@ ELEMENTS = 50
 DEFAULT_NOISE = 0.05
 DEFAULT_CHECK_BOUND = 8e-4
 DEFAULT_SAMPLE = 16              # rods followed by the shadow systems
-# launch shape of the shadows: two 50-element rods per 128-thread block, one warp per SM
-# sub-partition (an FP64 warp instruction holds a sub-partition's FP64 unit for 64 cycles
-# however many lanes are active, so a single rod per block is no faster), and half the SMs
-# that one rod per block would take from the network
-SHADOW_SHAPE = (128, 128)
-# shadow systems of a locally checked rollout: one check (500 plain steps of the sampled rods,
-# ~5 ms, a latency-bound step) lasts about three segments of the network, so three checks in
-# flight keep the network busy (64 x 64 carpet, 200 calls: two shadows 52 ms, three 38 ms, four
-# 42 ms -- the fourth's SMs cost the network a fifth round of its groups)
-LOCAL_SHADOWS = 3
+# launch shape of the shadows: three 50-element rods per 192-thread block.  A shadow's step is
+# latency-bound, and an FP64 warp instruction holds a sub-partition's FP64 unit for 64 cycles
+# however many lanes are active: two rods per block (one warp per sub-partition) took 4.86 ms
+# for a check of 500 steps, three 5.38 ms (two sub-partitions then hold two warps) on 6 SMs
+# instead of 8, five rods 7.85 ms.
+SHADOW_SHAPE = (192, 192)
+# shadow systems of a locally checked rollout: one check lasts about four segments of the
+# network, so four checks are in flight; with three rods per block they take 24 SMs, and the
+# network keeps 128, on which its 1024 groups of four windows take four rounds as on 152 (64 x 64
+# carpet, 200 calls: 2 rods per block and three shadows 38 ms, 3 rods and four shadows 34 ms,
+# five shadows 40 ms -- their 30 SMs cost the network a fifth round)
+LOCAL_SHADOWS = 4
 
 
 def couple_samples(problem, t: float, T: float) -> np.ndarray:

@@ -367,8 +367,12 @@ int32_t rod_max_elements_per_rod(void);
  *                                   sampled rods at the segment's start (on shadow k mod
  *                                   n_shadows, each holding the n_sample rods) and compares the
  *                                   tips at its end; up to n_shadows (1..8) checks run while the
- *                                   network goes on; a segment above the bound is undone with
- *                                   every later one and redone with the plain step.
+ *                                   network goes on; a segment above its share of the bound
+ *                                   (bound x its calls / check_every) is undone with every later
+ *                                   one and redone with the plain step.  Segments have
+ *                                   check_every calls except toward the end, where each has about
+ *                                   a third of the calls after it (at least one), so that the
+ *                                   last checks end soon after the network does.
  * All calls return ROD_ERR_ARG for bad arguments, ROD_ERR_CUDA for CUDA failures. */
 typedef struct rod_surrogate rod_surrogate;
 typedef struct {

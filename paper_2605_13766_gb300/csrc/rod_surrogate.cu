@@ -888,24 +888,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_apply_kernel(double* x, doub
           }
         }
       } else {
-        // U(k-1): the FP64 update of the previous group's node positions
-        if (k > 0) {
-          const int bp = first_rod(k - 1);
-          if (ptid < min(kGW, nrods - bp) * kPos) {
-            float o[kCO];
-#pragma unroll
-            for (int c4 = 0; c4 < kCO / 4; ++c4) {
-              const float4 f4 = outs[c4 * kGW * kPos + ptid];
-              o[4 * c4] = f4.x;
-              o[4 * c4 + 1] = f4.y;
-              o[4 * c4 + 2] = f4.z;
-              o[4 * c4 + 3] = f4.w;
-            }
-            const int ub = bp + ptid / kPos, j = ptid % kPos;
-            update_node(S, ub, j, o, sc, rods[ub].clamp != 0, x, v, Q, w, N, E, static_cast<int64_t>(ub) * kPos + j,
-                        static_cast<int64_t>(ub) * (kPos - 1) + j);
-          }
-        }
+        // Fk first (its stores go to shared memory, so the update's global loads below may be
+        // issued under its arithmetic), then U(k-1)
         if (k < nmine) {
           // Fk: the features, one thread per node position (a window slot past the last rod gets
           // zeros); the threads past them take the next group's base-couple samples
@@ -929,6 +913,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_apply_kernel(double* x, doub
                              __bfloat162float(__ushort_as_bfloat16(static_cast<unsigned short>(pk[c / 2] >> (16 * (c & 1))))));
           } else if (k + 1 < nmine) {
             couple_samples(k + 1);
+          }
+        }
+        // U(k-1): the FP64 update of the previous group's node positions
+        if (k > 0) {
+          const int bp = first_rod(k - 1);
+          if (ptid < min(kGW, nrods - bp) * kPos) {
+            float o[kCO];
+#pragma unroll
+            for (int c4 = 0; c4 < kCO / 4; ++c4) {
+              const float4 f4 = outs[c4 * kGW * kPos + ptid];
+              o[4 * c4] = f4.x;
+              o[4 * c4 + 1] = f4.y;
+              o[4 * c4 + 2] = f4.z;
+              o[4 * c4 + 3] = f4.w;
+            }
+            const int ub = bp + ptid / kPos, j = ptid % kPos;
+            update_node(S, ub, j, o, sc, rods[ub].clamp != 0, x, v, Q, w, N, E, static_cast<int64_t>(ub) * kPos + j,
+                        static_cast<int64_t>(ub) * (kPos - 1) + j);
           }
         }
       }
@@ -1690,7 +1692,30 @@ rod_status rod_surrogate_rollout_local(rod_surrogate* s, rod_system* sys, rod_sy
   int reserve = 0;
   for (int k = 0; k < n_shadows; ++k) reserve += H[k].n_packs;
   reserve = std::min(reserve, 64);
-  const int64_t n_seg = (n_calls + check_every - 1) / check_every;
+  // Segments: check_every calls each, except toward the end, where a segment has about a third
+  // of the calls that follow it (at least one): a check runs its segment's plain steps after
+  // the network has passed the segment's start, so the last checks end soon after the network
+  // instead of a whole check_every-call check later.  A segment's allowance is its share of
+  // the bound, bound x calls / check_every.
+  std::vector<int64_t> seg_len;
+  {
+    int64_t after = 0;
+    std::vector<int64_t> tail;
+    while (after < n_calls) {
+      int64_t L = std::max<int64_t>(1, std::min<int64_t>(check_every, after / 3));
+      if (L == check_every) break;
+      L = std::min(L, n_calls - after);
+      tail.push_back(L);
+      after += L;
+    }
+    const int64_t head = n_calls - after;   // covered by segments of check_every calls
+    for (int64_t done = 0; done < head; done += check_every)
+      seg_len.push_back(std::min<int64_t>(check_every, head - done));
+    for (auto it = tail.rbegin(); it != tail.rend(); ++it) seg_len.push_back(*it);
+  }
+  std::vector<int64_t> seg_first(seg_len.size() + 1, 0);
+  for (size_t k = 0; k < seg_len.size(); ++k) seg_first[k + 1] = seg_first[k] + seg_len[k];
+  const int64_t n_seg = static_cast<int64_t>(seg_len.size());
   rod_surrogate_stats st{};
   int64_t seg = 0;
   int inflight = 0;
@@ -1712,12 +1737,12 @@ rod_status rod_surrogate_rollout_local(rod_surrogate* s, rod_system* sys, rod_sy
       if ((e = system_clear_error(shadows[qi]))) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
     }
     const int64_t k = q.seg;
-    const int64_t calls = std::min<int64_t>(check_every, n_calls - k * check_every);
+    const int64_t calls = seg_len[k];
     q.seg = -1;
     --inflight;
     st.checks += 1;
     st.last_err = err;
-    if (err <= bound) {
+    if (err <= bound * static_cast<double>(calls) / check_every) {
       st.surrogate_calls += calls;
       st.max_err = std::max(st.max_err, err);
       st.sum_err += err;
@@ -1778,7 +1803,7 @@ rod_status rod_surrogate_rollout_local(rod_surrogate* s, rod_system* sys, rod_sy
       if (rej) continue;
     }
     Slot& q = sl[qi];
-    const int64_t calls = std::min<int64_t>(check_every, n_calls - seg * check_every);
+    const int64_t calls = seg_len[seg];
     q.seg = seg;
     q.t0 = *V.t;
     ++inflight;

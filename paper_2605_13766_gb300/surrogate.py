@@ -33,6 +33,9 @@ DEFAULT_SAMPLE = 16              # rods followed by the shadow systems
 # for a check of 500 steps, three 5.38 ms (two sub-partitions then hold two warps) on 6 SMs
 # instead of 8, five rods 7.85 ms.
 SHADOW_SHAPE = (192, 192)
+# the global check's single shadow runs the whole horizon with sequential plain steps: two rods
+# per block, the shortest step
+GLOBAL_SHADOW_SHAPE = (128, 128)
 # shadow systems of a locally checked rollout: one check lasts about four segments of the
 # network, so four checks are in flight; with three rods per block they take 24 SMs, and the
 # network keeps 128, on which its 1024 groups of four windows take four rounds as on 152 (64 x 64
@@ -397,7 +400,7 @@ class CheckedRollout:
     problem's state (the actuation phase)."""
 
     def __init__(self, sur: Surrogate, problem, n_sample: int = DEFAULT_SAMPLE, seed: int = 0,
-                 shadow_shape=SHADOW_SHAPE, mode: str = "global", n_shadows: int = LOCAL_SHADOWS, t0: float = 0.0):
+                 shadow_shape=None, mode: str = "global", n_shadows: int = LOCAL_SHADOWS, t0: float = 0.0):
         if mode not in ("global", "local"):
             raise ValueError("mode is 'global' or 'local'")
         R = len(problem.n_elem)
@@ -409,12 +412,12 @@ class CheckedRollout:
         self.system.set_state(*problem.state())
         self.system.time = t0
         sub = subset_problem(problem, self.sample)
+        if shadow_shape is None:
+            shadow_shape = GLOBAL_SHADOW_SHAPE if mode == "global" else SHADOW_SHAPE
         self.shadows = []
         for _ in range(1 if mode == "global" else n_shadows):
             sh = RodSystem(sub, use_torch_stream=False)
-            if shadow_shape is not None:
-                # few rods per block: the shadow's step is latency-bound, not throughput-bound
-                sh.set_launch(*shadow_shape)
+            sh.set_launch(*shadow_shape)   # few rods per block: the shadow's step is latency-bound
             sh.set_state(*sub.state())
             sh.time = t0
             self.shadows.append(sh)
@@ -422,7 +425,8 @@ class CheckedRollout:
 
     def run(self, n_calls: int, check_every: int = 10, bound: float = DEFAULT_CHECK_BOUND) -> dict:
         """``bound`` is the target for the accumulated sampled tip error; a local check gets its
-        share per segment, bound x check_every / n_calls."""
+        share per segment, bound x (the segment's calls) / n_calls (segments have check_every
+        calls, fewer toward the end: see rod_surrogate_rollout_local)."""
         if self.mode == "global":
             return self.sur.rollout(self.system, self.shadow, self.sample, n_calls, check_every, bound)
         local = bound * min(1.0, check_every / max(n_calls, 1))

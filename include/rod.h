@@ -420,6 +420,25 @@ rod_status rod_surrogate_raw_features(rod_surrogate* sur, const double* x, const
 rod_status rod_surrogate_raw_targets(rod_surrogate* sur, const double* x0, const double* v0, const double* Q0,
                                      const double* w0, const double* x1, const double* v1, const double* Q1,
                                      const double* w1, int32_t nwin, double* out, void* cuda_stream);
+/* Noise-injected training-window start (the surrogate's training, which perturbs each window's
+ * start so that the network learns to contract perturbations; the paper has no counterpart).
+ *   x0, v0, Q0, w0  device window starts of nwin rods of 50 elements ([3][nwin 51], [3][nwin 51],
+ *                   [9][nwin 50], [3][nwin 50])
+ *   rx, rv, rw, ra  device standard normal draws shaped like x, v, w, w (may be NULL when noise = 0)
+ *   spread          host double [15]: the output scales of the 15 state channels
+ *   noise           >= 0; positions, velocities and angular velocities move by noise x their
+ *                   channel's spread x the draw, the directors d1, d2 turn by the lab-frame
+ *                   angle vector noise x (largest director spread) x ra to first order and are
+ *                   re-orthonormalised (Gram-Schmidt, d3 = d1 x d2); noise = 0 only
+ *                   re-orthonormalises the directors
+ *   held            device int8 [nwin] (NULL: none): a held window keeps node 0's position and
+ *                   element 0's directors, with zero velocity and angular velocity there
+ *   x, v, Q, w      device outputs, shaped like the inputs and not overlapping them
+ * Asynchronous on cuda_stream.  ROD_ERR_ARG for a bad argument or a non-finite spread. */
+rod_status rod_surrogate_perturb(rod_surrogate* sur, const double* x0, const double* v0, const double* Q0,
+                                 const double* w0, int32_t nwin, const double* rx, const double* rv, const double* rw,
+                                 const double* ra, const double* spread, double noise, const int8_t* held, double* x,
+                                 double* v, double* Q, double* w, void* cuda_stream);
 rod_status rod_surrogate_apply(rod_surrogate* sur, rod_system* sys, int64_t n_calls);
 /* Polls of the fused inference kernel's waits for its tensor-core MMAs before it gives up
  * (0: the default, 2^20).  A wait that runs out latches ROD_ERR_TIMEOUT into the system's error

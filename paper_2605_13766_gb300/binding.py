@@ -133,6 +133,8 @@ _SIGNATURES = {
     "rod_surrogate_set_prior": ([_P, C.c_int32], C.c_int),
     "rod_surrogate_raw_features": ([_P, _P, _P, _P, _P, _P, C.c_int32, _P, _P, _P], C.c_int),
     "rod_surrogate_raw_targets": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int32, _P, _P], C.c_int),
+    "rod_surrogate_perturb": ([_P, _P, _P, _P, _P, C.c_int32, _P, _P, _P, _P, _P, C.c_double, _P, _P, _P, _P, _P, _P],
+                              C.c_int),
     "rod_surrogate_apply": ([_P, _P, C.c_int64], C.c_int),
     "rod_surrogate_rollout": ([_P, _P, _P, _P, C.c_int32, C.c_int64, C.c_int32, C.c_double, _P], C.c_int),
     "rod_surrogate_rollout_local": ([_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_int64, C.c_int32, C.c_double, _P],
@@ -630,6 +632,24 @@ class Surrogate:
         out = torch.empty((nwin, self.N_OUTPUTS, self.POSITIONS), dtype=torch.float64, device="cuda")
         s = torch.cuda.current_stream().cuda_stream if stream is None else stream
         _check(self.lib.rod_surrogate_raw_targets(self.handle, *[a.data_ptr() for a in arrs], nwin, out.data_ptr(), s))
+        return out
+
+    def perturb(self, state, draws, spread, noise: float, held=None, stream=None):
+        """Window starts (x, v, Q, w) (CUDA float64) plus noise (rod_surrogate_perturb): draws =
+        standard normal tensors shaped like (x, v, w, w), or None with noise = 0; spread: the 15
+        output scales; held: CUDA int8 (nwin,) or None.  Returns new tensors."""
+        import torch
+        nwin = int(state[0].shape[1]) // self.POSITIONS
+        src = [a.contiguous() for a in state]
+        out = [torch.empty_like(a) for a in src]
+        dr = [None] * 4 if draws is None else [a.contiguous() for a in draws]
+        sp = np.ascontiguousarray(spread, dtype=np.float64)
+        if sp.size != self.N_OUTPUTS:
+            raise ValueError("spread holds the 15 output scales")
+        s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        ptr = lambda a: None if a is None else a.data_ptr()
+        _check(self.lib.rod_surrogate_perturb(self.handle, *[a.data_ptr() for a in src], nwin, *[ptr(a) for a in dr],
+                                              sp.ctypes.data, float(noise), ptr(held), *[a.data_ptr() for a in out], s))
         return out
 
     def forward(self, state, act, stream=None):

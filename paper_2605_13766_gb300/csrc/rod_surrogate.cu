@@ -546,6 +546,64 @@ __device__ __forceinline__ void update_node(const WinState& S, int b, int j, con
   }
 }
 
+// Noise-injected training-window start (the surrogate's training; the paper has no
+// counterpart): out = in plus noise x spread x r for positions (r: rx), velocities (rv) and
+// angular velocities (rw); directors turned to first order by the lab-frame angle vector
+// noise x turn x ra, d_a + ang x d_a for d1 and d2, then Gram-Schmidt and d3 = d1 x d2; the node
+// 0 and element 0 of a held window keep their position and directors with zero rates.  The
+// normal draws r are inputs.  noise = 0 re-orthonormalises the directors alone.
+struct Spread {
+  double s[kOut];
+  double turn;   // largest director scale
+};
+
+__global__ void perturb_kernel(WinState S, int nwin, const double* __restrict__ rx, const double* __restrict__ rv,
+                               const double* __restrict__ rw, const double* __restrict__ ra, Spread sp, double noise,
+                               const int8_t* __restrict__ held, double* __restrict__ x, double* __restrict__ v,
+                               double* __restrict__ Q, double* __restrict__ w) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= static_cast<int64_t>(nwin) * kPos) return;
+  const int b = static_cast<int>(i / kPos), j = static_cast<int>(i % kPos);
+  const bool hold = held && held[b] && j == 0;
+  for (int c = 0; c < 3; ++c) {
+    const int64_t k = c * S.N + i;
+    x[k] = hold ? S.x[k] : fma(noise * sp.s[c], rx[k], S.x[k]);
+    v[k] = hold ? 0.0 : fma(noise * sp.s[3 + c], rv[k], S.v[k]);
+  }
+  if (j >= kPos - 1) return;
+  const int64_t e = static_cast<int64_t>(b) * (kPos - 1) + j;
+  if (hold) {
+    for (int a = 0; a < 9; ++a) Q[a * S.E + e] = S.Q[a * S.E + e];
+    for (int c = 0; c < 3; ++c) w[c * S.E + e] = 0.0;
+    return;
+  }
+  double ang[3], d1[3], d2[3];
+  for (int c = 0; c < 3; ++c) {
+    w[c * S.E + e] = fma(noise * sp.s[12 + c], rw[c * S.E + e], S.w[c * S.E + e]);
+    ang[c] = noise * sp.turn * ra[c * S.E + e];
+    d1[c] = S.Q[c * S.E + e];
+    d2[c] = S.Q[(3 + c) * S.E + e];
+  }
+  const double t1[3] = {ang[1] * d1[2] - ang[2] * d1[1], ang[2] * d1[0] - ang[0] * d1[2], ang[0] * d1[1] - ang[1] * d1[0]};
+  const double t2[3] = {ang[1] * d2[2] - ang[2] * d2[1], ang[2] * d2[0] - ang[0] * d2[2], ang[0] * d2[1] - ang[1] * d2[0]};
+  for (int c = 0; c < 3; ++c) {
+    d1[c] += t1[c];
+    d2[c] += t2[c];
+  }
+  const double n1 = 1.0 / sqrt(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
+  for (int c = 0; c < 3; ++c) d1[c] *= n1;
+  const double p = d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2];
+  for (int c = 0; c < 3; ++c) d2[c] -= p * d1[c];
+  const double n2 = 1.0 / sqrt(d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2]);
+  for (int c = 0; c < 3; ++c) d2[c] *= n2;
+  const double d3[3] = {d1[1] * d2[2] - d1[2] * d2[1], d1[2] * d2[0] - d1[0] * d2[2], d1[0] * d2[1] - d1[1] * d2[0]};
+  for (int c = 0; c < 3; ++c) {
+    Q[c * S.E + e] = d1[c];
+    Q[(3 + c) * S.E + e] = d2[c];
+    Q[(6 + c) * S.E + e] = d3[c];
+  }
+}
+
 // unfused update of every node position from the network output [nrods][51][16] (in place)
 __global__ void apply_kernel(double* x, double* v, double* Q, double* w, int64_t N, int64_t E, int nrods,
                              const float* __restrict__ out, Scales sc, const RodConst* __restrict__ rods) {
@@ -1499,6 +1557,30 @@ rod_status rod_surrogate_raw_targets(rod_surrogate* s, const double* x0, const d
                                                       s->sc.prior_q ? s->sc.T : 0.0, s->sc.keep_v, s->sc.keep_w, out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return internal_fail(ROD_ERR_CUDA, "rod_surrogate_raw_targets", cudaGetErrorString(e));
+  return ROD_OK;
+}
+
+rod_status rod_surrogate_perturb(rod_surrogate* s, const double* x0, const double* v0, const double* Q0,
+                                 const double* w0, int32_t nwin, const double* rx, const double* rv, const double* rw,
+                                 const double* ra, const double* spread, double noise, const int8_t* held, double* x,
+                                 double* v, double* Q, double* w, void* cuda_stream) {
+  const char* who = "rod_surrogate_perturb";
+  if (!s || !x0 || !v0 || !Q0 || !w0 || nwin < 1 || !spread || !x || !v || !Q || !w || !(noise >= 0.0) ||
+      (noise > 0.0 && (!rx || !rv || !rw || !ra)))
+    return internal_fail(ROD_ERR_ARG, who, "bad argument");
+  Spread sp{};
+  sp.turn = 0.0;
+  for (int c = 0; c < kOut; ++c) {
+    if (!std::isfinite(spread[c])) return internal_fail(ROD_ERR_ARG, who, "non-finite spread");
+    sp.s[c] = spread[c];
+    if (c >= 6 && c < 12) sp.turn = std::max(sp.turn, spread[c]);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int64_t n = static_cast<int64_t>(nwin) * kPos;
+  perturb_kernel<<<(n + 255) / 256, 256, 0, st>>>(win_state(x0, v0, Q0, w0, nwin), nwin, rx, rv, rw, ra, sp, noise, held,
+                                                  x, v, Q, w);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return internal_fail(ROD_ERR_CUDA, who, cudaGetErrorString(e));
   return ROD_OK;
 }
 

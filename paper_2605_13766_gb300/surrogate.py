@@ -121,13 +121,10 @@ def generate(problem, n_windows: int, window: int = 50, dt: Optional[float] = No
             for a, b in zip(acc[k], st):
                 a.add_(b, alpha=wt)
 
+    ortho = Surrogate(window, dt)   # its perturbation kernel at zero noise re-orthonormalises
+
     def finish(k):
-        x, v, Q, w = acc.pop(k)
-        d1, d2 = Q[0:3], Q[3:6]
-        d1 = d1 / d1.norm(dim=0, keepdim=True)
-        d2 = d2 - (d1 * d2).sum(dim=0, keepdim=True) * d1
-        d2 = d2 / d2.norm(dim=0, keepdim=True)
-        states[k] = [x, v, torch.cat([d1, d2, torch.cross(d1, d2, dim=0)]), w]
+        states[k] = ortho.perturb(acc.pop(k), None, np.ones(ortho.N_OUTPUTS), 0.0)
 
     # samples m = -h+1 .. 0 are the initial state
     for m in range(-h + 1, 1):
@@ -248,8 +245,7 @@ def train(sur: Surrogate, data: Sequence[Windows], steps: int, lr: float = 1e-3,
         out = np.asarray(sur.scales[2], dtype=np.float64)
         # one noise level per group (positions, velocities, directors, angular velocities):
         # the largest output scale of the group
-        grp = np.concatenate([np.full(len(g), out[list(g)].max()) for g in OUTPUT_GROUPS])
-        spread = torch.tensor(grp, device="cuda")
+        spread = np.concatenate([np.full(len(g), out[list(g)].max()) for g in OUTPUT_GROUPS])
     scratch = {}
     losses = []
     weights = np.array([d.n_windows for d in data], dtype=np.float64)
@@ -271,7 +267,7 @@ def train(sur: Surrogate, data: Sequence[Windows], steps: int, lr: float = 1e-3,
             a = [t.clone() for t in sysk.get_state(device=True)]
             torch.cuda.synchronize()
         if noise > 0:
-            a = _perturb(a, d, spread, noise, gen)
+            a = _perturb(sur, a, d, spread, noise, gen)
         if batch_rods and batch_rods < d.n_rods:
             r0 = int(rng.integers(0, d.n_rods - batch_rods + 1))
             a = _rod_slice(a, r0, batch_rods)
@@ -289,38 +285,23 @@ def train(sur: Surrogate, data: Sequence[Windows], steps: int, lr: float = 1e-3,
     return losses
 
 
-def _perturb(state, d, spread, noise, gen):
-    """Window start plus noise: positions, velocities and angular velocities by noise x the output
-    scale of their channel; directors turned by angles of noise x the largest director scale
-    (first-order turn, then Gram-Schmidt)."""
+def _perturb(sur, state, d, spread, noise, gen):
+    """Window start plus noise (rod_surrogate_perturb): positions, velocities and angular
+    velocities by noise x the output scale of their channel; directors turned by angles of
+    noise x the largest director scale (first-order turn, then Gram-Schmidt); clamped ends kept.
+    The standard normal draws come from ``gen``."""
     import torch
-    x, v, Q, w = [a.clone() for a in state]
+    x, v, Q, w = state
 
     def rnd(a):
         return torch.randn(a.shape, generator=gen, device=a.device, dtype=a.dtype)
 
-    x += noise * spread[0:3, None] * rnd(x)
-    v += noise * spread[3:6, None] * rnd(v)
-    w += noise * spread[12:15, None] * rnd(w)
-    ang = noise * spread[6:12].max() * rnd(w)                  # (3, E) small rotation vectors
-    dd = [Q[3 * a:3 * a + 3] for a in range(3)]
-    # d_a <- d_a + ang x d_a (lab-frame first-order turn), then re-orthonormalise
-    d1 = dd[0] + torch.cross(ang, dd[0], dim=0)
-    d2 = dd[1] + torch.cross(ang, dd[1], dim=0)
-    d1 = d1 / d1.norm(dim=0, keepdim=True)
-    d2 = d2 - (d1 * d2).sum(dim=0, keepdim=True) * d1
-    d2 = d2 / d2.norm(dim=0, keepdim=True)
-    Qn = torch.cat([d1, d2, torch.cross(d1, d2, dim=0)], dim=0)
+    draws = [rnd(x), rnd(v), rnd(w), rnd(w)]
     clamp = getattr(d.problem, "clamp_base", None)
-    held_rods = np.flatnonzero(np.asarray(clamp)) if clamp is not None else np.zeros(0, dtype=np.int64)
-    if held_rods.size:
-        hn = torch.tensor(held_rods * POSITIONS, device=x.device)
-        he = torch.tensor(held_rods * ELEMENTS, device=x.device)
-        x[:, hn] = state[0][:, hn]
-        v[:, hn] = 0.0
-        Qn[:, he] = state[2][:, he]
-        w[:, he] = 0.0
-    return [x, v, Qn, w]
+    held = None
+    if clamp is not None and np.any(np.asarray(clamp)):
+        held = torch.tensor(np.asarray(clamp).astype(np.int8), device=x.device)
+    return sur.perturb(state, draws, spread, noise, held)
 
 
 def train_default(steps: int = 15000, side: int = 32, n_windows: int = 200, seed: int = 101,

@@ -419,3 +419,59 @@ def test_untrained_network_falls_back_to_the_plain_step(mode):
         assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1.0)
     assert stats["max_err"] < 1e-12
     ro.close()
+
+
+def _perturb_reference(state, draws, spread, noise, held):
+    """NumPy statement of the noise-injected window start: additive noise on x, v, w, a
+    first-order lab-frame turn d_a + ang x d_a of d1 and d2 with ang = noise x (largest director
+    spread) x draw, Gram-Schmidt, d3 = d1 x d2, and the held windows' node 0 and element 0 kept."""
+    x, v, Q, w = [np.array(a, dtype=np.float64) for a in state]
+    rx, rv, rw, ra = [np.asarray(a, dtype=np.float64) for a in draws]
+    sp = np.asarray(spread, dtype=np.float64)
+    nwin = x.shape[1] // R.POS
+    xo = x + noise * sp[0:3, None] * rx
+    vo = v + noise * sp[3:6, None] * rv
+    wo = w + noise * sp[12:15, None] * rw
+    ang = noise * sp[6:12].max() * ra
+    d1 = Q[0:3] + np.cross(ang, Q[0:3], axis=0)
+    d2 = Q[3:6] + np.cross(ang, Q[3:6], axis=0)
+    d1 = d1 / np.linalg.norm(d1, axis=0)
+    d2 = d2 - (d1 * d2).sum(axis=0) * d1
+    d2 = d2 / np.linalg.norm(d2, axis=0)
+    Qo = np.concatenate([d1, d2, np.cross(d1, d2, axis=0)])
+    for b in np.flatnonzero(held):
+        n, e = b * R.POS, b * (R.POS - 1)
+        xo[:, n] = x[:, n]
+        vo[:, n] = 0.0
+        Qo[:, e] = Q[:, e]
+        wo[:, e] = 0.0
+    return xo, vo, Qo, wo
+
+
+@pytest.mark.parametrize("noise", [0.05, 0.0])
+def test_training_perturbation_kernel_matches_its_statement(oracle_window, noise):
+    """The training's noise-injected window start (rod_surrogate_perturb) against its NumPy
+    statement on the oracle window's perturbed states, with two of the nine windows held; at
+    zero noise it only re-orthonormalises the directors (given slightly off-orthonormal)."""
+    import torch
+    from paper_2605_13766_gb300 import Surrogate
+    p, s0, s1, t0, dt, W = oracle_window
+    rng = np.random.default_rng(8)
+    x, v, Q, w = [np.array(a, dtype=np.float64) for a in s0]
+    Q = Q + 1e-6 * rng.normal(size=Q.shape)          # off SO(3) by a little
+    draws = [rng.normal(size=x.shape), rng.normal(size=v.shape), rng.normal(size=w.shape), rng.normal(size=w.shape)]
+    spread = np.abs(rng.normal(size=15)) * 1e-3 + 1e-4
+    held = np.zeros(x.shape[1] // R.POS, dtype=np.int8)
+    held[[0, 4]] = 1
+    sur = Surrogate(W, dt)
+    got = sur.perturb(_cuda([x, v, Q, w]), _cuda(draws), spread, noise, torch.tensor(held, device="cuda"))
+    ref = _perturb_reference((x, v, Q, w), draws, spread, noise, held)
+    for g, r in zip(got, ref):
+        g = g.cpu().numpy()
+        assert np.abs(g - r).max() <= 1e-14 * max(np.abs(r).max(), 1.0)
+    Qg = got[2].cpu().numpy()
+    d1, d2, d3 = Qg[0:3], Qg[3:6], Qg[6:9]
+    free = np.ones(Qg.shape[1], dtype=bool)
+    free[[0, 4 * (R.POS - 1)]] = False
+    for a, b, want in ((d1, d1, 1.0), (d2, d2, 1.0), (d3, d3, 1.0), (d1, d2, 0.0), (d1, d3, 0.0)):
+        assert np.abs((a * b).sum(axis=0)[free] - want).max() <= 1e-15

@@ -677,22 +677,24 @@ __global__ void local_error_kernel(const double* __restrict__ xs, int64_t Ns, co
 //
 // One persistent block per SM keeps the four layers' BF16 weights in shared memory and runs two
 // independent pipelines of 256 threads, each walking its own groups of four windows (rods).  A
-// group's activations live in the pipeline's shared-memory store of rows: window i takes rows
-// 53 i .. 53 i + 52, two zero rows and then its 51 node positions, so the two zero rows in
-// front of each window are the right-hand padding of the window before it as well.  A
-// convolution layer is then one GEMM per tile of 128 output rows,
+// group's activations live in the pipeline's shared-memory store of rows, two 128-row tiles of
+// two windows each: window slot i of a tile takes rows 53 i .. 53 i + 52 of it, two zero rows
+// and then its 51 node positions, so the two zero rows in front of a window are the right-hand
+// padding of the window before it as well (rows 106..127 of a tile stay zero).  A convolution
+// layer is then one GEMM per tile,
 //   D[m][o] = sum_t sum_c S[m + t][c] W[o][t c],   t = 0..4,
-// where output row m (window m / 53, position m % 53, an output where that is below 51) reads
+// where output row m (slot m / 53, position m % 53, an output where that is below 51) reads
 // store rows m .. m + 4, i.e. the positions m % 53 - 2 .. m % 53 + 2 of its own window.  The
 // store is K-major with consecutive rows 16 bytes apart inside each block of 8 channels (core
 // matrices of 8 consecutive rows, row-group stride 128 bytes, channel-block stride one whole
 // column block of the store), so the A operand of tap t is the store seen from row t -- its
-// descriptor starts 16 t bytes further on -- and no im2col copy is made.  Two tiles (256 rows)
-// accumulate in FP32 in tensor memory, 64 columns each.  The pipeline's first thread issues the
-// MMAs (tile x tap x 16 input channels) and commits them to the pipeline's mbarrier; after the
-// wait the pipeline's warp w reads lanes 32 (w % 4) .. + 31 of tile w / 4, adds the bias,
-// applies SiLU, rounds to BF16 and writes its row back into the store as the next layer's input
-// (store row m + 2).  The output layer's epilogue leaves the 16 outputs of each node position in
+// descriptor starts 16 t bytes further on -- and no im2col copy is made.  A tile's outputs read
+// only its own rows, so each tile -- its four warps, warp w reading lanes 32 (w % 4) .. + 31 of
+// the tile's 64 accumulator columns in tensor memory -- runs the layers on its own: its first
+// thread issues the tile's MMAs (tap x 16 input channels) and commits them to the tile's
+// mbarrier, the warps wait, add the bias, apply SiLU, round to BF16 and write their rows back
+// into the store as the next layer's input (store row m + 2), and meet at the tile's own named
+// barrier before the next layer; one tile's epilogue runs while the other's MMAs do.  The output layer's epilogue leaves the 16 outputs of each node position in
 // shared memory.  The FP64 work -- the features (computed one thread per node position from the
 // state in global memory) and the update of the state in place (one thread per node position;
 // update_node reads only that node and the element starting there) -- runs in separate phases,
@@ -706,7 +708,8 @@ constexpr int kPipes = 2;                        // independent pipelines per bl
 constexpr int kTiles = 2;                        // 128-row tiles per group
 constexpr int kTM = 128;
 constexpr int kWS = kPos + 2;                    // store rows per window (53)
-constexpr int kGW = kTiles * kTM / kWS;          // windows per group (4)
+constexpr int kWPT = kTM / kWS;                  // windows per tile (2): no window crosses a tile
+constexpr int kGW = kTiles * kWPT;               // windows per group (4)
 constexpr int kSR = kTiles * kTM + kTaps - 1;    // store rows (260): the last tile reads 4 rows past it
 constexpr uint32_t kChunk = kSR * 16;            // bytes of one block of 8 channels of a store
 constexpr uint32_t kCoreK = 128;                 // K-direction stride of the weights' core matrices
@@ -728,7 +731,8 @@ static_assert(kTcSmem <= 227 * 1024, "the fused kernel's shared memory exceeds a
 static_assert(kTcS % 16 == 0 && kTcW1 % 16 == 0 && kTcW2 % 16 == 0 && kTcW4 % 16 == 0, "16-byte operands");
 static_assert(kTcOut % 16 == 0, "16-byte output rows");
 static_assert((kPipes * (kTcS + kTcOut) + kTcW1 + 2 * kTcW2 + kTcW4 + kTcBias) % 8 == 0, "aligned base-couple samples");
-static_assert(kGW * kWS + 2 <= kSR, "the last window's right-hand padding rows lie inside the store");
+static_assert((kWPT - 1) * kWS + (kPos - 1) + (kTaps - 1) + 2 < kTM,
+              "a tile's outputs read only its own rows: the tiles' layers are independent");
 static_assert(kGW * kPos + kGW * 3 <= kPipeThreads, "one thread per node position, the rest for the base couple");
 static_assert((kTmemCols & (kTmemCols - 1)) == 0 && kTmemCols >= 32, "tensor-memory allocation size");
 
@@ -762,7 +766,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_apply_kernel(double* x, doub
   unsigned char* sW4 = sW3 + kTcW2;
   float* bias = reinterpret_cast<float*>(sW4 + kTcW4);
   __shared__ uint32_t tmem_base;
-  __shared__ __align__(8) uint64_t mbar[kPipes];
+  __shared__ __align__(8) uint64_t mbar[kPipes * kTiles];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   // the stores zero (rows that are no node position stay so), the weights in the K-major
@@ -789,7 +793,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_apply_kernel(double* x, doub
   }
   if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
   if (tid == 0)
-    for (int p = 0; p < kPipes; ++p) tc::mbar_init(&mbar[p], 1);
+    for (int p = 0; p < kPipes * kTiles; ++p) tc::mbar_init(&mbar[p], 1);
   tc::fence_proxy_async();
   tc::fence_before_sync();
   __syncthreads();
@@ -803,14 +807,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_apply_kernel(double* x, doub
   unsigned char* sS = smem_raw + pipe * kTcS;
   float4* outs = reinterpret_cast<float4*>(smem_raw + kPipes * kTcS + pipe * kTcOut);  // [c / 4][node]
   double* act_s = reinterpret_cast<double*>(bias + 3 * kC + kCO) + pipe * 2 * kGW * 3;  // [group & 1][window][3]
-  uint64_t* mb = &mbar[pipe];
+
   const uint32_t tcol = static_cast<uint32_t>(64 * kTiles * pipe);   // the pipeline's first accumulator column
   uint32_t phase = 0;
   const int wl = ptid >> 5;
   const int q = wl & 3, g = wl >> 2;             // lane quadrant (= warp % 4) and tile of this warp's rows
   const int m = kTM * g + 32 * q + lane;         // the output row of this thread
-  const int mw = m / kWS, mp = m % kWS;          // its window in the group and its node position
-  const bool row_pos = mw < kGW && mp < kPos;    // a node position (of a window slot of the group)
+  const int slot = (32 * q + lane) / kWS;        // its window slot in the tile
+  const int mw = kWPT * g + slot, mp = (32 * q + lane) % kWS;   // its window in the group, node position
+  const bool row_pos = slot < kWPT && mp < kPos; // a node position (of a window slot of the group)
+  // each tile (its four warps) runs the layers on its own: own barrier, mbarrier, issuing thread
+  const uint32_t tbar = 4u + static_cast<uint32_t>(kTiles * pipe + g);
+  uint64_t* mb = &mbar[kTiles * pipe + g];
+  const bool issuer = (32 * q + lane) == 0;
   const uint32_t tmem = tmem_base;
   const uint32_t tacc = tmem + (static_cast<uint32_t>(32 * q) << 16) + tcol + 64u * static_cast<uint32_t>(g);
   WinState S;                                    // the system's state, read in place
@@ -831,28 +840,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_apply_kernel(double* x, doub
   auto run_layer = [&](int l) -> bool {
     tc::fence_proxy_async();
     tc::fence_before_sync();
-    tc::bar_sync(bar_id, kPipeThreads);
-    if (ptid == 0 && !no_issue) {
+    tc::bar_sync(tbar, 128);
+    if (issuer && !no_issue) {
       tc::fence_after_sync();
       const uint32_t s0 = tc::smem_addr(sS);
       const int cin = l == 0 ? kC0 : kC;
       const uint32_t id = tc::idesc_bf16_f32(kTM, l == 3 ? kCO : kC);
       const uint32_t w0 = tc::smem_addr(l == 0 ? sW1 : (l == 1 ? sW2 : (l == 2 ? sW3 : sW4)));
       const uint32_t rw = l == 0 ? kRowW1 : kRowW;
-      for (int gt = 0; gt < kTiles; ++gt) {
-        int s = 0;
-        for (int tp = 0; tp < kTaps; ++tp)
-          for (int h = 0; h < cin / 16; ++h, ++s)
-            tc::mma_bf16(tmem + tcol + 64u * gt,
-                         tc::smem_desc(s0 + static_cast<uint32_t>(kTM * gt + tp) * 16u + 2u * h * kChunk, kChunk, 128u),
-                         tc::smem_desc(w0 + static_cast<uint32_t>((tp * cin + 16 * h) / 8) * kCoreK, kCoreK, rw), id,
-                         s > 0);
-      }
+      int s = 0;
+      for (int tp = 0; tp < kTaps; ++tp)
+        for (int h = 0; h < cin / 16; ++h, ++s)
+          tc::mma_bf16(tmem + tcol + 64u * g,
+                       tc::smem_desc(s0 + static_cast<uint32_t>(kTM * g + tp) * 16u + 2u * h * kChunk, kChunk, 128u),
+                       tc::smem_desc(w0 + static_cast<uint32_t>((tp * cin + 16 * h) / 8) * kCoreK, kCoreK, rw), id,
+                       s > 0);
       tc::commit(mb);
     }
     const bool ok = tc::mbar_wait(mb, phase, polls);
-    if (tc::bar_or(bar_id, kPipeThreads, !ok)) {
-      if (ptid == 0) atomicOr(err, ERR_TIMEOUT);
+    if (tc::bar_or(tbar, 128, !ok)) {
+      if (issuer) atomicOr(err, ERR_TIMEOUT);
       tc::mbar_wait(mb, phase, no_issue ? polls : kWaitPolls);  // the MMAs in flight finish first
       return false;
     }
@@ -945,6 +952,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_apply_kernel(double* x, doub
               for (int c = 0; c < kCO; ++c) tc_debug_put(dbg.pre, 3, nrods, b0 + mw, mp, c, o[c]);
           }
         }
+        // a wait that ran out in either tile stops the whole pipeline
+        alive = !tc::bar_or(bar_id, kPipeThreads, !alive);
       } else {
         // Fk first (its stores go to shared memory, so the update's global loads below may be
         // issued under its arithmetic), then U(k-1)
@@ -960,7 +969,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_apply_kernel(double* x, doub
 #pragma unroll
               for (int i = 0; i < kC0 / 2; ++i) pk[i] = 0u;
             }
-            const int r = wi * kWS + j + 2;
+            const int r = kTM * (wi / kWPT) + kWS * (wi % kWPT) + j + 2;
 #pragma unroll
             for (int cb = 0; cb < kC0 / 8; ++cb)
               *reinterpret_cast<uint4*>(sS + store_off(r, 8 * cb)) =
@@ -993,6 +1002,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_apply_kernel(double* x, doub
         }
       }
     }
+    tc::fence_proxy_async();                    // this thread's store writes, for either tile's MMAs
     tc::bar_sync(kPipes + 1, kTcThreads);       // the phase boundary of the whole block
   }
   tc::fence_before_sync();

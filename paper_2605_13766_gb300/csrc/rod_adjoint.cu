@@ -25,9 +25,18 @@
 namespace rod {
 namespace {
 
-// d a / d(th^2) and d b / d(th^2) of a = sin th / th, b = (1 - cos th) / th^2.
+// d a / d(th^2) and d b / d(th^2) of a = sin th / th, b = (1 - cos th) / th^2: the derivatives
+// of the series that rot_coeffs evaluates, cut by the same warp-uniform rule (two terms below
+// th^2 = 2^-20, four below 2^-10), otherwise of the full series or of sin and cos.
 __device__ __forceinline__ void rot_coeff_derivs(double th2, double& da, double& db) {
-  if (th2 <= 0.25) {
+  const unsigned mx = __reduce_max_sync(__activemask(), hi_word(th2));
+  if (mx < kHi2m20) {
+    da = -1.0 / 6.0;
+    db = -1.0 / 24.0;
+  } else if (mx < kHi2m10) {
+    da = fma(fma(th2, 3.0 * (-1.0 / 5040.0), 2.0 / 120.0), th2, -1.0 / 6.0);
+    db = fma(fma(th2, 3.0 * (-1.0 / 40320.0), 2.0 / 720.0), th2, -1.0 / 24.0);
+  } else if (th2 <= 0.25) {
     // term n of a: (-1)^n th^(2n) / (2n+1)!, derivative n (-1)^n th^(2n-2) / (2n+1)!
     da = 7.0 * (-1.0 / 1307674368000.0);
     da = fma(da, th2, 6.0 / 6227020800.0);
@@ -78,7 +87,7 @@ struct Rot {
 __device__ __forceinline__ Rot make_rot(const double p[3]) {
   Rot r;
   r.th2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
-  rot_coeffs_full(r.th2, r.a, r.b);
+  rot_coeffs(r.th2, r.a, r.b);   // the forward's series, cut per warp
   const double c0 = 1.0 - r.b * r.th2;
   r.R[0] = c0 + r.b * p[0] * p[0];
   r.R[4] = c0 + r.b * p[1] * p[1];
@@ -444,7 +453,19 @@ __global__ void __launch_bounds__(256) adjoint_kernel(AdjointParams A, LaunchSha
     const double s2 = 0.25 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     const double cth = 0.5 * (tr - 1.0);
     double f, dfds2, dfdc = 0.0;
-    if (s2 <= 0.0625 && cth > 0.0) {
+    // theta / sin theta and its derivative: the asin(s)/s series cut per warp like the forward's
+    // (three terms below s^2 = 2^-20, six below 2^-10, when every lane's angle is below 90 deg)
+    const unsigned act = __activemask();
+    const bool series = __all_sync(act, s2 <= 0.0625 && cth > 0.0);
+    const unsigned mx = __reduce_max_sync(act, hi_word(s2));
+    if (series && mx < kHi2m20) {
+      f = fma(fma(s2, 3.0 / 40.0, 1.0 / 6.0), s2, 1.0);
+      dfds2 = fma(s2, 2.0 * (3.0 / 40.0), 1.0 / 6.0);
+    } else if (series && mx < kHi2m10) {
+      f = fma(fma(fma(fma(fma(s2, 63.0 / 2816.0, 35.0 / 1152.0), s2, 5.0 / 112.0), s2, 3.0 / 40.0), s2, 1.0 / 6.0), s2, 1.0);
+      dfds2 = fma(fma(fma(fma(s2, 5.0 * (63.0 / 2816.0), 4.0 * (35.0 / 1152.0)), s2, 3.0 * (5.0 / 112.0)), s2,
+                      2.0 * (3.0 / 40.0)), s2, 1.0 / 6.0);
+    } else if (s2 <= 0.0625 && cth > 0.0) {
       f = asin_over_s(s2);
       dfds2 = dasin_over_s(s2);
     } else {
@@ -465,7 +486,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(AdjointParams A, LaunchSha
     const double kf = -f * i2D;
     double kap[3] = {kf * u[0], kf * u[1], kf * u[2]};
     const double eps = (m.ELL[i] + m.ELL[i + 1]) * i2D;
-    const double ieps = 1.0 / eps;
+    const double ieps = rcp_nr(eps);
     const double ie3 = ieps * ieps * ieps;
     double mk[3];
     for (int c = 0; c < 3; ++c)

@@ -83,6 +83,16 @@ ORACLE_CONTACT_FLOPS_PER_UNIT = 511.02
 BYTES_PER_UNIT = {"packing": 312.0, "carpet": 296.0, "cantilever": 296.0}
 
 
+def _measured_bf16_tflops():
+    """(dense BF16 TFLOP/s, where it comes from): the measured sustained cuBLAS figure when the pod's
+    MEASURED_PEAKS.json is present, else an earlier measurement on a GB300 (1.7 PFLOP/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]), "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
+    except Exception:
+        return 1700.0, "1.7 PFLOP/s sustained, an earlier GB300 measurement (of fallback)"
+
+
 def _measured_hbm_gbs():
     """(HBM copy bandwidth in GB/s, where it comes from): the measured figure when the pod's
     MEASURED_PEAKS.json is present, else an earlier measurement on a GB300 (6.8 TB/s)."""
@@ -365,10 +375,21 @@ def _surrogate_speedup(train_steps: int):
     net = RodSystem(p)
     net.set_state(*p.state())
     worst = 0.0
+    t_net = 0.0
     for k in range(1, 11):
+        n0, n1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0.record(net.torch_stream)
         sur.apply(net, 20)
+        n1.record(net.torch_stream)
+        torch.cuda.synchronize()
+        t_net += n0.elapsed_time(n1) / 1e3
         worst = max(worst, float(S.tip_error(p, net.get_state()[0], ref[20 * k]).max()))
     net.close()
+    # the network alone: 200 calls of the fused tcgen05 kernel, CUDA events around each 20;
+    # executed BF16 work per call: 256 tile rows per four windows, 32 input and 16 output channels
+    us_call = t_net / n_calls * 1e6
+    flop_call = p.n_rods / 4 * 256 * 2 * 5 * (32 * 64 + 64 * 64 + 64 * 64 + 64 * 16)
+    bf16_peak = _measured_bf16_tflops()
     el = p.n_elems * n_calls * W
     modes = {}
     for mode in ("local", "global"):
@@ -401,7 +422,13 @@ def _surrogate_speedup(train_steps: int):
             "err_unit": "|x_tip - x_tip(plain)| / L, max over all rods", "bound": 1e-3,
             "check_bound_sampled": S.DEFAULT_CHECK_BOUND, "modes": modes,
             "timing": "plain: CUDA events on its stream; rollout: host wall clock around the whole checked rollout",
-            "training": info, "dtype": "bf16 tensor cores (tcgen05, accumulators in tensor memory), FP32 accumulation, FP64 state"}
+            "training": info, "dtype": "bf16 tensor cores (tcgen05, accumulators in tensor memory), FP32 accumulation, FP64 state",
+            "network": {"us_per_call": us_call, "tensor_tflops_executed": flop_call / (us_call * 1e-6) / 1e12,
+                        "bf16_peak_tflops": bf16_peak[0], "bf16_frac": flop_call / (us_call * 1e-6) / 1e12 / bf16_peak[0],
+                        "peak_source": bf16_peak[1],
+                        "note": "fused inference kernel alone (features, four convolutions, FP64 update) per call "
+                                "of 50 fine steps on the 4096 rods, CUDA events; the FP64 features and update, "
+                                "not the tensor cores, bound it"}}
 
 
 def _pre_rolled(p, dt, n_steps):

@@ -18,7 +18,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "librod.so")
 SOURCES = ["rod_api.cu", "rod_step.cu", "rod_contact.cu", "rod_noalloc.cu", "rod_adjoint.cu", "rod_surrogate.cu", "rod_diag.cu"]
 HEADERS = ["rod_internal.h", "rod_contact.h", "rod_step_device.cuh", "rod_adjoint.h", "rod_sysview.h", "rod_diag.h",
-           "rod_fp.h", "rod_tc.cuh", "rod_cull.h"]
+           "rod_fp.h", "rod_tc.cuh", "rod_cull.h", "rod_rot.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-diag-suppress", "550"]

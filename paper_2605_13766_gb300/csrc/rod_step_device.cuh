@@ -10,70 +10,18 @@
 
 #include "rod_fp.h"
 #include "rod_internal.h"
+#include "rod_rot.cuh"
 
 namespace rod {
 namespace {
 
 // ---------------------------------------------------------------------------------- math
 
-// High 32 bits of a non-negative double: x < 2^k exactly when hi_word(x) < hi_word(2^k), so a
-// warp-wide integer maximum of these words bounds every lane's argument.
-__device__ __forceinline__ unsigned hi_word(double x) { return static_cast<unsigned>(__double2hiint(x)); }
 // Exponent field of a double (all ones: Inf or NaN), from its high word on the integer pipe.
 __device__ __forceinline__ unsigned exp_field(double x) {
   return static_cast<unsigned>(__double2hiint(x)) & 0x7FF00000u;
 }
 constexpr unsigned kExpAllOnes = 0x7FF00000u;
-constexpr unsigned kHi2m20 = 0x3EB00000u;  // 2^-20
-constexpr unsigned kHi2m10 = 0x3F500000u;  // 2^-10
-
-// sin(th)/th and (1 - cos th)/th^2 as Taylor series in th^2 (8 terms each; the dropped terms
-// are below 5e-20 relative for th^2 <= 1/4); larger angles use sincos.
-__device__ __forceinline__ void rot_coeffs_full(double th2, double& a, double& b) {
-  if (th2 <= 0.25) {
-    a = -1.0 / 1307674368000.0;
-    a = fma(a, th2, 1.0 / 6227020800.0);
-    a = fma(a, th2, -1.0 / 39916800.0);
-    a = fma(a, th2, 1.0 / 362880.0);
-    a = fma(a, th2, -1.0 / 5040.0);
-    a = fma(a, th2, 1.0 / 120.0);
-    a = fma(a, th2, -1.0 / 6.0);
-    a = fma(a, th2, 1.0);
-    b = -1.0 / 20922789888000.0;
-    b = fma(b, th2, 1.0 / 87178291200.0);
-    b = fma(b, th2, -1.0 / 479001600.0);
-    b = fma(b, th2, 1.0 / 3628800.0);
-    b = fma(b, th2, -1.0 / 40320.0);
-    b = fma(b, th2, 1.0 / 720.0);
-    b = fma(b, th2, -1.0 / 24.0);
-    b = fma(b, th2, 0.5);
-  } else {
-    double th = sqrt(th2);
-    double s, c, sh;
-    sincos(th, &s, &c);
-    sh = sin(0.5 * th) / th;
-    a = s / th;
-    b = 2.0 * sh * sh;
-  }
-}
-
-// Same coefficients with the series cut to the warp's largest th^2.  a multiplies K = [p]x and
-// b multiplies p p^T, of sizes th and th^2, so a term dropped from a costs R at most its size
-// times th: below th^2 = 2^-20 two terms (R off by < th^5 / 120 < 2^-56), below 2^-10 four terms
-// (< th^9 / 362880 < 2^-63), otherwise the full series.  The choice is uniform across the warp,
-// so lanes never diverge on it.
-__device__ __forceinline__ void rot_coeffs(double th2, double& a, double& b) {
-  const unsigned mx = __reduce_max_sync(__activemask(), hi_word(th2));
-  if (mx < kHi2m20) {
-    a = fma(th2, -1.0 / 6.0, 1.0);
-    b = fma(th2, -1.0 / 24.0, 0.5);
-  } else if (mx < kHi2m10) {
-    a = fma(fma(fma(th2, -1.0 / 5040.0, 1.0 / 120.0), th2, -1.0 / 6.0), th2, 1.0);
-    b = fma(fma(fma(th2, -1.0 / 40320.0, 1.0 / 720.0), th2, -1.0 / 24.0), th2, 0.5);
-  } else {
-    rot_coeffs_full(th2, a, b);
-  }
-}
 
 // asin(s)/s as a Taylor series in s^2 = |w|^2 (13 terms; dropped tail < 2e-18 for s <= 1/4).
 __device__ __forceinline__ double asin_over_s(double s2) {

@@ -36,6 +36,7 @@
 #include "rod_fp.h"
 #include "rod_tc.cuh"
 #include "rod_internal.h"
+#include "rod_rot.cuh"
 
 namespace rod {
 namespace sur {
@@ -262,19 +263,7 @@ __device__ __forceinline__ void rotate_directors(const double w[3], double T, co
   const double p0 = -T * w[0], p1 = -T * w[1], p2 = -T * w[2];
   const double th2 = fma(p0, p0, fma(p1, p1, p2 * p2));
   double a, b;
-  if (th2 < 2.5e-3) {
-    a = fma(fma(fma(th2, -1.0 / 5040.0, 1.0 / 120.0), th2, -1.0 / 6.0), th2, 1.0);
-    b = fma(fma(fma(th2, -1.0 / 40320.0, 1.0 / 720.0), th2, -1.0 / 24.0), th2, 0.5);
-  } else {
-    // half-angle forms: sin th = 2 s c and 1 - cos th = 2 s^2 with s, c of th / 2 (no cancellation)
-    const double th = sqrt(th2);
-    const double ith = 1.0 / th;
-    double sh, ch;
-    sincos(0.5 * th, &sh, &ch);
-    const double shi = sh * ith;
-    a = 2.0 * shi * ch;
-    b = 2.0 * shi * shi;
-  }
+  rot_coeffs(th2, a, b);  // series cut per warp from its largest angle
   const double c0 = fma(-b, th2, 1.0);
   const double b0 = b * p0, b1 = b * p1;
   const double a0 = a * p0, a1 = a * p1, a2 = a * p2;

@@ -42,20 +42,20 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
 # FP64 flops per unit of each kernel as the kernel evaluates them, counted by ncu on the active
 # threads (add/sub/mul = 1 flop, fma = 2) and divided by the units of the launch.  pack_one_step:
-# one launch of pack_kernel<3> on the 10^4-rod packing near step 1000, 131.25M DFMA + 32.11M
-# DADD + 102.47M DMUL on 1,366,295 element-steps.  pack_steps: one 20-step launch of
-# pack_kernel<0> on the 64 x 64 carpet, 400.25M DFMA + 78.80M DADD + 304.75M DMUL on 4,096,000
+# one launch of pack_kernel_plain<3> on the 10^4-rod packing near step 1000, 124.40M DFMA +
+# 22.41M DADD + 91.46M DMUL on 1,366,295 element-steps.  pack_steps: one 20-step launch of
+# pack_kernel<0> on the 64 x 64 carpet, 370.54M DFMA + 70.36M DADD + 284.39M DMUL on 4,096,000
 # element-steps.
 FLOPS_PER_UNIT = {
-    "pack_one_step": 290.6,   # per element-step
-    "pack_steps": 289.1,      # per element-step
+    "pack_one_step": 265.4,   # per element-step
+    "pack_steps": 267.5,      # per element-step
 }
 # FP64-pipe instructions per unit (thread level, ncu smsp__sass_thread_inst_executed_op_fp64):
 # a DMUL or DADD takes the FP64 unit as long as a DFMA, so the pipe is bound by instructions,
 # not flops; peak 2 per clock per SM x 152 SMs x 2.07 GHz.
 FP64_INSTR_PER_UNIT = {
-    "pack_one_step": 196.57,
-    "pack_steps": 193.44,
+    "pack_one_step": 176.40,
+    "pack_steps": 179.15,
 }
 FP64_INSTR_PEAK = 2 * 152 * 2.07e9
 FLOPS_SOURCE = "executed FP64 arithmetic of the kernel (ncu: DFMA x 2 + DADD + DMUL) per element-step"
@@ -112,8 +112,8 @@ def _measured_hbm_gbs():
 # CPU seconds the reference arm spends on its W + K samples (the whole run stays within minutes)
 REF_BUDGET_S = 90.0
 TRAFFIC_PER_LAUNCH = {
-    "pack_one_step": 275.33e6 + 144.05e6,
-    "pack_steps": 37.85e6,
+    "pack_one_step": 275.60e6 + 143.95e6,
+    "pack_steps": 37.78e6,
 }
 
 

@@ -253,13 +253,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(AdjointParams A, LaunchSha
     const bool held = (li == 0) && rc->clamp;
     const bool hasR = li < nr - 1, hasL = li > 0;
     double tau[3];
-    for (int c = 0; c < 3; ++c) {
-      const double Pr = hasR ? m.PP[c * m.CV + k] : 0.0;
-      const double Pl = hasL ? m.PP[c * m.CV + k - 1] : 0.0;
-      const double Tr = hasR ? m.TT[c * m.CV + k] : 0.0;
-      const double Tl = hasL ? m.TT[c * m.CV + k - 1] : 0.0;
-      tau[c] = fma(0.5, Tl + Tr, (Pr - Pl) + m.TA[c * m.CE + i]);
-    }
+    element_couple<true>(P, m, i, k, hasR, hasL, tau);
     double ebar = 0.0;
     for (int c = 0; c < 3; ++c) {
       const double wb = held ? 0.0 : a.WB[c * m.CE + i];

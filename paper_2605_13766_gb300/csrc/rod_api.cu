@@ -185,7 +185,7 @@ struct rod_system {
   // state
   DevBuf<double> x, v, Q, w;
   // constants
-  DevBuf<double> rest_len, inv_rl, inv_rl2, inv_2D, Dhat, inv_m;
+  DevBuf<double> rest_len, inv_rl, inv_rl2, inv_2D, sq_2D, Dhat, inv_m;
   DevBuf<double> rest_kappa, rest_sigma, elem_couple;
   DevBuf<double> magnet, arc0;  // magnetisation [3E], rest arc length of each element's first node [E]
   double field_b0[3] = {0, 0, 0}, field_bc[3] = {0, 0, 0}, field_bs[3] = {0, 0, 0}, field_omega = 0.0;
@@ -209,7 +209,7 @@ struct rod_system {
   bool shape_user = false;
   // misc
   double gravity[3] = {0, 0, 0};
-  bool has_gravity = false, has_act = false, has_damp_lin = false;
+  bool has_gravity = false, has_act = false, has_damp_lin = false, has_damp_rot = false, has_tip = false;
   DevBuf<int> err;
   int* err_host = nullptr;  // pinned
   bool state_set = false;
@@ -420,6 +420,7 @@ StepParams make_params(rod_system* s) {
   P.rest_len = s->rest_len.p;
   P.inv_rl = s->inv_rl.p;
   P.inv_2D = s->inv_2D.p;
+  P.sq_2D = s->sq_2D.p;
   P.Dhat = s->Dhat.p;
   P.inv_rl2 = s->inv_rl2.p;
   P.inv_m = s->inv_m.p;
@@ -436,6 +437,8 @@ StepParams make_params(rod_system* s) {
   for (int c = 0; c < 3; ++c) P.gravity[c] = s->gravity[c];
   P.has_gravity = s->has_gravity;
   P.has_damp_lin = s->has_damp_lin;
+  P.has_damp_rot = s->has_damp_rot;
+  P.has_tip = s->has_tip;
   P.has_act = s->has_act;
   P.magnet = s->magnet.p;
   for (int c = 0; c < 3; ++c) {
@@ -767,9 +770,10 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
     rc.damp_lin = (d->nu_damp + d->stokes_gamma) / (rho * A);
     rc.damp_rot = d->nu_damp / (rho * A);
     s->has_damp_lin = s->has_damp_lin || rc.damp_lin != 0.0;
+    s->has_damp_rot = s->has_damp_rot || rc.damp_rot != 0.0;
     rc.rhoI_12 = rc.rhoI[1] - rc.rhoI[2];
     rc.B_21 = rc.B[2] - rc.B[1];
-    rc.B_21h = 0.5 * rc.B_21;
+    rc.B_21q = 0.25 * rc.B_21;
     rc.radius = rad;
     rc.radius_f = static_cast<float>(rad);
     rc.node0 = static_cast<int32_t>(n0);
@@ -785,7 +789,10 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
       any_act = true;
     }
     if (d->tip_force)
-      for (int c = 0; c < 3; ++c) rc.tip[c] = d->tip_force[c * R + r];
+      for (int c = 0; c < 3; ++c) {
+        rc.tip[c] = d->tip_force[c * R + r];
+        s->has_tip = s->has_tip || rc.tip[c] != 0.0;
+      }
     if (d->muscle_amp && d->muscle_amp[r] != 0.0) {
       rc.muscle_amp = d->muscle_amp[r];
       rc.muscle_omega = 2.0 * kPi / d->muscle_period[r];
@@ -820,7 +827,8 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
 
   // per-item constants
   s->rest_len_h.assign(d->rest_len, d->rest_len + E);
-  std::vector<double> inv_rl(E), inv_rl2(E), inv_2D(std::max<int64_t>(V, 1)), Dh(std::max<int64_t>(V, 1)), inv_m(N);
+  std::vector<double> inv_rl(E), inv_rl2(E), inv_2D(std::max<int64_t>(V, 1)), sq_2D(std::max<int64_t>(V, 1)),
+      Dh(std::max<int64_t>(V, 1)), inv_m(N);
   for (int r = 0; r < R; ++r) {
     const RodConst& rc = s->rods_h[r];
     const double rhoA = d->density[r] * kPi * d->radius[r] * d->radius[r];
@@ -831,6 +839,7 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
     for (int k = 0; k < rc.n - 1; ++k) {
       const double a = d->rest_len[rc.elem0 + k], b = d->rest_len[rc.elem0 + k + 1];
       inv_2D[rc.elem0 - r + k] = 1.0 / (a + b);
+      sq_2D[rc.elem0 - r + k] = (a + b) * (a + b);
       Dh[rc.elem0 - r + k] = 0.5 * (a + b);
     }
     for (int j = 0; j <= rc.n; ++j) {
@@ -849,7 +858,8 @@ rod_status rod_system_create(const rod_system_desc* d, rod_system** out) {
   if ((ce = s->x.alloc(3 * N)) || (ce = s->v.alloc(3 * N)) || (ce = s->Q.alloc(9 * E)) || (ce = s->w.alloc(3 * E)) ||
       (ce = up(s->rest_len, d->rest_len, E)) || (ce = up(s->inv_rl, inv_rl.data(), E)) ||
       (ce = up(s->inv_rl2, inv_rl2.data(), E)) ||
-      (ce = up(s->inv_2D, inv_2D.data(), inv_2D.size())) || (ce = up(s->Dhat, Dh.data(), Dh.size())) ||
+      (ce = up(s->inv_2D, inv_2D.data(), inv_2D.size())) || (ce = up(s->sq_2D, sq_2D.data(), sq_2D.size())) ||
+      (ce = up(s->Dhat, Dh.data(), Dh.size())) ||
       (ce = up(s->inv_m, inv_m.data(), N)) || (ce = up(s->rods, s->rods_h.data(), R)) ||
       (ce = s->clamp_x.alloc(3 * R)) || (ce = s->clamp_Q.alloc(9 * R)) || (ce = s->err.alloc(1)))
     return cleanup(fail(ROD_ERR_CUDA, "device allocation/copy failed: %s", cudaGetErrorString(ce)));
@@ -899,6 +909,7 @@ rod_status rod_system_destroy(rod_system* s) {
   s->rest_len.release();
   s->inv_rl.release();
   s->inv_2D.release();
+  s->sq_2D.release();
   s->Dhat.release();
   s->inv_rl2.release();
   s->inv_m.release();

@@ -42,7 +42,8 @@ struct RodConst {
   // folds the products that these equalities make redundant, with
   double rhoI_12;       // rhoI[1] - rhoI[2]: (rho I w) x w = rhoI_12 (w1 w2, -w0 w2, 0)
   double B_21;          // B[2] - B[1]: kappa x (B kappa) = B_21 (k1 k2, -k0 k2, 0)
-  double B_21h;         // B_21 / 2 (the factor D / (2 D) of the Voronoi couple, exactly 1/2)
+  double B_21q;         // B_21 / 4 (the factor D / (2 D) = 1/2 of the Voronoi couple, times the
+                        // trapezoid's 1/2)
 };
 
 constexpr int kMaxWalls = 8;
@@ -100,6 +101,7 @@ struct StepParams {
   const double* rest_len;     // [E]
   const double* inv_rl;       // [E]  1/rl
   const double* inv_2D;       // [V]  1/(rl_k + rl_{k+1}) = 1/(2 D_k)
+  const double* sq_2D;        // [V]  (rl_k + rl_{k+1})^2 = (2 D_k)^2
   const double* Dhat;         // [V]  D_k
   const double* inv_rl2;      // [E]  1/rl^2
   const double* inv_m;        // [N]  1/lumped mass
@@ -116,6 +118,8 @@ struct StepParams {
   double gravity[3];
   int32_t has_gravity;
   int32_t has_damp_lin;       // some rod has linear damping or drag (damp_lin != 0)
+  int32_t has_damp_rot;       // some rod has rotational damping (damp_rot != 0)
+  int32_t has_tip;            // some rod has a tip force
   int32_t has_act;
   // magnetic couple rl (m x (Q b(t))): m per unit reference length (local) [3E] or null
   const double* magnet;

@@ -15,26 +15,32 @@ __device__ __forceinline__ unsigned hi_word(double x) { return static_cast<unsig
 constexpr unsigned kHi2m20 = 0x3EB00000u;  // 2^-20
 constexpr unsigned kHi2m10 = 0x3F500000u;  // 2^-10
 
-// sin(th)/th and (1 - cos th)/th^2 as Taylor series in th^2 (8 terms each; the dropped terms
-// are below 5e-20 relative for th^2 <= 1/4); larger angles use sincos.
+// Taylor coefficients in th^2 of a = sin(th)/th and b = (1 - cos th)/th^2: (-1)^k / (2k+1)! and
+// (-1)^k / (2k+2)!.
+namespace {
+__constant__ double kRotA[8] = {1.0, -1.0 / 6.0, 1.0 / 120.0, -1.0 / 5040.0, 1.0 / 362880.0, -1.0 / 39916800.0,
+                                1.0 / 6227020800.0, -1.0 / 1307674368000.0};
+__constant__ double kRotB[8] = {0.5, -1.0 / 24.0, 1.0 / 720.0, -1.0 / 40320.0, 1.0 / 3628800.0, -1.0 / 479001600.0,
+                                1.0 / 87178291200.0, -1.0 / 20922789888000.0};
+}  // namespace
+
+// The first n terms of both series by Horner's rule.  The trip count is a loop bound, not an
+// unrolled chain, so a warp that needs two terms issues two FMAs and no predicated remainder.
+__device__ __forceinline__ void rot_series(double th2, int n, double& a, double& b) {
+  a = kRotA[n - 1];
+  b = kRotB[n - 1];
+#pragma unroll 1
+  for (int k = n - 2; k >= 0; --k) {
+    a = fma(a, th2, kRotA[k]);
+    b = fma(b, th2, kRotB[k]);
+  }
+}
+
+// sin(th)/th and (1 - cos th)/th^2: 8 terms of the series for th^2 <= 1/4 (the dropped terms are
+// below 5e-20 relative there); larger angles use sincos.
 __device__ __forceinline__ void rot_coeffs_full(double th2, double& a, double& b) {
   if (th2 <= 0.25) {
-    a = -1.0 / 1307674368000.0;
-    a = fma(a, th2, 1.0 / 6227020800.0);
-    a = fma(a, th2, -1.0 / 39916800.0);
-    a = fma(a, th2, 1.0 / 362880.0);
-    a = fma(a, th2, -1.0 / 5040.0);
-    a = fma(a, th2, 1.0 / 120.0);
-    a = fma(a, th2, -1.0 / 6.0);
-    a = fma(a, th2, 1.0);
-    b = -1.0 / 20922789888000.0;
-    b = fma(b, th2, 1.0 / 87178291200.0);
-    b = fma(b, th2, -1.0 / 479001600.0);
-    b = fma(b, th2, 1.0 / 3628800.0);
-    b = fma(b, th2, -1.0 / 40320.0);
-    b = fma(b, th2, 1.0 / 720.0);
-    b = fma(b, th2, -1.0 / 24.0);
-    b = fma(b, th2, 0.5);
+    rot_series(th2, 8, a, b);
   } else {
     double th = sqrt(th2);
     double s, c, sh;
@@ -52,12 +58,8 @@ __device__ __forceinline__ void rot_coeffs_full(double th2, double& a, double& b
 // so lanes never diverge on it.
 __device__ __forceinline__ void rot_coeffs(double th2, double& a, double& b) {
   const unsigned mx = __reduce_max_sync(__activemask(), hi_word(th2));
-  if (mx < kHi2m20) {
-    a = fma(th2, -1.0 / 6.0, 1.0);
-    b = fma(th2, -1.0 / 24.0, 0.5);
-  } else if (mx < kHi2m10) {
-    a = fma(fma(fma(th2, -1.0 / 5040.0, 1.0 / 120.0), th2, -1.0 / 6.0), th2, 1.0);
-    b = fma(fma(fma(th2, -1.0 / 40320.0, 1.0 / 720.0), th2, -1.0 / 24.0), th2, 0.5);
+  if (mx < kHi2m10) {
+    rot_series(th2, mx < kHi2m20 ? 2 : 4, a, b);
   } else {
     rot_coeffs_full(th2, a, b);
   }

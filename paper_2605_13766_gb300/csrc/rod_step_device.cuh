@@ -51,6 +51,10 @@ __device__ __forceinline__ float f32_approx_hi(double x) {
   return __uint_as_float(e > 896u ? (sign | ((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3)) : sign);
 }
 
+// Coefficients of theta / sin(theta) = asin(s)/s in s^2 (s = sin theta), times 4^-k so that the
+// series runs in s4 = 4 s^2: (2k)! / (4^k (k!)^2 (2k+1)) / 4^k.
+__constant__ double kTosC[6] = {1.0, 1.0 / 24.0, 3.0 / 640.0, 5.0 / 7168.0, 35.0 / 294912.0, 63.0 / 2883584.0};
+
 // theta / sin(theta) of the relative rotation R = Q_{k+1} Q_k^T, from s4 = |u|^2 = 4 sin^2
 // theta (u = (R32 - R23, R13 - R31, R21 - R12)).  Warp-uniform cut of the series like
 // rot_coeffs (sin^2 < 2^-20: three terms, dropped < 4e-20; sin^2 < 2^-10: six terms, dropped
@@ -73,15 +77,14 @@ __device__ __forceinline__ double theta_over_sin(double s4, const double* qa, co
     d3 = fmaf(f32_approx_hi(qb[6 + c]), f32_approx_hi(qa[6 + c]), d3);
   }
   const bool small = __all_sync(act, d1 > 0.25f && d3 > 0.25f);
-  // the series in sin^2 = s4 / 4, with its coefficients scaled by powers of 1/4
-  if (small && mx < kHi2m18) return fma(fma(s4, 3.0 / 640.0, 1.0 / 24.0), s4, 1.0);
   if (small && mx < kHi2m8) {
-    double f = 63.0 / 2883584.0;
-    f = fma(f, s4, 35.0 / 294912.0);
-    f = fma(f, s4, 5.0 / 7168.0);
-    f = fma(f, s4, 3.0 / 640.0);
-    f = fma(f, s4, 1.0 / 24.0);
-    return fma(f, s4, 1.0);
+    // the series in sin^2 = s4 / 4, its coefficients scaled by powers of 1/4, by Horner's rule
+    // over a warp-uniform trip count (no predicated remainder)
+    int k = (mx < kHi2m18) ? 2 : 5;
+    double f = kTosC[k];
+#pragma unroll 1
+    for (--k; k >= 0; --k) f = fma(f, s4, kTosC[k]);
+    return f;
   }
   const double s2 = 0.25 * s4;
   const double dd1 = fma(qb[0], qa[0], fma(qb[1], qa[1], qb[2] * qa[2]));
@@ -179,25 +182,29 @@ __device__ __forceinline__ void kin_element(const StepParams& P, const Pack& pk,
 #pragma unroll
     for (int a = 0; a < 9; ++a) q[a] = P.clamp_Q[a * P.n_rods + g];
   } else {
-    // Q <- R Q, R = exp([phi]x), phi = -h w:  R = I + a K + b K^2 = (1 - b th^2) I + a K + b phi phi^T
+    // Q <- R Q, R = exp([phi]x), phi = -h w:  R = I + a K + b K^2 = (1 - b th^2) I + a K + b phi phi^T.
+    // The directors are the rows of Q: d1' and d2' take rows 0 and 1 of R, and d3' = d1' x d2'
+    // (the same rotation of a right-handed orthonormal frame; 6 entries of R instead of 9, and 24
+    // products instead of 27).
     const double p0 = -h * m.WW[i], p1 = -h * m.WW[m.CE + i], p2 = -h * m.WW[2 * m.CE + i];
     const double th2 = fma(p0, p0, fma(p1, p1, p2 * p2));
     double ca, cb;
     rot_coeffs(th2, ca, cb);
     const double c0 = fma(-cb, th2, 1.0);
-    const double b0 = cb * p0, b1 = cb * p1, b2 = cb * p2;
+    const double b0 = cb * p0, b1 = cb * p1;
     const double a0 = ca * p0, a1 = ca * p1, a2 = ca * p2;
-    const double R00 = fma(b0, p0, c0), R11 = fma(b1, p1, c0), R22 = fma(b2, p2, c0);
+    const double R00 = fma(b0, p0, c0), R11 = fma(b1, p1, c0);
     const double R01 = fma(b0, p1, -a2), R10 = fma(b1, p0, a2);
-    const double R02 = fma(b0, p2, a1), R20 = fma(b2, p0, -a1);
-    const double R12 = fma(b1, p2, -a0), R21 = fma(b2, p1, a0);
+    const double R02 = fma(b0, p2, a1), R12 = fma(b1, p2, -a0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const double q0 = q[c], q1 = q[3 + c], q2 = q[6 + c];
       q[c] = fma(R00, q0, fma(R01, q1, R02 * q2));
       q[3 + c] = fma(R10, q0, fma(R11, q1, R12 * q2));
-      q[6 + c] = fma(R20, q0, fma(R21, q1, R22 * q2));
     }
+    q[6] = fma(q[1], q[5], -q[2] * q[4]);
+    q[7] = fma(q[2], q[3], -q[0] * q[5]);
+    q[8] = fma(q[0], q[4], -q[1] * q[3]);
   }
 #pragma unroll
   for (int a = 0; a < 9; ++a) m.QQ[a * m.CE + i] = q[a];
@@ -224,8 +231,14 @@ __device__ __forceinline__ void kinematic(const StepParams& P, const Pack& pk, S
 
 // --------------------------------------------------------------- dynamic stage (a3-a7, a10, a2)
 
+// The stage functions take GEN = false for the plain step: circular sections without rest
+// strain or rest curvature, and no external element couples, actuation, magnetic field,
+// muscles, walls, tip forces or damping.  Each of those tests is then false at compile time, so
+// no predicated instruction of theirs reaches the FP64 pipe; GEN = true tests the parameters.
+
 // Stage A (elements): geometry, shear strain, internal force, shear couple, transport couples,
 // damping and external couples.
+template <bool GEN = true>
 __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& pk, Smem& m) {
   const int Ep = pk.nelem;
   for (int i = m.t0; i < Ep; i += m.ts) {
@@ -247,11 +260,12 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
     const double ell = ll * rs;
     const double rl = __ldg(P.rest_len + ge);
     const double ie = rl * rs;              // 1 / e
-    double Ql[3], sg[3], n[3];
+    double Ql[3], sg[3], n[3], tc[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) Ql[a] = fma(q[3 * a], l[0], fma(q[3 * a + 1], l[1], q[3 * a + 2] * l[2]));
-    // n / e = S sigma / e  (the 1/e of the internal force, folded once)
-    if (P.rest_sigma) {
+    // n / e = S sigma / e  (the 1/e of the internal force, folded once), and the shear couple
+    // ((Q t) x n) rl = (Ql x n) rl / ell = Ql x (n / e)
+    if (GEN && P.rest_sigma) {
       const double irl = __ldg(P.inv_rl + ge);
       sg[0] = Ql[0] * irl;
       sg[1] = Ql[1] * irl;
@@ -260,22 +274,25 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
       for (int c = 0; c < 3; ++c) sg[c] -= __ldg(P.rest_sigma + c * P.E + ge);
 #pragma unroll
       for (int c = 0; c < 3; ++c) n[c] = (__ldg(&rc->S[c]) * ie) * sg[c];
+      tc[0] = fma(Ql[1], n[2], -Ql[2] * n[1]);
+      tc[1] = fma(Ql[2], n[0], -Ql[0] * n[2]);
+      tc[2] = fma(Ql[0], n[1], -Ql[1] * n[0]);
     } else {
-      // sigma / e = (Q l / rl - e3) rl / ell = Q l / ell - e3 rl / ell  (S[0] = S[1])
+      // sigma / e = (Q l / rl - e3) rl / ell = Q l / ell - e3 rl / ell  (S[0] = S[1]), so
+      // n_0,1 = s01 Ql_0,1 and Ql x n = (Ql_1 z, -Ql_0 z, 0) with z = n_2 - s01 Ql_2
       const double s2 = __ldg(&rc->S[2]);
       const double s01 = __ldg(&rc->S[0]) * rs;
       n[0] = s01 * Ql[0];
       n[1] = s01 * Ql[1];
       n[2] = s2 * fma(rs, Ql[2], -ie);
+      const double z = fma(-s01, Ql[2], n[2]);
+      tc[0] = Ql[1] * z;
+      tc[1] = -Ql[0] * z;
+      tc[2] = 0.0;
     }
     // lab internal force N = Q^T n / e
 #pragma unroll
     for (int b = 0; b < 3; ++b) m.NF[b * m.CE + i] = fma(q[b], n[0], fma(q[3 + b], n[1], q[6 + b] * n[2]));
-    // shear couple ((Q t) x n) rl = (Ql x n) rl / ell = Ql x (n / e)
-    double tc[3];
-    tc[0] = fma(Ql[1], n[2], -Ql[2] * n[1]);
-    tc[1] = fma(Ql[2], n[0], -Ql[0] * n[2]);
-    tc[2] = fma(Ql[0], n[1], -Ql[1] * n[0]);
     // transport couples (J w / e) x w + (J w / e^2) de/dt,  de/dt = (l . dv) / (ell rl), and the
     // rotational damping -nu rl (I/A) w; with J w = rl g, g = rho I w:
     //   rl/e (g x w) + rl (de/dt / e^2 - damp_rot) g
@@ -283,19 +300,19 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
     // rl (de/dt / e^2 - damp_rot) = ie^2 ((l . dv) rs) - rl damp_rot   (rl / (ell rl e^2) = ie^2 rs)
     const double ldv = fma(l[0], dv[0], fma(l[1], dv[1], l[2] * dv[2]));
     const double k1 = (rl * ie) * __ldg(&rc->rhoI_12);
-    const double k2 = fma(ie * ie, ldv * rs, -rl * __ldg(&rc->damp_rot));
+    const double k2 = (GEN && P.has_damp_rot) ? fma(ie * ie, ldv * rs, -rl * __ldg(&rc->damp_rot)) : (ie * ie) * (ldv * rs);
     tc[0] = fma(k1, w[1] * w[2], tc[0]);
     tc[1] = fma(-k1, w[0] * w[2], tc[1]);
     const double k2j = k2 * __ldg(&rc->rhoI[0]);
     tc[0] = fma(k2j, w[0], tc[0]);
     tc[1] = fma(k2j, w[1], tc[1]);
     tc[2] = fma(k2 * __ldg(&rc->rhoI[2]), w[2], tc[2]);
-    if (P.elem_couple) {
+    if (GEN && P.elem_couple) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) tc[c] += __ldg(P.elem_couple + c * P.E + ge);
     }
-    if (P.has_act && (i - m.rel0[r]) == rc->act_elem) tc[0] += m.ACT[r];
-    if (P.magnet) {
+    if (GEN && P.has_act && (i - m.rel0[r]) == rc->act_elem) tc[0] += m.ACT[r];
+    if (GEN && P.magnet) {
       // magnetic couple rl (m x (Q b)), Q b: the field in the element's frame
       double qb[3], mg[3];
 #pragma unroll
@@ -306,7 +323,7 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
       tc[1] += fma(mg[2], qb[0], -mg[0] * qb[2]);
       tc[2] += fma(mg[0], qb[1], -mg[1] * qb[0]);
     }
-    if (P.arc0 && rc->muscle_amp != 0.0) {
+    if (GEN && P.arc0 && rc->muscle_amp != 0.0) {
       // muscle couples about d1 at the Voronoi points on both sides: tau_{i-1} - tau_i
       const int li = i - m.rel0[r], nr = m.rel0[r + 1] - m.rel0[r];
       const double t = m.BF[3], sl = __ldg(P.arc0 + ge), sr = sl + rl;
@@ -322,7 +339,12 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
 }
 
 // Stage B (Voronoi points): curvature by the rotation logarithm, Voronoi dilatation,
-// bending/twist couple m = B(kappa - kappa0), P = m/eps^3, T = (kappa x m) D/eps^3.
+// bending/twist couple m = B(kappa - kappa0), P = m/eps^3, T = (kappa x m) D/eps^3.  The
+// element couple of stage C takes P_k - P_{k-1} + (T_k + T_{k-1}) / 2 over its two Voronoi
+// points, so each point stores its two shares: PP = P + T/2 (to the element on its left) and
+// TT = T/2 - P (to the element on its right).  For a circular section without rest curvature
+// T_3 = 0: PP holds P_3 and TT's third component is not written.
+template <bool GEN = true>
 __device__ __forceinline__ void stage_voronoi(const StepParams& P, const Pack& pk, Smem& m) {
   const int Vp = pk.nvor;
   for (int k = m.t0; k < Vp; k += m.ts) {
@@ -357,43 +379,65 @@ __device__ __forceinline__ void stage_voronoi(const StepParams& P, const Pack& p
     u2 = fma(-qb[2], qa[5], u2);
     const double s4 = fma(u0, u0, fma(u1, u1, u2 * u2));  // |u|^2 = 4 sin^2(theta)
     const double f = theta_over_sin(s4, qa, qb);
-    const double i2D = __ldg(P.inv_2D + gv);
-    const double eps = (m.ELL[i] + m.ELL[i + 1]) * i2D;
-    const double ieps = rcp_nr(eps);
-    const double ie3 = ieps * ieps * ieps;
-    if (P.rest_kappa) {
+    const double ls = m.ELL[i] + m.ELL[i + 1];   // eps = ls / (2D)
+    if (GEN && P.rest_kappa) {
+      const double i2D = __ldg(P.inv_2D + gv);
+      const double ieps = rcp_nr(ls * i2D);
+      const double ie3 = ieps * ieps * ieps;
       const double kf = -f * i2D;           // kappa = -(theta/s) w / D = -f u / (2D)
-      const double tD = __ldg(P.Dhat + gv) * ie3;
+      const double tDh = (0.5 * __ldg(P.Dhat + gv)) * ie3;
       const double kap[3] = {kf * u0, kf * u1, kf * u2};
       double mk[3];
 #pragma unroll
       for (int cc = 0; cc < 3; ++cc) mk[cc] = __ldg(&rc->B[cc]) * (kap[cc] - __ldg(P.rest_kappa + cc * P.V + gv));
-      m.PP[k] = mk[0] * ie3;
-      m.PP[m.CV + k] = mk[1] * ie3;
-      m.PP[2 * m.CV + k] = mk[2] * ie3;
-      m.TT[k] = fma(kap[1], mk[2], -kap[2] * mk[1]) * tD;
-      m.TT[m.CV + k] = fma(kap[2], mk[0], -kap[0] * mk[2]) * tD;
-      m.TT[2 * m.CV + k] = fma(kap[0], mk[1], -kap[1] * mk[0]) * tD;
+      const double cr[3] = {fma(kap[1], mk[2], -kap[2] * mk[1]), fma(kap[2], mk[0], -kap[0] * mk[2]),
+                            fma(kap[0], mk[1], -kap[1] * mk[0])};
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        const double pc = mk[cc] * ie3;
+        m.PP[cc * m.CV + k] = fma(cr[cc], tDh, pc);
+        m.TT[cc * m.CV + k] = fma(cr[cc], tDh, -pc);
+      }
     } else {
       // m = B kappa = kf B u with kf = -f / (2D); with B = (b, b, b3) (circular section) kappa x m
-      // = kf^2 (b3 - b) (u1 u2, -u0 u2, 0), and as D / (2D) = 1/2 exactly, the couple's factor
-      // kf^2 D / eps^3 = f g / 2 with g = f / (2D eps^3)
-      const double g = (f * ie3) * i2D;
+      // = kf^2 (b3 - b) (u1 u2, -u0 u2, 0), and as D / (2D) = 1/2 exactly, T/2 = kf^2 D / (2 eps^3)
+      // (kappa x m) / kf^2 = f g B_21 / 4 (u1 u2, -u0 u2, 0) with g = f / (2D eps^3) = f (2D)^2 / ls^3
+      const double is = rcp_nr(ls);
+      const double g = (f * (is * is * is)) * __ldg(P.sq_2D + gv);
       const double sb = -g * __ldg(&rc->B[0]);
-      m.PP[k] = sb * u0;
-      m.PP[m.CV + k] = sb * u1;
+      const double ct = (f * g) * __ldg(&rc->B_21q);
+      const double p0 = sb * u0, p1 = sb * u1;
+      const double u12 = u1 * u2, u02 = u0 * u2;
+      m.PP[k] = fma(ct, u12, p0);
+      m.TT[k] = fma(ct, u12, -p0);
+      m.PP[m.CV + k] = fma(-ct, u02, p1);
+      m.TT[m.CV + k] = fma(-ct, u02, -p1);
       m.PP[2 * m.CV + k] = (-g * __ldg(&rc->B[2])) * u2;
-      const double ct = (f * g) * __ldg(&rc->B_21h);
-      m.TT[k] = ct * (u1 * u2);
-      m.TT[m.CV + k] = -ct * (u0 * u2);
-      m.TT[2 * m.CV + k] = 0.0;
+    }
+  }
+}
+
+// The element couple of element i from its Voronoi points (right: k, if hasR; left: k - 1, if
+// hasL) and its own couple TA: P_k - P_{k-1} + (T_k + T_{k-1}) / 2 + TA as PP_k + TT_{k-1} + TA.
+template <bool GEN = true>
+__device__ __forceinline__ void element_couple(const StepParams& P, const Smem& m, int i, int k, bool hasR, bool hasL,
+                                               double tau[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double Ar = hasR ? m.PP[c * m.CV + k] : 0.0;
+    if (c == 2 && !(GEN && P.rest_kappa)) {
+      const double Al = hasL ? m.PP[c * m.CV + k - 1] : 0.0;
+      tau[c] = (Ar - Al) + m.TA[c * m.CE + i];
+    } else {
+      const double Bl = hasL ? m.TT[c * m.CV + k - 1] : 0.0;
+      tau[c] = (Ar + Bl) + m.TA[c * m.CE + i];
     }
   }
 }
 
 // Stage C (elements): bending couple from the difference and trapezoid operators, angular
 // acceleration e J^{-1} tau, rate update and constraint; optional kinematic rotation.
-template <int MODE>
+template <int MODE, bool GEN = true>
 __device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& pk, Smem& m, double dt, double h,
                                                double* acc_w) {
   const int Ep = pk.nelem;
@@ -408,20 +452,7 @@ __device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& 
     const int k = i - r;                     // right Voronoi point (valid if li < nr-1)
     const bool hasR = li < nr - 1, hasL = li > 0;
     double tau[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const double Pr = hasR ? m.PP[c * m.CV + k] : 0.0;
-      const double Pl = hasL ? m.PP[c * m.CV + k - 1] : 0.0;
-      if (c == 2 && !P.rest_kappa) {
-        // the third component of kappa x (B kappa) vanishes for a circular section without rest
-        // curvature (stage_voronoi writes zeros there)
-        tau[c] = (Pr - Pl) + m.TA[c * m.CE + i];
-        continue;
-      }
-      const double Tr = hasR ? m.TT[c * m.CV + k] : 0.0;
-      const double Tl = hasL ? m.TT[c * m.CV + k - 1] : 0.0;
-      tau[c] = fma(0.5, Tl + Tr, (Pr - Pl) + m.TA[c * m.CE + i]);
-    }
+    element_couple<GEN>(P, m, i, k, hasR, hasL, tau);
     const bool held = (li == 0) && rc->clamp;
     if (MODE == MODE_RHS) {
       const double ke = m.EDIL[i];
@@ -441,7 +472,7 @@ __device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& 
 }
 
 // Stage D (nodes): internal force difference, external forces, velocity update + constraint.
-template <int MODE>
+template <int MODE, bool GEN = true>
 __device__ __forceinline__ void stage_translation(const StepParams& P, const Pack& pk, Smem& m, double dt,
                                                   double* acc_v, double t, double h = 0.0) {
   const int Np = pk.nnode;
@@ -472,28 +503,25 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
       // warps without a contact force take the plain difference (the common case)
       contact = __any_sync(__activemask(), fR || fL);
     }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double Nr = hasR ? m.NF[c * m.CE + iR] : 0.0;
+      const double Nl = hasL ? m.NF[c * m.CE + iR - 1] : 0.0;
+      F[c] = Nr - Nl;
+    }
     if (contact) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const double Nr = hasR ? m.NF[c * m.CE + iR] : 0.0;
-        const double Nl = hasL ? m.NF[c * m.CE + iR - 1] : 0.0;
         const double fa = fR ? __ldg(P.fseg + c * P.E + ge) : 0.0;
         const double fb = fL ? __ldg(P.fseg + (3 + c) * P.E + ge - 1) : 0.0;
-        F[c] = (Nr + fa) - (Nl - fb);
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double Nr = hasR ? m.NF[c * m.CE + iR] : 0.0;
-        const double Nl = hasL ? m.NF[c * m.CE + iR - 1] : 0.0;
-        F[c] = Nr - Nl;
+        F[c] += fa + fb;
       }
     }
-    if (lj == nr) {
+    if (GEN && P.has_tip && lj == nr) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) F[c] += __ldg(&rc->tip[c]);
     }
-    for (int k = 0; k < P.n_walls; ++k) {
+    for (int k = 0; k < (GEN ? P.n_walls : 0); ++k) {
       // node sphere (radius of the rod) against the half-space n . (x - p - u t) >= 0
       double d[3], vr[3];
 #pragma unroll
@@ -526,13 +554,19 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
     } else {
       // v += dt (F/m - c v + g)  as  v (1 - dt c) + (dt/m) F + dt g  (keep = 1 without damping)
       const double dtim = dt * im;
-      const double keep = P.has_damp_lin ? fma(-dt, dl, 1.0) : 1.0;
+      if (GEN) {
+        const double keep = P.has_damp_lin ? fma(-dt, dl, 1.0) : 1.0;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double vj = m.VN[c * m.CN + j];
-        const double base = P.has_damp_lin ? (P.has_gravity ? fma(vj, keep, dtg[c]) : vj * keep)
-                                           : (P.has_gravity ? vj + dtg[c] : vj);
-        m.VN[c * m.CN + j] = held ? 0.0 : fma(F[c], dtim, base);
+        for (int c = 0; c < 3; ++c) {
+          const double vj = m.VN[c * m.CN + j];
+          const double base = P.has_damp_lin ? (P.has_gravity ? fma(vj, keep, dtg[c]) : vj * keep)
+                                             : (P.has_gravity ? vj + dtg[c] : vj);
+          m.VN[c * m.CN + j] = held ? 0.0 : fma(F[c], dtim, base);
+        }
+      } else {
+        // no damping; dtg is zero without gravity
+#pragma unroll
+        for (int c = 0; c < 3; ++c) m.VN[c * m.CN + j] = held ? 0.0 : fma(F[c], dtim, m.VN[c * m.CN + j] + dtg[c]);
       }
       // the following kinematic half/full step of this node (it reads only its own x, v)
       if (h != 0.0) kin_node(P, pk, m, j, h);

@@ -2,12 +2,14 @@
 //
 // On this part an FP64 -> FP32 or FP32 -> FP64 conversion instruction issues on the FP64 pipe,
 // at the rate of an FP64 fused multiply-add, which the step kernels are bound by.  These
-// functions do the same conversions with integer operations on the bit patterns, for the
-// numbers whose conversion stays within the FP32 normal range (and zero); for the rest they
-// report `ok = false` and the caller takes the conversion instruction.  Host-compilable, so the
+// functions do the same conversions with integer operations on the bit patterns.  The `_bits`
+// forms cover the numbers whose conversion stays within the FP32 normal range (and zero) and
+// report `ok = false` for the rest (the Newton seeds below need that range); the `_all` forms
+// cover every input (subnormal results, overflow, infinities, NaN), so a caller has no
+// conversion instruction to fall back to (a fallback branch that short compiles as a predicated
+// instruction, which issues on the FP64 pipe for every warp).  Host-compilable, so the
 // bit logic is tested on the CPU against the compiler's own conversions.  Device code also gets
-// the FP64 reciprocal and reciprocal square root by Newton-Raphson from seeds formed with them,
-// and the two conversions with their instruction as the fallback.
+// the FP64 reciprocal and reciprocal square root by Newton-Raphson from seeds formed with them.
 #pragma once
 #include <cstdint>
 #include <cstring>
@@ -85,6 +87,59 @@ ROD_FP_HD float f32_rn_bits(double x, bool& ok) {
   return 0.0f;
 }
 
+// Count of leading zero bits of a nonzero 32-bit word.
+ROD_FP_HD int clz32(uint32_t v) {
+#if defined(__CUDA_ARCH__)
+  return __clz(static_cast<int>(v));
+#else
+  return __builtin_clz(v);
+#endif
+}
+
+// x rounded to the nearest FP32, ties to even, for every x: FP32 normal and subnormal results,
+// zero, overflow to infinity, infinities, and NaN (a quiet NaN of x's sign that keeps the top
+// bits of x's payload).
+ROD_FP_HD float f32_rn_all(double x) {
+  const uint64_t u = fp64_bits(x);
+  const uint32_t hi = static_cast<uint32_t>(u >> 32), lo = static_cast<uint32_t>(u);
+  const uint32_t e = (hi >> 20) & 0x7FFu;
+  const uint32_t sign = hi & 0x80000000u;
+  const uint32_t m23 = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  if (e - 897u <= 253u) {                          // an FP32 normal exponent (carry: infinity)
+    uint32_t bits = sign | ((e - 896u) << 23) | m23;
+    const uint32_t rest = lo & 0x1FFFFFFFu;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (bits & 1u))) ++bits;
+    return fp32_from_bits(bits);
+  }
+  if (e == 0x7FFu) {                               // infinity or NaN
+    const bool nan = ((hi & 0xFFFFFu) | lo) != 0u;
+    return fp32_from_bits(sign | 0x7F800000u | (nan ? (0x400000u | m23) : 0u));
+  }
+  if (e > 1150u) return fp32_from_bits(sign | 0x7F800000u);   // |x| >= 2^128
+  if (e < 873u) return fp32_from_bits(sign);       // |x| <= 2^-150 (a tie there goes to zero)
+  // FP32 subnormal range: |x| = m53 2^(e - 1075) = (m53 2^(e - 926)) units of 2^-149
+  const uint64_t m53 = (static_cast<uint64_t>((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
+  const uint32_t sh = 926u - e;                    // 30..53
+  uint64_t q = m53 >> sh;
+  const uint64_t rem = m53 & ((1ull << sh) - 1ull), half = 1ull << (sh - 1u);
+  if (rem > half || (rem == half && (q & 1ull))) ++q;   // may carry to the smallest normal
+  return fp32_from_bits(sign | static_cast<uint32_t>(q));
+}
+
+// An FP32 value widened to FP64 exactly, for every input (subnormals normalised; infinities;
+// NaN keeps its payload).
+ROD_FP_HD double f64_of_f32_all(float f) {
+  const uint32_t b = fp32_bits(f);
+  const uint32_t e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+  const uint64_t sign = static_cast<uint64_t>(b & 0x80000000u) << 32;
+  if (e - 1u <= 253u) return fp64_from_bits(sign | (static_cast<uint64_t>(e + 896u) << 52) | (static_cast<uint64_t>(m) << 29));
+  if (e == 0xFFu) return fp64_from_bits(sign | (0x7FFull << 52) | (static_cast<uint64_t>(m) << 29));
+  if (m == 0u) return fp64_from_bits(sign);
+  const int p = 31 - clz32(m);                     // m 2^-149 = 2^(p - 149) (m / 2^p)
+  const uint64_t frac = (static_cast<uint64_t>(m) << (52 - p)) & 0xFFFFFFFFFFFFFull;
+  return fp64_from_bits(sign | (static_cast<uint64_t>(p + 874) << 52) | frac);
+}
+
 // An FP32 value widened to FP64 exactly, for zero and FP32 normal numbers (ok = false for
 // subnormals, infinities and NaN).
 ROD_FP_HD double f64_of_f32_bits(float f, bool& ok) {
@@ -134,16 +189,17 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
   return fma(h0, r, y0);
 }
 
-// a double rounded to FP32 (integer pipe; the conversion instruction only for results outside
-// the FP32 normal range)
+// A double rounded to FP32 and an FP32 value widened to FP64: the normal-range integer form with
+// the conversion instruction as the fallback.  The fallback compiles as a predicated instruction
+// that issues for every warp, one FP64-pipe slot per conversion; code bound by the FP64 pipe
+// (the step kernels) takes f32_rn_all / f64_of_f32_all instead, whose extra integer work costs
+// more than that slot on a latency-bound path (the surrogate's features and update).
 __device__ __forceinline__ float f32_rn(double x) {
   bool ok;
   const float f = f32_rn_bits(x, ok);
   return ok ? f : static_cast<float>(x);
 }
 
-// an FP32 value widened to FP64 (integer pipe; the conversion instruction for subnormals,
-// infinities and NaN)
 __device__ __forceinline__ double f64_of(float f) {
   bool ok;
   const double d = f64_of_f32_bits(f, ok);

@@ -219,7 +219,7 @@ __device__ __forceinline__ void kin_node(const StepParams& P, const Pack& pk, Sm
   for (int c = 0; c < 3; ++c) {
     const double val = held ? P.clamp_x[c * P.n_rods + g] : fma(h, m.VN[c * m.CN + j], m.X[c * m.CN + j]);
     m.X[c * m.CN + j] = val;
-    if (m.XF) m.XF[c * m.CN + j] = f32_rn(val);
+    if (m.XF) m.XF[c * m.CN + j] = f32_rn_all(val);   // integer pipe for every input
   }
 }
 

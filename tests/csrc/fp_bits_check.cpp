@@ -1,6 +1,8 @@
 // Checks the integer-pipe FP64 <-> FP32 conversions of rod_fp.h against the host compiler's own
-// conversions (round to nearest, ties to even) on edge cases and random bit patterns.
-// Prints "<checked> <mismatches> <not_ok_in_range>" and exits 0.
+// conversions (round to nearest, ties to even) on edge cases and random bit patterns: the
+// range-limited forms (`_bits`, with their ok flag) and the full-range forms (`_all`, bit for
+// bit on every input but NaN, where both must give a NaN of the same sign).
+// Prints "<checked> <mismatches> <not_ok_in_range> <checked_all> <mismatches_all>" and exits 0.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -18,7 +20,10 @@ static uint64_t next() {  // xorshift64*
 }
 
 int main() {
-  long checked = 0, bad = 0, missed = 0;
+  long checked = 0, bad = 0, missed = 0, checked_all = 0, bad_all = 0;
+  auto same = [](uint64_t a, uint64_t b, bool nan_a, bool nan_b, bool sign_a, bool sign_b) {
+    return (nan_a || nan_b) ? (nan_a && nan_b && sign_a == sign_b) : a == b;
+  };
   auto check_d = [&](double x) {
     bool ok = false;
     const float got = rod::f32_rn_bits(x, ok);
@@ -33,32 +38,45 @@ int main() {
     } else if (in_range) {
       ++missed;
     }
+    const float all = rod::f32_rn_all(x);
+    ++checked_all;
+    if (!same(rod::fp32_bits(all), rod::fp32_bits(ref), std::isnan(all), std::isnan(ref), std::signbit(all),
+              std::signbit(ref)))
+      ++bad_all;
   };
   auto check_f = [&](float f) {
     bool ok = false;
     const double got = rod::f64_of_f32_bits(f, ok);
     const bool in_range = std::isfinite(f) && (f == 0.0f || std::fabs(f) >= std::numeric_limits<float>::min());
+    const double ref = static_cast<double>(f);
     if (ok) {
       ++checked;
-      const double ref = static_cast<double>(f);
       if (rod::fp64_bits(got) != rod::fp64_bits(ref)) ++bad;
     } else if (in_range) {
       ++missed;
     }
+    const double all = rod::f64_of_f32_all(f);
+    ++checked_all;
+    if (!same(rod::fp64_bits(all), rod::fp64_bits(ref), std::isnan(all), std::isnan(ref), std::signbit(all),
+              std::signbit(ref)))
+      ++bad_all;
   };
   const double edges[] = {0.0, -0.0, 1.0, -1.0, 0x1p-126, -0x1p-126, 0x1p-127, 0x1.fffffep127, 0x1.ffffffp127,
                           0x1.fffffefffffffp127, 0x1p128, 1e300, -1e-300, INFINITY, -INFINITY, NAN,
-                          1.0 + 0x1p-24, 1.0 + 0x1p-23 + 0x1p-24, 1.0 + 0x1p-24 + 0x1p-52, 3.0e-39, 1e-45};
+                          1.0 + 0x1p-24, 1.0 + 0x1p-23 + 0x1p-24, 1.0 + 0x1p-24 + 0x1p-52, 3.0e-39, 1e-45,
+                          0x1p-149, 0x1p-150, 0x1.0000000000001p-150, 0x1.8p-149, 0x1.4p-148, 0x1.fffffcp-127,
+                          0x1.fffffep-127, 0x1.fffffdp-127, -0x1p-160, 5e-324, 0x1.fffffffffffffp-127};
   for (double x : edges) check_d(x);
   const float fedges[] = {0.0f, -0.0f, 1.0f, std::numeric_limits<float>::min(), std::numeric_limits<float>::max(),
-                          std::numeric_limits<float>::denorm_min(), INFINITY, NAN, -3.5f};
+                          std::numeric_limits<float>::denorm_min(), INFINITY, NAN, -3.5f, -INFINITY, 0x1.fffffcp-127f,
+                          -0x1p-140f, 0x1p-149f};
   for (float f : fedges) check_f(f);
   for (int i = 0; i < 2000000; ++i) {
     const uint64_t r = next();
     // exponents spread over the whole range, and concentrated around the FP32 range
     uint64_t u = r;
     if (i & 1) {
-      const uint64_t e = 860 + (next() % 330);
+      const uint64_t e = 840 + (next() % 350);
       u = (r & 0x800FFFFFFFFFFFFFull) | (e << 52);
     }
     if (i % 4 == 2) u = (u & ~0x1FFFFFFFull) | 0x10000000ull;   // exact ties
@@ -70,6 +88,18 @@ int main() {
     std::memcpy(&f, &v, sizeof f);
     check_f(f);
   }
-  std::printf("%ld %ld %ld\n", checked, bad, missed);
+  // every seventh FP32 subnormal with its neighbouring FP64 values and the tie above it
+  for (uint32_t v = 0; v < 0x800000u; v += 7) {
+    float f;
+    std::memcpy(&f, &v, sizeof f);
+    check_f(f);
+    check_f(-f);
+    const double d = static_cast<double>(f);
+    check_d(d);
+    check_d(std::nextafter(d, 1.0));
+    check_d(std::nextafter(d, -1.0));
+    check_d(d + 0x1p-150);   // the ties between neighbouring subnormals
+  }
+  std::printf("%ld %ld %ld %ld %ld\n", checked, bad, missed, checked_all, bad_all);
   return 0;
 }

@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(AdjointParams A, LaunchSha
     const bool held = (li == 0) && rc->clamp;
     const bool hasR = li < nr - 1, hasL = li > 0;
     double tau[3];
-    element_couple<true>(P, m, i, k, hasR, hasL, tau);
+    element_couple<kFeatAll>(P, m, i, k, hasR, hasL, tau);
     double ebar = 0.0;
     for (int c = 0; c < 3; ++c) {
       const double wb = held ? 0.0 : a.WB[c * m.CE + i];

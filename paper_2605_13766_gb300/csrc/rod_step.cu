@@ -37,8 +37,8 @@ namespace {
 
 // The work of one pack, shared by the block kernel (pack in shared memory, one block) and the
 // cooperative kernel (pack in global memory, every block of the grid); stage_sync is the
-// block's or the grid's barrier.  GEN = false: the plain step (see stage_elements).
-template <int MODE, bool GEN = true>
+// block's or the grid's barrier.  FS: the feature set compiled in (see stage_elements).
+template <int MODE, int FS = kFeatAll>
 __device__ __forceinline__ void pack_body(const StepParams& P, const Pack& pk, Smem& m, int64_t n_steps, double t0,
                                           double dt, int last_half, double* acc_v, double* acc_w) {
   // a step after a latched error (non-finite state, contact overflow) is skipped: a block
@@ -74,17 +74,17 @@ __device__ __forceinline__ void pack_body(const StepParams& P, const Pack& pk, S
     const bool timed = has_time_values(P);
     if (n_steps > 0) actuation_values(P, pk, m, tbase + 0.5 * dt);
     for (int64_t s = 0; s < n_steps; ++s) {
-      stage_elements<GEN>(P, pk, m);
+      stage_elements<FS>(P, pk, m);
       stage_sync(m);
-      stage_voronoi<GEN>(P, pk, m);
+      stage_voronoi<FS>(P, pk, m);
       stage_sync(m);
       // rate updates fused with the following kinematic stage: each thread moves only the
       // elements and nodes whose rates it has just updated
       const bool last = (s == n_steps - 1);
       const double h = (last && (MODE == MODE_STEPS || last_half)) ? 0.5 * dt : dt;
       const double t = tbase + (static_cast<double>(s) + 0.5) * dt;
-      stage_rotation<MODE_STEPS, GEN>(P, pk, m, dt, h, nullptr);
-      stage_translation<MODE_STEPS, GEN>(P, pk, m, dt, nullptr, t, h);
+      stage_rotation<MODE_STEPS, FS>(P, pk, m, dt, h, nullptr);
+      stage_translation<MODE_STEPS, FS>(P, pk, m, dt, nullptr, t, h);
       // the next step's time values: their only readers (the element stage) are past a barrier;
       // the next step's element stage waits for the barrier below
       if (timed && !last) time_values(P, pk, m, t + dt);
@@ -212,20 +212,20 @@ __device__ __forceinline__ void pack_body(const StepParams& P, const Pack& pk, S
   }
 }
 
-template <int MODE, bool GEN>
+template <int MODE, int FS>
 __device__ __forceinline__ void block_pack(const StepParams& P, const LaunchShape& S, int64_t n_steps, double t0,
                                            double dt, int last_half, double* acc_v, double* acc_w) {
   extern __shared__ double smem_d[];
   const Pack pk = P.packs[blockIdx.x];
   Smem m = carve(smem_d, S);
   if (P.xf_smem_off) m.XF = reinterpret_cast<float*>(reinterpret_cast<char*>(smem_d) + P.xf_smem_off);
-  pack_body<MODE, GEN>(P, pk, m, n_steps, t0, dt, last_half, acc_v, acc_w);
+  pack_body<MODE, FS>(P, pk, m, n_steps, t0, dt, last_half, acc_v, acc_w);
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, int64_t n_steps,
                                                    double t0, double dt, int last_half, double* acc_v, double* acc_w) {
-  block_pack<MODE, true>(P, S, n_steps, t0, dt, last_half, acc_v, acc_w);
+  block_pack<MODE, kFeatAll>(P, S, n_steps, t0, dt, last_half, acc_v, acc_w);
 }
 
 // The plain step, held to 80 registers a thread for one step (no spills) and 84 for the step
@@ -234,7 +234,15 @@ __global__ void __launch_bounds__(512) pack_kernel(StepParams P, LaunchShape S, 
 template <int MODE>
 __global__ void __maxnreg__(MODE == MODE_STEPS ? 84 : 80) pack_kernel_plain(StepParams P, LaunchShape S, int64_t n_steps,
                                                   double t0, double dt, int last_half, double* acc_v, double* acc_w) {
-  block_pack<MODE, false>(P, S, n_steps, t0, dt, last_half, acc_v, acc_w);
+  block_pack<MODE, 0>(P, S, n_steps, t0, dt, last_half, acc_v, acc_w);
+}
+
+// Driven rods (actuation couples, damping or drag, and nothing else of kFeatAll): the cilia
+// carpet.
+template <int MODE>
+__global__ void __launch_bounds__(512) pack_kernel_driven(StepParams P, LaunchShape S, int64_t n_steps, double t0,
+                                                          double dt, int last_half, double* acc_v, double* acc_w) {
+  block_pack<MODE, kFeatAct | kFeatDamp>(P, S, n_steps, t0, dt, last_half, acc_v, acc_w);
 }
 
 // One pack too long for a block: its working arrays live in global memory (scratch, carved
@@ -302,15 +310,44 @@ cudaError_t launch_grid_packs(const StepParams& P, int64_t n_steps, double t0, d
   return cudaSuccess;
 }
 
-template <int MODE, bool GEN>
+template <int MODE, int FS>
 void launch_block_packs(const StepParams& P, const LaunchShape& s, dim3 grid, dim3 block, size_t smem, int64_t n_steps,
                         double t0, double dt, int last_half, double* acc_v, double* acc_w, cudaStream_t st) {
-  if constexpr (GEN) {
+  if constexpr (FS == kFeatAll) {
     cudaFuncSetAttribute(pack_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     pack_kernel<MODE><<<grid, block, smem, st>>>(P, s, n_steps, t0, dt, last_half, acc_v, acc_w);
-  } else {
+  } else if constexpr (FS == 0) {
     cudaFuncSetAttribute(pack_kernel_plain<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     pack_kernel_plain<MODE><<<grid, block, smem, st>>>(P, s, n_steps, t0, dt, last_half, acc_v, acc_w);
+  } else {
+    static_assert(FS == (kFeatAct | kFeatDamp), "no kernel for this feature set");
+    cudaFuncSetAttribute(pack_kernel_driven<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    pack_kernel_driven<MODE><<<grid, block, smem, st>>>(P, s, n_steps, t0, dt, last_half, acc_v, acc_w);
+  }
+}
+
+// The step's features (kFeat* bits) that some rod of the system uses.
+int step_features(const StepParams& P) {
+  int f = 0;
+  if (P.rest_sigma || P.rest_kappa) f |= kFeatRest;
+  if (P.elem_couple || P.magnet || P.arc0 || P.n_walls > 0 || P.has_tip) f |= kFeatExt;
+  if (P.has_act) f |= kFeatAct;
+  if (P.has_damp_lin || P.has_damp_rot) f |= kFeatDamp;
+  return f;
+}
+
+// Launch the kernel of the smallest instantiated feature set that covers the system's.
+template <int MODE>
+void launch_feature_packs(const StepParams& P, const LaunchShape& s, dim3 grid, dim3 block, size_t smem,
+                          int64_t n_steps, double t0, double dt, int last_half, double* acc_v, double* acc_w,
+                          cudaStream_t st) {
+  const int f = step_features(P);
+  if (f == 0) {
+    launch_block_packs<MODE, 0>(P, s, grid, block, smem, n_steps, t0, dt, last_half, acc_v, acc_w, st);
+  } else if ((f & ~(kFeatAct | kFeatDamp)) == 0) {
+    launch_block_packs<MODE, kFeatAct | kFeatDamp>(P, s, grid, block, smem, n_steps, t0, dt, last_half, acc_v, acc_w, st);
+  } else {
+    launch_block_packs<MODE, kFeatAll>(P, s, grid, block, smem, n_steps, t0, dt, last_half, acc_v, acc_w, st);
   }
 }
 
@@ -340,42 +377,29 @@ cudaError_t launch_pack_kernel(const StepParams& P0, const LaunchShape& s, int m
     const LaunchHook& h; int c; cudaStream_t s;
     ~After() { h.after(c, s); }
   } after_guard{hook, cls, st};
-  // the plain step (GEN = false) when no rod uses a feature it leaves out
-  const bool plain = !P.rest_sigma && !P.rest_kappa && !P.elem_couple && !P.has_act && !P.magnet && !P.arc0 &&
-                     P.n_walls == 0 && !P.has_tip && !P.has_damp_lin && !P.has_damp_rot;
   cudaError_t e = cudaSuccess;
   switch (mode) {
     case MODE_STEPS: {
-      if (P.n_packs > 0) {
-        if (plain) {
-          launch_block_packs<MODE_STEPS, false>(P, s, grid, block, smem, n_steps, t0, dt, last_half, acc_v, acc_w, st);
-        } else {
-          launch_block_packs<MODE_STEPS, true>(P, s, grid, block, smem, n_steps, t0, dt, last_half, acc_v, acc_w, st);
-        }
-      }
+      if (P.n_packs > 0)
+        launch_feature_packs<MODE_STEPS>(P, s, grid, block, smem, n_steps, t0, dt, last_half, acc_v, acc_w, st);
       if (P.n_long) e = launch_grid_packs<MODE_STEPS>(P, n_steps, t0, dt, last_half, acc_v, acc_w, st);
       break;
     }
     case MODE_ONE_STEP: {
-      if (P.n_packs > 0) {
-        if (plain) {
-          launch_block_packs<MODE_ONE_STEP, false>(P, s, grid, block, smem, n_steps, t0, dt, last_half, acc_v, acc_w, st);
-        } else {
-          launch_block_packs<MODE_ONE_STEP, true>(P, s, grid, block, smem, n_steps, t0, dt, last_half, acc_v, acc_w, st);
-        }
-      }
+      if (P.n_packs > 0)
+        launch_feature_packs<MODE_ONE_STEP>(P, s, grid, block, smem, n_steps, t0, dt, last_half, acc_v, acc_w, st);
       if (P.n_long) e = launch_grid_packs<MODE_ONE_STEP>(P, n_steps, t0, dt, last_half, acc_v, acc_w, st);
       break;
     }
     case MODE_KIN_HALF: {
       if (P.n_packs > 0)
-        launch_block_packs<MODE_KIN_HALF, true>(P, s, grid, block, smem, n_steps, t0, dt, last_half, acc_v, acc_w, st);
+        launch_block_packs<MODE_KIN_HALF, kFeatAll>(P, s, grid, block, smem, n_steps, t0, dt, last_half, acc_v, acc_w, st);
       if (P.n_long) e = launch_grid_packs<MODE_KIN_HALF>(P, n_steps, t0, dt, last_half, acc_v, acc_w, st);
       break;
     }
     case MODE_RHS: {
       if (P.n_packs > 0)
-        launch_block_packs<MODE_RHS, true>(P, s, grid, block, smem, n_steps, t0, dt, last_half, acc_v, acc_w, st);
+        launch_block_packs<MODE_RHS, kFeatAll>(P, s, grid, block, smem, n_steps, t0, dt, last_half, acc_v, acc_w, st);
       if (P.n_long) e = launch_grid_packs<MODE_RHS>(P, n_steps, t0, dt, last_half, acc_v, acc_w, st);
       break;
     }

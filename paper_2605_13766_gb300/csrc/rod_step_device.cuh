@@ -231,14 +231,19 @@ __device__ __forceinline__ void kinematic(const StepParams& P, const Pack& pk, S
 
 // --------------------------------------------------------------- dynamic stage (a3-a7, a10, a2)
 
-// The stage functions take GEN = false for the plain step: circular sections without rest
-// strain or rest curvature, and no external element couples, actuation, magnetic field,
-// muscles, walls, tip forces or damping.  Each of those tests is then false at compile time, so
-// no predicated instruction of theirs reaches the FP64 pipe; GEN = true tests the parameters.
+// Feature sets of the stage functions (template argument FS): a stage compiled for a set tests
+// only the features in it, the others being false at compile time, so that none of their
+// predicated instructions reaches the FP64 pipe.  FS = 0 is the plain step (circular sections
+// without rest strain or curvature, no loads but gravity and contact); kFeatAll tests them all.
+constexpr int kFeatRest = 1;   // rest strain or rest curvature
+constexpr int kFeatExt = 2;    // element couples, magnetic field, muscles, walls, tip forces
+constexpr int kFeatAct = 4;    // actuation couples
+constexpr int kFeatDamp = 8;   // linear or rotational damping, drag
+constexpr int kFeatAll = 15;
 
 // Stage A (elements): geometry, shear strain, internal force, shear couple, transport couples,
 // damping and external couples.
-template <bool GEN = true>
+template <int FS = kFeatAll>
 __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& pk, Smem& m) {
   const int Ep = pk.nelem;
   for (int i = m.t0; i < Ep; i += m.ts) {
@@ -265,7 +270,7 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
     for (int a = 0; a < 3; ++a) Ql[a] = fma(q[3 * a], l[0], fma(q[3 * a + 1], l[1], q[3 * a + 2] * l[2]));
     // n / e = S sigma / e  (the 1/e of the internal force, folded once), and the shear couple
     // ((Q t) x n) rl = (Ql x n) rl / ell = Ql x (n / e)
-    if (GEN && P.rest_sigma) {
+    if ((FS & kFeatRest) && P.rest_sigma) {
       const double irl = __ldg(P.inv_rl + ge);
       sg[0] = Ql[0] * irl;
       sg[1] = Ql[1] * irl;
@@ -300,19 +305,19 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
     // rl (de/dt / e^2 - damp_rot) = ie^2 ((l . dv) rs) - rl damp_rot   (rl / (ell rl e^2) = ie^2 rs)
     const double ldv = fma(l[0], dv[0], fma(l[1], dv[1], l[2] * dv[2]));
     const double k1 = (rl * ie) * __ldg(&rc->rhoI_12);
-    const double k2 = (GEN && P.has_damp_rot) ? fma(ie * ie, ldv * rs, -rl * __ldg(&rc->damp_rot)) : (ie * ie) * (ldv * rs);
+    const double k2 = ((FS & kFeatDamp) && P.has_damp_rot) ? fma(ie * ie, ldv * rs, -rl * __ldg(&rc->damp_rot)) : (ie * ie) * (ldv * rs);
     tc[0] = fma(k1, w[1] * w[2], tc[0]);
     tc[1] = fma(-k1, w[0] * w[2], tc[1]);
     const double k2j = k2 * __ldg(&rc->rhoI[0]);
     tc[0] = fma(k2j, w[0], tc[0]);
     tc[1] = fma(k2j, w[1], tc[1]);
     tc[2] = fma(k2 * __ldg(&rc->rhoI[2]), w[2], tc[2]);
-    if (GEN && P.elem_couple) {
+    if ((FS & kFeatExt) && P.elem_couple) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) tc[c] += __ldg(P.elem_couple + c * P.E + ge);
     }
-    if (GEN && P.has_act && (i - m.rel0[r]) == rc->act_elem) tc[0] += m.ACT[r];
-    if (GEN && P.magnet) {
+    if ((FS & kFeatAct) && P.has_act && (i - m.rel0[r]) == rc->act_elem) tc[0] += m.ACT[r];
+    if ((FS & kFeatExt) && P.magnet) {
       // magnetic couple rl (m x (Q b)), Q b: the field in the element's frame
       double qb[3], mg[3];
 #pragma unroll
@@ -323,7 +328,7 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
       tc[1] += fma(mg[2], qb[0], -mg[0] * qb[2]);
       tc[2] += fma(mg[0], qb[1], -mg[1] * qb[0]);
     }
-    if (GEN && P.arc0 && rc->muscle_amp != 0.0) {
+    if ((FS & kFeatExt) && P.arc0 && rc->muscle_amp != 0.0) {
       // muscle couples about d1 at the Voronoi points on both sides: tau_{i-1} - tau_i
       const int li = i - m.rel0[r], nr = m.rel0[r + 1] - m.rel0[r];
       const double t = m.BF[3], sl = __ldg(P.arc0 + ge), sr = sl + rl;
@@ -344,7 +349,7 @@ __device__ __forceinline__ void stage_elements(const StepParams& P, const Pack& 
 // points, so each point stores its two shares: PP = P + T/2 (to the element on its left) and
 // TT = T/2 - P (to the element on its right).  For a circular section without rest curvature
 // T_3 = 0: PP holds P_3 and TT's third component is not written.
-template <bool GEN = true>
+template <int FS = kFeatAll>
 __device__ __forceinline__ void stage_voronoi(const StepParams& P, const Pack& pk, Smem& m) {
   const int Vp = pk.nvor;
   for (int k = m.t0; k < Vp; k += m.ts) {
@@ -380,7 +385,7 @@ __device__ __forceinline__ void stage_voronoi(const StepParams& P, const Pack& p
     const double s4 = fma(u0, u0, fma(u1, u1, u2 * u2));  // |u|^2 = 4 sin^2(theta)
     const double f = theta_over_sin(s4, qa, qb);
     const double ls = m.ELL[i] + m.ELL[i + 1];   // eps = ls / (2D)
-    if (GEN && P.rest_kappa) {
+    if ((FS & kFeatRest) && P.rest_kappa) {
       const double i2D = __ldg(P.inv_2D + gv);
       const double ieps = rcp_nr(ls * i2D);
       const double ie3 = ieps * ieps * ieps;
@@ -419,13 +424,13 @@ __device__ __forceinline__ void stage_voronoi(const StepParams& P, const Pack& p
 
 // The element couple of element i from its Voronoi points (right: k, if hasR; left: k - 1, if
 // hasL) and its own couple TA: P_k - P_{k-1} + (T_k + T_{k-1}) / 2 + TA as PP_k + TT_{k-1} + TA.
-template <bool GEN = true>
+template <int FS = kFeatAll>
 __device__ __forceinline__ void element_couple(const StepParams& P, const Smem& m, int i, int k, bool hasR, bool hasL,
                                                double tau[3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const double Ar = hasR ? m.PP[c * m.CV + k] : 0.0;
-    if (c == 2 && !(GEN && P.rest_kappa)) {
+    if (c == 2 && !((FS & kFeatRest) && P.rest_kappa)) {
       const double Al = hasL ? m.PP[c * m.CV + k - 1] : 0.0;
       tau[c] = (Ar - Al) + m.TA[c * m.CE + i];
     } else {
@@ -437,7 +442,7 @@ __device__ __forceinline__ void element_couple(const StepParams& P, const Smem& 
 
 // Stage C (elements): bending couple from the difference and trapezoid operators, angular
 // acceleration e J^{-1} tau, rate update and constraint; optional kinematic rotation.
-template <int MODE, bool GEN = true>
+template <int MODE, int FS = kFeatAll>
 __device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& pk, Smem& m, double dt, double h,
                                                double* acc_w) {
   const int Ep = pk.nelem;
@@ -452,7 +457,7 @@ __device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& 
     const int k = i - r;                     // right Voronoi point (valid if li < nr-1)
     const bool hasR = li < nr - 1, hasL = li > 0;
     double tau[3];
-    element_couple<GEN>(P, m, i, k, hasR, hasL, tau);
+    element_couple<FS>(P, m, i, k, hasR, hasL, tau);
     const bool held = (li == 0) && rc->clamp;
     if (MODE == MODE_RHS) {
       const double ke = m.EDIL[i];
@@ -472,7 +477,7 @@ __device__ __forceinline__ void stage_rotation(const StepParams& P, const Pack& 
 }
 
 // Stage D (nodes): internal force difference, external forces, velocity update + constraint.
-template <int MODE, bool GEN = true>
+template <int MODE, int FS = kFeatAll>
 __device__ __forceinline__ void stage_translation(const StepParams& P, const Pack& pk, Smem& m, double dt,
                                                   double* acc_v, double t, double h = 0.0) {
   const int Np = pk.nnode;
@@ -517,11 +522,11 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
         F[c] += fa + fb;
       }
     }
-    if (GEN && P.has_tip && lj == nr) {
+    if ((FS & kFeatExt) && P.has_tip && lj == nr) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) F[c] += __ldg(&rc->tip[c]);
     }
-    for (int k = 0; k < (GEN ? P.n_walls : 0); ++k) {
+    for (int k = 0; k < ((FS & kFeatExt) ? P.n_walls : 0); ++k) {
       // node sphere (radius of the rod) against the half-space n . (x - p - u t) >= 0
       double d[3], vr[3];
 #pragma unroll
@@ -554,7 +559,7 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
     } else {
       // v += dt (F/m - c v + g)  as  v (1 - dt c) + (dt/m) F + dt g  (keep = 1 without damping)
       const double dtim = dt * im;
-      if (GEN) {
+      if (FS & kFeatDamp) {
         const double keep = P.has_damp_lin ? fma(-dt, dl, 1.0) : 1.0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {

@@ -4,8 +4,9 @@
 // at the rate of an FP64 fused multiply-add, which the step kernels are bound by.  These
 // functions do the same conversions with integer operations on the bit patterns.  The `_bits`
 // forms cover the numbers whose conversion stays within the FP32 normal range (and zero) and
-// report `ok = false` for the rest (the Newton seeds below need that range); the `_all` forms
-// cover every input (subnormal results, overflow, infinities, NaN), so a caller has no
+// report `ok = false` for the rest (the Newton seeds below need that range); the `_ftz` forms
+// flush what lies outside it, without a branch; the `_all` forms cover every input (subnormal
+// results, overflow, infinities, NaN), so a caller has no
 // conversion instruction to fall back to (a fallback branch that short compiles as a predicated
 // instruction, which issues on the FP64 pipe for every warp).  Host-compilable, so the
 // bit logic is tested on the CPU against the compiler's own conversions.  Device code also gets
@@ -140,6 +141,37 @@ ROD_FP_HD double f64_of_f32_all(float f) {
   return fp64_from_bits(sign | (static_cast<uint64_t>(p + 874) << 52) | frac);
 }
 
+// x rounded to the nearest FP32 (ties to even) when |x| lies in the FP32 normal range or is zero;
+// smaller magnitudes give a zero of x's sign, larger ones (and infinities, NaN) an infinity of
+// x's sign.  Branch-free integer operations, for code where neither those edge ranges nor a
+// conversion instruction are wanted.
+ROD_FP_HD float f32_rn_ftz(double x) {
+  const uint64_t u = fp64_bits(x);
+  const uint32_t hi = static_cast<uint32_t>(u >> 32), lo = static_cast<uint32_t>(u);
+  const uint32_t e = (hi >> 20) & 0x7FFu;
+  const uint32_t sign = hi & 0x80000000u;
+  uint32_t bits = sign | ((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const uint32_t rest = lo & 0x1FFFFFFFu;
+  bits += (rest > 0x10000000u || (rest == 0x10000000u && (bits & 1u))) ? 1u : 0u;
+  bits = e < 897u ? sign : bits;
+  bits = e > 1150u ? (sign | 0x7F800000u) : bits;
+  return fp32_from_bits(bits);
+}
+
+// An FP32 value widened to FP64 exactly, except that FP32 subnormals give a zero of their sign;
+// infinities and NaN (with its payload) carry over.  Branch-free integer operations.
+ROD_FP_HD double f64_of_f32_ftz(float f) {
+  const uint32_t b = fp32_bits(f);
+  const uint32_t e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+  const uint32_t sign = b & 0x80000000u;
+  uint32_t hi = sign | ((e + 896u) << 20) | (m >> 3);
+  uint32_t lo = m << 29;
+  hi = e == 0xFFu ? (sign | 0x7FF00000u | (m >> 3)) : hi;
+  hi = e == 0u ? sign : hi;
+  lo = e == 0u ? 0u : lo;
+  return fp64_from_bits((static_cast<uint64_t>(hi) << 32) | lo);
+}
+
 // An FP32 value widened to FP64 exactly, for zero and FP32 normal numbers (ok = false for
 // subnormals, infinities and NaN).
 ROD_FP_HD double f64_of_f32_bits(float f, bool& ok) {
@@ -189,22 +221,14 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
   return fma(h0, r, y0);
 }
 
-// A double rounded to FP32 and an FP32 value widened to FP64: the normal-range integer form with
-// the conversion instruction as the fallback.  The fallback compiles as a predicated instruction
-// that issues for every warp, one FP64-pipe slot per conversion; code bound by the FP64 pipe
-// (the step kernels) takes f32_rn_all / f64_of_f32_all instead, whose extra integer work costs
-// more than that slot on a latency-bound path (the surrogate's features and update).
-__device__ __forceinline__ float f32_rn(double x) {
-  bool ok;
-  const float f = f32_rn_bits(x, ok);
-  return ok ? f : static_cast<float>(x);
-}
-
-__device__ __forceinline__ double f64_of(float f) {
-  bool ok;
-  const double d = f64_of_f32_bits(f, ok);
-  return ok ? d : static_cast<double>(f);
-}
+// A double rounded to FP32 and an FP32 value widened to FP64 for the surrogate's features and
+// update: the branch-free forms (magnitudes outside the FP32 normal range flushed, see above).
+// A form with the conversion instruction as the fallback for those ranges compiles to a
+// predicated instruction that issues on the FP64 pipe for every warp, and the full-range
+// integer forms cost more integer work than that slot saves on the surrogate's latency-bound
+// path; the step kernels round with f32_rn_all.
+__device__ __forceinline__ float f32_rn(double x) { return f32_rn_ftz(x); }
+__device__ __forceinline__ double f64_of(float f) { return f64_of_f32_ftz(f); }
 
 #endif  // __CUDACC__
 

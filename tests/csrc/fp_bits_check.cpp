@@ -1,8 +1,11 @@
 // Checks the integer-pipe FP64 <-> FP32 conversions of rod_fp.h against the host compiler's own
 // conversions (round to nearest, ties to even) on edge cases and random bit patterns: the
 // range-limited forms (`_bits`, with their ok flag) and the full-range forms (`_all`, bit for
-// bit on every input but NaN, where both must give a NaN of the same sign).
-// Prints "<checked> <mismatches> <not_ok_in_range> <checked_all> <mismatches_all>" and exits 0.
+// bit on every input but NaN, where both must give a NaN of the same sign), and the flushing
+// forms (`_ftz`: bit for bit in the FP32 normal range, signed zero below it, signed infinity
+// above it and for NaN in the rounding; FP32 subnormals widen to signed zero).
+// Prints "<checked> <mismatches> <not_ok_in_range> <checked_all> <mismatches_all>
+// <checked_ftz> <mismatches_ftz>" and exits 0.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -20,7 +23,7 @@ static uint64_t next() {  // xorshift64*
 }
 
 int main() {
-  long checked = 0, bad = 0, missed = 0, checked_all = 0, bad_all = 0;
+  long checked = 0, bad = 0, missed = 0, checked_all = 0, bad_all = 0, checked_ftz = 0, bad_ftz = 0;
   auto same = [](uint64_t a, uint64_t b, bool nan_a, bool nan_b, bool sign_a, bool sign_b) {
     return (nan_a || nan_b) ? (nan_a && nan_b && sign_a == sign_b) : a == b;
   };
@@ -43,6 +46,15 @@ int main() {
     if (!same(rod::fp32_bits(all), rod::fp32_bits(ref), std::isnan(all), std::isnan(ref), std::signbit(all),
               std::signbit(ref)))
       ++bad_all;
+    // the flushing form: the compiler's result wherever |x| is zero or in [2^-126, 2^128)
+    const float ftz = rod::f32_rn_ftz(x);
+    const uint32_t sgn = std::signbit(x) ? 0x80000000u : 0u;
+    uint32_t want;
+    if (std::isnan(x) || ax >= 0x1p128) want = sgn | 0x7F800000u;
+    else if (ax < 0x1p-126) want = sgn;
+    else want = rod::fp32_bits(ref);
+    ++checked_ftz;
+    if (rod::fp32_bits(ftz) != want) ++bad_ftz;
   };
   auto check_f = [&](float f) {
     bool ok = false;
@@ -60,6 +72,13 @@ int main() {
     if (!same(rod::fp64_bits(all), rod::fp64_bits(ref), std::isnan(all), std::isnan(ref), std::signbit(all),
               std::signbit(ref)))
       ++bad_all;
+    const double ftz = rod::f64_of_f32_ftz(f);
+    const bool sub = std::fpclassify(f) == FP_SUBNORMAL;
+    ++checked_ftz;
+    if (sub ? rod::fp64_bits(ftz) != (std::signbit(f) ? 0x8000000000000000ull : 0ull)
+            : !same(rod::fp64_bits(ftz), rod::fp64_bits(ref), std::isnan(ftz), std::isnan(ref), std::signbit(ftz),
+                    std::signbit(ref)))
+      ++bad_ftz;
   };
   const double edges[] = {0.0, -0.0, 1.0, -1.0, 0x1p-126, -0x1p-126, 0x1p-127, 0x1.fffffep127, 0x1.ffffffp127,
                           0x1.fffffefffffffp127, 0x1p128, 1e300, -1e-300, INFINITY, -INFINITY, NAN,
@@ -100,6 +119,6 @@ int main() {
     check_d(std::nextafter(d, -1.0));
     check_d(d + 0x1p-150);   // the ties between neighbouring subnormals
   }
-  std::printf("%ld %ld %ld %ld %ld\n", checked, bad, missed, checked_all, bad_all);
+  std::printf("%ld %ld %ld %ld %ld %ld %ld\n", checked, bad, missed, checked_all, bad_all, checked_ftz, bad_ftz);
   return 0;
 }

@@ -565,13 +565,14 @@ __device__ __forceinline__ void stage_translation(const StepParams& P, const Pac
         for (int c = 0; c < 3; ++c) {
           const double vj = m.VN[c * m.CN + j];
           const double base = P.has_damp_lin ? (P.has_gravity ? fma(vj, keep, dtg[c]) : vj * keep)
-                                             : (P.has_gravity ? vj + dtg[c] : vj);
+                                             : (P.has_gravity ? fma(dt, P.gravity[c], vj) : vj);
           m.VN[c * m.CN + j] = held ? 0.0 : fma(F[c], dtim, base);
         }
       } else {
-        // no damping; dtg is zero without gravity
+        // no damping: v + dt g as one FMA, as the general kernel forms it (gravity zero: v)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) m.VN[c * m.CN + j] = held ? 0.0 : fma(F[c], dtim, m.VN[c * m.CN + j] + dtg[c]);
+        for (int c = 0; c < 3; ++c)
+          m.VN[c * m.CN + j] = held ? 0.0 : fma(F[c], dtim, fma(dt, P.gravity[c], m.VN[c * m.CN + j]));
       }
       // the following kinematic half/full step of this node (it reads only its own x, v)
       if (h != 0.0) kin_node(P, pk, m, j, h);
